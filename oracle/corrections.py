@@ -1,0 +1,184 @@
+"""Precomputation of all near and self corrections and the corrected layer potential
+(Sec. 5.2 Precomputation, Sec. 5.3 subtract-and-add, Sec. 4.4 Eq. for I(x)).
+
+Order of steps (Sec. 5.2): geometry -> near lists -> far order q_j (Eq. qj) and the
+annulus rule order -> self weights S_j -> near weights N_j (adaptive inside
+eta_1 R_j, one oversampled rule in the annulus) -> net corrections.
+
+Net correction (subtract-and-add, Sec. 5.3, folded into the stored entry):
+    c_{t,l} = a^j_l(x_t) - s^j_l(x_t),
+where a is the self or near point weight and s the weight the smooth rule q_j puts
+on node l for the same target.  Apply then computes
+    u(x_t) = sum_j sum_{q in rule q_j} K(x_t, X_q) J_q w_q sigma~_q + sum_row c_{t,col} sigma_col.
+Rows are targets; within a row, patches ascend, and each patch contributes its n
+nodes in node order.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import geometry, nearlist, quadrature, rules
+from .quadrature import Kern
+
+
+@dataclass
+class Params:
+    eps: float
+    eta: float = -1.0            # <= 0: default by degree (Sec. 4.1)
+    eta1: float = 1.25           # Remark on eta_1
+    eps_loosen: float = 1.0      # termination loosening of Sec. 4.3 Remark (unstated there)
+    max_depth: int = 24
+    m_max: int = 24              # largest smooth rule of the family
+    self_order: int = 0          # 0: rules.default_self_order(eps)
+    leaf_order: int = 0          # 0: the patch's far order q_j
+    test_dirs: np.ndarray | None = None
+
+
+def fibonacci_dirs(n: int = 15) -> np.ndarray:
+    """Default test directions: z_k = 1 - (2k+1)/n, azimuth k pi (3 - sqrt 5)."""
+    k = np.arange(n, dtype=np.float64)
+    z = 1.0 - (2.0 * k + 1.0) / n
+    r = np.sqrt(1.0 - z * z)
+    phi = k * np.pi * (3.0 - np.sqrt(5.0))
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+@dataclass
+class Corrections:
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    q: np.ndarray                 # far order per patch
+    q_near: np.ndarray            # annulus order per patch (0: no annulus targets)
+    q_saturated: np.ndarray
+    eta: np.ndarray
+    eta1: np.ndarray
+    near: list
+    patches: list
+    pair_stats: dict = field(default_factory=dict)   # (t, j) -> dict
+    depth_hit: bool = False
+
+
+def patch_of_node(node_off, tgt_node):
+    tp = np.full(tgt_node.shape, -1, dtype=np.int64)
+    on = tgt_node >= 0
+    tp[on] = np.searchsorted(node_off, tgt_node[on], side="right") - 1
+    return tp
+
+
+def gen_corrections(deg, node_off, xyz, tgt_xyz, tgt_node, kind, k, alpha=1.0, beta=0.0,
+                    params: Params = None, patches=None, only_patches=None):
+    """All corrections for the targets; `only_patches` restricts the work to some patches
+    (rows then hold only those patches' entries)."""
+    p = params
+    kern = Kern(kind, k, alpha, beta)
+    deg = np.asarray(deg)
+    node_off = np.asarray(node_off)
+    tgt_node = np.asarray(tgt_node)
+    if patches is None:
+        patches = geometry.make_patches(deg, node_off, xyz)
+    npat = len(patches)
+    tgt_patch = patch_of_node(node_off, tgt_node)
+    eta = np.array([p.eta if p.eta > 0 else geometry.default_eta(int(d)) for d in deg])
+    eta1 = np.minimum(p.eta1, eta)
+    centers = np.array([pt.c for pt in patches])
+    radii = np.array([pt.R for pt in patches])
+    near = nearlist.near_lists(centers, radii, eta, eta1, tgt_xyz, tgt_patch)
+    dirs = fibonacci_dirs() if p.test_dirs is None else np.asarray(p.test_dirs)
+    self_order = p.self_order if p.self_order > 0 else rules.default_self_order(p.eps)
+
+    work = range(npat) if only_patches is None else only_patches
+    q = np.zeros(npat, dtype=np.int64)
+    q_near = np.zeros(npat, dtype=np.int64)
+    q_sat = np.zeros(npat, dtype=bool)
+    entries = {}          # (t, j) -> values [n]
+    stats = {}
+    depth_hit = False
+    for j in work:
+        pt = patches[j]
+        ids, adaptive, d2 = near[j]
+        m_min = (pt.d + 2) // 2
+        # far order q_j (Sec. 4.2, Eq. qj)
+        far_t, add_sphere = nearlist.far_test_targets(ids, d2)
+        F = [tgt_xyz[:, t] for t in far_t]
+        if add_sphere:
+            F += [pt.c + eta[j] * pt.R * dvec for dvec in dirs]
+        q[j], q_sat[j], _ = quadrature.far_order(pt, F, kern, p.eps, m_min, p.m_max)
+        # annulus rule order (reading): 15 points on the eta_1 sphere + 10 nearest annulus targets
+        if (~adaptive).any():
+            F1 = [pt.c + eta1[j] * pt.R * dvec for dvec in dirs]
+            F1 += [tgt_xyz[:, t] for t in nearlist.annulus_test_targets(ids, adaptive, d2)]
+            q_near[j], sat, _ = quadrature.far_order(pt, F1, kern, p.eps, m_min, p.m_max)
+            q_sat[j] |= sat
+        # near weights
+        leaf_m = p.leaf_order if p.leaf_order > 0 else int(q[j])
+        cache = quadrature.LeafCache(pt, leaf_m)
+        tol0 = p.eps * p.eps_loosen * pt.dj / pt.normV
+        an_rule = rules.conical_rule(int(q_near[j])) if q_near[j] > 0 else None
+        for t, ad in zip(ids, adaptive):
+            x = tgt_xyz[:, t]
+            if ad:
+                I, st = quadrature.adaptive_moments(cache, x, kern, tol0, p.max_depth)
+                depth_hit |= st["depth_hit"]
+                st["kind"] = "adaptive"
+            else:
+                I = quadrature.rule_moments(pt, x, *an_rule, kern)
+                st = {"kind": "annulus"}
+            a = pt.V.T @ I
+            s = quadrature.smooth_weights(pt, x, int(q[j]), kern)
+            entries[(int(t), j)] = a - s
+            stats[(int(t), j)] = st
+        # self weights
+        for t in np.nonzero(tgt_patch == j)[0]:
+            i = int(tgt_node[t] - node_off[j])
+            x = tgt_xyz[:, t]
+            a = quadrature.self_weights(pt, i, x, kern, self_order)
+            s = quadrature.smooth_weights(pt, x, int(q[j]), kern)
+            entries[(int(t), j)] = a - s
+            stats[(int(t), j)] = {"kind": "self"}
+
+    nt = tgt_xyz.shape[1]
+    keys = sorted(entries.keys())
+    counts = np.zeros(nt + 1, dtype=np.int64)
+    for (t, j) in keys:
+        counts[t + 1] += patches[j].n
+    row_ptr = np.cumsum(counts)
+    col = np.empty(int(row_ptr[-1]), dtype=np.int64)
+    val = np.empty(int(row_ptr[-1]), dtype=np.complex128)
+    pos = 0
+    for (t, j) in keys:
+        n = patches[j].n
+        col[pos:pos + n] = node_off[j] + np.arange(n)
+        val[pos:pos + n] = entries[(t, j)]
+        pos += n
+    return Corrections(row_ptr, col, val, q, q_near, q_sat, eta, eta1, near, patches, stats,
+                       depth_hit)
+
+
+def far_sources(patches, q, sigma, node_off):
+    """Oversampled sources of the smooth rules q_j: positions, normals, w_q sigma~_q (Sec. 4.2
+    Remark: sigma~_q = sum_nm s_nm K_nm(u_q, v_q), s = V sigma)."""
+    Xs, Ns, str_ = [], [], []
+    for j, pt in enumerate(patches):
+        ru, rv, rw = rules.conical_rule(int(q[j]))
+        X, N, K = pt.eval(ru, rv)
+        s = pt.V @ sigma[node_off[j]:node_off[j + 1]]
+        Xs.append(X)
+        Ns.append(N)
+        str_.append(rw * (K.T @ s))
+    return np.concatenate(Xs, axis=1), np.concatenate(Ns, axis=1), np.concatenate(str_)
+
+
+def apply_corrected(corr: Corrections, node_off, sigma, tgt_xyz, kind, k, alpha=1.0, beta=0.0):
+    """u(x_t) = far sum over all oversampled sources + CSR correction (Sec. 5.3)."""
+    kern = Kern(kind, k, alpha, beta)
+    X, N, strength = far_sources(corr.patches, corr.q, sigma, node_off)
+    nt = tgt_xyz.shape[1]
+    u = np.zeros(nt, dtype=np.complex128)
+    for t in range(nt):
+        u[t] = (kern(tgt_xyz[:, t], X, N) * strength).sum()
+        a, b = corr.row_ptr[t], corr.row_ptr[t + 1]
+        u[t] += (corr.val[a:b] * sigma[corr.col[a:b]]).sum()
+    return u

@@ -1,0 +1,96 @@
+"""Patch geometry from node samples (Sec. 3.1-3.2, Sec. 4 centroid and radius).
+
+x_nm = sum_l V[(nm), l] y_l (chart expansion, Sec. 3.2); X, X_u, X_v from the
+Koornwinder series; n = X_u x X_v (unnormalized), J = |n| (Eq. loc).
+
+Readings:
+  * Centroid c_j (Sec. 4, printed as the unnormalized, unweighted integral of X
+    over T0): the area-weighted centroid on the node rule,
+    c_j = sum_l w_l J_l y_l / sum_l w_l J_l.
+  * Radius R_j (Eq. rjdef, the minimal ball about c_j containing the patch): the
+    largest |X - c_j| over the nodes and the 153 vertices of the level-4 uniform
+    subdivision of T0, i.e. (a/16, b/16), a+b <= 16.
+  * d_j = min_l sqrt(J_l w_l) (Sec. 4.2).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import koornwinder as kw
+from . import rules
+
+
+@dataclass
+class Patch:
+    d: int
+    y: np.ndarray          # [3, n] node coordinates
+    coefs: np.ndarray      # [n, 3] Koornwinder coefficients x_nm
+    V: np.ndarray          # [n, n]
+    normV: float
+    w: np.ndarray          # [n] node weights
+    J: np.ndarray          # [n] Jacobian at the nodes
+    c: np.ndarray          # [3] centroid
+    R: float               # radius
+    dj: float              # min sqrt(J w)
+
+    @property
+    def n(self) -> int:
+        return kw.n_basis(self.d)
+
+    def eval(self, u, v):
+        """X, n = X_u x X_v at reference points; returns (X [3,P], N [3,P], K [n,P])."""
+        K, Ku, Kv = kw.basis(self.d, u, v, derivs=True)
+        X = self.coefs.T @ K
+        Xu = self.coefs.T @ Ku
+        Xv = self.coefs.T @ Kv
+        N = np.cross(Xu, Xv, axis=0)
+        return X, N, K
+
+
+_TABLES: dict = {}
+
+
+def tables(d: int):
+    if d not in _TABLES:
+        V = rules.vals_to_coefs(d)
+        _TABLES[d] = (V, float(np.linalg.norm(V, 2)), rules.interp_weights(d), rules.interp_nodes(d))
+    return _TABLES[d]
+
+
+def sample_points_level4():
+    a, b = np.meshgrid(np.arange(17), np.arange(17), indexing="ij")
+    keep = (a + b) <= 16
+    return a[keep] / 16.0, b[keep] / 16.0
+
+
+def make_patch(d: int, y: np.ndarray) -> Patch:
+    V, nV, w, (un, vn) = tables(d)
+    coefs = V @ y.T
+    K, Ku, Kv = kw.basis(d, un, vn, derivs=True)
+    Xu = coefs.T @ Ku
+    Xv = coefs.T @ Kv
+    J = np.linalg.norm(np.cross(Xu, Xv, axis=0), axis=0)
+    wJ = w * J
+    c = (y * wJ[None, :]).sum(axis=1) / wJ.sum()
+    su, sv = sample_points_level4()
+    Xs = coefs.T @ kw.basis(d, su, sv)
+    R = max(np.linalg.norm(Xs - c[:, None], axis=0).max(),
+            np.linalg.norm(y - c[:, None], axis=0).max())
+    dj = float(np.sqrt(J * w).min())
+    return Patch(d, y, coefs, V, nV, w, J, c, float(R), dj)
+
+
+def make_patches(deg, node_off, xyz):
+    return [make_patch(int(deg[j]), xyz[:, node_off[j]:node_off[j + 1]]) for j in range(len(deg))]
+
+
+def default_eta(d: int) -> float:
+    """eta by the paper's order p = d+1: 2.75 (p <= 4), 2 (4 < p <= 8), 1.25 (p > 8) (Sec. 4.1, 5.2)."""
+    p = d + 1
+    if p <= 4:
+        return 2.75
+    if p <= 8:
+        return 2.0
+    return 1.25

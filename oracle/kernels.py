@@ -1,0 +1,37 @@
+"""Layer-potential kernels times the area element (Sec. 3, Eq. greenfunhelm, sldef, dldef).
+
+G_k(x,y) = e^{ik|x-y|} / (4 pi |x-y|).
+Single layer: K_S J = G_k(x, X) |n|.
+Double layer: n(y).grad_y G_k J; with n = X_u x X_v unnormalized this is
+    n.(x-y) (1 - ik r) e^{ikr} / (4 pi r^3).
+Combined field (Eq. urep, inteq): alpha D + beta S, default alpha = 1, beta = -ik.
+A source point at r = 0 contributes 0 (it only occurs when a rule node meets a target).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+FOUR_PI = 4.0 * np.pi
+
+
+def kernel_jac(x, X, N, k, kind: str, alpha=1.0, beta=0.0):
+    """Kernel values times J at sources X [3,P] with normals N [3,P] for target x [3].
+
+    kind: "S", "D" or "CFIE" (alpha D + beta S).  Returns complex [P].
+    """
+    x = np.asarray(x, dtype=np.float64)
+    dvec = x[:, None] - X
+    r = np.sqrt((dvec * dvec).sum(axis=0))
+    zero = r == 0.0
+    rs = np.where(zero, 1.0, r)
+    e = np.exp(1j * k * rs) / (FOUR_PI * rs)
+    out = np.zeros(X.shape[1], dtype=np.complex128)
+    if kind in ("S", "CFIE"):
+        s = e * np.sqrt((N * N).sum(axis=0))
+        out = out + (s if kind == "S" else beta * s)
+    if kind in ("D", "CFIE"):
+        ndx = (N * dvec).sum(axis=0)
+        dd = ndx * (1.0 - 1j * k * rs) * e / (rs * rs)
+        out = out + (dd if kind == "D" else alpha * dd)
+    out[zero] = 0.0
+    return out

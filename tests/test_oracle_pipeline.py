@@ -1,0 +1,73 @@
+"""Pins of the oracle's whole pipeline (near lists, far order, self, adaptive and annulus
+weights, CSR assembly, subtract-and-add apply) against identities fixed by potential
+theory."""
+import numpy as np
+import pytest
+
+from oracle import corrections as C
+from oracle import nearlist, truth
+from paper_2006_02545_gb300 import workloads
+
+
+@pytest.fixture(scope="module")
+def flat_icosa_D0():
+    s = workloads.ellipsoid(1, 3, flat=True)
+    x_on, t_on = workloads.onsurface_targets(s)
+    inner = workloads.radial_targets(s, 6, 5, 0.02, 0.3, outside=False)
+    outer = workloads.radial_targets(s, 6, 6, 0.02, 0.3, outside=True)
+    x = np.concatenate([x_on, inner, outer], axis=1)
+    tn = np.concatenate([t_on, -np.ones(12, np.int64)])
+    p = C.Params(eps=1e-7, test_dirs=workloads.test_directions(2))
+    corr = C.gen_corrections(s.deg, s.node_off, s.xyz, x, tn, "D", 0.0, params=p)
+    u = C.apply_corrected(corr, s.node_off, np.ones(s.n_points, complex), x, "D", 0.0)
+    return s, corr, u
+
+
+def test_gauss_identity_flat_polyhedron(flat_icosa_D0):
+    """D_0[1] = -1/2 on the surface, -1 inside, 0 outside, for a closed flat polyhedron
+    (charts match along edges, so the identity is exact up to quadrature error)."""
+    s, corr, u = flat_icosa_D0
+    n = s.n_points
+    assert np.abs(u[:n] + 0.5).max() < 2e-7
+    assert np.abs(u[n:n + 6] + 1.0).max() < 2e-7
+    assert np.abs(u[n + 6:]).max() < 2e-7
+    assert not corr.depth_hit
+
+
+def test_csr_structure(flat_icosa_D0):
+    s, corr, _ = flat_icosa_D0
+    nt = len(corr.row_ptr) - 1
+    for t in range(nt):
+        cols = corr.col[corr.row_ptr[t]:corr.row_ptr[t + 1]]
+        patches = np.searchsorted(s.node_off, cols, side="right") - 1
+        # patches ascend, each contributes its n nodes in order
+        assert (np.diff(patches) >= 0).all()
+        for j in np.unique(patches):
+            cj = cols[patches == j]
+            assert (cj == s.node_off[j] + np.arange(len(cj))).all() and len(cj) == s.node_off[j + 1] - s.node_off[j]
+
+
+def test_near_list_definition_tiny():
+    """Hand-placed targets around one patch: the <= boundary, self exclusion, eta_1 flag."""
+    c = np.array([[0.0, 0.0, 0.0]])
+    R = np.array([1.0])
+    tx = np.array([[0.5, 0, 0], [2.0, 0, 0], [2.0000001, 0, 0], [1.2, 0, 0], [0.1, 0, 0]]).T
+    tp = np.array([-1, -1, -1, -1, 0])
+    ids, ad, _ = nearlist.near_lists(c, R, np.array([2.0]), np.array([1.25]), tx, tp)[0]
+    assert list(ids) == [0, 1, 3] and list(ad) == [True, False, True]
+
+
+def test_sphere_single_layer_eigenvalue_converges():
+    """S_k Y_0 = i k j_0(k) h_0(k) Y_0 on the unit sphere (target of the full pipeline);
+    the error falls with the patch size as the chart approximation improves."""
+    k = 1.0
+    lam = truth.sphere_eigen_S(0, k)
+    errs = []
+    for sdiv, d in ((1, 2), (1, 4), (1, 6)):
+        s = workloads.ellipsoid(sdiv, d)
+        x, tn = workloads.onsurface_targets(s)
+        p = C.Params(eps=1e-7, eta=1.25, test_dirs=workloads.test_directions(4))
+        corr = C.gen_corrections(s.deg, s.node_off, s.xyz, x, tn, "S", k, params=p)
+        u = C.apply_corrected(corr, s.node_off, np.ones(s.n_points, complex), x, "S", k)
+        errs.append(np.abs(u - lam).max() / abs(lam))
+    assert errs[1] < 0.2 * errs[0] and errs[2] < 0.2 * errs[1] and errs[2] < 3e-3, errs
