@@ -1,0 +1,189 @@
+/*
+ * lcq.h - C ABI of the GB300 locally corrected quadrature library (liblcq.so).
+ *
+ * Near-field quadrature corrections for Helmholtz layer potentials on surfaces
+ * made of curved triangular patches, after Greengard, O'Neil, Rachh and Vico,
+ * "Fast multipole methods for the evaluation of layer potentials with
+ * locally-corrected quadratures" (arXiv 2006.02545).
+ *
+ * Conventions shared by every entry point
+ *  - Degrees: a patch of degree d carries n_d = (d+1)(d+2)/2 discretization
+ *    nodes (the paper's order p = d+1 with n_p = p(p+1)/2).  1 <= d <= 10.
+ *  - Discretization nodes on T0 = {u,v >= 0, u+v <= 1} are the library's
+ *    stand-in for the Vioreanu-Rokhlin nodes of Sec. 2.2; lcq_ref_nodes()
+ *    returns them so that callers can sample their charts there.
+ *  - Pointers documented "device" are CUDA device pointers on the context's
+ *    device; pointers documented "host" are ordinary host memory.  The caller
+ *    owns every pointer it passes; handles (lcq_ctx, lcq_near, lcq_corr) are
+ *    owned by the library and released by the matching _destroy call.
+ *  - Complex values are interleaved (re, im) doubles (complex128).
+ *  - All device work is queued on the context's stream.  Calls that must size
+ *    outputs (lcq_build_near_lists) synchronize that stream once.  Errors found
+ *    on the device (depth cap, capacity) are latched in a device status word and
+ *    returned by lcq_sync() or the next call that synchronizes.
+ *  - No call aborts, traps or throws across the ABI; every failure is a status.
+ *  - Results are deterministic: fixed orderings, no floating-point atomics.
+ */
+#ifndef LCQ_H
+#define LCQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lcq_ctx lcq_ctx;
+typedef struct lcq_near lcq_near;
+typedef struct lcq_corr lcq_corr;
+
+typedef enum {
+  LCQ_OK = 0,
+  LCQ_ERR_ARG = 1,              /* invalid argument (null pointer, bad size or degree)  */
+  LCQ_ERR_NONFINITE = 2,        /* NaN/Inf in node or target coordinates                 */
+  LCQ_ERR_DEGENERATE_PATCH = 3, /* Jacobian <= 0 at a node of some patch                 */
+  LCQ_ERR_MAX_DEPTH = 4,        /* adaptive refinement reached max_depth (result kept)   */
+  LCQ_ERR_CAPACITY = 5,         /* internal work storage too small                       */
+  LCQ_ERR_CUDA = 6,             /* CUDA runtime error                                    */
+  LCQ_ERR_OOM = 7,              /* device allocation failed                              */
+  LCQ_ERR_TABLES = 8,           /* reference tables could not be built                   */
+  LCQ_ERR_TIMEOUT = 9           /* lcq_sync gave up waiting                              */
+} lcq_status;
+
+/* Layer potential kernels (Sec. 3, Eq. sldef / dldef / urep):
+ *   LCQ_S    : G_k(x,y) = e^{ik|x-y|} / (4 pi |x-y|)
+ *   LCQ_D    : n(y) . grad_y G_k(x,y)   (n outward)
+ *   LCQ_CFIE : alpha D + beta S          (the paper's D - ik S is alpha = 1, beta = -ik) */
+typedef enum { LCQ_S = 0, LCQ_D = 1, LCQ_CFIE = 2 } lcq_kernel;
+
+typedef enum { LCQ_FP64 = 0 } lcq_precision;
+
+/* Surface: n_patches charts; patch j owns nodes node_off[j] .. node_off[j+1]-1,
+ * sampled at lcq_ref_nodes(deg[j]) in that order (Sec. 5.2).
+ *   deg      host   int32 [n_patches]
+ *   node_off host   int64 [n_patches+1], node_off[0] = 0, node_off[j+1]-node_off[j] = n_{deg[j]}
+ *   xyz      device double SoA [3][N], N = node_off[n_patches] (x row, then y, then z)
+ * Charts must be oriented so that X_u x X_v points out of the body. */
+typedef struct {
+  int64_t n_patches;
+  const int32_t* deg;
+  const int64_t* node_off;
+  const double* xyz;
+} lcq_surface;
+
+/* Parameters (Sec. 4.1-4.3, 5.2).  lcq_params_default() fills the defaults.
+ *   eps        requested precision epsilon (> 0)
+ *   eta        near-field radius factor; <= 0 selects the paper's default by order
+ *              (2.75 for p <= 4, 2 for 4 < p <= 8, 1.25 for p > 8, p = d+1)
+ *   eta1       adaptive radius factor (default 1.25); min(eta1, eta) is used
+ *   eps_loosen factor on eps in the adaptive termination test (default 1)
+ *   max_depth  deepest refinement level (default 24)
+ *   m_max      largest smooth rule of the family (m^2 nodes, default 24, <= 32)
+ *   self_order Gauss-Legendre order of the self rules (0: from eps)
+ *   leaf_order smooth rule used on each subtriangle (0: the patch's far order q_j)
+ *   test_dirs  host [n_test_dirs][3] unit vectors for the far-order test points
+ *              (NULL: 15-point Fibonacci sphere) */
+typedef struct {
+  double eps;
+  double eta;
+  double eta1;
+  double eps_loosen;
+  int32_t max_depth;
+  int32_t m_max;
+  int32_t self_order;
+  int32_t leaf_order;
+  int32_t n_test_dirs;
+  const double* test_dirs;
+} lcq_params;
+
+void lcq_params_default(lcq_params* p);
+
+/* Context on one CUDA device; stream may be NULL (legacy default stream) or a
+ * cudaStream_t.  Allocates the device status word and per-device constants. */
+lcq_status lcq_create(lcq_ctx** out, int device, void* cuda_stream);
+void lcq_destroy(lcq_ctx* ctx);
+
+/* Discretization nodes of degree deg (Sec. 2.1-2.2 stand-in): writes host
+ * u[n], v[n] and interpolatory weights w[n], n = (deg+1)(deg+2)/2.  Host only. */
+lcq_status lcq_ref_nodes(int deg, double* u, double* v, double* w);
+
+/* Patch geometry and near lists (Sec. 4 N_eta definition; Sec. 5.2).
+ *   tgt_xyz  device double SoA [3][NT]
+ *   tgt_node device int64 [NT]: global node id of an on-surface target (it is
+ *            then excluded from its own patch's near list and gets a self row),
+ *            or -1 for an off-surface target.
+ * Target t is near patch j iff |x_t - c_j|^2 <= (eta R_j)^2 and t is not on j;
+ * it is adaptive iff |x_t - c_j|^2 <= (eta1 R_j)^2.  Synchronizes the stream. */
+lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const double* tgt_xyz,
+                                const int64_t* tgt_node, int64_t n_targets,
+                                const lcq_params* params, lcq_near** out);
+
+/* Sizes of a near-list object: near pairs, self pairs, adaptive pairs, CSR nnz. */
+lcq_status lcq_near_info(const lcq_near* near, int64_t* n_pairs, int64_t* n_self,
+                         int64_t* n_adaptive, int64_t* nnz);
+
+/* Patch-major near lists to host: pair_ptr[n_patches+1], tgt[n_pairs] (ascending
+ * per patch), adaptive[n_pairs] (0/1); per-patch centroid c[3*n_patches] and
+ * radius R[n_patches].  Any pointer may be NULL to skip it. */
+lcq_status lcq_near_export(lcq_near* near, int64_t* pair_ptr, int32_t* tgt, uint8_t* adaptive,
+                           double* centroid, double* radius);
+
+void lcq_near_destroy(lcq_near* near);
+
+/* Net corrections (Sec. 4.2-4.3, 5.2-5.3): for every near pair (t, j) and every
+ * self pair, c_{t,l} = a^j_l(x_t) - s^j_l(x_t), the quadrature weight minus the
+ * weight the smooth rule q_j gives node l, stored as a target-major CSR matrix.
+ * k = k_re + i k_im (k_im >= 0); alpha, beta are the CFIE coefficients (ignored
+ * for S and D). */
+lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                               lcq_kernel kernel, double k_re, double k_im, double alpha_re,
+                               double alpha_im, double beta_re, double beta_im,
+                               lcq_precision precision, const lcq_params* params,
+                               lcq_corr** out);
+
+/* nnz of the CSR, N_over = sum_j n_{q_j} (Sec. 5.2), value dtype (0 = complex128). */
+lcq_status lcq_corr_info(const lcq_corr* corr, int64_t* nnz, int64_t* n_over, int* value_dtype);
+
+/* CSR to host: row_ptr[NT+1], col[nnz] (global node ids), val[2*nnz] (complex128).
+ * Synchronizes the stream.  Any pointer may be NULL. */
+lcq_status lcq_corr_export(lcq_corr* corr, int64_t* row_ptr, int32_t* col, double* val);
+
+/* Per-patch far order q_j and annulus order (0: no annulus targets) to host
+ * [n_patches]; per-near-pair number of accepted leaf triangles (0 for annulus
+ * pairs) to host [n_pairs] in patch-major order.  Any pointer may be NULL. */
+lcq_status lcq_corr_export_stats(lcq_corr* corr, int32_t* q, int32_t* q_near, int32_t* leaves);
+
+/* Corrected layer potential (Sec. 5.3, subtract-and-add with a direct far sum):
+ *   u(x_t) = sum_j sum_{q in rule q_j} K(x_t, X_j(u_q)) J w_q sigma~_q + sum_row c sigma
+ * sigma device complex128 [N] at the nodes, out device complex128 [NT].
+ * jump != 0 adds jump * sigma(x_t) for on-surface targets (e.g. 0.5 for the
+ * exterior limit of D).  The kernel must match the one the corrections were
+ * generated for. */
+lcq_status lcq_apply_corrected_S(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                                 const lcq_corr* corr, const double* sigma, double jump,
+                                 double* out);
+lcq_status lcq_apply_corrected_D(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                                 const lcq_corr* corr, const double* sigma, double jump,
+                                 double* out);
+lcq_status lcq_apply_corrected_CFIE(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                                    const lcq_corr* corr, const double* sigma, double jump,
+                                    double* out);
+
+void lcq_corr_destroy(lcq_corr* corr);
+
+/* Wait for the context's stream (polling, at most timeout_ms; < 0 waits
+ * without limit), then return and clear the latched device status. */
+lcq_status lcq_sync(lcq_ctx* ctx, int64_t timeout_ms);
+
+/* Device-side work counters of the last lcq_gen_corrections on ctx (host out):
+ * [0] adaptive tests, [1] adaptive leaf-rule node evaluations, [2] self node
+ * evaluations, [3] smooth/annulus node evaluations (per target).  Synchronizes. */
+lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out4);
+
+const char* lcq_status_string(lcq_status s);
+const char* lcq_last_error(const lcq_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LCQ_H */

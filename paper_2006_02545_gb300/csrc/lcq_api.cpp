@@ -1,0 +1,777 @@
+// C ABI of liblcq: contexts, near lists, corrections, corrected potentials.
+// Host orchestration only; every numerical step runs in the kernels of lcq_kernels.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <thread>
+#include <vector>
+
+#include "lcq_internal.h"
+#include "lcq_launch.h"
+
+using namespace lcq;
+
+namespace {
+
+const char* kStatusNames[] = {"ok",
+                              "invalid argument",
+                              "non-finite coordinates",
+                              "degenerate patch (Jacobian <= 0 at a node)",
+                              "adaptive refinement reached max_depth",
+                              "internal capacity exceeded",
+                              "CUDA runtime error",
+                              "device out of memory",
+                              "reference tables could not be built",
+                              "timeout"};
+
+lcq_status fail(lcq_ctx* c, lcq_status s, const char* msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+lcq_status cuda_fail(lcq_ctx* c, cudaError_t e, const char* where) {
+  if (c) {
+    c->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  }
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? LCQ_ERR_OOM : LCQ_ERR_CUDA;
+}
+
+#define CK(call)                                             \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(cudaStream_t st, T** p, size_t count) {
+  *p = nullptr;
+  return cudaMallocAsync(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T), st);
+}
+
+template <class T>
+void dfree(cudaStream_t st, T*& p) {
+  if (p) cudaFreeAsync(p, st);
+  p = nullptr;
+}
+
+int default_self_order(double eps) {
+  const double e = std::min(std::max(eps, 1e-15), 1e-1);
+  const double digits = -log10(e);
+  const int o = (int)ceil(1.2 * digits - 1e-9) + 3;
+  return std::min(24, std::max(6, o));
+}
+
+lcq_status ensure_rules(lcq_ctx* ctx) {
+  if (ctx->rules_ready) return LCQ_OK;
+  RuleTables& r = ctx->rules;
+  if (!build_rule_tables(&r)) return fail(ctx, LCQ_ERR_TABLES, "rule tables");
+  cudaStream_t st = ctx->stream;
+  CK(dalloc(st, &r.doff, r.off.size()));
+  CK(dalloc(st, &r.du, r.u.size()));
+  CK(dalloc(st, &r.dv, r.v.size()));
+  CK(dalloc(st, &r.dw, r.w.size()));
+  CK(dalloc(st, &r.dgl_off, r.gl_off.size()));
+  CK(dalloc(st, &r.dgl_x, r.gl_x.size()));
+  CK(dalloc(st, &r.dgl_w, r.gl_w.size()));
+  CK(cudaMemcpyAsync(r.doff, r.off.data(), r.off.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(r.du, r.u.data(), r.u.size() * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(r.dv, r.v.data(), r.v.size() * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(r.dw, r.w.data(), r.w.size() * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(r.dgl_off, r.gl_off.data(), r.gl_off.size() * sizeof(int),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(r.dgl_x, r.gl_x.data(), r.gl_x.size() * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(r.dgl_w, r.gl_w.data(), r.gl_w.size() * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->rules_ready = true;
+  return LCQ_OK;
+}
+
+lcq_status ensure_deg(lcq_ctx* ctx, int d) {
+  DegTables& t = ctx->deg[d];
+  if (t.dV) return LCQ_OK;
+  if (!build_deg_tables(d, &t)) return fail(ctx, LCQ_ERR_TABLES, "degree tables");
+  cudaStream_t st = ctx->stream;
+  const int n = t.n;
+  std::vector<double> nodes(3 * n);
+  for (int i = 0; i < n; ++i) {
+    nodes[i] = t.u[i];
+    nodes[n + i] = t.v[i];
+    nodes[2 * n + i] = t.w[i];
+  }
+  CK(dalloc(st, &t.dV, (size_t)n * n));
+  CK(dalloc(st, &t.dnodes, (size_t)3 * n));
+  CK(cudaMemcpyAsync(t.dV, t.V.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(t.dnodes, nodes.data(), (size_t)3 * n * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return LCQ_OK;
+}
+
+}  // namespace
+
+// ============================================================================ API
+extern "C" {
+
+void lcq_params_default(lcq_params* p) {
+  if (!p) return;
+  p->eps = 1e-6;
+  p->eta = -1.0;
+  p->eta1 = 1.25;
+  p->eps_loosen = 1.0;
+  p->max_depth = 24;
+  p->m_max = 24;
+  p->self_order = 0;
+  p->leaf_order = 0;
+  p->n_test_dirs = 0;
+  p->test_dirs = nullptr;
+}
+
+const char* lcq_status_string(lcq_status s) {
+  const int i = (int)s;
+  if (i < 0 || i > 9) return "unknown status";
+  return kStatusNames[i];
+}
+
+const char* lcq_last_error(const lcq_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+lcq_status lcq_ref_nodes(int deg, double* u, double* v, double* w) {
+  if (deg < 1 || deg > kMaxDeg || !u || !v || !w) return LCQ_ERR_ARG;
+  DegTables t;
+  if (!build_deg_tables(deg, &t)) return LCQ_ERR_TABLES;
+  for (int i = 0; i < t.n; ++i) {
+    u[i] = t.u[i];
+    v[i] = t.v[i];
+    w[i] = t.w[i];
+  }
+  return LCQ_OK;
+}
+
+lcq_status lcq_create(lcq_ctx** out, int device, void* cuda_stream) {
+  if (!out) return LCQ_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return e != cudaSuccess ? LCQ_ERR_CUDA : LCQ_ERR_ARG;
+  }
+  lcq_ctx* ctx = new lcq_ctx();
+  ctx->device = device;
+  ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  CK(cudaSetDevice(device));
+  CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
+  CK(cudaMalloc(&ctx->d_status, sizeof(int)));
+  CK(cudaMalloc(&ctx->d_counters, 4 * sizeof(long long)));
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(long long), ctx->stream));
+  CK(upload_constants(ctx->stream));
+  lcq_status s = ensure_rules(ctx);
+  if (s != LCQ_OK) {
+    lcq_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return LCQ_OK;
+}
+
+void lcq_destroy(lcq_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (int d = 0; d <= kMaxDeg; ++d) {
+    dfree(ctx->stream, ctx->deg[d].dV);
+    dfree(ctx->stream, ctx->deg[d].dnodes);
+  }
+  RuleTables& r = ctx->rules;
+  dfree(ctx->stream, r.doff);
+  dfree(ctx->stream, r.du);
+  dfree(ctx->stream, r.dv);
+  dfree(ctx->stream, r.dw);
+  dfree(ctx->stream, r.dgl_off);
+  dfree(ctx->stream, r.dgl_x);
+  dfree(ctx->stream, r.dgl_w);
+  if (ctx->work) cudaFreeAsync(ctx->work, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->d_counters);
+  cudaGetLastError();
+  delete ctx;
+}
+
+lcq_status lcq_sync(lcq_ctx* ctx, int64_t timeout_ms) {
+  if (!ctx) return LCQ_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t q = cudaStreamQuery(ctx->stream);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return cuda_fail(ctx, q, "cudaStreamQuery");
+    if (timeout_ms >= 0) {
+      const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(
+                          std::chrono::steady_clock::now() - t0).count();
+      if (el > timeout_ms) return fail(ctx, LCQ_ERR_TIMEOUT, "lcq_sync timed out");
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  int st = 0;
+  CK(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+  if (st & kStNonFinite) return fail(ctx, LCQ_ERR_NONFINITE, "non-finite coordinates");
+  if (st & kStDegenerate) return fail(ctx, LCQ_ERR_DEGENERATE_PATCH, "degenerate patch");
+  if (st & kStCapacity) return fail(ctx, LCQ_ERR_CAPACITY, "work storage exceeded");
+  if (st & kStMaxDepth) return fail(ctx, LCQ_ERR_MAX_DEPTH, "max_depth reached");
+  return LCQ_OK;
+}
+
+lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out4) {
+  if (!ctx || !out4) return LCQ_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream));
+  long long h[4];
+  CK(cudaMemcpy(h, ctx->d_counters, sizeof(h), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 4; ++i) out4[i] = h[i];
+  return LCQ_OK;
+}
+
+// ---------------------------------------------------------------------------- near lists
+lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const double* tgt_xyz,
+                                const int64_t* tgt_node, int64_t NT, const lcq_params* params,
+                                lcq_near** out) {
+  if (!ctx || !surf || !params || !out || NT < 0) return fail(ctx, LCQ_ERR_ARG, "null argument");
+  *out = nullptr;
+  const int64_t P = surf->n_patches;
+  if (P <= 0 || !surf->deg || !surf->node_off || !surf->xyz)
+    return fail(ctx, LCQ_ERR_ARG, "empty or incomplete surface");
+  if (NT > 0 && (!tgt_xyz || !tgt_node)) return fail(ctx, LCQ_ERR_ARG, "null targets");
+  if (!(params->eps > 0.0) || !(params->eta1 > 0.0))
+    return fail(ctx, LCQ_ERR_ARG, "eps and eta1 must be positive");
+  if (surf->node_off[0] != 0) return fail(ctx, LCQ_ERR_ARG, "node_off[0] != 0");
+  for (int64_t j = 0; j < P; ++j) {
+    const int d = surf->deg[j];
+    if (d < 1 || d > kMaxDeg) return fail(ctx, LCQ_ERR_ARG, "degree outside 1..10");
+    if (surf->node_off[j + 1] - surf->node_off[j] != n_basis(d))
+      return fail(ctx, LCQ_ERR_ARG, "node_off inconsistent with degrees");
+  }
+  const int64_t N = surf->node_off[P];
+  if (N >= (int64_t)0x7fffffff) return fail(ctx, LCQ_ERR_ARG, "more than 2^31-1 nodes");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  LaunchCommon lc{st, ctx->num_sms};
+
+  lcq_near* nr = new lcq_near();
+  nr->params = *params;
+  nr->params.test_dirs = nullptr;
+  nr->params.n_test_dirs = 0;
+  nr->n_patches = P;
+  nr->n_targets = NT;
+  nr->n_points = N;
+  nr->deg_h.assign(surf->deg, surf->deg + P);
+  nr->node_off_h.assign(surf->node_off, surf->node_off + P + 1);
+  nr->stream = st;
+  nr->device = ctx->device;
+  std::vector<std::vector<int>> lists(kMaxDeg + 1);
+  for (int64_t j = 0; j < P; ++j) lists[surf->deg[j]].push_back((int)j);
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (lists[d].empty()) continue;
+    lcq_status s = ensure_deg(ctx, d);
+    if (s != LCQ_OK) return s;
+    nr->n_max = std::max(nr->n_max, n_basis(d));
+    nr->plist_count[d] = (int)lists[d].size();
+    CK(dalloc(st, &nr->plist_dev[d], lists[d].size()));
+    CK(cudaMemcpyAsync(nr->plist_dev[d], lists[d].data(), lists[d].size() * sizeof(int),
+                       cudaMemcpyHostToDevice, st));
+  }
+  const int64_t NTa = std::max<int64_t>(NT, 1);
+  CK(dalloc(st, &nr->deg, P));
+  CK(dalloc(st, &nr->node_off, P + 1));
+  CK(cudaMemcpyAsync(nr->deg, surf->deg, P * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(nr->node_off, surf->node_off, (P + 1) * sizeof(int64_t),
+                     cudaMemcpyHostToDevice, st));
+  CK(dalloc(st, &nr->coef, (size_t)N * 3));
+  CK(dalloc(st, &nr->cen, (size_t)P * 3));
+  CK(dalloc(st, &nr->rad, P));
+  CK(dalloc(st, &nr->dj, P));
+  CK(dalloc(st, &nr->eta, P));
+  CK(dalloc(st, &nr->eta1, P));
+  CK(dalloc(st, &nr->tgt, (size_t)3 * NTa));
+  CK(dalloc(st, &nr->tnode, NTa));
+  CK(dalloc(st, &nr->tgt_patch, NTa));
+  CK(dalloc(st, &nr->tgt_lnode, NTa));
+  if (NT > 0) {
+    CK(cudaMemcpyAsync(nr->tgt, tgt_xyz, (size_t)3 * NT * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(nr->tnode, tgt_node, (size_t)NT * 8, cudaMemcpyDeviceToDevice, st));
+    launch_tgt_patch(lc, nr->tgt, nr->tnode, NT, nr->node_off, P, N, nr->tgt_patch, nr->tgt_lnode,
+                     ctx->d_status);
+  }
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_geom(d, lc, nr->plist_dev[d], nr->plist_count[d], nr->node_off, surf->xyz, N, ctx->deg[d].dV,
+                ctx->deg[d].dnodes, params->eta, params->eta1, nr->coef, nr->cen, nr->rad, nr->dj,
+                nr->eta, nr->eta1, ctx->d_status);
+  }
+  CK(cudaGetLastError());
+  NearArgs na{nr->tgt, NT, nr->cen, nr->rad, nr->eta, nr->eta1};
+  // counts (arrays carry one trailing zero so that the exclusive scan yields the total)
+  int64_t *row_np, *row_nnz, *npair, *nad, *nself;
+  CK(dalloc(st, &row_np, NT + 1));
+  CK(dalloc(st, &row_nnz, NT + 1));
+  CK(dalloc(st, &npair, P + 1));
+  CK(dalloc(st, &nad, P + 1));
+  CK(dalloc(st, &nself, P + 1));
+  CK(cudaMemsetAsync(row_np, 0, (NT + 1) * 8, st));
+  CK(cudaMemsetAsync(row_nnz, 0, (NT + 1) * 8, st));
+  CK(cudaMemsetAsync(npair, 0, (P + 1) * 8, st));
+  CK(cudaMemsetAsync(nad, 0, (P + 1) * 8, st));
+  CK(cudaMemsetAsync(nself, 0, (P + 1) * 8, st));
+  if (NT > 0) {
+    launch_row_count(lc, na, nr->tgt_patch, P, nr->deg, row_np, row_nnz);
+    launch_patch_count(lc, na, nr->tgt_patch, P, npair, nad, nself);
+  }
+  CK(dalloc(st, &nr->row_ptr, NT + 1));
+  CK(dalloc(st, &nr->rowp_ptr, NT + 1));
+  CK(dalloc(st, &nr->pair_ptr, P + 1));
+  CK(dalloc(st, &nr->ad_ptr, P + 1));
+  CK(dalloc(st, &nr->an_ptr, P + 1));
+  CK(dalloc(st, &nr->self_ptr, P + 1));
+  const int64_t mx = std::max(NT, P) + 1;
+  int64_t* scr;
+  CK(dalloc(st, &scr, 2 * ((mx + 1023) / 1024) + 4096));
+  launch_scan(lc, row_nnz, nr->row_ptr, NT + 1, scr);
+  launch_scan(lc, row_np, nr->rowp_ptr, NT + 1, scr);
+  launch_scan(lc, npair, nr->pair_ptr, P + 1, scr);
+  launch_scan(lc, nad, nr->ad_ptr, P + 1, scr);
+  launch_scan(lc, nself, nr->self_ptr, P + 1, scr);
+  CK(cudaGetLastError());
+  std::vector<int64_t> h_np(P + 1), h_nad(P + 1), h_ns(P + 1);
+  int64_t tot[2];
+  CK(cudaMemcpyAsync(h_np.data(), npair, (P + 1) * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h_nad.data(), nad, (P + 1) * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h_ns.data(), nself, (P + 1) * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&tot[0], nr->row_ptr + NT, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&tot[1], nr->rowp_ptr + NT, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int hst = 0;
+  CK(cudaMemcpy(&hst, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (hst & (kStNonFinite | kStDegenerate)) {
+    cudaMemset(ctx->d_status, 0, sizeof(int));
+    lcq_near_destroy(nr);
+    return fail(ctx, (hst & kStNonFinite) ? LCQ_ERR_NONFINITE : LCQ_ERR_DEGENERATE_PATCH,
+                (hst & kStNonFinite) ? "non-finite coordinates" : "degenerate patch");
+  }
+  nr->nnz = tot[0];
+  const int64_t rowp_total = tot[1];
+  std::vector<int64_t> an_h(P + 1);
+  int64_t acc_p = 0, acc_a = 0, acc_s = 0, acc_n = 0;
+  for (int64_t j = 0; j < P; ++j) {
+    nr->max_adaptive = std::max(nr->max_adaptive, h_nad[j]);
+    nr->max_pairs = std::max(nr->max_pairs, h_np[j]);
+    nr->max_self = std::max(nr->max_self, h_ns[j]);
+    an_h[j] = acc_n;
+    acc_p += h_np[j];
+    acc_a += h_nad[j];
+    acc_s += h_ns[j];
+    acc_n += h_np[j] - h_nad[j];
+  }
+  an_h[P] = acc_n;
+  nr->n_pairs = acc_p;
+  nr->n_adaptive = acc_a;
+  nr->n_self = acc_s;
+  nr->n_annulus = acc_n;
+  CK(cudaMemcpyAsync(nr->an_ptr, an_h.data(), (P + 1) * 8, cudaMemcpyHostToDevice, st));
+  CK(dalloc(st, &nr->col, nr->nnz));
+  CK(dalloc(st, &nr->rowp_patch, rowp_total));
+  CK(dalloc(st, &nr->rowp_off, rowp_total));
+  CK(dalloc(st, &nr->pair_tgt, nr->n_pairs));
+  CK(dalloc(st, &nr->pair_ad, nr->n_pairs));
+  CK(dalloc(st, &nr->pair_d2, nr->n_pairs));
+  CK(dalloc(st, &nr->pair_csr, nr->n_pairs));
+  CK(dalloc(st, &nr->ad_pair, nr->n_adaptive));
+  CK(dalloc(st, &nr->an_pair, nr->n_annulus));
+  CK(dalloc(st, &nr->self_tgt, nr->n_self));
+  CK(dalloc(st, &nr->self_csr, nr->n_self));
+  if (NT > 0) {
+    launch_row_fill(lc, na, nr->tgt_patch, P, nr->deg, nr->node_off, nr->rowp_ptr, nr->row_ptr,
+                    nr->rowp_patch, nr->rowp_off, nr->col);
+    launch_patch_fill(lc, na, nr->tgt_patch, P, nr->pair_ptr, nr->ad_ptr, nr->an_ptr, nr->self_ptr,
+                      nr->rowp_ptr, nr->rowp_patch, nr->rowp_off, nr->row_ptr, nr->pair_tgt,
+                      nr->pair_ad, nr->pair_d2, nr->pair_csr, nr->ad_pair, nr->an_pair,
+                      nr->self_tgt, nr->self_csr);
+  }
+  CK(cudaGetLastError());
+  dfree(st, row_np);
+  dfree(st, row_nnz);
+  dfree(st, npair);
+  dfree(st, nad);
+  dfree(st, nself);
+  dfree(st, scr);
+  *out = nr;
+  return LCQ_OK;
+}
+
+lcq_status lcq_near_info(const lcq_near* nr, int64_t* n_pairs, int64_t* n_self,
+                         int64_t* n_adaptive, int64_t* nnz) {
+  if (!nr) return LCQ_ERR_ARG;
+  if (n_pairs) *n_pairs = nr->n_pairs;
+  if (n_self) *n_self = nr->n_self;
+  if (n_adaptive) *n_adaptive = nr->n_adaptive;
+  if (nnz) *nnz = nr->nnz;
+  return LCQ_OK;
+}
+
+lcq_status lcq_near_export(lcq_near* nr, int64_t* pair_ptr, int32_t* tgt, uint8_t* adaptive,
+                           double* centroid, double* radius) {
+  if (!nr) return LCQ_ERR_ARG;
+  lcq_ctx* ctx = nullptr;
+  CK(cudaSetDevice(nr->device));
+  cudaStream_t st = nr->stream;
+  if (pair_ptr)
+    CK(cudaMemcpyAsync(pair_ptr, nr->pair_ptr, (nr->n_patches + 1) * 8, cudaMemcpyDeviceToHost, st));
+  if (tgt && nr->n_pairs)
+    CK(cudaMemcpyAsync(tgt, nr->pair_tgt, nr->n_pairs * 4, cudaMemcpyDeviceToHost, st));
+  if (adaptive && nr->n_pairs)
+    CK(cudaMemcpyAsync(adaptive, nr->pair_ad, nr->n_pairs, cudaMemcpyDeviceToHost, st));
+  if (centroid)
+    CK(cudaMemcpyAsync(centroid, nr->cen, nr->n_patches * 3 * 8, cudaMemcpyDeviceToHost, st));
+  if (radius) CK(cudaMemcpyAsync(radius, nr->rad, nr->n_patches * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return LCQ_OK;
+}
+
+void lcq_near_destroy(lcq_near* nr) {
+  if (!nr) return;
+  cudaSetDevice(nr->device);
+  cudaStream_t st = nr->stream;
+  for (int d = 0; d <= kMaxDeg; ++d) dfree(st, nr->plist_dev[d]);
+  dfree(st, nr->deg);
+  dfree(st, nr->node_off);
+  dfree(st, nr->coef);
+  dfree(st, nr->cen);
+  dfree(st, nr->rad);
+  dfree(st, nr->dj);
+  dfree(st, nr->eta);
+  dfree(st, nr->eta1);
+  dfree(st, nr->tgt);
+  dfree(st, nr->tnode);
+  dfree(st, nr->tgt_patch);
+  dfree(st, nr->tgt_lnode);
+  dfree(st, nr->row_ptr);
+  dfree(st, nr->rowp_ptr);
+  dfree(st, nr->rowp_patch);
+  dfree(st, nr->rowp_off);
+  dfree(st, nr->col);
+  dfree(st, nr->pair_ptr);
+  dfree(st, nr->pair_tgt);
+  dfree(st, nr->pair_ad);
+  dfree(st, nr->pair_d2);
+  dfree(st, nr->pair_csr);
+  dfree(st, nr->ad_ptr);
+  dfree(st, nr->ad_pair);
+  dfree(st, nr->an_ptr);
+  dfree(st, nr->an_pair);
+  dfree(st, nr->self_tgt);
+  dfree(st, nr->self_csr);
+  dfree(st, nr->self_ptr);
+  cudaGetLastError();
+  delete nr;
+}
+
+// ---------------------------------------------------------------------------- corrections
+static Dev make_dev(lcq_ctx* ctx, const lcq_near* nr, const int32_t* q, int ldI) {
+  Dev dv{};
+  dv.coef = nr->coef;
+  dv.node_off = nr->node_off;
+  dv.cen = nr->cen;
+  dv.rad = nr->rad;
+  dv.dj = nr->dj;
+  dv.eta = nr->eta;
+  dv.eta1 = nr->eta1;
+  dv.tgt = nr->tgt;
+  dv.NT = nr->n_targets;
+  dv.tpatch = nr->tgt_patch;
+  dv.tlnode = nr->tgt_lnode;
+  dv.pair_ptr = nr->pair_ptr;
+  dv.pair_tgt = nr->pair_tgt;
+  dv.pair_d2 = nr->pair_d2;
+  dv.pair_csr = nr->pair_csr;
+  dv.ad_ptr = nr->ad_ptr;
+  dv.ad_pair = nr->ad_pair;
+  dv.an_ptr = nr->an_ptr;
+  dv.an_pair = nr->an_pair;
+  dv.self_ptr = nr->self_ptr;
+  dv.self_tgt = nr->self_tgt;
+  dv.self_csr = nr->self_csr;
+  dv.n_self = nr->n_self;
+  dv.q = q;
+  dv.roff = ctx->rules.doff;
+  dv.ru = ctx->rules.du;
+  dv.rv = ctx->rules.dv;
+  dv.rw = ctx->rules.dw;
+  dv.gl_off = ctx->rules.dgl_off;
+  dv.gl_x = ctx->rules.dgl_x;
+  dv.gl_w = ctx->rules.dgl_w;
+  for (int d = 0; d <= kMaxDeg; ++d) dv.nodes_uv[d] = ctx->deg[d].dnodes;
+  dv.counters = ctx->d_counters;
+  dv.status = ctx->d_status;
+  dv.ldI = ldI;
+  return dv;
+}
+
+lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* nr,
+                               lcq_kernel kernel, double k_re, double k_im, double alpha_re,
+                               double alpha_im, double beta_re, double beta_im,
+                               lcq_precision precision, const lcq_params* params, lcq_corr** out) {
+  if (!ctx || !nr || !params || !out) return fail(ctx, LCQ_ERR_ARG, "null argument");
+  (void)surf;
+  *out = nullptr;
+  if (precision != LCQ_FP64) return fail(ctx, LCQ_ERR_ARG, "unsupported precision");
+  if ((int)kernel < 0 || (int)kernel > 2) return fail(ctx, LCQ_ERR_ARG, "unknown kernel");
+  if (!(params->eps > 0.0) || k_im < 0.0 || !isfinite(k_re) || !isfinite(k_im))
+    return fail(ctx, LCQ_ERR_ARG, "eps must be > 0 and Im k >= 0");
+  if (params->m_max < 2 || params->m_max > kMaxRule || params->leaf_order < 0 ||
+      params->leaf_order > kMaxRule || params->self_order < 0 || params->self_order > kMaxGL ||
+      params->max_depth < 1 || params->max_depth > 24 || params->n_test_dirs < 0 ||
+      params->n_test_dirs > kMaxTestPts - 10)
+    return fail(ctx, LCQ_ERR_ARG, "parameter out of range");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  LaunchCommon lc{st, ctx->num_sms};
+  const int64_t P = nr->n_patches;
+  KernelParams kp{(int)kernel, k_re, k_im, alpha_re, alpha_im, beta_re, beta_im};
+  if (kernel == LCQ_S) kp.ar = kp.ai = kp.br = kp.bi = 0.0;
+
+  lcq_corr* c = new lcq_corr();
+  c->near = nr;
+  c->stream = st;
+  c->device = ctx->device;
+  c->kernel = (int)kernel;
+  c->n_patches = P;
+  c->n_targets = nr->n_targets;
+  c->nnz = nr->nnz;
+  c->n_pairs = nr->n_pairs;
+  c->n_self = nr->n_self;
+  c->kp = kp;
+  CK(dalloc(st, &c->val, (size_t)2 * nr->nnz));
+  CK(dalloc(st, &c->q, P));
+  CK(dalloc(st, &c->q_near, P));
+  CK(dalloc(st, &c->leaves, nr->n_pairs));
+  CK(cudaMemsetAsync(c->leaves, 0, std::max<int64_t>(nr->n_pairs, 1) * 4, st));
+  CK(cudaMemsetAsync(c->val, 0, std::max<int64_t>(nr->nnz, 1) * 16, st));
+  CK(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(long long), st));
+
+  // test directions
+  std::vector<double> dirs;
+  if (params->test_dirs && params->n_test_dirs > 0) {
+    dirs.assign(params->test_dirs, params->test_dirs + 3 * params->n_test_dirs);
+  } else {
+    const int nd = 15;
+    for (int k = 0; k < nd; ++k) {
+      const double z = 1.0 - (2.0 * k + 1.0) / nd, r = sqrt(1.0 - z * z);
+      const double phi = k * M_PI * (3.0 - sqrt(5.0));
+      dirs.push_back(r * cos(phi));
+      dirs.push_back(r * sin(phi));
+      dirs.push_back(z);
+    }
+  }
+  const int ndirs = (int)dirs.size() / 3;
+  double* ddirs;
+  CK(dalloc(st, &ddirs, dirs.size()));
+  CK(cudaMemcpyAsync(ddirs, dirs.data(), dirs.size() * 8, cudaMemcpyHostToDevice, st));
+
+  const int ldI = nr->n_max;
+  const int64_t npr = std::max<int64_t>(nr->n_pairs, 1), nsf = std::max<int64_t>(nr->n_self, 1);
+  void *Is, *In, *IsS, *InS;
+  CK(dalloc(st, reinterpret_cast<double**>(&Is), (size_t)2 * npr * ldI));
+  CK(dalloc(st, reinterpret_cast<double**>(&In), (size_t)2 * npr * ldI));
+  CK(dalloc(st, reinterpret_cast<double**>(&IsS), (size_t)2 * nsf * ldI));
+  CK(dalloc(st, reinterpret_cast<double**>(&InS), (size_t)2 * nsf * ldI));
+  Dev dv = make_dev(ctx, nr, c->q, ldI);
+
+  // 1. far order q_j and annulus order (Sec. 4.2, Eq. qj)
+  const int fgrid = ctx->num_sms * 2;
+  double* fscr;
+  CK(dalloc(st, &fscr, (size_t)fgrid * 2 * kMaxTestPts * kMaxBasis * 2));
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_farorder(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, kp, params->eps, params->m_max,
+                    ctx->deg[d].normV, ddirs, ndirs, fscr, fgrid, c->q, c->q_near);
+  }
+  CK(cudaGetLastError());
+  // 2. smooth-rule moments of every near and self pair; 3. annulus moments
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 0, c->q, kp, Is, IsS);
+    launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 1, c->q_near, kp, In, nullptr);
+  }
+  CK(cudaGetLastError());
+  // 4. adaptive near moments (Sec. 4.3)
+  if (nr->n_adaptive > 0) {
+    const int levels = params->max_depth;
+    const int64_t A = nr->max_adaptive;
+    const int64_t n = ldI;
+    int64_t stride = A * n * 16 + A * 4 * n * 16 + (int64_t)levels * A * 4 * n * 16 +
+                     (int64_t)levels * A * 4 + 2 * A * 4 + (int64_t)levels * 4 + 256;
+    stride = (stride + 255) / 256 * 256;
+    const int agrid = ctx->num_sms;
+    const size_t need = (size_t)stride * agrid;
+    if (ctx->work_bytes < need) {
+      if (ctx->work) CK(cudaFreeAsync(ctx->work, st));
+      ctx->work = nullptr;
+      ctx->work_bytes = 0;
+      CK(cudaMallocAsync(&ctx->work, need, st));
+      ctx->work_bytes = need;
+    }
+    for (int d = 1; d <= kMaxDeg; ++d) {
+      if (!nr->plist_count[d]) continue;
+      launch_adaptive(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, kp,
+                      params->eps * params->eps_loosen, ctx->deg[d].normV, params->leaf_order,
+                      params->max_depth, Is, In, c->leaves, ctx->work, stride, (int)A, levels, agrid,
+                      ctx->d_status);
+    }
+    CK(cudaGetLastError());
+  }
+  // 5. self weights (Sec. 4, Eq. errestself)
+  const int sorder = params->self_order > 0 ? params->self_order : default_self_order(params->eps);
+  if (nr->n_self > 0)
+    for (int d = 1; d <= kMaxDeg; ++d) {
+      if (!nr->plist_count[d]) continue;
+      launch_self(d, lc, dv, nr->deg, kp, sorder, InS);
+    }
+  CK(cudaGetLastError());
+  // 6. c = V^T (I_near - I_smooth) into the CSR
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_v2c(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, In, Is, InS, IsS, c->val);
+  }
+  CK(cudaGetLastError());
+  dfree(st, ddirs);
+  dfree(st, fscr);
+  cudaFreeAsync(Is, st);
+  cudaFreeAsync(In, st);
+  cudaFreeAsync(IsS, st);
+  cudaFreeAsync(InS, st);
+  // stash the stream/device for later calls on the correction object
+  c->q_h.clear();
+  c->src_off = nullptr;
+  *out = c;
+  return LCQ_OK;
+}
+
+static lcq_status ensure_q_host(lcq_ctx* ctx, lcq_corr* c) {
+  if (!c->q_h.empty()) return LCQ_OK;
+  CK(cudaSetDevice(c->device));
+  c->q_h.resize(c->n_patches);
+  CK(cudaMemcpyAsync(c->q_h.data(), c->q, c->n_patches * 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int64_t acc = 0;
+  std::vector<int64_t> off(c->n_patches + 1);
+  for (int64_t j = 0; j < c->n_patches; ++j) {
+    off[j] = acc;
+    acc += (int64_t)c->q_h[j] * c->q_h[j];
+  }
+  off[c->n_patches] = acc;
+  c->n_over = acc;
+  CK(dalloc(c->stream, &c->src_off, c->n_patches + 1));
+  CK(cudaMemcpyAsync(c->src_off, off.data(), (c->n_patches + 1) * 8, cudaMemcpyHostToDevice,
+                     c->stream));
+  return LCQ_OK;
+}
+
+lcq_status lcq_corr_info(const lcq_corr* c, int64_t* nnz, int64_t* n_over, int* value_dtype) {
+  if (!c) return LCQ_ERR_ARG;
+  lcq_status s = ensure_q_host(nullptr, const_cast<lcq_corr*>(c));
+  if (s != LCQ_OK) return s;
+  if (nnz) *nnz = c->nnz;
+  if (n_over) *n_over = c->n_over;
+  if (value_dtype) *value_dtype = 0;
+  return LCQ_OK;
+}
+
+lcq_status lcq_corr_export(lcq_corr* c, int64_t* row_ptr, int32_t* col, double* val) {
+  if (!c || !c->near) return LCQ_ERR_ARG;
+  lcq_ctx* ctx = nullptr;
+  CK(cudaSetDevice(c->device));
+  const lcq_near* nr = c->near;
+  cudaStream_t st = c->stream;
+  if (row_ptr)
+    CK(cudaMemcpyAsync(row_ptr, nr->row_ptr, (nr->n_targets + 1) * 8, cudaMemcpyDeviceToHost, st));
+  if (col && c->nnz) CK(cudaMemcpyAsync(col, nr->col, c->nnz * 4, cudaMemcpyDeviceToHost, st));
+  if (val && c->nnz) CK(cudaMemcpyAsync(val, c->val, c->nnz * 16, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return LCQ_OK;
+}
+
+lcq_status lcq_corr_export_stats(lcq_corr* c, int32_t* q, int32_t* q_near, int32_t* leaves) {
+  if (!c) return LCQ_ERR_ARG;
+  lcq_ctx* ctx = nullptr;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  if (q) CK(cudaMemcpyAsync(q, c->q, c->n_patches * 4, cudaMemcpyDeviceToHost, st));
+  if (q_near) CK(cudaMemcpyAsync(q_near, c->q_near, c->n_patches * 4, cudaMemcpyDeviceToHost, st));
+  if (leaves && c->n_pairs)
+    CK(cudaMemcpyAsync(leaves, c->leaves, c->n_pairs * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return LCQ_OK;
+}
+
+static lcq_status apply_impl(lcq_ctx* ctx, const lcq_near* nr, const lcq_corr* cc,
+                             const double* sigma, double jump, double* out, int kind) {
+  if (!ctx || !nr || !cc || !sigma || !out) return fail(ctx, LCQ_ERR_ARG, "null argument");
+  if (cc->kernel != kind) return fail(ctx, LCQ_ERR_ARG, "kernel differs from the corrections'");
+  if (cc->near != nr) return fail(ctx, LCQ_ERR_ARG, "corrections belong to another near list");
+  lcq_corr* c = const_cast<lcq_corr*>(cc);
+  CK(cudaSetDevice(ctx->device));
+  lcq_status s = ensure_q_host(ctx, c);
+  if (s != LCQ_OK) return s;
+  cudaStream_t st = ctx->stream;
+  LaunchCommon lc{st, ctx->num_sms};
+  Dev dv = make_dev(ctx, nr, c->q, nr->n_max);
+  double* src;
+  CK(dalloc(st, &src, (size_t)9 * std::max<int64_t>(c->n_over, 1)));
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_far_src(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, c->q,
+                   c->src_off, sigma, src, c->n_over);
+  }
+  launch_far_sum(lc, nr->tgt, nr->n_targets, src, c->n_over, c->kp, out);
+  launch_csr_apply(lc, nr->row_ptr, nr->col, c->val, sigma, nr->tnode, nr->n_targets, jump, out);
+  CK(cudaGetLastError());
+  dfree(st, src);
+  return LCQ_OK;
+}
+
+lcq_status lcq_apply_corrected_S(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                                 const lcq_corr* corr, const double* sigma, double jump,
+                                 double* out) {
+  (void)surf;
+  return apply_impl(ctx, near, corr, sigma, jump, out, LCQ_S);
+}
+lcq_status lcq_apply_corrected_D(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                                 const lcq_corr* corr, const double* sigma, double jump,
+                                 double* out) {
+  (void)surf;
+  return apply_impl(ctx, near, corr, sigma, jump, out, LCQ_D);
+}
+lcq_status lcq_apply_corrected_CFIE(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                                    const lcq_corr* corr, const double* sigma, double jump,
+                                    double* out) {
+  (void)surf;
+  return apply_impl(ctx, near, corr, sigma, jump, out, LCQ_CFIE);
+}
+
+void lcq_corr_destroy(lcq_corr* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  dfree(c->stream, c->val);
+  dfree(c->stream, c->q);
+  dfree(c->stream, c->q_near);
+  dfree(c->stream, c->leaves);
+  dfree(c->stream, c->src_off);
+  cudaGetLastError();
+  delete c;
+}
+
+}  // extern "C"

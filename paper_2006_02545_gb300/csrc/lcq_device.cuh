@@ -1,0 +1,195 @@
+// Device building blocks: Koornwinder recurrences (Sec. 2, Eq. for K_nm), chart
+// geometry (Sec. 3.1-3.2) and the Helmholtz kernels times the area element
+// (Sec. 3, Eq. greenfunhelm, sldef, dldef, urep).  Templated on the patch degree D
+// so that the basis loops unroll into registers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "lcq_internal.h"
+
+namespace lcq {
+
+// c_nm = sqrt(2(2m+1)(n+1)), index n(n+1)/2 + m; filled once per device.
+__constant__ double c_kw[kMaxBasis];
+
+struct cplx {
+  double re, im;
+};
+
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+// Jacobi P^{(0,b)}_a three-term recurrence coefficients (alpha = 0):
+//   P_{a+1} = (c1 y + c0) P_a - c2 P_{a-1}.
+// All arguments are compile-time constants after unrolling, so these fold.
+__host__ __device__ __forceinline__ void jacobi_coef(int a, int b, double* c1, double* c0,
+                                                     double* c2) {
+  const double den = 2.0 * (a + 1) * (a + b + 1) * (2 * a + b);
+  *c1 = (double)((2 * a + b + 1) * (2 * a + b + 2) * (2 * a + b)) / den;
+  *c0 = -(double)((2 * a + b + 1) * b * b) / den;
+  *c2 = (double)(2 * a * (a + b) * (2 * a + b + 2)) / den;
+}
+
+// Koornwinder values K[nm] at (u, v) written with stride `ks`.
+template <int D>
+__device__ __forceinline__ void kw_values(double u, double v, double* K, int ks) {
+  const double s = 2.0 * u + v - 1.0, q2 = (1.0 - v) * (1.0 - v), y = 1.0 - 2.0 * v;
+  double Lp = 0.0, L = 1.0;
+#pragma unroll
+  for (int m = 0; m <= D; ++m) {
+    if (m > 0) {
+      const double Ln = ((2.0 * m - 1.0) * s * L - (m - 1.0) * q2 * Lp) * (1.0 / m);
+      Lp = L;
+      L = Ln;
+    }
+    const int b = 2 * m + 1;
+    double Pp = 0.0, P = 1.0;
+#pragma unroll
+    for (int a = 0; a <= D - m; ++a) {
+      const int n = m + a, idx = n * (n + 1) / 2 + m;
+      K[idx * ks] = c_kw[idx] * L * P;
+      if (a < D - m) {
+        double c1, c0, c2;
+        jacobi_coef(a, b, &c1, &c0, &c2);
+        const double Pn = (c1 * y + c0) * P - c2 * Pp;
+        Pp = P;
+        P = Pn;
+      }
+    }
+  }
+}
+
+// acc[nm] += g * K_nm(u, v) for all nm (values recurrence fused with the update).
+template <int D>
+__device__ __forceinline__ void kw_accumulate(double u, double v, cplx g, cplx* acc) {
+  const double s = 2.0 * u + v - 1.0, q2 = (1.0 - v) * (1.0 - v), y = 1.0 - 2.0 * v;
+  double Lp = 0.0, L = 1.0;
+#pragma unroll
+  for (int m = 0; m <= D; ++m) {
+    if (m > 0) {
+      const double Ln = ((2.0 * m - 1.0) * s * L - (m - 1.0) * q2 * Lp) * (1.0 / m);
+      Lp = L;
+      L = Ln;
+    }
+    const int b = 2 * m + 1;
+    double Pp = 0.0, P = 1.0;
+#pragma unroll
+    for (int a = 0; a <= D - m; ++a) {
+      const int n = m + a, idx = n * (n + 1) / 2 + m;
+      const double K = c_kw[idx] * L * P;
+      acc[idx].re = fma(g.re, K, acc[idx].re);
+      acc[idx].im = fma(g.im, K, acc[idx].im);
+      if (a < D - m) {
+        double c1, c0, c2;
+        jacobi_coef(a, b, &c1, &c0, &c2);
+        const double Pn = (c1 * y + c0) * P - c2 * Pp;
+        Pp = P;
+        P = Pn;
+      }
+    }
+  }
+}
+
+// Chart X, X_u, X_v at (u, v) from Koornwinder coefficients cf[nm][3]; optionally
+// also K values (stride ks) when K != nullptr.
+template <int D>
+__device__ __forceinline__ void kw_geometry(double u, double v, const double* __restrict__ cf,
+                                            double* X, double* Xu, double* Xv, double* K, int ks) {
+  const double s = 2.0 * u + v - 1.0, q = 1.0 - v, q2 = q * q, y = 1.0 - 2.0 * v;
+  double Lp = 0.0, L = 1.0, Lup = 0.0, Lu = 0.0, Lvp = 0.0, Lv = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) X[c] = Xu[c] = Xv[c] = 0.0;
+#pragma unroll
+  for (int m = 0; m <= D; ++m) {
+    if (m > 0) {
+      const double f1 = 2.0 * m - 1.0, f2 = m - 1.0, im = 1.0 / m;
+      const double Ln = (f1 * s * L - f2 * q2 * Lp) * im;
+      const double Lun = (f1 * (2.0 * L + s * Lu) - f2 * q2 * Lup) * im;
+      const double Lvn = (f1 * (L + s * Lv) - f2 * (-2.0 * q * Lp + q2 * Lvp)) * im;
+      Lp = L;
+      L = Ln;
+      Lup = Lu;
+      Lu = Lun;
+      Lvp = Lv;
+      Lv = Lvn;
+    }
+    const int b = 2 * m + 1;
+    double Pp = 0.0, P = 1.0, dPp = 0.0, dP = 0.0;
+#pragma unroll
+    for (int a = 0; a <= D - m; ++a) {
+      const int n = m + a, idx = n * (n + 1) / 2 + m;
+      const double cn = c_kw[idx];
+      const double k0 = cn * L * P;
+      const double ku = cn * Lu * P;
+      const double kv = cn * (Lv * P - 2.0 * L * dP);
+      if (K) K[idx * ks] = k0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double x = cf[idx * 3 + c];
+        X[c] = fma(x, k0, X[c]);
+        Xu[c] = fma(x, ku, Xu[c]);
+        Xv[c] = fma(x, kv, Xv[c]);
+      }
+      if (a < D - m) {
+        double c1, c0, c2;
+        jacobi_coef(a, b, &c1, &c0, &c2);
+        const double t = c1 * y + c0;
+        const double Pn = t * P - c2 * Pp;
+        const double dPn = c1 * P + t * dP - c2 * dPp;
+        Pp = P;
+        P = Pn;
+        dPp = dP;
+        dP = dPn;
+      }
+    }
+  }
+}
+
+// Kernel times area element and weight, at a source with position X, weighted
+// unnormalized normal Nw = (X_u x X_v) w and weighted Jacobian Jw = |X_u x X_v| w:
+//   S: G_k(x, X) Jw
+//   D: Nw.(x - X) (1 - ik r) e^{ikr} / (4 pi r^3)
+//   CFIE: alpha D + beta S.   r = 0 contributes 0.
+__device__ __forceinline__ cplx kernel_eval(const KernelParams& kp, double x0, double x1, double x2,
+                                            double X0, double X1, double X2, double N0, double N1,
+                                            double N2, double Jw) {
+  const double d0 = x0 - X0, d1 = x1 - X1, d2 = x2 - X2;
+  const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+  if (r2 == 0.0) return {0.0, 0.0};
+  const double r = sqrt(r2);
+  const double rinv = 1.0 / r;
+  double sn, cs;
+  sincos(kp.kr * r, &sn, &cs);
+  double ex = 0.07957747154594767 * rinv;  // 1/(4 pi r)
+  if (kp.ki != 0.0) ex *= exp(-kp.ki * r);
+  const cplx G = {ex * cs, ex * sn};
+  cplx out = {0.0, 0.0};
+  if (kp.kind != 1) {  // S part
+    const cplx s = {G.re * Jw, G.im * Jw};
+    if (kp.kind == 0) return s;
+    out = cmul({kp.br, kp.bi}, s);
+  }
+  const double ndx = (N0 * d0 + N1 * d1 + N2 * d2) * rinv * rinv;
+  // (1 - i k r) with k = kr + i ki: (1 + ki r) - i kr r
+  const cplx f = {1.0 + kp.ki * r, -kp.kr * r};
+  cplx dd = cmul(G, f);
+  dd.re *= ndx;
+  dd.im *= ndx;
+  if (kp.kind == 1) return dd;
+  const cplx ad = cmul({kp.ar, kp.ai}, dd);
+  out.re += ad.re;
+  out.im += ad.im;
+  return out;
+}
+
+// Cross product helper.
+__device__ __forceinline__ void cross3(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+}  // namespace lcq

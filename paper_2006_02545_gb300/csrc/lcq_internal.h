@@ -1,0 +1,144 @@
+// Internal declarations shared by the host API and the kernel launchers of liblcq.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lcq.h"
+
+namespace lcq {
+
+constexpr int kMaxDeg = 10;
+constexpr int kMaxBasis = (kMaxDeg + 1) * (kMaxDeg + 2) / 2;  // 66
+constexpr int kMaxRule = 32;                                   // smooth rules m = 1..32
+constexpr int kMaxGL = 32;                                     // Gauss-Legendre orders 1..32
+constexpr int kMaxTestPts = 64;
+
+inline int n_basis(int d) { return (d + 1) * (d + 2) / 2; }
+
+// Device status bits (OR-ed into the status word by kernels).
+enum : int {
+  kStMaxDepth = 1,
+  kStCapacity = 2,
+  kStDegenerate = 4,
+  kStNonFinite = 8,
+};
+
+// Kernel parameters (Sec. 3): K = alpha D + beta S for CFIE.
+struct KernelParams {
+  int kind;          // 0 S, 1 D, 2 CFIE
+  double kr, ki;     // k = kr + i ki
+  double ar, ai;     // alpha
+  double br, bi;     // beta
+};
+
+// Per-degree reference tables uploaded to the device (built on the host).
+struct DegTables {
+  int d = 0, n = 0;
+  double normV = 0;
+  std::vector<double> u, v, w;   // discretization nodes and weights [n]
+  std::vector<double> V;         // values-to-coefficients, row-major [n][n] (row = nm)
+  double* dV = nullptr;          // device copy of V
+  double* dnodes = nullptr;      // device [3][n]: u, v, w
+};
+
+// Smooth rule family and Gauss-Legendre tables on the device.
+struct RuleTables {
+  std::vector<int> off;          // off[m] = first node of rule m (m = 1..kMaxRule), size kMaxRule+2
+  std::vector<double> u, v, w;
+  std::vector<int> gl_off;       // Gauss-Legendre order g at gl_off[g], g = 1..kMaxGL
+  std::vector<double> gl_x, gl_w;   // on [0,1]
+  int* doff = nullptr;
+  double* du = nullptr;
+  double* dv = nullptr;
+  double* dw = nullptr;
+  int* dgl_off = nullptr;
+  double* dgl_x = nullptr;
+  double* dgl_w = nullptr;
+};
+
+// Host table construction (lcq_tables.cu).
+bool build_deg_tables(int d, DegTables* t);
+bool build_rule_tables(RuleTables* t);
+void ref_nodes_host(int d, std::vector<double>* u, std::vector<double>* v);
+void koornwinder_host(int d, double u, double v, double* K);
+
+}  // namespace lcq
+
+// ----------------------------------------------------------------------------- handles
+struct lcq_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int* d_status = nullptr;
+  long long* d_counters = nullptr;   // [4]
+  int num_sms = 0;
+  lcq::DegTables deg[lcq::kMaxDeg + 1];
+  lcq::RuleTables rules;
+  bool rules_ready = false;
+  std::string last_error;
+  // grow-only workspace for the adaptive kernel
+  void* work = nullptr;
+  size_t work_bytes = 0;
+};
+
+struct lcq_near {
+  int64_t n_patches = 0, n_targets = 0, n_points = 0;
+  std::vector<int32_t> deg_h;
+  std::vector<int64_t> node_off_h;
+  int32_t* deg = nullptr;
+  int64_t* node_off = nullptr;
+  double* coef = nullptr;        // [N][3] Koornwinder coefficients of the charts
+  double* cen = nullptr;         // [P][3]
+  double* rad = nullptr;         // [P]
+  double* dj = nullptr;          // [P]
+  double* eta = nullptr;         // [P]
+  double* eta1 = nullptr;        // [P]
+  double* tgt = nullptr;         // [3][NT] copy of the targets
+  int32_t* tgt_patch = nullptr;  // [NT]
+  int32_t* tgt_lnode = nullptr;  // [NT] node index within its patch (-1 off surface)
+  int64_t* tnode = nullptr;      // [NT] copy of the caller's global node ids
+  int64_t* row_ptr = nullptr;    // [NT+1] CSR entries
+  int64_t* rowp_ptr = nullptr;   // [NT+1] patches per row
+  int32_t* rowp_patch = nullptr; // [sum] patch ids of each row, ascending
+  int64_t* rowp_off = nullptr;   // [sum] entry offset of that patch inside the row
+  int32_t* col = nullptr;        // [nnz]
+  int64_t* pair_ptr = nullptr;   // [P+1] patch-major near pairs
+  int32_t* pair_tgt = nullptr;   // [n_pairs]
+  uint8_t* pair_ad = nullptr;    // [n_pairs] 1 = adaptive
+  double* pair_d2 = nullptr;     // [n_pairs]
+  int64_t* pair_csr = nullptr;   // [n_pairs] first CSR entry of the pair
+  int64_t* ad_ptr = nullptr;     // [P+1]
+  int32_t* ad_pair = nullptr;    // [n_adaptive] pair ids
+  int64_t* an_ptr = nullptr;     // [P+1]
+  int32_t* an_pair = nullptr;    // [n_annulus]
+  int32_t* self_tgt = nullptr;   // [n_self]
+  int64_t* self_csr = nullptr;   // [n_self]
+  int64_t* self_ptr = nullptr;   // [P+1] self pairs grouped by patch
+  int64_t n_pairs = 0, n_self = 0, n_adaptive = 0, n_annulus = 0, nnz = 0;
+  int64_t max_adaptive = 0, max_pairs = 0, max_self = 0;
+  lcq_params params{};
+  // launch bookkeeping
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int n_max = 0;                              // largest n over the degrees present
+  int plist_count[lcq::kMaxDeg + 1] = {0};    // patches of each degree
+  int* plist_dev[lcq::kMaxDeg + 1] = {nullptr};
+};
+
+struct lcq_corr {
+  const lcq_near* near = nullptr;   // not owned; must outlive the correction object
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int kernel = 0;
+  int64_t n_patches = 0, n_targets = 0, nnz = 0, n_pairs = 0, n_self = 0, n_over = 0;
+  lcq::KernelParams kp{};
+  double* val = nullptr;         // [nnz][2]
+  int32_t* q = nullptr;          // [P]
+  int32_t* q_near = nullptr;     // [P]
+  int32_t* leaves = nullptr;     // [n_pairs]
+  int64_t* src_off = nullptr;    // [P+1] oversampled source offsets (apply)
+  std::vector<int32_t> q_h;
+};

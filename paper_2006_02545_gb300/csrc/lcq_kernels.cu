@@ -1,0 +1,1545 @@
+// CUDA kernels of the correction path (sm_103a).  FP64 throughout.
+//
+//   k_geom         chart coefficients, centroid, radius, d_j        (Sec. 3.2, Sec. 4)
+//   k_row_* /k_patch_*  near lists both ways, deterministic order   (Sec. 4 N_eta, Sec. 5.2)
+//   k_farorder     far order q_j and annulus order                  (Sec. 4.2, Eq. qj)
+//   k_rule_moments smooth-rule / annulus moments for many targets    (Sec. 4.2, Remark on eta_1)
+//   k_adaptive     adaptive subdivision over a per-patch union tree  (Sec. 4.3)
+//   k_self         singular self rules                              (Sec. 4, Eq. errestself)
+//   k_v2c          a - s = V^T (I_near - I_smooth) into the CSR       (Sec. 4.3, 5.3)
+//   k_far_src / k_far_sum / k_csr_apply   corrected potential      (Sec. 5.3)
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "lcq_device.cuh"
+#include "lcq_launch.h"
+
+namespace lcq {
+
+
+constexpr int kThreads = 256;
+
+// ============================================================================ helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide exclusive prefix of 0/1 flags for one chunk of blockDim items.
+// Returns this thread's position; *total receives the chunk's count.  Uses sm[33].
+__device__ __forceinline__ int block_flag_scan(int flag, int* sm, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, flag);
+  const int inwarp = __popc(bal & ((1u << lane) - 1u));
+  __syncthreads();
+  if (lane == 0) sm[warp] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int c = sm[w];
+      sm[w] = acc;
+      acc += c;
+    }
+    sm[32] = acc;
+  }
+  __syncthreads();
+  *total = sm[32];
+  return sm[warp] + inwarp;
+}
+
+__device__ __forceinline__ double eta_default(int d) {
+  const int p = d + 1;
+  return p <= 4 ? 2.75 : (p <= 8 ? 2.0 : 1.25);
+}
+
+// ============================================================================ geometry
+// One block per patch: x_nm = V y, J at the nodes, c_j, R_j, d_j (Sec. 3.2, 4).
+template <int D>
+__global__ void k_geom(const int* __restrict__ plist, int count, const int64_t* __restrict__ node_off,
+                       const double* __restrict__ xyz, int64_t N, const double* __restrict__ Vt,
+                       const double* __restrict__ nodes, double eta_p, double eta1_p,
+                       double* __restrict__ coef, double* __restrict__ cen, double* __restrict__ rad,
+                       double* __restrict__ dj, double* __restrict__ eta, double* __restrict__ eta1,
+                       int* __restrict__ status) {
+  constexpr int n = (D + 1) * (D + 2) / 2;
+  __shared__ double y[3][n];
+  __shared__ double cf[n * 3];
+  __shared__ double J[n];
+  __shared__ double c[3];
+  __shared__ double red[kThreads / 32];
+  for (int b = blockIdx.x; b < count; b += gridDim.x) {
+    const int j = plist[b];
+    const int64_t off = node_off[j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < 3 * n; e += blockDim.x) {
+      const int cc = e / n, l = e % n;
+      const double val = xyz[cc * N + off + l];
+      if (!isfinite(val)) atomicOr(status, kStNonFinite);
+      y[cc][l] = val;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 3 * n; e += blockDim.x) {
+      const int nm = e / 3, cc = e % 3;
+      double acc = 0.0;
+      for (int l = 0; l < n; ++l) acc = fma(Vt[nm * n + l], y[cc][l], acc);
+      cf[nm * 3 + cc] = acc;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+      double X[3], Xu[3], Xv[3], Nn[3];
+      kw_geometry<D>(nodes[l], nodes[n + l], cf, X, Xu, Xv, nullptr, 1);
+      cross3(Xu, Xv, Nn);
+      const double jj = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
+      if (!(jj > 0.0)) atomicOr(status, kStDegenerate);
+      J[l] = jj;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sw = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0, dmin = 1e300;
+      for (int l = 0; l < n; ++l) {
+        const double wj = nodes[2 * n + l] * J[l];
+        sw += wj;
+        s0 += wj * y[0][l];
+        s1 += wj * y[1][l];
+        s2 += wj * y[2][l];
+        dmin = fmin(dmin, sqrt(wj));
+      }
+      c[0] = s0 / sw;
+      c[1] = s1 / sw;
+      c[2] = s2 / sw;
+      dj[j] = dmin;
+      const double e1 = eta_p > 0.0 ? eta_p : eta_default(D);
+      eta[j] = e1;
+      eta1[j] = fmin(eta1_p, e1);
+    }
+    __syncthreads();
+    // radius: 153 vertices of the level-4 subdivision of T0 plus the nodes
+    double rmax = 0.0;
+    for (int s = threadIdx.x; s < 153 + n; s += blockDim.x) {
+      double p0, p1, p2;
+      if (s < 153) {
+        int a = 0, r = s;
+        while (r >= 17 - a) {
+          r -= 17 - a;
+          ++a;
+        }
+        double X[3], Xu[3], Xv[3];
+        kw_geometry<D>(a / 16.0, r / 16.0, cf, X, Xu, Xv, nullptr, 1);
+        p0 = X[0];
+        p1 = X[1];
+        p2 = X[2];
+      } else {
+        p0 = y[0][s - 153];
+        p1 = y[1][s - 153];
+        p2 = y[2][s - 153];
+      }
+      const double d0 = p0 - c[0], d1 = p1 - c[1], d2 = p2 - c[2];
+      rmax = fmax(rmax, sqrt(d0 * d0 + d1 * d1 + d2 * d2));
+    }
+    rmax = warp_max(rmax);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double r = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+      rad[j] = r;
+      cen[3 * j] = c[0];
+      cen[3 * j + 1] = c[1];
+      cen[3 * j + 2] = c[2];
+    }
+    for (int e = threadIdx.x; e < 3 * n; e += blockDim.x) coef[off * 3 + e] = cf[e];
+  }
+}
+
+// ============================================================================ near lists
+__global__ void k_tgt_patch(const double* __restrict__ tgt, const int64_t* __restrict__ tnode,
+                            int64_t NT, const int64_t* __restrict__ node_off, int64_t P, int64_t N,
+                            int32_t* __restrict__ tpatch, int32_t* __restrict__ tlnode,
+                            int* __restrict__ status) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < NT;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    for (int c = 0; c < 3; ++c)
+      if (!isfinite(tgt[c * NT + t])) atomicOr(status, kStNonFinite);
+    const int64_t nd = tnode[t];
+    if (nd < 0 || nd >= N) {
+      tpatch[t] = -1;
+      tlnode[t] = -1;
+      continue;
+    }
+    int64_t lo = 0, hi = P;  // largest j with node_off[j] <= nd
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) / 2;
+      if (node_off[mid] <= nd) lo = mid; else hi = mid;
+    }
+    tpatch[t] = (int32_t)lo;
+    tlnode[t] = (int32_t)(nd - node_off[lo]);
+  }
+}
+
+struct NearView {
+  const double* tgt;
+  int64_t NT;
+  const double* cen;
+  const double* rad;
+  const double* eta;
+  const double* eta1;
+};
+
+// Near predicate of Sec. 4: |x - c_j|^2 <= (eta R_j)^2, t not on patch j.
+__device__ __forceinline__ bool is_near(const NearView& v, int64_t t, int j, double* d2out) {
+  const double d0 = v.tgt[t] - v.cen[3 * j], d1 = v.tgt[v.NT + t] - v.cen[3 * j + 1],
+               d2 = v.tgt[2 * v.NT + t] - v.cen[3 * j + 2];
+  const double d = d0 * d0 + d1 * d1 + d2 * d2;
+  const double r = v.eta[j] * v.rad[j];
+  *d2out = d;
+  return d <= r * r;
+}
+
+// Warp per target: number of patches in row t (near patches and the own patch) and entries.
+__global__ void k_row_count(NearView v, const int32_t* __restrict__ tpatch, int64_t P,
+                            const int32_t* __restrict__ deg, int64_t* __restrict__ row_np,
+                            int64_t* __restrict__ row_nnz) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < v.NT; t += warps) {
+    const int tp = tpatch[t];
+    long long cnt = 0, nnz = 0;
+    for (int64_t j0 = 0; j0 < P; j0 += 32) {
+      const int j = (int)(j0 + lane);
+      if (j < P) {
+        double d2;
+        const bool in = (j == tp) || is_near(v, t, j, &d2);
+        if (in) {
+          cnt += 1;
+          nnz += (deg[j] + 1) * (deg[j] + 2) / 2;
+        }
+      }
+    }
+    cnt = warp_sum_ll(cnt);
+    nnz = warp_sum_ll(nnz);
+    if (lane == 0) {
+      row_np[t] = cnt;
+      row_nnz[t] = nnz;
+    }
+  }
+}
+
+__global__ void k_row_fill(NearView v, const int32_t* __restrict__ tpatch, int64_t P,
+                           const int32_t* __restrict__ deg, const int64_t* __restrict__ node_off,
+                           const int64_t* __restrict__ rowp_ptr, const int64_t* __restrict__ row_ptr,
+                           int32_t* __restrict__ rowp_patch, int64_t* __restrict__ rowp_off,
+                           int32_t* __restrict__ col) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < v.NT; t += warps) {
+    const int tp = tpatch[t];
+    int64_t k = rowp_ptr[t];
+    int64_t eoff = 0;
+    const int64_t rbase = row_ptr[t];
+    for (int64_t j0 = 0; j0 < P; j0 += 32) {
+      const int j = (int)(j0 + lane);
+      bool in = false;
+      if (j < P) {
+        double d2;
+        in = (j == tp) || is_near(v, t, j, &d2);
+      }
+      unsigned bal = __ballot_sync(0xffffffffu, in);
+      while (bal) {
+        const int b = __ffs(bal) - 1;
+        bal &= bal - 1u;
+        const int jj = (int)(j0 + b);
+        const int nj = (deg[jj] + 1) * (deg[jj] + 2) / 2;
+        if (lane == 0) {
+          rowp_patch[k] = jj;
+          rowp_off[k] = eoff;
+        }
+        const int64_t nb = node_off[jj];
+        for (int l = lane; l < nj; l += 32) col[rbase + eoff + l] = (int32_t)(nb + l);
+        ++k;
+        eoff += nj;
+      }
+    }
+  }
+}
+
+// Block per patch: near pairs, adaptive pairs and self targets of patch j.
+__global__ void k_patch_count(NearView v, const int32_t* __restrict__ tpatch, int64_t P,
+                              int64_t* __restrict__ npair, int64_t* __restrict__ nad,
+                              int64_t* __restrict__ nself) {
+  __shared__ long long red[3][kThreads / 32];
+  for (int64_t j = blockIdx.x; j < P; j += gridDim.x) {
+    long long a = 0, b = 0, c = 0;
+    for (int64_t t = threadIdx.x; t < v.NT; t += blockDim.x) {
+      double d2;
+      const int tp = tpatch[t];
+      if (tp == (int)j) {
+        ++c;
+      } else if (is_near(v, t, (int)j, &d2)) {
+        ++a;
+        const double r1 = v.eta1[j] * v.rad[j];
+        if (d2 <= r1 * r1) ++b;
+      }
+    }
+    a = warp_sum_ll(a);
+    b = warp_sum_ll(b);
+    c = warp_sum_ll(c);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = a;
+      red[1][threadIdx.x >> 5] = b;
+      red[2][threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long s0 = 0, s1 = 0, s2 = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        s0 += red[0][w];
+        s1 += red[1][w];
+        s2 += red[2][w];
+      }
+      npair[j] = s0;
+      nad[j] = s1;
+      nself[j] = s2;
+    }
+  }
+}
+
+__device__ __forceinline__ int64_t row_entry(const int64_t* rowp_ptr, const int32_t* rowp_patch,
+                                             const int64_t* rowp_off, const int64_t* row_ptr,
+                                             int64_t t, int j) {
+  int64_t lo = rowp_ptr[t], hi = rowp_ptr[t + 1] - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    if (rowp_patch[mid] < j) lo = mid + 1; else hi = mid;
+  }
+  return row_ptr[t] + rowp_off[lo];
+}
+
+__global__ void k_patch_fill(NearView v, const int32_t* __restrict__ tpatch, int64_t P,
+                             const int64_t* __restrict__ pair_ptr, const int64_t* __restrict__ ad_ptr,
+                             const int64_t* __restrict__ an_ptr, const int64_t* __restrict__ self_ptr,
+                             const int64_t* __restrict__ rowp_ptr, const int32_t* __restrict__ rowp_patch,
+                             const int64_t* __restrict__ rowp_off, const int64_t* __restrict__ row_ptr,
+                             int32_t* __restrict__ pair_tgt, uint8_t* __restrict__ pair_ad,
+                             double* __restrict__ pair_d2, int64_t* __restrict__ pair_csr,
+                             int32_t* __restrict__ ad_pair, int32_t* __restrict__ an_pair,
+                             int32_t* __restrict__ self_tgt, int64_t* __restrict__ self_csr) {
+  __shared__ int sm[33];
+  for (int64_t j = blockIdx.x; j < P; j += gridDim.x) {
+    int64_t pbase = pair_ptr[j], abase = ad_ptr[j], nbase = an_ptr[j], sbase = self_ptr[j];
+    for (int64_t t0 = 0; t0 < v.NT; t0 += blockDim.x) {
+      const int64_t t = t0 + threadIdx.x;
+      bool near = false, ad = false, self = false;
+      double d2 = 0.0;
+      if (t < v.NT) {
+        const int tp = tpatch[t];
+        if (tp == (int)j) {
+          self = true;
+        } else if (is_near(v, t, (int)j, &d2)) {
+          near = true;
+          const double r1 = v.eta1[j] * v.rad[j];
+          ad = d2 <= r1 * r1;
+        }
+      }
+      int tot;
+      const int pos = block_flag_scan(near, sm, &tot);
+      if (near) {
+        const int64_t p = pbase + pos;
+        pair_tgt[p] = (int32_t)t;
+        pair_ad[p] = ad ? 1 : 0;
+        pair_d2[p] = d2;
+        pair_csr[p] = row_entry(rowp_ptr, rowp_patch, rowp_off, row_ptr, t, (int)j);
+      }
+      int tota;
+      const int apos = block_flag_scan(near && ad, sm, &tota);
+      if (near && ad) ad_pair[abase + apos] = (int32_t)(pbase + pos);
+      int totn;
+      const int npos = block_flag_scan(near && !ad, sm, &totn);
+      if (near && !ad) an_pair[nbase + npos] = (int32_t)(pbase + pos);
+      int tots;
+      const int spos = block_flag_scan(self, sm, &tots);
+      if (self) {
+        self_tgt[sbase + spos] = (int32_t)t;
+        self_csr[sbase + spos] = row_entry(rowp_ptr, rowp_patch, rowp_off, row_ptr, t, (int)j);
+      }
+      pbase += tot;
+      abase += tota;
+      nbase += totn;
+      sbase += tots;
+    }
+  }
+}
+
+// ============================================================================ scans
+// Exclusive scan of int64 in blocks of 1024 (two passes + recursion on block sums).
+__global__ void k_scan_block(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
+                             int64_t* __restrict__ bsum) {
+  __shared__ int64_t s[1024];
+  const int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+  const int64_t x = i < n ? in[i] : 0;
+  s[threadIdx.x] = x;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int64_t add = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+    __syncthreads();
+    s[threadIdx.x] += add;
+    __syncthreads();
+  }
+  if (i < n) out[i] = s[threadIdx.x] - x;
+  if (threadIdx.x == 1023) bsum[blockIdx.x] = s[1023];
+}
+__global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ boff) {
+  const int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+  if (i < n) out[i] += boff[blockIdx.x];
+}
+
+// ============================================================================ moments
+template <int D>
+struct Cfg {
+  static constexpr int n = (D + 1) * (D + 2) / 2;
+  static constexpr int NP = n <= 32 ? 32 : (n <= 64 ? 64 : 96);
+  static constexpr int CH = D <= 6 ? 256 : 128;
+  static constexpr int BS = n + 1;
+  static constexpr int TT = 16;
+  // doubles of shared workspace used by block_moments
+  static constexpr int WS = CH * BS + 7 * CH + 2 * TT * CH + 3 * TT;
+};
+
+struct SegMap {
+  double ax, ay, e1x, e1y, e2x, e2y, det;
+};
+
+// Moments I[i][seg][nm] = sum_{q in seg} w_q K(x_i, X_q) J_q K_nm(u_q, v_q) for a smooth
+// rule (Q nodes) pushed onto nseg affine images of T0, for T targets.  Geometry is
+// evaluated once per chunk of nodes and shared by all targets (Sec. 4.3 reuse).
+// TA: target accessor (pos(i, x[3])); out row of target i: out + orow(i) * ostride.
+template <int D, class TA, class OR>
+__device__ void block_moments(const double* cf, const double* __restrict__ ru,
+                              const double* __restrict__ rv, const double* __restrict__ rw, int Q,
+                              const SegMap* segs, int nseg, const TA& ta, int T, OR orow,
+                              int64_t ostride, const KernelParams& kp, double* sm) {
+  using C = Cfg<D>;
+  double* B = sm;
+  double* Xs = B + C::CH * C::BS;
+  double* Ns = Xs + 3 * C::CH;
+  double* Js = Ns + 3 * C::CH;
+  cplx* G = reinterpret_cast<cplx*>(Js + C::CH);
+  double* tx = reinterpret_cast<double*>(G + C::TT * C::CH);
+  const int total = nseg * Q;
+  for (int c0 = 0; c0 < total; c0 += C::CH) {
+    const int nch = min(C::CH, total - c0);
+    __syncthreads();
+    for (int ql = threadIdx.x; ql < nch; ql += blockDim.x) {
+      const int q = c0 + ql;
+      const int sg = q / Q, l = q - sg * Q;
+      const SegMap& S = segs[sg];
+      const double r0 = ru[l], r1 = rv[l];
+      const double u = S.ax + r0 * S.e1x + r1 * S.e2x;
+      const double v = S.ay + r0 * S.e1y + r1 * S.e2y;
+      const double w = rw[l] * S.det;
+      double X[3], Xu[3], Xv[3], Nn[3];
+      kw_geometry<D>(u, v, cf, X, Xu, Xv, B + ql * C::BS, 1);
+      cross3(Xu, Xv, Nn);
+      const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Xs[c * C::CH + ql] = X[c];
+        Ns[c * C::CH + ql] = Nn[c] * w;
+      }
+      Js[ql] = J * w;
+    }
+    __syncthreads();
+    for (int t0 = 0; t0 < T; t0 += C::TT) {
+      const int nt = min(C::TT, T - t0);
+      if (threadIdx.x < nt) ta.pos(t0 + threadIdx.x, tx + 3 * threadIdx.x);
+      __syncthreads();
+      for (int e = threadIdx.x; e < nt * C::CH; e += blockDim.x) {
+        const int i = e / C::CH, ql = e - i * C::CH;
+        cplx g = {0.0, 0.0};
+        if (ql < nch)
+          g = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql], Xs[C::CH + ql],
+                          Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql], Js[ql]);
+        G[i * C::CH + ql] = g;
+      }
+      __syncthreads();
+      const int nout = nt * nseg * C::NP;
+      for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        const int nm = o % C::NP;
+        const int rest = o / C::NP;
+        const int sg = rest % nseg, i = rest / nseg;
+        if (nm >= C::n) continue;
+        const int qa = max(sg * Q - c0, 0), qb = min((sg + 1) * Q - c0, nch);
+        double are = 0.0, aim = 0.0;
+        const cplx* Gi = G + i * C::CH;
+        for (int ql = qa; ql < qb; ++ql) {
+          const cplx g = Gi[ql];
+          const double bv = B[ql * C::BS + nm];
+          are = fma(g.re, bv, are);
+          aim = fma(g.im, bv, aim);
+        }
+        cplx* dst = reinterpret_cast<cplx*>(orow(t0 + i)) + (int64_t)sg * C::n + nm;
+        (void)ostride;
+        if (c0 == 0) {
+          dst->re = are;
+          dst->im = aim;
+        } else {
+          dst->re += are;
+          dst->im += aim;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void load_coef(const double* __restrict__ coef, int64_t off, double* cf) {
+  constexpr int n = (D + 1) * (D + 2) / 2;
+  for (int e = threadIdx.x; e < 3 * n; e += blockDim.x) cf[e] = coef[off * 3 + e];
+}
+
+struct TgtIdx {  // targets by id list
+  const double* tgt;
+  int64_t NT;
+  const int32_t* ids;
+  __device__ void pos(int i, double* x) const {
+    const int64_t t = ids[i];
+    x[0] = tgt[t];
+    x[1] = tgt[NT + t];
+    x[2] = tgt[2 * NT + t];
+  }
+};
+struct TgtPairIdx {  // targets of pair ids
+  const double* tgt;
+  int64_t NT;
+  const int32_t* pair_tgt;
+  const int32_t* pairs;
+  __device__ void pos(int i, double* x) const {
+    const int64_t t = pair_tgt[pairs[i]];
+    x[0] = tgt[t];
+    x[1] = tgt[NT + t];
+    x[2] = tgt[2 * NT + t];
+  }
+};
+struct TgtPts {  // explicit points [i][3]
+  const double* p;
+  __device__ void pos(int i, double* x) const {
+    x[0] = p[3 * i];
+    x[1] = p[3 * i + 1];
+    x[2] = p[3 * i + 2];
+  }
+};
+
+struct TgtAdaptive {  // targets of a union-tree node: local ids -> pairs -> targets
+  const double* tgt;
+  int64_t NT;
+  const int32_t* pair_tgt;
+  const int32_t* apairs;
+  const int* ST;
+  __device__ void pos(int i, double* x) const {
+    const int64_t t = pair_tgt[apairs[ST[i]]];
+    x[0] = tgt[t];
+    x[1] = tgt[NT + t];
+    x[2] = tgt[2 * NT + t];
+  }
+};
+
+__device__ __forceinline__ SegMap seg_T0() { return {0.0, 0.0, 1.0, 0.0, 0.0, 1.0, 1.0}; }
+
+// Smooth rule q_j moments for every near pair and self target of the patch (Sec. 4.2):
+// I_smooth; and annulus-rule moments for annulus pairs (Remark on eta_1).
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_rule_moments(
+    const int* __restrict__ plist, int count, Dev dv, int mode, const int32_t* __restrict__ qv,
+    const KernelParams kp, cplx* __restrict__ out_pairs, cplx* __restrict__ out_self) {
+  using C = Cfg<D>;
+  extern __shared__ double smem[];
+  double* cf = smem;
+  SegMap* segs = reinterpret_cast<SegMap*>(cf + C::n * 3);
+  double* ws = reinterpret_cast<double*>(segs + 4);
+  for (int b = blockIdx.x; b < count; b += gridDim.x) {
+    const int j = plist[b];
+    const int m = qv[j];
+    __syncthreads();
+    load_coef<D>(dv.coef, dv.node_off[j], cf);
+    if (threadIdx.x == 0) segs[0] = seg_T0();
+    __syncthreads();
+    if (m <= 0) continue;
+    const double* ru = dv.ru + dv.roff[m];
+    const double* rv = dv.rv + dv.roff[m];
+    const double* rw = dv.rw + dv.roff[m];
+    if (mode == 0) {
+      const int64_t p0 = dv.pair_ptr[j], np = dv.pair_ptr[j + 1] - p0;
+      TgtIdx ta{dv.tgt, dv.NT, dv.pair_tgt + p0};
+      const int64_t ld = dv.ldI;
+      cplx* base = out_pairs + p0 * ld;
+      block_moments<D>(cf, ru, rv, rw, m * m, segs, 1, ta, (int)np,
+                       [=] __device__(int i) { return base + (int64_t)i * ld; }, C::n, kp, ws);
+      const int64_t s0 = dv.self_ptr[j], ns = dv.self_ptr[j + 1] - s0;
+      TgtIdx ts{dv.tgt, dv.NT, dv.self_tgt + s0};
+      cplx* sb = out_self + s0 * ld;
+      block_moments<D>(cf, ru, rv, rw, m * m, segs, 1, ts, (int)ns,
+                       [=] __device__(int i) { return sb + (int64_t)i * ld; }, C::n, kp, ws);
+    } else {
+      const int64_t a0 = dv.an_ptr[j], na = dv.an_ptr[j + 1] - a0;
+      const int32_t* pl = dv.an_pair + a0;
+      TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl};
+      const int64_t ld = dv.ldI;
+      block_moments<D>(cf, ru, rv, rw, m * m, segs, 1, ta, (int)na,
+                       [=] __device__(int i) { return out_pairs + (int64_t)pl[i] * ld; }, C::n, kp,
+                       ws);
+    }
+    if (threadIdx.x == 0) {
+      const long long nt = mode == 0 ? (dv.pair_ptr[j + 1] - dv.pair_ptr[j] + dv.self_ptr[j + 1] -
+                                        dv.self_ptr[j])
+                                     : (dv.an_ptr[j + 1] - dv.an_ptr[j]);
+      atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 3),
+                (unsigned long long)(nt * m * m));
+    }
+  }
+}
+
+// ============================================================================ far order
+// q_j (Eq. qj) and the annulus order: smallest m with
+//   max_x ||I_m(x) - I_{m+1}(x)||_2 <= eps d_j / ||V||  over the test points.
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ plist, int count,
+                                                       Dev dv, const KernelParams kp, double eps,
+                                                       int m_max, double normV,
+                                                       const double* __restrict__ dirs, int ndirs,
+                                                       cplx* __restrict__ scratch,
+                                                       int32_t* __restrict__ q_out,
+                                                       int32_t* __restrict__ qn_out) {
+  using C = Cfg<D>;
+  extern __shared__ double smem[];
+  double* cf = smem;
+  SegMap* segs = reinterpret_cast<SegMap*>(cf + C::n * 3);
+  double* pts = reinterpret_cast<double*>(segs + 4);        // [kMaxTestPts][3]
+  double* red = pts + 3 * kMaxTestPts;                      // [kThreads/32]
+  int* sel = reinterpret_cast<int*>(red + kThreads / 32);   // [2]
+  double* ws = reinterpret_cast<double*>(sel + 4);
+  cplx* bufA = scratch + (int64_t)blockIdx.x * 2 * kMaxTestPts * C::n;
+  cplx* bufB = bufA + kMaxTestPts * C::n;
+  const int m_min = (D + 2) / 2;
+  for (int b = blockIdx.x; b < count; b += gridDim.x) {
+    const int j = plist[b];
+    __syncthreads();
+    load_coef<D>(dv.coef, dv.node_off[j], cf);
+    if (threadIdx.x == 0) segs[0] = seg_T0();
+    const int64_t p0 = dv.pair_ptr[j], np = dv.pair_ptr[j + 1] - p0;
+    const double R = dv.rad[j], c0 = dv.cen[3 * j], c1 = dv.cen[3 * j + 1], c2 = dv.cen[3 * j + 2];
+    const double tol = eps * dv.dj[j] / normV;
+    for (int pass = 0; pass < 2; ++pass) {
+      // test points (Sec. 4.2): pass 0 = far order, pass 1 = annulus order
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int F = 0;
+        if (pass == 0) {
+          const int cnt = np >= 20 ? 10 : (int)(np / 2);
+          // repeated selection: largest d2, ties by smaller target id
+          double lastd = 1e300;
+          int lastt = -1;
+          for (int k = 0; k < cnt; ++k) {
+            double bd = -1.0;
+            int bt = 0x7fffffff;
+            for (int64_t p = 0; p < np; ++p) {
+              const double d = dv.pair_d2[p0 + p];
+              const int t = dv.pair_tgt[p0 + p];
+              const bool after = (d < lastd) || (d == lastd && t > lastt);
+              if (!after) continue;
+              if (d > bd || (d == bd && t < bt)) {
+                bd = d;
+                bt = t;
+              }
+            }
+            lastd = bd;
+            lastt = bt;
+            pts[3 * F] = dv.tgt[bt];
+            pts[3 * F + 1] = dv.tgt[dv.NT + bt];
+            pts[3 * F + 2] = dv.tgt[2 * dv.NT + bt];
+            ++F;
+          }
+          if (np < 20)
+            for (int k = 0; k < ndirs && F < kMaxTestPts; ++k) {
+              const double rr = dv.eta[j] * R;
+              pts[3 * F] = c0 + rr * dirs[3 * k];
+              pts[3 * F + 1] = c1 + rr * dirs[3 * k + 1];
+              pts[3 * F + 2] = c2 + rr * dirs[3 * k + 2];
+              ++F;
+            }
+        } else {
+          const int64_t a0 = dv.an_ptr[j], na = dv.an_ptr[j + 1] - a0;
+          if (na > 0) {
+            for (int k = 0; k < ndirs && F < kMaxTestPts; ++k) {
+              const double rr = dv.eta1[j] * R;
+              pts[3 * F] = c0 + rr * dirs[3 * k];
+              pts[3 * F + 1] = c1 + rr * dirs[3 * k + 1];
+              pts[3 * F + 2] = c2 + rr * dirs[3 * k + 2];
+              ++F;
+            }
+            const int cnt = na < 10 ? (int)na : 10;
+            double lastd = -1.0;
+            int lastt = -1;
+            for (int k = 0; k < cnt && F < kMaxTestPts; ++k) {
+              double bd = 1e300;
+              int bt = 0x7fffffff;
+              for (int64_t a = 0; a < na; ++a) {
+                const int64_t p = dv.an_pair[a0 + a];
+                const double d = dv.pair_d2[p];
+                const int t = dv.pair_tgt[p];
+                const bool after = (d > lastd) || (d == lastd && t > lastt);
+                if (!after) continue;
+                if (d < bd || (d == bd && t < bt)) {
+                  bd = d;
+                  bt = t;
+                }
+              }
+              lastd = bd;
+              lastt = bt;
+              pts[3 * F] = dv.tgt[bt];
+              pts[3 * F + 1] = dv.tgt[dv.NT + bt];
+              pts[3 * F + 2] = dv.tgt[2 * dv.NT + bt];
+              ++F;
+            }
+          }
+        }
+        sel[0] = F;
+      }
+      __syncthreads();
+      const int F = sel[0];
+      if (pass == 1 && F == 0) {
+        if (threadIdx.x == 0) qn_out[j] = 0;
+        continue;
+      }
+      TgtPts ta{pts};
+      int m = m_min, chosen = m_max;
+      {
+        const double* ru = dv.ru + dv.roff[m];
+        block_moments<D>(cf, ru, dv.rv + dv.roff[m], dv.rw + dv.roff[m], m * m, segs, 1, ta, F,
+                         [=] __device__(int i) { return bufA + (int64_t)i * C::n; }, C::n, kp, ws);
+      }
+      cplx* A = bufA;
+      cplx* Bf = bufB;
+      for (; m < m_max; ++m) {
+        const int m1 = m + 1;
+        block_moments<D>(cf, dv.ru + dv.roff[m1], dv.rv + dv.roff[m1], dv.rw + dv.roff[m1], m1 * m1,
+                         segs, 1, ta, F, [=] __device__(int i) { return Bf + (int64_t)i * C::n; },
+                         C::n, kp, ws);
+        __syncthreads();
+        // max over points of the 2-norm of the difference
+        double e = 0.0;
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int i = w; i < F; i += blockDim.x >> 5) {
+          double s = 0.0;
+          for (int nm = lane; nm < C::n; nm += 32) {
+            const cplx a = A[i * C::n + nm], bb = Bf[i * C::n + nm];
+            const double dr = a.re - bb.re, di = a.im - bb.im;
+            s += dr * dr + di * di;
+          }
+          s = warp_sum(s);
+          e = fmax(e, sqrt(s));
+        }
+        if (lane == 0) red[w] = e;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double mx = 0.0;
+          for (int k = 0; k < (int)(blockDim.x >> 5); ++k) mx = fmax(mx, red[k]);
+          sel[1] = mx <= tol ? 1 : 0;
+        }
+        __syncthreads();
+        if (sel[1]) {
+          chosen = m;
+          break;
+        }
+        cplx* tmp = A;
+        A = Bf;
+        Bf = tmp;
+      }
+      if (threadIdx.x == 0) {
+        if (pass == 0) q_out[j] = chosen; else qn_out[j] = chosen;
+      }
+    }
+  }
+}
+
+// ============================================================================ adaptive
+// Adaptive subdivision (Sec. 4.3) for all eta_1-near targets of a patch at once.
+// The refinement trees of the targets are walked as one union tree, depth first:
+// a node T carries the set S of targets that refine T; the leaf-rule geometry of T's
+// four children is evaluated once and contracted with every target in S (the reuse
+// of X, K_nm and J across targets of Fig. multipletargpot).  A target accepts the
+// children's sum when ||I_T - sum_c I_c||_2 <= max(tol0 4^-L, 1e-12 ||sum_c I_c||_2).
+constexpr int kMaxTreeNodes = 1 << 16;  // union-tree nodes walked per patch at most
+
+struct AdaptiveWS {
+  int64_t stride;   // bytes per block
+  int A_max, levels;
+};
+
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_adaptive(const int* __restrict__ plist, int count,
+                                                       Dev dv, const KernelParams kp, double eps,
+                                                       double normV, int leaf_order, int max_depth,
+                                                       const cplx* __restrict__ I_smooth,
+                                                       cplx* __restrict__ I_near,
+                                                       int32_t* __restrict__ leaves_out,
+                                                       unsigned char* __restrict__ work,
+                                                       AdaptiveWS wsd, int* __restrict__ status) {
+  using C = Cfg<D>;
+  constexpr int n = C::n;
+  extern __shared__ double smem[];
+  double* cf = smem;
+  SegMap* segs = reinterpret_cast<SegMap*>(cf + n * 3);
+  int* ism = reinterpret_cast<int*>(segs + 4);  // [64]: scan scratch + misc
+  unsigned long long* stk = reinterpret_cast<unsigned long long*>(ism + 64);  // [4 * 32]
+  double* ws = reinterpret_cast<double*>(stk + 4 * 32);
+  // per-block global workspace
+  unsigned char* wb = work + (int64_t)blockIdx.x * wsd.stride;
+  const int A_max = wsd.A_max;
+  cplx* acc = reinterpret_cast<cplx*>(wb);                          // [A_max][n]
+  cplx* tmp = acc + (int64_t)A_max * n;                             // [A_max][4][n]
+  cplx* lvlI = tmp + (int64_t)A_max * 4 * n;                        // [levels][A_max][4][n]
+  int* lvlT = reinterpret_cast<int*>(lvlI + (int64_t)wsd.levels * A_max * 4 * n);  // [levels][A_max]
+  int* flags = lvlT + (int64_t)wsd.levels * A_max;                  // [A_max]
+  int* lcnt = flags + A_max;                                        // [A_max]
+  int* cnt = lcnt + A_max;                                          // [levels]
+  long long my_tests = 0, my_nodes = 0;
+
+  for (int b = blockIdx.x; b < count; b += gridDim.x) {
+    const int j = plist[b];
+    const int64_t a0 = dv.ad_ptr[j];
+    const int A = (int)(dv.ad_ptr[j + 1] - a0);
+    if (A == 0) continue;
+    if (A > A_max) {
+      if (threadIdx.x == 0) atomicOr(status, kStCapacity);
+      continue;
+    }
+    const int m = leaf_order > 0 ? leaf_order : dv.q[j];
+    const int Q = m * m;
+    const double* ru = dv.ru + dv.roff[m];
+    const double* rv = dv.rv + dv.roff[m];
+    const double* rw = dv.rw + dv.roff[m];
+    const double tol0 = eps * dv.dj[j] / normV;
+    const int32_t* apairs = dv.ad_pair + a0;
+    __syncthreads();
+    load_coef<D>(dv.coef, dv.node_off[j], cf);
+    // root: level 0 block holds all targets with I_T0 in slot c = 0
+    for (int e = threadIdx.x; e < A * n; e += blockDim.x) {
+      const int i = e / n, nm = e - i * n;
+      acc[e] = {0.0, 0.0};
+      if (leaf_order <= 0) lvlI[(int64_t)i * 4 * n + nm] = I_smooth[(int64_t)apairs[i] * dv.ldI + nm];
+    }
+    for (int i = threadIdx.x; i < A; i += blockDim.x) {
+      lvlT[i] = i;
+      lcnt[i] = 0;
+    }
+    if (threadIdx.x == 0) {
+      segs[0] = seg_T0();
+      cnt[0] = A;
+    }
+    __syncthreads();
+    if (leaf_order > 0) {
+      TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, apairs};
+      block_moments<D>(cf, ru, rv, rw, Q, segs, 1, ta, A,
+                       [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, 4 * n, kp, ws);
+    }
+    // DFS stack entries: level (8 bits) | child (2 bits) | path (2 bits per level) << 16
+    int sp = 0;
+    if (threadIdx.x == 0) stk[0] = 0ull;  // root: level 0, child 0, empty path
+    sp = 1;
+    int visited = 0;
+    while (sp > 0) {
+      if (++visited > kMaxTreeNodes) {  // bounded walk: give up on this patch
+        if (threadIdx.x == 0) atomicOr(status, kStCapacity);
+        break;
+      }
+      __syncthreads();
+      const unsigned long long top = stk[sp - 1];
+      --sp;
+      const int L = (int)(top & 0xff);
+      const int cidx = (int)((top >> 8) & 3);
+      const unsigned long long path = top >> 16;  // child digits of T, level 1 at bits 0-1
+      // vertices of T
+      double ax = 0, ay = 0, bx = 1, by = 0, cx = 0, cy = 1;
+      for (int l = 0; l < L; ++l) {
+        const int dgt = (int)((path >> (2 * l)) & 3);
+        const double abx = 0.5 * (ax + bx), aby = 0.5 * (ay + by);
+        const double bcx = 0.5 * (bx + cx), bcy = 0.5 * (by + cy);
+        const double cax = 0.5 * (cx + ax), cay = 0.5 * (cy + ay);
+        if (dgt == 0) { bx = abx; by = aby; cx = cax; cy = cay; }
+        else if (dgt == 1) { ax = abx; ay = aby; cx = bcx; cy = bcy; }
+        else if (dgt == 2) { ax = cax; ay = cay; bx = bcx; by = bcy; }
+        else { ax = bcx; ay = bcy; bx = cax; by = cay; cx = abx; cy = aby; }
+      }
+      const int S = cnt[L];
+      const int* ST = lvlT + (int64_t)L * A_max;
+      const cplx* IT = lvlI + (int64_t)L * A_max * 4 * n;
+      if (threadIdx.x == 0) {
+        const double abx = 0.5 * (ax + bx), aby = 0.5 * (ay + by);
+        const double bcx = 0.5 * (bx + cx), bcy = 0.5 * (by + cy);
+        const double cax = 0.5 * (cx + ax), cay = 0.5 * (cy + ay);
+        const double V[4][6] = {{ax, ay, abx, aby, cax, cay},
+                                {abx, aby, bx, by, bcx, bcy},
+                                {cax, cay, bcx, bcy, cx, cy},
+                                {bcx, bcy, cax, cay, abx, aby}};
+        for (int k = 0; k < 4; ++k) {
+          SegMap s;
+          s.ax = V[k][0];
+          s.ay = V[k][1];
+          s.e1x = V[k][2] - V[k][0];
+          s.e1y = V[k][3] - V[k][1];
+          s.e2x = V[k][4] - V[k][0];
+          s.e2y = V[k][5] - V[k][1];
+          s.det = fabs(s.e1x * s.e2y - s.e1y * s.e2x);
+          segs[k] = s;
+        }
+      }
+      __syncthreads();
+      // children moments of every target in S
+      TgtAdaptive ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, ST};
+      block_moments<D>(cf, ru, rv, rw, Q, segs, 4, ta, S,
+                       [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, 4 * n, kp, ws);
+      __syncthreads();
+      my_tests += S;
+      my_nodes += (long long)S * 4 * Q;
+      // decisions: one warp per target
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      const double tauL = tol0 * ldexp(1.0, -2 * L);
+      for (int s = w; s < S; s += nw) {
+        double e2 = 0.0, s2 = 0.0;
+        for (int nm = lane; nm < n; nm += 32) {
+          const cplx* tc = tmp + (int64_t)s * 4 * n + nm;
+          const double sr = tc[0].re + tc[n].re + tc[2 * n].re + tc[3 * n].re;
+          const double si = tc[0].im + tc[n].im + tc[2 * n].im + tc[3 * n].im;
+          const cplx it = IT[(int64_t)s * 4 * n + (int64_t)cidx * n + nm];
+          const double dr = it.re - sr, di = it.im - si;
+          e2 += dr * dr + di * di;
+          s2 += sr * sr + si * si;
+        }
+        e2 = warp_sum(e2);
+        s2 = warp_sum(s2);
+        const double err = sqrt(e2);
+        const double tau = fmax(tauL, 1e-12 * sqrt(s2));
+        const bool finite = isfinite(err) && isfinite(tau);
+        const bool accept = !finite || (err <= tau) || (L + 1 >= max_depth);
+        if (lane == 0) {
+          if (!finite) atomicOr(status, kStNonFinite);
+          else if (err > tau && accept) atomicOr(status, kStMaxDepth);
+        }
+        const int tl = ST[s];
+        if (accept) {
+          for (int nm = lane; nm < n; nm += 32) {
+            const cplx* tc = tmp + (int64_t)s * 4 * n + nm;
+            cplx& a = acc[(int64_t)tl * n + nm];
+            a.re += tc[0].re + tc[n].re + tc[2 * n].re + tc[3 * n].re;
+            a.im += tc[0].im + tc[n].im + tc[2 * n].im + tc[3 * n].im;
+          }
+          if (lane == 0) lcnt[tl] += 4;
+        }
+        if (lane == 0) flags[s] = accept ? 0 : 1;
+      }
+      __syncthreads();
+      // stable compaction of the refining targets into level L+1
+      int base = 0;
+      int* DT = lvlT + (int64_t)(L + 1) * A_max;
+      cplx* DI = lvlI + (int64_t)(L + 1) * A_max * 4 * n;
+      for (int s0 = 0; s0 < S; s0 += blockDim.x) {
+        const int s = s0 + threadIdx.x;
+        const int f = s < S ? flags[s] : 0;
+        int tot;
+        const int pos = block_flag_scan(f, ism, &tot);
+        if (f) {
+          flags[s] = -(base + pos) - 1;  // remember destination
+          DT[base + pos] = ST[s];
+        }
+        base += tot;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < S * 4 * n; e += blockDim.x) {
+        const int s = e / (4 * n);
+        const int f = flags[s];
+        if (f < 0) DI[(int64_t)(-f - 1) * 4 * n + (e - s * 4 * n)] = tmp[e];
+      }
+      if (threadIdx.x == 0) cnt[L + 1] = base;
+      __syncthreads();
+      if (base > 0) {
+        if (sp + 4 > 4 * 32) {
+          if (threadIdx.x == 0) atomicOr(status, kStCapacity);
+        } else {
+          const unsigned long long np = (L == 0) ? 0ull : path;
+          if (threadIdx.x == 0) {
+            for (int c = 3; c >= 0; --c)
+              stk[sp + (3 - c)] = (unsigned long long)(L + 1) | ((unsigned long long)c << 8) |
+                                  ((np | ((unsigned long long)c << (2 * L))) << 16);
+          }
+          sp += 4;
+        }
+      }
+      (void)cidx;
+    }
+    __syncthreads();
+    // results of the patch
+    for (int e = threadIdx.x; e < A * n; e += blockDim.x) {
+      const int i = e / n, nm = e - i * n;
+      I_near[(int64_t)apairs[i] * dv.ldI + nm] = acc[e];
+    }
+    for (int i = threadIdx.x; i < A; i += blockDim.x) leaves_out[apairs[i]] = lcnt[i];
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 0), (unsigned long long)my_tests);
+    atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 1), (unsigned long long)my_nodes);
+  }
+}
+
+// ============================================================================ self
+// Self rule for the target at node i (Sec. 4, Eq. errestself; stand-in for
+// generalized Gaussian rules): affine map M = G^{-1/2} (G the first fundamental
+// form at the node) making the chart conformal there, split at the node into three
+// Duffy triangles; s: n_s-point Gauss-Legendre; t: split at the foot of the
+// perpendicular, sinh substitution t - t0 = mu sinh(xi), [0, xi_max] cut into
+// ceil(xi_max / 1.5) panels of n_t-point Gauss-Legendre.
+struct SelfSeg {
+  double E0x, E0y, Dx, Dy, t0, mu, area2, xi_max, side;
+  int npan, off;
+};
+
+template <int D>
+__global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict__ deg_of_patch,
+                                              const KernelParams kp, int order,
+                                              cplx* __restrict__ out_self) {
+  constexpr int n = (D + 1) * (D + 2) / 2;
+  __shared__ double cf[3 * n];
+  __shared__ SelfSeg sg[6];
+  __shared__ double Mm[5];  // M00 M01 M10 M11 detM
+  __shared__ double P[2];
+  __shared__ int nseg, total;
+  __shared__ cplx red[4][n];
+  const int ns = order, nt = order;
+  const double* glx_s = dv.gl_x + dv.gl_off[ns];
+  const double* glw_s = dv.gl_w + dv.gl_off[ns];
+  const double* glx_t = dv.gl_x + dv.gl_off[nt];
+  const double* glw_t = dv.gl_w + dv.gl_off[nt];
+  long long my_nodes = 0;
+  for (int64_t s = blockIdx.x; s < dv.n_self; s += gridDim.x) {
+    const int t = dv.self_tgt[s];
+    const int j = dv.tpatch[t];
+    if (deg_of_patch[j] != D) continue;
+    const int i = dv.tlnode[t];
+    __syncthreads();
+    load_coef<D>(dv.coef, dv.node_off[j], cf);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double pu = dv.nodes_uv[D][i], pv = dv.nodes_uv[D][n + i];
+      P[0] = pu;
+      P[1] = pv;
+      double X[3], Xu[3], Xv[3];
+      kw_geometry<D>(pu, pv, cf, X, Xu, Xv, nullptr, 1);
+      const double a = Xu[0] * Xu[0] + Xu[1] * Xu[1] + Xu[2] * Xu[2];
+      const double bb = Xu[0] * Xv[0] + Xu[1] * Xv[1] + Xu[2] * Xv[2];
+      const double c = Xv[0] * Xv[0] + Xv[1] * Xv[1] + Xv[2] * Xv[2];
+      const double sq = sqrt(a * c - bb * bb);
+      const double tt = sqrt(a + c + 2.0 * sq);
+      // R = sqrt(G) = (G + sq I)/tt ; M = R^{-1}
+      const double R00 = (a + sq) / tt, R01 = bb / tt, R11 = (c + sq) / tt;
+      const double detR = R00 * R11 - R01 * R01;
+      Mm[0] = R11 / detR;
+      Mm[1] = -R01 / detR;
+      Mm[2] = -R01 / detR;
+      Mm[3] = R00 / detR;
+      Mm[4] = 1.0 / detR;
+      double Z[3][2];
+      const double VX[3] = {0.0, 1.0, 0.0}, VY[3] = {0.0, 0.0, 1.0};
+      for (int k = 0; k < 3; ++k) {
+        const double dx = VX[k] - pu, dy = VY[k] - pv;
+        Z[k][0] = R00 * dx + R01 * dy;
+        Z[k][1] = R01 * dx + R11 * dy;
+      }
+      int cntg = 0, off = 0;
+      for (int e = 0; e < 3; ++e) {
+        const double E0x = Z[e][0], E0y = Z[e][1];
+        const double Dx = Z[(e + 1) % 3][0] - E0x, Dy = Z[(e + 1) % 3][1] - E0y;
+        const double L2 = Dx * Dx + Dy * Dy;
+        double t0 = -(E0x * Dx + E0y * Dy) / L2;
+        t0 = fmin(fmax(t0, 0.0), 1.0);
+        const double area2 = fabs(E0x * Dy - E0y * Dx);
+        const double mu = area2 / L2;
+        for (int sd = 0; sd < 2; ++sd) {
+          const double side = sd == 0 ? 1.0 : -1.0;
+          const double len = sd == 0 ? 1.0 - t0 : t0;
+          if (len <= 0.0) continue;
+          const double xm = asinh(len / mu);
+          int npan = 1;
+          if (isfinite(xm) && xm > 0.0) npan = (int)fmin(ceil(xm / 1.5), 64.0);
+          else atomicOr(dv.status, kStNonFinite);
+          SelfSeg g{E0x, E0y, Dx, Dy, t0, mu, area2, xm, side, npan, off};
+          sg[cntg++] = g;
+          off += npan * nt * ns;
+        }
+      }
+      nseg = cntg;
+      total = off;
+    }
+    __syncthreads();
+    const double x0 = dv.tgt[t], x1 = dv.tgt[dv.NT + t], x2 = dv.tgt[2 * dv.NT + t];
+    cplx acc[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) acc[k] = {0.0, 0.0};
+    const int tot = total;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      int k = 0;
+      while (k + 1 < nseg && idx >= sg[k + 1].off) ++k;
+      const SelfSeg& g = sg[k];
+      const int loc = idx - g.off;
+      const int p = loc / (nt * ns);
+      const int rem = loc - p * nt * ns;
+      const int ti = rem / ns, si = rem - ti * ns;
+      const double lo = g.xi_max * p / g.npan, hi = g.xi_max * (p + 1) / g.npan;
+      const double xi = lo + (hi - lo) * glx_t[ti];
+      const double tpar = g.t0 + g.side * g.mu * sinh(xi);
+      const double wt = glw_t[ti] * (hi - lo) * g.mu * cosh(xi);
+      const double sv = glx_s[si];
+      const double w = glw_s[si] * wt * sv * g.area2 * Mm[4];
+      const double zx = sv * (g.E0x + tpar * g.Dx), zy = sv * (g.E0y + tpar * g.Dy);
+      const double u = P[0] + Mm[0] * zx + Mm[1] * zy;
+      const double v = P[1] + Mm[2] * zx + Mm[3] * zy;
+      double X[3], Xu[3], Xv[3], Nn[3];
+      kw_geometry<D>(u, v, cf, X, Xu, Xv, nullptr, 1);
+      cross3(Xu, Xv, Nn);
+      const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
+      const cplx gk = kernel_eval(kp, x0, x1, x2, X[0], X[1], X[2], Nn[0] * w, Nn[1] * w, Nn[2] * w,
+                                  J * w);
+      kw_accumulate<D>(u, v, gk, acc);
+    }
+    my_nodes += tot;
+    // block reduction (4 warps)
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      const double r = warp_sum(acc[k].re), im = warp_sum(acc[k].im);
+      if (lane == 0) red[wp][k] = {r, im};
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      cplx sum = red[0][k];
+      for (int q = 1; q < 4; ++q) {
+        sum.re += red[q][k].re;
+        sum.im += red[q][k].im;
+      }
+      out_self[s * dv.ldI + k] = sum;
+    }
+  }
+  if (threadIdx.x == 0)
+    atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 2), (unsigned long long)my_nodes);
+}
+
+// ============================================================================ V contraction
+// c_l = sum_nm V[nm][l] (I_near[nm] - I_smooth[nm]) written to the CSR (Sec. 4.3, 5.3).
+template <int D>
+__global__ void k_v2c(const int* __restrict__ plist, int count, Dev dv,
+                      const double* __restrict__ Vt, const cplx* __restrict__ In,
+                      const cplx* __restrict__ Is, const cplx* __restrict__ InS,
+                      const cplx* __restrict__ IsS, double* __restrict__ val) {
+  constexpr int n = (D + 1) * (D + 2) / 2;
+  __shared__ double V[n * n];
+  __shared__ cplx diff[kThreads / 32][n];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = Vt[e];
+  __syncthreads();
+  for (int b = blockIdx.x; b < count; b += gridDim.x) {
+    const int j = plist[b];
+    const int64_t p0 = dv.pair_ptr[j], np = dv.pair_ptr[j + 1] - p0;
+    const int64_t s0 = dv.self_ptr[j], nsf = dv.self_ptr[j + 1] - s0;
+    for (int64_t k = w; k < np + nsf; k += nw) {
+      const bool self = k >= np;
+      const int64_t id = self ? (s0 + k - np) : (p0 + k);
+      const cplx* a = self ? InS + id * dv.ldI : In + id * dv.ldI;
+      const cplx* s = self ? IsS + id * dv.ldI : Is + id * dv.ldI;
+      for (int nm = lane; nm < n; nm += 32) diff[w][nm] = {a[nm].re - s[nm].re, a[nm].im - s[nm].im};
+      __syncwarp();
+      const int64_t dst = self ? dv.self_csr[id] : dv.pair_csr[id];
+      for (int l = lane; l < n; l += 32) {
+        double re = 0.0, im = 0.0;
+        for (int nm = 0; nm < n; ++nm) {
+          const double vv = V[nm * n + l];
+          re = fma(vv, diff[w][nm].re, re);
+          im = fma(vv, diff[w][nm].im, im);
+        }
+        val[2 * (dst + l)] = re;
+        val[2 * (dst + l) + 1] = im;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// ============================================================================ apply
+// Oversampled sources of rule q_j: X, (X_u x X_v) w, |.| w and w-weighted density
+// sigma~_q = sum_nm K_nm(u_q) s_nm, s = V sigma (Sec. 4.2 Remark, Sec. 5.3).
+template <int D>
+__global__ void k_far_src(const int* __restrict__ plist, int count, Dev dv,
+                          const double* __restrict__ Vt, const int32_t* __restrict__ qv,
+                          const int64_t* __restrict__ src_off, const cplx* __restrict__ sigma,
+                          double* __restrict__ src /*[8][N_over]*/, int64_t n_over) {
+  constexpr int n = (D + 1) * (D + 2) / 2;
+  __shared__ double cf[3 * n];
+  __shared__ cplx sc[n];
+  for (int b = blockIdx.x; b < count; b += gridDim.x) {
+    const int j = plist[b];
+    const int64_t off = dv.node_off[j];
+    __syncthreads();
+    load_coef<D>(dv.coef, off, cf);
+    for (int nm = threadIdx.x; nm < n; nm += blockDim.x) {
+      double re = 0.0, im = 0.0;
+      for (int l = 0; l < n; ++l) {
+        re = fma(Vt[nm * n + l], sigma[off + l].re, re);
+        im = fma(Vt[nm * n + l], sigma[off + l].im, im);
+      }
+      sc[nm] = {re, im};
+    }
+    __syncthreads();
+    const int m = qv[j], Q = m * m;
+    const double* ru = dv.ru + dv.roff[m];
+    const double* rv = dv.rv + dv.roff[m];
+    const double* rw = dv.rw + dv.roff[m];
+    for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+      double X[3], Xu[3], Xv[3], Nn[3], K[n];
+      kw_geometry<D>(ru[q], rv[q], cf, X, Xu, Xv, K, 1);
+      cross3(Xu, Xv, Nn);
+      const double w = rw[q];
+      const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        re = fma(K[k], sc[k].re, re);
+        im = fma(K[k], sc[k].im, im);
+      }
+      const int64_t o = src_off[j] + q;
+      src[0 * n_over + o] = X[0];
+      src[1 * n_over + o] = X[1];
+      src[2 * n_over + o] = X[2];
+      src[3 * n_over + o] = Nn[0] * w;
+      src[4 * n_over + o] = Nn[1] * w;
+      src[5 * n_over + o] = Nn[2] * w;
+      src[6 * n_over + o] = J * w;
+      src[7 * n_over + o] = re;
+      src[8 * n_over + o] = im;
+    }
+  }
+}
+
+// Direct far sum over all oversampled sources, one thread per target (tiles of sources
+// staged through shared memory).
+__global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__ tgt, int64_t NT,
+                                                      const double* __restrict__ src, int64_t n_over,
+                                                      const KernelParams kp, cplx* __restrict__ out) {
+  __shared__ double s[9][kThreads];
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double x0 = 0, x1 = 0, x2 = 0;
+  if (t < NT) {
+    x0 = tgt[t];
+    x1 = tgt[NT + t];
+    x2 = tgt[2 * NT + t];
+  }
+  double re = 0.0, im = 0.0;
+  for (int64_t s0 = 0; s0 < n_over; s0 += kThreads) {
+    __syncthreads();
+    const int64_t q = s0 + threadIdx.x;
+    for (int c = 0; c < 9; ++c) s[c][threadIdx.x] = q < n_over ? src[c * n_over + q] : 0.0;
+    __syncthreads();
+    const int cnt = (int)min((int64_t)kThreads, n_over - s0);
+    if (t < NT)
+      for (int k = 0; k < cnt; ++k) {
+        const cplx g = kernel_eval(kp, x0, x1, x2, s[0][k], s[1][k], s[2][k], s[3][k], s[4][k],
+                                   s[5][k], s[6][k]);
+        re = fma(g.re, s[7][k], re);
+        re = fma(-g.im, s[8][k], re);
+        im = fma(g.re, s[8][k], im);
+        im = fma(g.im, s[7][k], im);
+      }
+  }
+  if (t < NT) out[t] = {re, im};
+}
+
+__global__ void k_csr_apply(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ val, const cplx* __restrict__ sigma,
+                            const int64_t* __restrict__ tnode, int64_t NT, double jump,
+                            cplx* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < NT; t += warps) {
+    double re = 0.0, im = 0.0;
+    for (int64_t e = row_ptr[t] + lane; e < row_ptr[t + 1]; e += 32) {
+      const double vr = val[2 * e], vi = val[2 * e + 1];
+      const cplx sg = sigma[col[e]];
+      re += vr * sg.re - vi * sg.im;
+      im += vr * sg.im + vi * sg.re;
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) {
+      cplx o = out[t];
+      o.re += re;
+      o.im += im;
+      if (jump != 0.0 && tnode[t] >= 0) {
+        o.re += jump * sigma[tnode[t]].re;
+        o.im += jump * sigma[tnode[t]].im;
+      }
+      out[t] = o;
+    }
+  }
+}
+
+// ============================================================================ launchers
+namespace {
+template <template <int> class F, class... Args>
+bool dispatch(int d, Args&&... args) {
+  switch (d) {
+    case 1: F<1>::run(args...); return true;
+    case 2: F<2>::run(args...); return true;
+    case 3: F<3>::run(args...); return true;
+    case 4: F<4>::run(args...); return true;
+    case 5: F<5>::run(args...); return true;
+    case 6: F<6>::run(args...); return true;
+    case 7: F<7>::run(args...); return true;
+    case 8: F<8>::run(args...); return true;
+    case 9: F<9>::run(args...); return true;
+    case 10: F<10>::run(args...); return true;
+    default: return false;
+  }
+}
+
+template <int D>
+struct GeomL {
+  static void run(const LaunchCommon& lc, const int* plist, int count, const int64_t* node_off,
+                  const double* xyz, int64_t N, const double* Vt, const double* nodes, double eta_p,
+                  double eta1_p, double* coef, double* cen, double* rad, double* dj, double* eta,
+                  double* eta1, int* status) {
+    const int grid = count < lc.num_sms * 8 ? count : lc.num_sms * 8;
+    k_geom<D><<<grid, 128, 0, lc.stream>>>(plist, count, node_off, xyz, N, Vt, nodes, eta_p, eta1_p,
+                                           coef, cen, rad, dj, eta, eta1, status);
+  }
+};
+
+template <class K>
+void set_smem(K kern, size_t bytes) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int D>
+size_t moments_smem_bytes(int extra_doubles) {
+  using C = Cfg<D>;
+  return sizeof(double) * (C::n * 3 + extra_doubles + C::WS) + sizeof(SegMap) * 4 + 1024;
+}
+
+template <int D>
+struct RuleMomL {
+  static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv, int mode,
+                  const int32_t* qv, const KernelParams& kp, void* out_pairs, void* out_self) {
+    const size_t sm = moments_smem_bytes<D>(0);
+    set_smem(k_rule_moments<D>, sm);
+    const int grid = count < lc.num_sms ? count : lc.num_sms;
+    k_rule_moments<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, mode, qv, kp,
+                                                         (cplx*)out_pairs, (cplx*)out_self);
+  }
+};
+
+template <int D>
+struct FarOrderL {
+  static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                  const KernelParams& kp, double eps, int m_max, double normV, const double* dirs,
+                  int ndirs, void* scratch, int grid, int32_t* q, int32_t* qn) {
+    const size_t sm = moments_smem_bytes<D>(3 * kMaxTestPts + kThreads / 32 + 4);
+    set_smem(k_farorder<D>, sm);
+    k_farorder<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, kp, eps, m_max, normV, dirs,
+                                                     ndirs, (cplx*)scratch, q, qn);
+  }
+};
+
+template <int D>
+struct AdaptiveL {
+  static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                  const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
+                  const void* I_smooth, void* I_near, int32_t* leaves, void* work,
+                  int64_t stride, int A_max, int levels, int grid, int* status) {
+    const size_t sm = moments_smem_bytes<D>(64 / 2 + 4 * 32) + 64 * sizeof(int);
+    set_smem(k_adaptive<D>, sm);
+    AdaptiveWS w{stride, A_max, levels};
+    k_adaptive<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, kp, eps, normV, leaf_order,
+                                                     max_depth, (const cplx*)I_smooth, (cplx*)I_near,
+                                                     leaves, (unsigned char*)work, w, status);
+  }
+};
+
+template <int D>
+struct SelfL {
+  static void run(const LaunchCommon& lc, const Dev& dv, const int32_t* deg, const KernelParams& kp,
+                  int order, void* out) {
+    const int64_t g = dv.n_self < (int64_t)lc.num_sms * 16 ? dv.n_self : (int64_t)lc.num_sms * 16;
+    if (g <= 0) return;
+    k_self<D><<<(int)g, 128, 0, lc.stream>>>(dv, deg, kp, order, (cplx*)out);
+  }
+};
+
+template <int D>
+struct V2cL {
+  static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                  const double* Vt, const void* In, const void* Is, const void* InS,
+                  const void* IsS, double* val) {
+    const int grid = count < lc.num_sms * 4 ? count : lc.num_sms * 4;
+    k_v2c<D><<<grid, kThreads, 0, lc.stream>>>(plist, count, dv, Vt, (const cplx*)In,
+                                               (const cplx*)Is, (const cplx*)InS, (const cplx*)IsS,
+                                               val);
+  }
+};
+
+template <int D>
+struct FarSrcL {
+  static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                  const double* Vt, const int32_t* qv, const int64_t* src_off, const void* sigma,
+                  double* src, int64_t n_over) {
+    const int grid = count < lc.num_sms * 4 ? count : lc.num_sms * 4;
+    k_far_src<D><<<grid, 128, 0, lc.stream>>>(plist, count, dv, Vt, qv, src_off,
+                                              (const cplx*)sigma, src, n_over);
+  }
+};
+}  // namespace
+
+cudaError_t upload_constants(cudaStream_t st) {
+  double c[kMaxBasis];
+  for (int nn = 0; nn <= kMaxDeg; ++nn)
+    for (int m = 0; m <= nn; ++m) c[nn * (nn + 1) / 2 + m] = sqrt(2.0 * (2 * m + 1) * (nn + 1));
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_kw, c, sizeof(c), 0, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+bool launch_geom(int d, const LaunchCommon& lc, const int* plist, int count, const int64_t* node_off,
+                 const double* xyz, int64_t N, const double* Vt, const double* nodes, double eta_p,
+                 double eta1_p, double* coef, double* cen, double* rad, double* dj, double* eta,
+                 double* eta1, int* status) {
+  return dispatch<GeomL>(d, lc, plist, count, node_off, xyz, N, Vt, nodes, eta_p, eta1_p, coef, cen,
+                         rad, dj, eta, eta1, status);
+}
+
+void launch_tgt_patch(const LaunchCommon& lc, const double* tgt, const int64_t* tnode, int64_t NT,
+                      const int64_t* node_off, int64_t P, int64_t N, int32_t* tpatch,
+                      int32_t* tlnode, int* status) {
+  const int64_t blocks = (NT + 255) / 256;
+  const int g = (int)(blocks < lc.num_sms * 16 ? (blocks > 0 ? blocks : 1) : lc.num_sms * 16);
+  k_tgt_patch<<<g, 256, 0, lc.stream>>>(tgt, tnode, NT, node_off, P, N, tpatch, tlnode, status);
+}
+
+static NearView nv(const NearArgs& a) { return {a.tgt, a.NT, a.cen, a.rad, a.eta, a.eta1}; }
+
+void launch_row_count(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
+                      const int32_t* deg, int64_t* row_np, int64_t* row_nnz) {
+  const int g = lc.num_sms * 8;
+  k_row_count<<<g, 256, 0, lc.stream>>>(nv(a), tpatch, P, deg, row_np, row_nnz);
+}
+void launch_row_fill(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
+                     const int32_t* deg, const int64_t* node_off, const int64_t* rowp_ptr,
+                     const int64_t* row_ptr, int32_t* rowp_patch, int64_t* rowp_off, int32_t* col) {
+  const int g = lc.num_sms * 8;
+  k_row_fill<<<g, 256, 0, lc.stream>>>(nv(a), tpatch, P, deg, node_off, rowp_ptr, row_ptr,
+                                       rowp_patch, rowp_off, col);
+}
+void launch_patch_count(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
+                        int64_t* npair, int64_t* nad, int64_t* nself) {
+  const int g = (int)(P < lc.num_sms * 8 ? P : lc.num_sms * 8);
+  k_patch_count<<<g, 256, 0, lc.stream>>>(nv(a), tpatch, P, npair, nad, nself);
+}
+void launch_patch_fill(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
+                       const int64_t* pair_ptr, const int64_t* ad_ptr, const int64_t* an_ptr,
+                       const int64_t* self_ptr, const int64_t* rowp_ptr, const int32_t* rowp_patch,
+                       const int64_t* rowp_off, const int64_t* row_ptr, int32_t* pair_tgt,
+                       uint8_t* pair_ad, double* pair_d2, int64_t* pair_csr, int32_t* ad_pair,
+                       int32_t* an_pair, int32_t* self_tgt, int64_t* self_csr) {
+  const int g = (int)(P < lc.num_sms * 8 ? P : lc.num_sms * 8);
+  k_patch_fill<<<g, 256, 0, lc.stream>>>(nv(a), tpatch, P, pair_ptr, ad_ptr, an_ptr, self_ptr,
+                                         rowp_ptr, rowp_patch, rowp_off, row_ptr, pair_tgt, pair_ad,
+                                         pair_d2, pair_csr, ad_pair, an_pair, self_tgt, self_csr);
+}
+
+// out[i] = sum_{k<i} in[i]; needs scratch of >= 2 * ceil(n/1024) + 2048 int64 elements.
+void launch_scan(const LaunchCommon& lc, const int64_t* in, int64_t* out, int64_t n,
+                 int64_t* scratch) {
+  if (n <= 0) return;
+  const int64_t nb = (n + 1023) / 1024;
+  k_scan_block<<<(unsigned)nb, 1024, 0, lc.stream>>>(in, out, n, scratch);
+  if (nb > 1) {
+    launch_scan(lc, scratch, scratch + nb, nb, scratch + 2 * nb);
+    k_scan_add<<<(unsigned)nb, 1024, 0, lc.stream>>>(out, n, scratch + nb);
+  }
+}
+
+bool launch_rule_moments(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                         int mode, const int32_t* qv, const KernelParams& kp, void* out_pairs,
+                         void* out_self) {
+  return dispatch<RuleMomL>(d, lc, plist, count, dv, mode, qv, kp, out_pairs, out_self);
+}
+bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                     const KernelParams& kp, double eps, int m_max, double normV, const double* dirs,
+                     int ndirs, void* scratch, int grid, int32_t* q, int32_t* qn) {
+  return dispatch<FarOrderL>(d, lc, plist, count, dv, kp, eps, m_max, normV, dirs, ndirs, scratch,
+                             grid, q, qn);
+}
+bool launch_adaptive(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                     const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
+                     const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
+                     int A_max, int levels, int grid, int* status) {
+  return dispatch<AdaptiveL>(d, lc, plist, count, dv, kp, eps, normV, leaf_order, max_depth,
+                             I_smooth, I_near, leaves, work, stride, A_max, levels, grid, status);
+}
+bool launch_self(int d, const LaunchCommon& lc, const Dev& dv, const int32_t* deg,
+                 const KernelParams& kp, int order, void* out) {
+  return dispatch<SelfL>(d, lc, dv, deg, kp, order, out);
+}
+bool launch_v2c(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                const double* Vt, const void* In, const void* Is, const void* InS, const void* IsS,
+                double* val) {
+  return dispatch<V2cL>(d, lc, plist, count, dv, Vt, In, Is, InS, IsS, val);
+}
+bool launch_far_src(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                    const double* Vt, const int32_t* qv, const int64_t* src_off, const void* sigma,
+                    double* src, int64_t n_over) {
+  return dispatch<FarSrcL>(d, lc, plist, count, dv, Vt, qv, src_off, sigma, src, n_over);
+}
+void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const double* src,
+                    int64_t n_over, const KernelParams& kp, void* out) {
+  const int64_t g = (NT + kThreads - 1) / kThreads;
+  if (g <= 0) return;
+  k_far_sum<<<(unsigned)g, kThreads, 0, lc.stream>>>(tgt, NT, src, n_over, kp, (cplx*)out);
+}
+void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int32_t* col,
+                      const double* val, const void* sigma, const int64_t* tnode, int64_t NT,
+                      double jump, void* out) {
+  const int g = lc.num_sms * 8;
+  k_csr_apply<<<g, 256, 0, lc.stream>>>(row_ptr, col, val, (const cplx*)sigma, tnode, NT, jump,
+                                        (cplx*)out);
+}
+
+size_t adaptive_smem_bytes(int d) {
+  switch (d) {
+#define LCQ_CASE(D) \
+  case D: return moments_smem_bytes<D>(64 / 2 + 4 * 32) + 64 * sizeof(int);
+    LCQ_CASE(1) LCQ_CASE(2) LCQ_CASE(3) LCQ_CASE(4) LCQ_CASE(5)
+    LCQ_CASE(6) LCQ_CASE(7) LCQ_CASE(8) LCQ_CASE(9) LCQ_CASE(10)
+#undef LCQ_CASE
+    default: return 0;
+  }
+}
+
+}  // namespace lcq

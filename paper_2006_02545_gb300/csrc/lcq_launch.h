@@ -1,0 +1,114 @@
+// Kernel launchers of liblcq (defined in lcq_kernels.cu, called by lcq_api.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lcq_internal.h"
+
+namespace lcq {
+
+struct LaunchCommon {
+  cudaStream_t stream;
+  int num_sms;
+};
+
+// Read-only device view of a near-list object plus tables, passed by value to kernels.
+struct Dev {
+  const double* coef;
+  const int64_t* node_off;
+  const double* cen;
+  const double* rad;
+  const double* dj;
+  const double* eta;
+  const double* eta1;
+  const double* tgt;
+  int64_t NT;
+  const int32_t* tpatch;
+  const int32_t* tlnode;
+  const int64_t* pair_ptr;
+  const int32_t* pair_tgt;
+  const double* pair_d2;
+  const int64_t* pair_csr;
+  const int64_t* ad_ptr;
+  const int32_t* ad_pair;
+  const int64_t* an_ptr;
+  const int32_t* an_pair;
+  const int64_t* self_ptr;
+  const int32_t* self_tgt;
+  const int64_t* self_csr;
+  int64_t n_self;
+  const int32_t* q;
+  // tables
+  const int* roff;
+  const double* ru;
+  const double* rv;
+  const double* rw;
+  const int* gl_off;
+  const double* gl_x;
+  const double* gl_w;
+  const double* nodes_uv[kMaxDeg + 1];
+  long long* counters;
+  int* status;
+  int ldI;  // row stride (complex entries) of the pair/self moment buffers
+};
+
+struct NearArgs {
+  const double* tgt;
+  int64_t NT;
+  const double* cen;
+  const double* rad;
+  const double* eta;
+  const double* eta1;
+};
+
+cudaError_t upload_constants(cudaStream_t st);
+
+bool launch_geom(int d, const LaunchCommon& lc, const int* plist, int count, const int64_t* node_off,
+                 const double* xyz, int64_t N, const double* Vt, const double* nodes, double eta_p,
+                 double eta1_p, double* coef, double* cen, double* rad, double* dj, double* eta,
+                 double* eta1, int* status);
+void launch_tgt_patch(const LaunchCommon& lc, const double* tgt, const int64_t* tnode, int64_t NT,
+                      const int64_t* node_off, int64_t P, int64_t N, int32_t* tpatch,
+                      int32_t* tlnode, int* status);
+void launch_row_count(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
+                      const int32_t* deg, int64_t* row_np, int64_t* row_nnz);
+void launch_row_fill(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
+                     const int32_t* deg, const int64_t* node_off, const int64_t* rowp_ptr,
+                     const int64_t* row_ptr, int32_t* rowp_patch, int64_t* rowp_off, int32_t* col);
+void launch_patch_count(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
+                        int64_t* npair, int64_t* nad, int64_t* nself);
+void launch_patch_fill(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
+                       const int64_t* pair_ptr, const int64_t* ad_ptr, const int64_t* an_ptr,
+                       const int64_t* self_ptr, const int64_t* rowp_ptr, const int32_t* rowp_patch,
+                       const int64_t* rowp_off, const int64_t* row_ptr, int32_t* pair_tgt,
+                       uint8_t* pair_ad, double* pair_d2, int64_t* pair_csr, int32_t* ad_pair,
+                       int32_t* an_pair, int32_t* self_tgt, int64_t* self_csr);
+void launch_scan(const LaunchCommon& lc, const int64_t* in, int64_t* out, int64_t n,
+                 int64_t* scratch);
+bool launch_rule_moments(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                         int mode, const int32_t* qv, const KernelParams& kp, void* out_pairs,
+                         void* out_self);
+bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                     const KernelParams& kp, double eps, int m_max, double normV, const double* dirs,
+                     int ndirs, void* scratch, int grid, int32_t* q, int32_t* qn);
+bool launch_adaptive(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                     const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
+                     const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
+                     int A_max, int levels, int grid, int* status);
+bool launch_self(int d, const LaunchCommon& lc, const Dev& dv, const int32_t* deg,
+                 const KernelParams& kp, int order, void* out);
+bool launch_v2c(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                const double* Vt, const void* In, const void* Is, const void* InS, const void* IsS,
+                double* val);
+bool launch_far_src(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                    const double* Vt, const int32_t* qv, const int64_t* src_off, const void* sigma,
+                    double* src, int64_t n_over);
+void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const double* src,
+                    int64_t n_over, const KernelParams& kp, void* out);
+void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int32_t* col,
+                      const double* val, const void* sigma, const int64_t* tnode, int64_t NT,
+                      double jump, void* out);
+size_t adaptive_smem_bytes(int d);
+
+}  // namespace lcq
