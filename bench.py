@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Near-field correction points/sec on GB300: one step = build_near_lists +
+gen_corrections (geometry, near lists, far order q_j, smooth/annulus moments, adaptive
+near moments, self weights, V contraction into the CSR) over the whole surface.
+
+Default workload: CFIE D - ik S, k = 2 pi, ellipsoid with semi-axes (1, 2, 3) as 1280
+degree-6 patches (28 nodes each, 35,840 points), eps = 1e-9, FP64; all nodes are
+targets.  Metric: N / T_step (the paper's S_init = N / T_init).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain FP64 restatement in oracle/) on the
+host cores, each step a bounded sample of the same workload.  Under torchrun every
+rank runs an independent copy of the workload (weak scaling, no collective on the data
+path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("near-field correction points/sec on 1 GB300 (FP64 vs mixed/batched) at "
+          "ε=1e-6/1e-9")
+UNIT = "points/s"
+WORKLOAD = "CFIE D-ikS k=2pi ellipsoid(1,2,3) 1280 order-6 patches (35,840 pts) eps=1e-9 FP64"
+
+# Algorithmic FLOPs of one (target, leaf node) evaluation in the adaptive kernel:
+# kernel (difference, r^2, r, 1/r, phase, e^{ikr}/(4 pi r), S and D parts, CFIE
+# combination: 50 arithmetic operations + sqrt, reciprocal and sincos counted as one
+# each) plus the contraction onto n Koornwinder moments (complex x real: 4 per moment).
+KERNEL_FLOPS = 53
+
+
+def fp64_peak_tflops():
+    """Derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (the 1.25 TFLOP/s
+    nominal GB300 figure corresponds to 2 FP64 FMA lanes per SM per clock)."""
+    return 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--s", type=int, default=8, help="icosahedral refinement (1280 patches at 8)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- oracle leg
+def _oracle_worker(job):
+    """Oracle corrections for some patches of the workload (runs in a spawned process)."""
+    import numpy as np  # noqa: F401
+    s_div, patches, dirs_seed = job
+    from oracle import corrections as C
+    from oracle import geometry
+    from paper_2006_02545_gb300 import workloads as W
+    wl = W.ellipsoid_cfie_k2pi(s_div)
+    surf = wl.surface
+    pts = geometry.make_patches(surf.deg, surf.node_off, surf.xyz)
+    p = C.Params(eps=wl.eps, eta=wl.eta, test_dirs=W.test_directions(dirs_seed))
+    t0 = time.perf_counter()
+    C.gen_corrections(surf.deg, surf.node_off, surf.xyz, wl.tgt_xyz, wl.tgt_node, wl.kernel, wl.k,
+                      wl.alpha, wl.beta, params=p, patches=pts, only_patches=patches)
+    return len(patches), time.perf_counter() - t0
+
+
+def oracle_sample(s_div, n_patches_total, workers, per_worker, seed, pool):
+    """Time the oracle on workers*per_worker patches spread over the surface.
+    Throughput = points of the sampled patches / the slowest worker's compute time."""
+    n = 28
+    total = workers * per_worker
+    stride = max(1, n_patches_total // total)
+    picks = [(i * stride + seed) % n_patches_total for i in range(total)]
+    jobs = [(s_div, picks[w::workers], 7) for w in range(workers)]
+    res = pool.map(_oracle_worker, jobs)
+    done = sum(r[0] for r in res)
+    worst = max(r[1] for r in res)
+    return done * n / worst, done, worst
+
+
+def make_pool(workers):
+    import multiprocessing as mp
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    return mp.get_context("spawn").Pool(workers)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    workers = max(1, min(16, os.cpu_count() or 1))
+    pool = make_pool(workers)
+    npat = 20 * args.s * args.s
+    vals, times = [], []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        v, done, worst = oracle_sample(args.s, npat, workers, 1, it * 37, pool)
+        if it >= args.warmup:
+            vals.append(v)
+            times.append(time.perf_counter() - t0)
+    pool.close()
+    value = statistics.median(vals)
+    sample = (f"{workers} patches per step (1 per worker) of {npat}; throughput = sampled "
+              f"points / slowest worker's compute time")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "patches": npat, "order": 6},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" +
+                                       self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- our leg
+def traffic_for(kernel_name):
+    """DRAM bytes per launch of `kernel_name` from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2006_02545_gb300", "csrc", "lcq_kernels.cu")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel_name)
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if rec and rec.get("src_sha256") == sha:
+            return rec.get("bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2006_02545_gb300 import build as B
+    B.build()
+    from paper_2006_02545_gb300 import lcq
+    from paper_2006_02545_gb300 import workloads as W
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wl = W.ellipsoid_cfie_k2pi(args.s)
+    surf = wl.surface
+    N, NT, P = surf.n_points, wl.tgt_xyz.shape[1], surf.n_patches
+    n = 28
+    ctx = lcq.Context(local_rank)
+    stream = ctx.stream
+    xyz_d = torch.from_numpy(surf.xyz).to(dev)
+    tx_d = torch.from_numpy(np.ascontiguousarray(wl.tgt_xyz)).to(dev)
+    tn_d = torch.from_numpy(wl.tgt_node).to(dev)
+    ds = lcq.DeviceSurface(surf.deg, surf.node_off, xyz_d)
+    prm = lcq.params(wl.eps, eta=wl.eta, test_dirs=W.test_directions(7))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        near = lcq.build_near_lists(ctx, ds, tx_d, tn_d, prm)
+        corr = lcq.gen_corrections(ctx, ds, near, wl.kernel, wl.k, prm, wl.alpha, wl.beta)
+        return near, corr
+
+    for _ in range(args.warmup):
+        near, corr = step()
+        st = ctx.sync()
+        corr.close()
+        near.close()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    step_ms, adapt_ms, stages, statuses, launches, nodes = [], [], [], [], 0, 0
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        near, corr = step()
+        e1.record(stream)
+        st = ctx.sync()
+        statuses.append(st)
+        step_ms.append(e0.elapsed_time(e1))
+        ms, nl = ctx.stage_times()
+        stages.append(ms)
+        adapt_ms.append(ms[3])
+        launches += nl
+        cnt = ctx.counters()
+        nodes = int(cnt[1])
+        corr.close()
+        near.close()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop() if clocks else None
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * N * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: H2D of inputs, D2H of the CSR
+    e2e = None
+    if not args.no_e2e:
+        xyz_h = torch.from_numpy(surf.xyz).pin_memory()
+        tx_h = torch.from_numpy(np.ascontiguousarray(wl.tgt_xyz)).pin_memory()
+        tn_h = torch.from_numpy(wl.tgt_node).pin_memory()
+        near, corr = step()
+        nnz = near.nnz
+        corr.close()
+        near.close()
+        rp_h = torch.empty(NT + 1, dtype=torch.int64).pin_memory()
+        col_h = torch.empty(nnz, dtype=torch.int32).pin_memory()
+        val_h = torch.empty(nnz, dtype=torch.complex128).pin_memory()
+        out = (rp_h.numpy(), col_h.numpy(), val_h.numpy())
+        xyz_e = torch.empty_like(xyz_d)
+        tx_e = torch.empty_like(tx_d)
+        tn_e = torch.empty_like(tn_d)
+        ds_e = lcq.DeviceSurface(surf.deg, surf.node_off, xyz_e)
+        e2e_t = []
+        for it in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                xyz_e.copy_(xyz_h, non_blocking=True)
+                tx_e.copy_(tx_h, non_blocking=True)
+                tn_e.copy_(tn_h, non_blocking=True)
+            near = lcq.build_near_lists(ctx, ds_e, tx_e, tn_e, prm)
+            corr = lcq.gen_corrections(ctx, ds_e, near, wl.kernel, wl.k, prm, wl.alpha, wl.beta)
+            corr.export(NT, out=out)
+            t1 = time.perf_counter()
+            corr.close()
+            near.close()
+            if it >= args.warmup:
+                e2e_t.append(t1 - t0)
+        tot = sum(e2e_t)
+        if world > 1:
+            t = torch.tensor([tot], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot = float(t.item())
+        e2e = {"value": world * N * len(e2e_t) / tot, "unit": UNIT,
+               "h2d_bytes_per_step": int(xyz_h.numel() * 8 + tx_h.numel() * 8 + tn_h.numel() * 8),
+               "d2h_bytes_per_step": int((NT + 1) * 8 + nnz * 4 + nnz * 16)}
+
+    if rank != 0:
+        return
+    flops = nodes * (4 * n + KERNEL_FLOPS)
+    a_ms = statistics.mean(adapt_ms)
+    achieved = flops / (a_ms / 1e3) / 1e12
+    peak = fp64_peak_tflops()
+    roofline = {"bound": "alu", "kernel": "k_adaptive<6> (FP64)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic_for("k_adaptive"),
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
+                "flops_per_launch": flops, "node_evals_per_launch": nodes,
+                "avg_launch_ms": a_ms}
+    cpu = None
+    if not args.no_cpu_baseline:
+        workers = max(1, min(16, os.cpu_count() or 1))
+        pool = make_pool(workers)
+        v, done, worst = oracle_sample(args.s, P, workers, 1, 0, pool)
+        pool.close()
+        cpu = {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
+               "sample": f"{done} of {P} patches (1 per worker, spread over the surface); "
+                         f"sampled points / slowest worker's compute time ({worst:.1f} s)"}
+    st_mean = [statistics.mean(s[i] for s in stages) for i in range(6)]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "patches": P, "order": 6, "points": N,
+                   "near_pairs": None, "l2": "256 MiB buffer written between steps (outside the "
+                                             "timed events)"},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+        "clocks": clk, "status": max(statuses) if statuses else None,
+        "stages_ms": dict(zip(["near_lists", "far_order", "smooth_annulus", "adaptive", "self",
+                               "v2c"], st_mean)),
+        "wall_s_timed_region": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -130,9 +130,10 @@ lcq_status lcq_near_export(lcq_near* near, int64_t* pair_ptr, int32_t* tgt, uint
 
 void lcq_near_destroy(lcq_near* near);
 
-/* Net corrections (Sec. 4.2-4.3, 5.2-5.3): for every near pair (t, j) and every
- * self pair, c_{t,l} = a^j_l(x_t) - s^j_l(x_t), the quadrature weight minus the
- * weight the smooth rule q_j gives node l, stored as a target-major CSR matrix.
+/* Net corrections (Sec. 4.2-4.3, 5.2-5.3), stored as a target-major CSR matrix: for
+ * every near pair (t, j), c_{t,l} = a^j_l(x_t) - s^j_l(x_t), the quadrature weight
+ * minus the weight the smooth rule q_j gives node l; for a self pair (t on patch j),
+ * c_{t,l} = a^j_l(x_t), since apply masks the own patch out of the far sum.
  * k = k_re + i k_im (k_im >= 0); alpha, beta are the CFIE coefficients (ignored
  * for S and D). */
 lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
@@ -153,8 +154,10 @@ lcq_status lcq_corr_export(lcq_corr* corr, int64_t* row_ptr, int32_t* col, doubl
  * pairs) to host [n_pairs] in patch-major order.  Any pointer may be NULL. */
 lcq_status lcq_corr_export_stats(lcq_corr* corr, int32_t* q, int32_t* q_near, int32_t* leaves);
 
-/* Corrected layer potential (Sec. 5.3, subtract-and-add with a direct far sum):
- *   u(x_t) = sum_j sum_{q in rule q_j} K(x_t, X_j(u_q)) J w_q sigma~_q + sum_row c sigma
+/* Corrected layer potential (Sec. 5.3, subtract-and-add with a direct far sum; the
+ * own patch of an on-surface target is masked out of the far sum):
+ *   u(x_t) = sum_{j != own(t)} sum_{q in rule q_j} K(x_t, X_j(u_q)) J w_q sigma~_q
+ *            + sum_row c sigma
  * sigma device complex128 [N] at the nodes, out device complex128 [NT].
  * jump != 0 adds jump * sigma(x_t) for on-surface targets (e.g. 0.5 for the
  * exterior limit of D).  The kernel must match the one the corrections were
@@ -179,6 +182,14 @@ lcq_status lcq_sync(lcq_ctx* ctx, int64_t timeout_ms);
  * [0] adaptive tests, [1] adaptive leaf-rule node evaluations, [2] self node
  * evaluations, [3] smooth/annulus node evaluations (per target).  Synchronizes. */
 lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out4);
+
+/* Stage timings of the last lcq_build_near_lists and lcq_gen_corrections on ctx, from
+ * CUDA events recorded on the context's stream (host out, milliseconds):
+ *   ms[0] near lists (geometry + both orientations)   ms[1] far order q_j
+ *   ms[2] smooth-rule and annulus moments              ms[3] adaptive near moments
+ *   ms[4] self weights                                 ms[5] V contraction into the CSR
+ * *launches receives the number of kernels those two calls launched.  Synchronizes. */
+lcq_status lcq_stage_times(lcq_ctx* ctx, float* ms6, int64_t* launches);
 
 const char* lcq_status_string(lcq_status s);
 const char* lcq_last_error(const lcq_ctx* ctx);

@@ -6,10 +6,16 @@ annulus rule order -> self weights S_j -> near weights N_j (adaptive inside
 eta_1 R_j, one oversampled rule in the annulus) -> net corrections.
 
 Net correction (subtract-and-add, Sec. 5.3, folded into the stored entry):
-    c_{t,l} = a^j_l(x_t) - s^j_l(x_t),
+    c_{t,l} = a^j_l(x_t) - s^j_l(x_t)   for near pairs,
+    c_{t,l} = a^j_l(x_t)                for the target's own patch (self pair),
 where a is the self or near point weight and s the weight the smooth rule q_j puts
 on node l for the same target.  Apply then computes
-    u(x_t) = sum_j sum_{q in rule q_j} K(x_t, X_q) J_q w_q sigma~_q + sum_row c_{t,col} sigma_col.
+    u(x_t) = sum_{j != own(t)} sum_{q in rule q_j} K(x_t, X_q) J_q w_q sigma~_q
+             + sum_row c_{t,col} sigma_col,
+i.e. the own patch of an on-surface target is masked out of the far sum instead of
+being subtracted (the masked variant of Sec. 5.3; equal in exact arithmetic).  A
+smooth-rule node can fall very close to a node of the same patch, and subtracting
+its large spurious contribution loses digits; masking avoids that cancellation.
 Rows are targets; within a row, patches ascend, and each patch contributes its n
 nodes in node order.
 """
@@ -59,6 +65,7 @@ class Corrections:
     patches: list
     pair_stats: dict = field(default_factory=dict)   # (t, j) -> dict
     depth_hit: bool = False
+    tgt_patch: np.ndarray = None                       # own patch of each target (-1: off surface)
 
 
 def patch_of_node(node_off, tgt_node):
@@ -130,13 +137,11 @@ def gen_corrections(deg, node_off, xyz, tgt_xyz, tgt_node, kind, k, alpha=1.0, b
             s = quadrature.smooth_weights(pt, x, int(q[j]), kern)
             entries[(int(t), j)] = a - s
             stats[(int(t), j)] = st
-        # self weights
+        # self weights (the own patch is masked out of the far sum, nothing to subtract)
         for t in np.nonzero(tgt_patch == j)[0]:
             i = int(tgt_node[t] - node_off[j])
             x = tgt_xyz[:, t]
-            a = quadrature.self_weights(pt, i, x, kern, self_order)
-            s = quadrature.smooth_weights(pt, x, int(q[j]), kern)
-            entries[(int(t), j)] = a - s
+            entries[(int(t), j)] = quadrature.self_weights(pt, i, x, kern, self_order)
             stats[(int(t), j)] = {"kind": "self"}
 
     nt = tgt_xyz.shape[1]
@@ -154,13 +159,13 @@ def gen_corrections(deg, node_off, xyz, tgt_xyz, tgt_node, kind, k, alpha=1.0, b
         val[pos:pos + n] = entries[(t, j)]
         pos += n
     return Corrections(row_ptr, col, val, q, q_near, q_sat, eta, eta1, near, patches, stats,
-                       depth_hit)
+                       depth_hit, tgt_patch)
 
 
 def far_sources(patches, q, sigma, node_off):
     """Oversampled sources of the smooth rules q_j: positions, normals, w_q sigma~_q (Sec. 4.2
-    Remark: sigma~_q = sum_nm s_nm K_nm(u_q, v_q), s = V sigma)."""
-    Xs, Ns, str_ = [], [], []
+    Remark: sigma~_q = sum_nm s_nm K_nm(u_q, v_q), s = V sigma), and their patch ids."""
+    Xs, Ns, str_, pid = [], [], [], []
     for j, pt in enumerate(patches):
         ru, rv, rw = rules.conical_rule(int(q[j]))
         X, N, K = pt.eval(ru, rv)
@@ -168,17 +173,21 @@ def far_sources(patches, q, sigma, node_off):
         Xs.append(X)
         Ns.append(N)
         str_.append(rw * (K.T @ s))
-    return np.concatenate(Xs, axis=1), np.concatenate(Ns, axis=1), np.concatenate(str_)
+        pid.append(np.full(len(rw), j))
+    return (np.concatenate(Xs, axis=1), np.concatenate(Ns, axis=1), np.concatenate(str_),
+            np.concatenate(pid))
 
 
 def apply_corrected(corr: Corrections, node_off, sigma, tgt_xyz, kind, k, alpha=1.0, beta=0.0):
-    """u(x_t) = far sum over all oversampled sources + CSR correction (Sec. 5.3)."""
+    """u(x_t) = far sum over the oversampled sources of every patch but the target's own
+    + CSR correction (Sec. 5.3)."""
     kern = Kern(kind, k, alpha, beta)
-    X, N, strength = far_sources(corr.patches, corr.q, sigma, node_off)
+    X, N, strength, pid = far_sources(corr.patches, corr.q, sigma, node_off)
     nt = tgt_xyz.shape[1]
     u = np.zeros(nt, dtype=np.complex128)
     for t in range(nt):
-        u[t] = (kern(tgt_xyz[:, t], X, N) * strength).sum()
+        keep = pid != corr.tgt_patch[t]
+        u[t] = (kern(tgt_xyz[:, t], X[:, keep], N[:, keep]) * strength[keep]).sum()
         a, b = corr.row_ptr[t], corr.row_ptr[t + 1]
         u[t] += (corr.val[a:b] * sigma[corr.col[a:b]]).sum()
     return u

@@ -11,6 +11,9 @@ Readings:
     largest |X - c_j| over the nodes and the 153 vertices of the level-4 uniform
     subdivision of T0, i.e. (a/16, b/16), a+b <= 16.
   * d_j = min_l sqrt(J_l w_l) (Sec. 4.2).
+  * Local quadratures evaluate X - c_j (the series with x_00 shifted by c_j/K_00)
+    against x - c_j: the same differences x - X, with rounding proportional to the
+    patch size instead of the distance from the origin.
 """
 from __future__ import annotations
 
@@ -34,6 +37,7 @@ class Patch:
     c: np.ndarray          # [3] centroid
     R: float               # radius
     dj: float              # min sqrt(J w)
+    coefs_rel: np.ndarray = None   # [n, 3] coefficients of X - c_j
 
     @property
     def n(self) -> int:
@@ -41,10 +45,17 @@ class Patch:
 
     def eval(self, u, v):
         """X, n = X_u x X_v at reference points; returns (X [3,P], N [3,P], K [n,P])."""
+        return self._eval(self.coefs, u, v)
+
+    def eval_rel(self, u, v):
+        """As eval, with X measured from the centroid: X - c_j (series with shifted x_00)."""
+        return self._eval(self.coefs_rel, u, v)
+
+    def _eval(self, coefs, u, v):
         K, Ku, Kv = kw.basis(self.d, u, v, derivs=True)
-        X = self.coefs.T @ K
-        Xu = self.coefs.T @ Ku
-        Xv = self.coefs.T @ Kv
+        X = coefs.T @ K
+        Xu = coefs.T @ Ku
+        Xv = coefs.T @ Kv
         N = np.cross(Xu, Xv, axis=0)
         return X, N, K
 
@@ -79,7 +90,10 @@ def make_patch(d: int, y: np.ndarray) -> Patch:
     R = max(np.linalg.norm(Xs - c[:, None], axis=0).max(),
             np.linalg.norm(y - c[:, None], axis=0).max())
     dj = float(np.sqrt(J * w).min())
-    return Patch(d, y, coefs, V, nV, w, J, c, float(R), dj)
+    # X - c_j = sum x_nm K_nm - c_j, and K_00 = sqrt(2) is constant
+    coefs_rel = coefs.copy()
+    coefs_rel[0] -= c / np.sqrt(2.0)
+    return Patch(d, y, coefs, V, nV, w, J, c, float(R), dj, coefs_rel)
 
 
 def make_patches(deg, node_off, xyz):

@@ -35,3 +35,25 @@ def kernel_jac(x, X, N, k, kind: str, alpha=1.0, beta=0.0):
         out = out + (dd if kind == "D" else alpha * dd)
     out[zero] = 0.0
     return out
+
+
+def kernel_envelope(x, X, N, k, kind: str, alpha=1.0, beta=0.0, R=1.0):
+    """Rounding envelope of kernel_jac at each source (a reading; the paper is silent on
+    finite precision): |G| J (b + a |1 - ik r| R / r^2), with b = 1, 0, |beta| and
+    a = 0, 1, |alpha| for S, D, CFIE.  The double-layer term is the size of
+    |n| |delta(x - X)| / r^2 for a coordinate rounding error delta ~ u R (charts and
+    targets are taken relative to the patch centroid), which bounds the noise of
+    n.(x - X) when x is nearly in the tangent plane."""
+    x = np.asarray(x, dtype=np.float64)
+    dvec = x[:, None] - X
+    r = np.sqrt((dvec * dvec).sum(axis=0))
+    zero = r == 0.0
+    rs = np.where(zero, 1.0, r)
+    k = complex(k)
+    g = np.exp(-k.imag * rs) / (FOUR_PI * rs) * np.sqrt((N * N).sum(axis=0))
+    b = {"S": 1.0, "D": 0.0, "CFIE": abs(beta)}[kind]
+    a = {"S": 0.0, "D": 1.0, "CFIE": abs(alpha)}[kind]
+    f = np.sqrt((1.0 + k.imag * rs) ** 2 + (k.real * rs) ** 2)
+    out = g * (b + a * f * R / (rs * rs))
+    out[zero] = 0.0
+    return out

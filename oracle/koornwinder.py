@@ -77,3 +77,57 @@ def basis(d: int, u, v, derivs: bool = False):
     if derivs:
         return K, Ku, Kv
     return K
+
+
+def jacobi_recurrence(a: int, b: int):
+    """P^{(0,b)}_{a+1}(y) = (c1 y + c0) P_a(y) - c2 P_{a-1}(y) (standard three-term recurrence)."""
+    den = 2.0 * (a + 1) * (a + b + 1) * (2 * a + b)
+    c1 = (2 * a + b + 1) * (2 * a + b + 2) * (2 * a + b) / den
+    c0 = -(2 * a + b + 1) * b * b / den
+    c2 = 2.0 * a * (a + b) * (2 * a + b + 2) / den
+    return c1, c0, c2
+
+
+def basis_delta(d: int, P, du, dv):
+    """K_nm(P + delta) - K_nm(P) for offsets delta = (du, dv), computed without forming
+    the two values: the differences obey the same recurrences, e.g. for the scaled
+    Legendre factor
+        (m) dL_m = (2m-1)(s_Q dL_{m-1} + ds L_{m-1}(P)) - (m-1)(q_Q^2 dL_{m-2} + d(q^2) L_{m-2}(P)),
+    with ds = 2 du + dv and d(q^2) = -dv (q_Q + q_P), and for the Jacobi factor
+        dP_{a+1} = (c1 y_Q + c0) dP_a + c1 dy P_a(P) - c2 dP_{a-1},  dy = -2 dv.
+    The result keeps full relative precision as delta -> 0 (used by the self rules, where
+    x - X(P + delta) = -(X(P + delta) - X(P)) sets the near-singular behaviour)."""
+    du = np.atleast_1d(np.asarray(du, dtype=np.float64))
+    dv = np.atleast_1d(np.asarray(dv, dtype=np.float64))
+    pu, pv = float(P[0]), float(P[1])
+    uq, vq = pu + du, pv + dv
+    sP, qP, yP = 2 * pu + pv - 1.0, 1.0 - pv, 1.0 - 2.0 * pv
+    sQ, qQ, yQ = 2 * uq + vq - 1.0, 1.0 - vq, 1.0 - 2.0 * vq
+    ds = 2.0 * du + dv
+    dq2 = -dv * (qQ + qP)
+    dy = -2.0 * dv
+    nb = n_basis(d)
+    out = np.empty((nb, du.size))
+    LP = [1.0, sP]
+    LQ = [np.ones_like(du), sQ]
+    dL = [np.zeros_like(du), ds]
+    for m in range(1, d):
+        LP.append(((2 * m + 1) * sP * LP[m] - m * qP * qP * LP[m - 1]) / (m + 1))
+        LQ.append(((2 * m + 1) * sQ * LQ[m] - m * qQ * qQ * LQ[m - 1]) / (m + 1))
+        dL.append(((2 * m + 1) * (sQ * dL[m] + ds * LP[m])
+                   - m * (qQ * qQ * dL[m - 1] + dq2 * LP[m - 1])) / (m + 1))
+    for m in range(d + 1):
+        b = 2 * m + 1
+        PP, PQ, dP = 1.0, np.ones_like(du), np.zeros_like(du)
+        PPm, PQm, dPm = 0.0, np.zeros_like(du), np.zeros_like(du)
+        for a in range(d - m + 1):
+            n = m + a
+            out[index(n, m)] = c_nm(n, m) * (dL[m] * PQ + LP[m] * dP)
+            c1, c0, c2 = jacobi_recurrence(a, b)
+            PPn = (c1 * yP + c0) * PP - c2 * PPm
+            PQn = (c1 * yQ + c0) * PQ - c2 * PQm
+            dPn = (c1 * yQ + c0) * dP + c1 * dy * PP - c2 * dPm
+            PPm, PP = PP, PPn
+            PQm, PQ = PQ, PQn
+            dPm, dP = dP, dPn
+    return out

@@ -12,7 +12,7 @@ import numpy as np
 
 from . import koornwinder as kw
 from . import rules
-from .kernels import kernel_jac
+from .kernels import kernel_envelope, kernel_jac
 
 
 class Kern:
@@ -22,11 +22,15 @@ class Kern:
     def __call__(self, x, X, N):
         return kernel_jac(x, X, N, self.k, self.kind, self.alpha, self.beta)
 
+    def envelope(self, x, X, N, R):
+        return kernel_envelope(x, X, N, self.k, self.kind, self.alpha, self.beta, R)
+
 
 def rule_moments(patch, x, ru, rv, rw, kern):
-    """I_nm(x) by one rule (u_q, v_q, w_q) on T0: sum_q w_q K(x, X_q) J_q K_nm(u_q, v_q)."""
-    X, N, K = patch.eval(ru, rv)
-    return K @ (rw * kern(x, X, N))
+    """I_nm(x) by one rule (u_q, v_q, w_q) on T0: sum_q w_q K(x, X_q) J_q K_nm(u_q, v_q).
+    Positions are taken relative to the patch centroid (x - c_j against X - c_j)."""
+    X, N, K = patch.eval_rel(ru, rv)
+    return K @ (rw * kern(np.asarray(x) - patch.c, X, N))
 
 
 def far_order(patch, test_pts, kern, eps, m_min, m_max):
@@ -38,8 +42,8 @@ def far_order(patch, test_pts, kern, eps, m_min, m_max):
 
     def mom(m):
         ru, rv, rw = rules.conical_rule(m)
-        X, N, K = patch.eval(ru, rv)
-        return [K @ (rw * kern(x, X, N)) for x in test_pts]
+        X, N, K = patch.eval_rel(ru, rv)
+        return [K @ (rw * kern(np.asarray(x) - patch.c, X, N)) for x in test_pts]
 
     prev = mom(m_min)
     margin = np.inf
@@ -69,9 +73,19 @@ def conformal_map(patch, i):
 
 
 def self_weights(patch, i, x, kern, order):
-    """Self point weights a_l(x_i) for the target at node i (Sec. 4, Eq. errestself)."""
-    ru, rv, rw = rules.self_rule(patch.d, i, order, order, conformal_map(patch, i))
-    return patch.V.T @ rule_moments(patch, x, ru, rv, rw, kern)
+    """Self point weights a_l(x_i) for the target at node i (Sec. 4, Eq. errestself).
+
+    The target is the chart's value at the node, X(P); the chord x - X(P + delta) is
+    formed as -(X(P + delta) - X(P)) from Koornwinder differences (koornwinder.
+    basis_delta), so that the near-singular double-layer factor n.(x - X) keeps its
+    relative precision as delta -> 0.  (x itself is not used beyond that.)"""
+    ru, rv, rw, du, dv = rules.self_rule(patch.d, i, order, order, conformal_map(patch, i),
+                                         offsets=True)
+    un, vn = rules.interp_nodes(patch.d)
+    _, N, K = patch.eval_rel(ru, rv)
+    dX = patch.coefs.T @ kw.basis_delta(patch.d, (un[i], vn[i]), du, dv)
+    g = kern(np.zeros(3), dX, N)
+    return patch.V.T @ (K @ (rw * g))
 
 
 class LeafCache:
@@ -86,43 +100,61 @@ class LeafCache:
     def get(self, path, T):
         if path not in self.memo:
             u, v, w = rules.map_rule(T, *self.rule)
-            X, N, K = self.patch.eval(u, v)
+            X, N, K = self.patch.eval_rel(u, v)
             self.memo[path] = (X, N, K, w)
         return self.memo[path]
 
 
-ROUNDING_FLOOR = 1e-12
+ROUNDING_FLOOR = 2e-13
 
 
 def adaptive_moments(cache: LeafCache, x, kern, tol0, max_depth):
     """Adaptive integration of I_nm(x) over T0 by midpoint subdivision (Sec. 4.3).
 
     A triangle T at level L (|T|/|T0| = 4^-L) is compared with its 4 children;
-    if ||I_T - sum_c I_c||_2 <= max(tol0 4^-L, 1e-12 ||sum_c I_c||_2) the children's
-    sum is accepted, otherwise each child is tested in turn (breadth first).  The
-    second term is a rounding floor (a reading: the paper's absolute tolerance can
-    fall below what FP64 resolves for near-singular integrands).  Children at level
-    max_depth are not tested further: their sum is accepted and the depth flag set.
+    if ||I_T - sum_c I_c||_2 <= max(tol0 4^-L, 2e-13 sum_c E_c) the children's sum is
+    accepted, otherwise each child is tested in turn (breadth first).  E_c is the
+    rounding envelope of the kernel summed over child c's nodes (kernels.
+    kernel_envelope): the second term is a rounding floor (a reading: the paper's
+    absolute tolerance can fall below what FP64 resolves for near-singular
+    integrands, and the double-layer integrand loses digits to cancellation for
+    targets near the tangent plane).  Children at level max_depth are not tested
+    further: their sum is accepted and the depth flag set.
     Returns (I [n], stats dict).
     """
+    patch = cache.patch
+    xr = np.asarray(x) - patch.c
+
     def moments(path, T):
         X, N, K, w = cache.get(path, T)
-        return K @ (w * kern(x, X, N))
+        return K @ (w * kern(xr, X, N))
+
+    def envelope(path, T):
+        X, N, K, w = cache.get(path, T)
+        return float((w * kern.envelope(xr, X, N, patch.R)).sum())
 
     I_root = moments((), rules.T0)
     queue = deque([((), rules.T0, I_root)])
     total = np.zeros_like(I_root)
     leaves, tests, min_margin, depth_hit, max_level = 0, 0, np.inf, False, 0
+    floor_sum = 0.0   # sum of the tolerances of tests decided by the rounding floor
+    close_sum = 0.0   # sum of the tolerances of tests decided within 1e-3 of the threshold
     while queue:
         path, T, I_T = queue.popleft()
         L = len(path)
         kids = rules.subdivide(T)
         I_c = [moments(path + (c,), kids[c]) for c in range(4)]
         S = I_c[0] + I_c[1] + I_c[2] + I_c[3]
+        E = sum(envelope(path + (c,), kids[c]) for c in range(4))
         err = float(np.linalg.norm(I_T - S))
-        tau = max(tol0 * 0.25 ** L, ROUNDING_FLOOR * float(np.linalg.norm(S)))
+        tauL = tol0 * 0.25 ** L
+        tau = max(tauL, ROUNDING_FLOOR * E)
+        if tau > tauL:
+            floor_sum += tau
         tests += 1
         min_margin = min(min_margin, abs(err - tau) / tau)
+        if abs(err - tau) < 1e-3 * tau:
+            close_sum += tau
         if err <= tau or L + 1 >= max_depth:
             if err > tau:
                 depth_hit = True
@@ -133,4 +165,4 @@ def adaptive_moments(cache: LeafCache, x, kern, tol0, max_depth):
             for c in range(4):
                 queue.append((path + (c,), kids[c], I_c[c]))
     return total, dict(leaves=leaves, tests=tests, margin=min_margin, depth_hit=depth_hit,
-                       max_level=max_level)
+                       max_level=max_level, floor_sum=floor_sum, close_sum=close_sum, tol0=tol0)

@@ -84,7 +84,7 @@ def conical_rule(m: int):
     return u, v, w
 
 
-def self_rule(d: int, i: int, ns: int, nt: int, M=None):
+def self_rule(d: int, i: int, ns: int, nt: int, M=None, offsets: bool = False):
     """Singular rule on T0 for the target at node i (reading of Sec. 4, Eq. errestself).
 
     M is a 2x2 matrix mapping local coordinates zeta to reference offsets
@@ -96,7 +96,8 @@ def self_rule(d: int, i: int, ns: int, nt: int, M=None):
     Gauss-Legendre, t is split at the foot of the perpendicular from the node and each
     side uses t - t0 = mu sinh(xi), mu = h/L, with [0, xi_max] cut into
     ceil(xi_max / 1.5) equal panels of nt-point Gauss-Legendre.
-    Returns (u, v, w) on T0; the weights carry all Jacobians.
+    Returns (u, v, w) on T0 (and the offsets (u - u_i, v - v_i) computed directly
+    when offsets=True); the weights carry all Jacobians.
     """
     un, vn = interp_nodes(d)
     P = np.array([un[i], vn[i]])
@@ -131,7 +132,10 @@ def self_rule(d: int, i: int, ns: int, nt: int, M=None):
                     out_w.append(ws[a] * wt * s[a] * area2 * detM)
     Z = np.concatenate(out_z)
     W = np.concatenate(out_w)
-    UV = P[None, :] + Z @ M.T
+    dUV = Z @ M.T
+    UV = P[None, :] + dUV
+    if offsets:
+        return UV[:, 0], UV[:, 1], W, dUV[:, 0], dUV[:, 1]
     return UV[:, 0], UV[:, 1], W
 
 

@@ -169,6 +169,7 @@ lcq_status lcq_create(lcq_ctx** out, int device, void* cuda_stream) {
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(long long), ctx->stream));
   CK(upload_constants(ctx->stream));
+  for (int i = 0; i < 8; ++i) CK(cudaEventCreate(&ctx->ev[i]));
   lcq_status s = ensure_rules(ctx);
   if (s != LCQ_OK) {
     lcq_destroy(ctx);
@@ -196,6 +197,8 @@ void lcq_destroy(lcq_ctx* ctx) {
   dfree(ctx->stream, r.dgl_w);
   if (ctx->work) cudaFreeAsync(ctx->work, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
+  for (int i = 0; i < 8; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_counters);
   cudaGetLastError();
@@ -224,6 +227,18 @@ lcq_status lcq_sync(lcq_ctx* ctx, int64_t timeout_ms) {
   if (st & kStDegenerate) return fail(ctx, LCQ_ERR_DEGENERATE_PATCH, "degenerate patch");
   if (st & kStCapacity) return fail(ctx, LCQ_ERR_CAPACITY, "work storage exceeded");
   if (st & kStMaxDepth) return fail(ctx, LCQ_ERR_MAX_DEPTH, "max_depth reached");
+  return LCQ_OK;
+}
+
+lcq_status lcq_stage_times(lcq_ctx* ctx, float* ms6, int64_t* launches) {
+  if (!ctx) return LCQ_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ms6) {
+    CK(cudaEventElapsedTime(&ms6[0], ctx->ev[0], ctx->ev[1]));
+    for (int i = 0; i < 5; ++i) CK(cudaEventElapsedTime(&ms6[1 + i], ctx->ev[2 + i], ctx->ev[3 + i]));
+  }
+  if (launches) *launches = ctx->launches_near + ctx->launches_corr;
   return LCQ_OK;
 }
 
@@ -260,7 +275,9 @@ lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const dou
   if (N >= (int64_t)0x7fffffff) return fail(ctx, LCQ_ERR_ARG, "more than 2^31-1 nodes");
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
-  LaunchCommon lc{st, ctx->num_sms};
+  ctx->launches_near = 0;
+  LaunchCommon lc{st, ctx->num_sms, &ctx->launches_near};
+  CK(cudaEventRecord(ctx->ev[0], st));
 
   lcq_near* nr = new lcq_near();
   nr->params = *params;
@@ -402,6 +419,7 @@ lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const dou
                       nr->self_tgt, nr->self_csr);
   }
   CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev[1], st));
   dfree(st, row_np);
   dfree(st, row_nnz);
   dfree(st, npair);
@@ -538,7 +556,8 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
     return fail(ctx, LCQ_ERR_ARG, "parameter out of range");
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = ctx->stream;
-  LaunchCommon lc{st, ctx->num_sms};
+  ctx->launches_corr = 0;
+  LaunchCommon lc{st, ctx->num_sms, &ctx->launches_corr};
   const int64_t P = nr->n_patches;
   KernelParams kp{(int)kernel, k_re, k_im, alpha_re, alpha_im, beta_re, beta_im};
   if (kernel == LCQ_S) kp.ar = kp.ai = kp.br = kp.bi = 0.0;
@@ -554,7 +573,7 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
   c->n_pairs = nr->n_pairs;
   c->n_self = nr->n_self;
   c->kp = kp;
-  CK(dalloc(st, &c->val, (size_t)2 * nr->nnz));
+  CK(dalloc(st, &c->val, (size_t)2 * std::max<int64_t>(nr->nnz, 1)));
   CK(dalloc(st, &c->q, P));
   CK(dalloc(st, &c->q_near, P));
   CK(dalloc(st, &c->leaves, nr->n_pairs));
@@ -590,6 +609,7 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
   CK(dalloc(st, reinterpret_cast<double**>(&InS), (size_t)2 * nsf * ldI));
   Dev dv = make_dev(ctx, nr, c->q, ldI);
 
+  CK(cudaEventRecord(ctx->ev[2], st));
   // 1. far order q_j and annulus order (Sec. 4.2, Eq. qj)
   const int fgrid = ctx->num_sms * 2;
   double* fscr;
@@ -600,6 +620,7 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
                     ctx->deg[d].normV, ddirs, ndirs, fscr, fgrid, c->q, c->q_near);
   }
   CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev[3], st));
   // 2. smooth-rule moments of every near and self pair; 3. annulus moments
   for (int d = 1; d <= kMaxDeg; ++d) {
     if (!nr->plist_count[d]) continue;
@@ -607,13 +628,15 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
     launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 1, c->q_near, kp, In, nullptr);
   }
   CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev[4], st));
   // 4. adaptive near moments (Sec. 4.3)
   if (nr->n_adaptive > 0) {
     const int levels = params->max_depth;
     const int64_t A = nr->max_adaptive;
     const int64_t n = ldI;
     int64_t stride = A * n * 16 + A * 4 * n * 16 + (int64_t)levels * A * 4 * n * 16 +
-                     (int64_t)levels * A * 4 + 2 * A * 4 + (int64_t)levels * 4 + 256;
+                     (int64_t)levels * A * 4 + 2 * A * 4 + (int64_t)levels * 4 + 8 + A * 4 * 8 +
+                     256;
     stride = (stride + 255) / 256 * 256;
     const int agrid = ctx->num_sms;
     const size_t need = (size_t)stride * agrid;
@@ -633,6 +656,7 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
     }
     CK(cudaGetLastError());
   }
+  CK(cudaEventRecord(ctx->ev[5], st));
   // 5. self weights (Sec. 4, Eq. errestself)
   const int sorder = params->self_order > 0 ? params->self_order : default_self_order(params->eps);
   if (nr->n_self > 0)
@@ -641,12 +665,14 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
       launch_self(d, lc, dv, nr->deg, kp, sorder, InS);
     }
   CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev[6], st));
   // 6. c = V^T (I_near - I_smooth) into the CSR
   for (int d = 1; d <= kMaxDeg; ++d) {
     if (!nr->plist_count[d]) continue;
     launch_v2c(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, In, Is, InS, IsS, c->val);
   }
   CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev[7], st));
   dfree(st, ddirs);
   dfree(st, fscr);
   cudaFreeAsync(Is, st);
@@ -727,7 +753,8 @@ static lcq_status apply_impl(lcq_ctx* ctx, const lcq_near* nr, const lcq_corr* c
   lcq_status s = ensure_q_host(ctx, c);
   if (s != LCQ_OK) return s;
   cudaStream_t st = ctx->stream;
-  LaunchCommon lc{st, ctx->num_sms};
+  long long napply = 0;
+  LaunchCommon lc{st, ctx->num_sms, &napply};
   Dev dv = make_dev(ctx, nr, c->q, nr->n_max);
   double* src;
   CK(dalloc(st, &src, (size_t)9 * std::max<int64_t>(c->n_over, 1)));
@@ -736,7 +763,8 @@ static lcq_status apply_impl(lcq_ctx* ctx, const lcq_near* nr, const lcq_corr* c
     launch_far_src(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, c->q,
                    c->src_off, sigma, src, c->n_over);
   }
-  launch_far_sum(lc, nr->tgt, nr->n_targets, src, c->n_over, c->kp, out);
+  launch_far_sum(lc, nr->tgt, nr->n_targets, src, c->n_over, c->kp, nr->tgt_patch, c->src_off,
+                 out);
   launch_csr_apply(lc, nr->row_ptr, nr->col, c->val, sigma, nr->tnode, nr->n_targets, jump, out);
   CK(cudaGetLastError());
   dfree(st, src);

@@ -148,6 +148,70 @@ __device__ __forceinline__ void kw_geometry(double u, double v, const double* __
   }
 }
 
+// Self-rule geometry at Q = P + delta: the chord dX = X(Q) - X(P), formed from Koornwinder
+// differences K_nm(Q) - K_nm(P) that obey the same recurrences (so dX keeps its relative
+// precision as delta -> 0), and X_u, X_v at Q.
+template <int D>
+__device__ __forceinline__ void kw_delta_geometry(double pu, double pv, double du, double dv,
+                                                  const double* __restrict__ cf, double* dX,
+                                                  double* Xu, double* Xv) {
+  const double uq = pu + du, vq = pv + dv;
+  const double sP = 2.0 * pu + pv - 1.0, qP = 1.0 - pv, yP = 1.0 - 2.0 * pv;
+  const double sQ = 2.0 * uq + vq - 1.0, qQ = 1.0 - vq, yQ = 1.0 - 2.0 * vq;
+  const double ds = 2.0 * du + dv, dq2 = -dv * (qQ + qP), dy = -2.0 * dv;
+  const double qQ2 = qQ * qQ, qP2 = qP * qP;
+  double LPp = 0.0, LP = 1.0, LQp = 0.0, LQ = 1.0, dLp = 0.0, dL = 0.0;
+  double Lup = 0.0, Lu = 0.0, Lvp = 0.0, Lv = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dX[c] = Xu[c] = Xv[c] = 0.0;
+#pragma unroll
+  for (int m = 0; m <= D; ++m) {
+    if (m > 0) {
+      const double f1 = 2.0 * m - 1.0, f2 = m - 1.0, im = 1.0 / m;
+      const double nLP = (f1 * sP * LP - f2 * qP2 * LPp) * im;
+      const double nLQ = (f1 * sQ * LQ - f2 * qQ2 * LQp) * im;
+      const double ndL = (f1 * (sQ * dL + ds * LP) - f2 * (qQ2 * dLp + dq2 * LPp)) * im;
+      const double nLu = (f1 * (2.0 * LQ + sQ * Lu) - f2 * qQ2 * Lup) * im;
+      const double nLv = (f1 * (LQ + sQ * Lv) - f2 * (-2.0 * qQ * LQp + qQ2 * Lvp)) * im;
+      LPp = LP; LP = nLP;
+      LQp = LQ; LQ = nLQ;
+      dLp = dL; dL = ndL;
+      Lup = Lu; Lu = nLu;
+      Lvp = Lv; Lv = nLv;
+    }
+    const int b = 2 * m + 1;
+    double PPp = 0.0, PP = 1.0, PQp = 0.0, PQ = 1.0, dPp = 0.0, dP = 0.0, pQp = 0.0, pQ = 0.0;
+#pragma unroll
+    for (int a = 0; a <= D - m; ++a) {
+      const int n = m + a, idx = n * (n + 1) / 2 + m;
+      const double cn = c_kw[idx];
+      const double dk = cn * (dL * PQ + LP * dP);
+      const double ku = cn * Lu * PQ;
+      const double kv = cn * (Lv * PQ - 2.0 * LQ * pQ);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double x = cf[idx * 3 + c];
+        dX[c] = fma(x, dk, dX[c]);
+        Xu[c] = fma(x, ku, Xu[c]);
+        Xv[c] = fma(x, kv, Xv[c]);
+      }
+      if (a < D - m) {
+        double c1, c0, c2;
+        jacobi_coef(a, b, &c1, &c0, &c2);
+        const double tQ = c1 * yQ + c0;
+        const double nPP = (c1 * yP + c0) * PP - c2 * PPp;
+        const double nPQ = tQ * PQ - c2 * PQp;
+        const double ndP = tQ * dP + c1 * dy * PP - c2 * dPp;
+        const double npQ = c1 * PQ + tQ * pQ - c2 * pQp;
+        PPp = PP; PP = nPP;
+        PQp = PQ; PQ = nPQ;
+        dPp = dP; dP = ndP;
+        pQp = pQ; pQ = npQ;
+      }
+    }
+  }
+}
+
 // Kernel times area element and weight, at a source with position X, weighted
 // unnormalized normal Nw = (X_u x X_v) w and weighted Jacobian Jw = |X_u x X_v| w:
 //   S: G_k(x, X) Jw
@@ -183,6 +247,32 @@ __device__ __forceinline__ cplx kernel_eval(const KernelParams& kp, double x0, d
   out.re += ad.re;
   out.im += ad.im;
   return out;
+}
+
+// Rounding envelope of kernel_eval (same arguments, plus the patch radius R):
+//   |G| Jw (b + a |1 - ik r| R / r^2), b = 1, 0, |beta|, a = 0, 1, |alpha| for S, D, CFIE.
+// It bounds the size of the rounding noise of the kernel value when positions carry
+// errors of order u R (positions are relative to the patch centroid); the adaptive
+// test never asks for less than a fixed multiple of its sum.
+__device__ __forceinline__ double kernel_envelope(const KernelParams& kp, double x0, double x1,
+                                                  double x2, double X0, double X1, double X2,
+                                                  double Jw, double R) {
+  const double d0 = x0 - X0, d1 = x1 - X1, d2 = x2 - X2;
+  const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+  if (r2 == 0.0) return 0.0;
+  const double r = sqrt(r2);
+  double g = 0.07957747154594767 / r * Jw;
+  if (kp.ki != 0.0) g *= exp(-kp.ki * r);
+  double b, a;
+  if (kp.kind == 0) { b = 1.0; a = 0.0; }
+  else if (kp.kind == 1) { b = 0.0; a = 1.0; }
+  else { b = sqrt(kp.br * kp.br + kp.bi * kp.bi); a = sqrt(kp.ar * kp.ar + kp.ai * kp.ai); }
+  double e = b;
+  if (a != 0.0) {
+    const double f0 = 1.0 + kp.ki * r, f1 = kp.kr * r;
+    e += a * sqrt(f0 * f0 + f1 * f1) * R / r2;
+  }
+  return g * e;
 }
 
 // Cross product helper.

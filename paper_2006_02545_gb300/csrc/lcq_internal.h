@@ -82,6 +82,9 @@ struct lcq_ctx {
   // grow-only workspace for the adaptive kernel
   void* work = nullptr;
   size_t work_bytes = 0;
+  // stage events: [0,1] near lists, [2..7] corrections
+  cudaEvent_t ev[8] = {};
+  long long launches_near = 0, launches_corr = 0;
 };
 
 struct lcq_near {

@@ -160,7 +160,10 @@ __global__ void k_geom(const int* __restrict__ plist, int count, const int64_t* 
       cen[3 * j + 1] = c[1];
       cen[3 * j + 2] = c[2];
     }
-    for (int e = threadIdx.x; e < 3 * n; e += blockDim.x) coef[off * 3 + e] = cf[e];
+    // coefficients of X - c_j (K_00 = sqrt(2) is constant): every local quadrature works
+    // with positions relative to the centroid
+    for (int e = threadIdx.x; e < 3 * n; e += blockDim.x)
+      coef[off * 3 + e] = e < 3 ? cf[e] - c[e] * 0.70710678118654752 : cf[e];
   }
 }
 
@@ -415,7 +418,7 @@ struct Cfg {
   static constexpr int BS = n + 1;
   static constexpr int TT = 16;
   // doubles of shared workspace used by block_moments
-  static constexpr int WS = CH * BS + 7 * CH + 2 * TT * CH + 3 * TT;
+  static constexpr int WS = CH * BS + 7 * CH + 3 * TT * CH + 3 * TT;
 };
 
 struct SegMap {
@@ -426,18 +429,22 @@ struct SegMap {
 // rule (Q nodes) pushed onto nseg affine images of T0, for T targets.  Geometry is
 // evaluated once per chunk of nodes and shared by all targets (Sec. 4.3 reuse).
 // TA: target accessor (pos(i, x[3])); out row of target i: out + orow(i) * ostride.
-template <int D, class TA, class OR>
+// Positions are relative to the patch centroid cen (the coefficients cf describe
+// X - cen).  With ENV, eout[i * nseg + seg] also receives the summed rounding envelope.
+template <int D, bool ENV = false, class TA, class OR>
 __device__ void block_moments(const double* cf, const double* __restrict__ ru,
                               const double* __restrict__ rv, const double* __restrict__ rw, int Q,
                               const SegMap* segs, int nseg, const TA& ta, int T, OR orow,
-                              int64_t ostride, const KernelParams& kp, double* sm) {
+                              int64_t ostride, const KernelParams& kp, double* sm,
+                              const double* cen, double R = 0.0, double* eout = nullptr) {
   using C = Cfg<D>;
   double* B = sm;
   double* Xs = B + C::CH * C::BS;
   double* Ns = Xs + 3 * C::CH;
   double* Js = Ns + 3 * C::CH;
   cplx* G = reinterpret_cast<cplx*>(Js + C::CH);
-  double* tx = reinterpret_cast<double*>(G + C::TT * C::CH);
+  double* Ev = reinterpret_cast<double*>(G + C::TT * C::CH);
+  double* tx = Ev + C::TT * C::CH;
   const int total = nseg * Q;
   for (int c0 = 0; c0 < total; c0 += C::CH) {
     const int nch = min(C::CH, total - c0);
@@ -464,15 +471,27 @@ __device__ void block_moments(const double* cf, const double* __restrict__ ru,
     __syncthreads();
     for (int t0 = 0; t0 < T; t0 += C::TT) {
       const int nt = min(C::TT, T - t0);
-      if (threadIdx.x < nt) ta.pos(t0 + threadIdx.x, tx + 3 * threadIdx.x);
+      if (threadIdx.x < nt) {
+        double* xp = tx + 3 * threadIdx.x;
+        ta.pos(t0 + threadIdx.x, xp);
+        xp[0] -= cen[0];
+        xp[1] -= cen[1];
+        xp[2] -= cen[2];
+      }
       __syncthreads();
       for (int e = threadIdx.x; e < nt * C::CH; e += blockDim.x) {
         const int i = e / C::CH, ql = e - i * C::CH;
         cplx g = {0.0, 0.0};
-        if (ql < nch)
+        double ev = 0.0;
+        if (ql < nch) {
           g = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql], Xs[C::CH + ql],
                           Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql], Js[ql]);
+          if (ENV)
+            ev = kernel_envelope(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql],
+                                 Xs[C::CH + ql], Xs[2 * C::CH + ql], Js[ql], R);
+        }
         G[i * C::CH + ql] = g;
+        if (ENV) Ev[i * C::CH + ql] = ev;
       }
       __syncthreads();
       const int nout = nt * nseg * C::NP;
@@ -498,6 +517,12 @@ __device__ void block_moments(const double* cf, const double* __restrict__ ru,
         } else {
           dst->re += are;
           dst->im += aim;
+        }
+        if (ENV && nm == 0) {
+          double es = 0.0;
+          for (int ql = qa; ql < qb; ++ql) es += Ev[i * C::CH + ql];
+          double* ed = eout + (int64_t)(t0 + i) * nseg + sg;
+          *ed = (c0 == 0) ? es : *ed + es;
         }
       }
       __syncthreads();
@@ -587,12 +612,9 @@ __global__ void __launch_bounds__(kThreads) k_rule_moments(
       const int64_t ld = dv.ldI;
       cplx* base = out_pairs + p0 * ld;
       block_moments<D>(cf, ru, rv, rw, m * m, segs, 1, ta, (int)np,
-                       [=] __device__(int i) { return base + (int64_t)i * ld; }, C::n, kp, ws);
-      const int64_t s0 = dv.self_ptr[j], ns = dv.self_ptr[j + 1] - s0;
-      TgtIdx ts{dv.tgt, dv.NT, dv.self_tgt + s0};
-      cplx* sb = out_self + s0 * ld;
-      block_moments<D>(cf, ru, rv, rw, m * m, segs, 1, ts, (int)ns,
-                       [=] __device__(int i) { return sb + (int64_t)i * ld; }, C::n, kp, ws);
+                       [=] __device__(int i) { return base + (int64_t)i * ld; }, C::n, kp, ws,
+                       dv.cen + 3 * j);
+      (void)out_self;
     } else {
       const int64_t a0 = dv.an_ptr[j], na = dv.an_ptr[j + 1] - a0;
       const int32_t* pl = dv.an_pair + a0;
@@ -600,11 +622,10 @@ __global__ void __launch_bounds__(kThreads) k_rule_moments(
       const int64_t ld = dv.ldI;
       block_moments<D>(cf, ru, rv, rw, m * m, segs, 1, ta, (int)na,
                        [=] __device__(int i) { return out_pairs + (int64_t)pl[i] * ld; }, C::n, kp,
-                       ws);
+                       ws, dv.cen + 3 * j);
     }
     if (threadIdx.x == 0) {
-      const long long nt = mode == 0 ? (dv.pair_ptr[j + 1] - dv.pair_ptr[j] + dv.self_ptr[j + 1] -
-                                        dv.self_ptr[j])
+      const long long nt = mode == 0 ? (dv.pair_ptr[j + 1] - dv.pair_ptr[j])
                                      : (dv.an_ptr[j + 1] - dv.an_ptr[j]);
       atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 3),
                 (unsigned long long)(nt * m * m));
@@ -729,7 +750,8 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
       {
         const double* ru = dv.ru + dv.roff[m];
         block_moments<D>(cf, ru, dv.rv + dv.roff[m], dv.rw + dv.roff[m], m * m, segs, 1, ta, F,
-                         [=] __device__(int i) { return bufA + (int64_t)i * C::n; }, C::n, kp, ws);
+                         [=] __device__(int i) { return bufA + (int64_t)i * C::n; }, C::n, kp, ws,
+                         dv.cen + 3 * j);
       }
       cplx* A = bufA;
       cplx* Bf = bufB;
@@ -737,7 +759,7 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
         const int m1 = m + 1;
         block_moments<D>(cf, dv.ru + dv.roff[m1], dv.rv + dv.roff[m1], dv.rw + dv.roff[m1], m1 * m1,
                          segs, 1, ta, F, [=] __device__(int i) { return Bf + (int64_t)i * C::n; },
-                         C::n, kp, ws);
+                         C::n, kp, ws, dv.cen + 3 * j);
         __syncthreads();
         // max over points of the 2-norm of the difference
         double e = 0.0;
@@ -783,6 +805,7 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
 // of X, K_nm and J across targets of Fig. multipletargpot).  A target accepts the
 // children's sum when ||I_T - sum_c I_c||_2 <= max(tol0 4^-L, 1e-12 ||sum_c I_c||_2).
 constexpr int kMaxTreeNodes = 1 << 16;  // union-tree nodes walked per patch at most
+constexpr double kRoundingFloor = 2e-13;  // multiple of the rounding envelope never asked below
 
 struct AdaptiveWS {
   int64_t stride;   // bytes per block
@@ -816,6 +839,8 @@ __global__ void __launch_bounds__(kThreads) k_adaptive(const int* __restrict__ p
   int* flags = lvlT + (int64_t)wsd.levels * A_max;                  // [A_max]
   int* lcnt = flags + A_max;                                        // [A_max]
   int* cnt = lcnt + A_max;                                          // [levels]
+  double* tmpE = reinterpret_cast<double*>(                          // [A_max][4], 8-aligned
+      (reinterpret_cast<uintptr_t>(cnt + wsd.levels) + 7) & ~static_cast<uintptr_t>(7));
   long long my_tests = 0, my_nodes = 0;
 
   for (int b = blockIdx.x; b < count; b += gridDim.x) {
@@ -833,6 +858,7 @@ __global__ void __launch_bounds__(kThreads) k_adaptive(const int* __restrict__ p
     const double* rv = dv.rv + dv.roff[m];
     const double* rw = dv.rw + dv.roff[m];
     const double tol0 = eps * dv.dj[j] / normV;
+    const double Rj = dv.rad[j];
     const int32_t* apairs = dv.ad_pair + a0;
     __syncthreads();
     load_coef<D>(dv.coef, dv.node_off[j], cf);
@@ -854,7 +880,8 @@ __global__ void __launch_bounds__(kThreads) k_adaptive(const int* __restrict__ p
     if (leaf_order > 0) {
       TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, apairs};
       block_moments<D>(cf, ru, rv, rw, Q, segs, 1, ta, A,
-                       [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, 4 * n, kp, ws);
+                       [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, 4 * n, kp, ws,
+                       dv.cen + 3 * j);
     }
     // DFS stack entries: level (8 bits) | child (2 bits) | path (2 bits per level) << 16
     int sp = 0;
@@ -910,8 +937,9 @@ __global__ void __launch_bounds__(kThreads) k_adaptive(const int* __restrict__ p
       __syncthreads();
       // children moments of every target in S
       TgtAdaptive ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, ST};
-      block_moments<D>(cf, ru, rv, rw, Q, segs, 4, ta, S,
-                       [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, 4 * n, kp, ws);
+      block_moments<D, true>(cf, ru, rv, rw, Q, segs, 4, ta, S,
+                             [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, 4 * n, kp,
+                             ws, dv.cen + 3 * j, Rj, tmpE);
       __syncthreads();
       my_tests += S;
       my_nodes += (long long)S * 4 * Q;
@@ -930,9 +958,9 @@ __global__ void __launch_bounds__(kThreads) k_adaptive(const int* __restrict__ p
           s2 += sr * sr + si * si;
         }
         e2 = warp_sum(e2);
-        s2 = warp_sum(s2);
         const double err = sqrt(e2);
-        const double tau = fmax(tauL, 1e-12 * sqrt(s2));
+        const double* ee = tmpE + (int64_t)s * 4;
+        const double tau = fmax(tauL, kRoundingFloor * (ee[0] + ee[1] + ee[2] + ee[3]));
         const bool finite = isfinite(err) && isfinite(tau);
         const bool accept = !finite || (err <= tau) || (L + 1 >= max_depth);
         if (lane == 0) {
@@ -1093,7 +1121,7 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
       total = off;
     }
     __syncthreads();
-    const double x0 = dv.tgt[t], x1 = dv.tgt[dv.NT + t], x2 = dv.tgt[2 * dv.NT + t];
+    // the target is the chart's value at the node: x - X(P + delta) = -(dX)
     cplx acc[n];
 #pragma unroll
     for (int k = 0; k < n; ++k) acc[k] = {0.0, 0.0};
@@ -1113,14 +1141,16 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
       const double sv = glx_s[si];
       const double w = glw_s[si] * wt * sv * g.area2 * Mm[4];
       const double zx = sv * (g.E0x + tpar * g.Dx), zy = sv * (g.E0y + tpar * g.Dy);
-      const double u = P[0] + Mm[0] * zx + Mm[1] * zy;
-      const double v = P[1] + Mm[2] * zx + Mm[3] * zy;
-      double X[3], Xu[3], Xv[3], Nn[3];
-      kw_geometry<D>(u, v, cf, X, Xu, Xv, nullptr, 1);
+      const double du = Mm[0] * zx + Mm[1] * zy;
+      const double dvv = Mm[2] * zx + Mm[3] * zy;
+      const double u = P[0] + du;
+      const double v = P[1] + dvv;
+      double dX[3], Xu[3], Xv[3], Nn[3];
+      kw_delta_geometry<D>(P[0], P[1], du, dvv, cf, dX, Xu, Xv);
       cross3(Xu, Xv, Nn);
       const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
-      const cplx gk = kernel_eval(kp, x0, x1, x2, X[0], X[1], X[2], Nn[0] * w, Nn[1] * w, Nn[2] * w,
-                                  J * w);
+      const cplx gk = kernel_eval(kp, 0.0, 0.0, 0.0, dX[0], dX[1], dX[2], Nn[0] * w, Nn[1] * w,
+                                  Nn[2] * w, J * w);
       kw_accumulate<D>(u, v, gk, acc);
     }
     my_nodes += tot;
@@ -1165,9 +1195,12 @@ __global__ void k_v2c(const int* __restrict__ plist, int count, Dev dv,
     for (int64_t k = w; k < np + nsf; k += nw) {
       const bool self = k >= np;
       const int64_t id = self ? (s0 + k - np) : (p0 + k);
+      // self pairs store the self weights themselves: the own patch is masked out of the
+      // far sum (no spurious smooth-rule contribution to subtract)
       const cplx* a = self ? InS + id * dv.ldI : In + id * dv.ldI;
-      const cplx* s = self ? IsS + id * dv.ldI : Is + id * dv.ldI;
-      for (int nm = lane; nm < n; nm += 32) diff[w][nm] = {a[nm].re - s[nm].re, a[nm].im - s[nm].im};
+      const cplx* s = Is + id * dv.ldI;
+      for (int nm = lane; nm < n; nm += 32)
+        diff[w][nm] = self ? a[nm] : cplx{a[nm].re - s[nm].re, a[nm].im - s[nm].im};
       __syncwarp();
       const int64_t dst = self ? dv.self_csr[id] : dv.pair_csr[id];
       for (int l = lane; l < n; l += 32) {
@@ -1227,9 +1260,9 @@ __global__ void k_far_src(const int* __restrict__ plist, int count, Dev dv,
         im = fma(K[k], sc[k].im, im);
       }
       const int64_t o = src_off[j] + q;
-      src[0 * n_over + o] = X[0];
-      src[1 * n_over + o] = X[1];
-      src[2 * n_over + o] = X[2];
+      src[0 * n_over + o] = X[0] + dv.cen[3 * j];
+      src[1 * n_over + o] = X[1] + dv.cen[3 * j + 1];
+      src[2 * n_over + o] = X[2] + dv.cen[3 * j + 2];
       src[3 * n_over + o] = Nn[0] * w;
       src[4 * n_over + o] = Nn[1] * w;
       src[5 * n_over + o] = Nn[2] * w;
@@ -1242,16 +1275,27 @@ __global__ void k_far_src(const int* __restrict__ plist, int count, Dev dv,
 
 // Direct far sum over all oversampled sources, one thread per target (tiles of sources
 // staged through shared memory).
+// The sources of an on-surface target's own patch are skipped (their contribution is
+// carried entirely by the self correction).
 __global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__ tgt, int64_t NT,
                                                       const double* __restrict__ src, int64_t n_over,
-                                                      const KernelParams kp, cplx* __restrict__ out) {
+                                                      const KernelParams kp,
+                                                      const int32_t* __restrict__ tpatch,
+                                                      const int64_t* __restrict__ src_off,
+                                                      cplx* __restrict__ out) {
   __shared__ double s[9][kThreads];
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double x0 = 0, x1 = 0, x2 = 0;
+  int64_t skip0 = -1, skip1 = -1;
   if (t < NT) {
     x0 = tgt[t];
     x1 = tgt[NT + t];
     x2 = tgt[2 * NT + t];
+    const int tp = tpatch[t];
+    if (tp >= 0) {
+      skip0 = src_off[tp];
+      skip1 = src_off[tp + 1];
+    }
   }
   double re = 0.0, im = 0.0;
   for (int64_t s0 = 0; s0 < n_over; s0 += kThreads) {
@@ -1262,6 +1306,8 @@ __global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__
     const int cnt = (int)min((int64_t)kThreads, n_over - s0);
     if (t < NT)
       for (int k = 0; k < cnt; ++k) {
+        const int64_t qq = s0 + k;
+        if (qq >= skip0 && qq < skip1) continue;
         const cplx g = kernel_eval(kp, x0, x1, x2, s[0][k], s[1][k], s[2][k], s[3][k], s[4][k],
                                    s[5][k], s[6][k]);
         re = fma(g.re, s[7][k], re);
@@ -1328,6 +1374,7 @@ struct GeomL {
                   double eta1_p, double* coef, double* cen, double* rad, double* dj, double* eta,
                   double* eta1, int* status) {
     const int grid = count < lc.num_sms * 8 ? count : lc.num_sms * 8;
+    ++*lc.launches;
     k_geom<D><<<grid, 128, 0, lc.stream>>>(plist, count, node_off, xyz, N, Vt, nodes, eta_p, eta1_p,
                                            coef, cen, rad, dj, eta, eta1, status);
   }
@@ -1351,6 +1398,7 @@ struct RuleMomL {
     const size_t sm = moments_smem_bytes<D>(0);
     set_smem(k_rule_moments<D>, sm);
     const int grid = count < lc.num_sms ? count : lc.num_sms;
+    ++*lc.launches;
     k_rule_moments<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, mode, qv, kp,
                                                          (cplx*)out_pairs, (cplx*)out_self);
   }
@@ -1363,6 +1411,7 @@ struct FarOrderL {
                   int ndirs, void* scratch, int grid, int32_t* q, int32_t* qn) {
     const size_t sm = moments_smem_bytes<D>(3 * kMaxTestPts + kThreads / 32 + 4);
     set_smem(k_farorder<D>, sm);
+    ++*lc.launches;
     k_farorder<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, kp, eps, m_max, normV, dirs,
                                                      ndirs, (cplx*)scratch, q, qn);
   }
@@ -1377,6 +1426,7 @@ struct AdaptiveL {
     const size_t sm = moments_smem_bytes<D>(64 / 2 + 4 * 32) + 64 * sizeof(int);
     set_smem(k_adaptive<D>, sm);
     AdaptiveWS w{stride, A_max, levels};
+    ++*lc.launches;
     k_adaptive<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, kp, eps, normV, leaf_order,
                                                      max_depth, (const cplx*)I_smooth, (cplx*)I_near,
                                                      leaves, (unsigned char*)work, w, status);
@@ -1389,6 +1439,7 @@ struct SelfL {
                   int order, void* out) {
     const int64_t g = dv.n_self < (int64_t)lc.num_sms * 16 ? dv.n_self : (int64_t)lc.num_sms * 16;
     if (g <= 0) return;
+    ++*lc.launches;
     k_self<D><<<(int)g, 128, 0, lc.stream>>>(dv, deg, kp, order, (cplx*)out);
   }
 };
@@ -1399,6 +1450,7 @@ struct V2cL {
                   const double* Vt, const void* In, const void* Is, const void* InS,
                   const void* IsS, double* val) {
     const int grid = count < lc.num_sms * 4 ? count : lc.num_sms * 4;
+    ++*lc.launches;
     k_v2c<D><<<grid, kThreads, 0, lc.stream>>>(plist, count, dv, Vt, (const cplx*)In,
                                                (const cplx*)Is, (const cplx*)InS, (const cplx*)IsS,
                                                val);
@@ -1411,6 +1463,7 @@ struct FarSrcL {
                   const double* Vt, const int32_t* qv, const int64_t* src_off, const void* sigma,
                   double* src, int64_t n_over) {
     const int grid = count < lc.num_sms * 4 ? count : lc.num_sms * 4;
+    ++*lc.launches;
     k_far_src<D><<<grid, 128, 0, lc.stream>>>(plist, count, dv, Vt, qv, src_off,
                                               (const cplx*)sigma, src, n_over);
   }
@@ -1439,6 +1492,7 @@ void launch_tgt_patch(const LaunchCommon& lc, const double* tgt, const int64_t* 
                       int32_t* tlnode, int* status) {
   const int64_t blocks = (NT + 255) / 256;
   const int g = (int)(blocks < lc.num_sms * 16 ? (blocks > 0 ? blocks : 1) : lc.num_sms * 16);
+  ++*lc.launches;
   k_tgt_patch<<<g, 256, 0, lc.stream>>>(tgt, tnode, NT, node_off, P, N, tpatch, tlnode, status);
 }
 
@@ -1447,18 +1501,21 @@ static NearView nv(const NearArgs& a) { return {a.tgt, a.NT, a.cen, a.rad, a.eta
 void launch_row_count(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
                       const int32_t* deg, int64_t* row_np, int64_t* row_nnz) {
   const int g = lc.num_sms * 8;
+  ++*lc.launches;
   k_row_count<<<g, 256, 0, lc.stream>>>(nv(a), tpatch, P, deg, row_np, row_nnz);
 }
 void launch_row_fill(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
                      const int32_t* deg, const int64_t* node_off, const int64_t* rowp_ptr,
                      const int64_t* row_ptr, int32_t* rowp_patch, int64_t* rowp_off, int32_t* col) {
   const int g = lc.num_sms * 8;
+  ++*lc.launches;
   k_row_fill<<<g, 256, 0, lc.stream>>>(nv(a), tpatch, P, deg, node_off, rowp_ptr, row_ptr,
                                        rowp_patch, rowp_off, col);
 }
 void launch_patch_count(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
                         int64_t* npair, int64_t* nad, int64_t* nself) {
   const int g = (int)(P < lc.num_sms * 8 ? P : lc.num_sms * 8);
+  ++*lc.launches;
   k_patch_count<<<g, 256, 0, lc.stream>>>(nv(a), tpatch, P, npair, nad, nself);
 }
 void launch_patch_fill(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
@@ -1468,6 +1525,7 @@ void launch_patch_fill(const LaunchCommon& lc, const NearArgs& a, const int32_t*
                        uint8_t* pair_ad, double* pair_d2, int64_t* pair_csr, int32_t* ad_pair,
                        int32_t* an_pair, int32_t* self_tgt, int64_t* self_csr) {
   const int g = (int)(P < lc.num_sms * 8 ? P : lc.num_sms * 8);
+  ++*lc.launches;
   k_patch_fill<<<g, 256, 0, lc.stream>>>(nv(a), tpatch, P, pair_ptr, ad_ptr, an_ptr, self_ptr,
                                          rowp_ptr, rowp_patch, rowp_off, row_ptr, pair_tgt, pair_ad,
                                          pair_d2, pair_csr, ad_pair, an_pair, self_tgt, self_csr);
@@ -1478,9 +1536,11 @@ void launch_scan(const LaunchCommon& lc, const int64_t* in, int64_t* out, int64_
                  int64_t* scratch) {
   if (n <= 0) return;
   const int64_t nb = (n + 1023) / 1024;
+  ++*lc.launches;
   k_scan_block<<<(unsigned)nb, 1024, 0, lc.stream>>>(in, out, n, scratch);
   if (nb > 1) {
     launch_scan(lc, scratch, scratch + nb, nb, scratch + 2 * nb);
+    ++*lc.launches;
     k_scan_add<<<(unsigned)nb, 1024, 0, lc.stream>>>(out, n, scratch + nb);
   }
 }
@@ -1518,15 +1578,19 @@ bool launch_far_src(int d, const LaunchCommon& lc, const int* plist, int count, 
   return dispatch<FarSrcL>(d, lc, plist, count, dv, Vt, qv, src_off, sigma, src, n_over);
 }
 void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const double* src,
-                    int64_t n_over, const KernelParams& kp, void* out) {
+                    int64_t n_over, const KernelParams& kp, const int32_t* tpatch,
+                    const int64_t* src_off, void* out) {
   const int64_t g = (NT + kThreads - 1) / kThreads;
   if (g <= 0) return;
-  k_far_sum<<<(unsigned)g, kThreads, 0, lc.stream>>>(tgt, NT, src, n_over, kp, (cplx*)out);
+  ++*lc.launches;
+  k_far_sum<<<(unsigned)g, kThreads, 0, lc.stream>>>(tgt, NT, src, n_over, kp, tpatch, src_off,
+                                                     (cplx*)out);
 }
 void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int32_t* col,
                       const double* val, const void* sigma, const int64_t* tnode, int64_t NT,
                       double jump, void* out) {
   const int g = lc.num_sms * 8;
+  ++*lc.launches;
   k_csr_apply<<<g, 256, 0, lc.stream>>>(row_ptr, col, val, (const cplx*)sigma, tnode, NT, jump,
                                         (cplx*)out);
 }

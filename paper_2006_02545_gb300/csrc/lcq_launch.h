@@ -11,6 +11,7 @@ namespace lcq {
 struct LaunchCommon {
   cudaStream_t stream;
   int num_sms;
+  long long* launches;  // incremented once per kernel launch
 };
 
 // Read-only device view of a near-list object plus tables, passed by value to kernels.
@@ -105,7 +106,8 @@ bool launch_far_src(int d, const LaunchCommon& lc, const int* plist, int count, 
                     const double* Vt, const int32_t* qv, const int64_t* src_off, const void* sigma,
                     double* src, int64_t n_over);
 void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const double* src,
-                    int64_t n_over, const KernelParams& kp, void* out);
+                    int64_t n_over, const KernelParams& kp, const int32_t* tpatch,
+                    const int64_t* src_off, void* out);
 void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int32_t* col,
                       const double* val, const void* sigma, const int64_t* tnode, int64_t NT,
                       double jump, void* out);

@@ -67,6 +67,7 @@ _sig = {
     "lcq_corr_destroy": (None, [_vp]),
     "lcq_sync": (C.c_int, [_vp, _i64]),
     "lcq_counters": (C.c_int, [_vp, _vp]),
+    "lcq_stage_times": (C.c_int, [_vp, _vp, _vp]),
     "lcq_status_string": (C.c_char_p, [C.c_int]),
     "lcq_last_error": (C.c_char_p, [_vp]),
 }
@@ -140,6 +141,13 @@ class Context:
         out = np.zeros(4, np.int64)
         self.check(_lib.lcq_counters(self.h, _ptr(out)), "lcq_counters")
         return out
+
+    def stage_times(self):
+        """(ms per stage [near, far order, smooth+annulus, adaptive, self, v2c], launches)."""
+        ms = np.zeros(6, np.float32)
+        nl = C.c_int64()
+        self.check(_lib.lcq_stage_times(self.h, _ptr(ms), C.byref(nl)), "lcq_stage_times")
+        return ms.astype(np.float64), int(nl.value)
 
     def close(self):
         if getattr(self, "h", None):
@@ -215,11 +223,13 @@ class Corrections:
                        "lcq_corr_info")
         return int(nnz.value), int(nover.value)
 
-    def export(self, n_targets: int):
+    def export(self, n_targets: int, out=None):
+        """CSR (row_ptr, col, val) to host; `out` may supply preallocated (pinned) arrays."""
         nnz = self.near.nnz
-        rp = np.empty(n_targets + 1, np.int64)
-        col = np.empty(max(nnz, 1), np.int32)
-        val = np.empty(max(nnz, 1), np.complex128)
+        if out is None:
+            out = (np.empty(n_targets + 1, np.int64), np.empty(max(nnz, 1), np.int32),
+                   np.empty(max(nnz, 1), np.complex128))
+        rp, col, val = out
         self.ctx.check(_lib.lcq_corr_export(self.h, _ptr(rp), _ptr(col), _ptr(val)),
                        "lcq_corr_export")
         return rp, col[:nnz], val[:nnz]

@@ -1,0 +1,228 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on the same seeded
+inputs, plus GPU-side identities and edge cases.
+
+Tolerances (FP64 path): the applied potential within relative L2 1e-10 (the FP64 bar);
+each (target, patch) correction vector within 1e-10 of its own norm plus 1e-12 of the
+largest, plus the change that refinement decisions taken at the rounding floor or within
+1e-3 of the threshold can cause (tests/gpu_helpers.pair_tolerance derives it from the
+oracle's record of those decisions).
+"""
+import numpy as np
+import pytest
+
+from oracle import truth
+from paper_2006_02545_gb300 import workloads as W
+
+from .gpu_helpers import compare_pairs, leaves_by_pair, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+APPLY_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2006_02545_gb300 import lcq
+    c = lcq.Context(0)
+    yield c
+    c.close()
+
+
+def check_full(g, oc, uo, node_off):
+    assert g["status"] == 0 and g["status_apply"] == 0
+    assert np.array_equal(g["row_ptr"], oc.row_ptr)
+    assert np.array_equal(g["col"], oc.col)
+    assert np.array_equal(g["q"], oc.q) and np.array_equal(g["q_near"], oc.q_near)
+    rel = np.linalg.norm(g["u"] - uo) / np.linalg.norm(uo)
+    assert rel <= APPLY_TOL, rel
+    worst, npairs, where = compare_pairs(g, oc, node_off)
+    assert worst <= 1.0, (worst, where)
+    lv = leaves_by_pair(g, oc)
+    same = sum(a == b for a, b, _ in lv)
+    assert same >= 0.98 * len(lv), (same, len(lv))
+    return rel
+
+
+def test_sphere_single_layer_k1(ctx):
+    """Single layer, k=1, 20-patch degree-4 sphere, eps=1e-6, eta=1.25 (every near target
+    adaptive): the whole correction matrix and the applied potential."""
+    wl = W.sphere_s_k1()
+    s = wl.surface
+    g = run_gpu(ctx, s, wl.tgt_xyz, wl.tgt_node, "S", 1.0, 1e-6, 1.25)
+    oc, uo = run_oracle(s, wl.tgt_xyz, wl.tgt_node, "S", 1.0, 1e-6, 1.25, sigma=g["sigma"])
+    check_full(g, oc, uo, s.node_off)
+    assert g["pair_ad"].all()
+
+
+def test_flat_polyhedron_gauss_identity(ctx):
+    """D_0[1] = -1/2 at every node of a closed flat polyhedron, on the GPU, and parity."""
+    s = W.ellipsoid(1, 3, flat=True)
+    x, tn = W.onsurface_targets(s)
+    g = run_gpu(ctx, s, x, tn, "D", 0.0, 1e-7)
+    import torch
+    from paper_2006_02545_gb300 import lcq
+    one = torch.ones(s.n_points, dtype=torch.complex128, device=ctx.torch_device)
+    u1 = lcq.apply_corrected_D(ctx, g["ds"], g["near"], g["corr"], one, x.shape[1]).cpu().numpy()
+    assert np.abs(u1 + 0.5).max() < 2e-7
+    u2 = lcq.apply_corrected_D(ctx, g["ds"], g["near"], g["corr"], one, x.shape[1],
+                               jump=0.5).cpu().numpy()
+    assert np.abs(u2).max() < 2e-7          # exterior limit D + 1/2 of sigma = 1 is 0
+    oc, uo = run_oracle(s, x, tn, "D", 0.0, 1e-7, sigma=g["sigma"])
+    check_full(g, oc, uo, s.node_off)
+
+
+def merged_surface():
+    a = W.ellipsoid(1, 2, axes=(1.0, 1.0, 1.0))
+    b = W.ellipsoid(1, 5, axes=(0.7, 0.9, 1.1))
+    xyz_b = b.xyz + np.array([[2.6], [0.3], [0.0]])
+    deg = np.concatenate([a.deg, b.deg])
+    off = np.concatenate([a.node_off, a.node_off[-1] + b.node_off[1:]])
+    return W.Surface("two_bodies_d2_d5", deg, off, np.ascontiguousarray(np.concatenate(
+        [a.xyz, xyz_b], axis=1)))
+
+
+def test_mixed_degrees_cfie(ctx):
+    """Two bodies with degree-2 and degree-5 patches in one surface, CFIE, k = 3."""
+    s = merged_surface()
+    x, tn = W.onsurface_targets(s)
+    k = 3.0
+    g = run_gpu(ctx, s, x, tn, "CFIE", k, 1e-7, alpha=1.0, beta=-1j * k)
+    oc, uo = run_oracle(s, x, tn, "CFIE", k, 1e-7, alpha=1.0, beta=-1j * k, sigma=g["sigma"])
+    check_full(g, oc, uo, s.node_off)
+
+
+def test_offsurface_targets_double_layer(ctx):
+    """Off-surface targets near and far (inside and outside), D with complex k."""
+    s = W.ellipsoid(1, 4, axes=(1.0, 1.3, 0.8))
+    x = np.concatenate([W.radial_targets(s, 40, 1, 0.005, 0.2, True),
+                        W.radial_targets(s, 40, 2, 0.005, 0.2, False),
+                        W.radial_targets(s, 10, 3, 1.0, 2.0, True)], axis=1)
+    tn = -np.ones(x.shape[1], np.int64)
+    k = 2.0 + 0.3j
+    g = run_gpu(ctx, s, x, tn, "D", k, 1e-8)
+    oc, uo = run_oracle(s, x, tn, "D", k, 1e-8, sigma=g["sigma"])
+    check_full(g, oc, uo, s.node_off)
+    assert g["pair_ad"].any() and (~g["pair_ad"]).any()
+
+
+def test_ellipsoid_cfie_full_size_sampled(ctx):
+    """The benchmark workload at full size (1280 degree-6 patches, CFIE, k = 2 pi,
+    eps = 1e-9) on the GPU; the oracle recomputes a sample of patches one by one."""
+    wl = W.ellipsoid_cfie_k2pi(8)
+    s = wl.surface
+    g = run_gpu(ctx, s, wl.tgt_xyz, wl.tgt_node, "CFIE", wl.k, wl.eps, wl.eta, wl.alpha, wl.beta,
+                dirs_seed=7)
+    assert g["status"] == 0
+    sample = [0, 517, 1279]
+    oc, _ = run_oracle(s, wl.tgt_xyz, wl.tgt_node, "CFIE", wl.k, wl.eps, wl.eta, wl.alpha,
+                       wl.beta, dirs_seed=7, only_patches=sample, apply=False)
+    for j in sample:
+        assert g["q"][j] == oc.q[j] and g["q_near"][j] == oc.q_near[j]
+        seg = g["pair_tgt"][g["pair_ptr"][j]:g["pair_ptr"][j + 1]]
+        assert np.array_equal(seg, oc.near[j][0])
+        assert np.array_equal(g["pair_ad"][g["pair_ptr"][j]:g["pair_ptr"][j + 1]], oc.near[j][1])
+    worst, npairs, where = compare_pairs(g, oc, s.node_off)
+    assert npairs > 1000 and worst <= 1.0, (worst, where)
+    lv = leaves_by_pair(g, oc)
+    assert sum(a == b for a, b, _ in lv) >= 0.98 * len(lv)
+
+
+def test_torus_sampled_parity(ctx):
+    """Perturbed torus (degree 3, 2 x 8 x 16 patches, S, k = 7), sampled patches."""
+    s = W.torus(8, 16, 3)
+    x, tn = W.onsurface_targets(s)
+    g = run_gpu(ctx, s, x, tn, "S", 7.0, 1e-6)
+    sample = [0, 77, 200]
+    oc, _ = run_oracle(s, x, tn, "S", 7.0, 1e-6, only_patches=sample, apply=False)
+    worst, npairs, where = compare_pairs(g, oc, s.node_off)
+    assert worst <= 1.0 and npairs > 100, (worst, where)
+    for j in sample:
+        assert g["q"][j] == oc.q[j]
+
+
+def test_leaf_order_and_depth_cap(ctx):
+    """An explicit leaf rule and a shallow depth cap: status is reported, results still
+    match the oracle run with the same parameters."""
+    wl = W.sphere_s_k1()
+    s = wl.surface
+    g = run_gpu(ctx, s, wl.tgt_xyz, wl.tgt_node, "S", 1.0, 1e-6, 1.25, leaf_order=5, max_depth=2)
+    assert g["status"] == 4   # LCQ_ERR_MAX_DEPTH
+    oc, uo = run_oracle(s, wl.tgt_xyz, wl.tgt_node, "S", 1.0, 1e-6, 1.25, sigma=g["sigma"],
+                        leaf_order=5, max_depth=2)
+    assert oc.depth_hit
+    g["status"] = 0
+    check_full(g, oc, uo, s.node_off)
+
+
+def test_deterministic(ctx):
+    wl = W.sphere_s_k1()
+    s = wl.surface
+    a = run_gpu(ctx, s, wl.tgt_xyz, wl.tgt_node, "S", 1.0, 1e-6, 1.25)
+    b = run_gpu(ctx, s, wl.tgt_xyz, wl.tgt_node, "S", 1.0, 1e-6, 1.25)
+    assert np.array_equal(a["val"], b["val"]) and np.array_equal(a["u"], b["u"])
+
+
+def test_sphere_eigenvalue_gpu(ctx):
+    """S_k Y_0 = i k j_0(k) h_0(k) on a finer sphere, from the GPU alone."""
+    s = W.ellipsoid(4, 6)
+    x, tn = W.onsurface_targets(s)
+    import torch
+    from paper_2006_02545_gb300 import lcq
+    g = run_gpu(ctx, s, x, tn, "S", 1.0, 1e-9)
+    one = torch.ones(s.n_points, dtype=torch.complex128, device=ctx.torch_device)
+    u = lcq.apply_corrected_S(ctx, g["ds"], g["near"], g["corr"], one, x.shape[1]).cpu().numpy()
+    lam = truth.sphere_eigen_S(0, 1.0)
+    assert np.abs(u - lam).max() / abs(lam) < 1e-6
+
+
+def test_edge_cases(ctx):
+    import torch
+    from paper_2006_02545_gb300 import lcq
+    dev = ctx.torch_device
+    s = W.ellipsoid(1, 2)
+    ds = lcq.DeviceSurface(s.deg, s.node_off, torch.from_numpy(s.xyz).to(dev))
+    prm = lcq.params(1e-6)
+    # no targets
+    e3 = torch.zeros((3, 0), dtype=torch.float64, device=dev)
+    en = torch.zeros(0, dtype=torch.int64, device=dev)
+    near = lcq.build_near_lists(ctx, ds, e3, en, prm)
+    assert near.n_pairs == 0 and near.nnz == 0
+    corr = lcq.gen_corrections(ctx, ds, near, "S", 1.0, prm)
+    assert ctx.sync(60000) == 0
+    corr.close()
+    near.close()
+    # one patch, one far target, one on-surface node
+    one = W.Surface("one", s.deg[:1], s.node_off[:2], np.ascontiguousarray(s.xyz[:, :6]))
+    ds1 = lcq.DeviceSurface(one.deg, one.node_off, torch.from_numpy(one.xyz).to(dev))
+    tx = torch.tensor([[5.0, one.xyz[0, 2]], [0.0, one.xyz[1, 2]], [0.0, one.xyz[2, 2]]],
+                      dtype=torch.float64, device=dev)
+    tnd = torch.tensor([-1, 2], dtype=torch.int64, device=dev)
+    near = lcq.build_near_lists(ctx, ds1, tx, tnd, prm)
+    assert near.n_pairs == 0 and near.n_self == 1 and near.nnz == 6
+    corr = lcq.gen_corrections(ctx, ds1, near, "CFIE", 2.0, prm, 1.0, -2j)
+    assert ctx.sync(60000) == 0
+    rp, col, val = corr.export(2)
+    assert list(rp) == [0, 0, 6] and np.isfinite(val).all()
+    corr.close()
+    near.close()
+    # non-finite coordinates are reported, not computed on
+    bad = s.xyz.copy()
+    bad[1, 3] = np.nan
+    dsb = lcq.DeviceSurface(s.deg, s.node_off, torch.from_numpy(bad).to(dev))
+    x, tn = W.onsurface_targets(s)
+    with pytest.raises(lcq.LCQError) as ei:
+        lcq.build_near_lists(ctx, dsb, torch.from_numpy(x).to(dev), torch.from_numpy(tn).to(dev),
+                             prm)
+    assert ei.value.status == 2
+    # invalid arguments
+    near = lcq.build_near_lists(ctx, ds, torch.from_numpy(x).to(dev), torch.from_numpy(tn).to(dev),
+                                prm)
+    with pytest.raises(lcq.LCQError) as ei:
+        lcq.gen_corrections(ctx, ds, near, "S", 1.0 - 0.5j, prm)
+    assert ei.value.status == 1
+    with pytest.raises(lcq.LCQError):
+        lcq.gen_corrections(ctx, ds, near, "S", 1.0, lcq.params(1e-6, m_max=40))
+    near.close()
+    assert ctx.sync(60000) == 0
