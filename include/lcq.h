@@ -191,6 +191,39 @@ lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out4);
  * *launches receives the number of kernels those two calls launched.  Synchronizes. */
 lcq_status lcq_stage_times(lcq_ctx* ctx, float* ms6, int64_t* launches);
 
+/* Allocation-free variant for callers that cannot allocate device memory: code that
+ * runs where cudaMalloc is unavailable or forbidden (inside a host callback or a
+ * real-time loop that must not touch the allocator, or under a memory manager that owns
+ * every byte of the device).  The paper has no counterpart; this is a library facility.
+ *
+ * Computes the adaptive near corrections of ONE patch for targets that are all treated
+ * as adaptive (Sec. 4.3), exactly as lcq_gen_corrections computes them for adaptive
+ * near pairs: out[t][l] = sum_nm V[nm][l] (I^adaptive_nm(x_t) - I^{rule q}_nm(x_t)).
+ *   deg       patch degree, 1..8
+ *   y         device double SoA [3][n] node coordinates, n = (deg+1)(deg+2)/2
+ *   n_targets 1..128; tgt_xyz device double SoA [3][n_targets] (off-surface points)
+ *   kernel, k, alpha, beta as for lcq_gen_corrections
+ *   q         leaf / smooth rule order (the patch's far order q_j), 1..32
+ *   eps       adaptive tolerance; max_depth 1..16
+ *   out       device complex128 [n_targets][n] (interleaved re, im), caller-owned
+ * All device storage (tables, geometry, moments, the union-tree workspace) lives in one
+ * static 8 MiB device array that every GPU loading liblcq holds until process exit; no
+ * call allocates or frees device memory.  The first call on a device, with that device
+ * current, looks up the array's device address and uploads constant tables; make that
+ * first call before any stream capture.  Calls share the array and keep the previous
+ * call's contents (each call rewrites what it reads): calls that overlap on the GPU --
+ * on different streams or from different threads -- race and must be serialized by the
+ * caller.  The call queues its work on cuda_stream (NULL: legacy default stream) and
+ * synchronizes that stream before returning.  Returns LCQ_ERR_CAPACITY when deg,
+ * n_targets or max_depth exceed the limits above, LCQ_ERR_MAX_DEPTH (result kept) or
+ * LCQ_ERR_NONFINITE as lcq_gen_corrections does. */
+lcq_status lcq_adaptive_corrections_noalloc(int deg, const double* y, int64_t n_targets,
+                                            const double* tgt_xyz, lcq_kernel kernel,
+                                            double k_re, double k_im, double alpha_re,
+                                            double alpha_im, double beta_re, double beta_im,
+                                            int q, double eps, int max_depth, void* cuda_stream,
+                                            double* out);
+
 const char* lcq_status_string(lcq_status s);
 const char* lcq_last_error(const lcq_ctx* ctx);
 

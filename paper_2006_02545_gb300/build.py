@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblcq.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lcq_kernels.cu", "lcq_api.cpp", "lcq_tables.cpp"]
+SOURCES = ["lcq_kernels.cu", "lcq_api.cpp", "lcq_tables.cpp", "lcq_noalloc.cu"]
 
 
 def _nvcc() -> str:

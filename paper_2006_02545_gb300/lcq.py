@@ -68,6 +68,8 @@ _sig = {
     "lcq_sync": (C.c_int, [_vp, _i64]),
     "lcq_counters": (C.c_int, [_vp, _vp]),
     "lcq_stage_times": (C.c_int, [_vp, _vp, _vp]),
+    "lcq_adaptive_corrections_noalloc": (C.c_int, [C.c_int, _vp, _i64, _vp, C.c_int, _d, _d, _d,
+                                                   _d, _d, _d, C.c_int, _d, C.c_int, _vp, _vp]),
     "lcq_status_string": (C.c_char_p, [C.c_int]),
     "lcq_last_error": (C.c_char_p, [_vp]),
 }
@@ -288,3 +290,17 @@ def apply_corrected_D(ctx, surf, near, corr, sigma, n_targets, jump=0.0):
 def apply_corrected_CFIE(ctx, surf, near, corr, sigma, n_targets, jump=0.0):
     return _apply(_lib.lcq_apply_corrected_CFIE, ctx, surf, near, corr, sigma, jump,
                   _out_like(ctx, n_targets))
+
+
+def adaptive_corrections_noalloc(deg, y_dev, tgt_dev, kernel, k, q, eps, out, alpha=1.0, beta=0.0,
+                                 max_depth=16, stream=None):
+    """lcq_adaptive_corrections_noalloc: one patch's adaptive near corrections into the
+    caller's `out` (device complex128 [n_targets][n]); the library allocates nothing."""
+    import torch
+    k, alpha, beta = complex(k), complex(alpha), complex(beta)
+    if stream is None:
+        stream = torch.cuda.current_stream(y_dev.device)
+    return _lib.lcq_adaptive_corrections_noalloc(
+        deg, _ptr(y_dev), int(tgt_dev.shape[1]), _ptr(tgt_dev), KERNELS[kernel], k.real, k.imag,
+        alpha.real, alpha.imag, beta.real, beta.imag, int(q), float(eps), int(max_depth),
+        C.c_void_p(stream.cuda_stream), _ptr(out))
