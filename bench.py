@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--s", type=int, default=8, help="icosahedral refinement (1280 patches at 8)")
+    ap.add_argument("--leaf-order", type=int, default=0,
+                    help="smooth rule used on subtriangles (0: the patch's far order q_j)")
+    ap.add_argument("--eps", type=float, default=1e-9)
     return ap.parse_args()
 
 
@@ -64,28 +67,28 @@ def parse():
 def _oracle_worker(job):
     """Oracle corrections for some patches of the workload (runs in a spawned process)."""
     import numpy as np  # noqa: F401
-    s_div, patches, dirs_seed = job
+    s_div, patches, dirs_seed, eps, leaf = job
     from oracle import corrections as C
     from oracle import geometry
     from paper_2006_02545_gb300 import workloads as W
     wl = W.ellipsoid_cfie_k2pi(s_div)
     surf = wl.surface
     pts = geometry.make_patches(surf.deg, surf.node_off, surf.xyz)
-    p = C.Params(eps=wl.eps, eta=wl.eta, test_dirs=W.test_directions(dirs_seed))
+    p = C.Params(eps=eps, eta=wl.eta, test_dirs=W.test_directions(dirs_seed), leaf_order=leaf)
     t0 = time.perf_counter()
     C.gen_corrections(surf.deg, surf.node_off, surf.xyz, wl.tgt_xyz, wl.tgt_node, wl.kernel, wl.k,
                       wl.alpha, wl.beta, params=p, patches=pts, only_patches=patches)
     return len(patches), time.perf_counter() - t0
 
 
-def oracle_sample(s_div, n_patches_total, workers, per_worker, seed, pool):
+def oracle_sample(s_div, n_patches_total, workers, per_worker, seed, pool, eps=1e-9, leaf=0):
     """Time the oracle on workers*per_worker patches spread over the surface.
     Throughput = points of the sampled patches / the slowest worker's compute time."""
     n = 28
     total = workers * per_worker
     stride = max(1, n_patches_total // total)
     picks = [(i * stride + seed) % n_patches_total for i in range(total)]
-    jobs = [(s_div, picks[w::workers], 7) for w in range(workers)]
+    jobs = [(s_div, picks[w::workers], 7, eps, leaf) for w in range(workers)]
     res = pool.map(_oracle_worker, jobs)
     done = sum(r[0] for r in res)
     worst = max(r[1] for r in res)
@@ -108,7 +111,8 @@ def run_reference(args, rank):
     vals, times = [], []
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        v, done, worst = oracle_sample(args.s, npat, workers, 1, it * 37, pool)
+        v, done, worst = oracle_sample(args.s, npat, workers, 1, it * 37, pool, args.eps,
+                                       args.leaf_order)
         if it >= args.warmup:
             vals.append(v)
             times.append(time.perf_counter() - t0)
@@ -212,7 +216,8 @@ def run_ours(args, rank, world, local_rank):
     tx_d = torch.from_numpy(np.ascontiguousarray(wl.tgt_xyz)).to(dev)
     tn_d = torch.from_numpy(wl.tgt_node).to(dev)
     ds = lcq.DeviceSurface(surf.deg, surf.node_off, xyz_d)
-    prm = lcq.params(wl.eps, eta=wl.eta, test_dirs=W.test_directions(7))
+    prm = lcq.params(args.eps, eta=wl.eta, test_dirs=W.test_directions(7),
+                     leaf_order=args.leaf_order)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -230,6 +235,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     clocks = ClockSampler(local_rank) if rank == 0 else None
     step_ms, adapt_ms, stages, statuses, launches, nodes = [], [], [], [], 0, 0
+    tree_nodes = tests = 0
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
@@ -248,6 +254,8 @@ def run_ours(args, rank, world, local_rank):
         launches += nl
         cnt = ctx.counters()
         nodes = int(cnt[1])
+        tree_nodes = int(cnt[4])
+        tests = int(cnt[0])
         corr.close()
         near.close()
     torch.cuda.synchronize()
@@ -315,12 +323,13 @@ def run_ours(args, rank, world, local_rank):
                 "traffic": traffic_for("k_adaptive"),
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
                 "flops_per_launch": flops, "node_evals_per_launch": nodes,
+                "tests_per_launch": tests, "union_tree_nodes_per_launch": tree_nodes,
                 "avg_launch_ms": a_ms}
     cpu = None
     if not args.no_cpu_baseline:
         workers = max(1, min(16, os.cpu_count() or 1))
         pool = make_pool(workers)
-        v, done, worst = oracle_sample(args.s, P, workers, 1, 0, pool)
+        v, done, worst = oracle_sample(args.s, P, workers, 1, 0, pool, args.eps, args.leaf_order)
         pool.close()
         cpu = {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
                "sample": f"{done} of {P} patches (1 per worker, spread over the surface); "
@@ -331,8 +340,8 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "patches": P, "order": 6, "points": N,
-                   "near_pairs": None, "l2": "256 MiB buffer written between steps (outside the "
-                                             "timed events)"},
+                   "eps": args.eps, "leaf_order": args.leaf_order or "q_j",
+                   "l2": "256 MiB buffer written between steps (outside the timed events)"},
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
         "clocks": clk, "status": max(statuses) if statuses else None,
         "stages_ms": dict(zip(["near_lists", "far_order", "smooth_annulus", "adaptive", "self",

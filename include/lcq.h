@@ -178,10 +178,12 @@ void lcq_corr_destroy(lcq_corr* corr);
  * without limit), then return and clear the latched device status. */
 lcq_status lcq_sync(lcq_ctx* ctx, int64_t timeout_ms);
 
-/* Device-side work counters of the last lcq_gen_corrections on ctx (host out):
- * [0] adaptive tests, [1] adaptive leaf-rule node evaluations, [2] self node
- * evaluations, [3] smooth/annulus node evaluations (per target).  Synchronizes. */
-lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out4);
+/* Device-side work counters of the last lcq_gen_corrections on ctx (host out8[8]):
+ * [0] adaptive tests, [1] adaptive leaf-rule node evaluations (target x node),
+ * [2] self node evaluations, [3] smooth/annulus node evaluations (target x node),
+ * [4] union-tree nodes walked by the adaptive kernel (each evaluates the chart geometry
+ * at 4Q leaf nodes), [5..7] zero.  Synchronizes. */
+lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out8);
 
 /* Stage timings of the last lcq_build_near_lists and lcq_gen_corrections on ctx, from
  * CUDA events recorded on the context's stream (host out, milliseconds):

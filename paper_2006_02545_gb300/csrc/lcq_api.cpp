@@ -165,9 +165,10 @@ lcq_status lcq_create(lcq_ctx** out, int device, void* cuda_stream) {
   CK(cudaSetDevice(device));
   CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
   CK(cudaMalloc(&ctx->d_status, sizeof(int)));
-  CK(cudaMalloc(&ctx->d_counters, 4 * sizeof(long long)));
+  CK(cudaMalloc(&ctx->d_counters, 8 * sizeof(long long)));
+  CK(cudaMalloc(&ctx->d_sched, 16 * sizeof(int)));
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
-  CK(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(long long), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(long long), ctx->stream));
   CK(upload_constants(ctx->stream));
   for (int i = 0; i < 8; ++i) CK(cudaEventCreate(&ctx->ev[i]));
   lcq_status s = ensure_rules(ctx);
@@ -201,6 +202,7 @@ void lcq_destroy(lcq_ctx* ctx) {
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_counters);
+  cudaFree(ctx->d_sched);
   cudaGetLastError();
   delete ctx;
 }
@@ -242,13 +244,13 @@ lcq_status lcq_stage_times(lcq_ctx* ctx, float* ms6, int64_t* launches) {
   return LCQ_OK;
 }
 
-lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out4) {
-  if (!ctx || !out4) return LCQ_ERR_ARG;
+lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out8) {
+  if (!ctx || !out8) return LCQ_ERR_ARG;
   cudaSetDevice(ctx->device);
   CK(cudaStreamSynchronize(ctx->stream));
-  long long h[4];
+  long long h[8];
   CK(cudaMemcpy(h, ctx->d_counters, sizeof(h), cudaMemcpyDeviceToHost));
-  for (int i = 0; i < 4; ++i) out4[i] = h[i];
+  for (int i = 0; i < 8; ++i) out8[i] = h[i];
   return LCQ_OK;
 }
 
@@ -394,6 +396,20 @@ lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const dou
     acc_n += h_np[j] - h_nad[j];
   }
   an_h[P] = acc_n;
+  // patches with adaptive targets, per degree, most adaptive targets first (the adaptive
+  // kernel takes them in this order from a shared counter: longest jobs first)
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    std::vector<int> l;
+    for (int j : lists[d])
+      if (h_nad[j] > 0) l.push_back(j);
+    std::stable_sort(l.begin(), l.end(), [&](int a, int b) { return h_nad[a] > h_nad[b]; });
+    nr->ad_count[d] = (int)l.size();
+    if (!l.empty()) {
+      CK(dalloc(st, &nr->ad_list_dev[d], l.size()));
+      CK(cudaMemcpyAsync(nr->ad_list_dev[d], l.data(), l.size() * sizeof(int),
+                         cudaMemcpyHostToDevice, st));
+    }
+  }
   nr->n_pairs = acc_p;
   nr->n_adaptive = acc_a;
   nr->n_self = acc_s;
@@ -463,7 +479,10 @@ void lcq_near_destroy(lcq_near* nr) {
   if (!nr) return;
   cudaSetDevice(nr->device);
   cudaStream_t st = nr->stream;
-  for (int d = 0; d <= kMaxDeg; ++d) dfree(st, nr->plist_dev[d]);
+  for (int d = 0; d <= kMaxDeg; ++d) {
+    dfree(st, nr->plist_dev[d]);
+    dfree(st, nr->ad_list_dev[d]);
+  }
   dfree(st, nr->deg);
   dfree(st, nr->node_off);
   dfree(st, nr->coef);
@@ -559,8 +578,8 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
   ctx->launches_corr = 0;
   LaunchCommon lc{st, ctx->num_sms, &ctx->launches_corr};
   const int64_t P = nr->n_patches;
-  KernelParams kp{(int)kernel, k_re, k_im, alpha_re, alpha_im, beta_re, beta_im};
-  if (kernel == LCQ_S) kp.ar = kp.ai = kp.br = kp.bi = 0.0;
+  const KernelParams kp =
+      make_kernel_params((int)kernel, k_re, k_im, alpha_re, alpha_im, beta_re, beta_im);
 
   lcq_corr* c = new lcq_corr();
   c->near = nr;
@@ -579,7 +598,7 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
   CK(dalloc(st, &c->leaves, nr->n_pairs));
   CK(cudaMemsetAsync(c->leaves, 0, std::max<int64_t>(nr->n_pairs, 1) * 4, st));
   CK(cudaMemsetAsync(c->val, 0, std::max<int64_t>(nr->nnz, 1) * 16, st));
-  CK(cudaMemsetAsync(ctx->d_counters, 0, 4 * sizeof(long long), st));
+  CK(cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(long long), st));
 
   // test directions
   std::vector<double> dirs;
@@ -638,7 +657,10 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
                      (int64_t)levels * A * 4 + 2 * A * 4 + (int64_t)levels * 4 + 8 + A * 4 * 8 +
                      256;
     stride = (stride + 255) / 256 * 256;
-    const int agrid = ctx->num_sms;
+    int bps = 1;
+    for (int d = 1; d <= kMaxDeg; ++d)
+      if (nr->ad_count[d]) bps = std::max(bps, adaptive_blocks_per_sm(d));
+    const int agrid = ctx->num_sms * bps;
     const size_t need = (size_t)stride * agrid;
     if (ctx->work_bytes < need) {
       if (ctx->work) CK(cudaFreeAsync(ctx->work, st));
@@ -648,11 +670,11 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
       ctx->work_bytes = need;
     }
     for (int d = 1; d <= kMaxDeg; ++d) {
-      if (!nr->plist_count[d]) continue;
-      launch_adaptive(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, kp,
+      if (!nr->ad_count[d]) continue;
+      launch_adaptive(d, lc, nr->ad_list_dev[d], nr->ad_count[d], dv, kp,
                       params->eps * params->eps_loosen, ctx->deg[d].normV, params->leaf_order,
                       params->max_depth, Is, In, c->leaves, ctx->work, stride, (int)A, levels, agrid,
-                      ctx->d_status);
+                      ctx->d_status, ctx->d_sched + d);
     }
     CK(cudaGetLastError());
   }

@@ -217,19 +217,34 @@ __device__ __forceinline__ void kw_delta_geometry(double pu, double pv, double d
 //   S: G_k(x, X) Jw
 //   D: Nw.(x - X) (1 - ik r) e^{ikr} / (4 pi r^3)
 //   CFIE: alpha D + beta S.   r = 0 contributes 0.
+// With env != nullptr also the rounding envelope from the same r,
+//   |G| Jw (|beta| + |alpha| |1 - ik r| R / r^2)   (kp.eb = |beta|, kp.ea = |alpha|),
+// the size of the kernel value's rounding noise when positions carry errors of order u R
+// (positions are relative to the patch centroid): the adaptive test never asks for less
+// than a fixed multiple of its sum.
 __device__ __forceinline__ cplx kernel_eval(const KernelParams& kp, double x0, double x1, double x2,
                                             double X0, double X1, double X2, double N0, double N1,
-                                            double N2, double Jw) {
+                                            double N2, double Jw, double R = 0.0,
+                                            double* env = nullptr) {
   const double d0 = x0 - X0, d1 = x1 - X1, d2 = x2 - X2;
   const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-  if (r2 == 0.0) return {0.0, 0.0};
-  const double r = sqrt(r2);
-  const double rinv = 1.0 / r;
+  if (r2 == 0.0) {
+    if (env) *env = 0.0;
+    return {0.0, 0.0};
+  }
+  const double rinv = rsqrt(r2);
+  const double r = r2 * rinv;
   double sn, cs;
   sincos(kp.kr * r, &sn, &cs);
   double ex = 0.07957747154594767 * rinv;  // 1/(4 pi r)
   if (kp.ki != 0.0) ex *= exp(-kp.ki * r);
   const cplx G = {ex * cs, ex * sn};
+  if (env) {
+    // |G| Jw (|beta| + |alpha| |1 - ik r| R / r^2); |1 - ik r| only scales a floor, FP32 is ample
+    const float f0 = (float)(1.0 + kp.ki * r), f1 = (float)(kp.kr * r);
+    const double fa = (double)sqrtf(f0 * f0 + f1 * f1);
+    *env = ex * Jw * (kp.eb + kp.ea * fa * R * rinv * rinv);
+  }
   cplx out = {0.0, 0.0};
   if (kp.kind != 1) {  // S part
     const cplx s = {G.re * Jw, G.im * Jw};
@@ -247,32 +262,6 @@ __device__ __forceinline__ cplx kernel_eval(const KernelParams& kp, double x0, d
   out.re += ad.re;
   out.im += ad.im;
   return out;
-}
-
-// Rounding envelope of kernel_eval (same arguments, plus the patch radius R):
-//   |G| Jw (b + a |1 - ik r| R / r^2), b = 1, 0, |beta|, a = 0, 1, |alpha| for S, D, CFIE.
-// It bounds the size of the rounding noise of the kernel value when positions carry
-// errors of order u R (positions are relative to the patch centroid); the adaptive
-// test never asks for less than a fixed multiple of its sum.
-__device__ __forceinline__ double kernel_envelope(const KernelParams& kp, double x0, double x1,
-                                                  double x2, double X0, double X1, double X2,
-                                                  double Jw, double R) {
-  const double d0 = x0 - X0, d1 = x1 - X1, d2 = x2 - X2;
-  const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-  if (r2 == 0.0) return 0.0;
-  const double r = sqrt(r2);
-  double g = 0.07957747154594767 / r * Jw;
-  if (kp.ki != 0.0) g *= exp(-kp.ki * r);
-  double b, a;
-  if (kp.kind == 0) { b = 1.0; a = 0.0; }
-  else if (kp.kind == 1) { b = 0.0; a = 1.0; }
-  else { b = sqrt(kp.br * kp.br + kp.bi * kp.bi); a = sqrt(kp.ar * kp.ar + kp.ai * kp.ai); }
-  double e = b;
-  if (a != 0.0) {
-    const double f0 = 1.0 + kp.ki * r, f1 = kp.kr * r;
-    e += a * sqrt(f0 * f0 + f1 * f1) * R / r2;
-  }
-  return g * e;
 }
 
 // Cross product helper.

@@ -33,7 +33,23 @@ struct KernelParams {
   double kr, ki;     // k = kr + i ki
   double ar, ai;     // alpha
   double br, bi;     // beta
+  double eb, ea;     // rounding-envelope weights: |beta| and |alpha| (1,0 for S; 0,1 for D)
 };
+
+inline KernelParams make_kernel_params(int kind, double kr, double ki, double ar, double ai,
+                                       double br, double bi) {
+  KernelParams kp{kind, kr, ki, ar, ai, br, bi, 0.0, 0.0};
+  if (kind == 0) {
+    kp.ar = kp.ai = kp.br = kp.bi = 0.0;
+    kp.eb = 1.0;
+  } else if (kind == 1) {
+    kp.ea = 1.0;
+  } else {
+    kp.eb = __builtin_sqrt(br * br + bi * bi);
+    kp.ea = __builtin_sqrt(ar * ar + ai * ai);
+  }
+  return kp;
+}
 
 // Per-degree reference tables uploaded to the device (built on the host).
 struct DegTables {
@@ -73,7 +89,8 @@ struct lcq_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   int* d_status = nullptr;
-  long long* d_counters = nullptr;   // [4]
+  long long* d_counters = nullptr;   // [8]
+  int* d_sched = nullptr;            // dynamic-scheduling counters, one per degree
   int num_sms = 0;
   lcq::DegTables deg[lcq::kMaxDeg + 1];
   lcq::RuleTables rules;
@@ -129,6 +146,8 @@ struct lcq_near {
   int n_max = 0;                              // largest n over the degrees present
   int plist_count[lcq::kMaxDeg + 1] = {0};    // patches of each degree
   int* plist_dev[lcq::kMaxDeg + 1] = {nullptr};
+  int ad_count[lcq::kMaxDeg + 1] = {0};       // patches with adaptive targets, by degree,
+  int* ad_list_dev[lcq::kMaxDeg + 1] = {nullptr};  // most adaptive targets first
 };
 
 struct lcq_corr {

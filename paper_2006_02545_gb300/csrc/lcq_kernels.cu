@@ -414,7 +414,7 @@ template <int D>
 struct Cfg {
   static constexpr int n = (D + 1) * (D + 2) / 2;
   static constexpr int NP = n <= 32 ? 32 : (n <= 64 ? 64 : 96);
-  static constexpr int CH = D <= 6 ? 256 : 128;
+  static constexpr int CH = 128;  // nodes per chunk (two blocks per SM fit in shared memory)
   static constexpr int BS = n + 1;
   static constexpr int TT = 16;
   // doubles of shared workspace used by block_moments
@@ -483,13 +483,10 @@ __device__ void block_moments(const double* cf, const double* __restrict__ ru,
         const int i = e / C::CH, ql = e - i * C::CH;
         cplx g = {0.0, 0.0};
         double ev = 0.0;
-        if (ql < nch) {
+        if (ql < nch)
           g = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql], Xs[C::CH + ql],
-                          Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql], Js[ql]);
-          if (ENV)
-            ev = kernel_envelope(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql],
-                                 Xs[C::CH + ql], Xs[2 * C::CH + ql], Js[ql], R);
-        }
+                          Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql], Js[ql],
+                          R, ENV ? &ev : nullptr);
         G[i * C::CH + ql] = g;
         if (ENV) Ev[i * C::CH + ql] = ev;
       }
@@ -587,7 +584,7 @@ __device__ __forceinline__ SegMap seg_T0() { return {0.0, 0.0, 1.0, 0.0, 0.0, 1.
 // Smooth rule q_j moments for every near pair and self target of the patch (Sec. 4.2):
 // I_smooth; and annulus-rule moments for annulus pairs (Remark on eta_1).
 template <int D>
-__global__ void __launch_bounds__(kThreads) k_rule_moments(
+__global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
     const int* __restrict__ plist, int count, Dev dv, int mode, const int32_t* __restrict__ qv,
     const KernelParams kp, cplx* __restrict__ out_pairs, cplx* __restrict__ out_self) {
   using C = Cfg<D>;
@@ -812,15 +809,18 @@ struct AdaptiveWS {
   int A_max, levels;
 };
 
+// Patches are taken dynamically from `plist` (ordered by decreasing number of adaptive
+// targets) through the counter *sched, which the caller zeroes before the launch.
 template <int D>
-__global__ void __launch_bounds__(kThreads) k_adaptive(const int* __restrict__ plist, int count,
+__global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict__ plist, int count,
                                                        Dev dv, const KernelParams kp, double eps,
                                                        double normV, int leaf_order, int max_depth,
                                                        const cplx* __restrict__ I_smooth,
                                                        cplx* __restrict__ I_near,
                                                        int32_t* __restrict__ leaves_out,
                                                        unsigned char* __restrict__ work,
-                                                       AdaptiveWS wsd, int* __restrict__ status) {
+                                                       AdaptiveWS wsd, int* __restrict__ status,
+                                                       int* __restrict__ sched) {
   using C = Cfg<D>;
   constexpr int n = C::n;
   extern __shared__ double smem[];
@@ -841,9 +841,15 @@ __global__ void __launch_bounds__(kThreads) k_adaptive(const int* __restrict__ p
   int* cnt = lcnt + A_max;                                          // [levels]
   double* tmpE = reinterpret_cast<double*>(                          // [A_max][4], 8-aligned
       (reinterpret_cast<uintptr_t>(cnt + wsd.levels) + 7) & ~static_cast<uintptr_t>(7));
-  long long my_tests = 0, my_nodes = 0;
+  long long my_tests = 0, my_nodes = 0, my_tree = 0;
+  __shared__ int next_b;
 
-  for (int b = blockIdx.x; b < count; b += gridDim.x) {
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) next_b = atomicAdd(sched, 1);
+    __syncthreads();
+    const int b = next_b;
+    if (b >= count) break;
     const int j = plist[b];
     const int64_t a0 = dv.ad_ptr[j];
     const int A = (int)(dv.ad_ptr[j + 1] - a0);
@@ -943,6 +949,7 @@ __global__ void __launch_bounds__(kThreads) k_adaptive(const int* __restrict__ p
       __syncthreads();
       my_tests += S;
       my_nodes += (long long)S * 4 * Q;
+      my_tree += 1;
       // decisions: one warp per target
       const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
       const double tauL = tol0 * ldexp(1.0, -2 * L);
@@ -1029,6 +1036,7 @@ __global__ void __launch_bounds__(kThreads) k_adaptive(const int* __restrict__ p
   if (threadIdx.x == 0) {
     atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 0), (unsigned long long)my_tests);
     atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 1), (unsigned long long)my_nodes);
+    atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 4), (unsigned long long)my_tree);
   }
 }
 
@@ -1397,7 +1405,7 @@ struct RuleMomL {
                   const int32_t* qv, const KernelParams& kp, void* out_pairs, void* out_self) {
     const size_t sm = moments_smem_bytes<D>(0);
     set_smem(k_rule_moments<D>, sm);
-    const int grid = count < lc.num_sms ? count : lc.num_sms;
+    const int grid = count < 2 * lc.num_sms ? count : 2 * lc.num_sms;
     ++*lc.launches;
     k_rule_moments<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, mode, qv, kp,
                                                          (cplx*)out_pairs, (cplx*)out_self);
@@ -1422,14 +1430,15 @@ struct AdaptiveL {
   static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                   const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                   const void* I_smooth, void* I_near, int32_t* leaves, void* work,
-                  int64_t stride, int A_max, int levels, int grid, int* status) {
+                  int64_t stride, int A_max, int levels, int grid, int* status, int* sched) {
     const size_t sm = moments_smem_bytes<D>(64 / 2 + 4 * 32) + 64 * sizeof(int);
     set_smem(k_adaptive<D>, sm);
     AdaptiveWS w{stride, A_max, levels};
     ++*lc.launches;
+    cudaMemsetAsync(sched, 0, sizeof(int), lc.stream);
     k_adaptive<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, kp, eps, normV, leaf_order,
                                                      max_depth, (const cplx*)I_smooth, (cplx*)I_near,
-                                                     leaves, (unsigned char*)work, w, status);
+                                                     leaves, (unsigned char*)work, w, status, sched);
   }
 };
 
@@ -1559,9 +1568,10 @@ bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count,
 bool launch_adaptive(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                      const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
-                     int A_max, int levels, int grid, int* status) {
+                     int A_max, int levels, int grid, int* status, int* sched) {
   return dispatch<AdaptiveL>(d, lc, plist, count, dv, kp, eps, normV, leaf_order, max_depth,
-                             I_smooth, I_near, leaves, work, stride, A_max, levels, grid, status);
+                             I_smooth, I_near, leaves, work, stride, A_max, levels, grid, status,
+                             sched);
 }
 bool launch_self(int d, const LaunchCommon& lc, const Dev& dv, const int32_t* deg,
                  const KernelParams& kp, int order, void* out) {
@@ -1593,6 +1603,26 @@ void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int3
   ++*lc.launches;
   k_csr_apply<<<g, 256, 0, lc.stream>>>(row_ptr, col, val, (const cplx*)sigma, tnode, NT, jump,
                                         (cplx*)out);
+}
+
+// Resident blocks per SM of k_adaptive<d> (the persistent grid is this times the SM count).
+int adaptive_blocks_per_sm(int d) {
+  int nb = 1;
+  switch (d) {
+#define LCQ_CASE(D)                                                                          \
+  case D: {                                                                                  \
+    const size_t sm = moments_smem_bytes<D>(64 / 2 + 4 * 32) + 64 * sizeof(int);             \
+    set_smem(k_adaptive<D>, sm);                                                             \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adaptive<D>, kThreads, sm);         \
+    break;                                                                                   \
+  }
+    LCQ_CASE(1) LCQ_CASE(2) LCQ_CASE(3) LCQ_CASE(4) LCQ_CASE(5)
+    LCQ_CASE(6) LCQ_CASE(7) LCQ_CASE(8) LCQ_CASE(9) LCQ_CASE(10)
+#undef LCQ_CASE
+    default: break;
+  }
+  cudaGetLastError();
+  return nb < 1 ? 1 : nb;
 }
 
 size_t adaptive_smem_bytes(int d) {

@@ -96,7 +96,7 @@ bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count,
 bool launch_adaptive(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                      const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
-                     int A_max, int levels, int grid, int* status);
+                     int A_max, int levels, int grid, int* status, int* sched);
 bool launch_self(int d, const LaunchCommon& lc, const Dev& dv, const int32_t* deg,
                  const KernelParams& kp, int order, void* out);
 bool launch_v2c(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
@@ -112,5 +112,6 @@ void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int3
                       const double* val, const void* sigma, const int64_t* tnode, int64_t NT,
                       double jump, void* out);
 size_t adaptive_smem_bytes(int d);
+int adaptive_blocks_per_sm(int d);
 
 }  // namespace lcq

@@ -38,7 +38,7 @@ std::mutex g_mu;
 
 // Byte offsets of the regions inside g_scratch.
 struct Layout {
-  size_t status, counters, plist, node_off, Vt, nodes, coef, cen, rad, dj, eta, eta1, tpatch,
+  size_t status, counters, sched, plist, node_off, Vt, nodes, coef, cen, rad, dj, eta, eta1, tpatch,
       tlnode, pair_ptr, pair_tgt, pair_d2, pair_csr, ad_ptr, ad_pair, an_ptr, an_pair, self_ptr,
       self_tgt, self_csr, q, qn, roff, ru, rv, rw, gl_off, gl_x, gl_w, Is, In, leaves, work;
   size_t end;
@@ -55,7 +55,8 @@ Layout layout(const RuleTables& r, int64_t work_bytes) {
   Layout L{};
   size_t at = 0;
   L.status = bump(&at, sizeof(int));
-  L.counters = bump(&at, 4 * sizeof(long long));
+  L.counters = bump(&at, 8 * sizeof(long long));
+  L.sched = bump(&at, sizeof(int));
   L.plist = bump(&at, sizeof(int));
   L.node_off = bump(&at, 2 * 8);
   L.Vt = bump(&at, n * n * 8);
@@ -145,7 +146,7 @@ __global__ void k_noalloc_view(int NT, int n, int32_t* tpatch, int32_t* tlnode, 
     node_off[1] = n;
     *status = 0;
   }
-  if (threadIdx.x < 4) counters[threadIdx.x] = 0;
+  if (threadIdx.x < 8) counters[threadIdx.x] = 0;
 }
 
 // Once per device, with that device current: the scratch array's device address, the
@@ -253,8 +254,8 @@ extern "C" lcq_status lcq_adaptive_corrections_noalloc(
   const double eta_p = -1.0, eta1_p = 1.25;
   launch_geom(deg, lc, I(L.plist), 1, I64(L.node_off), y, n, F(L.Vt), F(L.nodes), eta_p, eta1_p,
               F(L.coef), F(L.cen), F(L.rad), F(L.dj), F(L.eta), F(L.eta1), I(L.status));
-  KernelParams kp{(int)kernel, k_re, k_im, alpha_re, alpha_im, beta_re, beta_im};
-  if (kernel == LCQ_S) kp.ar = kp.ai = kp.br = kp.bi = 0.0;
+  const KernelParams kp =
+      make_kernel_params((int)kernel, k_re, k_im, alpha_re, alpha_im, beta_re, beta_im);
   Dev dv{};
   dv.coef = F(L.coef);
   dv.node_off = I64(L.node_off);
@@ -294,7 +295,7 @@ extern "C" lcq_status lcq_adaptive_corrections_noalloc(
   // smooth-rule moments (the root of the adaptive walk), adaptive moments, V^T contraction
   launch_rule_moments(deg, lc, I(L.plist), 1, dv, 0, I32(L.q), kp, F(L.Is), nullptr);
   launch_adaptive(deg, lc, I(L.plist), 1, dv, kp, eps, dt.normV, 0, max_depth, F(L.Is), F(L.In),
-                  I32(L.leaves), b + L.work, stride, NT, max_depth, 1, I(L.status));
+                  I32(L.leaves), b + L.work, stride, NT, max_depth, 1, I(L.status), I(L.sched));
   launch_v2c(deg, lc, I(L.plist), 1, dv, F(L.Vt), F(L.In), F(L.Is), nullptr, nullptr, out);
   int hst = 0;
   e = cudaGetLastError();

@@ -140,7 +140,7 @@ class Context:
         return st
 
     def counters(self):
-        out = np.zeros(4, np.int64)
+        out = np.zeros(8, np.int64)
         self.check(_lib.lcq_counters(self.h, _ptr(out)), "lcq_counters")
         return out
 
