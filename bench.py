@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--leaf-order", type=int, default=0,
                     help="smooth rule used on subtriangles (0: the patch's far order q_j)")
     ap.add_argument("--eps", type=float, default=1e-9)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the mixed-precision and eps=1e-6 comparison runs")
     return ap.parse_args()
 
 
@@ -268,6 +270,48 @@ def run_ours(args, rank, world, local_rank):
         total_ms = float(t.item())
     value = world * N * args.steps / (total_ms / 1e3)
 
+    # FP64 vs mixed at eps = 1e-9 and 1e-6: throughput and the applied potential's
+    # relative L2 difference from the FP64 result on the same density
+    variants = None
+    if not args.no_variants:
+        variants = {}
+        sig = torch.from_numpy(W.density(N, 0)).to(dev)
+        ref_u = {}
+        for eps in (args.eps, 1e-6):
+            for prec in ("fp64", "mixed"):
+                p2 = lcq.params(eps, eta=wl.eta, test_dirs=W.test_directions(7),
+                                leaf_order=args.leaf_order)
+                times, ad = [], []
+                for it in range(3):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    near = lcq.build_near_lists(ctx, ds, tx_d, tn_d, p2)
+                    corr = lcq.gen_corrections(ctx, ds, near, wl.kernel, wl.k, p2, wl.alpha, wl.beta,
+                                               precision=prec)
+                    e1.record(stream)
+                    st = ctx.sync()
+                    if it > 0:
+                        times.append(e0.elapsed_time(e1))
+                        ad.append(ctx.stage_times()[0][3])
+                    if it < 2:
+                        corr.close()
+                        near.close()
+                u = lcq.apply_corrected_CFIE(ctx, ds, near, corr, sig, NT).cpu().numpy()
+                corr.close()
+                near.close()
+                key = f"{prec}_eps{eps:g}"
+                rec = {"value": N / (statistics.mean(times) / 1e3), "unit": UNIT,
+                       "ms_per_step": statistics.mean(times), "adaptive_ms": statistics.mean(ad),
+                       "status": st}
+                if prec == "fp64":
+                    ref_u[eps] = u
+                else:
+                    rec["rel_l2_vs_fp64"] = float(np.linalg.norm(u - ref_u[eps]) /
+                                                  np.linalg.norm(ref_u[eps]))
+                variants[key] = rec
+
     # end to end through the C ABI with host buffers: H2D of inputs, D2H of the CSR
     e2e = None
     if not args.no_e2e:
@@ -346,6 +390,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk, "status": max(statuses) if statuses else None,
         "stages_ms": dict(zip(["near_lists", "far_order", "smooth_annulus", "adaptive", "self",
                                "v2c"], st_mean)),
+        "variants": variants,
         "wall_s_timed_region": t_wall,
     }
     print(json.dumps(line), flush=True)

@@ -56,7 +56,15 @@ typedef enum {
  *   LCQ_CFIE : alpha D + beta S          (the paper's D - ik S is alpha = 1, beta = -ik) */
 typedef enum { LCQ_S = 0, LCQ_D = 1, LCQ_CFIE = 2 } lcq_kernel;
 
-typedef enum { LCQ_FP64 = 0 } lcq_precision;
+/* LCQ_FP64: every step in FP64.
+ * LCQ_MIXED: in the adaptive near integration, leaf nodes farther from the target than
+ * twice the size of their subtriangle get their kernel value in FP32 (the difference
+ * x - X, the phase k r and its reduction stay FP64); everything else -- self rules,
+ * refinement estimates, moments accumulation, the values-to-coefficients contraction --
+ * stays FP64.  Such nodes raise the adaptive test's rounding floor to the FP32 level, so
+ * the result differs from LCQ_FP64 by about 1e-7 relative (stated per result by the
+ * tests and the benchmark). */
+typedef enum { LCQ_FP64 = 0, LCQ_MIXED = 1 } lcq_precision;
 
 /* Surface: n_patches charts; patch j owns nodes node_off[j] .. node_off[j+1]-1,
  * sampled at lcq_ref_nodes(deg[j]) in that order (Sec. 5.2).

@@ -564,7 +564,8 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
   if (!ctx || !nr || !params || !out) return fail(ctx, LCQ_ERR_ARG, "null argument");
   (void)surf;
   *out = nullptr;
-  if (precision != LCQ_FP64) return fail(ctx, LCQ_ERR_ARG, "unsupported precision");
+  if (precision != LCQ_FP64 && precision != LCQ_MIXED)
+    return fail(ctx, LCQ_ERR_ARG, "unsupported precision");
   if ((int)kernel < 0 || (int)kernel > 2) return fail(ctx, LCQ_ERR_ARG, "unknown kernel");
   if (!(params->eps > 0.0) || k_im < 0.0 || !isfinite(k_re) || !isfinite(k_im))
     return fail(ctx, LCQ_ERR_ARG, "eps must be > 0 and Im k >= 0");
@@ -674,7 +675,7 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
       launch_adaptive(d, lc, nr->ad_list_dev[d], nr->ad_count[d], dv, kp,
                       params->eps * params->eps_loosen, ctx->deg[d].normV, params->leaf_order,
                       params->max_depth, Is, In, c->leaves, ctx->work, stride, (int)A, levels, agrid,
-                      ctx->d_status, ctx->d_sched + d);
+                      ctx->d_status, ctx->d_sched + d, precision == LCQ_MIXED ? 2.0 : 0.0);
     }
     CK(cudaGetLastError());
   }

@@ -264,6 +264,61 @@ __device__ __forceinline__ cplx kernel_eval(const KernelParams& kp, double x0, d
   return out;
 }
 
+// Mixed-precision variant for sources well separated from the target: the difference
+// d = x - X and r^2 arrive in FP64 (kept in FP64, as is the phase k r, refined from the
+// FP32 distance by one Newton step and reduced modulo 2 pi); everything else -- 1/r,
+// sin/cos of the reduced phase, the S and D factors, the CFIE combination -- is FP32.
+// The rounding envelope is returned multiplied by env_scale (the FP32 noise is larger).
+__device__ __forceinline__ cplx kernel_eval_f32(const KernelParams& kp, double d0, double d1,
+                                                double d2, double r2, double N0, double N1,
+                                                double N2, double Jw, double R, double* env,
+                                                double env_scale) {
+  const float fr2 = (float)r2;
+  const float frinv = rsqrtf(fr2);
+  const float fr = fr2 * frinv;
+  const double r = (double)fr + (r2 - (double)fr * (double)fr) * (0.5 * (double)frinv);
+  double th = kp.kr * r;
+  th -= 6.283185307179586 * rint(th * 0.15915494309189535);
+  float sn, cs;
+  sincosf((float)th, &sn, &cs);
+  float ex = 0.0795774715459f * frinv;
+  if (kp.ki != 0.0) ex *= expf(-(float)kp.ki * fr);
+  const float Gr = ex * cs, Gi = ex * sn;
+  float ore = 0.0f, oim = 0.0f;
+  const float fJw = (float)Jw;
+  if (kp.kind != 1) {
+    const float sr = Gr * fJw, si = Gi * fJw;
+    if (kp.kind == 0) {
+      ore = sr;
+      oim = si;
+    } else {
+      const float br = (float)kp.br, bi = (float)kp.bi;
+      ore = br * sr - bi * si;
+      oim = br * si + bi * sr;
+    }
+  }
+  const float f0 = 1.0f + (float)kp.ki * fr, f1 = -(float)kp.kr * fr;
+  if (kp.kind != 0) {
+    const float ndx = ((float)N0 * (float)d0 + (float)N1 * (float)d1 + (float)N2 * (float)d2) *
+                      frinv * frinv;
+    float dr = (Gr * f0 - Gi * f1) * ndx, di = (Gr * f1 + Gi * f0) * ndx;
+    if (kp.kind == 2) {
+      const float ar = (float)kp.ar, ai = (float)kp.ai;
+      const float tr = ar * dr - ai * di, ti = ar * di + ai * dr;
+      dr = tr;
+      di = ti;
+    }
+    ore += dr;
+    oim += di;
+  }
+  if (env) {
+    const float fa = sqrtf(f0 * f0 + f1 * f1);
+    *env = (double)(ex * fJw * ((float)kp.eb + (float)kp.ea * fa * (float)R * frinv * frinv)) *
+           env_scale;
+  }
+  return {(double)ore, (double)oim};
+}
+
 // Cross product helper.
 __device__ __forceinline__ void cross3(const double* a, const double* b, double* c) {
   c[0] = a[1] * b[2] - a[2] * b[1];

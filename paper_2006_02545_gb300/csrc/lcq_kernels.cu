@@ -19,6 +19,8 @@ namespace lcq {
 
 
 constexpr int kThreads = 256;
+constexpr double kRoundingFloor = 2e-13;  // multiple of the FP64 rounding envelope never asked below
+constexpr double kF32Floor = 2e-6;        // the same for kernel values evaluated in FP32
 
 // ============================================================================ helpers
 __device__ __forceinline__ double warp_sum(double v) {
@@ -431,12 +433,16 @@ struct SegMap {
 // TA: target accessor (pos(i, x[3])); out row of target i: out + orow(i) * ostride.
 // Positions are relative to the patch centroid cen (the coefficients cf describe
 // X - cen).  With ENV, eout[i * nseg + seg] also receives the summed rounding envelope.
+// mix > 0 (mixed precision): a node farther than mix * 2R sqrt(det_seg) -- mix times the
+// size of its subtriangle -- from the target is evaluated by kernel_eval_f32, and its
+// envelope is scaled by kF32Floor / kRoundingFloor.
 template <int D, bool ENV = false, class TA, class OR>
 __device__ void block_moments(const double* cf, const double* __restrict__ ru,
                               const double* __restrict__ rv, const double* __restrict__ rw, int Q,
                               const SegMap* segs, int nseg, const TA& ta, int T, OR orow,
                               int64_t ostride, const KernelParams& kp, double* sm,
-                              const double* cen, double R = 0.0, double* eout = nullptr) {
+                              const double* cen, double R = 0.0, double* eout = nullptr,
+                              double mix = 0.0) {
   using C = Cfg<D>;
   double* B = sm;
   double* Xs = B + C::CH * C::BS;
@@ -483,10 +489,26 @@ __device__ void block_moments(const double* cf, const double* __restrict__ ru,
         const int i = e / C::CH, ql = e - i * C::CH;
         cplx g = {0.0, 0.0};
         double ev = 0.0;
-        if (ql < nch)
-          g = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql], Xs[C::CH + ql],
-                          Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql], Js[ql],
-                          R, ENV ? &ev : nullptr);
+        if (ql < nch) {
+          bool f32 = false;
+          double d0 = 0, d1 = 0, d2 = 0, r2 = 0;
+          if (mix > 0.0) {
+            const int sg = (c0 + ql) / Q;
+            const double h = mix * 2.0 * R * sqrt(segs[sg].det);
+            d0 = tx[3 * i] - Xs[ql];
+            d1 = tx[3 * i + 1] - Xs[C::CH + ql];
+            d2 = tx[3 * i + 2] - Xs[2 * C::CH + ql];
+            r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            f32 = r2 >= h * h;
+          }
+          if (f32)
+            g = kernel_eval_f32(kp, d0, d1, d2, r2, Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql],
+                                Js[ql], R, ENV ? &ev : nullptr, kF32Floor / kRoundingFloor);
+          else
+            g = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql], Xs[C::CH + ql],
+                            Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql],
+                            Js[ql], R, ENV ? &ev : nullptr);
+        }
         G[i * C::CH + ql] = g;
         if (ENV) Ev[i * C::CH + ql] = ev;
       }
@@ -802,7 +824,6 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
 // of X, K_nm and J across targets of Fig. multipletargpot).  A target accepts the
 // children's sum when ||I_T - sum_c I_c||_2 <= max(tol0 4^-L, 1e-12 ||sum_c I_c||_2).
 constexpr int kMaxTreeNodes = 1 << 16;  // union-tree nodes walked per patch at most
-constexpr double kRoundingFloor = 2e-13;  // multiple of the rounding envelope never asked below
 
 struct AdaptiveWS {
   int64_t stride;   // bytes per block
@@ -820,7 +841,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
                                                        int32_t* __restrict__ leaves_out,
                                                        unsigned char* __restrict__ work,
                                                        AdaptiveWS wsd, int* __restrict__ status,
-                                                       int* __restrict__ sched) {
+                                                       int* __restrict__ sched, double mix) {
   using C = Cfg<D>;
   constexpr int n = C::n;
   extern __shared__ double smem[];
@@ -945,7 +966,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
       TgtAdaptive ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, ST};
       block_moments<D, true>(cf, ru, rv, rw, Q, segs, 4, ta, S,
                              [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, 4 * n, kp,
-                             ws, dv.cen + 3 * j, Rj, tmpE);
+                             ws, dv.cen + 3 * j, Rj, tmpE, mix);
       __syncthreads();
       my_tests += S;
       my_nodes += (long long)S * 4 * Q;
@@ -1430,7 +1451,8 @@ struct AdaptiveL {
   static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                   const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                   const void* I_smooth, void* I_near, int32_t* leaves, void* work,
-                  int64_t stride, int A_max, int levels, int grid, int* status, int* sched) {
+                  int64_t stride, int A_max, int levels, int grid, int* status, int* sched,
+                  double mix) {
     const size_t sm = moments_smem_bytes<D>(64 / 2 + 4 * 32) + 64 * sizeof(int);
     set_smem(k_adaptive<D>, sm);
     AdaptiveWS w{stride, A_max, levels};
@@ -1438,7 +1460,8 @@ struct AdaptiveL {
     cudaMemsetAsync(sched, 0, sizeof(int), lc.stream);
     k_adaptive<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, kp, eps, normV, leaf_order,
                                                      max_depth, (const cplx*)I_smooth, (cplx*)I_near,
-                                                     leaves, (unsigned char*)work, w, status, sched);
+                                                     leaves, (unsigned char*)work, w, status, sched,
+                                                     mix);
   }
 };
 
@@ -1568,10 +1591,10 @@ bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count,
 bool launch_adaptive(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                      const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
-                     int A_max, int levels, int grid, int* status, int* sched) {
+                     int A_max, int levels, int grid, int* status, int* sched, double mix) {
   return dispatch<AdaptiveL>(d, lc, plist, count, dv, kp, eps, normV, leaf_order, max_depth,
                              I_smooth, I_near, leaves, work, stride, A_max, levels, grid, status,
-                             sched);
+                             sched, mix);
 }
 bool launch_self(int d, const LaunchCommon& lc, const Dev& dv, const int32_t* deg,
                  const KernelParams& kp, int order, void* out) {

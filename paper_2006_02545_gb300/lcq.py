@@ -256,13 +256,17 @@ class Corrections:
             pass
 
 
+PRECISIONS = {"fp64": 0, "mixed": 1}
+
+
 def gen_corrections(ctx: Context, surf: DeviceSurface, near: NearLists, kernel: str, k,
-                    prm, alpha=1.0, beta=0.0) -> Corrections:
+                    prm, alpha=1.0, beta=0.0, precision: str = "fp64") -> Corrections:
     k, alpha, beta = complex(k), complex(alpha), complex(beta)
     h = C.c_void_p()
     ctx.check(_lib.lcq_gen_corrections(ctx.h, C.byref(surf.s), near.h, KERNELS[kernel], k.real,
-                                       k.imag, alpha.real, alpha.imag, beta.real, beta.imag, 0,
-                                       C.byref(prm), C.byref(h)), "lcq_gen_corrections")
+                                       k.imag, alpha.real, alpha.imag, beta.real, beta.imag,
+                                       PRECISIONS[precision], C.byref(prm), C.byref(h)),
+              "lcq_gen_corrections")
     return Corrections(ctx, h, near, kernel)
 
 

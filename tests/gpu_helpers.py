@@ -7,7 +7,7 @@ from paper_2006_02545_gb300 import workloads as W
 
 
 def run_gpu(ctx, surf, x, tn, kind, k, eps, eta=-1.0, alpha=1.0, beta=0.0, dirs_seed=3, sigma_seed=0,
-            **kw):
+            precision="fp64", **kw):
     import torch
     from paper_2006_02545_gb300 import lcq
     dev = ctx.torch_device
@@ -15,7 +15,7 @@ def run_gpu(ctx, surf, x, tn, kind, k, eps, eta=-1.0, alpha=1.0, beta=0.0, dirs_
     prm = lcq.params(eps, eta=eta, test_dirs=W.test_directions(dirs_seed), **kw)
     near = lcq.build_near_lists(ctx, ds, torch.from_numpy(np.ascontiguousarray(x)).to(dev),
                                 torch.from_numpy(tn).to(dev), prm)
-    corr = lcq.gen_corrections(ctx, ds, near, kind, k, prm, alpha, beta)
+    corr = lcq.gen_corrections(ctx, ds, near, kind, k, prm, alpha, beta, precision=precision)
     st = ctx.sync(120000)
     rp, col, val = corr.export(x.shape[1])
     q, qn, leaves = corr.stats(surf.n_patches)

@@ -226,3 +226,17 @@ def test_edge_cases(ctx):
         lcq.gen_corrections(ctx, ds, near, "S", 1.0, lcq.params(1e-6, m_max=40))
     near.close()
     assert ctx.sync(60000) == 0
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_mixed_precision_error_stated(ctx, eps):
+    """LCQ_MIXED (FP32 kernel values on well-separated leaf nodes) against the FP64 oracle:
+    the applied potential within max(eps, 1e-7) relative L2 (the form's stated error)."""
+    s = W.ellipsoid(2, 5, axes=(1.0, 1.5, 2.0))
+    x, tn = W.onsurface_targets(s)
+    k = 4.0
+    g = run_gpu(ctx, s, x, tn, "CFIE", k, eps, alpha=1.0, beta=-1j * k, precision="mixed")
+    assert g["status"] == 0
+    oc, uo = run_oracle(s, x, tn, "CFIE", k, eps, alpha=1.0, beta=-1j * k, sigma=g["sigma"])
+    rel = np.linalg.norm(g["u"] - uo) / np.linalg.norm(uo)
+    assert rel <= max(eps, 1e-7), rel
