@@ -150,6 +150,42 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
                                lcq_precision precision, const lcq_params* params,
                                lcq_corr** out);
 
+/* ---- Batches of independent surfaces (no counterpart in the paper: many small
+ * problems, e.g. a parameter study, generated together so that one launch per stage
+ * covers all of them).  The surface lcq_surface is the concatenation of n_surfaces
+ * surfaces; surface s owns patches [surface_patch_off[s], surface_patch_off[s+1])
+ * (host int64 [n_surfaces+1], starting at 0, ending at n_patches, strictly
+ * increasing).  A target is near only to patches of its own surface: an on-surface
+ * target belongs to its patch's surface; an off-surface target to tgt_surface[t]
+ * (device int32 [NT]; NULL puts every off-surface target in surface 0; a value
+ * outside [0, n_surfaces) is LCQ_ERR_ARG).  Everything else is as for
+ * lcq_build_near_lists. */
+lcq_status lcq_build_near_lists_batched(lcq_ctx* ctx, const lcq_surface* surf, int n_surfaces,
+                                        const int64_t* surface_patch_off, const double* tgt_xyz,
+                                        const int64_t* tgt_node, const int32_t* tgt_surface,
+                                        int64_t n_targets, const lcq_params* params,
+                                        lcq_near** out);
+
+/* Physics of one surface of a batch: wavenumber k (Im k >= 0), CFIE coefficients
+ * (ignored for S and D) and the tolerance eps that replaces params->eps for it
+ * (far order, adaptive tolerance eps * eps_loosen, default self-rule order). */
+typedef struct {
+  double k_re, k_im;
+  double alpha_re, alpha_im;
+  double beta_re, beta_im;
+  double eps;
+} lcq_surface_physics;
+
+/* lcq_gen_corrections over near lists built by lcq_build_near_lists_batched, with
+ * physics[s] (host [n_surfaces]) for surface s.  One launch per stage and patch
+ * degree covers every surface.  The CSR and the apply functions work on the whole
+ * batch: the far sum of a target runs over its own surface's sources with that
+ * surface's kernel. */
+lcq_status lcq_gen_corrections_batched(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                                       lcq_kernel kernel, int n_surfaces,
+                                       const lcq_surface_physics* physics, lcq_precision precision,
+                                       const lcq_params* params, lcq_corr** out);
+
 /* nnz of the CSR, N_over = sum_j n_{q_j} (Sec. 5.2), value dtype (0 = complex128). */
 lcq_status lcq_corr_info(const lcq_corr* corr, int64_t* nnz, int64_t* n_over, int* value_dtype);
 

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <thread>
 #include <vector>
@@ -111,6 +112,42 @@ lcq_status ensure_deg(lcq_ctx* ctx, int d) {
   return LCQ_OK;
 }
 
+
+// Grid over the centroid box b[0..2]..b[3..5] with cell edge a little above max eta_j R_j
+// (b[6]), so that a ball of radius eta_j R_j never reaches beyond the neighbouring cells even
+// after rounding of the cell coordinates; coarsened until it has at most
+// max(4096, 2 P) cells.
+GridSpec make_grid(const double* b, int64_t P) {
+  double ext = 0.0;
+  for (int a = 0; a < 3; ++a) ext = std::max(ext, b[3 + a] - b[a]);
+  double h = b[6] * (1.0 + 1e-6);
+  if (!(h > ext * 1e-9)) h = std::max(ext * 1e-9, 1e-300);
+  const int64_t cap = std::max<int64_t>(4096, 2 * P);
+  GridSpec g{};
+  for (;;) {
+    g.inv_h = 1.0 / h;
+    int64_t tot = 1;
+    int n[3];
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) {
+      const double f = std::floor((b[3 + a] - b[a]) * g.inv_h);
+      if (!(f < 1e6)) {
+        ok = false;
+        break;
+      }
+      n[a] = (int)f + 1;
+      tot *= n[a];
+    }
+    if (ok && tot <= cap) {
+      for (int a = 0; a < 3; ++a) g.lo[a] = b[a];
+      g.nx = n[0];
+      g.ny = n[1];
+      g.nz = n[2];
+      return g;
+    }
+    h *= 1.25;
+  }
+}
 }  // namespace
 
 // ============================================================================ API
@@ -255,15 +292,25 @@ lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out8) {
 }
 
 // ---------------------------------------------------------------------------- near lists
-lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const double* tgt_xyz,
-                                const int64_t* tgt_node, int64_t NT, const lcq_params* params,
-                                lcq_near** out) {
+static lcq_status build_near_impl(lcq_ctx* ctx, const lcq_surface* surf, int n_groups,
+                                  const int64_t* group_patch_off, const double* tgt_xyz,
+                                  const int64_t* tgt_node, const int32_t* tgt_group, int64_t NT,
+                                  const lcq_params* params, lcq_near** out) {
   if (!ctx || !surf || !params || !out || NT < 0) return fail(ctx, LCQ_ERR_ARG, "null argument");
   *out = nullptr;
   const int64_t P = surf->n_patches;
   if (P <= 0 || !surf->deg || !surf->node_off || !surf->xyz)
     return fail(ctx, LCQ_ERR_ARG, "empty or incomplete surface");
+  const bool grouped = group_patch_off != nullptr;
+  if (grouped) {
+    if (n_groups < 1 || group_patch_off[0] != 0 || group_patch_off[n_groups] != P)
+      return fail(ctx, LCQ_ERR_ARG, "surface ranges must start at 0 and end at n_patches");
+    for (int g = 0; g < n_groups; ++g)
+      if (group_patch_off[g + 1] <= group_patch_off[g])
+        return fail(ctx, LCQ_ERR_ARG, "every surface of a batch needs at least one patch");
+  }
   if (NT > 0 && (!tgt_xyz || !tgt_node)) return fail(ctx, LCQ_ERR_ARG, "null targets");
+  if (NT >= (int64_t)0x7fffffff) return fail(ctx, LCQ_ERR_ARG, "more than 2^31-2 targets");
   if (!(params->eps > 0.0) || !(params->eta1 > 0.0))
     return fail(ctx, LCQ_ERR_ARG, "eps and eta1 must be positive");
   if (surf->node_off[0] != 0) return fail(ctx, LCQ_ERR_ARG, "node_off[0] != 0");
@@ -292,6 +339,9 @@ lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const dou
   nr->node_off_h.assign(surf->node_off, surf->node_off + P + 1);
   nr->stream = st;
   nr->device = ctx->device;
+  nr->grouped = grouped;
+  nr->n_groups = grouped ? n_groups : 1;
+  if (grouped) nr->gpatch_off.assign(group_patch_off, group_patch_off + n_groups + 1);
   std::vector<std::vector<int>> lists(kMaxDeg + 1);
   for (int64_t j = 0; j < P; ++j) lists[surf->deg[j]].push_back((int)j);
   for (int d = 1; d <= kMaxDeg; ++d) {
@@ -333,56 +383,109 @@ lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const dou
                 nr->eta, nr->eta1, ctx->d_status);
   }
   CK(cudaGetLastError());
-  NearArgs na{nr->tgt, NT, nr->cen, nr->rad, nr->eta, nr->eta1};
-  // counts (arrays carry one trailing zero so that the exclusive scan yields the total)
-  int64_t *row_np, *row_nnz, *npair, *nad, *nself;
+  if (grouped) {
+    int64_t* goff;
+    CK(dalloc(st, &goff, n_groups + 1));
+    CK(cudaMemcpyAsync(goff, group_patch_off, (n_groups + 1) * 8, cudaMemcpyHostToDevice, st));
+    CK(dalloc(st, &nr->pgroup, P));
+    CK(dalloc(st, &nr->tgroup, std::max<int64_t>(NT, 1)));
+    launch_groups(lc, NT, nr->tgt_patch, goff, n_groups, tgt_group, nr->pgroup, nr->tgroup,
+                  ctx->d_status);
+    dfree(st, goff);
+  }
+  NearArgs na{nr->tgt, NT, nr->cen, nr->rad, nr->eta, nr->eta1, nr->pgroup, nr->tgroup};
+  // uniform grid over the patch centroids (cell edge >= max eta_j R_j)
+  double* bnd;
+  CK(dalloc(st, &bnd, 8));
+  launch_grid_bounds(lc, na, P, bnd);
+  double hb[7];
+  CK(cudaMemcpyAsync(hb, bnd, sizeof(hb), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  {
+    int hst = 0;
+    CK(cudaMemcpy(&hst, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hst & kStBadGroup) {
+      cudaMemset(ctx->d_status, 0, sizeof(int));
+      dfree(st, bnd);
+      lcq_near_destroy(nr);
+      return fail(ctx, LCQ_ERR_ARG, "target surface index outside [0, n_surfaces)");
+    }
+    if (hst & (kStNonFinite | kStDegenerate)) {
+      cudaMemset(ctx->d_status, 0, sizeof(int));
+      dfree(st, bnd);
+      lcq_near_destroy(nr);
+      return fail(ctx, (hst & kStNonFinite) ? LCQ_ERR_NONFINITE : LCQ_ERR_DEGENERATE_PATCH,
+                  (hst & kStNonFinite) ? "non-finite coordinates" : "degenerate patch");
+    }
+  }
+  const GridSpec g = make_grid(hb, P);
+  const int64_t ncell = (int64_t)g.nx * g.ny * g.nz;
+  unsigned long long *cell_cnt, *cell_cur;
+  int64_t* cell_ptr;
+  int32_t* cell_patch;
+  CK(dalloc(st, &cell_cnt, ncell + 1));
+  CK(dalloc(st, &cell_cur, ncell));
+  CK(dalloc(st, &cell_ptr, ncell + 1));
+  CK(dalloc(st, &cell_patch, P));
+  CK(cudaMemsetAsync(cell_cnt, 0, (ncell + 1) * 8, st));
+  CK(cudaMemsetAsync(cell_cur, 0, ncell * 8, st));
+  const int64_t mx = std::max(std::max(NT, P), ncell) + 1;
+  int64_t* scr;
+  CK(dalloc(st, &scr, 2 * ((mx + 1023) / 1024) + 4096));
+  launch_cell_bins(lc, na, P, g, cell_cnt, cell_ptr, cell_cur, cell_patch, scr);
+
+  // rows: counts, offsets, then the sorted patches of each row and the CSR columns
+  int64_t *row_np, *row_nnz;
+  unsigned long long *npair, *nad, *nself, *pcur, *scur;
   CK(dalloc(st, &row_np, NT + 1));
   CK(dalloc(st, &row_nnz, NT + 1));
   CK(dalloc(st, &npair, P + 1));
   CK(dalloc(st, &nad, P + 1));
   CK(dalloc(st, &nself, P + 1));
+  CK(dalloc(st, &pcur, P));
+  CK(dalloc(st, &scur, P));
   CK(cudaMemsetAsync(row_np, 0, (NT + 1) * 8, st));
   CK(cudaMemsetAsync(row_nnz, 0, (NT + 1) * 8, st));
   CK(cudaMemsetAsync(npair, 0, (P + 1) * 8, st));
   CK(cudaMemsetAsync(nad, 0, (P + 1) * 8, st));
   CK(cudaMemsetAsync(nself, 0, (P + 1) * 8, st));
-  if (NT > 0) {
-    launch_row_count(lc, na, nr->tgt_patch, P, nr->deg, row_np, row_nnz);
-    launch_patch_count(lc, na, nr->tgt_patch, P, npair, nad, nself);
-  }
+  CK(cudaMemsetAsync(pcur, 0, P * 8, st));
+  CK(cudaMemsetAsync(scur, 0, P * 8, st));
+  if (NT > 0)
+    launch_row_count(lc, na, g, cell_ptr, cell_patch, nr->tgt_patch, nr->deg, row_np, row_nnz);
   CK(dalloc(st, &nr->row_ptr, NT + 1));
   CK(dalloc(st, &nr->rowp_ptr, NT + 1));
   CK(dalloc(st, &nr->pair_ptr, P + 1));
   CK(dalloc(st, &nr->ad_ptr, P + 1));
   CK(dalloc(st, &nr->an_ptr, P + 1));
   CK(dalloc(st, &nr->self_ptr, P + 1));
-  const int64_t mx = std::max(NT, P) + 1;
-  int64_t* scr;
-  CK(dalloc(st, &scr, 2 * ((mx + 1023) / 1024) + 4096));
   launch_scan(lc, row_nnz, nr->row_ptr, NT + 1, scr);
   launch_scan(lc, row_np, nr->rowp_ptr, NT + 1, scr);
-  launch_scan(lc, npair, nr->pair_ptr, P + 1, scr);
-  launch_scan(lc, nad, nr->ad_ptr, P + 1, scr);
-  launch_scan(lc, nself, nr->self_ptr, P + 1, scr);
   CK(cudaGetLastError());
-  std::vector<int64_t> h_np(P + 1), h_nad(P + 1), h_ns(P + 1);
   int64_t tot[2];
-  CK(cudaMemcpyAsync(h_np.data(), npair, (P + 1) * 8, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h_nad.data(), nad, (P + 1) * 8, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h_ns.data(), nself, (P + 1) * 8, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&tot[0], nr->row_ptr + NT, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&tot[1], nr->rowp_ptr + NT, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  int hst = 0;
-  CK(cudaMemcpy(&hst, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-  if (hst & (kStNonFinite | kStDegenerate)) {
-    cudaMemset(ctx->d_status, 0, sizeof(int));
-    lcq_near_destroy(nr);
-    return fail(ctx, (hst & kStNonFinite) ? LCQ_ERR_NONFINITE : LCQ_ERR_DEGENERATE_PATCH,
-                (hst & kStNonFinite) ? "non-finite coordinates" : "degenerate patch");
-  }
   nr->nnz = tot[0];
   const int64_t rowp_total = tot[1];
+  int32_t* row_tmp;
+  CK(dalloc(st, &nr->col, nr->nnz));
+  CK(dalloc(st, &nr->rowp_patch, rowp_total));
+  CK(dalloc(st, &nr->rowp_off, rowp_total));
+  CK(dalloc(st, &row_tmp, rowp_total));
+  if (NT > 0)
+    launch_row_fill(lc, na, g, cell_ptr, cell_patch, nr->tgt_patch, nr->deg, nr->node_off,
+                    nr->rowp_ptr, nr->row_ptr, row_tmp, nr->rowp_patch, nr->rowp_off, nr->col,
+                    npair, nad, nself);
+  launch_scan(lc, reinterpret_cast<int64_t*>(npair), nr->pair_ptr, P + 1, scr);
+  launch_scan(lc, reinterpret_cast<int64_t*>(nad), nr->ad_ptr, P + 1, scr);
+  launch_scan(lc, reinterpret_cast<int64_t*>(nself), nr->self_ptr, P + 1, scr);
+  CK(cudaGetLastError());
+  std::vector<int64_t> h_np(P + 1), h_nad(P + 1), h_ns(P + 1);
+  CK(cudaMemcpyAsync(h_np.data(), npair, (P + 1) * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h_nad.data(), nad, (P + 1) * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h_ns.data(), nself, (P + 1) * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   std::vector<int64_t> an_h(P + 1);
   int64_t acc_p = 0, acc_a = 0, acc_s = 0, acc_n = 0;
   for (int64_t j = 0; j < P; ++j) {
@@ -396,6 +499,10 @@ lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const dou
     acc_n += h_np[j] - h_nad[j];
   }
   an_h[P] = acc_n;
+  if (acc_p >= (int64_t)0x7fffffff) {
+    lcq_near_destroy(nr);
+    return fail(ctx, LCQ_ERR_CAPACITY, "more than 2^31-1 near pairs");
+  }
   // patches with adaptive targets, per degree, most adaptive targets first (the adaptive
   // kernel takes them in this order from a shared counter: longest jobs first)
   for (int d = 1; d <= kMaxDeg; ++d) {
@@ -415,9 +522,9 @@ lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const dou
   nr->n_self = acc_s;
   nr->n_annulus = acc_n;
   CK(cudaMemcpyAsync(nr->an_ptr, an_h.data(), (P + 1) * 8, cudaMemcpyHostToDevice, st));
-  CK(dalloc(st, &nr->col, nr->nnz));
-  CK(dalloc(st, &nr->rowp_patch, rowp_total));
-  CK(dalloc(st, &nr->rowp_off, rowp_total));
+  int32_t *ptmp, *stmp;
+  CK(dalloc(st, &ptmp, nr->n_pairs));
+  CK(dalloc(st, &stmp, nr->n_self));
   CK(dalloc(st, &nr->pair_tgt, nr->n_pairs));
   CK(dalloc(st, &nr->pair_ad, nr->n_pairs));
   CK(dalloc(st, &nr->pair_d2, nr->n_pairs));
@@ -426,14 +533,21 @@ lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const dou
   CK(dalloc(st, &nr->an_pair, nr->n_annulus));
   CK(dalloc(st, &nr->self_tgt, nr->n_self));
   CK(dalloc(st, &nr->self_csr, nr->n_self));
-  if (NT > 0) {
-    launch_row_fill(lc, na, nr->tgt_patch, P, nr->deg, nr->node_off, nr->rowp_ptr, nr->row_ptr,
-                    nr->rowp_patch, nr->rowp_off, nr->col);
+  if (NT > 0)
     launch_patch_fill(lc, na, nr->tgt_patch, P, nr->pair_ptr, nr->ad_ptr, nr->an_ptr, nr->self_ptr,
-                      nr->rowp_ptr, nr->rowp_patch, nr->rowp_off, nr->row_ptr, nr->pair_tgt,
-                      nr->pair_ad, nr->pair_d2, nr->pair_csr, nr->ad_pair, nr->an_pair,
-                      nr->self_tgt, nr->self_csr);
-  }
+                      nr->rowp_ptr, nr->rowp_patch, nr->rowp_off, nr->row_ptr, pcur, scur, ptmp,
+                      stmp, nr->pair_tgt, nr->pair_ad, nr->pair_d2, nr->pair_csr, nr->ad_pair,
+                      nr->an_pair, nr->self_tgt, nr->self_csr);
+  dfree(st, bnd);
+  dfree(st, cell_cnt);
+  dfree(st, cell_cur);
+  dfree(st, cell_ptr);
+  dfree(st, cell_patch);
+  dfree(st, pcur);
+  dfree(st, scur);
+  dfree(st, ptmp);
+  dfree(st, stmp);
+  dfree(st, row_tmp);
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[1], st));
   dfree(st, row_np);
@@ -444,6 +558,21 @@ lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const dou
   dfree(st, scr);
   *out = nr;
   return LCQ_OK;
+}
+
+lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const double* tgt_xyz,
+                                const int64_t* tgt_node, int64_t NT, const lcq_params* params,
+                                lcq_near** out) {
+  return build_near_impl(ctx, surf, 1, nullptr, tgt_xyz, tgt_node, nullptr, NT, params, out);
+}
+
+lcq_status lcq_build_near_lists_batched(lcq_ctx* ctx, const lcq_surface* surf, int n_surfaces,
+                                        const int64_t* surface_patch_off, const double* tgt_xyz,
+                                        const int64_t* tgt_node, const int32_t* tgt_surface,
+                                        int64_t NT, const lcq_params* params, lcq_near** out) {
+  if (!surface_patch_off) return fail(ctx, LCQ_ERR_ARG, "null surface ranges");
+  return build_near_impl(ctx, surf, n_surfaces, surface_patch_off, tgt_xyz, tgt_node, tgt_surface,
+                         NT, params, out);
 }
 
 lcq_status lcq_near_info(const lcq_near* nr, int64_t* n_pairs, int64_t* n_self,
@@ -495,6 +624,8 @@ void lcq_near_destroy(lcq_near* nr) {
   dfree(st, nr->tnode);
   dfree(st, nr->tgt_patch);
   dfree(st, nr->tgt_lnode);
+  dfree(st, nr->pgroup);
+  dfree(st, nr->tgroup);
   dfree(st, nr->row_ptr);
   dfree(st, nr->rowp_ptr);
   dfree(st, nr->rowp_patch);
@@ -517,8 +648,11 @@ void lcq_near_destroy(lcq_near* nr) {
 }
 
 // ---------------------------------------------------------------------------- corrections
-static Dev make_dev(lcq_ctx* ctx, const lcq_near* nr, const int32_t* q, int ldI) {
+static Dev make_dev(lcq_ctx* ctx, const lcq_near* nr, const int32_t* q, int ldI,
+                    const GroupParams* grp) {
   Dev dv{};
+  dv.pgroup = grp ? nr->pgroup : nullptr;
+  dv.grp = grp;
   dv.coef = nr->coef;
   dv.node_off = nr->node_off;
   dv.cen = nr->cen;
@@ -557,18 +691,27 @@ static Dev make_dev(lcq_ctx* ctx, const lcq_near* nr, const int32_t* q, int ldI)
   return dv;
 }
 
-lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* nr,
-                               lcq_kernel kernel, double k_re, double k_im, double alpha_re,
-                               double alpha_im, double beta_re, double beta_im,
-                               lcq_precision precision, const lcq_params* params, lcq_corr** out) {
-  if (!ctx || !nr || !params || !out) return fail(ctx, LCQ_ERR_ARG, "null argument");
-  (void)surf;
+static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, int n_phys,
+                           const lcq_surface_physics* phys, lcq_precision precision,
+                           const lcq_params* params, lcq_corr** out) {
+  if (!ctx || !nr || !params || !out || !phys) return fail(ctx, LCQ_ERR_ARG, "null argument");
   *out = nullptr;
   if (precision != LCQ_FP64 && precision != LCQ_MIXED)
     return fail(ctx, LCQ_ERR_ARG, "unsupported precision");
   if ((int)kernel < 0 || (int)kernel > 2) return fail(ctx, LCQ_ERR_ARG, "unknown kernel");
-  if (!(params->eps > 0.0) || k_im < 0.0 || !isfinite(k_re) || !isfinite(k_im))
-    return fail(ctx, LCQ_ERR_ARG, "eps must be > 0 and Im k >= 0");
+  if (n_phys != nr->n_groups)
+    return fail(ctx, LCQ_ERR_ARG, "one physics record per surface of the near lists");
+  for (int g = 0; g < n_phys; ++g) {
+    const lcq_surface_physics& f = phys[g];
+    if (!(f.eps > 0.0) || f.k_im < 0.0 || !isfinite(f.k_re) || !isfinite(f.k_im) ||
+        !isfinite(f.alpha_re) || !isfinite(f.alpha_im) || !isfinite(f.beta_re) ||
+        !isfinite(f.beta_im))
+      return fail(ctx, LCQ_ERR_ARG, "eps must be > 0, Im k >= 0 and coefficients finite");
+  }
+  const double k_re = phys[0].k_re, k_im = phys[0].k_im;
+  const double alpha_re = phys[0].alpha_re, alpha_im = phys[0].alpha_im;
+  const double beta_re = phys[0].beta_re, beta_im = phys[0].beta_im;
+  const double eps0 = phys[0].eps;
   if (params->m_max < 2 || params->m_max > kMaxRule || params->leaf_order < 0 ||
       params->leaf_order > kMaxRule || params->self_order < 0 || params->self_order > kMaxGL ||
       params->max_depth < 1 || params->max_depth > 24 || params->n_test_dirs < 0 ||
@@ -627,7 +770,22 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
   CK(dalloc(st, reinterpret_cast<double**>(&In), (size_t)2 * npr * ldI));
   CK(dalloc(st, reinterpret_cast<double**>(&IsS), (size_t)2 * nsf * ldI));
   CK(dalloc(st, reinterpret_cast<double**>(&InS), (size_t)2 * nsf * ldI));
-  Dev dv = make_dev(ctx, nr, c->q, ldI);
+  if (nr->grouped) {
+    std::vector<GroupParams> gp(n_phys);
+    for (int g = 0; g < n_phys; ++g) {
+      const lcq_surface_physics& f = phys[g];
+      gp[g].kp = make_kernel_params((int)kernel, f.k_re, f.k_im, f.alpha_re, f.alpha_im, f.beta_re,
+                                    f.beta_im);
+      gp[g].eps = f.eps;
+      gp[g].eps_ad = f.eps * params->eps_loosen;
+      gp[g].self_order = params->self_order > 0 ? params->self_order : default_self_order(f.eps);
+    }
+    CK(dalloc(st, &c->grp, gp.size()));
+    CK(cudaMemcpyAsync(c->grp, gp.data(), gp.size() * sizeof(GroupParams), cudaMemcpyHostToDevice,
+                       st));
+    c->grp_h = gp;
+  }
+  Dev dv = make_dev(ctx, nr, c->q, ldI, c->grp);
 
   CK(cudaEventRecord(ctx->ev[2], st));
   // 1. far order q_j and annulus order (Sec. 4.2, Eq. qj)
@@ -636,7 +794,7 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
   CK(dalloc(st, &fscr, (size_t)fgrid * 2 * kMaxTestPts * kMaxBasis * 2));
   for (int d = 1; d <= kMaxDeg; ++d) {
     if (!nr->plist_count[d]) continue;
-    launch_farorder(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, kp, params->eps, params->m_max,
+    launch_farorder(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, kp, eps0, params->m_max,
                     ctx->deg[d].normV, ddirs, ndirs, fscr, fgrid, c->q, c->q_near);
   }
   CK(cudaGetLastError());
@@ -673,7 +831,7 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
     for (int d = 1; d <= kMaxDeg; ++d) {
       if (!nr->ad_count[d]) continue;
       launch_adaptive(d, lc, nr->ad_list_dev[d], nr->ad_count[d], dv, kp,
-                      params->eps * params->eps_loosen, ctx->deg[d].normV, params->leaf_order,
+                      eps0 * params->eps_loosen, ctx->deg[d].normV, params->leaf_order,
                       params->max_depth, Is, In, c->leaves, ctx->work, stride, (int)A, levels, agrid,
                       ctx->d_status, ctx->d_sched + d, precision == LCQ_MIXED ? 2.0 : 0.0);
     }
@@ -681,7 +839,7 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
   }
   CK(cudaEventRecord(ctx->ev[5], st));
   // 5. self weights (Sec. 4, Eq. errestself)
-  const int sorder = params->self_order > 0 ? params->self_order : default_self_order(params->eps);
+  const int sorder = params->self_order > 0 ? params->self_order : default_self_order(eps0);
   if (nr->n_self > 0)
     for (int d = 1; d <= kMaxDeg; ++d) {
       if (!nr->plist_count[d]) continue;
@@ -709,6 +867,28 @@ lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
   return LCQ_OK;
 }
 
+lcq_status lcq_gen_corrections(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* nr,
+                               lcq_kernel kernel, double k_re, double k_im, double alpha_re,
+                               double alpha_im, double beta_re, double beta_im,
+                               lcq_precision precision, const lcq_params* params, lcq_corr** out) {
+  (void)surf;
+  if (!params) return fail(ctx, LCQ_ERR_ARG, "null argument");
+  if (nr && nr->grouped)
+    return fail(ctx, LCQ_ERR_ARG, "near lists of a batch: use lcq_gen_corrections_batched");
+  const lcq_surface_physics f{k_re, k_im, alpha_re, alpha_im, beta_re, beta_im, params->eps};
+  return gen_impl(ctx, nr, kernel, 1, &f, precision, params, out);
+}
+
+lcq_status lcq_gen_corrections_batched(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* nr,
+                                       lcq_kernel kernel, int n_surfaces,
+                                       const lcq_surface_physics* physics, lcq_precision precision,
+                                       const lcq_params* params, lcq_corr** out) {
+  (void)surf;
+  if (nr && !nr->grouped)
+    return fail(ctx, LCQ_ERR_ARG, "near lists were not built by lcq_build_near_lists_batched");
+  return gen_impl(ctx, nr, kernel, n_surfaces, physics, precision, params, out);
+}
+
 static lcq_status ensure_q_host(lcq_ctx* ctx, lcq_corr* c) {
   if (!c->q_h.empty()) return LCQ_OK;
   CK(cudaSetDevice(c->device));
@@ -726,6 +906,14 @@ static lcq_status ensure_q_host(lcq_ctx* ctx, lcq_corr* c) {
   CK(dalloc(c->stream, &c->src_off, c->n_patches + 1));
   CK(cudaMemcpyAsync(c->src_off, off.data(), (c->n_patches + 1) * 8, cudaMemcpyHostToDevice,
                      c->stream));
+  if (c->grp) {
+    const lcq_near* nr = c->near;
+    c->gsrc_h.resize(nr->n_groups + 1);
+    for (int g = 0; g <= nr->n_groups; ++g) c->gsrc_h[g] = off[nr->gpatch_off[g]];
+    CK(dalloc(c->stream, &c->gsrc, c->gsrc_h.size()));
+    CK(cudaMemcpyAsync(c->gsrc, c->gsrc_h.data(), c->gsrc_h.size() * 8, cudaMemcpyHostToDevice,
+                       c->stream));
+  }
   return LCQ_OK;
 }
 
@@ -778,7 +966,7 @@ static lcq_status apply_impl(lcq_ctx* ctx, const lcq_near* nr, const lcq_corr* c
   cudaStream_t st = ctx->stream;
   long long napply = 0;
   LaunchCommon lc{st, ctx->num_sms, &napply};
-  Dev dv = make_dev(ctx, nr, c->q, nr->n_max);
+  Dev dv = make_dev(ctx, nr, c->q, nr->n_max, c->grp);
   double* src;
   CK(dalloc(st, &src, (size_t)9 * std::max<int64_t>(c->n_over, 1)));
   for (int d = 1; d <= kMaxDeg; ++d) {
@@ -787,7 +975,7 @@ static lcq_status apply_impl(lcq_ctx* ctx, const lcq_near* nr, const lcq_corr* c
                    c->src_off, sigma, src, c->n_over);
   }
   launch_far_sum(lc, nr->tgt, nr->n_targets, src, c->n_over, c->kp, nr->tgt_patch, c->src_off,
-                 out);
+                 c->grp ? nr->tgroup : nullptr, c->grp, c->gsrc, out);
   launch_csr_apply(lc, nr->row_ptr, nr->col, c->val, sigma, nr->tnode, nr->n_targets, jump, out);
   CK(cudaGetLastError());
   dfree(st, src);
@@ -821,6 +1009,8 @@ void lcq_corr_destroy(lcq_corr* c) {
   dfree(c->stream, c->q_near);
   dfree(c->stream, c->leaves);
   dfree(c->stream, c->src_off);
+  dfree(c->stream, c->grp);
+  dfree(c->stream, c->gsrc);
   cudaGetLastError();
   delete c;
 }

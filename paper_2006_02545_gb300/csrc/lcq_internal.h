@@ -25,6 +25,7 @@ enum : int {
   kStCapacity = 2,
   kStDegenerate = 4,
   kStNonFinite = 8,
+  kStBadGroup = 16,
 };
 
 // Kernel parameters (Sec. 3): K = alpha D + beta S for CFIE.
@@ -50,6 +51,16 @@ inline KernelParams make_kernel_params(int kind, double kr, double ki, double ar
   }
   return kp;
 }
+
+// Physics of one independent surface of a batch (patches of a contiguous range): kernel,
+// far-order tolerance eps, adaptive tolerance eps * eps_loosen, self-rule order.
+struct GroupParams {
+  KernelParams kp;
+  double eps;
+  double eps_ad;
+  int self_order;
+  int pad;
+};
 
 // Per-degree reference tables uploaded to the device (built on the host).
 struct DegTables {
@@ -148,6 +159,12 @@ struct lcq_near {
   int* plist_dev[lcq::kMaxDeg + 1] = {nullptr};
   int ad_count[lcq::kMaxDeg + 1] = {0};       // patches with adaptive targets, by degree,
   int* ad_list_dev[lcq::kMaxDeg + 1] = {nullptr};  // most adaptive targets first
+  // batches of independent surfaces (n_groups > 1 or built by the batched entry point)
+  int n_groups = 1;
+  bool grouped = false;
+  std::vector<int64_t> gpatch_off;  // [n_groups+1] patch range of each surface
+  int32_t* pgroup = nullptr;        // [P] surface of each patch
+  int32_t* tgroup = nullptr;        // [NT] surface of each target
 };
 
 struct lcq_corr {
@@ -163,4 +180,8 @@ struct lcq_corr {
   int32_t* leaves = nullptr;     // [n_pairs]
   int64_t* src_off = nullptr;    // [P+1] oversampled source offsets (apply)
   std::vector<int32_t> q_h;
+  lcq::GroupParams* grp = nullptr;  // [n_groups] per-surface physics (batched), else null
+  std::vector<lcq::GroupParams> grp_h;
+  int64_t* gsrc = nullptr;          // [n_groups+1] oversampled source range of each surface
+  std::vector<int64_t> gsrc_h;
 };

@@ -1,7 +1,7 @@
 // CUDA kernels of the correction path (sm_103a).  FP64 throughout.
 //
 //   k_geom         chart coefficients, centroid, radius, d_j        (Sec. 3.2, Sec. 4)
-//   k_row_* /k_patch_*  near lists both ways, deterministic order   (Sec. 4 N_eta, Sec. 5.2)
+//   (near lists: lcq_nearlist.cu)
 //   k_farorder     far order q_j and annulus order                  (Sec. 4.2, Eq. qj)
 //   k_rule_moments smooth-rule / annulus moments for many targets    (Sec. 4.2, Remark on eta_1)
 //   k_adaptive     adaptive subdivision over a per-patch union tree  (Sec. 4.3)
@@ -60,6 +60,11 @@ __device__ __forceinline__ int block_flag_scan(int flag, int* sm, int* total) {
   __syncthreads();
   *total = sm[32];
   return sm[warp] + inwarp;
+}
+
+// Kernel of patch j: its surface's in a batch of independent surfaces, else the launch's.
+__device__ __forceinline__ KernelParams patch_kp(const Dev& dv, int j, const KernelParams& kp) {
+  return dv.pgroup ? dv.grp[dv.pgroup[j]].kp : kp;
 }
 
 __device__ __forceinline__ double eta_default(int d) {
@@ -191,200 +196,6 @@ __global__ void k_tgt_patch(const double* __restrict__ tgt, const int64_t* __res
     }
     tpatch[t] = (int32_t)lo;
     tlnode[t] = (int32_t)(nd - node_off[lo]);
-  }
-}
-
-struct NearView {
-  const double* tgt;
-  int64_t NT;
-  const double* cen;
-  const double* rad;
-  const double* eta;
-  const double* eta1;
-};
-
-// Near predicate of Sec. 4: |x - c_j|^2 <= (eta R_j)^2, t not on patch j.
-__device__ __forceinline__ bool is_near(const NearView& v, int64_t t, int j, double* d2out) {
-  const double d0 = v.tgt[t] - v.cen[3 * j], d1 = v.tgt[v.NT + t] - v.cen[3 * j + 1],
-               d2 = v.tgt[2 * v.NT + t] - v.cen[3 * j + 2];
-  const double d = d0 * d0 + d1 * d1 + d2 * d2;
-  const double r = v.eta[j] * v.rad[j];
-  *d2out = d;
-  return d <= r * r;
-}
-
-// Warp per target: number of patches in row t (near patches and the own patch) and entries.
-__global__ void k_row_count(NearView v, const int32_t* __restrict__ tpatch, int64_t P,
-                            const int32_t* __restrict__ deg, int64_t* __restrict__ row_np,
-                            int64_t* __restrict__ row_nnz) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < v.NT; t += warps) {
-    const int tp = tpatch[t];
-    long long cnt = 0, nnz = 0;
-    for (int64_t j0 = 0; j0 < P; j0 += 32) {
-      const int j = (int)(j0 + lane);
-      if (j < P) {
-        double d2;
-        const bool in = (j == tp) || is_near(v, t, j, &d2);
-        if (in) {
-          cnt += 1;
-          nnz += (deg[j] + 1) * (deg[j] + 2) / 2;
-        }
-      }
-    }
-    cnt = warp_sum_ll(cnt);
-    nnz = warp_sum_ll(nnz);
-    if (lane == 0) {
-      row_np[t] = cnt;
-      row_nnz[t] = nnz;
-    }
-  }
-}
-
-__global__ void k_row_fill(NearView v, const int32_t* __restrict__ tpatch, int64_t P,
-                           const int32_t* __restrict__ deg, const int64_t* __restrict__ node_off,
-                           const int64_t* __restrict__ rowp_ptr, const int64_t* __restrict__ row_ptr,
-                           int32_t* __restrict__ rowp_patch, int64_t* __restrict__ rowp_off,
-                           int32_t* __restrict__ col) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < v.NT; t += warps) {
-    const int tp = tpatch[t];
-    int64_t k = rowp_ptr[t];
-    int64_t eoff = 0;
-    const int64_t rbase = row_ptr[t];
-    for (int64_t j0 = 0; j0 < P; j0 += 32) {
-      const int j = (int)(j0 + lane);
-      bool in = false;
-      if (j < P) {
-        double d2;
-        in = (j == tp) || is_near(v, t, j, &d2);
-      }
-      unsigned bal = __ballot_sync(0xffffffffu, in);
-      while (bal) {
-        const int b = __ffs(bal) - 1;
-        bal &= bal - 1u;
-        const int jj = (int)(j0 + b);
-        const int nj = (deg[jj] + 1) * (deg[jj] + 2) / 2;
-        if (lane == 0) {
-          rowp_patch[k] = jj;
-          rowp_off[k] = eoff;
-        }
-        const int64_t nb = node_off[jj];
-        for (int l = lane; l < nj; l += 32) col[rbase + eoff + l] = (int32_t)(nb + l);
-        ++k;
-        eoff += nj;
-      }
-    }
-  }
-}
-
-// Block per patch: near pairs, adaptive pairs and self targets of patch j.
-__global__ void k_patch_count(NearView v, const int32_t* __restrict__ tpatch, int64_t P,
-                              int64_t* __restrict__ npair, int64_t* __restrict__ nad,
-                              int64_t* __restrict__ nself) {
-  __shared__ long long red[3][kThreads / 32];
-  for (int64_t j = blockIdx.x; j < P; j += gridDim.x) {
-    long long a = 0, b = 0, c = 0;
-    for (int64_t t = threadIdx.x; t < v.NT; t += blockDim.x) {
-      double d2;
-      const int tp = tpatch[t];
-      if (tp == (int)j) {
-        ++c;
-      } else if (is_near(v, t, (int)j, &d2)) {
-        ++a;
-        const double r1 = v.eta1[j] * v.rad[j];
-        if (d2 <= r1 * r1) ++b;
-      }
-    }
-    a = warp_sum_ll(a);
-    b = warp_sum_ll(b);
-    c = warp_sum_ll(c);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) {
-      red[0][threadIdx.x >> 5] = a;
-      red[1][threadIdx.x >> 5] = b;
-      red[2][threadIdx.x >> 5] = c;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      long long s0 = 0, s1 = 0, s2 = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        s0 += red[0][w];
-        s1 += red[1][w];
-        s2 += red[2][w];
-      }
-      npair[j] = s0;
-      nad[j] = s1;
-      nself[j] = s2;
-    }
-  }
-}
-
-__device__ __forceinline__ int64_t row_entry(const int64_t* rowp_ptr, const int32_t* rowp_patch,
-                                             const int64_t* rowp_off, const int64_t* row_ptr,
-                                             int64_t t, int j) {
-  int64_t lo = rowp_ptr[t], hi = rowp_ptr[t + 1] - 1;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) / 2;
-    if (rowp_patch[mid] < j) lo = mid + 1; else hi = mid;
-  }
-  return row_ptr[t] + rowp_off[lo];
-}
-
-__global__ void k_patch_fill(NearView v, const int32_t* __restrict__ tpatch, int64_t P,
-                             const int64_t* __restrict__ pair_ptr, const int64_t* __restrict__ ad_ptr,
-                             const int64_t* __restrict__ an_ptr, const int64_t* __restrict__ self_ptr,
-                             const int64_t* __restrict__ rowp_ptr, const int32_t* __restrict__ rowp_patch,
-                             const int64_t* __restrict__ rowp_off, const int64_t* __restrict__ row_ptr,
-                             int32_t* __restrict__ pair_tgt, uint8_t* __restrict__ pair_ad,
-                             double* __restrict__ pair_d2, int64_t* __restrict__ pair_csr,
-                             int32_t* __restrict__ ad_pair, int32_t* __restrict__ an_pair,
-                             int32_t* __restrict__ self_tgt, int64_t* __restrict__ self_csr) {
-  __shared__ int sm[33];
-  for (int64_t j = blockIdx.x; j < P; j += gridDim.x) {
-    int64_t pbase = pair_ptr[j], abase = ad_ptr[j], nbase = an_ptr[j], sbase = self_ptr[j];
-    for (int64_t t0 = 0; t0 < v.NT; t0 += blockDim.x) {
-      const int64_t t = t0 + threadIdx.x;
-      bool near = false, ad = false, self = false;
-      double d2 = 0.0;
-      if (t < v.NT) {
-        const int tp = tpatch[t];
-        if (tp == (int)j) {
-          self = true;
-        } else if (is_near(v, t, (int)j, &d2)) {
-          near = true;
-          const double r1 = v.eta1[j] * v.rad[j];
-          ad = d2 <= r1 * r1;
-        }
-      }
-      int tot;
-      const int pos = block_flag_scan(near, sm, &tot);
-      if (near) {
-        const int64_t p = pbase + pos;
-        pair_tgt[p] = (int32_t)t;
-        pair_ad[p] = ad ? 1 : 0;
-        pair_d2[p] = d2;
-        pair_csr[p] = row_entry(rowp_ptr, rowp_patch, rowp_off, row_ptr, t, (int)j);
-      }
-      int tota;
-      const int apos = block_flag_scan(near && ad, sm, &tota);
-      if (near && ad) ad_pair[abase + apos] = (int32_t)(pbase + pos);
-      int totn;
-      const int npos = block_flag_scan(near && !ad, sm, &totn);
-      if (near && !ad) an_pair[nbase + npos] = (int32_t)(pbase + pos);
-      int tots;
-      const int spos = block_flag_scan(self, sm, &tots);
-      if (self) {
-        self_tgt[sbase + spos] = (int32_t)t;
-        self_csr[sbase + spos] = row_entry(rowp_ptr, rowp_patch, rowp_off, row_ptr, t, (int)j);
-      }
-      pbase += tot;
-      abase += tota;
-      nbase += totn;
-      sbase += tots;
-    }
   }
 }
 
@@ -614,12 +425,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
   double* cf = smem;
   SegMap* segs = reinterpret_cast<SegMap*>(cf + C::n * 3);
   double* ws = reinterpret_cast<double*>(segs + 4);
+  __shared__ KernelParams kps;
   for (int b = blockIdx.x; b < count; b += gridDim.x) {
     const int j = plist[b];
     const int m = qv[j];
     __syncthreads();
     load_coef<D>(dv.coef, dv.node_off[j], cf);
-    if (threadIdx.x == 0) segs[0] = seg_T0();
+    if (threadIdx.x == 0) {
+      segs[0] = seg_T0();
+      kps = patch_kp(dv, j, kp);
+    }
     __syncthreads();
     if (m <= 0) continue;
     const double* ru = dv.ru + dv.roff[m];
@@ -631,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
       const int64_t ld = dv.ldI;
       cplx* base = out_pairs + p0 * ld;
       block_moments<D>(cf, ru, rv, rw, m * m, segs, 1, ta, (int)np,
-                       [=] __device__(int i) { return base + (int64_t)i * ld; }, C::n, kp, ws,
+                       [=] __device__(int i) { return base + (int64_t)i * ld; }, C::n, kps, ws,
                        dv.cen + 3 * j);
       (void)out_self;
     } else {
@@ -640,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
       TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl};
       const int64_t ld = dv.ldI;
       block_moments<D>(cf, ru, rv, rw, m * m, segs, 1, ta, (int)na,
-                       [=] __device__(int i) { return out_pairs + (int64_t)pl[i] * ld; }, C::n, kp,
+                       [=] __device__(int i) { return out_pairs + (int64_t)pl[i] * ld; }, C::n, kps,
                        ws, dv.cen + 3 * j);
     }
     if (threadIdx.x == 0) {
@@ -671,6 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
   double* red = pts + 3 * kMaxTestPts;                      // [kThreads/32]
   int* sel = reinterpret_cast<int*>(red + kThreads / 32);   // [2]
   double* ws = reinterpret_cast<double*>(sel + 4);
+  __shared__ KernelParams kps;
   cplx* bufA = scratch + (int64_t)blockIdx.x * 2 * kMaxTestPts * C::n;
   cplx* bufB = bufA + kMaxTestPts * C::n;
   const int m_min = (D + 2) / 2;
@@ -678,10 +494,13 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
     const int j = plist[b];
     __syncthreads();
     load_coef<D>(dv.coef, dv.node_off[j], cf);
-    if (threadIdx.x == 0) segs[0] = seg_T0();
+    if (threadIdx.x == 0) {
+      segs[0] = seg_T0();
+      kps = patch_kp(dv, j, kp);
+    }
     const int64_t p0 = dv.pair_ptr[j], np = dv.pair_ptr[j + 1] - p0;
     const double R = dv.rad[j], c0 = dv.cen[3 * j], c1 = dv.cen[3 * j + 1], c2 = dv.cen[3 * j + 2];
-    const double tol = eps * dv.dj[j] / normV;
+    const double tol = (dv.pgroup ? dv.grp[dv.pgroup[j]].eps : eps) * dv.dj[j] / normV;
     for (int pass = 0; pass < 2; ++pass) {
       // test points (Sec. 4.2): pass 0 = far order, pass 1 = annulus order
       __syncthreads();
@@ -769,7 +588,7 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
       {
         const double* ru = dv.ru + dv.roff[m];
         block_moments<D>(cf, ru, dv.rv + dv.roff[m], dv.rw + dv.roff[m], m * m, segs, 1, ta, F,
-                         [=] __device__(int i) { return bufA + (int64_t)i * C::n; }, C::n, kp, ws,
+                         [=] __device__(int i) { return bufA + (int64_t)i * C::n; }, C::n, kps, ws,
                          dv.cen + 3 * j);
       }
       cplx* A = bufA;
@@ -778,7 +597,7 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
         const int m1 = m + 1;
         block_moments<D>(cf, dv.ru + dv.roff[m1], dv.rv + dv.roff[m1], dv.rw + dv.roff[m1], m1 * m1,
                          segs, 1, ta, F, [=] __device__(int i) { return Bf + (int64_t)i * C::n; },
-                         C::n, kp, ws, dv.cen + 3 * j);
+                         C::n, kps, ws, dv.cen + 3 * j);
         __syncthreads();
         // max over points of the 2-norm of the difference
         double e = 0.0;
@@ -864,6 +683,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
       (reinterpret_cast<uintptr_t>(cnt + wsd.levels) + 7) & ~static_cast<uintptr_t>(7));
   long long my_tests = 0, my_nodes = 0, my_tree = 0;
   __shared__ int next_b;
+  __shared__ KernelParams kps;
 
   for (;;) {
     __syncthreads();
@@ -884,11 +704,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
     const double* ru = dv.ru + dv.roff[m];
     const double* rv = dv.rv + dv.roff[m];
     const double* rw = dv.rw + dv.roff[m];
-    const double tol0 = eps * dv.dj[j] / normV;
+    const double tol0 = (dv.pgroup ? dv.grp[dv.pgroup[j]].eps_ad : eps) * dv.dj[j] / normV;
     const double Rj = dv.rad[j];
     const int32_t* apairs = dv.ad_pair + a0;
     __syncthreads();
     load_coef<D>(dv.coef, dv.node_off[j], cf);
+    if (threadIdx.x == 0) kps = patch_kp(dv, j, kp);  // read after block_moments' barrier
     // root: level 0 block holds all targets with I_T0 in slot c = 0
     for (int e = threadIdx.x; e < A * n; e += blockDim.x) {
       const int i = e / n, nm = e - i * n;
@@ -907,7 +728,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
     if (leaf_order > 0) {
       TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, apairs};
       block_moments<D>(cf, ru, rv, rw, Q, segs, 1, ta, A,
-                       [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, 4 * n, kp, ws,
+                       [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, 4 * n, kps, ws,
                        dv.cen + 3 * j);
     }
     // DFS stack entries: level (8 bits) | child (2 bits) | path (2 bits per level) << 16
@@ -965,7 +786,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
       // children moments of every target in S
       TgtAdaptive ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, ST};
       block_moments<D, true>(cf, ru, rv, rw, Q, segs, 4, ta, S,
-                             [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, 4 * n, kp,
+                             [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, 4 * n, kps,
                              ws, dv.cen + 3 * j, Rj, tmpE, mix);
       __syncthreads();
       my_tests += S;
@@ -1084,11 +905,8 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
   __shared__ double P[2];
   __shared__ int nseg, total;
   __shared__ cplx red[4][n];
-  const int ns = order, nt = order;
-  const double* glx_s = dv.gl_x + dv.gl_off[ns];
-  const double* glw_s = dv.gl_w + dv.gl_off[ns];
-  const double* glx_t = dv.gl_x + dv.gl_off[nt];
-  const double* glw_t = dv.gl_w + dv.gl_off[nt];
+  __shared__ KernelParams kps;
+  __shared__ int ord;
   long long my_nodes = 0;
   for (int64_t s = blockIdx.x; s < dv.n_self; s += gridDim.x) {
     const int t = dv.self_tgt[s];
@@ -1097,7 +915,16 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
     const int i = dv.tlnode[t];
     __syncthreads();
     load_coef<D>(dv.coef, dv.node_off[j], cf);
+    if (threadIdx.x == 0) {
+      kps = patch_kp(dv, j, kp);
+      ord = dv.pgroup ? dv.grp[dv.pgroup[j]].self_order : order;
+    }
     __syncthreads();
+    const int ns = ord, nt = ord;
+    const double* glx_s = dv.gl_x + dv.gl_off[ns];
+    const double* glw_s = dv.gl_w + dv.gl_off[ns];
+    const double* glx_t = dv.gl_x + dv.gl_off[nt];
+    const double* glw_t = dv.gl_w + dv.gl_off[nt];
     if (threadIdx.x == 0) {
       const double pu = dv.nodes_uv[D][i], pv = dv.nodes_uv[D][n + i];
       P[0] = pu;
@@ -1178,7 +1005,7 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
       kw_delta_geometry<D>(P[0], P[1], du, dvv, cf, dX, Xu, Xv);
       cross3(Xu, Xv, Nn);
       const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
-      const cplx gk = kernel_eval(kp, 0.0, 0.0, 0.0, dX[0], dX[1], dX[2], Nn[0] * w, Nn[1] * w,
+      const cplx gk = kernel_eval(kps, 0.0, 0.0, 0.0, dX[0], dX[1], dX[2], Nn[0] * w, Nn[1] * w,
                                   Nn[2] * w, J * w);
       kw_accumulate<D>(u, v, gk, acc);
     }
@@ -1305,17 +1132,28 @@ __global__ void k_far_src(const int* __restrict__ plist, int count, Dev dv,
 // Direct far sum over all oversampled sources, one thread per target (tiles of sources
 // staged through shared memory).
 // The sources of an on-surface target's own patch are skipped (their contribution is
-// carried entirely by the self correction).
+// carried entirely by the self correction).  In a batch of independent surfaces a target
+// sums only its own surface's sources [gsrc[g], gsrc[g+1]) with that surface's kernel.
 __global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__ tgt, int64_t NT,
                                                       const double* __restrict__ src, int64_t n_over,
                                                       const KernelParams kp,
                                                       const int32_t* __restrict__ tpatch,
                                                       const int64_t* __restrict__ src_off,
+                                                      const int32_t* __restrict__ tgroup,
+                                                      const GroupParams* __restrict__ grp,
+                                                      const int64_t* __restrict__ gsrc,
                                                       cplx* __restrict__ out) {
   __shared__ double s[9][kThreads];
+  __shared__ unsigned long long blo, bhi;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double x0 = 0, x1 = 0, x2 = 0;
-  int64_t skip0 = -1, skip1 = -1;
+  int64_t skip0 = -1, skip1 = -1, lo = 0, hi = 0;
+  KernelParams kt = kp;
+  if (threadIdx.x == 0) {
+    blo = ~0ull;
+    bhi = 0ull;
+  }
+  __syncthreads();
   if (t < NT) {
     x0 = tgt[t];
     x1 = tgt[NT + t];
@@ -1325,19 +1163,30 @@ __global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__
       skip0 = src_off[tp];
       skip1 = src_off[tp + 1];
     }
+    hi = n_over;
+    if (tgroup) {
+      const int g = tgroup[t];
+      kt = grp[g].kp;
+      lo = gsrc[g];
+      hi = gsrc[g + 1];
+    }
+    atomicMin(&blo, (unsigned long long)lo);
+    atomicMax(&bhi, (unsigned long long)hi);
   }
+  __syncthreads();
+  const int64_t b0 = (int64_t)blo, b1 = (int64_t)bhi;
   double re = 0.0, im = 0.0;
-  for (int64_t s0 = 0; s0 < n_over; s0 += kThreads) {
+  for (int64_t s0 = b0; s0 < b1; s0 += kThreads) {
     __syncthreads();
     const int64_t q = s0 + threadIdx.x;
-    for (int c = 0; c < 9; ++c) s[c][threadIdx.x] = q < n_over ? src[c * n_over + q] : 0.0;
+    for (int c = 0; c < 9; ++c) s[c][threadIdx.x] = q < b1 ? src[c * n_over + q] : 0.0;
     __syncthreads();
-    const int cnt = (int)min((int64_t)kThreads, n_over - s0);
+    const int cnt = (int)min((int64_t)kThreads, b1 - s0);
     if (t < NT)
       for (int k = 0; k < cnt; ++k) {
         const int64_t qq = s0 + k;
-        if (qq >= skip0 && qq < skip1) continue;
-        const cplx g = kernel_eval(kp, x0, x1, x2, s[0][k], s[1][k], s[2][k], s[3][k], s[4][k],
+        if (qq < lo || qq >= hi || (qq >= skip0 && qq < skip1)) continue;
+        const cplx g = kernel_eval(kt, x0, x1, x2, s[0][k], s[1][k], s[2][k], s[3][k], s[4][k],
                                    s[5][k], s[6][k]);
         re = fma(g.re, s[7][k], re);
         re = fma(-g.im, s[8][k], re);
@@ -1528,41 +1377,6 @@ void launch_tgt_patch(const LaunchCommon& lc, const double* tgt, const int64_t* 
   k_tgt_patch<<<g, 256, 0, lc.stream>>>(tgt, tnode, NT, node_off, P, N, tpatch, tlnode, status);
 }
 
-static NearView nv(const NearArgs& a) { return {a.tgt, a.NT, a.cen, a.rad, a.eta, a.eta1}; }
-
-void launch_row_count(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
-                      const int32_t* deg, int64_t* row_np, int64_t* row_nnz) {
-  const int g = lc.num_sms * 8;
-  ++*lc.launches;
-  k_row_count<<<g, 256, 0, lc.stream>>>(nv(a), tpatch, P, deg, row_np, row_nnz);
-}
-void launch_row_fill(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
-                     const int32_t* deg, const int64_t* node_off, const int64_t* rowp_ptr,
-                     const int64_t* row_ptr, int32_t* rowp_patch, int64_t* rowp_off, int32_t* col) {
-  const int g = lc.num_sms * 8;
-  ++*lc.launches;
-  k_row_fill<<<g, 256, 0, lc.stream>>>(nv(a), tpatch, P, deg, node_off, rowp_ptr, row_ptr,
-                                       rowp_patch, rowp_off, col);
-}
-void launch_patch_count(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
-                        int64_t* npair, int64_t* nad, int64_t* nself) {
-  const int g = (int)(P < lc.num_sms * 8 ? P : lc.num_sms * 8);
-  ++*lc.launches;
-  k_patch_count<<<g, 256, 0, lc.stream>>>(nv(a), tpatch, P, npair, nad, nself);
-}
-void launch_patch_fill(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
-                       const int64_t* pair_ptr, const int64_t* ad_ptr, const int64_t* an_ptr,
-                       const int64_t* self_ptr, const int64_t* rowp_ptr, const int32_t* rowp_patch,
-                       const int64_t* rowp_off, const int64_t* row_ptr, int32_t* pair_tgt,
-                       uint8_t* pair_ad, double* pair_d2, int64_t* pair_csr, int32_t* ad_pair,
-                       int32_t* an_pair, int32_t* self_tgt, int64_t* self_csr) {
-  const int g = (int)(P < lc.num_sms * 8 ? P : lc.num_sms * 8);
-  ++*lc.launches;
-  k_patch_fill<<<g, 256, 0, lc.stream>>>(nv(a), tpatch, P, pair_ptr, ad_ptr, an_ptr, self_ptr,
-                                         rowp_ptr, rowp_patch, rowp_off, row_ptr, pair_tgt, pair_ad,
-                                         pair_d2, pair_csr, ad_pair, an_pair, self_tgt, self_csr);
-}
-
 // out[i] = sum_{k<i} in[i]; needs scratch of >= 2 * ceil(n/1024) + 2048 int64 elements.
 void launch_scan(const LaunchCommon& lc, const int64_t* in, int64_t* out, int64_t n,
                  int64_t* scratch) {
@@ -1612,12 +1426,13 @@ bool launch_far_src(int d, const LaunchCommon& lc, const int* plist, int count, 
 }
 void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const double* src,
                     int64_t n_over, const KernelParams& kp, const int32_t* tpatch,
-                    const int64_t* src_off, void* out) {
+                    const int64_t* src_off, const int32_t* tgroup, const GroupParams* grp,
+                    const int64_t* gsrc, void* out) {
   const int64_t g = (NT + kThreads - 1) / kThreads;
   if (g <= 0) return;
   ++*lc.launches;
   k_far_sum<<<(unsigned)g, kThreads, 0, lc.stream>>>(tgt, NT, src, n_over, kp, tpatch, src_off,
-                                                     (cplx*)out);
+                                                     tgroup, grp, gsrc, (cplx*)out);
 }
 void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int32_t* col,
                       const double* val, const void* sigma, const int64_t* tnode, int64_t NT,

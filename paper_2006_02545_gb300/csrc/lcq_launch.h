@@ -40,6 +40,10 @@ struct Dev {
   const int64_t* self_csr;
   int64_t n_self;
   const int32_t* q;
+  // batches of independent surfaces: surface of each patch and its physics (null: one
+  // surface whose physics come from the launch arguments)
+  const int32_t* pgroup;
+  const GroupParams* grp;
   // tables
   const int* roff;
   const double* ru;
@@ -61,6 +65,8 @@ struct NearArgs {
   const double* rad;
   const double* eta;
   const double* eta1;
+  const int32_t* pgroup;  // null: one surface
+  const int32_t* tgroup;
 };
 
 cudaError_t upload_constants(cudaStream_t st);
@@ -72,17 +78,36 @@ bool launch_geom(int d, const LaunchCommon& lc, const int* plist, int count, con
 void launch_tgt_patch(const LaunchCommon& lc, const double* tgt, const int64_t* tnode, int64_t NT,
                       const int64_t* node_off, int64_t P, int64_t N, int32_t* tpatch,
                       int32_t* tlnode, int* status);
-void launch_row_count(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
+// Uniform grid over patch centroids: cell (i, j, k) holds centroids c with
+// floor((c - lo) * inv_h) = (i, j, k); 1 / inv_h >= max eta_j R_j.
+struct GridSpec {
+  double lo[3];
+  double inv_h;
+  int nx, ny, nz;
+};
+// Surface of each patch (from the patch ranges) and of each target (kStBadGroup on a
+// caller's value outside [0, G)).
+void launch_groups(const LaunchCommon& lc, int64_t NT, const int32_t* tpatch,
+                   const int64_t* gpatch_off, int G, const int32_t* user, int32_t* pgroup,
+                   int32_t* tgroup, int* status);
+void launch_grid_bounds(const LaunchCommon& lc, const NearArgs& a, int64_t P, double* out7);
+void launch_cell_bins(const LaunchCommon& lc, const NearArgs& a, int64_t P, const GridSpec& g,
+                      unsigned long long* cnt, int64_t* cell_ptr, unsigned long long* cursor,
+                      int32_t* cell_patch, int64_t* scan_scratch);
+void launch_row_count(const LaunchCommon& lc, const NearArgs& a, const GridSpec& g,
+                      const int64_t* cell_ptr, const int32_t* cell_patch, const int32_t* tpatch,
                       const int32_t* deg, int64_t* row_np, int64_t* row_nnz);
-void launch_row_fill(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
+void launch_row_fill(const LaunchCommon& lc, const NearArgs& a, const GridSpec& g,
+                     const int64_t* cell_ptr, const int32_t* cell_patch, const int32_t* tpatch,
                      const int32_t* deg, const int64_t* node_off, const int64_t* rowp_ptr,
-                     const int64_t* row_ptr, int32_t* rowp_patch, int64_t* rowp_off, int32_t* col);
-void launch_patch_count(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
-                        int64_t* npair, int64_t* nad, int64_t* nself);
+                     const int64_t* row_ptr, int32_t* tmp, int32_t* rowp_patch, int64_t* rowp_off,
+                     int32_t* col, unsigned long long* npair, unsigned long long* nad,
+                     unsigned long long* nself);
 void launch_patch_fill(const LaunchCommon& lc, const NearArgs& a, const int32_t* tpatch, int64_t P,
                        const int64_t* pair_ptr, const int64_t* ad_ptr, const int64_t* an_ptr,
                        const int64_t* self_ptr, const int64_t* rowp_ptr, const int32_t* rowp_patch,
-                       const int64_t* rowp_off, const int64_t* row_ptr, int32_t* pair_tgt,
+                       const int64_t* rowp_off, const int64_t* row_ptr, unsigned long long* pcur,
+                       unsigned long long* scur, int32_t* ptmp, int32_t* stmp, int32_t* pair_tgt,
                        uint8_t* pair_ad, double* pair_d2, int64_t* pair_csr, int32_t* ad_pair,
                        int32_t* an_pair, int32_t* self_tgt, int64_t* self_csr);
 void launch_scan(const LaunchCommon& lc, const int64_t* in, int64_t* out, int64_t n,
@@ -107,7 +132,8 @@ bool launch_far_src(int d, const LaunchCommon& lc, const int* plist, int count, 
                     double* src, int64_t n_over);
 void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const double* src,
                     int64_t n_over, const KernelParams& kp, const int32_t* tpatch,
-                    const int64_t* src_off, void* out);
+                    const int64_t* src_off, const int32_t* tgroup, const GroupParams* grp,
+                    const int64_t* gsrc, void* out);
 void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int32_t* col,
                       const double* val, const void* sigma, const int64_t* tnode, int64_t NT,
                       double jump, void* out);

@@ -46,6 +46,12 @@ class Params_t(C.Structure):
                 ("test_dirs", C.c_void_p)]
 
 
+class Physics_t(C.Structure):
+    _fields_ = [("k_re", C.c_double), ("k_im", C.c_double), ("alpha_re", C.c_double),
+                ("alpha_im", C.c_double), ("beta_re", C.c_double), ("beta_im", C.c_double),
+                ("eps", C.c_double)]
+
+
 _vp, _i64, _i32, _d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
 _sig = {
     "lcq_params_default": (None, [_vp]),
@@ -53,11 +59,15 @@ _sig = {
     "lcq_destroy": (None, [_vp]),
     "lcq_ref_nodes": (C.c_int, [C.c_int, _vp, _vp, _vp]),
     "lcq_build_near_lists": (C.c_int, [_vp, _vp, _vp, _vp, _i64, _vp, _vp]),
+    "lcq_build_near_lists_batched": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp, _i64, _vp,
+                                               _vp]),
     "lcq_near_info": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "lcq_near_export": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "lcq_near_destroy": (None, [_vp]),
     "lcq_gen_corrections": (C.c_int, [_vp, _vp, _vp, C.c_int, _d, _d, _d, _d, _d, _d, C.c_int,
                                       _vp, _vp]),
+    "lcq_gen_corrections_batched": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp, C.c_int, _vp,
+                                              _vp]),
     "lcq_corr_info": (C.c_int, [_vp, _vp, _vp, _vp]),
     "lcq_corr_export": (C.c_int, [_vp, _vp, _vp, _vp]),
     "lcq_corr_export_stats": (C.c_int, [_vp, _vp, _vp, _vp]),
@@ -215,6 +225,23 @@ def build_near_lists(ctx: Context, surf: DeviceSurface, tgt_xyz, tgt_node, prm) 
     return NearLists(ctx, h, (surf, tgt_xyz, tgt_node))
 
 
+def build_near_lists_batched(ctx: Context, surf: DeviceSurface, surface_patch_off, tgt_xyz,
+                             tgt_node, prm, tgt_surface=None) -> NearLists:
+    """Near lists of a batch of independent surfaces: surface s owns patches
+    [surface_patch_off[s], surface_patch_off[s+1]); targets pair only with their own
+    surface (off-surface targets: tgt_surface, device int32, or surface 0)."""
+    off = np.ascontiguousarray(surface_patch_off, dtype=np.int64)
+    nt = int(tgt_node.shape[0])
+    h = C.c_void_p()
+    ctx.check(_lib.lcq_build_near_lists_batched(ctx.h, C.byref(surf.s), len(off) - 1, _ptr(off),
+                                                _ptr(tgt_xyz), _ptr(tgt_node), _ptr(tgt_surface),
+                                                nt, C.byref(prm), C.byref(h)),
+              "lcq_build_near_lists_batched")
+    nl = NearLists(ctx, h, (surf, tgt_xyz, tgt_node, tgt_surface, off))
+    nl.n_surfaces = len(off) - 1
+    return nl
+
+
 class Corrections:
     def __init__(self, ctx, h, near, kernel):
         self.ctx, self.h, self.near, self.kernel = ctx, h, near, kernel
@@ -267,6 +294,22 @@ def gen_corrections(ctx: Context, surf: DeviceSurface, near: NearLists, kernel: 
                                        k.imag, alpha.real, alpha.imag, beta.real, beta.imag,
                                        PRECISIONS[precision], C.byref(prm), C.byref(h)),
               "lcq_gen_corrections")
+    return Corrections(ctx, h, near, kernel)
+
+
+def gen_corrections_batched(ctx: Context, surf: DeviceSurface, near: NearLists, kernel: str,
+                            physics, prm, precision: str = "fp64") -> Corrections:
+    """lcq_gen_corrections_batched; physics: one (k, alpha, beta, eps) per surface."""
+    arr = (Physics_t * len(physics))()
+    for i, (k, alpha, beta, eps) in enumerate(physics):
+        k, alpha, beta = complex(k), complex(alpha), complex(beta)
+        arr[i] = Physics_t(k.real, k.imag, alpha.real, alpha.imag, beta.real, beta.imag,
+                           float(eps))
+    h = C.c_void_p()
+    ctx.check(_lib.lcq_gen_corrections_batched(ctx.h, C.byref(surf.s), near.h, KERNELS[kernel],
+                                               len(physics), arr, PRECISIONS[precision],
+                                               C.byref(prm), C.byref(h)),
+              "lcq_gen_corrections_batched")
     return Corrections(ctx, h, near, kernel)
 
 

@@ -296,3 +296,34 @@ def batched_tori(count: int = 64, seed: int = 0, scale: float = 1.0):
         dt = str(rng.choice(["complex64", "complex128"]))
         out.append(dict(n_patches=max(8, int(npat * scale)), deg=deg, k=k, eps=eps, dtype=dt))
     return out
+
+
+def concat_surfaces(parts, shifts=None, name: str = "batch"):
+    """Several surfaces as one Surface, one after another (part i translated by shifts[i]),
+    and the patch range of each part ([n_parts + 1], starting at 0)."""
+    shifts = shifts if shifts is not None else [(0.0, 0.0, 0.0)] * len(parts)
+    deg = np.concatenate([p.deg for p in parts]).astype(np.int32)
+    off = [np.zeros(1, np.int64)]
+    xyz = []
+    for p, sh in zip(parts, shifts):
+        off.append(off[-1][-1] + p.node_off[1:])
+        xyz.append(p.xyz + np.asarray(sh, dtype=np.float64)[:, None])
+    patch_off = np.concatenate([[0], np.cumsum([p.n_patches for p in parts])]).astype(np.int64)
+    return Surface(name, deg, np.concatenate(off), np.ascontiguousarray(np.concatenate(xyz, 1)),
+                   {"kind": "batch", "parts": [p.name for p in parts]}), patch_off
+
+
+def batched_tori_batch(count: int = 64, seed: int = 0, scale: float = 1.0, spacing: float = 8.0):
+    """The batched-tori workload as one concatenated surface: the tori drawn by
+    batched_tori (n_phi = 2 n_theta cells nearest the drawn patch count) on a square
+    lattice `spacing` apart (the tori, of outer radius 3.2, do not touch), their patch
+    ranges, and per torus the CFIE physics (k, alpha=1, beta=-ik, eps) and density dtype."""
+    specs = batched_tori(count, seed, scale)
+    side = int(math.ceil(math.sqrt(count)))
+    parts, shifts, phys = [], [], []
+    for i, sp in enumerate(specs):
+        parts.append(torus_with_patches(sp["n_patches"], sp["deg"]))
+        shifts.append((spacing * (i % side), spacing * (i // side), 0.0))
+        phys.append((sp["k"], 1.0, -1j * sp["k"], sp["eps"]))
+    surf, patch_off = concat_surfaces(parts, shifts, f"tori{count}_seed{seed}_x{scale:g}")
+    return surf, patch_off, phys, [sp["dtype"] for sp in specs]

@@ -240,3 +240,100 @@ def test_mixed_precision_error_stated(ctx, eps):
     oc, uo = run_oracle(s, x, tn, "CFIE", k, eps, alpha=1.0, beta=-1j * k, sigma=g["sigma"])
     rel = np.linalg.norm(g["u"] - uo) / np.linalg.norm(uo)
     assert rel <= max(eps, 1e-7), rel
+
+
+def test_near_lists_grid_uneven_sizes(ctx):
+    """Near lists through the centroid grid on three bodies whose patch radii differ by about
+    an order of magnitude, with on-surface nodes, near-surface points and a cloud of
+    off-surface targets partly far outside every ball: the patch-major lists (ascending
+    targets, adaptive flags), the self counts and the CSR size equal the oracle's all-pairs
+    search."""
+    import torch
+    from oracle import geometry as OG
+    from oracle import nearlist as ON
+    from paper_2006_02545_gb300 import lcq
+    dev = ctx.torch_device
+    a = W.ellipsoid(1, 4, axes=(1.0, 1.2, 0.9))
+    b = W.torus(12, 24, 3)
+    c = W.ellipsoid(6, 2, axes=(0.4, 0.5, 0.6))
+    parts = [(a, (0.0, 0.0, 0.0)), (b, (5.0, 0.0, 0.0)), (c, (0.0, 4.0, 1.0))]
+    deg = np.concatenate([p.deg for p, _ in parts])
+    off = [np.zeros(1, np.int64)]
+    xyz = []
+    for p, sh in parts:
+        off.append(off[-1][-1] + p.node_off[1:])
+        xyz.append(p.xyz + np.array(sh)[:, None])
+    s = W.Surface("three_bodies", deg, np.concatenate(off), np.ascontiguousarray(np.concatenate(xyz, 1)))
+    xs, tns = W.onsurface_targets(s)
+    xr = W.radial_targets(s, 300, 5, 0.002, 0.3, False)
+    rng = np.random.default_rng(11)
+    cloud = rng.uniform([-3, -3, -3], [9, 7, 5], size=(20000, 3)).T
+    far = rng.uniform(-1e3, 1e3, size=(3, 50))
+    x = np.ascontiguousarray(np.concatenate([xs, xr, cloud, far], axis=1))
+    tn = np.concatenate([tns, -np.ones(x.shape[1] - xs.shape[1], np.int64)])
+
+    ds = lcq.DeviceSurface(s.deg, s.node_off, torch.from_numpy(s.xyz).to(dev))
+    near = lcq.build_near_lists(ctx, ds, torch.from_numpy(x).to(dev), torch.from_numpy(tn).to(dev),
+                                lcq.params(1e-6))
+    assert ctx.sync(60000) == 0
+    pp, tg, ad, _, _ = near.export(s.n_patches)
+
+    pats = OG.make_patches(s.deg, s.node_off, s.xyz)
+    cen = np.array([p.c for p in pats])
+    rad = np.array([p.R for p in pats])
+    eta = np.array([OG.default_eta(int(d)) for d in s.deg])
+    tpatch = np.full(x.shape[1], -1, np.int64)
+    tpatch[:xs.shape[1]] = np.searchsorted(s.node_off, tns, side="right") - 1
+    ref = ON.near_lists(cen, rad, eta, np.full(s.n_patches, 1.25), x, tpatch)
+    nb = (s.deg + 1) * (s.deg + 2) // 2
+    nnz = 0
+    for j, (ids, adf, _) in enumerate(ref):
+        assert np.array_equal(tg[pp[j]:pp[j + 1]], ids), j
+        assert np.array_equal(ad[pp[j]:pp[j + 1]].astype(bool), adf), j
+        nnz += (len(ids) + np.count_nonzero(tpatch == j)) * nb[j]
+    assert near.n_self == xs.shape[1] and near.nnz == nnz
+    assert near.n_pairs > 50000
+    near.close()
+
+
+BATCH_PARTS = lambda: [W.torus(3, 6, 3), W.ellipsoid(1, 5, axes=(1.5, 1.2, 1.0)),
+                       W.ellipsoid(1, 4, axes=(0.6, 0.8, 0.9))]
+BATCH_PHYS = [(3.0, 1.0, -3j, 1e-6), (6.5, 1.0, -6.5j, 1e-9), (1.5 + 0.2j, 0.5, -1.5j, 1e-8)]
+
+
+def test_batched_surfaces_parity(ctx):
+    """Three independent surfaces of different degree, wavenumber, CFIE coefficients and
+    tolerance, overlapping in space, generated as one batch: per surface the CSR rows, the
+    far orders and the applied potential equal the oracle run on that surface alone (no
+    near pair and no far source crosses surfaces)."""
+    import torch
+    from paper_2006_02545_gb300 import lcq
+    dev = ctx.torch_device
+    parts = BATCH_PARTS()
+    s, poff = W.concat_surfaces(parts)
+    x, tn = W.onsurface_targets(s)
+    ds = lcq.DeviceSurface(s.deg, s.node_off, torch.from_numpy(s.xyz).to(dev))
+    prm = lcq.params(1e-6, test_dirs=W.test_directions(3))
+    near = lcq.build_near_lists_batched(ctx, ds, poff, torch.from_numpy(x).to(dev),
+                                        torch.from_numpy(tn).to(dev), prm)
+    corr = lcq.gen_corrections_batched(ctx, ds, near, "CFIE", BATCH_PHYS, prm)
+    assert ctx.sync(120000) == 0
+    rp, col, val = corr.export(x.shape[1])
+    q, qn, _ = corr.stats(s.n_patches)
+    sig = W.density(s.n_points, 0)
+    u = lcq.apply_corrected_CFIE(ctx, ds, near, corr, torch.from_numpy(sig).to(dev),
+                                 x.shape[1]).cpu().numpy()
+    assert ctx.sync(120000) == 0
+    for i, (p, (k, a, b, eps)) in enumerate(zip(parts, BATCH_PHYS)):
+        n0, n1 = s.node_off[poff[i]], s.node_off[poff[i + 1]]
+        xp, tnp = W.onsurface_targets(p)
+        oc, uo = run_oracle(p, xp, tnp, "CFIE", k, eps, alpha=a, beta=b, sigma=sig[n0:n1])
+        r = rp[n0:n1 + 1] - rp[n0]
+        assert np.array_equal(r, oc.row_ptr), i
+        assert np.array_equal(col[rp[n0]:rp[n1]] - n0, oc.col), i
+        assert np.array_equal(q[poff[i]:poff[i + 1]], oc.q), i
+        assert np.array_equal(qn[poff[i]:poff[i + 1]], oc.q_near), i
+        rel = np.linalg.norm(u[n0:n1] - uo) / np.linalg.norm(uo)
+        assert rel <= APPLY_TOL, (i, rel)
+    corr.close()
+    near.close()
