@@ -40,6 +40,7 @@ class Params:
     self_order: int = 0          # 0: rules.default_self_order(eps)
     leaf_order: int = 0          # 0: the patch's far order q_j
     test_dirs: np.ndarray | None = None
+    record_leaves: bool = False  # keep each adaptive pair's leaf triangles (adjoint)
 
 
 def fibonacci_dirs(n: int = 15) -> np.ndarray:
@@ -127,9 +128,12 @@ def gen_corrections(deg, node_off, xyz, tgt_xyz, tgt_node, kind, k, alpha=1.0, b
         for t, ad in zip(ids, adaptive):
             x = tgt_xyz[:, t]
             if ad:
-                I, st = quadrature.adaptive_moments(cache, x, kern, tol0, p.max_depth)
+                rec = [] if p.record_leaves else None
+                I, st = quadrature.adaptive_moments(cache, x, kern, tol0, p.max_depth, rec)
                 depth_hit |= st["depth_hit"]
                 st["kind"] = "adaptive"
+                if rec is not None:
+                    st["leaf_tris"] = rec
             else:
                 I = quadrature.rule_moments(pt, x, *an_rule, kern)
                 st = {"kind": "annulus"}

@@ -108,7 +108,7 @@ class LeafCache:
 ROUNDING_FLOOR = 2e-13
 
 
-def adaptive_moments(cache: LeafCache, x, kern, tol0, max_depth):
+def adaptive_moments(cache: LeafCache, x, kern, tol0, max_depth, record=None):
     """Adaptive integration of I_nm(x) over T0 by midpoint subdivision (Sec. 4.3).
 
     A triangle T at level L (|T|/|T0| = 4^-L) is compared with its 4 children;
@@ -120,7 +120,8 @@ def adaptive_moments(cache: LeafCache, x, kern, tol0, max_depth):
     integrands, and the double-layer integrand loses digits to cancellation for
     targets near the tangent plane).  Children at level max_depth are not tested
     further: their sum is accepted and the depth flag set.
-    Returns (I [n], stats dict).
+    Returns (I [n], stats dict).  With `record` (a list), the accepted leaf triangles
+    (the children of every accepted triangle) are appended to it.
     """
     patch = cache.patch
     xr = np.asarray(x) - patch.c
@@ -160,6 +161,8 @@ def adaptive_moments(cache: LeafCache, x, kern, tol0, max_depth):
                 depth_hit = True
             total = total + S
             leaves += 4
+            if record is not None:
+                record.extend(kids)
             max_level = max(max_level, L + 1)
         else:
             for c in range(4):
