@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batched-scale", type=float, default=0.05,
+                    help="patch-count scale of the 64-torus batch variant (0: skip it)")
+    ap.add_argument("--large", action="store_true",
+                    help="also time the 40,000-patch torus (k=20, eps=1e-9), FP64 and mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--s", type=int, default=8, help="icosahedral refinement (1280 patches at 8)")
     ap.add_argument("--leaf-order", type=int, default=0,
@@ -312,6 +316,91 @@ def run_ours(args, rank, world, local_rank):
                                                   np.linalg.norm(ref_u[eps]))
                 variants[key] = rec
 
+    # 64 independent tori in one batched generation against the same surfaces one by one
+    batched = None
+    if not args.no_variants and args.batched_scale > 0:
+        bs, poff, phys, _ = W.batched_tori_batch(64, 0, args.batched_scale)
+        bx, btn = W.onsurface_targets(bs)
+        bds = lcq.DeviceSurface(bs.deg, bs.node_off, torch.from_numpy(bs.xyz).to(dev))
+        bx_d = torch.from_numpy(bx).to(dev)
+        btn_d = torch.from_numpy(btn).to(dev)
+        bp = lcq.params(1e-6, test_dirs=W.test_directions(7))
+        times, st_b = [], 0
+        for it in range(3):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            near = lcq.build_near_lists_batched(ctx, bds, poff, bx_d, btn_d, bp)
+            corr = lcq.gen_corrections_batched(ctx, bds, near, "CFIE", phys, bp)
+            e1.record(stream)
+            st_b = max(st_b, ctx.sync())
+            if it > 0:
+                times.append(e0.elapsed_time(e1))
+                b_launches = ctx.stage_times()[1]
+            corr.close()
+            near.close()
+        one_ms, one_launches = 0.0, 0
+        for i, (k, a, b, eps) in enumerate(phys):
+            n0, n1 = int(bs.node_off[poff[i]]), int(bs.node_off[poff[i + 1]])
+            dsi = lcq.DeviceSurface(bs.deg[poff[i]:poff[i + 1]],
+                                    bs.node_off[poff[i]:poff[i + 1] + 1] - n0, bds.xyz[:, n0:n1].contiguous())
+            xi = bx_d[:, n0:n1].contiguous()
+            ti = btn_d[n0:n1] - n0
+            pi = lcq.params(eps, test_dirs=W.test_directions(7))
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            near = lcq.build_near_lists(ctx, dsi, xi, ti, pi)
+            corr = lcq.gen_corrections(ctx, dsi, near, "CFIE", k, pi, a, b)
+            e1.record(stream)
+            ctx.sync()
+            one_ms += e0.elapsed_time(e1)
+            one_launches += ctx.stage_times()[1]
+            corr.close()
+            near.close()
+        bms = statistics.mean(times)
+        batched = {"workload": f"64 perturbed tori (R=2, r=1), patch counts U[200,5000] x "
+                               f"{args.batched_scale:g}, degree U{{3..8}}, k U[1,20], eps "
+                               f"U{{1e-6,1e-9}}, CFIE D-ikS, seed 0",
+                   "patches": bs.n_patches, "points": bs.n_points,
+                   "value": bs.n_points / (bms / 1e3), "unit": UNIT, "ms_per_step": bms,
+                   "launches_per_step": int(b_launches), "status": st_b,
+                   "one_by_one": {"value": bs.n_points / (one_ms / 1e3), "ms": one_ms,
+                                  "launches": int(one_launches)}}
+        del bds, bx_d, btn_d
+
+    # the 40,000-patch torus (k = 20, eps = 1e-9), FP64 and mixed, one timed step each
+    large = None
+    if args.large:
+        lw = W.torus_cfie_k20(100)
+        ls = lw.surface
+        lds = lcq.DeviceSurface(ls.deg, ls.node_off, torch.from_numpy(ls.xyz).to(dev))
+        lx = torch.from_numpy(lw.tgt_xyz).to(dev)
+        ltn = torch.from_numpy(lw.tgt_node).to(dev)
+        lp = lcq.params(lw.eps, test_dirs=W.test_directions(7))
+        large, vals = {"workload": lw.name, "patches": ls.n_patches, "points": ls.n_points}, {}
+        for prec in ("fp64", "mixed"):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            near = lcq.build_near_lists(ctx, lds, lx, ltn, lp)
+            corr = lcq.gen_corrections(ctx, lds, near, lw.kernel, lw.k, lp, lw.alpha, lw.beta,
+                                       precision=prec)
+            e1.record(stream)
+            st_l = ctx.sync()
+            ms = e0.elapsed_time(e1)
+            vals[prec] = corr.export(ls.n_points)[2].copy()
+            large[prec] = {"value": ls.n_points / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                           "status": st_l, "nnz": near.nnz}
+            corr.close()
+            near.close()
+        large["mixed"]["csr_rel_l2_vs_fp64"] = float(np.linalg.norm(vals["mixed"] - vals["fp64"]) /
+                                                     np.linalg.norm(vals["fp64"]))
+        del vals, lds, lx, ltn
+
     # end to end through the C ABI with host buffers: H2D of inputs, D2H of the CSR
     e2e = None
     if not args.no_e2e:
@@ -391,6 +480,8 @@ def run_ours(args, rank, world, local_rank):
         "stages_ms": dict(zip(["near_lists", "far_order", "smooth_annulus", "adaptive", "self",
                                "v2c"], st_mean)),
         "variants": variants,
+        "batched": batched,
+        "large": large,
         "wall_s_timed_region": t_wall,
     }
     print(json.dumps(line), flush=True)

@@ -216,6 +216,28 @@ lcq_status lcq_apply_corrected_CFIE(lcq_ctx* ctx, const lcq_surface* surf, const
                                     const lcq_corr* corr, const double* sigma, double jump,
                                     double* out);
 
+/* ---- Adjoint (no counterpart in the paper).  For a real functional L of the
+ * corrected potential u = A(y) sigma with upstream gradient g = dL/d(conj u)
+ * (device complex128 [NT]; PyTorch's convention, dL = Re sum_t conj(g_t) du_t):
+ *
+ * lcq_apply_adjoint: out = A^H g (device complex128 [N]), the density gradient, for the
+ * operator of lcq_apply_corrected_* with the same jump (the far sum transposed per
+ * source, the CSR transposed patch by patch: deterministic, no atomics).
+ *
+ * lcq_shape_gradient: out = dL/dy (device double SoA [3][N]) with respect to the node
+ * coordinates, for the density sigma (device complex128 [N]), differentiating the
+ * discrete method with every discrete choice frozen: near lists, far orders q_j,
+ * annulus orders and refinement trees.  Each (target, patch) pair contributes through
+ * the one rule that defines it (q_j, the annulus rule, or the accepted leaves); the
+ * trees are recomputed by the adaptive kernel in gradient mode, not stored.  Targets
+ * must be off the surface (a near list with self pairs is LCQ_ERR_ARG): on-surface
+ * targets move with the nodes and use the self rules, which this does not cover. */
+lcq_status lcq_apply_adjoint(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                             const lcq_corr* corr, const double* g, double jump, double* out);
+lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                              const lcq_corr* corr, const double* sigma, const double* g,
+                              double* out);
+
 void lcq_corr_destroy(lcq_corr* corr);
 
 /* Wait for the context's stream (polling, at most timeout_ms; < 0 waits

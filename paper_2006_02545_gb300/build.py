@@ -19,8 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblcq.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lcq_kernels.cu", "lcq_nearlist.cu", "lcq_api.cpp", "lcq_tables.cpp",
-           "lcq_noalloc.cu"]
+SOURCES = ["lcq_kernels.cu", "lcq_adjoint.cu", "lcq_nearlist.cu", "lcq_api.cpp",
+           "lcq_tables.cpp", "lcq_noalloc.cu"]
 
 
 def _nvcc() -> str:

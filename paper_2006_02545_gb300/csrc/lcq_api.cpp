@@ -207,6 +207,7 @@ lcq_status lcq_create(lcq_ctx** out, int device, void* cuda_stream) {
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(long long), ctx->stream));
   CK(upload_constants(ctx->stream));
+  CK(upload_constants_adjoint(ctx->stream));
   for (int i = 0; i < 8; ++i) CK(cudaEventCreate(&ctx->ev[i]));
   lcq_status s = ensure_rules(ctx);
   if (s != LCQ_OK) {
@@ -691,6 +692,36 @@ static Dev make_dev(lcq_ctx* ctx, const lcq_near* nr, const int32_t* q, int ldI,
   return dv;
 }
 
+// Per-block workspace of the adaptive kernel (sized by the largest adaptive set and the
+// depth cap) and its grid; grows ctx->work when needed.
+static cudaError_t adaptive_work(lcq_ctx* ctx, const lcq_near* nr, int levels, int64_t* stride_out,
+                                 int* grid_out) {
+  const int64_t A = nr->max_adaptive;
+  const int64_t n = nr->n_max;
+  int64_t stride = A * n * 16 + A * 4 * n * 16 + (int64_t)levels * A * 4 * n * 16 +
+                   (int64_t)levels * A * 4 + 2 * A * 4 + (int64_t)levels * 4 + 8 + A * 4 * 8 + 256;
+  stride = (stride + 255) / 256 * 256;
+  int bps = 1;
+  for (int d = 1; d <= kMaxDeg; ++d)
+    if (nr->ad_count[d]) bps = std::max(bps, adaptive_blocks_per_sm(d));
+  const int agrid = ctx->num_sms * bps;
+  const size_t need = (size_t)stride * agrid;
+  if (ctx->work_bytes < need) {
+    if (ctx->work) {
+      cudaError_t e = cudaFreeAsync(ctx->work, ctx->stream);
+      if (e != cudaSuccess) return e;
+    }
+    ctx->work = nullptr;
+    ctx->work_bytes = 0;
+    cudaError_t e = cudaMallocAsync(&ctx->work, need, ctx->stream);
+    if (e != cudaSuccess) return e;
+    ctx->work_bytes = need;
+  }
+  *stride_out = stride;
+  *grid_out = agrid;
+  return cudaSuccess;
+}
+
 static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, int n_phys,
                            const lcq_surface_physics* phys, lcq_precision precision,
                            const lcq_params* params, lcq_corr** out) {
@@ -736,6 +767,11 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   c->n_pairs = nr->n_pairs;
   c->n_self = nr->n_self;
   c->kp = kp;
+  c->params = *params;
+  c->params.test_dirs = nullptr;
+  c->params.n_test_dirs = 0;
+  c->eps0 = eps0;
+  c->precision = (int)precision;
   CK(dalloc(st, &c->val, (size_t)2 * std::max<int64_t>(nr->nnz, 1)));
   CK(dalloc(st, &c->q, P));
   CK(dalloc(st, &c->q_near, P));
@@ -811,23 +847,9 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   if (nr->n_adaptive > 0) {
     const int levels = params->max_depth;
     const int64_t A = nr->max_adaptive;
-    const int64_t n = ldI;
-    int64_t stride = A * n * 16 + A * 4 * n * 16 + (int64_t)levels * A * 4 * n * 16 +
-                     (int64_t)levels * A * 4 + 2 * A * 4 + (int64_t)levels * 4 + 8 + A * 4 * 8 +
-                     256;
-    stride = (stride + 255) / 256 * 256;
-    int bps = 1;
-    for (int d = 1; d <= kMaxDeg; ++d)
-      if (nr->ad_count[d]) bps = std::max(bps, adaptive_blocks_per_sm(d));
-    const int agrid = ctx->num_sms * bps;
-    const size_t need = (size_t)stride * agrid;
-    if (ctx->work_bytes < need) {
-      if (ctx->work) CK(cudaFreeAsync(ctx->work, st));
-      ctx->work = nullptr;
-      ctx->work_bytes = 0;
-      CK(cudaMallocAsync(&ctx->work, need, st));
-      ctx->work_bytes = need;
-    }
+    int64_t stride;
+    int agrid;
+    CK(adaptive_work(ctx, nr, levels, &stride, &agrid));
     for (int d = 1; d <= kMaxDeg; ++d) {
       if (!nr->ad_count[d]) continue;
       launch_adaptive(d, lc, nr->ad_list_dev[d], nr->ad_count[d], dv, kp,
@@ -999,6 +1021,135 @@ lcq_status lcq_apply_corrected_CFIE(lcq_ctx* ctx, const lcq_surface* surf, const
                                     double* out) {
   (void)surf;
   return apply_impl(ctx, near, corr, sigma, jump, out, LCQ_CFIE);
+}
+
+// Oversampled far sources of every patch (positions, weighted normals, J w, interpolated
+// density if sigma is given) into a new buffer [9][n_over].
+static lcq_status far_sources(lcq_ctx* ctx, const lcq_near* nr, lcq_corr* c, const Dev& dv,
+                              const LaunchCommon& lc, const double* sigma, double** src_out) {
+  double* src;
+  CK(dalloc(ctx->stream, &src, (size_t)9 * std::max<int64_t>(c->n_over, 1)));
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_far_src(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, c->q,
+                   c->src_off, sigma, src, c->n_over);
+  }
+  *src_out = src;
+  return LCQ_OK;
+}
+
+lcq_status lcq_apply_adjoint(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* nr,
+                             const lcq_corr* cc, const double* g, double jump, double* out) {
+  (void)surf;
+  if (!ctx || !nr || !cc || !g || !out) return fail(ctx, LCQ_ERR_ARG, "null argument");
+  if (cc->near != nr) return fail(ctx, LCQ_ERR_ARG, "corrections belong to another near list");
+  lcq_corr* c = const_cast<lcq_corr*>(cc);
+  CK(cudaSetDevice(ctx->device));
+  lcq_status s = ensure_q_host(ctx, c);
+  if (s != LCQ_OK) return s;
+  cudaStream_t st = ctx->stream;
+  long long nl = 0;
+  LaunchCommon lc{st, ctx->num_sms, &nl};
+  Dev dv = make_dev(ctx, nr, c->q, nr->n_max, c->grp);
+  double* src;
+  s = far_sources(ctx, nr, c, dv, lc, nullptr, &src);
+  if (s != LCQ_OK) return s;
+  double* z;
+  CK(dalloc(st, &z, (size_t)2 * std::max<int64_t>(c->n_over, 1)));
+  launch_far_sum_T(lc, dv, nr->n_patches, src, c->n_over, c->src_off, c->kp,
+                   c->grp ? nr->tgroup : nullptr, g, z);
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_adj_patch(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, c->src_off, z,
+                     c->val, g, jump, out);
+  }
+  CK(cudaGetLastError());
+  dfree(st, src);
+  dfree(st, z);
+  return LCQ_OK;
+}
+
+lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* nr,
+                              const lcq_corr* cc, const double* sigma, const double* g,
+                              double* out) {
+  (void)surf;
+  if (!ctx || !nr || !cc || !sigma || !g || !out) return fail(ctx, LCQ_ERR_ARG, "null argument");
+  if (cc->near != nr) return fail(ctx, LCQ_ERR_ARG, "corrections belong to another near list");
+  if (nr->n_self > 0)
+    return fail(ctx, LCQ_ERR_ARG, "shape gradient: off-surface targets only (no self pairs)");
+  lcq_corr* c = const_cast<lcq_corr*>(cc);
+  CK(cudaSetDevice(ctx->device));
+  lcq_status s = ensure_q_host(ctx, c);
+  if (s != LCQ_OK) return s;
+  cudaStream_t st = ctx->stream;
+  long long nl = 0;
+  LaunchCommon lc{st, ctx->num_sms, &nl};
+  const int ldI = nr->n_max;
+  Dev dv = make_dev(ctx, nr, c->q, ldI, c->grp);
+  const int64_t N = nr->n_points, P = nr->n_patches;
+  double *shat, *M, *tg, *src;
+  CK(dalloc(st, &shat, (size_t)2 * N));
+  CK(dalloc(st, &M, (size_t)3 * N));
+  CK(dalloc(st, &tg, (size_t)12 * std::max<int64_t>(c->n_over, 1)));
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_shat(d, lc, nr->plist_dev[d], nr->plist_count[d], nr->node_off, ctx->deg[d].dV, sigma,
+                shat);
+  }
+  s = far_sources(ctx, nr, c, dv, lc, nullptr, &src);
+  if (s != LCQ_OK) return s;
+  // 1. far pairs through the rules q_j; 2. annulus pairs (both write M)
+  launch_far_grad_sum(lc, dv, P, src, c->n_over, c->src_off, c->kp, c->grp ? nr->tgroup : nullptr,
+                      g, tg);
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_grad_rules(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, c->kp, c->q_near,
+                      c->src_off, c->n_over, tg, g, shat, M);
+  }
+  // 3. adaptive pairs: the union-tree kernel again, in gradient mode (adds to M)
+  if (nr->n_adaptive > 0) {
+    const lcq_params& pr = c->params;
+    const int levels = pr.max_depth;
+    int64_t stride;
+    int agrid;
+    CK(adaptive_work(ctx, nr, levels, &stride, &agrid));
+    const int64_t npr = std::max<int64_t>(nr->n_pairs, 1);
+    double *Is, *In;
+    int32_t* leaves;
+    CK(dalloc(st, &Is, (size_t)2 * npr * ldI));
+    CK(dalloc(st, &In, (size_t)2 * npr * ldI));
+    CK(dalloc(st, &leaves, npr));
+    if (pr.leaf_order <= 0)  // root moments of the adaptive pairs: the smooth rule q_j
+      for (int d = 1; d <= kMaxDeg; ++d) {
+        if (!nr->plist_count[d]) continue;
+        launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 0, c->q, c->kp, Is,
+                            nullptr);
+      }
+    const GradArgs ga{g, shat, M};
+    for (int d = 1; d <= kMaxDeg; ++d) {
+      if (!nr->ad_count[d]) continue;
+      launch_adaptive_grad(d, lc, nr->ad_list_dev[d], nr->ad_count[d], dv, c->kp,
+                           c->eps0 * pr.eps_loosen, ctx->deg[d].normV, pr.leaf_order, pr.max_depth,
+                           Is, In, leaves, ctx->work, stride, (int)nr->max_adaptive, levels, agrid,
+                           ctx->d_status, ctx->d_sched + d,
+                           c->precision == LCQ_MIXED ? 2.0 : 0.0, ga);
+    }
+    dfree(st, Is);
+    dfree(st, In);
+    dfree(st, leaves);
+  }
+  // 4. dL/dy = V^T M per patch
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_grad_v2c(d, lc, nr->plist_dev[d], nr->plist_count[d], nr->node_off, ctx->deg[d].dV, M,
+                    N, out);
+  }
+  CK(cudaGetLastError());
+  dfree(st, shat);
+  dfree(st, M);
+  dfree(st, tg);
+  dfree(st, src);
+  return LCQ_OK;
 }
 
 void lcq_corr_destroy(lcq_corr* c) {

@@ -1,0 +1,637 @@
+// Device code shared by the forward kernels (lcq_kernels.cu) and the adjoint kernels
+// (lcq_adjoint.cu): block-level helpers, the moment engine of Sec. 4.2-4.3 and the
+// union-tree adaptive kernel, which the adjoint instantiates with gradient accumulation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "lcq_device.cuh"
+#include "lcq_launch.h"
+
+namespace lcq {
+
+constexpr int kThreads = 256;
+constexpr double kRoundingFloor = 2e-13;  // multiple of the FP64 rounding envelope never asked below
+constexpr double kF32Floor = 2e-6;        // the same for kernel values evaluated in FP32
+
+// ============================================================================ helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide exclusive prefix of 0/1 flags for one chunk of blockDim items.
+// Returns this thread's position; *total receives the chunk's count.  Uses sm[33].
+__device__ __forceinline__ int block_flag_scan(int flag, int* sm, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, flag);
+  const int inwarp = __popc(bal & ((1u << lane) - 1u));
+  __syncthreads();
+  if (lane == 0) sm[warp] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int c = sm[w];
+      sm[w] = acc;
+      acc += c;
+    }
+    sm[32] = acc;
+  }
+  __syncthreads();
+  *total = sm[32];
+  return sm[warp] + inwarp;
+}
+
+// Kernel of patch j: its surface's in a batch of independent surfaces, else the launch's.
+__device__ __forceinline__ KernelParams patch_kp(const Dev& dv, int j, const KernelParams& kp) {
+  return dv.pgroup ? dv.grp[dv.pgroup[j]].kp : kp;
+}
+
+__device__ __forceinline__ double eta_default(int d) {
+  const int p = d + 1;
+  return p <= 4 ? 2.75 : (p <= 8 ? 2.0 : 1.25);
+}
+
+// ============================================================================ moments
+template <int D>
+struct Cfg {
+  static constexpr int n = (D + 1) * (D + 2) / 2;
+  static constexpr int NP = n <= 32 ? 32 : (n <= 64 ? 64 : 96);
+  static constexpr int CH = 128;  // nodes per chunk (two blocks per SM fit in shared memory)
+  static constexpr int BS = n + 1;
+  static constexpr int TT = 16;
+  // doubles of shared workspace used by block_moments
+  static constexpr int WS = CH * BS + 7 * CH + 3 * TT * CH + 3 * TT;
+};
+
+struct SegMap {
+  double ax, ay, e1x, e1y, e2x, e2y, det;
+};
+
+// Moments I[i][seg][nm] = sum_{q in seg} w_q K(x_i, X_q) J_q K_nm(u_q, v_q) for a smooth
+// rule (Q nodes) pushed onto nseg affine images of T0, for T targets.  Geometry is
+// evaluated once per chunk of nodes and shared by all targets (Sec. 4.3 reuse).
+// TA: target accessor (pos(i, x[3])); out row of target i: out + orow(i) * ostride.
+// Positions are relative to the patch centroid cen (the coefficients cf describe
+// X - cen).  With ENV, eout[i * nseg + seg] also receives the summed rounding envelope.
+// mix > 0 (mixed precision): a node farther than mix * 2R sqrt(det_seg) -- mix times the
+// size of its subtriangle -- from the target is evaluated by kernel_eval_f32, and its
+// envelope is scaled by kF32Floor / kRoundingFloor.
+template <int D, bool ENV = false, class TA, class OR>
+__device__ void block_moments(const double* cf, const double* __restrict__ ru,
+                              const double* __restrict__ rv, const double* __restrict__ rw, int Q,
+                              const SegMap* segs, int nseg, const TA& ta, int T, OR orow,
+                              int64_t ostride, const KernelParams& kp, double* sm,
+                              const double* cen, double R = 0.0, double* eout = nullptr,
+                              double mix = 0.0) {
+  using C = Cfg<D>;
+  double* B = sm;
+  double* Xs = B + C::CH * C::BS;
+  double* Ns = Xs + 3 * C::CH;
+  double* Js = Ns + 3 * C::CH;
+  cplx* G = reinterpret_cast<cplx*>(Js + C::CH);
+  double* Ev = reinterpret_cast<double*>(G + C::TT * C::CH);
+  double* tx = Ev + C::TT * C::CH;
+  const int total = nseg * Q;
+  for (int c0 = 0; c0 < total; c0 += C::CH) {
+    const int nch = min(C::CH, total - c0);
+    __syncthreads();
+    for (int ql = threadIdx.x; ql < nch; ql += blockDim.x) {
+      const int q = c0 + ql;
+      const int sg = q / Q, l = q - sg * Q;
+      const SegMap& S = segs[sg];
+      const double r0 = ru[l], r1 = rv[l];
+      const double u = S.ax + r0 * S.e1x + r1 * S.e2x;
+      const double v = S.ay + r0 * S.e1y + r1 * S.e2y;
+      const double w = rw[l] * S.det;
+      double X[3], Xu[3], Xv[3], Nn[3];
+      kw_geometry<D>(u, v, cf, X, Xu, Xv, B + ql * C::BS, 1);
+      cross3(Xu, Xv, Nn);
+      const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Xs[c * C::CH + ql] = X[c];
+        Ns[c * C::CH + ql] = Nn[c] * w;
+      }
+      Js[ql] = J * w;
+    }
+    __syncthreads();
+    for (int t0 = 0; t0 < T; t0 += C::TT) {
+      const int nt = min(C::TT, T - t0);
+      if (threadIdx.x < nt) {
+        double* xp = tx + 3 * threadIdx.x;
+        ta.pos(t0 + threadIdx.x, xp);
+        xp[0] -= cen[0];
+        xp[1] -= cen[1];
+        xp[2] -= cen[2];
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < nt * C::CH; e += blockDim.x) {
+        const int i = e / C::CH, ql = e - i * C::CH;
+        cplx g = {0.0, 0.0};
+        double ev = 0.0;
+        if (ql < nch) {
+          bool f32 = false;
+          double d0 = 0, d1 = 0, d2 = 0, r2 = 0;
+          if (mix > 0.0) {
+            const int sg = (c0 + ql) / Q;
+            const double h = mix * 2.0 * R * sqrt(segs[sg].det);
+            d0 = tx[3 * i] - Xs[ql];
+            d1 = tx[3 * i + 1] - Xs[C::CH + ql];
+            d2 = tx[3 * i + 2] - Xs[2 * C::CH + ql];
+            r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            f32 = r2 >= h * h;
+          }
+          if (f32)
+            g = kernel_eval_f32(kp, d0, d1, d2, r2, Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql],
+                                Js[ql], R, ENV ? &ev : nullptr, kF32Floor / kRoundingFloor);
+          else
+            g = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql], Xs[C::CH + ql],
+                            Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql],
+                            Js[ql], R, ENV ? &ev : nullptr);
+        }
+        G[i * C::CH + ql] = g;
+        if (ENV) Ev[i * C::CH + ql] = ev;
+      }
+      __syncthreads();
+      const int nout = nt * nseg * C::NP;
+      for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        const int nm = o % C::NP;
+        const int rest = o / C::NP;
+        const int sg = rest % nseg, i = rest / nseg;
+        if (nm >= C::n) continue;
+        const int qa = max(sg * Q - c0, 0), qb = min((sg + 1) * Q - c0, nch);
+        double are = 0.0, aim = 0.0;
+        const cplx* Gi = G + i * C::CH;
+        for (int ql = qa; ql < qb; ++ql) {
+          const cplx g = Gi[ql];
+          const double bv = B[ql * C::BS + nm];
+          are = fma(g.re, bv, are);
+          aim = fma(g.im, bv, aim);
+        }
+        cplx* dst = reinterpret_cast<cplx*>(orow(t0 + i)) + (int64_t)sg * C::n + nm;
+        (void)ostride;
+        if (c0 == 0) {
+          dst->re = are;
+          dst->im = aim;
+        } else {
+          dst->re += are;
+          dst->im += aim;
+        }
+        if (ENV && nm == 0) {
+          double es = 0.0;
+          for (int ql = qa; ql < qb; ++ql) es += Ev[i * C::CH + ql];
+          double* ed = eout + (int64_t)(t0 + i) * nseg + sg;
+          *ed = (c0 == 0) ? es : *ed + es;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void load_coef(const double* __restrict__ coef, int64_t off, double* cf) {
+  constexpr int n = (D + 1) * (D + 2) / 2;
+  for (int e = threadIdx.x; e < 3 * n; e += blockDim.x) cf[e] = coef[off * 3 + e];
+}
+
+struct TgtIdx {  // targets by id list
+  const double* tgt;
+  int64_t NT;
+  const int32_t* ids;
+  __device__ void pos(int i, double* x) const {
+    const int64_t t = ids[i];
+    x[0] = tgt[t];
+    x[1] = tgt[NT + t];
+    x[2] = tgt[2 * NT + t];
+  }
+};
+struct TgtPairIdx {  // targets of pair ids
+  const double* tgt;
+  int64_t NT;
+  const int32_t* pair_tgt;
+  const int32_t* pairs;
+  __device__ void pos(int i, double* x) const {
+    const int64_t t = pair_tgt[pairs[i]];
+    x[0] = tgt[t];
+    x[1] = tgt[NT + t];
+    x[2] = tgt[2 * NT + t];
+  }
+};
+struct TgtPts {  // explicit points [i][3]
+  const double* p;
+  __device__ void pos(int i, double* x) const {
+    x[0] = p[3 * i];
+    x[1] = p[3 * i + 1];
+    x[2] = p[3 * i + 2];
+  }
+};
+
+struct TgtAdaptive {  // targets of a union-tree node: local ids -> pairs -> targets
+  const double* tgt;
+  int64_t NT;
+  const int32_t* pair_tgt;
+  const int32_t* apairs;
+  const int* ST;
+  __device__ void pos(int i, double* x) const {
+    const int64_t t = pair_tgt[apairs[ST[i]]];
+    x[0] = tgt[t];
+    x[1] = tgt[NT + t];
+    x[2] = tgt[2 * NT + t];
+  }
+};
+
+__device__ __forceinline__ SegMap seg_T0() { return {0.0, 0.0, 1.0, 0.0, 0.0, 1.0, 1.0}; }
+
+// ============================================================================ adjoint
+// Gradient moments (adjoint of Sec. 4.2-4.3 rules with the rule frozen): for the nodes of
+// a rule pushed onto nseg sub-triangles and T targets with weights wf(i) = conj(g_t)
+// (0: skip), accumulates into the thread-private M[3n]
+//   dL/dx_nm += sum_nodes K_nm a_X + dK_nm/du (X_v x a_N) + dK_nm/dv (a_N x X_u),
+//   a_X = Re(w sigma(u) sum_i wf(i) dK~/dX),  a_N = Re(w sigma(u) sum_i wf(i) dK~/dN),
+// where sigma(u) = sum_nm shat_nm K_nm(u) and N = X_u x X_v (so a_N.dN splits into the
+// two cross products).  Thread per node; targets staged through shared memory.
+template <int D, class TA, class WF>
+__device__ void block_grad(const double* cf, const double* __restrict__ ru,
+                           const double* __restrict__ rv, const double* __restrict__ rw, int Q,
+                           const SegMap* segs, int nseg, const TA& ta, int T, WF wf,
+                           const KernelParams& kp, const cplx* shat, const double* cen,
+                           double* M) {
+  constexpr int TG = 32;
+  __shared__ double gx[TG][3];
+  __shared__ cplx gwt[TG];
+  const int total = nseg * Q;
+  for (int c0 = 0; c0 < total; c0 += blockDim.x) {
+    const int q = c0 + threadIdx.x;
+    const bool on = q < total;
+    double u = 0.0, v = 0.0, w = 0.0, X[3] = {0, 0, 0}, Xu[3] = {0, 0, 0}, Xv[3] = {0, 0, 0};
+    double Nn[3] = {0, 0, 0};
+    cplx sg = {0.0, 0.0};
+    if (on) {
+      const int s = q / Q, l = q - s * Q;
+      const SegMap& S = segs[s];
+      u = S.ax + ru[l] * S.e1x + rv[l] * S.e2x;
+      v = S.ay + ru[l] * S.e1y + rv[l] * S.e2y;
+      w = rw[l] * S.det;
+      kw_geometry<D>(u, v, cf, X, Xu, Xv, nullptr, 1);
+      cross3(Xu, Xv, Nn);
+      kw_for_each<D>(u, v, [&](int idx, double k0, double, double) {
+        sg.re = fma(shat[idx].re, k0, sg.re);
+        sg.im = fma(shat[idx].im, k0, sg.im);
+      });
+    }
+    cplx SX[3] = {{0, 0}, {0, 0}, {0, 0}}, SN[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int t0 = 0; t0 < T; t0 += TG) {
+      const int nt = min(TG, T - t0);
+      __syncthreads();
+      if (threadIdx.x < nt) {
+        double xp[3];
+        ta.pos(t0 + threadIdx.x, xp);
+        gx[threadIdx.x][0] = xp[0] - cen[0];
+        gx[threadIdx.x][1] = xp[1] - cen[1];
+        gx[threadIdx.x][2] = xp[2] - cen[2];
+        gwt[threadIdx.x] = wf(t0 + threadIdx.x);
+      }
+      __syncthreads();
+      if (on)
+        for (int i = 0; i < nt; ++i) {
+          const cplx c = gwt[i];
+          if (c.re == 0.0 && c.im == 0.0) continue;
+          cplx dX[3], dN[3];
+          kernel_grad(kp, gx[i], X, Nn, dX, dN);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const cplx a = cmul(c, dX[k]), b = cmul(c, dN[k]);
+            SX[k].re += a.re;
+            SX[k].im += a.im;
+            SN[k].re += b.re;
+            SN[k].im += b.im;
+          }
+        }
+    }
+    if (on) {
+      double aX[3], aN[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        aX[k] = w * (sg.re * SX[k].re - sg.im * SX[k].im);
+        aN[k] = w * (sg.re * SN[k].re - sg.im * SN[k].im);
+      }
+      double bu[3], bv[3];
+      cross3(Xv, aN, bu);
+      cross3(aN, Xu, bv);
+      kw_for_each<D>(u, v, [&](int idx, double k0, double ku, double kv) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) M[idx * 3 + k] += k0 * aX[k] + ku * bu[k] + kv * bv[k];
+      });
+    }
+  }
+}
+
+// Block sum of the thread-private M[3n] in a fixed order, added to out[3n] (global).
+// Uses sm[(blockDim/32) * 3n] doubles of shared memory.
+template <int D>
+__device__ void block_reduce_M(const double* M, double* sm, double* out) {
+  constexpr int n3 = 3 * Cfg<D>::n;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+#pragma unroll 1
+  for (int e = 0; e < n3; ++e) {
+    const double v = warp_sum(M[e]);
+    if (lane == 0) sm[wp * n3 + e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n3; e += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < nw; ++k) acc += sm[k * n3 + e];
+    out[e] += acc;
+  }
+  __syncthreads();
+}
+
+// ============================================================================ adaptive
+// Adaptive subdivision (Sec. 4.3) for all eta_1-near targets of a patch at once.
+// The refinement trees of the targets are walked as one union tree, depth first:
+// a node T carries the set S of targets that refine T; the leaf-rule geometry of T's
+// four children is evaluated once and contracted with every target in S (the reuse
+// of X, K_nm and J across targets of Fig. multipletargpot).  A target accepts the
+// children's sum when ||I_T - sum_c I_c||_2 <= max(tol0 4^-L, 2e-13 E), E the summed
+// rounding envelope of the kernel over the children's nodes.
+constexpr int kMaxTreeNodes = 1 << 16;  // union-tree nodes walked per patch at most
+
+struct AdaptiveWS {
+  int64_t stride;   // bytes per block
+  int A_max, levels;
+};
+
+// Patches are taken dynamically from `plist` (ordered by decreasing number of adaptive
+// targets) through the counter *sched, which the caller zeroes before the launch.
+template <int D, bool GRAD = false>
+__global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict__ plist, int count,
+                                                       Dev dv, const KernelParams kp, double eps,
+                                                       double normV, int leaf_order, int max_depth,
+                                                       const cplx* __restrict__ I_smooth,
+                                                       cplx* __restrict__ I_near,
+                                                       int32_t* __restrict__ leaves_out,
+                                                       unsigned char* __restrict__ work,
+                                                       AdaptiveWS wsd, int* __restrict__ status,
+                                                       int* __restrict__ sched, double mix,
+                                                       GradArgs ga) {
+  using C = Cfg<D>;
+  constexpr int n = C::n;
+  // gradient mode: dL/dx_nm of the accepted leaves, per thread, reduced per patch
+  double Mg[GRAD ? 3 * n : 1];
+  __shared__ cplx shat[GRAD ? n : 1];
+  extern __shared__ double smem[];
+  double* cf = smem;
+  SegMap* segs = reinterpret_cast<SegMap*>(cf + n * 3);
+  int* ism = reinterpret_cast<int*>(segs + 4);  // [64]: scan scratch + misc
+  unsigned long long* stk = reinterpret_cast<unsigned long long*>(ism + 64);  // [4 * 32]
+  double* ws = reinterpret_cast<double*>(stk + 4 * 32);
+  // per-block global workspace
+  unsigned char* wb = work + (int64_t)blockIdx.x * wsd.stride;
+  const int A_max = wsd.A_max;
+  cplx* acc = reinterpret_cast<cplx*>(wb);                          // [A_max][n]
+  cplx* tmp = acc + (int64_t)A_max * n;                             // [A_max][4][n]
+  cplx* lvlI = tmp + (int64_t)A_max * 4 * n;                        // [levels][A_max][4][n]
+  int* lvlT = reinterpret_cast<int*>(lvlI + (int64_t)wsd.levels * A_max * 4 * n);  // [levels][A_max]
+  int* flags = lvlT + (int64_t)wsd.levels * A_max;                  // [A_max]
+  int* lcnt = flags + A_max;                                        // [A_max]
+  int* cnt = lcnt + A_max;                                          // [levels]
+  double* tmpE = reinterpret_cast<double*>(                          // [A_max][4], 8-aligned
+      (reinterpret_cast<uintptr_t>(cnt + wsd.levels) + 7) & ~static_cast<uintptr_t>(7));
+  long long my_tests = 0, my_nodes = 0, my_tree = 0;
+  __shared__ int next_b;
+  __shared__ KernelParams kps;
+
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) next_b = atomicAdd(sched, 1);
+    __syncthreads();
+    const int b = next_b;
+    if (b >= count) break;
+    const int j = plist[b];
+    const int64_t a0 = dv.ad_ptr[j];
+    const int A = (int)(dv.ad_ptr[j + 1] - a0);
+    if (A == 0) continue;
+    if (A > A_max) {
+      if (threadIdx.x == 0) atomicOr(status, kStCapacity);
+      continue;
+    }
+    const int m = leaf_order > 0 ? leaf_order : dv.q[j];
+    const int Q = m * m;
+    const double* ru = dv.ru + dv.roff[m];
+    const double* rv = dv.rv + dv.roff[m];
+    const double* rw = dv.rw + dv.roff[m];
+    const double tol0 = (dv.pgroup ? dv.grp[dv.pgroup[j]].eps_ad : eps) * dv.dj[j] / normV;
+    const double Rj = dv.rad[j];
+    const int32_t* apairs = dv.ad_pair + a0;
+    __syncthreads();
+    load_coef<D>(dv.coef, dv.node_off[j], cf);
+    if (threadIdx.x == 0) kps = patch_kp(dv, j, kp);  // read after block_moments' barrier
+    if constexpr (GRAD) {
+#pragma unroll
+      for (int e = 0; e < 3 * n; ++e) Mg[e] = 0.0;
+      const cplx* sh = reinterpret_cast<const cplx*>(ga.shat) + dv.node_off[j];
+      for (int e = threadIdx.x; e < n; e += blockDim.x) shat[e] = sh[e];
+    }
+    // root: level 0 block holds all targets with I_T0 in slot c = 0
+    for (int e = threadIdx.x; e < A * n; e += blockDim.x) {
+      const int i = e / n, nm = e - i * n;
+      acc[e] = {0.0, 0.0};
+      if (leaf_order <= 0) lvlI[(int64_t)i * 4 * n + nm] = I_smooth[(int64_t)apairs[i] * dv.ldI + nm];
+    }
+    for (int i = threadIdx.x; i < A; i += blockDim.x) {
+      lvlT[i] = i;
+      lcnt[i] = 0;
+    }
+    if (threadIdx.x == 0) {
+      segs[0] = seg_T0();
+      cnt[0] = A;
+    }
+    __syncthreads();
+    if (leaf_order > 0) {
+      TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, apairs};
+      block_moments<D>(cf, ru, rv, rw, Q, segs, 1, ta, A,
+                       [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, 4 * n, kps, ws,
+                       dv.cen + 3 * j);
+    }
+    // DFS stack entries: level (8 bits) | child (2 bits) | path (2 bits per level) << 16
+    int sp = 0;
+    if (threadIdx.x == 0) stk[0] = 0ull;  // root: level 0, child 0, empty path
+    sp = 1;
+    int visited = 0;
+    while (sp > 0) {
+      if (++visited > kMaxTreeNodes) {  // bounded walk: give up on this patch
+        if (threadIdx.x == 0) atomicOr(status, kStCapacity);
+        break;
+      }
+      __syncthreads();
+      const unsigned long long top = stk[sp - 1];
+      --sp;
+      const int L = (int)(top & 0xff);
+      const int cidx = (int)((top >> 8) & 3);
+      const unsigned long long path = top >> 16;  // child digits of T, level 1 at bits 0-1
+      // vertices of T
+      double ax = 0, ay = 0, bx = 1, by = 0, cx = 0, cy = 1;
+      for (int l = 0; l < L; ++l) {
+        const int dgt = (int)((path >> (2 * l)) & 3);
+        const double abx = 0.5 * (ax + bx), aby = 0.5 * (ay + by);
+        const double bcx = 0.5 * (bx + cx), bcy = 0.5 * (by + cy);
+        const double cax = 0.5 * (cx + ax), cay = 0.5 * (cy + ay);
+        if (dgt == 0) { bx = abx; by = aby; cx = cax; cy = cay; }
+        else if (dgt == 1) { ax = abx; ay = aby; cx = bcx; cy = bcy; }
+        else if (dgt == 2) { ax = cax; ay = cay; bx = bcx; by = bcy; }
+        else { ax = bcx; ay = bcy; bx = cax; by = cay; cx = abx; cy = aby; }
+      }
+      const int S = cnt[L];
+      const int* ST = lvlT + (int64_t)L * A_max;
+      const cplx* IT = lvlI + (int64_t)L * A_max * 4 * n;
+      if (threadIdx.x == 0) {
+        const double abx = 0.5 * (ax + bx), aby = 0.5 * (ay + by);
+        const double bcx = 0.5 * (bx + cx), bcy = 0.5 * (by + cy);
+        const double cax = 0.5 * (cx + ax), cay = 0.5 * (cy + ay);
+        const double V[4][6] = {{ax, ay, abx, aby, cax, cay},
+                                {abx, aby, bx, by, bcx, bcy},
+                                {cax, cay, bcx, bcy, cx, cy},
+                                {bcx, bcy, cax, cay, abx, aby}};
+        for (int k = 0; k < 4; ++k) {
+          SegMap s;
+          s.ax = V[k][0];
+          s.ay = V[k][1];
+          s.e1x = V[k][2] - V[k][0];
+          s.e1y = V[k][3] - V[k][1];
+          s.e2x = V[k][4] - V[k][0];
+          s.e2y = V[k][5] - V[k][1];
+          s.det = fabs(s.e1x * s.e2y - s.e1y * s.e2x);
+          segs[k] = s;
+        }
+      }
+      __syncthreads();
+      // children moments of every target in S
+      TgtAdaptive ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, ST};
+      block_moments<D, true>(cf, ru, rv, rw, Q, segs, 4, ta, S,
+                             [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, 4 * n, kps,
+                             ws, dv.cen + 3 * j, Rj, tmpE, mix);
+      __syncthreads();
+      my_tests += S;
+      my_nodes += (long long)S * 4 * Q;
+      my_tree += 1;
+      // decisions: one warp per target
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      const double tauL = tol0 * ldexp(1.0, -2 * L);
+      for (int s = w; s < S; s += nw) {
+        double e2 = 0.0, s2 = 0.0;
+        for (int nm = lane; nm < n; nm += 32) {
+          const cplx* tc = tmp + (int64_t)s * 4 * n + nm;
+          const double sr = tc[0].re + tc[n].re + tc[2 * n].re + tc[3 * n].re;
+          const double si = tc[0].im + tc[n].im + tc[2 * n].im + tc[3 * n].im;
+          const cplx it = IT[(int64_t)s * 4 * n + (int64_t)cidx * n + nm];
+          const double dr = it.re - sr, di = it.im - si;
+          e2 += dr * dr + di * di;
+          s2 += sr * sr + si * si;
+        }
+        e2 = warp_sum(e2);
+        const double err = sqrt(e2);
+        const double* ee = tmpE + (int64_t)s * 4;
+        const double tau = fmax(tauL, kRoundingFloor * (ee[0] + ee[1] + ee[2] + ee[3]));
+        const bool finite = isfinite(err) && isfinite(tau);
+        const bool accept = !finite || (err <= tau) || (L + 1 >= max_depth);
+        if (lane == 0) {
+          if (!finite) atomicOr(status, kStNonFinite);
+          else if (err > tau && accept) atomicOr(status, kStMaxDepth);
+        }
+        const int tl = ST[s];
+        if (accept) {
+          for (int nm = lane; nm < n; nm += 32) {
+            const cplx* tc = tmp + (int64_t)s * 4 * n + nm;
+            cplx& a = acc[(int64_t)tl * n + nm];
+            a.re += tc[0].re + tc[n].re + tc[2 * n].re + tc[3 * n].re;
+            a.im += tc[0].im + tc[n].im + tc[2 * n].im + tc[3 * n].im;
+          }
+          if (lane == 0) lcnt[tl] += 4;
+        }
+        if (lane == 0) flags[s] = accept ? 0 : 1;
+      }
+      __syncthreads();
+      if constexpr (GRAD) {
+        // kernel gradients on the accepted children (the tree itself is recomputed, not
+        // stored): weight conj(g_t) for a target that accepts here, else 0
+        const cplx* gt = reinterpret_cast<const cplx*>(ga.g);
+        block_grad<D>(cf, ru, rv, rw, Q, segs, 4, ta, S,
+                      [&](int i) -> cplx {
+                        if (flags[i] != 0) return {0.0, 0.0};
+                        const cplx c = gt[dv.pair_tgt[apairs[ST[i]]]];
+                        return {c.re, -c.im};
+                      },
+                      kps, shat, dv.cen + 3 * j, Mg);
+      }
+      // stable compaction of the refining targets into level L+1
+      int base = 0;
+      int* DT = lvlT + (int64_t)(L + 1) * A_max;
+      cplx* DI = lvlI + (int64_t)(L + 1) * A_max * 4 * n;
+      for (int s0 = 0; s0 < S; s0 += blockDim.x) {
+        const int s = s0 + threadIdx.x;
+        const int f = s < S ? flags[s] : 0;
+        int tot;
+        const int pos = block_flag_scan(f, ism, &tot);
+        if (f) {
+          flags[s] = -(base + pos) - 1;  // remember destination
+          DT[base + pos] = ST[s];
+        }
+        base += tot;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < S * 4 * n; e += blockDim.x) {
+        const int s = e / (4 * n);
+        const int f = flags[s];
+        if (f < 0) DI[(int64_t)(-f - 1) * 4 * n + (e - s * 4 * n)] = tmp[e];
+      }
+      if (threadIdx.x == 0) cnt[L + 1] = base;
+      __syncthreads();
+      if (base > 0) {
+        if (sp + 4 > 4 * 32) {
+          if (threadIdx.x == 0) atomicOr(status, kStCapacity);
+        } else {
+          const unsigned long long np = (L == 0) ? 0ull : path;
+          if (threadIdx.x == 0) {
+            for (int c = 3; c >= 0; --c)
+              stk[sp + (3 - c)] = (unsigned long long)(L + 1) | ((unsigned long long)c << 8) |
+                                  ((np | ((unsigned long long)c << (2 * L))) << 16);
+          }
+          sp += 4;
+        }
+      }
+      (void)cidx;
+    }
+    __syncthreads();
+    // results of the patch
+    for (int e = threadIdx.x; e < A * n; e += blockDim.x) {
+      const int i = e / n, nm = e - i * n;
+      I_near[(int64_t)apairs[i] * dv.ldI + nm] = acc[e];
+    }
+    for (int i = threadIdx.x; i < A; i += blockDim.x) leaves_out[apairs[i]] = lcnt[i];
+    if constexpr (GRAD) block_reduce_M<D>(Mg, ws, ga.M + dv.node_off[j] * 3);
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 0), (unsigned long long)my_tests);
+    atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 1), (unsigned long long)my_nodes);
+    atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 4), (unsigned long long)my_tree);
+  }
+}
+
+}  // namespace lcq

@@ -12,7 +12,8 @@
 namespace lcq {
 
 // c_nm = sqrt(2(2m+1)(n+1)), index n(n+1)/2 + m; filled once per device.
-__constant__ double c_kw[kMaxBasis];
+// (static: each translation unit holds and uploads its own copy)
+static __constant__ double c_kw[kMaxBasis];
 
 struct cplx {
   double re, im;
@@ -151,6 +152,48 @@ __device__ __forceinline__ void kw_geometry(double u, double v, const double* __
 // Self-rule geometry at Q = P + delta: the chord dX = X(Q) - X(P), formed from Koornwinder
 // differences K_nm(Q) - K_nm(P) that obey the same recurrences (so dX keeps its relative
 // precision as delta -> 0), and X_u, X_v at Q.
+// f(idx, K_nm, dK_nm/du, dK_nm/dv) for every basis function at (u, v): the recurrences of
+// kw_geometry, for callers that need the derivatives one by one (the adjoint).
+template <int D, class F>
+__device__ __forceinline__ void kw_for_each(double u, double v, F&& f) {
+  const double s = 2.0 * u + v - 1.0, q = 1.0 - v, q2 = q * q, y = 1.0 - 2.0 * v;
+  double Lp = 0.0, L = 1.0, Lup = 0.0, Lu = 0.0, Lvp = 0.0, Lv = 0.0;
+#pragma unroll
+  for (int m = 0; m <= D; ++m) {
+    if (m > 0) {
+      const double f1 = 2.0 * m - 1.0, f2 = m - 1.0, im = 1.0 / m;
+      const double Ln = (f1 * s * L - f2 * q2 * Lp) * im;
+      const double Lun = (f1 * (2.0 * L + s * Lu) - f2 * q2 * Lup) * im;
+      const double Lvn = (f1 * (L + s * Lv) - f2 * (-2.0 * q * Lp + q2 * Lvp)) * im;
+      Lp = L;
+      L = Ln;
+      Lup = Lu;
+      Lu = Lun;
+      Lvp = Lv;
+      Lv = Lvn;
+    }
+    const int b = 2 * m + 1;
+    double Pp = 0.0, P = 1.0, dPp = 0.0, dP = 0.0;
+#pragma unroll
+    for (int a = 0; a <= D - m; ++a) {
+      const int n = m + a, idx = n * (n + 1) / 2 + m;
+      const double cn = c_kw[idx];
+      f(idx, cn * L * P, cn * Lu * P, cn * (Lv * P - 2.0 * L * dP));
+      if (a < D - m) {
+        double c1, c0, c2;
+        jacobi_coef(a, b, &c1, &c0, &c2);
+        const double t = c1 * y + c0;
+        const double Pn = t * P - c2 * Pp;
+        const double dPn = c1 * P + t * dP - c2 * dPp;
+        Pp = P;
+        P = Pn;
+        dPp = dP;
+        dP = dPn;
+      }
+    }
+  }
+}
+
 template <int D>
 __device__ __forceinline__ void kw_delta_geometry(double pu, double pv, double du, double dv,
                                                   const double* __restrict__ cf, double* dX,
@@ -320,6 +363,69 @@ __device__ __forceinline__ cplx kernel_eval_f32(const KernelParams& kp, double d
 }
 
 // Cross product helper.
+// Derivatives of kernel_eval's K~(x, X, N) (N the unnormalized normal, no weight) with
+// respect to the source position X and to N, for the adjoint.  With d = x - X, r = |d|,
+// e = e^{ikr}, G = e/(4 pi r), h = (1 - ikr) e/(4 pi r^3):
+//   S~ = G |N|:        dS~/dX = -G (ik - 1/r) |N| d/r,      dS~/dN = G N/|N|
+//   D~ = h d.N:        dD~/dX = -h N - (d.N) h'(r) d/r,      dD~/dN = h d,
+//                      h'(r) = e (k^2 r^2 + 3ikr - 3)/(4 pi r^4)
+//   CFIE alpha D~ + beta S~.  Zero at r = 0 (as kernel_eval).  K~ is homogeneous of degree
+// one in N, so with N scaled by a weight w, dX scales by w and dN is unchanged.
+__device__ __forceinline__ void kernel_grad(const KernelParams& kp, const double* x,
+                                            const double* X, const double* N, cplx* dX,
+                                            cplx* dN) {
+  const double d[3] = {x[0] - X[0], x[1] - X[1], x[2] - X[2]};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dX[c] = dN[c] = {0.0, 0.0};
+  const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  if (r2 == 0.0) return;
+  const double r = sqrt(r2), ir = 1.0 / r;
+  double sn, cs;
+  sincos(kp.kr * r, &sn, &cs);
+  const double dec = exp(-kp.ki * r) * (0.25 / M_PI);
+  const cplx e = {dec * cs, dec * sn};  // e^{ikr} / (4 pi)
+  cplx cS = {0.0, 0.0}, cD = {0.0, 0.0};
+  if (kp.kind == 0) cS = {1.0, 0.0};
+  else if (kp.kind == 1) cD = {1.0, 0.0};
+  else {
+    cS = {kp.br, kp.bi};
+    cD = {kp.ar, kp.ai};
+  }
+  if (cS.re != 0.0 || cS.im != 0.0) {
+    const double nN = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    const cplx G = {e.re * ir, e.im * ir};
+    const cplx a = cmul(cS, cmul(G, {-kp.ki - ir, kp.kr}));  // beta G (ik - 1/r)
+    const double sa = nN * ir;
+    const cplx b = cmul(cS, G);
+    const double sb = nN > 0.0 ? 1.0 / nN : 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      dX[c].re -= a.re * sa * d[c];
+      dX[c].im -= a.im * sa * d[c];
+      dN[c].re += b.re * sb * N[c];
+      dN[c].im += b.im * sb * N[c];
+    }
+  }
+  if (cD.re != 0.0 || cD.im != 0.0) {
+    const double ir3 = ir * ir * ir;
+    const cplx h0 = cmul({1.0 + kp.ki * r, -kp.kr * r}, e);
+    const cplx h = cmul(cD, {h0.re * ir3, h0.im * ir3});
+    const cplx poly = {(kp.kr * kp.kr - kp.ki * kp.ki) * r2 - 3.0 * kp.ki * r - 3.0,
+                       2.0 * kp.kr * kp.ki * r2 + 3.0 * kp.kr * r};
+    const cplx p0 = cmul(poly, e);
+    const double ndx = N[0] * d[0] + N[1] * d[1] + N[2] * d[2];
+    const double sp = ndx * ir3 * ir * ir;  // (d.N) / r^4 / r
+    const cplx hp = cmul(cD, {p0.re * sp, p0.im * sp});
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      dX[c].re -= h.re * N[c] + hp.re * d[c];
+      dX[c].im -= h.im * N[c] + hp.im * d[c];
+      dN[c].re += h.re * d[c];
+      dN[c].im += h.im * d[c];
+    }
+  }
+}
+
 __device__ __forceinline__ void cross3(const double* a, const double* b, double* c) {
   c[0] = a[1] * b[2] - a[2] * b[1];
   c[1] = a[2] * b[0] - a[0] * b[2];

@@ -174,6 +174,9 @@ struct lcq_corr {
   int kernel = 0;
   int64_t n_patches = 0, n_targets = 0, nnz = 0, n_pairs = 0, n_self = 0, n_over = 0;
   lcq::KernelParams kp{};
+  lcq_params params{};           // generation parameters (test directions dropped)
+  double eps0 = 0.0;             // tolerance (first surface's in a batch)
+  int precision = 0;             // lcq_precision of the generation
   double* val = nullptr;         // [nnz][2]
   int32_t* q = nullptr;          // [P]
   int32_t* q_near = nullptr;     // [P]

@@ -58,6 +58,16 @@ struct Dev {
   int ldI;  // row stride (complex entries) of the pair/self moment buffers
 };
 
+// Adjoint inputs and accumulator of the adaptive kernel's gradient mode: g (complex
+// [NT], interleaved) the upstream gradient of the targets, shat (complex [N]) the
+// Koornwinder coefficients V sigma_j of the density in each patch's node slots, M
+// (double [N][3]) dL/dx_nm in the same slots (added to).
+struct GradArgs {
+  const double* g;
+  const double* shat;
+  double* M;
+};
+
 struct NearArgs {
   const double* tgt;
   int64_t NT;
@@ -139,5 +149,31 @@ void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int3
                       double jump, void* out);
 size_t adaptive_smem_bytes(int d);
 int adaptive_blocks_per_sm(int d);
+
+// Adjoint (lcq_adjoint.cu).
+cudaError_t upload_constants_adjoint(cudaStream_t st);
+bool launch_shat(int d, const LaunchCommon& lc, const int* plist, int count,
+                 const int64_t* node_off, const double* Vt, const void* sigma, void* shat);
+void launch_far_grad_sum(const LaunchCommon& lc, const Dev& dv, int64_t P, const double* src,
+                         int64_t n_over, const int64_t* src_off, const KernelParams& kp,
+                         const int32_t* tgroup, const void* g, double* tg);
+bool launch_grad_rules(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                       const KernelParams& kp, const int32_t* qn, const int64_t* src_off,
+                       int64_t n_over, const double* tg, const void* g, const void* shat,
+                       double* M);
+bool launch_adaptive_grad(int d, const LaunchCommon& lc, const int* plist, int count,
+                          const Dev& dv, const KernelParams& kp, double eps, double normV,
+                          int leaf_order, int max_depth, const void* I_smooth, void* I_near,
+                          int32_t* leaves, void* work, int64_t stride, int A_max, int levels,
+                          int grid, int* status, int* sched, double mix, const GradArgs& ga);
+bool launch_grad_v2c(int d, const LaunchCommon& lc, const int* plist, int count,
+                     const int64_t* node_off, const double* Vt, const double* M, int64_t N,
+                     double* out);
+void launch_far_sum_T(const LaunchCommon& lc, const Dev& dv, int64_t P, const double* src,
+                      int64_t n_over, const int64_t* src_off, const KernelParams& kp,
+                      const int32_t* tgroup, const void* g, void* z);
+bool launch_adj_patch(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
+                      const double* Vt, const int64_t* src_off, const void* z, const double* val,
+                      const void* g, double jump, void* out);
 
 }  // namespace lcq

@@ -75,6 +75,8 @@ _sig = {
     "lcq_apply_corrected_D": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
     "lcq_apply_corrected_CFIE": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
     "lcq_corr_destroy": (None, [_vp]),
+    "lcq_apply_adjoint": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
+    "lcq_shape_gradient": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "lcq_sync": (C.c_int, [_vp, _i64]),
     "lcq_counters": (C.c_int, [_vp, _vp]),
     "lcq_stage_times": (C.c_int, [_vp, _vp, _vp]),
@@ -337,6 +339,24 @@ def apply_corrected_D(ctx, surf, near, corr, sigma, n_targets, jump=0.0):
 def apply_corrected_CFIE(ctx, surf, near, corr, sigma, n_targets, jump=0.0):
     return _apply(_lib.lcq_apply_corrected_CFIE, ctx, surf, near, corr, sigma, jump,
                   _out_like(ctx, n_targets))
+
+
+def apply_adjoint(ctx, surf, near, corr, g, jump=0.0):
+    """A^H g (device complex128 [N]) for the operator of apply_corrected_* with `jump`."""
+    import torch
+    out = torch.empty(surf.n_points, dtype=torch.complex128, device=ctx.torch_device)
+    ctx.check(_lib.lcq_apply_adjoint(ctx.h, C.byref(surf.s), near.h, corr.h, _ptr(g), float(jump),
+                                     _ptr(out)), "lcq_apply_adjoint")
+    return out
+
+
+def shape_gradient(ctx, surf, near, corr, sigma, g):
+    """dL/dy (device float64 [3][N]) for dL = Re sum conj(g) du at off-surface targets."""
+    import torch
+    out = torch.empty((3, surf.n_points), dtype=torch.float64, device=ctx.torch_device)
+    ctx.check(_lib.lcq_shape_gradient(ctx.h, C.byref(surf.s), near.h, corr.h, _ptr(sigma), _ptr(g),
+                                      _ptr(out)), "lcq_shape_gradient")
+    return out
 
 
 def adaptive_corrections_noalloc(deg, y_dev, tgt_dev, kernel, k, q, eps, out, alpha=1.0, beta=0.0,

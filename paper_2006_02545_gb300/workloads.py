@@ -327,3 +327,26 @@ def batched_tori_batch(count: int = 64, seed: int = 0, scale: float = 1.0, spaci
         phys.append((sp["k"], 1.0, -1j * sp["k"], sp["eps"]))
     surf, patch_off = concat_surfaces(parts, shifts, f"tori{count}_seed{seed}_x{scale:g}")
     return surf, patch_off, phys, [sp["dtype"] for sp in specs]
+
+
+def exterior_targets(surf: Surface, n: int, seed: int, lo: float = 0.05, hi: float = 0.5):
+    """Off-surface points p (1 + delta), delta ~ U[lo, hi], where p is a random convex
+    combination (Dirichlet weights) of the nodes of a random patch: a point on or just
+    inside the patch, pushed outward along the radius (the ellipsoid family is star-shaped
+    about the origin)."""
+    rng = np.random.default_rng(seed)
+    pts = []
+    for _ in range(n):
+        j = int(rng.integers(0, surf.n_patches))
+        y = surf.xyz[:, surf.node_off[j]:surf.node_off[j + 1]]
+        p = y @ rng.dirichlet(np.ones(y.shape[1]))
+        pts.append(p * (1.0 + rng.uniform(lo, hi)))
+    return np.ascontiguousarray(np.array(pts).T)
+
+
+def ellipsoid_adjoint_s_k5(s: int = 10):
+    """Gradient workload: single layer k=5 on the ellipsoid (1, 1.5, 2.5) with 20 s^2
+    degree-5 patches, eps=1e-8, 1000 exterior targets."""
+    surf = ellipsoid(s, 5, axes=(1.0, 1.5, 2.5))
+    x = exterior_targets(surf, 1000, 0)
+    return surf, x
