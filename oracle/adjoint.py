@@ -40,6 +40,8 @@ def kernel_jac_grad(x, X, N, k, kind: str, alpha=1.0, beta=0.0):
           dD~/dX = -h N + (x - X).N h'(r) (X - x)/r,  dD~/dN = h (x - X),
           h'(r) = e^{ikr} (k^2 r^2 + 3ikr - 3)/(4 pi r^4)
       CFIE = alpha D~ + beta S~.  A source at r = 0 gives 0 (as in kernel_jac)."""
+    if kind not in ("S", "D", "CFIE"):
+        raise ValueError(f"no source-geometry derivative for kernel {kind}")
     x = np.asarray(x, dtype=np.float64)
     k = complex(k)
     dvec = x[:, None] - X                       # x - X

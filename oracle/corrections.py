@@ -76,10 +76,29 @@ def patch_of_node(node_off, tgt_node):
     return tp
 
 
+def target_normals(patches, node_off, tgt_node, tgt_normal):
+    """Unit target normals for S': the chart normal at the node for an on-surface target
+    (so that n_x.(x - y) vanishes to second order on its own patch), the caller's
+    tgt_normal [3, NT] (normalized) for an off-surface target."""
+    tgt_node = np.asarray(tgt_node)
+    tp = patch_of_node(node_off, tgt_node)
+    out = np.zeros((3, len(tgt_node)))
+    for t in range(len(tgt_node)):
+        if tp[t] >= 0:
+            out[:, t] = quadrature.node_normal(patches[tp[t]], int(tgt_node[t] - node_off[tp[t]]))
+        else:
+            if tgt_normal is None:
+                raise ValueError("S' needs the normals of off-surface targets")
+            v = np.asarray(tgt_normal[:, t], dtype=np.float64)
+            out[:, t] = v / np.linalg.norm(v)
+    return out
+
+
 def gen_corrections(deg, node_off, xyz, tgt_xyz, tgt_node, kind, k, alpha=1.0, beta=0.0,
-                    params: Params = None, patches=None, only_patches=None):
+                    params: Params = None, patches=None, only_patches=None, tgt_normal=None):
     """All corrections for the targets; `only_patches` restricts the work to some patches
-    (rows then hold only those patches' entries)."""
+    (rows then hold only those patches' entries).  kind "Sp" (S') uses target normals
+    (target_normals)."""
     p = params
     kern = Kern(kind, k, alpha, beta)
     deg = np.asarray(deg)
@@ -94,6 +113,7 @@ def gen_corrections(deg, node_off, xyz, tgt_xyz, tgt_node, kind, k, alpha=1.0, b
     centers = np.array([pt.c for pt in patches])
     radii = np.array([pt.R for pt in patches])
     near = nearlist.near_lists(centers, radii, eta, eta1, tgt_xyz, tgt_patch)
+    nrm = target_normals(patches, node_off, tgt_node, tgt_normal) if kind == "Sp" else None
     dirs = fibonacci_dirs() if p.test_dirs is None else np.asarray(p.test_dirs)
     self_order = p.self_order if p.self_order > 0 else rules.default_self_order(p.eps)
 
@@ -127,18 +147,19 @@ def gen_corrections(deg, node_off, xyz, tgt_xyz, tgt_node, kind, k, alpha=1.0, b
         an_rule = rules.conical_rule(int(q_near[j])) if q_near[j] > 0 else None
         for t, ad in zip(ids, adaptive):
             x = tgt_xyz[:, t]
+            nx = nrm[:, t] if nrm is not None else None
             if ad:
                 rec = [] if p.record_leaves else None
-                I, st = quadrature.adaptive_moments(cache, x, kern, tol0, p.max_depth, rec)
+                I, st = quadrature.adaptive_moments(cache, x, kern, tol0, p.max_depth, rec, nx)
                 depth_hit |= st["depth_hit"]
                 st["kind"] = "adaptive"
                 if rec is not None:
                     st["leaf_tris"] = rec
             else:
-                I = quadrature.rule_moments(pt, x, *an_rule, kern)
+                I = quadrature.rule_moments(pt, x, *an_rule, kern, nx)
                 st = {"kind": "annulus"}
             a = pt.V.T @ I
-            s = quadrature.smooth_weights(pt, x, int(q[j]), kern)
+            s = quadrature.smooth_weights(pt, x, int(q[j]), kern, nx)
             entries[(int(t), j)] = a - s
             stats[(int(t), j)] = st
         # self weights (the own patch is masked out of the far sum, nothing to subtract)
@@ -182,16 +203,20 @@ def far_sources(patches, q, sigma, node_off):
             np.concatenate(pid))
 
 
-def apply_corrected(corr: Corrections, node_off, sigma, tgt_xyz, kind, k, alpha=1.0, beta=0.0):
+def apply_corrected(corr: Corrections, node_off, sigma, tgt_xyz, kind, k, alpha=1.0, beta=0.0,
+                    tgt_node=None, tgt_normal=None):
     """u(x_t) = far sum over the oversampled sources of every patch but the target's own
-    + CSR correction (Sec. 5.3)."""
+    + CSR correction (Sec. 5.3).  S' (kind "Sp") needs tgt_node (and tgt_normal for
+    off-surface targets) for the target normals."""
     kern = Kern(kind, k, alpha, beta)
     X, N, strength, pid = far_sources(corr.patches, corr.q, sigma, node_off)
     nt = tgt_xyz.shape[1]
+    nrm = (target_normals(corr.patches, node_off, tgt_node, tgt_normal) if kind == "Sp"
+           else np.zeros((3, nt)))
     u = np.zeros(nt, dtype=np.complex128)
     for t in range(nt):
         keep = pid != corr.tgt_patch[t]
-        u[t] = (kern(tgt_xyz[:, t], X[:, keep], N[:, keep]) * strength[keep]).sum()
+        u[t] = (kern(tgt_xyz[:, t], X[:, keep], N[:, keep], nrm[:, t]) * strength[keep]).sum()
         a, b = corr.row_ptr[t], corr.row_ptr[t + 1]
         u[t] += (corr.val[a:b] * sigma[corr.col[a:b]]).sum()
     return u

@@ -19,18 +19,27 @@ class Kern:
     def __init__(self, kind, k, alpha=1.0, beta=0.0):
         self.kind, self.k, self.alpha, self.beta = kind, complex(k), complex(alpha), complex(beta)
 
-    def __call__(self, x, X, N):
-        return kernel_jac(x, X, N, self.k, self.kind, self.alpha, self.beta)
+    def __call__(self, x, X, N, nx=None):
+        return kernel_jac(x, X, N, self.k, self.kind, self.alpha, self.beta, nx)
 
     def envelope(self, x, X, N, R):
         return kernel_envelope(x, X, N, self.k, self.kind, self.alpha, self.beta, R)
 
 
-def rule_moments(patch, x, ru, rv, rw, kern):
+def rule_moments(patch, x, ru, rv, rw, kern, nx=None):
     """I_nm(x) by one rule (u_q, v_q, w_q) on T0: sum_q w_q K(x, X_q) J_q K_nm(u_q, v_q).
-    Positions are taken relative to the patch centroid (x - c_j against X - c_j)."""
+    Positions are taken relative to the patch centroid (x - c_j against X - c_j); nx is
+    the target normal of S'."""
     X, N, K = patch.eval_rel(ru, rv)
-    return K @ (rw * kern(np.asarray(x) - patch.c, X, N))
+    return K @ (rw * kern(np.asarray(x) - patch.c, X, N, nx))
+
+
+def radial_normal(patch, x):
+    """Target normal given to S' at a far-order test point: the unit vector from c_j to x
+    (a reading: the paper's test points carry no normal)."""
+    d = np.asarray(x, dtype=np.float64) - patch.c
+    r = np.linalg.norm(d)
+    return d / r if r > 0.0 else np.array([0.0, 0.0, 1.0])
 
 
 def far_order(patch, test_pts, kern, eps, m_min, m_max):
@@ -43,7 +52,8 @@ def far_order(patch, test_pts, kern, eps, m_min, m_max):
     def mom(m):
         ru, rv, rw = rules.conical_rule(m)
         X, N, K = patch.eval_rel(ru, rv)
-        return [K @ (rw * kern(np.asarray(x) - patch.c, X, N)) for x in test_pts]
+        return [K @ (rw * kern(np.asarray(x) - patch.c, X, N, radial_normal(patch, x)))
+                for x in test_pts]
 
     prev = mom(m_min)
     margin = np.inf
@@ -57,10 +67,10 @@ def far_order(patch, test_pts, kern, eps, m_min, m_max):
     return m_max, True, margin
 
 
-def smooth_weights(patch, x, m, kern):
+def smooth_weights(patch, x, m, kern, nx=None):
     """Weights the smooth rule m puts on the nodes: s_l(x) = sum_q w_q K J (K(u_q) V)_l (Sec. 4.2 Remark)."""
     ru, rv, rw = rules.conical_rule(m)
-    return patch.V.T @ rule_moments(patch, x, ru, rv, rw, kern)
+    return patch.V.T @ rule_moments(patch, x, ru, rv, rw, kern, nx)
 
 
 def conformal_map(patch, i):
@@ -70,6 +80,13 @@ def conformal_map(patch, i):
     A = np.stack([patch.coefs.T @ Ku[:, 0], patch.coefs.T @ Kv[:, 0]], axis=1)
     lam, Q = np.linalg.eigh(A.T @ A)
     return Q @ np.diag(lam ** -0.5) @ Q.T
+
+
+def node_normal(patch, i):
+    """Unit normal of the chart at node i (the target normal of S' for on-surface targets)."""
+    un, vn = rules.interp_nodes(patch.d)
+    _, N, _ = patch.eval(un[i:i + 1], vn[i:i + 1])
+    return N[:, 0] / np.linalg.norm(N[:, 0])
 
 
 def self_weights(patch, i, x, kern, order):
@@ -84,7 +101,7 @@ def self_weights(patch, i, x, kern, order):
     un, vn = rules.interp_nodes(patch.d)
     _, N, K = patch.eval_rel(ru, rv)
     dX = patch.coefs.T @ kw.basis_delta(patch.d, (un[i], vn[i]), du, dv)
-    g = kern(np.zeros(3), dX, N)
+    g = kern(np.zeros(3), dX, N, node_normal(patch, i) if kern.kind == "Sp" else None)
     return patch.V.T @ (K @ (rw * g))
 
 
@@ -108,7 +125,7 @@ class LeafCache:
 ROUNDING_FLOOR = 2e-13
 
 
-def adaptive_moments(cache: LeafCache, x, kern, tol0, max_depth, record=None):
+def adaptive_moments(cache: LeafCache, x, kern, tol0, max_depth, record=None, nx=None):
     """Adaptive integration of I_nm(x) over T0 by midpoint subdivision (Sec. 4.3).
 
     A triangle T at level L (|T|/|T0| = 4^-L) is compared with its 4 children;
@@ -121,14 +138,14 @@ def adaptive_moments(cache: LeafCache, x, kern, tol0, max_depth, record=None):
     targets near the tangent plane).  Children at level max_depth are not tested
     further: their sum is accepted and the depth flag set.
     Returns (I [n], stats dict).  With `record` (a list), the accepted leaf triangles
-    (the children of every accepted triangle) are appended to it.
+    (the children of every accepted triangle) are appended to it.  nx: target normal (S').
     """
     patch = cache.patch
     xr = np.asarray(x) - patch.c
 
     def moments(path, T):
         X, N, K, w = cache.get(path, T)
-        return K @ (w * kern(xr, X, N))
+        return K @ (w * kern(xr, X, N, nx))
 
     def envelope(path, T):
         X, N, K, w = cache.get(path, T)

@@ -71,3 +71,38 @@ def test_sphere_single_layer_eigenvalue_converges():
         u = C.apply_corrected(corr, s.node_off, np.ones(s.n_points, complex), x, "S", k)
         errs.append(np.abs(u - lam).max() / abs(lam))
     assert errs[1] < 0.2 * errs[0] and errs[2] < 0.2 * errs[1] and errs[2] < 3e-3, errs
+
+
+def test_sphere_adjoint_double_layer_eigenvalue_converges():
+    """S' (normal derivative of S at the target) on the unit sphere with outward normals:
+    S'_k Y_0 = (i k^2 / 2)(j_0 h_0' + j_0' h_0) Y_0, the same eigenvalue as D there
+    (truth.sphere_eigen_D); the error of the full pipeline falls with the chart error."""
+    k = 1.0
+    lam = truth.sphere_eigen_D(0, k)
+    errs = []
+    for sdiv, d in ((1, 2), (1, 4), (1, 6)):
+        s = workloads.ellipsoid(sdiv, d)
+        x, tn = workloads.onsurface_targets(s)
+        p = C.Params(eps=1e-7, eta=1.25, test_dirs=workloads.test_directions(4))
+        corr = C.gen_corrections(s.deg, s.node_off, s.xyz, x, tn, "Sp", k, params=p)
+        u = C.apply_corrected(corr, s.node_off, np.ones(s.n_points, complex), x, "Sp", k,
+                              tgt_node=tn)
+        errs.append(np.abs(u - lam).max() / abs(lam))
+    assert errs[1] < 0.2 * errs[0] and errs[2] < 0.2 * errs[1] and errs[2] < 3e-3, errs
+
+
+def test_adjoint_double_layer_kernel_is_normal_derivative_of_single_layer():
+    """kernel_jac "Sp" equals the central difference of the S kernel along the target
+    normal (x + h n_x)."""
+    from oracle.kernels import kernel_jac
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal(3)
+    X = x[:, None] + rng.uniform(0.3, 2.0, 5) * rng.standard_normal((3, 5))
+    N = rng.standard_normal((3, 5))
+    nx = rng.standard_normal(3)
+    nx /= np.linalg.norm(nx)
+    for k in (0.0, 1.7, 2.0 + 0.5j):
+        h = 1e-6
+        fd = (kernel_jac(x + h * nx, X, N, k, "S") - kernel_jac(x - h * nx, X, N, k, "S")) / (2 * h)
+        got = kernel_jac(x, X, N, k, "Sp", nx=nx)
+        assert np.abs(fd - got).max() <= 1e-7 * np.abs(got).max()
