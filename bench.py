@@ -55,8 +55,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--batched-scale", type=float, default=0.05,
-                    help="patch-count scale of the 64-torus batch variant (0: skip it)")
+    ap.add_argument("--batched-scale", type=float, default=0.0,
+                    help="patch-count scale of the 64-torus batch variant (0: skip it; 1: the "
+                         "full batch, about three minutes)")
+    ap.add_argument("--no-table1", action="store_true",
+                    help="skip the twisted-torus sweep over order p and eps (the paper's Table 1)")
     ap.add_argument("--large", action="store_true",
                     help="also time the 40,000-patch torus (k=20, eps=1e-9), FP64 and mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -209,6 +212,7 @@ def run_ours(args, rank, world, local_rank):
     B.build()
     from paper_2006_02545_gb300 import lcq
     from paper_2006_02545_gb300 import workloads as W
+    from paper_2006_02545_gb300.replicas import job_throughput, max_over_ranks
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -267,12 +271,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop() if clocks else None
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * N * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dev)
+    value = job_throughput(N, args.steps, world, total_ms)
 
     # FP64 vs mixed at eps = 1e-9 and 1e-6: throughput and the applied potential's
     # relative L2 difference from the FP64 result on the same density
@@ -303,6 +303,7 @@ def run_ours(args, rank, world, local_rank):
                         corr.close()
                         near.close()
                 u = lcq.apply_corrected_CFIE(ctx, ds, near, corr, sig, NT).cpu().numpy()
+                val = corr.export(NT)[2].copy()
                 corr.close()
                 near.close()
                 key = f"{prec}_eps{eps:g}"
@@ -310,10 +311,12 @@ def run_ours(args, rank, world, local_rank):
                        "ms_per_step": statistics.mean(times), "adaptive_ms": statistics.mean(ad),
                        "status": st}
                 if prec == "fp64":
-                    ref_u[eps] = u
+                    ref_u[eps] = (u, val)
                 else:
-                    rec["rel_l2_vs_fp64"] = float(np.linalg.norm(u - ref_u[eps]) /
-                                                  np.linalg.norm(ref_u[eps]))
+                    ru, rv = ref_u[eps]
+                    rec["rel_l2_vs_fp64"] = float(np.linalg.norm(u - ru) / np.linalg.norm(ru))
+                    rec["csr_rel_l2_vs_fp64"] = float(np.linalg.norm(val - rv) / np.linalg.norm(rv))
+                    rec["fp32_used"] = eps >= 1e-7
                 variants[key] = rec
 
     # 64 independent tori in one batched generation against the same surfaces one by one
@@ -370,6 +373,39 @@ def run_ours(args, rank, world, local_rank):
                    "one_by_one": {"value": bs.n_points / (one_ms / 1e3), "ms": one_ms,
                                   "launches": int(one_launches)}}
         del bds, bx_d, btn_d
+
+    # the paper's Table 1 on its twisted torus (2400 patches, S, k = 1): oversampling
+    # alpha = N_over / N, stored corrections per point m = nnz / N and S_init = N / T_init
+    # for p = d + 1 in {2, 3, 4, 6, 8} and eps in {5e-3, 5e-4, 5e-7, 5e-10}
+    table1 = None
+    if not args.no_variants and not args.no_table1:
+        table1 = []
+        for d in (1, 2, 3, 5, 7):
+            ts = W.stellarator(20, 60, d)
+            tx, ttn = W.onsurface_targets(ts)
+            tds = lcq.DeviceSurface(ts.deg, ts.node_off, torch.from_numpy(ts.xyz).to(dev))
+            tx_d1 = torch.from_numpy(tx).to(dev)
+            ttn_d1 = torch.from_numpy(ttn).to(dev)
+            for eps in (5e-3, 5e-4, 5e-7, 5e-10):
+                tp = lcq.params(eps, test_dirs=W.test_directions(7))
+                ms = []
+                for it in range(2):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    near = lcq.build_near_lists(ctx, tds, tx_d1, ttn_d1, tp)
+                    corr = lcq.gen_corrections(ctx, tds, near, "S", 1.0, tp)
+                    e1.record(stream)
+                    st_t = ctx.sync()
+                    ms.append(e0.elapsed_time(e1))
+                    nnz, n_over = corr.info()
+                    corr.close()
+                    near.close()
+                table1.append({"p": d + 1, "eps": eps, "points": ts.n_points,
+                               "alpha": n_over / ts.n_points, "m": nnz / ts.n_points,
+                               "S_init": ts.n_points / (ms[-1] / 1e3), "status": st_t})
+            del tds, tx_d1, ttn_d1
 
     # the 40,000-patch torus (k = 20, eps = 1e-9), FP64 and mixed, one timed step each
     large = None
@@ -436,12 +472,8 @@ def run_ours(args, rank, world, local_rank):
             near.close()
             if it >= args.warmup:
                 e2e_t.append(t1 - t0)
-        tot = sum(e2e_t)
-        if world > 1:
-            t = torch.tensor([tot], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            tot = float(t.item())
-        e2e = {"value": world * N * len(e2e_t) / tot, "unit": UNIT,
+        tot = max_over_ranks(sum(e2e_t), dev)
+        e2e = {"value": job_throughput(N, len(e2e_t), world, tot * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(xyz_h.numel() * 8 + tx_h.numel() * 8 + tn_h.numel() * 8),
                "d2h_bytes_per_step": int((NT + 1) * 8 + nnz * 4 + nnz * 16)}
 
@@ -481,6 +513,7 @@ def run_ours(args, rank, world, local_rank):
                                "v2c"], st_mean)),
         "variants": variants,
         "batched": batched,
+        "table1": table1,
         "large": large,
         "wall_s_timed_region": t_wall,
     }

@@ -53,17 +53,23 @@ typedef enum {
 /* Layer potential kernels (Sec. 3, Eq. sldef / dldef / urep):
  *   LCQ_S    : G_k(x,y) = e^{ik|x-y|} / (4 pi |x-y|)
  *   LCQ_D    : n(y) . grad_y G_k(x,y)   (n outward)
- *   LCQ_CFIE : alpha D + beta S          (the paper's D - ik S is alpha = 1, beta = -ik) */
-typedef enum { LCQ_S = 0, LCQ_D = 1, LCQ_CFIE = 2 } lcq_kernel;
+ *   LCQ_CFIE : alpha D + beta S          (the paper's D - ik S is alpha = 1, beta = -ik)
+ *   LCQ_SP   : S' = n(x) . grad_x G_k(x,y), the adjoint double layer of Neumann problems
+ *              (Sec. 3).  n(x) is the target's unit normal: for an on-surface target the
+ *              chart normal at its node, for an off-surface target the caller's
+ *              (lcq_near_set_target_normals); far-order test points use the direction
+ *              from the patch centroid.  LCQ_MIXED falls back to FP64 for S'. */
+typedef enum { LCQ_S = 0, LCQ_D = 1, LCQ_CFIE = 2, LCQ_SP = 3 } lcq_kernel;
 
 /* LCQ_FP64: every step in FP64.
  * LCQ_MIXED: in the adaptive near integration, leaf nodes farther from the target than
  * twice the size of their subtriangle get their kernel value in FP32 (the difference
  * x - X, the phase k r and its reduction stay FP64); everything else -- self rules,
  * refinement estimates, moments accumulation, the values-to-coefficients contraction --
- * stays FP64.  Such nodes raise the adaptive test's rounding floor to the FP32 level, so
- * the result differs from LCQ_FP64 by about 1e-7 relative (stated per result by the
- * tests and the benchmark). */
+ * stays FP64.  Such nodes raise the adaptive test's rounding floor to the FP32 level.
+ * FP32's unit roundoff (6e-8) cannot hold tighter tolerances, so the FP32 evaluation is
+ * used only for eps >= 1e-7 (per surface in a batch); below, LCQ_MIXED is LCQ_FP64.  The
+ * difference from LCQ_FP64 is stated per result by the tests and the benchmark. */
 typedef enum { LCQ_FP64 = 0, LCQ_MIXED = 1 } lcq_precision;
 
 /* Surface: n_patches charts; patch j owns nodes node_off[j] .. node_off[j+1]-1,
@@ -135,6 +141,11 @@ lcq_status lcq_near_info(const lcq_near* near, int64_t* n_pairs, int64_t* n_self
  * radius R[n_patches].  Any pointer may be NULL to skip it. */
 lcq_status lcq_near_export(lcq_near* near, int64_t* pair_ptr, int32_t* tgt, uint8_t* adaptive,
                            double* centroid, double* radius);
+
+/* Normals of the targets for LCQ_SP: device double SoA [3][NT] (copied; only the
+ * off-surface targets' columns are used, normalized by the library).  Required before an
+ * S' generation when the near lists have off-surface targets. */
+lcq_status lcq_near_set_target_normals(lcq_near* near, const double* tgt_normal);
 
 void lcq_near_destroy(lcq_near* near);
 
@@ -215,6 +226,9 @@ lcq_status lcq_apply_corrected_D(lcq_ctx* ctx, const lcq_surface* surf, const lc
 lcq_status lcq_apply_corrected_CFIE(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
                                     const lcq_corr* corr, const double* sigma, double jump,
                                     double* out);
+lcq_status lcq_apply_corrected_Sp(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                                  const lcq_corr* corr, const double* sigma, double jump,
+                                  double* out);
 
 /* ---- Adjoint (no counterpart in the paper).  For a real functional L of the
  * corrected potential u = A(y) sigma with upstream gradient g = dL/d(conj u)
@@ -255,7 +269,8 @@ lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out8);
  * CUDA events recorded on the context's stream (host out, milliseconds):
  *   ms[0] near lists (geometry + both orientations)   ms[1] far order q_j
  *   ms[2] smooth-rule and annulus moments              ms[3] adaptive near moments
- *   ms[4] self weights                                 ms[5] V contraction into the CSR
+ *   ms[4] self weights (on an internal side stream, concurrently with ms[1]-ms[3])
+ *   ms[5] V contraction into the CSR
  * *launches receives the number of kernels those two calls launched.  Synchronizes. */
 lcq_status lcq_stage_times(lcq_ctx* ctx, float* ms6, int64_t* launches);
 

@@ -69,6 +69,24 @@ class Corrections:
     tgt_patch: np.ndarray = None                       # own patch of each target (-1: off surface)
 
 
+class LazyPatches:
+    """Patches built on first use (for runs restricted to a few patches of a large
+    surface)."""
+
+    def __init__(self, deg, node_off, xyz):
+        self.deg, self.node_off, self.xyz = deg, node_off, xyz
+        self.memo = {}
+
+    def __len__(self):
+        return len(self.deg)
+
+    def __getitem__(self, j):
+        if j not in self.memo:
+            a, b = self.node_off[j], self.node_off[j + 1]
+            self.memo[j] = geometry.make_patch(int(self.deg[j]), self.xyz[:, a:b])
+        return self.memo[j]
+
+
 def patch_of_node(node_off, tgt_node):
     tp = np.full(tgt_node.shape, -1, dtype=np.int64)
     on = tgt_node >= 0
@@ -105,14 +123,18 @@ def gen_corrections(deg, node_off, xyz, tgt_xyz, tgt_node, kind, k, alpha=1.0, b
     node_off = np.asarray(node_off)
     tgt_node = np.asarray(tgt_node)
     if patches is None:
-        patches = geometry.make_patches(deg, node_off, xyz)
+        patches = (geometry.make_patches(deg, node_off, xyz) if only_patches is None
+                   else LazyPatches(deg, node_off, xyz))
     npat = len(patches)
     tgt_patch = patch_of_node(node_off, tgt_node)
     eta = np.array([p.eta if p.eta > 0 else geometry.default_eta(int(d)) for d in deg])
     eta1 = np.minimum(p.eta1, eta)
-    centers = np.array([pt.c for pt in patches])
-    radii = np.array([pt.R for pt in patches])
-    near = nearlist.near_lists(centers, radii, eta, eta1, tgt_xyz, tgt_patch)
+    listed = range(npat) if only_patches is None else only_patches
+    centers = np.zeros((npat, 3))
+    radii = np.zeros(npat)
+    for j in listed:
+        centers[j], radii[j] = patches[j].c, patches[j].R
+    near = nearlist.near_lists(centers, radii, eta, eta1, tgt_xyz, tgt_patch, only_patches)
     nrm = target_normals(patches, node_off, tgt_node, tgt_normal) if kind == "Sp" else None
     dirs = fibonacci_dirs() if p.test_dirs is None else np.asarray(p.test_dirs)
     self_order = p.self_order if p.self_order > 0 else rules.default_self_order(p.eps)

@@ -10,10 +10,15 @@ from __future__ import annotations
 import numpy as np
 
 
-def near_lists(centers, radii, eta, eta1, tgt_xyz, tgt_patch):
-    """Per patch: (ascending target ids, adaptive flags, squared distances)."""
+def near_lists(centers, radii, eta, eta1, tgt_xyz, tgt_patch, only=None):
+    """Per patch: (ascending target ids, adaptive flags, squared distances).  With `only`,
+    the lists of the other patches are left empty (their centers and radii are unused)."""
     out = []
+    keep = None if only is None else set(int(j) for j in only)
     for j in range(len(radii)):
+        if keep is not None and j not in keep:
+            out.append((np.zeros(0, np.int64), np.zeros(0, bool), np.zeros(0)))
+            continue
         c = centers[j]
         d2 = ((tgt_xyz - c[:, None]) ** 2).sum(axis=0)
         near = (d2 <= (eta[j] * radii[j]) ** 2) & (tgt_patch != j)

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_grad_rules(
     const int mn = qn[j];
     if (na > 0 && mn > 0) {
       const int32_t* pl = dv.an_pair + a0;
-      TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl};
+      TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl, dv.tnrm};
       block_grad<D>(cf, dv.ru + dv.roff[mn], dv.rv + dv.roff[mn], dv.rw + dv.roff[mn], mn * mn,
                     segs, 1, ta, (int)na,
                     [&](int i) -> cplx {
@@ -253,8 +253,11 @@ __global__ void __launch_bounds__(kThreads) k_far_sum_T(
     if (on)
       for (int i = 0; i < cnt; ++i) {
         if (stp[i] == j || sgr[i] != grp) continue;
+        const int64_t tt = t0 + i;
+        const double nx[3] = {dv.tnrm ? dv.tnrm[tt] : 0.0, dv.tnrm ? dv.tnrm[dv.NT + tt] : 0.0,
+                              dv.tnrm ? dv.tnrm[2 * dv.NT + tt] : 0.0};
         const cplx k = kernel_eval(kq, sx[0][i], sx[1][i], sx[2][i], s[0], s[1], s[2], s[3], s[4],
-                                   s[5], s[6]);
+                                   s[5], s[6], 0.0, nullptr, nx);
         // conj(k) * g
         re += k.re * sg[i].re + k.im * sg[i].im;
         im += k.re * sg[i].im - k.im * sg[i].re;

@@ -209,6 +209,10 @@ lcq_status lcq_create(lcq_ctx** out, int device, void* cuda_stream) {
   CK(upload_constants(ctx->stream));
   CK(upload_constants_adjoint(ctx->stream));
   for (int i = 0; i < 8; ++i) CK(cudaEventCreate(&ctx->ev[i]));
+  CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming));
+  for (int i = 0; i < 2; ++i) CK(cudaEventCreate(&ctx->ev_self[i]));
   lcq_status s = ensure_rules(ctx);
   if (s != LCQ_OK) {
     lcq_destroy(ctx);
@@ -238,6 +242,14 @@ void lcq_destroy(lcq_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (int i = 0; i < 8; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
+  if (ctx->join) cudaEventDestroy(ctx->join);
+  for (int i = 0; i < 2; ++i)
+    if (ctx->ev_self[i]) cudaEventDestroy(ctx->ev_self[i]);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_counters);
   cudaFree(ctx->d_sched);
@@ -277,6 +289,8 @@ lcq_status lcq_stage_times(lcq_ctx* ctx, float* ms6, int64_t* launches) {
   if (ms6) {
     CK(cudaEventElapsedTime(&ms6[0], ctx->ev[0], ctx->ev[1]));
     for (int i = 0; i < 5; ++i) CK(cudaEventElapsedTime(&ms6[1 + i], ctx->ev[2 + i], ctx->ev[3 + i]));
+    // the self weights run on the side stream, concurrently with stages 1-3
+    CK(cudaEventElapsedTime(&ms6[4], ctx->ev_self[0], ctx->ev_self[1]));
   }
   if (launches) *launches = ctx->launches_near + ctx->launches_corr;
   return LCQ_OK;
@@ -576,6 +590,20 @@ lcq_status lcq_build_near_lists_batched(lcq_ctx* ctx, const lcq_surface* surf, i
                          NT, params, out);
 }
 
+lcq_status lcq_near_set_target_normals(lcq_near* nr, const double* tgt_normal) {
+  if (!nr || !tgt_normal) return LCQ_ERR_ARG;
+  lcq_ctx* ctx = nullptr;
+  CK(cudaSetDevice(nr->device));
+  cudaStream_t st = nr->stream;
+  if (!nr->unrm) CK(dalloc(st, &nr->unrm, (size_t)3 * std::max<int64_t>(nr->n_targets, 1)));
+  if (nr->n_targets > 0)
+    CK(cudaMemcpyAsync(nr->unrm, tgt_normal, (size_t)3 * nr->n_targets * 8,
+                       cudaMemcpyDeviceToDevice, st));
+  dfree(st, nr->tnrm);  // recomputed at the next S' generation
+  nr->tnrm = nullptr;
+  return LCQ_OK;
+}
+
 lcq_status lcq_near_info(const lcq_near* nr, int64_t* n_pairs, int64_t* n_self,
                          int64_t* n_adaptive, int64_t* nnz) {
   if (!nr) return LCQ_ERR_ARG;
@@ -627,6 +655,8 @@ void lcq_near_destroy(lcq_near* nr) {
   dfree(st, nr->tgt_lnode);
   dfree(st, nr->pgroup);
   dfree(st, nr->tgroup);
+  dfree(st, nr->unrm);
+  dfree(st, nr->tnrm);
   dfree(st, nr->row_ptr);
   dfree(st, nr->rowp_ptr);
   dfree(st, nr->rowp_patch);
@@ -654,6 +684,7 @@ static Dev make_dev(lcq_ctx* ctx, const lcq_near* nr, const int32_t* q, int ldI,
   Dev dv{};
   dv.pgroup = grp ? nr->pgroup : nullptr;
   dv.grp = grp;
+  dv.tnrm = nr->tnrm;
   dv.coef = nr->coef;
   dv.node_off = nr->node_off;
   dv.cen = nr->cen;
@@ -729,7 +760,10 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   *out = nullptr;
   if (precision != LCQ_FP64 && precision != LCQ_MIXED)
     return fail(ctx, LCQ_ERR_ARG, "unsupported precision");
-  if ((int)kernel < 0 || (int)kernel > 2) return fail(ctx, LCQ_ERR_ARG, "unknown kernel");
+  if ((int)kernel < 0 || (int)kernel > 3) return fail(ctx, LCQ_ERR_ARG, "unknown kernel");
+  if (kernel == LCQ_SP && nr->n_targets > nr->n_self && !nr->unrm)
+    return fail(ctx, LCQ_ERR_ARG, "S' needs the normals of off-surface targets "
+                                  "(lcq_near_set_target_normals)");
   if (n_phys != nr->n_groups)
     return fail(ctx, LCQ_ERR_ARG, "one physics record per surface of the near lists");
   for (int g = 0; g < n_phys; ++g) {
@@ -821,6 +855,17 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
                        st));
     c->grp_h = gp;
   }
+  if (kernel == LCQ_SP && !nr->tnrm && nr->n_targets > 0) {
+    lcq_near* nw = const_cast<lcq_near*>(nr);
+    CK(dalloc(st, &nw->tnrm, (size_t)3 * nr->n_targets));
+    Dev d0 = make_dev(ctx, nr, c->q, ldI, c->grp);
+    bool first = true;
+    for (int d = 1; d <= kMaxDeg; ++d) {
+      if (!nr->plist_count[d]) continue;
+      launch_tgt_normals(d, lc, d0, nr->deg, nr->unrm, first && nr->unrm, nw->tnrm);
+      first = false;
+    }
+  }
   Dev dv = make_dev(ctx, nr, c->q, ldI, c->grp);
 
   CK(cudaEventRecord(ctx->ev[2], st));
@@ -843,6 +888,7 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   }
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[4], st));
+  CK(cudaEventRecord(ctx->fork, st));
   // 4. adaptive near moments (Sec. 4.3)
   if (nr->n_adaptive > 0) {
     const int levels = params->max_depth;
@@ -855,19 +901,30 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
       launch_adaptive(d, lc, nr->ad_list_dev[d], nr->ad_count[d], dv, kp,
                       eps0 * params->eps_loosen, ctx->deg[d].normV, params->leaf_order,
                       params->max_depth, Is, In, c->leaves, ctx->work, stride, (int)A, levels, agrid,
-                      ctx->d_status, ctx->d_sched + d, precision == LCQ_MIXED ? 2.0 : 0.0);
+                      ctx->d_status, ctx->d_sched + d,
+                      precision == LCQ_MIXED && kernel != LCQ_SP &&
+                              (nr->grouped || eps0 >= kMixedMinEps) ? 2.0 : 0.0);
     }
     CK(cudaGetLastError());
   }
-  CK(cudaEventRecord(ctx->ev[5], st));
-  // 5. self weights (Sec. 4, Eq. errestself)
+  // 5. self weights (Sec. 4, Eq. errestself), on the side stream: released together with
+  // the adaptive kernel but queued after it, so that their blocks take the SMs the
+  // persistent adaptive blocks release at the end of their work instead of delaying them
   const int sorder = params->self_order > 0 ? params->self_order : default_self_order(eps0);
-  if (nr->n_self > 0)
+  CK(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
+  CK(cudaEventRecord(ctx->ev_self[0], ctx->side));
+  if (nr->n_self > 0) {
+    LaunchCommon ls{ctx->side, ctx->num_sms, &ctx->launches_corr};
     for (int d = 1; d <= kMaxDeg; ++d) {
       if (!nr->plist_count[d]) continue;
-      launch_self(d, lc, dv, nr->deg, kp, sorder, InS);
+      launch_self(d, ls, dv, nr->deg, kp, sorder, InS);
     }
+  }
   CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev_self[1], ctx->side));
+  CK(cudaEventRecord(ctx->join, ctx->side));
+  CK(cudaEventRecord(ctx->ev[5], st));
+  CK(cudaStreamWaitEvent(st, ctx->join, 0));  // self weights done
   CK(cudaEventRecord(ctx->ev[6], st));
   // 6. c = V^T (I_near - I_smooth) into the CSR
   for (int d = 1; d <= kMaxDeg; ++d) {
@@ -997,7 +1054,8 @@ static lcq_status apply_impl(lcq_ctx* ctx, const lcq_near* nr, const lcq_corr* c
                    c->src_off, sigma, src, c->n_over);
   }
   launch_far_sum(lc, nr->tgt, nr->n_targets, src, c->n_over, c->kp, nr->tgt_patch, c->src_off,
-                 c->grp ? nr->tgroup : nullptr, c->grp, c->gsrc, out);
+                 c->grp ? nr->tgroup : nullptr, c->grp, c->gsrc,
+                 kind == LCQ_SP ? nr->tnrm : nullptr, out);
   launch_csr_apply(lc, nr->row_ptr, nr->col, c->val, sigma, nr->tnode, nr->n_targets, jump, out);
   CK(cudaGetLastError());
   dfree(st, src);
@@ -1021,6 +1079,12 @@ lcq_status lcq_apply_corrected_CFIE(lcq_ctx* ctx, const lcq_surface* surf, const
                                     double* out) {
   (void)surf;
   return apply_impl(ctx, near, corr, sigma, jump, out, LCQ_CFIE);
+}
+lcq_status lcq_apply_corrected_Sp(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                                  const lcq_corr* corr, const double* sigma, double jump,
+                                  double* out) {
+  (void)surf;
+  return apply_impl(ctx, near, corr, sigma, jump, out, LCQ_SP);
 }
 
 // Oversampled far sources of every patch (positions, weighted normals, J w, interpolated
@@ -1077,6 +1141,8 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
   if (cc->near != nr) return fail(ctx, LCQ_ERR_ARG, "corrections belong to another near list");
   if (nr->n_self > 0)
     return fail(ctx, LCQ_ERR_ARG, "shape gradient: off-surface targets only (no self pairs)");
+  if (cc->kernel == LCQ_SP)
+    return fail(ctx, LCQ_ERR_ARG, "shape gradient: S, D or CFIE only");
   lcq_corr* c = const_cast<lcq_corr*>(cc);
   CK(cudaSetDevice(ctx->device));
   lcq_status s = ensure_q_host(ctx, c);
@@ -1132,7 +1198,8 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
                            c->eps0 * pr.eps_loosen, ctx->deg[d].normV, pr.leaf_order, pr.max_depth,
                            Is, In, leaves, ctx->work, stride, (int)nr->max_adaptive, levels, agrid,
                            ctx->d_status, ctx->d_sched + d,
-                           c->precision == LCQ_MIXED ? 2.0 : 0.0, ga);
+                           c->precision == LCQ_MIXED && (nr->grouped || c->eps0 >= kMixedMinEps)
+                               ? 2.0 : 0.0, ga);
     }
     dfree(st, Is);
     dfree(st, In);

@@ -75,7 +75,7 @@ struct Cfg {
   static constexpr int BS = n + 1;
   static constexpr int TT = 16;
   // doubles of shared workspace used by block_moments
-  static constexpr int WS = CH * BS + 7 * CH + 3 * TT * CH + 3 * TT;
+  static constexpr int WS = CH * BS + 7 * CH + 3 * TT * CH + 6 * TT;
 };
 
 struct SegMap {
@@ -106,6 +106,7 @@ __device__ void block_moments(const double* cf, const double* __restrict__ ru,
   cplx* G = reinterpret_cast<cplx*>(Js + C::CH);
   double* Ev = reinterpret_cast<double*>(G + C::TT * C::CH);
   double* tx = Ev + C::TT * C::CH;
+  double* tn = tx + 3 * C::TT;  // target normals (S')
   const int total = nseg * Q;
   for (int c0 = 0; c0 < total; c0 += C::CH) {
     const int nch = min(C::CH, total - c0);
@@ -138,6 +139,7 @@ __device__ void block_moments(const double* cf, const double* __restrict__ ru,
         xp[0] -= cen[0];
         xp[1] -= cen[1];
         xp[2] -= cen[2];
+        if (kp.kind == 3) ta.nrm(t0 + threadIdx.x, xp, tn + 3 * threadIdx.x);
       }
       __syncthreads();
       for (int e = threadIdx.x; e < nt * C::CH; e += blockDim.x) {
@@ -162,7 +164,7 @@ __device__ void block_moments(const double* cf, const double* __restrict__ ru,
           else
             g = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql], Xs[C::CH + ql],
                             Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql],
-                            Js[ql], R, ENV ? &ev : nullptr);
+                            Js[ql], R, ENV ? &ev : nullptr, tn + 3 * i);
         }
         G[i * C::CH + ql] = g;
         if (ENV) Ev[i * C::CH + ql] = ev;
@@ -210,27 +212,41 @@ __device__ __forceinline__ void load_coef(const double* __restrict__ coef, int64
   for (int e = threadIdx.x; e < 3 * n; e += blockDim.x) cf[e] = coef[off * 3 + e];
 }
 
+// Target accessors of block_moments: pos(i, x) the position of target i; nrm(i, xrel, n)
+// its unit normal for S' (the caller's normals tn, SoA [3][NT]; for bare test points the
+// radial direction from the centroid, xrel being the position relative to it).
+__device__ __forceinline__ void read_nrm(const double* tn, int64_t NT, int64_t t, double* n) {
+  n[0] = tn[t];
+  n[1] = tn[NT + t];
+  n[2] = tn[2 * NT + t];
+}
 struct TgtIdx {  // targets by id list
   const double* tgt;
   int64_t NT;
   const int32_t* ids;
+  const double* tn;
   __device__ void pos(int i, double* x) const {
     const int64_t t = ids[i];
     x[0] = tgt[t];
     x[1] = tgt[NT + t];
     x[2] = tgt[2 * NT + t];
   }
+  __device__ void nrm(int i, const double*, double* n) const { read_nrm(tn, NT, ids[i], n); }
 };
 struct TgtPairIdx {  // targets of pair ids
   const double* tgt;
   int64_t NT;
   const int32_t* pair_tgt;
   const int32_t* pairs;
+  const double* tn;
   __device__ void pos(int i, double* x) const {
     const int64_t t = pair_tgt[pairs[i]];
     x[0] = tgt[t];
     x[1] = tgt[NT + t];
     x[2] = tgt[2 * NT + t];
+  }
+  __device__ void nrm(int i, const double*, double* n) const {
+    read_nrm(tn, NT, pair_tgt[pairs[i]], n);
   }
 };
 struct TgtPts {  // explicit points [i][3]
@@ -240,6 +256,17 @@ struct TgtPts {  // explicit points [i][3]
     x[1] = p[3 * i + 1];
     x[2] = p[3 * i + 2];
   }
+  __device__ void nrm(int, const double* xr, double* n) const {
+    const double r = sqrt(xr[0] * xr[0] + xr[1] * xr[1] + xr[2] * xr[2]);
+    if (r > 0.0) {
+      n[0] = xr[0] / r;
+      n[1] = xr[1] / r;
+      n[2] = xr[2] / r;
+    } else {
+      n[0] = n[1] = 0.0;
+      n[2] = 1.0;
+    }
+  }
 };
 
 struct TgtAdaptive {  // targets of a union-tree node: local ids -> pairs -> targets
@@ -248,11 +275,15 @@ struct TgtAdaptive {  // targets of a union-tree node: local ids -> pairs -> tar
   const int32_t* pair_tgt;
   const int32_t* apairs;
   const int* ST;
+  const double* tn;
   __device__ void pos(int i, double* x) const {
     const int64_t t = pair_tgt[apairs[ST[i]]];
     x[0] = tgt[t];
     x[1] = tgt[NT + t];
     x[2] = tgt[2 * NT + t];
+  }
+  __device__ void nrm(int i, const double*, double* n) const {
+    read_nrm(tn, NT, pair_tgt[apairs[ST[i]]], n);
   }
 };
 
@@ -438,6 +469,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
     const double* rv = dv.rv + dv.roff[m];
     const double* rw = dv.rw + dv.roff[m];
     const double tol0 = (dv.pgroup ? dv.grp[dv.pgroup[j]].eps_ad : eps) * dv.dj[j] / normV;
+    // per surface of a batch, the mixed form applies only where eps >= kMixedMinEps
+    const double mixj = (dv.pgroup && dv.grp[dv.pgroup[j]].eps < kMixedMinEps) ? 0.0 : mix;
     const double Rj = dv.rad[j];
     const int32_t* apairs = dv.ad_pair + a0;
     __syncthreads();
@@ -465,7 +498,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
     }
     __syncthreads();
     if (leaf_order > 0) {
-      TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, apairs};
+      TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, dv.tnrm};
       block_moments<D>(cf, ru, rv, rw, Q, segs, 1, ta, A,
                        [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, 4 * n, kps, ws,
                        dv.cen + 3 * j);
@@ -523,10 +556,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
       }
       __syncthreads();
       // children moments of every target in S
-      TgtAdaptive ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, ST};
+      TgtAdaptive ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, ST, dv.tnrm};
       block_moments<D, true>(cf, ru, rv, rw, Q, segs, 4, ta, S,
                              [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, 4 * n, kps,
-                             ws, dv.cen + 3 * j, Rj, tmpE, mix);
+                             ws, dv.cen + 3 * j, Rj, tmpE, mixj);
       __syncthreads();
       my_tests += S;
       my_nodes += (long long)S * 4 * Q;

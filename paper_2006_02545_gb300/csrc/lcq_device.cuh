@@ -268,7 +268,12 @@ __device__ __forceinline__ void kw_delta_geometry(double pu, double pv, double d
 __device__ __forceinline__ cplx kernel_eval(const KernelParams& kp, double x0, double x1, double x2,
                                             double X0, double X1, double X2, double N0, double N1,
                                             double N2, double Jw, double R = 0.0,
-                                            double* env = nullptr) {
+                                            double* env = nullptr, const double* nx = nullptr) {
+  if (kp.kind == 3) {  // S': the double-layer form with the source normal replaced by -n_x J
+    N0 = -nx[0] * Jw;
+    N1 = -nx[1] * Jw;
+    N2 = -nx[2] * Jw;
+  }
   const double d0 = x0 - X0, d1 = x1 - X1, d2 = x2 - X2;
   const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
   if (r2 == 0.0) {
@@ -289,7 +294,7 @@ __device__ __forceinline__ cplx kernel_eval(const KernelParams& kp, double x0, d
     *env = ex * Jw * (kp.eb + kp.ea * fa * R * rinv * rinv);
   }
   cplx out = {0.0, 0.0};
-  if (kp.kind != 1) {  // S part
+  if (kp.kind == 0 || kp.kind == 2) {  // S part
     const cplx s = {G.re * Jw, G.im * Jw};
     if (kp.kind == 0) return s;
     out = cmul({kp.br, kp.bi}, s);
@@ -300,7 +305,7 @@ __device__ __forceinline__ cplx kernel_eval(const KernelParams& kp, double x0, d
   cplx dd = cmul(G, f);
   dd.re *= ndx;
   dd.im *= ndx;
-  if (kp.kind == 1) return dd;
+  if (kp.kind != 2) return dd;
   const cplx ad = cmul({kp.ar, kp.ai}, dd);
   out.re += ad.re;
   out.im += ad.im;

@@ -28,9 +28,13 @@ enum : int {
   kStBadGroup = 16,
 };
 
+// The mixed form evaluates kernel values in FP32 only for tolerances eps >= kMixedMinEps:
+// FP32's unit roundoff (6e-8) cannot hold a tighter result, so below it the form is FP64.
+constexpr double kMixedMinEps = 1e-7;
+
 // Kernel parameters (Sec. 3): K = alpha D + beta S for CFIE.
 struct KernelParams {
-  int kind;          // 0 S, 1 D, 2 CFIE
+  int kind;          // 0 S, 1 D, 2 CFIE, 3 S' (target normal n_x)
   double kr, ki;     // k = kr + i ki
   double ar, ai;     // alpha
   double br, bi;     // beta
@@ -43,7 +47,8 @@ inline KernelParams make_kernel_params(int kind, double kr, double ki, double ar
   if (kind == 0) {
     kp.ar = kp.ai = kp.br = kp.bi = 0.0;
     kp.eb = 1.0;
-  } else if (kind == 1) {
+  } else if (kind == 1 || kind == 3) {
+    kp.ar = kp.ai = kp.br = kp.bi = 0.0;
     kp.ea = 1.0;
   } else {
     kp.eb = __builtin_sqrt(br * br + bi * bi);
@@ -112,6 +117,9 @@ struct lcq_ctx {
   size_t work_bytes = 0;
   // stage events: [0,1] near lists, [2..7] corrections
   cudaEvent_t ev[8] = {};
+  // side stream: the self weights run beside far order, moments and adaptive integration
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, ev_self[2] = {};
   long long launches_near = 0, launches_corr = 0;
 };
 
@@ -165,6 +173,9 @@ struct lcq_near {
   std::vector<int64_t> gpatch_off;  // [n_groups+1] patch range of each surface
   int32_t* pgroup = nullptr;        // [P] surface of each patch
   int32_t* tgroup = nullptr;        // [NT] surface of each target
+  // S': caller's normals of off-surface targets and the unit target normals in use
+  double* unrm = nullptr;           // [3][NT]
+  double* tnrm = nullptr;           // [3][NT]
 };
 
 struct lcq_corr {

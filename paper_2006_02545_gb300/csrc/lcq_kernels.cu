@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
     const double* rw = dv.rw + dv.roff[m];
     if (mode == 0) {
       const int64_t p0 = dv.pair_ptr[j], np = dv.pair_ptr[j + 1] - p0;
-      TgtIdx ta{dv.tgt, dv.NT, dv.pair_tgt + p0};
+      TgtIdx ta{dv.tgt, dv.NT, dv.pair_tgt + p0, dv.tnrm};
       const int64_t ld = dv.ldI;
       cplx* base = out_pairs + p0 * ld;
       block_moments<D>(cf, ru, rv, rw, m * m, segs, 1, ta, (int)np,
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
     } else {
       const int64_t a0 = dv.an_ptr[j], na = dv.an_ptr[j + 1] - a0;
       const int32_t* pl = dv.an_pair + a0;
-      TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl};
+      TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl, dv.tnrm};
       const int64_t ld = dv.ldI;
       block_moments<D>(cf, ru, rv, rw, m * m, segs, 1, ta, (int)na,
                        [=] __device__(int i) { return out_pairs + (int64_t)pl[i] * ld; }, C::n, kps,
@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
   __shared__ cplx red[4][n];
   __shared__ KernelParams kps;
   __shared__ int ord;
+  __shared__ double nP[3];  // unit chart normal at the target node (S')
   long long my_nodes = 0;
   for (int64_t s = blockIdx.x; s < dv.n_self; s += gridDim.x) {
     const int t = dv.self_tgt[s];
@@ -437,6 +438,14 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
       P[1] = pv;
       double X[3], Xu[3], Xv[3];
       kw_geometry<D>(pu, pv, cf, X, Xu, Xv, nullptr, 1);
+      {
+        double Np[3];
+        cross3(Xu, Xv, Np);
+        const double ln = sqrt(Np[0] * Np[0] + Np[1] * Np[1] + Np[2] * Np[2]);
+        nP[0] = Np[0] / ln;
+        nP[1] = Np[1] / ln;
+        nP[2] = Np[2] / ln;
+      }
       const double a = Xu[0] * Xu[0] + Xu[1] * Xu[1] + Xu[2] * Xu[2];
       const double bb = Xu[0] * Xv[0] + Xu[1] * Xv[1] + Xu[2] * Xv[2];
       const double c = Xv[0] * Xv[0] + Xv[1] * Xv[1] + Xv[2] * Xv[2];
@@ -512,7 +521,7 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
       cross3(Xu, Xv, Nn);
       const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
       const cplx gk = kernel_eval(kps, 0.0, 0.0, 0.0, dX[0], dX[1], dX[2], Nn[0] * w, Nn[1] * w,
-                                  Nn[2] * w, J * w);
+                                  Nn[2] * w, J * w, 0.0, nullptr, nP);
       kw_accumulate<D>(u, v, gk, acc);
     }
     my_nodes += tot;
@@ -535,6 +544,37 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
   }
   if (threadIdx.x == 0)
     atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 2), (unsigned long long)my_nodes);
+}
+
+// ============================================================================ target normals
+// Unit normals for S': the chart normal X_u x X_v / |.| at the node of an on-surface target
+// on a degree-D patch; with do_off, the normalized user normal of an off-surface target.
+template <int D>
+__global__ void k_tgt_normals(Dev dv, const int32_t* __restrict__ deg, const double* __restrict__ user,
+                              bool do_off, double* __restrict__ out) {
+  constexpr int n = (D + 1) * (D + 2) / 2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dv.NT;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int tp = dv.tpatch[t];
+    double v[3];
+    if (tp >= 0) {
+      if (deg[tp] != D) continue;
+      double cf[3 * n], X[3], Xu[3], Xv[3];
+      const int64_t off = dv.node_off[tp];
+      for (int e = 0; e < 3 * n; ++e) cf[e] = dv.coef[off * 3 + e];
+      const int i = dv.tlnode[t];
+      kw_geometry<D>(dv.nodes_uv[D][i], dv.nodes_uv[D][n + i], cf, X, Xu, Xv, nullptr, 1);
+      cross3(Xu, Xv, v);
+    } else {
+      if (!do_off) continue;
+      v[0] = user[t];
+      v[1] = user[dv.NT + t];
+      v[2] = user[2 * dv.NT + t];
+    }
+    const double l = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(l > 0.0) || !isfinite(l)) atomicOr(dv.status, kStNonFinite);
+    for (int c = 0; c < 3; ++c) out[c * dv.NT + t] = v[c] / l;
+  }
 }
 
 // ============================================================================ V contraction
@@ -649,12 +689,14 @@ __global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__
                                                       const int32_t* __restrict__ tgroup,
                                                       const GroupParams* __restrict__ grp,
                                                       const int64_t* __restrict__ gsrc,
+                                                      const double* __restrict__ tnrm,
                                                       cplx* __restrict__ out) {
   __shared__ double s[9][kThreads];
   __shared__ unsigned long long blo, bhi;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double x0 = 0, x1 = 0, x2 = 0;
   int64_t skip0 = -1, skip1 = -1, lo = 0, hi = 0;
+  double nx[3] = {0.0, 0.0, 0.0};
   KernelParams kt = kp;
   if (threadIdx.x == 0) {
     blo = ~0ull;
@@ -665,6 +707,11 @@ __global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__
     x0 = tgt[t];
     x1 = tgt[NT + t];
     x2 = tgt[2 * NT + t];
+    if (tnrm) {
+      nx[0] = tnrm[t];
+      nx[1] = tnrm[NT + t];
+      nx[2] = tnrm[2 * NT + t];
+    }
     const int tp = tpatch[t];
     if (tp >= 0) {
       skip0 = src_off[tp];
@@ -694,7 +741,7 @@ __global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__
         const int64_t qq = s0 + k;
         if (qq < lo || qq >= hi || (qq >= skip0 && qq < skip1)) continue;
         const cplx g = kernel_eval(kt, x0, x1, x2, s[0][k], s[1][k], s[2][k], s[3][k], s[4][k],
-                                   s[5][k], s[6][k]);
+                                   s[5][k], s[6][k], 0.0, nullptr, nx);
         re = fma(g.re, s[7][k], re);
         re = fma(-g.im, s[8][k], re);
         im = fma(g.re, s[8][k], im);
@@ -833,6 +880,17 @@ struct SelfL {
 };
 
 template <int D>
+struct TgtNormalsL {
+  static void run(const LaunchCommon& lc, const Dev& dv, const int32_t* deg, const double* user,
+                  bool do_off, double* out) {
+    const int64_t b = (dv.NT + 127) / 128;
+    const int g = (int)(b < lc.num_sms * 8 ? (b > 0 ? b : 1) : lc.num_sms * 8);
+    ++*lc.launches;
+    k_tgt_normals<D><<<g, 128, 0, lc.stream>>>(dv, deg, user, do_off, out);
+  }
+};
+
+template <int D>
 struct V2cL {
   static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                   const double* Vt, const void* In, const void* Is, const void* InS,
@@ -921,6 +979,10 @@ bool launch_self(int d, const LaunchCommon& lc, const Dev& dv, const int32_t* de
                  const KernelParams& kp, int order, void* out) {
   return dispatch<SelfL>(d, lc, dv, deg, kp, order, out);
 }
+bool launch_tgt_normals(int d, const LaunchCommon& lc, const Dev& dv, const int32_t* deg,
+                        const double* user, bool do_off, double* out) {
+  return dispatch<TgtNormalsL>(d, lc, dv, deg, user, do_off, out);
+}
 bool launch_v2c(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                 const double* Vt, const void* In, const void* Is, const void* InS, const void* IsS,
                 double* val) {
@@ -934,12 +996,12 @@ bool launch_far_src(int d, const LaunchCommon& lc, const int* plist, int count, 
 void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const double* src,
                     int64_t n_over, const KernelParams& kp, const int32_t* tpatch,
                     const int64_t* src_off, const int32_t* tgroup, const GroupParams* grp,
-                    const int64_t* gsrc, void* out) {
+                    const int64_t* gsrc, const double* tnrm, void* out) {
   const int64_t g = (NT + kThreads - 1) / kThreads;
   if (g <= 0) return;
   ++*lc.launches;
   k_far_sum<<<(unsigned)g, kThreads, 0, lc.stream>>>(tgt, NT, src, n_over, kp, tpatch, src_off,
-                                                     tgroup, grp, gsrc, (cplx*)out);
+                                                     tgroup, grp, gsrc, tnrm, (cplx*)out);
 }
 void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int32_t* col,
                       const double* val, const void* sigma, const int64_t* tnode, int64_t NT,

@@ -44,6 +44,8 @@ struct Dev {
   // surface whose physics come from the launch arguments)
   const int32_t* pgroup;
   const GroupParams* grp;
+  // unit target normals, SoA [3][NT] (S' only, else null)
+  const double* tnrm;
   // tables
   const int* roff;
   const double* ru;
@@ -143,12 +145,17 @@ bool launch_far_src(int d, const LaunchCommon& lc, const int* plist, int count, 
 void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const double* src,
                     int64_t n_over, const KernelParams& kp, const int32_t* tpatch,
                     const int64_t* src_off, const int32_t* tgroup, const GroupParams* grp,
-                    const int64_t* gsrc, void* out);
+                    const int64_t* gsrc, const double* tnrm, void* out);
 void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int32_t* col,
                       const double* val, const void* sigma, const int64_t* tnode, int64_t NT,
                       double jump, void* out);
 size_t adaptive_smem_bytes(int d);
 int adaptive_blocks_per_sm(int d);
+
+// Unit target normals for S' (SoA [3][NT]): the chart normal at the node of an on-surface
+// target of degree d; with do_off also the normalized user[t] of off-surface targets.
+bool launch_tgt_normals(int d, const LaunchCommon& lc, const Dev& dv, const int32_t* deg,
+                        const double* user, bool do_off, double* out);
 
 // Adjoint (lcq_adjoint.cu).
 cudaError_t upload_constants_adjoint(cudaStream_t st);

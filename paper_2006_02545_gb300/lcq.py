@@ -25,7 +25,7 @@ LCQ_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "non-finite coordinates", 3: "degenerate patch",
           4: "max_depth reached", 5: "capacity exceeded", 6: "CUDA error", 7: "out of memory",
           8: "tables", 9: "timeout"}
-KERNELS = {"S": 0, "D": 1, "CFIE": 2}
+KERNELS = {"S": 0, "D": 1, "CFIE": 2, "Sp": 3}
 
 
 class LCQError(RuntimeError):
@@ -74,6 +74,8 @@ _sig = {
     "lcq_apply_corrected_S": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
     "lcq_apply_corrected_D": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
     "lcq_apply_corrected_CFIE": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
+    "lcq_apply_corrected_Sp": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
+    "lcq_near_set_target_normals": (C.c_int, [_vp, _vp]),
     "lcq_corr_destroy": (None, [_vp]),
     "lcq_apply_adjoint": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
     "lcq_shape_gradient": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -206,6 +208,12 @@ class NearLists:
         self.ctx.check(_lib.lcq_near_export(self.h, _ptr(pp), _ptr(tg), _ptr(ad), _ptr(cen),
                                             _ptr(rad)), "lcq_near_export")
         return pp, tg[:self.n_pairs], ad[:self.n_pairs].astype(bool), cen, rad
+
+    def set_target_normals(self, normals):
+        """Normals of the off-surface targets for S' (device float64 [3][NT])."""
+        self._normals = normals
+        self.ctx.check(_lib.lcq_near_set_target_normals(self.h, _ptr(normals)),
+                       "lcq_near_set_target_normals")
 
     def close(self):
         if getattr(self, "h", None):
@@ -357,6 +365,11 @@ def shape_gradient(ctx, surf, near, corr, sigma, g):
     ctx.check(_lib.lcq_shape_gradient(ctx.h, C.byref(surf.s), near.h, corr.h, _ptr(sigma), _ptr(g),
                                       _ptr(out)), "lcq_shape_gradient")
     return out
+
+
+def apply_corrected_Sp(ctx, surf, near, corr, sigma, n_targets, jump=0.0):
+    return _apply(_lib.lcq_apply_corrected_Sp, ctx, surf, near, corr, sigma, jump,
+                  _out_like(ctx, n_targets))
 
 
 def adaptive_corrections_noalloc(deg, y_dev, tgt_dev, kernel, k, q, eps, out, alpha=1.0, beta=0.0,

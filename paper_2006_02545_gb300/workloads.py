@@ -198,6 +198,98 @@ def torus(n_theta: int, n_phi: int, deg: int, R: float = 2.0, amp: float = 0.2) 
                    {"kind": "torus", "n_theta": n_theta, "n_phi": n_phi, "R": R, "amp": amp})
 
 
+# Twisted torus of the paper's numerical examples (Sec. 6): nonzero delta_{i,j} of
+# X(u, v) = sum_{i,j} delta_{i,j} (cos v cos t, sin v cos t, sin t), t = (1 - i) u + j v.
+STELLARATOR_DELTA = {(-1, -1): 0.17, (-1, 0): 0.11, (0, 0): 1.0, (1, 0): 4.5, (2, 0): -0.25,
+                     (0, 1): 0.07, (2, 1): -0.45}
+
+
+def stellarator_point(u, v):
+    u, v = np.asarray(u, dtype=np.float64), np.asarray(v, dtype=np.float64)
+    out = np.zeros((3,) + u.shape)
+    for (i, j), dl in STELLARATOR_DELTA.items():
+        t = (1 - i) * u + j * v
+        out += dl * np.stack([np.cos(v) * np.cos(t), np.sin(v) * np.cos(t), np.sin(t)])
+    return out
+
+
+def stellarator(n_u: int, n_v: int, deg) -> Surface:
+    """The paper's twisted torus on an n_u x n_v grid of (u, v) in [0, 2 pi]^2 (u poloidal,
+    v toroidal), two triangles per cell with the right angle at the chart origin (so that
+    a cell of equal physical sides gives aspect ratio 1); deg is one degree or one per
+    patch.  Triangles are oriented so that X_u x X_v points away from the tube's centre circle 4.5 (cos v,
+    sin v, 0) (outward)."""
+    du, dv = 2 * math.pi / n_u, 2 * math.pi / n_v
+    charts = []
+    for a in range(n_u):
+        for b in range(n_v):
+            p0 = np.array([a * du, b * dv])
+            for tri in (((0, 0), (1, 0), (0, 1)), ((1, 1), (0, 1), (1, 0))):
+                P = [p0 + np.array(c) * [du, dv] for c in tri]
+                # orientation from the chart's normal at the centroid
+                cu, cv = (P[0] + P[1] + P[2]) / 3.0
+                h = 1e-6
+                e1, e2 = P[1] - P[0], P[2] - P[0]
+                Xa = stellarator_point(np.array([cu + h * e1[0]]), np.array([cv + h * e1[1]]))[:, 0]
+                Xb = stellarator_point(np.array([cu + h * e2[0]]), np.array([cv + h * e2[1]]))[:, 0]
+                X0 = stellarator_point(np.array([cu]), np.array([cv]))[:, 0]
+                nrm = np.cross(Xa - X0, Xb - X0)
+                ctr = 4.5 * np.array([math.cos(cv), math.sin(cv), 0.0])
+                if nrm @ (X0 - ctr) < 0:
+                    P = [P[0], P[2], P[1]]
+
+                def chart(uu, vv, P0=P[0], P1=P[1], P2=P[2]):
+                    q = P0[:, None] + uu[None, :] * (P1 - P0)[:, None] + vv[None, :] * (P2 - P0)[:, None]
+                    return stellarator_point(q[0], q[1])
+                charts.append(chart)
+    degs = np.full(len(charts), deg, np.int32) if np.isscalar(deg) else np.asarray(deg, np.int32)
+    off, xyz = _sample(charts, degs)
+    return Surface(f"stellarator_{n_u}x{n_v}_d{int(degs[0])}", degs, off, xyz,
+                   {"kind": "stellarator", "n_u": n_u, "n_v": n_v})
+
+
+def aspect_ratios(surf: Surface) -> np.ndarray:
+    """Per-patch aspect ratio of Sec. 6: a_j = sqrt(int (s1/s2)^2 da / int da), s1 >= s2 the
+    singular values of the chart's Jacobian DX, on the patch's node rule."""
+    out = np.empty(surf.n_patches)
+    cache = {}
+    for j in range(surf.n_patches):
+        d = int(surf.deg[j])
+        if d not in cache:
+            u, v = ref_nodes(d)
+            cache[d] = (u, v, _vander_derivs(d, u, v))
+        u, v, (Vm, Du, Dv) = cache[d]
+        y = surf.xyz[:, surf.node_off[j]:surf.node_off[j + 1]]
+        c = np.linalg.solve(Vm, y.T)          # monomial coefficients of the interpolant
+        Xu, Xv = (Du @ c).T, (Dv @ c).T       # [3, n]
+        G11, G12, G22 = (Xu * Xu).sum(0), (Xu * Xv).sum(0), (Xv * Xv).sum(0)
+        tr, det = G11 + G22, G11 * G22 - G12 * G12
+        disc = np.sqrt(np.maximum(tr * tr / 4 - det, 0.0))
+        s1, s2 = np.sqrt(tr / 2 + disc), np.sqrt(np.maximum(tr / 2 - disc, 0.0))
+        J = s1 * s2
+        w = _node_weights(d)
+        out[j] = math.sqrt(((s1 / s2) ** 2 * J * w).sum() / (J * w).sum())
+    return out
+
+
+def _vander_derivs(d, u, v):
+    """Monomial Vandermonde u^a v^b (a + b <= d) at the nodes and its u, v derivatives."""
+    ex = [(a, b) for a in range(d + 1) for b in range(d + 1 - a)]
+    Vm = np.stack([u ** a * v ** b for a, b in ex], axis=1)
+    Du = np.stack([a * u ** max(a - 1, 0) * v ** b if a else 0 * u for a, b in ex], axis=1)
+    Dv = np.stack([b * u ** a * v ** max(b - 1, 0) if b else 0 * u for a, b in ex], axis=1)
+    return Vm, Du, Dv
+
+
+def _node_weights(d):
+    """Interpolatory weights of the node set (monomial moments over T0)."""
+    u, v = ref_nodes(d)
+    ex = [(a, b) for a in range(d + 1) for b in range(d + 1 - a)]
+    Vm = np.stack([u ** a * v ** b for a, b in ex], axis=0)
+    mom = np.array([math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2) for a, b in ex])
+    return np.linalg.solve(Vm, mom)
+
+
 def torus_with_patches(n_patches: int, deg: int) -> Surface:
     """Torus with n_phi = 2 n_theta cells and the achievable count nearest n_patches."""
     nt = max(2, int(round(math.sqrt(n_patches / 4.0))))
@@ -350,3 +442,11 @@ def ellipsoid_adjoint_s_k5(s: int = 10):
     surf = ellipsoid(s, 5, axes=(1.0, 1.5, 2.5))
     x = exterior_targets(surf, 1000, 0)
     return surf, x
+
+
+def stellarator_s_k1(deg: int = 3) -> Workload:
+    """Single layer, k=1, on the paper's twisted torus with 2400 patches (20 x 60 cells,
+    average aspect ratio 1.61 as in the paper's Table 2 first column); eps=5e-7."""
+    surf = stellarator(20, 60, deg)
+    x, t = onsurface_targets(surf)
+    return Workload(f"stellarator2400_d{deg}_S_k1", surf, x, t, "S", 1.0, 5e-7, -1.0)

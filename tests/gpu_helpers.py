@@ -7,7 +7,7 @@ from paper_2006_02545_gb300 import workloads as W
 
 
 def run_gpu(ctx, surf, x, tn, kind, k, eps, eta=-1.0, alpha=1.0, beta=0.0, dirs_seed=3, sigma_seed=0,
-            precision="fp64", **kw):
+            precision="fp64", tgt_normal=None, **kw):
     import torch
     from paper_2006_02545_gb300 import lcq
     dev = ctx.torch_device
@@ -15,12 +15,15 @@ def run_gpu(ctx, surf, x, tn, kind, k, eps, eta=-1.0, alpha=1.0, beta=0.0, dirs_
     prm = lcq.params(eps, eta=eta, test_dirs=W.test_directions(dirs_seed), **kw)
     near = lcq.build_near_lists(ctx, ds, torch.from_numpy(np.ascontiguousarray(x)).to(dev),
                                 torch.from_numpy(tn).to(dev), prm)
+    if tgt_normal is not None:
+        near.set_target_normals(torch.from_numpy(np.ascontiguousarray(tgt_normal)).to(dev))
     corr = lcq.gen_corrections(ctx, ds, near, kind, k, prm, alpha, beta, precision=precision)
     st = ctx.sync(120000)
     rp, col, val = corr.export(x.shape[1])
     q, qn, leaves = corr.stats(surf.n_patches)
     sig = W.density(surf.n_points, sigma_seed)
-    fn = {"S": lcq.apply_corrected_S, "D": lcq.apply_corrected_D, "CFIE": lcq.apply_corrected_CFIE}
+    fn = {"S": lcq.apply_corrected_S, "D": lcq.apply_corrected_D, "CFIE": lcq.apply_corrected_CFIE,
+          "Sp": lcq.apply_corrected_Sp}
     u = fn[kind](ctx, ds, near, corr, torch.from_numpy(sig).to(dev), x.shape[1]).cpu().numpy()
     st2 = ctx.sync(120000)
     pp, tgt, ad, cen, rad = near.export(surf.n_patches)
@@ -31,11 +34,12 @@ def run_gpu(ctx, surf, x, tn, kind, k, eps, eta=-1.0, alpha=1.0, beta=0.0, dirs_
 
 
 def run_oracle(surf, x, tn, kind, k, eps, eta=-1.0, alpha=1.0, beta=0.0, dirs_seed=3, sigma=None,
-               only_patches=None, apply=True, **kw):
+               only_patches=None, apply=True, tgt_normal=None, **kw):
     p = C.Params(eps=eps, eta=eta, test_dirs=W.test_directions(dirs_seed), **kw)
     oc = C.gen_corrections(surf.deg, surf.node_off, surf.xyz, x, tn, kind, k, alpha, beta, params=p,
-                           only_patches=only_patches)
-    u = C.apply_corrected(oc, surf.node_off, sigma, x, kind, k, alpha, beta) if apply else None
+                           only_patches=only_patches, tgt_normal=tgt_normal)
+    u = (C.apply_corrected(oc, surf.node_off, sigma, x, kind, k, alpha, beta, tgt_node=tn,
+                           tgt_normal=tgt_normal) if apply else None)
     return oc, u
 
 
