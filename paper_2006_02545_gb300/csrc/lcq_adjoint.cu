@@ -372,7 +372,8 @@ struct AdaptiveGradL {
                   const GradArgs& ga) {
     using C = Cfg<D>;
     const size_t sm = sizeof(double) * (C::n * 3 + 64 / 2 + 4 * 32 + C::WS) +
-                      sizeof(SegMap) * 4 + 1024 + 64 * sizeof(int);
+                      sizeof(SegMap) * 4 + 1024 + 64 * sizeof(int) +
+                      (mix > 0.0 ? C::WS_F32 * sizeof(double) : 0);
     cudaFuncSetAttribute(k_adaptive<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     AdaptiveWS w{stride, A_max, levels};
     cudaMemsetAsync(sched, 0, sizeof(int), lc.stream);

@@ -76,6 +76,9 @@ struct Cfg {
   static constexpr int TT = 16;
   // doubles of shared workspace used by block_moments
   static constexpr int WS = CH * BS + 7 * CH + 3 * TT * CH + 6 * TT;
+  // doubles the mixed form adds after WS: FP32 copies of the basis rows, weighted
+  // normals and area elements of a chunk
+  static constexpr int WS_F32 = (CH * BS + 4 * CH + 1) / 2;
 };
 
 struct SegMap {
@@ -88,16 +91,17 @@ struct SegMap {
 // TA: target accessor (pos(i, x[3])); out row of target i: out + orow(i) * ostride.
 // Positions are relative to the patch centroid cen (the coefficients cf describe
 // X - cen).  With ENV, eout[i * nseg + seg] also receives the summed rounding envelope.
-// mix > 0 (mixed precision): a node farther than mix * 2R sqrt(det_seg) -- mix times the
-// size of its subtriangle -- from the target is evaluated by kernel_eval_f32, and its
-// envelope is scaled by kF32Floor / kRoundingFloor.
+// mixed (the mixed form; sm then has Cfg<D>::WS_F32 more doubles): every (target, node)
+// pair is evaluated by kernel_eval_f32f from the FP64 difference x - X, its envelope
+// scaled by kF32Floor / kRoundingFloor, and contracted with FP32 basis values in FP32 per
+// chunk (accumulated into the FP64 moments).
 template <int D, bool ENV = false, class TA, class OR>
 __device__ void block_moments(const double* cf, const double* __restrict__ ru,
                               const double* __restrict__ rv, const double* __restrict__ rw, int Q,
                               const SegMap* segs, int nseg, const TA& ta, int T, OR orow,
                               int64_t ostride, const KernelParams& kp, double* sm,
                               const double* cen, double R = 0.0, double* eout = nullptr,
-                              double mix = 0.0) {
+                              bool mixed = false) {
   using C = Cfg<D>;
   double* B = sm;
   double* Xs = B + C::CH * C::BS;
@@ -107,6 +111,12 @@ __device__ void block_moments(const double* cf, const double* __restrict__ ru,
   double* Ev = reinterpret_cast<double*>(G + C::TT * C::CH);
   double* tx = Ev + C::TT * C::CH;
   double* tn = tx + 3 * C::TT;  // target normals (S')
+  float* Bf = reinterpret_cast<float*>(sm + C::WS);  // mixed form only
+  float* Nf = Bf + C::CH * C::BS;
+  float* Jf = Nf + 3 * C::CH;
+  float2* Gf = reinterpret_cast<float2*>(G);
+  const KernelParamsF kf = to_f32(kp);
+  const float fR = (float)R;
   const int total = nseg * Q;
   for (int c0 = 0; c0 < total; c0 += C::CH) {
     const int nch = min(C::CH, total - c0);
@@ -129,6 +139,12 @@ __device__ void block_moments(const double* cf, const double* __restrict__ ru,
         Ns[c * C::CH + ql] = Nn[c] * w;
       }
       Js[ql] = J * w;
+      if (mixed) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Nf[c * C::CH + ql] = (float)(Nn[c] * w);
+        Jf[ql] = (float)(J * w);
+        for (int nm = 0; nm < C::n; ++nm) Bf[ql * C::BS + nm] = (float)B[ql * C::BS + nm];
+      }
     }
     __syncthreads();
     for (int t0 = 0; t0 < T; t0 += C::TT) {
@@ -144,30 +160,29 @@ __device__ void block_moments(const double* cf, const double* __restrict__ ru,
       __syncthreads();
       for (int e = threadIdx.x; e < nt * C::CH; e += blockDim.x) {
         const int i = e / C::CH, ql = e - i * C::CH;
-        cplx g = {0.0, 0.0};
-        double ev = 0.0;
-        if (ql < nch) {
-          bool f32 = false;
-          double d0 = 0, d1 = 0, d2 = 0, r2 = 0;
-          if (mix > 0.0) {
-            const int sg = (c0 + ql) / Q;
-            const double h = mix * 2.0 * R * sqrt(segs[sg].det);
-            d0 = tx[3 * i] - Xs[ql];
-            d1 = tx[3 * i + 1] - Xs[C::CH + ql];
-            d2 = tx[3 * i + 2] - Xs[2 * C::CH + ql];
-            r2 = d0 * d0 + d1 * d1 + d2 * d2;
-            f32 = r2 >= h * h;
+        if (mixed) {
+          float2 g = make_float2(0.0f, 0.0f);
+          float ev = 0.0f;
+          if (ql < nch) {
+            const double d0 = tx[3 * i] - Xs[ql], d1 = tx[3 * i + 1] - Xs[C::CH + ql],
+                         d2 = tx[3 * i + 2] - Xs[2 * C::CH + ql];
+            const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            if (r2 > 0.0)
+              g = kernel_eval_f32f(kp, kf, d0, d1, d2, r2, Nf[ql], Nf[C::CH + ql],
+                                   Nf[2 * C::CH + ql], Jf[ql], fR, ENV ? &ev : nullptr);
           }
-          if (f32)
-            g = kernel_eval_f32(kp, d0, d1, d2, r2, Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql],
-                                Js[ql], R, ENV ? &ev : nullptr, kF32Floor / kRoundingFloor);
-          else
+          Gf[i * C::CH + ql] = g;
+          if (ENV) Ev[i * C::CH + ql] = (double)ev * (kF32Floor / kRoundingFloor);
+        } else {
+          cplx g = {0.0, 0.0};
+          double ev = 0.0;
+          if (ql < nch)
             g = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql], Xs[C::CH + ql],
                             Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql],
                             Js[ql], R, ENV ? &ev : nullptr, tn + 3 * i);
+          G[i * C::CH + ql] = g;
+          if (ENV) Ev[i * C::CH + ql] = ev;
         }
-        G[i * C::CH + ql] = g;
-        if (ENV) Ev[i * C::CH + ql] = ev;
       }
       __syncthreads();
       const int nout = nt * nseg * C::NP;
@@ -178,12 +193,25 @@ __device__ void block_moments(const double* cf, const double* __restrict__ ru,
         if (nm >= C::n) continue;
         const int qa = max(sg * Q - c0, 0), qb = min((sg + 1) * Q - c0, nch);
         double are = 0.0, aim = 0.0;
-        const cplx* Gi = G + i * C::CH;
-        for (int ql = qa; ql < qb; ++ql) {
-          const cplx g = Gi[ql];
-          const double bv = B[ql * C::BS + nm];
-          are = fma(g.re, bv, are);
-          aim = fma(g.im, bv, aim);
+        if (mixed) {
+          float fre = 0.0f, fim = 0.0f;
+          const float2* Gi = Gf + i * C::CH;
+          for (int ql = qa; ql < qb; ++ql) {
+            const float2 g = Gi[ql];
+            const float bv = Bf[ql * C::BS + nm];
+            fre = fmaf(g.x, bv, fre);
+            fim = fmaf(g.y, bv, fim);
+          }
+          are = fre;
+          aim = fim;
+        } else {
+          const cplx* Gi = G + i * C::CH;
+          for (int ql = qa; ql < qb; ++ql) {
+            const cplx g = Gi[ql];
+            const double bv = B[ql * C::BS + nm];
+            are = fma(g.re, bv, are);
+            aim = fma(g.im, bv, aim);
+          }
         }
         cplx* dst = reinterpret_cast<cplx*>(orow(t0 + i)) + (int64_t)sg * C::n + nm;
         (void)ostride;
@@ -470,7 +498,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
     const double* rw = dv.rw + dv.roff[m];
     const double tol0 = (dv.pgroup ? dv.grp[dv.pgroup[j]].eps_ad : eps) * dv.dj[j] / normV;
     // per surface of a batch, the mixed form applies only where eps >= kMixedMinEps
-    const double mixj = (dv.pgroup && dv.grp[dv.pgroup[j]].eps < kMixedMinEps) ? 0.0 : mix;
+    const bool mixj = mix > 0.0 && !(dv.pgroup && dv.grp[dv.pgroup[j]].eps < kMixedMinEps);
     const double Rj = dv.rad[j];
     const int32_t* apairs = dv.ad_pair + a0;
     __syncthreads();

@@ -317,10 +317,22 @@ __device__ __forceinline__ cplx kernel_eval(const KernelParams& kp, double x0, d
 // FP32 distance by one Newton step and reduced modulo 2 pi); everything else -- 1/r,
 // sin/cos of the reduced phase, the S and D factors, the CFIE combination -- is FP32.
 // The rounding envelope is returned multiplied by env_scale (the FP32 noise is larger).
-__device__ __forceinline__ cplx kernel_eval_f32(const KernelParams& kp, double d0, double d1,
-                                                double d2, double r2, double N0, double N1,
-                                                double N2, double Jw, double R, double* env,
-                                                double env_scale) {
+// Kernel parameters converted to FP32 once per patch (the mixed form's pair evaluations).
+struct KernelParamsF {
+  float kr, ki, ar, ai, br, bi, eb, ea;
+};
+__device__ __forceinline__ KernelParamsF to_f32(const KernelParams& kp) {
+  return {(float)kp.kr, (float)kp.ki, (float)kp.ar, (float)kp.ai,
+          (float)kp.br, (float)kp.bi, (float)kp.eb, (float)kp.ea};
+}
+
+// Mixed form: K~ w in FP32 from the FP64 difference d = x - X and r2 = |d|^2; r and the
+// phase k r (reduced mod 2 pi) are formed in FP64 first, everything after in FP32.
+// N, J: FP32 copies of the weighted normal and area element.  r2 > 0.
+__device__ __forceinline__ float2 kernel_eval_f32f(const KernelParams& kp, const KernelParamsF& kf,
+                                                   double d0, double d1, double d2, double r2,
+                                                   float N0, float N1, float N2, float Jw,
+                                                   float R, float* env) {
   const float fr2 = (float)r2;
   const float frinv = rsqrtf(fr2);
   const float fr = fr2 * frinv;
@@ -330,29 +342,25 @@ __device__ __forceinline__ cplx kernel_eval_f32(const KernelParams& kp, double d
   float sn, cs;
   sincosf((float)th, &sn, &cs);
   float ex = 0.0795774715459f * frinv;
-  if (kp.ki != 0.0) ex *= expf(-(float)kp.ki * fr);
+  if (kf.ki != 0.0f) ex *= expf(-kf.ki * fr);
   const float Gr = ex * cs, Gi = ex * sn;
   float ore = 0.0f, oim = 0.0f;
-  const float fJw = (float)Jw;
   if (kp.kind != 1) {
-    const float sr = Gr * fJw, si = Gi * fJw;
+    const float sr = Gr * Jw, si = Gi * Jw;
     if (kp.kind == 0) {
       ore = sr;
       oim = si;
     } else {
-      const float br = (float)kp.br, bi = (float)kp.bi;
-      ore = br * sr - bi * si;
-      oim = br * si + bi * sr;
+      ore = kf.br * sr - kf.bi * si;
+      oim = kf.br * si + kf.bi * sr;
     }
   }
-  const float f0 = 1.0f + (float)kp.ki * fr, f1 = -(float)kp.kr * fr;
+  const float f0 = 1.0f + kf.ki * fr, f1 = -kf.kr * fr;
   if (kp.kind != 0) {
-    const float ndx = ((float)N0 * (float)d0 + (float)N1 * (float)d1 + (float)N2 * (float)d2) *
-                      frinv * frinv;
+    const float ndx = (N0 * (float)d0 + N1 * (float)d1 + N2 * (float)d2) * frinv * frinv;
     float dr = (Gr * f0 - Gi * f1) * ndx, di = (Gr * f1 + Gi * f0) * ndx;
     if (kp.kind == 2) {
-      const float ar = (float)kp.ar, ai = (float)kp.ai;
-      const float tr = ar * dr - ai * di, ti = ar * di + ai * dr;
+      const float tr = kf.ar * dr - kf.ai * di, ti = kf.ar * di + kf.ai * dr;
       dr = tr;
       di = ti;
     }
@@ -361,11 +369,11 @@ __device__ __forceinline__ cplx kernel_eval_f32(const KernelParams& kp, double d
   }
   if (env) {
     const float fa = sqrtf(f0 * f0 + f1 * f1);
-    *env = (double)(ex * fJw * ((float)kp.eb + (float)kp.ea * fa * (float)R * frinv * frinv)) *
-           env_scale;
+    *env = ex * Jw * (kf.eb + kf.ea * fa * R * frinv * frinv);
   }
-  return {(double)ore, (double)oim};
+  return make_float2(ore, oim);
 }
+
 
 // Cross product helper.
 // Derivatives of kernel_eval's K~(x, X, N) (N the unnormalized normal, no weight) with

@@ -856,7 +856,8 @@ struct AdaptiveL {
                   const void* I_smooth, void* I_near, int32_t* leaves, void* work,
                   int64_t stride, int A_max, int levels, int grid, int* status, int* sched,
                   double mix) {
-    const size_t sm = moments_smem_bytes<D>(64 / 2 + 4 * 32) + 64 * sizeof(int);
+    const size_t sm = moments_smem_bytes<D>(64 / 2 + 4 * 32) + 64 * sizeof(int) +
+                      (mix > 0.0 ? Cfg<D>::WS_F32 * sizeof(double) : 0);
     set_smem(k_adaptive<D>, sm);
     AdaptiveWS w{stride, A_max, levels};
     ++*lc.launches;

@@ -141,3 +141,45 @@ def test_autograd_matches_finite_differences():
                 worst = max(worst, abs(fd - an) / max(abs(an), 1e-3 * np.abs(gs).max()))
     assert worst <= 1e-6, worst
     ctx.close()
+
+
+def test_adjoint_of_a_batch_matches_oracle_per_surface(ctx):
+    """A^H g and the shape gradient of a two-surface batch (different k, CFIE coefficients
+    and eps, overlapping in space) equal the oracle's for each surface alone: nothing of
+    either gradient crosses surfaces."""
+    import torch
+    from paper_2006_02545_gb300 import lcq
+    dev = ctx.torch_device
+    parts = [W.ellipsoid(1, 3, axes=(1.0, 1.2, 0.9)), W.ellipsoid(1, 2, axes=(0.8, 0.7, 1.1))]
+    phys = [(2.0, 1.0, -2j, 1e-7), (3.5 + 0.2j, 0.5, -3.5j, 1e-6)]
+    s, poff = W.concat_surfaces(parts)
+    xs = [W.radial_targets(p, 20, 5 + i, 0.02, 0.6, True) for i, p in enumerate(parts)]
+    x = np.ascontiguousarray(np.concatenate(xs, axis=1))
+    tn = -np.ones(x.shape[1], np.int64)
+    tsurf = np.concatenate([np.full(xi.shape[1], i, np.int32) for i, xi in enumerate(xs)])
+    ds = lcq.DeviceSurface(s.deg, s.node_off, torch.from_numpy(s.xyz).to(dev))
+    prm = lcq.params(1e-6, test_dirs=W.test_directions(3))
+    near = lcq.build_near_lists_batched(ctx, ds, poff, torch.from_numpy(x).to(dev),
+                                        torch.from_numpy(tn).to(dev), prm,
+                                        torch.from_numpy(tsurf).to(dev))
+    corr = lcq.gen_corrections_batched(ctx, ds, near, "CFIE", phys, prm)
+    rng = np.random.default_rng(9)
+    g = rng.standard_normal(x.shape[1]) + 1j * rng.standard_normal(x.shape[1])
+    sig = W.density(s.n_points, 4)
+    gd, sd = torch.from_numpy(g).to(dev), torch.from_numpy(sig).to(dev)
+    ah = lcq.apply_adjoint(ctx, ds, near, corr, gd).cpu().numpy()
+    gy = lcq.shape_gradient(ctx, ds, near, corr, sd, gd).cpu().numpy()
+    assert ctx.sync(60000) == 0
+    t0 = 0
+    for i, (p, (k, a, b, eps)) in enumerate(zip(parts, phys)):
+        n0, n1 = s.node_off[poff[i]], s.node_off[poff[i + 1]]
+        t1 = t0 + xs[i].shape[1]
+        xi, ti, gi = xs[i], tn[t0:t1], g[t0:t1]
+        pp = C.Params(eps=eps, test_dirs=W.test_directions(3))
+        oc = C.gen_corrections(p.deg, p.node_off, p.xyz, xi, ti, "CFIE", k, a, b, params=pp)
+        ref = OA.apply_adjoint(oc, p.node_off, gi, xi, "CFIE", k, a, b)
+        assert np.linalg.norm(ah[n0:n1] - ref) <= 1e-10 * np.linalg.norm(ref), i
+        rg, _ = OA.shape_gradient(p.deg, p.node_off, p.xyz, xi, ti, "CFIE", k, a, b, pp,
+                                  sig[n0:n1], gi)
+        assert np.abs(gy[:, n0:n1] - rg).max() <= 1e-9 * np.abs(rg).max(), i
+        t0 = t1
