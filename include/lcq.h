@@ -62,16 +62,15 @@ typedef enum {
 typedef enum { LCQ_S = 0, LCQ_D = 1, LCQ_CFIE = 2, LCQ_SP = 3 } lcq_kernel;
 
 /* LCQ_FP64: every step in FP64.
- * LCQ_MIXED: in the adaptive near integration, every (target, leaf node) kernel value is
- * computed in FP32 from the FP64 difference x - X (r and the phase k r formed and
- * reduced in FP64) and contracted with FP32 basis values, summed in FP32 per chunk of
- * nodes into FP64 moments; the chart geometry, self rules, smooth and annulus rules,
- * far orders, refinement decisions and the values-to-coefficients contraction stay FP64.
- * The adaptive test's rounding floor is raised to FP32's level.  FP32's unit roundoff
- * (6e-8) cannot hold tighter tolerances, so the FP32 evaluation is used only for
- * eps >= 1e-7 (per surface in a batch); below, LCQ_MIXED is LCQ_FP64.  S' always runs
- * FP64.  The difference from LCQ_FP64 is stated per result by the tests and the
- * benchmark. */
+ * LCQ_MIXED: in the adaptive near integration and the smooth-rule and annulus moments,
+ * every (target, node) kernel value is computed in FP32 from the FP64 difference x - X
+ * (r and the phase k r formed and reduced in FP64) and contracted with FP32 basis
+ * values, summed in FP32 per chunk of nodes into FP64 moments; the chart geometry, self
+ * rules, far orders, refinement decisions and the values-to-coefficients contraction stay
+ * FP64.  The adaptive test's rounding floor is raised to FP32's level.  The result moves
+ * by about 1e-7 relative, so the FP32 evaluation is used only for eps >= 1e-6 (per
+ * surface in a batch); below, LCQ_MIXED is LCQ_FP64.  S' always runs FP64.  The
+ * difference from LCQ_FP64 is stated per result by the tests and the benchmark. */
 typedef enum { LCQ_FP64 = 0, LCQ_MIXED = 1 } lcq_precision;
 
 /* Surface: n_patches charts; patch j owns nodes node_off[j] .. node_off[j+1]-1,

@@ -108,6 +108,10 @@ lcq_status ensure_deg(lcq_ctx* ctx, int d) {
   CK(dalloc(st, &t.dnodes, (size_t)3 * n));
   CK(cudaMemcpyAsync(t.dV, t.V.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(t.dnodes, nodes.data(), (size_t)3 * n * 8, cudaMemcpyHostToDevice, st));
+  std::vector<double> duv(t.Du);
+  duv.insert(duv.end(), t.Dv.begin(), t.Dv.end());
+  CK(dalloc(st, &t.dDuv, duv.size()));
+  CK(cudaMemcpyAsync(t.dDuv, duv.data(), duv.size() * 8, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
   return LCQ_OK;
 }
@@ -229,6 +233,7 @@ void lcq_destroy(lcq_ctx* ctx) {
   for (int d = 0; d <= kMaxDeg; ++d) {
     dfree(ctx->stream, ctx->deg[d].dV);
     dfree(ctx->stream, ctx->deg[d].dnodes);
+    dfree(ctx->stream, ctx->deg[d].dDuv);
   }
   RuleTables& r = ctx->rules;
   dfree(ctx->stream, r.doff);
@@ -716,7 +721,10 @@ static Dev make_dev(lcq_ctx* ctx, const lcq_near* nr, const int32_t* q, int ldI,
   dv.gl_off = ctx->rules.dgl_off;
   dv.gl_x = ctx->rules.dgl_x;
   dv.gl_w = ctx->rules.dgl_w;
-  for (int d = 0; d <= kMaxDeg; ++d) dv.nodes_uv[d] = ctx->deg[d].dnodes;
+  for (int d = 0; d <= kMaxDeg; ++d) {
+    dv.nodes_uv[d] = ctx->deg[d].dnodes;
+    dv.duv[d] = ctx->deg[d].dDuv;
+  }
   dv.counters = ctx->d_counters;
   dv.status = ctx->d_status;
   dv.ldI = ldI;
@@ -869,6 +877,11 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   Dev dv = make_dev(ctx, nr, c->q, ldI, c->grp);
 
   CK(cudaEventRecord(ctx->ev[2], st));
+  // the mixed form (FP32 pair evaluation in the smooth, annulus and adaptive moments);
+  // per surface of a batch the kernels also check the surface's tolerance
+  const bool mixed_form = precision == LCQ_MIXED && kernel != LCQ_SP &&
+                          (nr->grouped || eps0 >= kMixedMinEps);
+  c->mixed_form = mixed_form;
   // 1. far order q_j and annulus order (Sec. 4.2, Eq. qj)
   const int fgrid = ctx->num_sms * 2;
   double* fscr;
@@ -883,8 +896,10 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   // 2. smooth-rule moments of every near and self pair; 3. annulus moments
   for (int d = 1; d <= kMaxDeg; ++d) {
     if (!nr->plist_count[d]) continue;
-    launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 0, c->q, kp, Is, IsS);
-    launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 1, c->q_near, kp, In, nullptr);
+    launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 0, c->q, kp, Is, IsS,
+                        mixed_form);
+    launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 1, c->q_near, kp, In,
+                        nullptr, mixed_form);
   }
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[4], st));
@@ -902,8 +917,7 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
                       eps0 * params->eps_loosen, ctx->deg[d].normV, params->leaf_order,
                       params->max_depth, Is, In, c->leaves, ctx->work, stride, (int)A, levels, agrid,
                       ctx->d_status, ctx->d_sched + d,
-                      precision == LCQ_MIXED && kernel != LCQ_SP &&
-                              (nr->grouped || eps0 >= kMixedMinEps) ? 2.0 : 0.0);
+                      mixed_form ? 2.0 : 0.0);
     }
     CK(cudaGetLastError());
   }
@@ -1189,7 +1203,7 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
       for (int d = 1; d <= kMaxDeg; ++d) {
         if (!nr->plist_count[d]) continue;
         launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 0, c->q, c->kp, Is,
-                            nullptr);
+                            nullptr, c->mixed_form);
       }
     const GradArgs ga{g, shat, M};
     for (int d = 1; d <= kMaxDeg; ++d) {
@@ -1198,8 +1212,7 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
                            c->eps0 * pr.eps_loosen, ctx->deg[d].normV, pr.leaf_order, pr.max_depth,
                            Is, In, leaves, ctx->work, stride, (int)nr->max_adaptive, levels, agrid,
                            ctx->d_status, ctx->d_sched + d,
-                           c->precision == LCQ_MIXED && (nr->grouped || c->eps0 >= kMixedMinEps)
-                               ? 2.0 : 0.0, ga);
+                           c->mixed_form ? 2.0 : 0.0, ga);
     }
     dfree(st, Is);
     dfree(st, In);

@@ -90,13 +90,14 @@ struct SegMap {
 // evaluated once per chunk of nodes and shared by all targets (Sec. 4.3 reuse).
 // TA: target accessor (pos(i, x[3])); out row of target i: out + orow(i) * ostride.
 // Positions are relative to the patch centroid cen (the coefficients cf describe
-// X - cen).  With ENV, eout[i * nseg + seg] also receives the summed rounding envelope.
+// X - cen); cfd holds the derivative series of load_coef_derivs, which replace the
+// derivative recurrences.  With ENV, eout[i * nseg + seg] also receives the summed rounding envelope.
 // mixed (the mixed form; sm then has Cfg<D>::WS_F32 more doubles): every (target, node)
 // pair is evaluated by kernel_eval_f32f from the FP64 difference x - X, its envelope
 // scaled by kF32Floor / kRoundingFloor, and contracted with FP32 basis values in FP32 per
 // chunk (accumulated into the FP64 moments).
 template <int D, bool ENV = false, class TA, class OR>
-__device__ void block_moments(const double* cf, const double* __restrict__ ru,
+__device__ void block_moments(const double* cf, const double* cfd, const double* __restrict__ ru,
                               const double* __restrict__ rv, const double* __restrict__ rw, int Q,
                               const SegMap* segs, int nseg, const TA& ta, int T, OR orow,
                               int64_t ostride, const KernelParams& kp, double* sm,
@@ -130,7 +131,7 @@ __device__ void block_moments(const double* cf, const double* __restrict__ ru,
       const double v = S.ay + r0 * S.e1y + r1 * S.e2y;
       const double w = rw[l] * S.det;
       double X[3], Xu[3], Xv[3], Nn[3];
-      kw_geometry<D>(u, v, cf, X, Xu, Xv, B + ql * C::BS, 1);
+      kw_geometry_proj<D>(u, v, cf, cfd, X, Xu, Xv, B + ql * C::BS);
       cross3(Xu, Xv, Nn);
       const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
 #pragma unroll
@@ -476,6 +477,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
   long long my_tests = 0, my_nodes = 0, my_tree = 0;
   __shared__ int next_b;
   __shared__ KernelParams kps;
+  __shared__ double cfd[2 * 3 * (D * (D + 1) / 2)];  // derivative series of the chart
+  const double* cfdp = cfd;
 
   for (;;) {
     __syncthreads();
@@ -504,6 +507,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
     __syncthreads();
     load_coef<D>(dv.coef, dv.node_off[j], cf);
     if (threadIdx.x == 0) kps = patch_kp(dv, j, kp);  // read after block_moments' barrier
+    __syncthreads();
+    load_coef_derivs<D>(cf, dv.duv[D], cfd);
     if constexpr (GRAD) {
 #pragma unroll
       for (int e = 0; e < 3 * n; ++e) Mg[e] = 0.0;
@@ -527,7 +532,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
     __syncthreads();
     if (leaf_order > 0) {
       TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, dv.tnrm};
-      block_moments<D>(cf, ru, rv, rw, Q, segs, 1, ta, A,
+      block_moments<D>(cf, cfdp, ru, rv, rw, Q, segs, 1, ta, A,
                        [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, 4 * n, kps, ws,
                        dv.cen + 3 * j);
     }
@@ -585,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
       __syncthreads();
       // children moments of every target in S
       TgtAdaptive ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, ST, dv.tnrm};
-      block_moments<D, true>(cf, ru, rv, rw, Q, segs, 4, ta, S,
+      block_moments<D, true>(cf, cfdp, ru, rv, rw, Q, segs, 4, ta, S,
                              [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, 4 * n, kps,
                              ws, dv.cen + 3 * j, Rj, tmpE, mixj);
       __syncthreads();

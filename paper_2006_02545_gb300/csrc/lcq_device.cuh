@@ -152,6 +152,66 @@ __device__ __forceinline__ void kw_geometry(double u, double v, const double* __
 // Self-rule geometry at Q = P + delta: the chord dX = X(Q) - X(P), formed from Koornwinder
 // differences K_nm(Q) - K_nm(P) that obey the same recurrences (so dX keeps its relative
 // precision as delta -> 0), and X_u, X_v at Q.
+// Chart X, X_u, X_v at (u, v) from the coefficients cf[nm][3] and the derivative series
+// cfd = (X_u coefficients [nd][3], X_v coefficients [nd][3]) in the degree D-1 basis
+// (nd its size: the first nd basis functions, those with n < D).  Only the values
+// recurrence runs; K (stride 1, written first and read back) receives the basis values.
+// Same polynomials as kw_geometry at about half its cost.
+template <int D>
+__device__ __forceinline__ void kw_geometry_proj(double u, double v, const double* cf,
+                                                 const double* cfd, double* X, double* Xu,
+                                                 double* Xv, double* K) {
+  constexpr int n = (D + 1) * (D + 2) / 2, nd = D * (D + 1) / 2;
+  kw_values<D>(u, v, K, 1);
+  double x0 = 0.0, x1 = 0.0, x2 = 0.0, u0 = 0.0, u1 = 0.0, u2 = 0.0, v0 = 0.0, v1 = 0.0,
+         v2 = 0.0;
+  // rolled loops over the stored values: keeps the coefficient loads next to their use
+#pragma unroll 1
+  for (int idx = 0; idx < nd; ++idx) {
+    const double k = K[idx];
+    x0 = fma(cf[idx * 3], k, x0);
+    x1 = fma(cf[idx * 3 + 1], k, x1);
+    x2 = fma(cf[idx * 3 + 2], k, x2);
+    u0 = fma(cfd[idx * 3], k, u0);
+    u1 = fma(cfd[idx * 3 + 1], k, u1);
+    u2 = fma(cfd[idx * 3 + 2], k, u2);
+    v0 = fma(cfd[(nd + idx) * 3], k, v0);
+    v1 = fma(cfd[(nd + idx) * 3 + 1], k, v1);
+    v2 = fma(cfd[(nd + idx) * 3 + 2], k, v2);
+  }
+#pragma unroll 1
+  for (int idx = nd; idx < n; ++idx) {
+    const double k = K[idx];
+    x0 = fma(cf[idx * 3], k, x0);
+    x1 = fma(cf[idx * 3 + 1], k, x1);
+    x2 = fma(cf[idx * 3 + 2], k, x2);
+  }
+  X[0] = x0;
+  X[1] = x1;
+  X[2] = x2;
+  Xu[0] = u0;
+  Xu[1] = u1;
+  Xu[2] = u2;
+  Xv[0] = v0;
+  Xv[1] = v1;
+  Xv[2] = v2;
+}
+
+// cfd for kw_geometry_proj from cf and the projections duv (Du [n][nd], then Dv), by
+// the block's threads.
+template <int D>
+__device__ __forceinline__ void load_coef_derivs(const double* cf, const double* __restrict__ duv,
+                                                 double* cfd) {
+  constexpr int n = (D + 1) * (D + 2) / 2, nd = D * (D + 1) / 2;
+  for (int e = threadIdx.x; e < 2 * nd * 3; e += blockDim.x) {
+    const int which = e / (nd * 3), r = e - which * nd * 3, j = r / 3, c = r - 3 * j;
+    const double* Dm = duv + (size_t)which * n * nd;
+    double acc = 0.0;
+    for (int nm = 0; nm < n; ++nm) acc = fma(cf[nm * 3 + c], Dm[nm * nd + j], acc);
+    cfd[e] = acc;
+  }
+}
+
 // f(idx, K_nm, dK_nm/du, dK_nm/dv) for every basis function at (u, v): the recurrences of
 // kw_geometry, for callers that need the derivatives one by one (the adjoint).
 template <int D, class F>

@@ -29,8 +29,9 @@ enum : int {
 };
 
 // The mixed form evaluates kernel values in FP32 only for tolerances eps >= kMixedMinEps:
-// FP32's unit roundoff (6e-8) cannot hold a tighter result, so below it the form is FP64.
-constexpr double kMixedMinEps = 1e-7;
+// with FP32 kernel values and contractions the result moves by about 1e-7 relative, so
+// below this tolerance the form is FP64.
+constexpr double kMixedMinEps = 1e-6;
 
 // Kernel parameters (Sec. 3): K = alpha D + beta S for CFIE.
 struct KernelParams {
@@ -75,6 +76,9 @@ struct DegTables {
   std::vector<double> V;         // values-to-coefficients, row-major [n][n] (row = nm)
   double* dV = nullptr;          // device copy of V
   double* dnodes = nullptr;      // device [3][n]: u, v, w
+  // derivative projections [n][n_{d-1}]: d/du and d/dv of K_nm in the degree d-1 basis
+  std::vector<double> Du, Dv;
+  double* dDuv = nullptr;        // device copy: Du then Dv
 };
 
 // Smooth rule family and Gauss-Legendre tables on the device.
@@ -188,6 +192,7 @@ struct lcq_corr {
   lcq_params params{};           // generation parameters (test directions dropped)
   double eps0 = 0.0;             // tolerance (first surface's in a batch)
   int precision = 0;             // lcq_precision of the generation
+  bool mixed_form = false;       // FP32 pair evaluation used (precision and tolerance)
   double* val = nullptr;         // [nnz][2]
   int32_t* q = nullptr;          // [P]
   int32_t* q_near = nullptr;     // [P]

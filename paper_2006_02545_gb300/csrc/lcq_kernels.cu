@@ -172,16 +172,20 @@ __global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* 
 template <int D>
 __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
     const int* __restrict__ plist, int count, Dev dv, int mode, const int32_t* __restrict__ qv,
-    const KernelParams kp, cplx* __restrict__ out_pairs, cplx* __restrict__ out_self) {
+    const KernelParams kp, cplx* __restrict__ out_pairs, cplx* __restrict__ out_self, bool mixed) {
   using C = Cfg<D>;
   extern __shared__ double smem[];
   double* cf = smem;
   SegMap* segs = reinterpret_cast<SegMap*>(cf + C::n * 3);
   double* ws = reinterpret_cast<double*>(segs + 4);
   __shared__ KernelParams kps;
+  __shared__ double cfd[2 * 3 * (D * (D + 1) / 2)];  // derivative series of the chart
+  const double* cfdp = cfd;
   for (int b = blockIdx.x; b < count; b += gridDim.x) {
     const int j = plist[b];
     const int m = qv[j];
+    // mixed form: FP32 pair evaluation where the (surface's) tolerance allows it
+    const bool mixj = mixed && !(dv.pgroup && dv.grp[dv.pgroup[j]].eps < kMixedMinEps);
     __syncthreads();
     load_coef<D>(dv.coef, dv.node_off[j], cf);
     if (threadIdx.x == 0) {
@@ -190,6 +194,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
     }
     __syncthreads();
     if (m <= 0) continue;
+    load_coef_derivs<D>(cf, dv.duv[D], cfd);
     const double* ru = dv.ru + dv.roff[m];
     const double* rv = dv.rv + dv.roff[m];
     const double* rw = dv.rw + dv.roff[m];
@@ -198,18 +203,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
       TgtIdx ta{dv.tgt, dv.NT, dv.pair_tgt + p0, dv.tnrm};
       const int64_t ld = dv.ldI;
       cplx* base = out_pairs + p0 * ld;
-      block_moments<D>(cf, ru, rv, rw, m * m, segs, 1, ta, (int)np,
+      block_moments<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)np,
                        [=] __device__(int i) { return base + (int64_t)i * ld; }, C::n, kps, ws,
-                       dv.cen + 3 * j);
+                       dv.cen + 3 * j, 0.0, nullptr, mixj);
       (void)out_self;
     } else {
       const int64_t a0 = dv.an_ptr[j], na = dv.an_ptr[j + 1] - a0;
       const int32_t* pl = dv.an_pair + a0;
       TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl, dv.tnrm};
       const int64_t ld = dv.ldI;
-      block_moments<D>(cf, ru, rv, rw, m * m, segs, 1, ta, (int)na,
+      block_moments<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)na,
                        [=] __device__(int i) { return out_pairs + (int64_t)pl[i] * ld; }, C::n, kps,
-                       ws, dv.cen + 3 * j);
+                       ws, dv.cen + 3 * j, 0.0, nullptr, mixj);
     }
     if (threadIdx.x == 0) {
       const long long nt = mode == 0 ? (dv.pair_ptr[j + 1] - dv.pair_ptr[j])
@@ -240,6 +245,8 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
   int* sel = reinterpret_cast<int*>(red + kThreads / 32);   // [2]
   double* ws = reinterpret_cast<double*>(sel + 4);
   __shared__ KernelParams kps;
+  __shared__ double cfd[2 * 3 * (D * (D + 1) / 2)];  // derivative series of the chart
+  const double* cfdp = cfd;
   cplx* bufA = scratch + (int64_t)blockIdx.x * 2 * kMaxTestPts * C::n;
   cplx* bufB = bufA + kMaxTestPts * C::n;
   const int m_min = (D + 2) / 2;
@@ -251,6 +258,8 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
       segs[0] = seg_T0();
       kps = patch_kp(dv, j, kp);
     }
+    __syncthreads();
+    load_coef_derivs<D>(cf, dv.duv[D], cfd);
     const int64_t p0 = dv.pair_ptr[j], np = dv.pair_ptr[j + 1] - p0;
     const double R = dv.rad[j], c0 = dv.cen[3 * j], c1 = dv.cen[3 * j + 1], c2 = dv.cen[3 * j + 2];
     const double tol = (dv.pgroup ? dv.grp[dv.pgroup[j]].eps : eps) * dv.dj[j] / normV;
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
       int m = m_min, chosen = m_max;
       {
         const double* ru = dv.ru + dv.roff[m];
-        block_moments<D>(cf, ru, dv.rv + dv.roff[m], dv.rw + dv.roff[m], m * m, segs, 1, ta, F,
+        block_moments<D>(cf, cfdp, ru, dv.rv + dv.roff[m], dv.rw + dv.roff[m], m * m, segs, 1, ta, F,
                          [=] __device__(int i) { return bufA + (int64_t)i * C::n; }, C::n, kps, ws,
                          dv.cen + 3 * j);
       }
@@ -348,7 +357,7 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
       cplx* Bf = bufB;
       for (; m < m_max; ++m) {
         const int m1 = m + 1;
-        block_moments<D>(cf, dv.ru + dv.roff[m1], dv.rv + dv.roff[m1], dv.rw + dv.roff[m1], m1 * m1,
+        block_moments<D>(cf, cfdp, dv.ru + dv.roff[m1], dv.rv + dv.roff[m1], dv.rw + dv.roff[m1], m1 * m1,
                          segs, 1, ta, F, [=] __device__(int i) { return Bf + (int64_t)i * C::n; },
                          C::n, kps, ws, dv.cen + 3 * j);
         __syncthreads();
@@ -826,13 +835,14 @@ size_t moments_smem_bytes(int extra_doubles) {
 template <int D>
 struct RuleMomL {
   static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv, int mode,
-                  const int32_t* qv, const KernelParams& kp, void* out_pairs, void* out_self) {
-    const size_t sm = moments_smem_bytes<D>(0);
+                  const int32_t* qv, const KernelParams& kp, void* out_pairs, void* out_self,
+                  bool mixed) {
+    const size_t sm = moments_smem_bytes<D>(0) + (mixed ? Cfg<D>::WS_F32 * sizeof(double) : 0);
     set_smem(k_rule_moments<D>, sm);
     const int grid = count < 2 * lc.num_sms ? count : 2 * lc.num_sms;
     ++*lc.launches;
     k_rule_moments<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, mode, qv, kp,
-                                                         (cplx*)out_pairs, (cplx*)out_self);
+                                                         (cplx*)out_pairs, (cplx*)out_self, mixed);
   }
 };
 
@@ -959,8 +969,8 @@ void launch_scan(const LaunchCommon& lc, const int64_t* in, int64_t* out, int64_
 
 bool launch_rule_moments(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                          int mode, const int32_t* qv, const KernelParams& kp, void* out_pairs,
-                         void* out_self) {
-  return dispatch<RuleMomL>(d, lc, plist, count, dv, mode, qv, kp, out_pairs, out_self);
+                         void* out_self, bool mixed) {
+  return dispatch<RuleMomL>(d, lc, plist, count, dv, mode, qv, kp, out_pairs, out_self, mixed);
 }
 bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, int m_max, double normV, const double* dirs,

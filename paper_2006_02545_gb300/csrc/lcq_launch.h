@@ -55,6 +55,7 @@ struct Dev {
   const double* gl_x;
   const double* gl_w;
   const double* nodes_uv[kMaxDeg + 1];
+  const double* duv[kMaxDeg + 1];  // derivative projections per degree: Du [n][n_{d-1}], then Dv
   long long* counters;
   int* status;
   int ldI;  // row stride (complex entries) of the pair/self moment buffers
@@ -126,7 +127,7 @@ void launch_scan(const LaunchCommon& lc, const int64_t* in, int64_t* out, int64_
                  int64_t* scratch);
 bool launch_rule_moments(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                          int mode, const int32_t* qv, const KernelParams& kp, void* out_pairs,
-                         void* out_self);
+                         void* out_self, bool mixed = false);
 bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, int m_max, double normV, const double* dirs,
                      int ndirs, void* scratch, int grid, int32_t* q, int32_t* qn);

@@ -38,7 +38,7 @@ std::mutex g_mu;
 
 // Byte offsets of the regions inside g_scratch.
 struct Layout {
-  size_t status, counters, sched, plist, node_off, Vt, nodes, coef, cen, rad, dj, eta, eta1, tpatch,
+  size_t status, counters, sched, plist, node_off, Vt, nodes, duv, coef, cen, rad, dj, eta, eta1, tpatch,
       tlnode, pair_ptr, pair_tgt, pair_d2, pair_csr, ad_ptr, ad_pair, an_ptr, an_pair, self_ptr,
       self_tgt, self_csr, q, qn, roff, ru, rv, rw, gl_off, gl_x, gl_w, Is, In, leaves, work;
   size_t end;
@@ -61,6 +61,7 @@ Layout layout(const RuleTables& r, int64_t work_bytes) {
   L.node_off = bump(&at, 2 * 8);
   L.Vt = bump(&at, n * n * 8);
   L.nodes = bump(&at, 3 * n * 8);
+  L.duv = bump(&at, 2 * n * n * 8);
   L.coef = bump(&at, 3 * n * 8);
   L.cen = bump(&at, 3 * 8);
   L.rad = bump(&at, 8);
@@ -238,6 +239,11 @@ extern "C" lcq_status lcq_adaptive_corrections_noalloc(
   cudaError_t e = cudaMemcpyAsync(F(L.Vt), dt.V.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(F(L.nodes), nodes, (size_t)3 * n * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(F(L.duv), dt.Du.data(), dt.Du.size() * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(F(L.duv) + dt.Du.size(), dt.Dv.data(), dt.Dv.size() * 8,
+                        cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(I32(L.q), &q, sizeof(int), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -289,6 +295,7 @@ extern "C" lcq_status lcq_adaptive_corrections_noalloc(
   dv.gl_x = F(L.gl_x);
   dv.gl_w = F(L.gl_w);
   dv.nodes_uv[deg] = F(L.nodes);
+  dv.duv[deg] = F(L.duv);
   dv.counters = reinterpret_cast<long long*>(b + L.counters);
   dv.status = I(L.status);
   dv.ldI = n;

@@ -205,6 +205,73 @@ void koornwinder_host(int d, double u, double v, double* K) {
   }
 }
 
+// K_nm and its u, v derivatives at (u, v) (the scaled-Legendre and Jacobi recurrences
+// differentiated term by term).
+static void koornwinder_host_derivs(int d, double u, double v, double* K, double* Ku, double* Kv) {
+  const double s = 2.0 * u + v - 1.0, q = 1.0 - v, q2 = q * q, y = 1.0 - 2.0 * v;
+  double Lp = 0.0, L = 1.0, Lup = 0.0, Lu = 0.0, Lvp = 0.0, Lv = 0.0;
+  for (int m = 0; m <= d; ++m) {
+    if (m > 0) {
+      const double f1 = 2.0 * m - 1.0, f2 = m - 1.0;
+      const double Ln = (f1 * s * L - f2 * q2 * Lp) / m;
+      const double Lun = (f1 * (2.0 * L + s * Lu) - f2 * q2 * Lup) / m;
+      const double Lvn = (f1 * (L + s * Lv) - f2 * (-2.0 * q * Lp + q2 * Lvp)) / m;
+      Lp = L;
+      L = Ln;
+      Lup = Lu;
+      Lu = Lun;
+      Lvp = Lv;
+      Lv = Lvn;
+    }
+    const double b = 2.0 * m + 1.0;
+    double Pp = 0.0, P = 1.0, dPp = 0.0, dP = 0.0;
+    for (int a = 0; a <= d - m; ++a) {
+      const int n = m + a, idx = n * (n + 1) / 2 + m;
+      const double cn = sqrt(2.0 * (2 * m + 1) * (n + 1));
+      K[idx] = cn * L * P;
+      Ku[idx] = cn * Lu * P;
+      Kv[idx] = cn * (Lv * P - 2.0 * L * dP);  // d/dv of P(1 - 2v) is -2 P'
+      const double den = 2.0 * (a + 1) * (a + b + 1) * (2 * a + b);
+      const double c1 = (2 * a + b + 1) * (2 * a + b + 2) * (2 * a + b) / den;
+      const double c0 = -(2 * a + b + 1) * b * b / den;
+      const double c2 = 2.0 * a * (a + b) * (2 * a + b + 2) / den;
+      const double t = c1 * y + c0;
+      const double Pn = t * P - c2 * Pp;
+      const double dPn = c1 * P + t * dP - c2 * dPp;
+      Pp = P;
+      P = Pn;
+      dPp = dP;
+      dP = dPn;
+    }
+  }
+}
+
+// Du[nm][j] = int_T0 dK_nm/du K_j, Dv likewise, j over the degree d-1 basis: the
+// derivative of a degree-d series sum_nm x_nm K_nm is sum_j (sum_nm x_nm D[nm][j]) K_j
+// (the basis is orthonormal on T0).  Conical-product rule of m = d + 1 points per
+// direction, exact to degree 2d + 1.
+static bool build_derivative_tables(int d, std::vector<double>* Du, std::vector<double>* Dv) {
+  const int n = n_basis(d), nd = n_basis(d - 1);
+  Du->assign((size_t)n * nd, 0.0);
+  Dv->assign((size_t)n * nd, 0.0);
+  std::vector<double> xa, wa, xb, wb, K(n), Ku(n), Kv(n);
+  const int m = d + 1;
+  if (!gauss_jacobi(m, 1.0, 0.0, &xa, &wa) || !gauss_jacobi(m, 0.0, 0.0, &xb, &wb)) return false;
+  for (int i = 0; i < m; ++i) {
+    const double a = 0.5 * (1.0 + xa[i]), Wa = wa[i] / 4.0;
+    for (int j = 0; j < m; ++j) {
+      const double bb = 0.5 * (1.0 + xb[j]), W = Wa * wb[j] / 2.0;
+      koornwinder_host_derivs(d, bb * (1.0 - a), a, K.data(), Ku.data(), Kv.data());
+      for (int r = 0; r < n; ++r)
+        for (int c = 0; c < nd; ++c) {
+          (*Du)[(size_t)r * nd + c] += W * Ku[r] * K[c];
+          (*Dv)[(size_t)r * nd + c] += W * Kv[r] * K[c];
+        }
+    }
+  }
+  return true;
+}
+
 bool build_deg_tables(int d, DegTables* t) {
   if (d < 1 || d > kMaxDeg) return false;
   const int n = n_basis(d);
@@ -229,7 +296,7 @@ bool build_deg_tables(int d, DegTables* t) {
       S[i * n + j] = acc;
     }
   t->normV = sqrt(sym_max_eig(n, S));
-  return true;
+  return build_derivative_tables(d, &t->Du, &t->Dv);
 }
 
 bool build_rule_tables(RuleTables* t) {
