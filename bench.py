@@ -328,6 +328,33 @@ def run_ours(args, rank, world, local_rank):
                     rec["fp32_used"] = eps >= 1e-6
                 variants[key] = rec
 
+    # the 20-patch sphere (single layer, k = 1, eps = 1e-6, eta = 1.25): 300 points, a
+    # latency-bound case (about 50 launches and three host synchronizations per step)
+    small = None
+    if not args.no_variants:
+        sw = W.sphere_s_k1()
+        sds = lcq.DeviceSurface(sw.surface.deg, sw.surface.node_off,
+                                torch.from_numpy(sw.surface.xyz).to(dev))
+        sx = torch.from_numpy(sw.tgt_xyz).to(dev)
+        stn = torch.from_numpy(sw.tgt_node).to(dev)
+        sp = lcq.params(sw.eps, eta=sw.eta, test_dirs=W.test_directions(7))
+        times = []
+        for it in range(8):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            near = lcq.build_near_lists(ctx, sds, sx, stn, sp)
+            corr = lcq.gen_corrections(ctx, sds, near, "S", 1.0, sp)
+            e1.record(stream)
+            st_s = ctx.sync()
+            if it >= 3:
+                times.append(e0.elapsed_time(e1))
+            corr.close()
+            near.close()
+        small = {"workload": sw.name, "points": sw.surface.n_points,
+                 "value": sw.surface.n_points / (statistics.median(times) / 1e3), "unit": UNIT,
+                 "ms_per_step": statistics.median(times), "status": st_s}
+
     # 64 independent tori in one batched generation against the same surfaces one by one
     batched = None
     if not args.no_variants and args.batched_scale > 0:
@@ -529,6 +556,7 @@ def run_ours(args, rank, world, local_rank):
         "stages_ms": dict(zip(["near_lists", "far_order", "smooth_annulus", "adaptive", "self",
                                "v2c"], st_mean)),
         "variants": variants,
+        "sphere20": small,
         "batched": batched,
         "table1": table1,
         "large": large,

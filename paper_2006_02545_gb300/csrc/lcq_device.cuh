@@ -212,6 +212,65 @@ __device__ __forceinline__ void load_coef_derivs(const double* cf, const double*
   }
 }
 
+// kw_delta_geometry with X_u, X_v at P + delta taken from the derivative series cfd (as in
+// kw_geometry_proj) instead of the differentiated recurrences.
+template <int D>
+__device__ __forceinline__ void kw_delta_geometry_proj(double pu, double pv, double du, double dv,
+                                                       const double* __restrict__ cf,
+                                                       const double* __restrict__ cfd, double* dX,
+                                                       double* Xu, double* Xv) {
+  constexpr int nd = D * (D + 1) / 2;
+  const double uq = pu + du, vq = pv + dv;
+  const double sP = 2.0 * pu + pv - 1.0, qP = 1.0 - pv, yP = 1.0 - 2.0 * pv;
+  const double sQ = 2.0 * uq + vq - 1.0, qQ = 1.0 - vq, yQ = 1.0 - 2.0 * vq;
+  const double ds = 2.0 * du + dv, dq2 = -dv * (qQ + qP), dy = -2.0 * dv;
+  const double qQ2 = qQ * qQ, qP2 = qP * qP;
+  double LPp = 0.0, LP = 1.0, LQp = 0.0, LQ = 1.0, dLp = 0.0, dL = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dX[c] = Xu[c] = Xv[c] = 0.0;
+#pragma unroll
+  for (int m = 0; m <= D; ++m) {
+    if (m > 0) {
+      const double f1 = 2.0 * m - 1.0, f2 = m - 1.0, im = 1.0 / m;
+      const double nLP = (f1 * sP * LP - f2 * qP2 * LPp) * im;
+      const double nLQ = (f1 * sQ * LQ - f2 * qQ2 * LQp) * im;
+      const double ndL = (f1 * (sQ * dL + ds * LP) - f2 * (qQ2 * dLp + dq2 * LPp)) * im;
+      LPp = LP; LP = nLP;
+      LQp = LQ; LQ = nLQ;
+      dLp = dL; dL = ndL;
+    }
+    const int b = 2 * m + 1;
+    double PPp = 0.0, PP = 1.0, PQp = 0.0, PQ = 1.0, dPp = 0.0, dP = 0.0;
+#pragma unroll
+    for (int a = 0; a <= D - m; ++a) {
+      const int n = m + a, idx = n * (n + 1) / 2 + m;
+      const double cn = c_kw[idx];
+      const double dk = cn * (dL * PQ + LP * dP);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dX[c] = fma(cf[idx * 3 + c], dk, dX[c]);
+      if (n < D) {
+        const double kq = cn * LQ * PQ;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Xu[c] = fma(cfd[idx * 3 + c], kq, Xu[c]);
+          Xv[c] = fma(cfd[(nd + idx) * 3 + c], kq, Xv[c]);
+        }
+      }
+      if (a < D - m) {
+        double c1, c0, c2;
+        jacobi_coef(a, b, &c1, &c0, &c2);
+        const double tQ = c1 * yQ + c0;
+        const double nPP = (c1 * yP + c0) * PP - c2 * PPp;
+        const double nPQ = tQ * PQ - c2 * PQp;
+        const double ndP = tQ * dP + c1 * dy * PP - c2 * dPp;
+        PPp = PP; PP = nPP;
+        PQp = PQ; PQ = nPQ;
+        dPp = dP; dP = ndP;
+      }
+    }
+  }
+}
+
 // f(idx, K_nm, dK_nm/du, dK_nm/dv) for every basis function at (u, v): the recurrences of
 // kw_geometry, for callers that need the derivatives one by one (the adjoint).
 template <int D, class F>

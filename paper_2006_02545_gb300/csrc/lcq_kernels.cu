@@ -423,6 +423,7 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
   __shared__ KernelParams kps;
   __shared__ int ord;
   __shared__ double nP[3];  // unit chart normal at the target node (S')
+  __shared__ double cfd[2 * 3 * (D * (D + 1) / 2)];  // derivative series of the chart
   long long my_nodes = 0;
   for (int64_t s = blockIdx.x; s < dv.n_self; s += gridDim.x) {
     const int t = dv.self_tgt[s];
@@ -436,6 +437,7 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
       ord = dv.pgroup ? dv.grp[dv.pgroup[j]].self_order : order;
     }
     __syncthreads();
+    load_coef_derivs<D>(cf, dv.duv[D], cfd);
     const int ns = ord, nt = ord;
     const double* glx_s = dv.gl_x + dv.gl_off[ns];
     const double* glw_s = dv.gl_w + dv.gl_off[ns];
@@ -526,7 +528,7 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
       const double u = P[0] + du;
       const double v = P[1] + dvv;
       double dX[3], Xu[3], Xv[3], Nn[3];
-      kw_delta_geometry<D>(P[0], P[1], du, dvv, cf, dX, Xu, Xv);
+      kw_delta_geometry_proj<D>(P[0], P[1], du, dvv, cf, cfd, dX, Xu, Xv);
       cross3(Xu, Xv, Nn);
       const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
       const cplx gk = kernel_eval(kps, 0.0, 0.0, 0.0, dX[0], dX[1], dX[2], Nn[0] * w, Nn[1] * w,
