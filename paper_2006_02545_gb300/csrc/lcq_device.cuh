@@ -63,37 +63,6 @@ __device__ __forceinline__ void kw_values(double u, double v, double* K, int ks)
   }
 }
 
-// acc[nm] += g * K_nm(u, v) for all nm (values recurrence fused with the update).
-template <int D>
-__device__ __forceinline__ void kw_accumulate(double u, double v, cplx g, cplx* acc) {
-  const double s = 2.0 * u + v - 1.0, q2 = (1.0 - v) * (1.0 - v), y = 1.0 - 2.0 * v;
-  double Lp = 0.0, L = 1.0;
-#pragma unroll
-  for (int m = 0; m <= D; ++m) {
-    if (m > 0) {
-      const double Ln = ((2.0 * m - 1.0) * s * L - (m - 1.0) * q2 * Lp) * (1.0 / m);
-      Lp = L;
-      L = Ln;
-    }
-    const int b = 2 * m + 1;
-    double Pp = 0.0, P = 1.0;
-#pragma unroll
-    for (int a = 0; a <= D - m; ++a) {
-      const int n = m + a, idx = n * (n + 1) / 2 + m;
-      const double K = c_kw[idx] * L * P;
-      acc[idx].re = fma(g.re, K, acc[idx].re);
-      acc[idx].im = fma(g.im, K, acc[idx].im);
-      if (a < D - m) {
-        double c1, c0, c2;
-        jacobi_coef(a, b, &c1, &c0, &c2);
-        const double Pn = (c1 * y + c0) * P - c2 * Pp;
-        Pp = P;
-        P = Pn;
-      }
-    }
-  }
-}
-
 // Chart X, X_u, X_v at (u, v) from Koornwinder coefficients cf[nm][3]; optionally
 // also K values (stride ks) when K != nullptr.
 template <int D>
@@ -213,12 +182,12 @@ __device__ __forceinline__ void load_coef_derivs(const double* cf, const double*
 }
 
 // kw_delta_geometry with X_u, X_v at P + delta taken from the derivative series cfd (as in
-// kw_geometry_proj) instead of the differentiated recurrences.
+// kw_geometry_proj) instead of the differentiated recurrences; KQ receives K_nm(P + delta).
 template <int D>
 __device__ __forceinline__ void kw_delta_geometry_proj(double pu, double pv, double du, double dv,
                                                        const double* __restrict__ cf,
                                                        const double* __restrict__ cfd, double* dX,
-                                                       double* Xu, double* Xv) {
+                                                       double* Xu, double* Xv, double* KQ) {
   constexpr int nd = D * (D + 1) / 2;
   const double uq = pu + du, vq = pv + dv;
   const double sP = 2.0 * pu + pv - 1.0, qP = 1.0 - pv, yP = 1.0 - 2.0 * pv;
@@ -248,8 +217,9 @@ __device__ __forceinline__ void kw_delta_geometry_proj(double pu, double pv, dou
       const double dk = cn * (dL * PQ + LP * dP);
 #pragma unroll
       for (int c = 0; c < 3; ++c) dX[c] = fma(cf[idx * 3 + c], dk, dX[c]);
+      const double kq = cn * LQ * PQ;
+      KQ[idx] = kq;
       if (n < D) {
-        const double kq = cn * LQ * PQ;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           Xu[c] = fma(cfd[idx * 3 + c], kq, Xu[c]);

@@ -424,6 +424,8 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
   __shared__ int ord;
   __shared__ double nP[3];  // unit chart normal at the target node (S')
   __shared__ double cfd[2 * 3 * (D * (D + 1) / 2)];  // derivative series of the chart
+  __shared__ cplx gbuf[128];                          // kernel values of a chunk's nodes
+  extern __shared__ double krows[];                   // [128][n + 1] basis rows of a chunk
   long long my_nodes = 0;
   for (int64_t s = blockIdx.x; s < dv.n_self; s += gridDim.x) {
     const int t = dv.self_tgt[s];
@@ -504,44 +506,66 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
     }
     __syncthreads();
     // the target is the chart's value at the node: x - X(P + delta) = -(dX)
-    cplx acc[n];
-#pragma unroll
-    for (int k = 0; k < n; ++k) acc[k] = {0.0, 0.0};
+    // chunks of 128 nodes: each thread forms one node's kernel value and basis row in
+    // shared memory, then the block contracts them, thread (nm, quarter of the chunk)
     const int tot = total;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int k = 0;
-      while (k + 1 < nseg && idx >= sg[k + 1].off) ++k;
-      const SelfSeg& g = sg[k];
-      const int loc = idx - g.off;
-      const int p = loc / (nt * ns);
-      const int rem = loc - p * nt * ns;
-      const int ti = rem / ns, si = rem - ti * ns;
-      const double lo = g.xi_max * p / g.npan, hi = g.xi_max * (p + 1) / g.npan;
-      const double xi = lo + (hi - lo) * glx_t[ti];
-      const double tpar = g.t0 + g.side * g.mu * sinh(xi);
-      const double wt = glw_t[ti] * (hi - lo) * g.mu * cosh(xi);
-      const double sv = glx_s[si];
-      const double w = glw_s[si] * wt * sv * g.area2 * Mm[4];
-      const double zx = sv * (g.E0x + tpar * g.Dx), zy = sv * (g.E0y + tpar * g.Dy);
-      const double du = Mm[0] * zx + Mm[1] * zy;
-      const double dvv = Mm[2] * zx + Mm[3] * zy;
-      const double u = P[0] + du;
-      const double v = P[1] + dvv;
-      double dX[3], Xu[3], Xv[3], Nn[3];
-      kw_delta_geometry_proj<D>(P[0], P[1], du, dvv, cf, cfd, dX, Xu, Xv);
-      cross3(Xu, Xv, Nn);
-      const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
-      const cplx gk = kernel_eval(kps, 0.0, 0.0, 0.0, dX[0], dX[1], dX[2], Nn[0] * w, Nn[1] * w,
-                                  Nn[2] * w, J * w, 0.0, nullptr, nP);
-      kw_accumulate<D>(u, v, gk, acc);
+    constexpr int NR = (n + 31) / 32;  // basis indices per thread in the contraction
+    const int lane = threadIdx.x & 31, part = threadIdx.x >> 5;
+    double are[NR], aim[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) are[r] = aim[r] = 0.0;
+    for (int c0 = 0; c0 < tot; c0 += 128) {
+      const int idx = c0 + threadIdx.x;
+      cplx gk = {0.0, 0.0};
+      double* Kq = krows + threadIdx.x * (n + 1);
+      if (idx < tot) {
+        int k = 0;
+        while (k + 1 < nseg && idx >= sg[k + 1].off) ++k;
+        const SelfSeg& g = sg[k];
+        const int loc = idx - g.off;
+        const int p = loc / (nt * ns);
+        const int rem = loc - p * nt * ns;
+        const int ti = rem / ns, si = rem - ti * ns;
+        const double lo = g.xi_max * p / g.npan, hi = g.xi_max * (p + 1) / g.npan;
+        const double xi = lo + (hi - lo) * glx_t[ti];
+        const double tpar = g.t0 + g.side * g.mu * sinh(xi);
+        const double wt = glw_t[ti] * (hi - lo) * g.mu * cosh(xi);
+        const double sv = glx_s[si];
+        const double w = glw_s[si] * wt * sv * g.area2 * Mm[4];
+        const double zx = sv * (g.E0x + tpar * g.Dx), zy = sv * (g.E0y + tpar * g.Dy);
+        const double du = Mm[0] * zx + Mm[1] * zy;
+        const double dvv = Mm[2] * zx + Mm[3] * zy;
+        double dX[3], Xu[3], Xv[3], Nn[3];
+        kw_delta_geometry_proj<D>(P[0], P[1], du, dvv, cf, cfd, dX, Xu, Xv, Kq);
+        cross3(Xu, Xv, Nn);
+        const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
+        gk = kernel_eval(kps, 0.0, 0.0, 0.0, dX[0], dX[1], dX[2], Nn[0] * w, Nn[1] * w,
+                         Nn[2] * w, J * w, 0.0, nullptr, nP);
+      } else {
+        for (int e = 0; e < n; ++e) Kq[e] = 0.0;
+      }
+      gbuf[threadIdx.x] = gk;
+      __syncthreads();
+      const int qa = part * 32, qb = min(qa + 32, tot - c0);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const int nm = lane + 32 * r;
+        if (nm < n)
+          for (int q = qa; q < qb; ++q) {
+            const cplx gq = gbuf[q];
+            const double kv = krows[q * (n + 1) + nm];
+            are[r] = fma(gq.re, kv, are[r]);
+            aim[r] = fma(gq.im, kv, aim[r]);
+          }
+      }
+      __syncthreads();
     }
     my_nodes += tot;
-    // block reduction (4 warps)
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    // the four quarters, in a fixed order
 #pragma unroll
-    for (int k = 0; k < n; ++k) {
-      const double r = warp_sum(acc[k].re), im = warp_sum(acc[k].im);
-      if (lane == 0) red[wp][k] = {r, im};
+    for (int r = 0; r < NR; ++r) {
+      const int nm = lane + 32 * r;
+      if (nm < n) red[part][nm] = {are[r], aim[r]};
     }
     __syncthreads();
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -888,7 +912,9 @@ struct SelfL {
     const int64_t g = dv.n_self < (int64_t)lc.num_sms * 16 ? dv.n_self : (int64_t)lc.num_sms * 16;
     if (g <= 0) return;
     ++*lc.launches;
-    k_self<D><<<(int)g, 128, 0, lc.stream>>>(dv, deg, kp, order, (cplx*)out);
+    const size_t sm = (size_t)128 * ((D + 1) * (D + 2) / 2 + 1) * sizeof(double);
+    set_smem(k_self<D>, sm);
+    k_self<D><<<(int)g, 128, sm, lc.stream>>>(dv, deg, kp, order, (cplx*)out);
   }
 };
 
