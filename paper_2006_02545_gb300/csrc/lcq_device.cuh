@@ -118,9 +118,6 @@ __device__ __forceinline__ void kw_geometry(double u, double v, const double* __
   }
 }
 
-// Self-rule geometry at Q = P + delta: the chord dX = X(Q) - X(P), formed from Koornwinder
-// differences K_nm(Q) - K_nm(P) that obey the same recurrences (so dX keeps its relative
-// precision as delta -> 0), and X_u, X_v at Q.
 // Chart X, X_u, X_v at (u, v) from the coefficients cf[nm][3] and the derivative series
 // cfd = (X_u coefficients [nd][3], X_v coefficients [nd][3]) in the degree D-1 basis
 // (nd its size: the first nd basis functions, those with n < D).  Only the values
@@ -181,8 +178,10 @@ __device__ __forceinline__ void load_coef_derivs(const double* cf, const double*
   }
 }
 
-// kw_delta_geometry with X_u, X_v at P + delta taken from the derivative series cfd (as in
-// kw_geometry_proj) instead of the differentiated recurrences; KQ receives K_nm(P + delta).
+// Self-rule geometry at Q = P + delta: the chord dX = X(Q) - X(P), formed from Koornwinder
+// differences K_nm(Q) - K_nm(P) that obey the same recurrences as the values (so dX keeps
+// its relative precision as delta -> 0); X_u, X_v at Q from the derivative series cfd (as
+// in kw_geometry_proj); KQ receives K_nm(Q).
 template <int D>
 __device__ __forceinline__ void kw_delta_geometry_proj(double pu, double pv, double du, double dv,
                                                        const double* __restrict__ cf,
@@ -283,72 +282,13 @@ __device__ __forceinline__ void kw_for_each(double u, double v, F&& f) {
   }
 }
 
-template <int D>
-__device__ __forceinline__ void kw_delta_geometry(double pu, double pv, double du, double dv,
-                                                  const double* __restrict__ cf, double* dX,
-                                                  double* Xu, double* Xv) {
-  const double uq = pu + du, vq = pv + dv;
-  const double sP = 2.0 * pu + pv - 1.0, qP = 1.0 - pv, yP = 1.0 - 2.0 * pv;
-  const double sQ = 2.0 * uq + vq - 1.0, qQ = 1.0 - vq, yQ = 1.0 - 2.0 * vq;
-  const double ds = 2.0 * du + dv, dq2 = -dv * (qQ + qP), dy = -2.0 * dv;
-  const double qQ2 = qQ * qQ, qP2 = qP * qP;
-  double LPp = 0.0, LP = 1.0, LQp = 0.0, LQ = 1.0, dLp = 0.0, dL = 0.0;
-  double Lup = 0.0, Lu = 0.0, Lvp = 0.0, Lv = 0.0;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) dX[c] = Xu[c] = Xv[c] = 0.0;
-#pragma unroll
-  for (int m = 0; m <= D; ++m) {
-    if (m > 0) {
-      const double f1 = 2.0 * m - 1.0, f2 = m - 1.0, im = 1.0 / m;
-      const double nLP = (f1 * sP * LP - f2 * qP2 * LPp) * im;
-      const double nLQ = (f1 * sQ * LQ - f2 * qQ2 * LQp) * im;
-      const double ndL = (f1 * (sQ * dL + ds * LP) - f2 * (qQ2 * dLp + dq2 * LPp)) * im;
-      const double nLu = (f1 * (2.0 * LQ + sQ * Lu) - f2 * qQ2 * Lup) * im;
-      const double nLv = (f1 * (LQ + sQ * Lv) - f2 * (-2.0 * qQ * LQp + qQ2 * Lvp)) * im;
-      LPp = LP; LP = nLP;
-      LQp = LQ; LQ = nLQ;
-      dLp = dL; dL = ndL;
-      Lup = Lu; Lu = nLu;
-      Lvp = Lv; Lv = nLv;
-    }
-    const int b = 2 * m + 1;
-    double PPp = 0.0, PP = 1.0, PQp = 0.0, PQ = 1.0, dPp = 0.0, dP = 0.0, pQp = 0.0, pQ = 0.0;
-#pragma unroll
-    for (int a = 0; a <= D - m; ++a) {
-      const int n = m + a, idx = n * (n + 1) / 2 + m;
-      const double cn = c_kw[idx];
-      const double dk = cn * (dL * PQ + LP * dP);
-      const double ku = cn * Lu * PQ;
-      const double kv = cn * (Lv * PQ - 2.0 * LQ * pQ);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double x = cf[idx * 3 + c];
-        dX[c] = fma(x, dk, dX[c]);
-        Xu[c] = fma(x, ku, Xu[c]);
-        Xv[c] = fma(x, kv, Xv[c]);
-      }
-      if (a < D - m) {
-        double c1, c0, c2;
-        jacobi_coef(a, b, &c1, &c0, &c2);
-        const double tQ = c1 * yQ + c0;
-        const double nPP = (c1 * yP + c0) * PP - c2 * PPp;
-        const double nPQ = tQ * PQ - c2 * PQp;
-        const double ndP = tQ * dP + c1 * dy * PP - c2 * dPp;
-        const double npQ = c1 * PQ + tQ * pQ - c2 * pQp;
-        PPp = PP; PP = nPP;
-        PQp = PQ; PQ = nPQ;
-        dPp = dP; dP = ndP;
-        pQp = pQ; pQ = npQ;
-      }
-    }
-  }
-}
-
 // Kernel times area element and weight, at a source with position X, weighted
 // unnormalized normal Nw = (X_u x X_v) w and weighted Jacobian Jw = |X_u x X_v| w:
 //   S: G_k(x, X) Jw
 //   D: Nw.(x - X) (1 - ik r) e^{ikr} / (4 pi r^3)
-//   CFIE: alpha D + beta S.   r = 0 contributes 0.
+//   CFIE: alpha D + beta S.
+//   S': the D form with Nw replaced by -n_x Jw (nx: the target's unit normal).
+// r = 0 contributes 0.
 // With env != nullptr also the rounding envelope from the same r,
 //   |G| Jw (|beta| + |alpha| |1 - ik r| R / r^2)   (kp.eb = |beta|, kp.ea = |alpha|),
 // the size of the kernel value's rounding noise when positions carry errors of order u R
@@ -401,11 +341,6 @@ __device__ __forceinline__ cplx kernel_eval(const KernelParams& kp, double x0, d
   return out;
 }
 
-// Mixed-precision variant for sources well separated from the target: the difference
-// d = x - X and r^2 arrive in FP64 (kept in FP64, as is the phase k r, refined from the
-// FP32 distance by one Newton step and reduced modulo 2 pi); everything else -- 1/r,
-// sin/cos of the reduced phase, the S and D factors, the CFIE combination -- is FP32.
-// The rounding envelope is returned multiplied by env_scale (the FP32 noise is larger).
 // Kernel parameters converted to FP32 once per patch (the mixed form's pair evaluations).
 struct KernelParamsF {
   float kr, ki, ar, ai, br, bi, eb, ea;
@@ -415,8 +350,10 @@ __device__ __forceinline__ KernelParamsF to_f32(const KernelParams& kp) {
           (float)kp.br, (float)kp.bi, (float)kp.eb, (float)kp.ea};
 }
 
-// Mixed form: K~ w in FP32 from the FP64 difference d = x - X and r2 = |d|^2; r and the
-// phase k r (reduced mod 2 pi) are formed in FP64 first, everything after in FP32.
+// Mixed form: K~ w in FP32 from the FP64 difference d = x - X and r2 = |d|^2; r (refined
+// from the FP32 distance by one Newton step) and the phase k r (reduced mod 2 pi) are
+// formed in FP64 first; 1/r, sin/cos of the reduced phase, the S and D factors and the
+// CFIE combination are FP32.
 // N, J: FP32 copies of the weighted normal and area element.  r2 > 0.
 __device__ __forceinline__ float2 kernel_eval_f32f(const KernelParams& kp, const KernelParamsF& kf,
                                                    double d0, double d1, double d2, double r2,

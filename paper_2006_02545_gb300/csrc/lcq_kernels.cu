@@ -1071,15 +1071,4 @@ int adaptive_blocks_per_sm(int d) {
   return nb < 1 ? 1 : nb;
 }
 
-size_t adaptive_smem_bytes(int d) {
-  switch (d) {
-#define LCQ_CASE(D) \
-  case D: return moments_smem_bytes<D>(64 / 2 + 4 * 32) + 64 * sizeof(int);
-    LCQ_CASE(1) LCQ_CASE(2) LCQ_CASE(3) LCQ_CASE(4) LCQ_CASE(5)
-    LCQ_CASE(6) LCQ_CASE(7) LCQ_CASE(8) LCQ_CASE(9) LCQ_CASE(10)
-#undef LCQ_CASE
-    default: return 0;
-  }
-}
-
 }  // namespace lcq

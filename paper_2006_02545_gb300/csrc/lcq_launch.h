@@ -150,7 +150,6 @@ void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const
 void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int32_t* col,
                       const double* val, const void* sigma, const int64_t* tnode, int64_t NT,
                       double jump, void* out);
-size_t adaptive_smem_bytes(int d);
 int adaptive_blocks_per_sm(int d);
 
 // Unit target normals for S' (SoA [3][NT]): the chart normal at the node of an on-surface

@@ -400,3 +400,42 @@ def test_stellarator_sampled_parity(ctx):
     worst, npairs, where = compare_pairs(g, oc, s.node_off)
     assert npairs > 100 and worst <= 1.0, (worst, where)
 
+
+
+def test_mixed_form_per_surface_tolerance(ctx):
+    """LCQ_MIXED on a batch whose surfaces ask eps = 1e-6 and 1e-9: the first surface gets
+    the FP32 pair evaluation (within its eps of the oracle), the second stays FP64 bit for
+    bit (its corrections equal those of an FP64 generation of the same batch)."""
+    import torch
+    from paper_2006_02545_gb300 import lcq
+    dev = ctx.torch_device
+    parts = [W.ellipsoid(1, 4, axes=(1.0, 1.3, 0.9)), W.ellipsoid(1, 3, axes=(0.8, 0.9, 1.2))]
+    phys = [(2.5, 1.0, -2.5j, 1e-6), (1.5, 1.0, -1.5j, 1e-9)]
+    s, poff = W.concat_surfaces(parts, [(0.0, 0.0, 0.0), (5.0, 0.0, 0.0)])
+    x, tn = W.onsurface_targets(s)
+    ds = lcq.DeviceSurface(s.deg, s.node_off, torch.from_numpy(s.xyz).to(dev))
+    prm = lcq.params(1e-6, test_dirs=W.test_directions(3))
+    near = lcq.build_near_lists_batched(ctx, ds, poff, torch.from_numpy(x).to(dev),
+                                        torch.from_numpy(tn).to(dev), prm)
+    vals = {}
+    for prec in ("fp64", "mixed"):
+        corr = lcq.gen_corrections_batched(ctx, ds, near, "CFIE", phys, prm, precision=prec)
+        assert ctx.sync(60000) == 0
+        vals[prec] = corr.export(x.shape[1])
+        if prec == "mixed":
+            sig = W.density(s.n_points, 0)
+            u = lcq.apply_corrected_CFIE(ctx, ds, near, corr, torch.from_numpy(sig).to(dev),
+                                         x.shape[1]).cpu().numpy()
+        corr.close()
+    rp, col, v64 = vals["fp64"]
+    _, _, vmx = vals["mixed"]
+    n0 = s.node_off[poff[1]]
+    a, b = rp[0], rp[n0]
+    assert not np.array_equal(v64[a:b], vmx[a:b])            # surface 0: FP32 evaluation
+    assert np.array_equal(v64[b:], vmx[b:])                   # surface 1: FP64
+    k, al, be, eps = phys[0]
+    xp, tnp = W.onsurface_targets(parts[0])
+    oc, uo = run_oracle(parts[0], xp, tnp, "CFIE", k, eps, alpha=al, beta=be, sigma=sig[:n0])
+    rel = np.linalg.norm(u[:n0] - uo) / np.linalg.norm(uo)
+    assert rel <= eps, rel
+    near.close()
