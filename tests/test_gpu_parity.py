@@ -439,3 +439,69 @@ def test_mixed_form_per_surface_tolerance(ctx):
     rel = np.linalg.norm(u[:n0] - uo) / np.linalg.norm(uo)
     assert rel <= eps, rel
     near.close()
+
+
+def test_green_identity_converges(ctx):
+    """Green's identity on a closed surface, the paper's own check of S and D together
+    (Sec. 6): for u = G_k(., x0) with x0 inside, every node x satisfies
+    u(x)/2 = D[u](x) - S[du/dn](x) (principal value of D, outward normals).  The GPU's
+    corrected potentials meet it to the discretization error, which falls with h."""
+    import torch
+    from paper_2006_02545_gb300 import lcq
+    dev = ctx.torch_device
+    axes = np.array([1.0, 1.5, 2.0])
+    x0 = np.array([0.1, 0.2, -0.15])
+    k = 2.0
+    errs = []
+    for sdiv in (1, 2, 4):
+        s = W.ellipsoid(sdiv, 4, axes=tuple(axes))
+        y = s.xyz
+        d = y - x0[:, None]
+        r = np.sqrt((d * d).sum(0))
+        u = np.exp(1j * k * r) / (4 * np.pi * r)
+        nrm = y / axes[:, None] ** 2
+        nrm /= np.linalg.norm(nrm, axis=0)
+        dudn = (nrm * d).sum(0) / r * u * (1j * k - 1.0 / r)
+        x, tn = W.onsurface_targets(s)
+        ds = lcq.DeviceSurface(s.deg, s.node_off, torch.from_numpy(y).to(dev))
+        prm = lcq.params(1e-9, test_dirs=W.test_directions(3))
+        near = lcq.build_near_lists(ctx, ds, torch.from_numpy(x).to(dev),
+                                    torch.from_numpy(tn).to(dev), prm)
+        cs = lcq.gen_corrections(ctx, ds, near, "S", k, prm)
+        cd = lcq.gen_corrections(ctx, ds, near, "D", k, prm)
+        ud = torch.from_numpy(u).to(dev)
+        gd = torch.from_numpy(dudn).to(dev)
+        Du = lcq.apply_corrected_D(ctx, ds, near, cd, ud, x.shape[1]).cpu().numpy()
+        Sg = lcq.apply_corrected_S(ctx, ds, near, cs, gd, x.shape[1]).cpu().numpy()
+        assert ctx.sync(60000) == 0
+        errs.append(np.abs(0.5 * u - (Du - Sg)).max() / np.abs(u).max())
+        cs.close()
+        cd.close()
+        near.close()
+    assert errs[1] < 0.25 * errs[0] and errs[2] < 0.25 * errs[1] and errs[2] < 1e-4, errs
+
+
+def test_sync_timeout_reports_and_recovers(ctx):
+    """A wait on the library's stream that runs out reports LCQ_ERR_TIMEOUT (9) without
+    touching the work in flight; the next wait without a limit completes it, and the
+    result equals that of an undisturbed run (host-side failure detection, no GPU fault)."""
+    import torch
+    from paper_2006_02545_gb300 import lcq
+    dev = ctx.torch_device
+    wl = W.ellipsoid_cfie_k2pi(8)
+    s = wl.surface
+    ds = lcq.DeviceSurface(s.deg, s.node_off, torch.from_numpy(s.xyz).to(dev))
+    x = torch.from_numpy(wl.tgt_xyz).to(dev)
+    tn = torch.from_numpy(wl.tgt_node).to(dev)
+    prm = lcq.params(wl.eps, test_dirs=W.test_directions(7))
+    vals = []
+    for interrupt in (True, False):
+        near = lcq.build_near_lists(ctx, ds, x, tn, prm)
+        corr = lcq.gen_corrections(ctx, ds, near, "CFIE", wl.k, prm, wl.alpha, wl.beta)
+        if interrupt:
+            assert ctx.sync(0) == 9          # the ~0.7 s generation is still running
+        assert ctx.sync(120000) == 0
+        vals.append(corr.export(s.n_points)[2].copy())
+        corr.close()
+        near.close()
+    assert np.array_equal(vals[0], vals[1])
