@@ -253,6 +253,13 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
                               const lcq_corr* corr, const double* sigma, const double* g,
                               double* out);
 
+/* lcq_apply_corrected_S/D/CFIE/Sp by kernel, for a density in either precision:
+ * sigma_dtype 0 = complex128, 1 = complex64 (widened to complex128 on the device before
+ * the FP64 sums).  out is complex128 [NT].  The kernel must match the corrections'. */
+lcq_status lcq_apply_corrected(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                               const lcq_corr* corr, lcq_kernel kernel, const void* sigma,
+                               int sigma_dtype, double jump, double* out);
+
 void lcq_corr_destroy(lcq_corr* corr);
 
 /* Wait for the context's stream (polling, at most timeout_ms; < 0 waits

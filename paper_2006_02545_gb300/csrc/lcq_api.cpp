@@ -1094,6 +1094,24 @@ lcq_status lcq_apply_corrected_CFIE(lcq_ctx* ctx, const lcq_surface* surf, const
   (void)surf;
   return apply_impl(ctx, near, corr, sigma, jump, out, LCQ_CFIE);
 }
+lcq_status lcq_apply_corrected(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                               const lcq_corr* corr, lcq_kernel kernel, const void* sigma,
+                               int sigma_dtype, double jump, double* out) {
+  (void)surf;
+  if (sigma_dtype == 0)
+    return apply_impl(ctx, near, corr, static_cast<const double*>(sigma), jump, out, kernel);
+  if (sigma_dtype != 1 || !ctx || !near || !sigma) return fail(ctx, LCQ_ERR_ARG, "sigma dtype");
+  CK(cudaSetDevice(ctx->device));
+  double* wide;
+  CK(dalloc(ctx->stream, &wide, (size_t)2 * std::max<int64_t>(near->n_points, 1)));
+  long long nl = 0;
+  LaunchCommon lc{ctx->stream, ctx->num_sms, &nl};
+  launch_widen_c64(lc, sigma, near->n_points, wide);
+  const lcq_status s = apply_impl(ctx, near, corr, wide, jump, out, kernel);
+  dfree(ctx->stream, wide);
+  return s;
+}
+
 lcq_status lcq_apply_corrected_Sp(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
                                   const lcq_corr* corr, const double* sigma, double jump,
                                   double* out) {

@@ -815,6 +815,15 @@ __global__ void k_csr_apply(const int64_t* __restrict__ row_ptr, const int32_t* 
   }
 }
 
+// complex64 density -> complex128 (apply of a density stored in single precision)
+__global__ void k_widen_c64(const float2* __restrict__ in, int64_t n, cplx* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = in[i];
+    out[i] = {(double)v.x, (double)v.y};
+  }
+}
+
 // ============================================================================ launchers
 namespace {
 template <template <int> class F, class... Args>
@@ -1041,6 +1050,13 @@ void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const
   ++*lc.launches;
   k_far_sum<<<(unsigned)g, kThreads, 0, lc.stream>>>(tgt, NT, src, n_over, kp, tpatch, src_off,
                                                      tgroup, grp, gsrc, tnrm, (cplx*)out);
+}
+void launch_widen_c64(const LaunchCommon& lc, const void* in, int64_t n, void* out) {
+  if (n <= 0) return;
+  const int64_t b = (n + 255) / 256;
+  ++*lc.launches;
+  k_widen_c64<<<(unsigned)(b < lc.num_sms * 8 ? b : lc.num_sms * 8), 256, 0, lc.stream>>>(
+      (const float2*)in, n, (cplx*)out);
 }
 void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int32_t* col,
                       const double* val, const void* sigma, const int64_t* tnode, int64_t NT,

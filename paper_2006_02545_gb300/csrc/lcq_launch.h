@@ -147,6 +147,7 @@ void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const
                     int64_t n_over, const KernelParams& kp, const int32_t* tpatch,
                     const int64_t* src_off, const int32_t* tgroup, const GroupParams* grp,
                     const int64_t* gsrc, const double* tnrm, void* out);
+void launch_widen_c64(const LaunchCommon& lc, const void* in, int64_t n, void* out);
 void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int32_t* col,
                       const double* val, const void* sigma, const int64_t* tnode, int64_t NT,
                       double jump, void* out);

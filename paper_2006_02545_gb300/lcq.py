@@ -75,6 +75,7 @@ _sig = {
     "lcq_apply_corrected_D": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
     "lcq_apply_corrected_CFIE": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
     "lcq_apply_corrected_Sp": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
+    "lcq_apply_corrected": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, C.c_int, _d, _vp]),
     "lcq_near_set_target_normals": (C.c_int, [_vp, _vp]),
     "lcq_corr_destroy": (None, [_vp]),
     "lcq_apply_adjoint": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
@@ -364,6 +365,17 @@ def shape_gradient(ctx, surf, near, corr, sigma, g):
     out = torch.empty((3, surf.n_points), dtype=torch.float64, device=ctx.torch_device)
     ctx.check(_lib.lcq_shape_gradient(ctx.h, C.byref(surf.s), near.h, corr.h, _ptr(sigma), _ptr(g),
                                       _ptr(out)), "lcq_shape_gradient")
+    return out
+
+
+def apply_corrected(ctx, surf, near, corr, sigma, n_targets, jump=0.0):
+    """The corrected potential for the corrections' kernel; sigma complex128 or complex64."""
+    import torch
+    dt = {torch.complex128: 0, torch.complex64: 1}[sigma.dtype]
+    out = _out_like(ctx, n_targets)
+    ctx.check(_lib.lcq_apply_corrected(ctx.h, C.byref(surf.s), near.h, corr.h,
+                                       KERNELS[corr.kernel], _ptr(sigma), dt, float(jump),
+                                       _ptr(out)), "lcq_apply_corrected")
     return out
 
 

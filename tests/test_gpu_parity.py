@@ -505,3 +505,21 @@ def test_sync_timeout_reports_and_recovers(ctx):
         corr.close()
         near.close()
     assert np.array_equal(vals[0], vals[1])
+
+
+def test_apply_complex64_density(ctx):
+    """lcq_apply_corrected with a complex64 density equals the complex128 apply of the same
+    (widened) values, for every kernel's corrections."""
+    import torch
+    from paper_2006_02545_gb300 import lcq
+    dev = ctx.torch_device
+    s = W.ellipsoid(1, 3)
+    x, tn = W.onsurface_targets(s)
+    sig32 = torch.from_numpy(W.density(s.n_points, 5)).to(torch.complex64).to(dev)
+    sig64 = sig32.to(torch.complex128)
+    for kind in ("S", "D", "CFIE", "Sp"):
+        g = run_gpu(ctx, s, x, tn, kind, 1.7, 1e-7, alpha=1.0, beta=-1.7j)
+        u32 = lcq.apply_corrected(ctx, g["ds"], g["near"], g["corr"], sig32, x.shape[1])
+        u64 = lcq.apply_corrected(ctx, g["ds"], g["near"], g["corr"], sig64, x.shape[1])
+        assert ctx.sync(60000) == 0
+        assert torch.equal(u32, u64), kind
