@@ -7,8 +7,8 @@
 // pairs; the grid only bounds the candidates.  Two orders are produced:
 //   target-major  rowp_patch (patches of row t, ascending), rowp_off, col   -> CSR rows
 //   patch-major   pair_tgt (targets of patch j, ascending), adaptive/annulus split, self
-// Ascending order comes from a rank sort of each short row / patch segment, so the
-// result does not depend on the order of the atomics that fill the buckets.
+// Ascending order comes from sorting each row / patch segment, so the result does not
+// depend on the order of the atomics that fill the buckets.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -316,24 +316,49 @@ __device__ __forceinline__ int flag_scan(int flag, int* sm, int* total) {
   return sm[warp] + __popc(bal & ((1u << lane) - 1u));
 }
 
-constexpr int kSortStage = 4096;  // segment entries staged in shared memory for the rank sort
+constexpr int kSortStage = 1024;  // segments up to this size: rank sort in shared memory
 
-// Sorts src[0, m) (distinct values) ascending into dst by rank; block-wide.
-__device__ void block_rank_sort(const int32_t* __restrict__ src, int m, int32_t* __restrict__ dst,
-                                int32_t* stage) {
-  const int32_t* s = src;
+// Sorts src[0, m) (distinct values) ascending into dst; block-wide.  Short segments: rank
+// of each element (O(m^2), staged in shared memory).  Longer ones: bottom-up merge sort
+// between src (scratch, overwritten) and dst, each element finding its place by a binary
+// search in the partner run (O(m log^2 m)).
+__device__ void block_sort(int32_t* __restrict__ src, int m, int32_t* __restrict__ dst,
+                           int32_t* stage) {
   if (m <= kSortStage) {
     for (int i = threadIdx.x; i < m; i += blockDim.x) stage[i] = src[i];
-    s = stage;
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const int e = stage[i];
+      int r = 0;
+      for (int q = 0; q < m; ++q) r += stage[q] < e;
+      dst[r] = e;
+    }
+    __syncthreads();
+    return;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const int e = s[i];
-    int r = 0;
-    for (int q = 0; q < m; ++q) r += s[q] < e;
-    dst[r] = e;
+  int32_t* in = src;
+  int32_t* out = dst;
+  for (int w = 1; w < m; w <<= 1) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const int run = i / w, left = (run & ~1) * w;
+      const int p0 = min((run ^ 1) * w, m), p1 = min(p0 + w, m);
+      const int e = in[i];
+      int lo = p0, hi = p1;  // first partner element not below e
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (in[mid] < e) lo = mid + 1; else hi = mid;
+      }
+      out[left + (i - run * w) + (lo - p0)] = e;
+    }
+    __syncthreads();
+    int32_t* t = in;
+    in = out;
+    out = t;
   }
-  __syncthreads();
+  if (in != dst) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) dst[i] = in[i];
+    __syncthreads();
+  }
 }
 
 __device__ __forceinline__ int64_t row_entry(const int64_t* rowp_ptr, const int32_t* rowp_patch,
@@ -354,7 +379,7 @@ __global__ void __launch_bounds__(kNT) k_patch_fill(
     const int64_t* __restrict__ an_ptr, const int64_t* __restrict__ self_ptr,
     const int64_t* __restrict__ rowp_ptr, const int32_t* __restrict__ rowp_patch,
     const int64_t* __restrict__ rowp_off, const int64_t* __restrict__ row_ptr,
-    const int32_t* __restrict__ ptmp, const int32_t* __restrict__ stmp,
+    int32_t* __restrict__ ptmp, int32_t* __restrict__ stmp,
     int32_t* __restrict__ pair_tgt, uint8_t* __restrict__ pair_ad, double* __restrict__ pair_d2,
     int64_t* __restrict__ pair_csr, int32_t* __restrict__ ad_pair, int32_t* __restrict__ an_pair,
     int32_t* __restrict__ self_tgt, int64_t* __restrict__ self_csr) {
@@ -363,8 +388,8 @@ __global__ void __launch_bounds__(kNT) k_patch_fill(
   for (int64_t j = blockIdx.x; j < P; j += gridDim.x) {
     const int64_t pb = pair_ptr[j], sb = self_ptr[j];
     const int m = (int)(pair_ptr[j + 1] - pb), ms = (int)(self_ptr[j + 1] - sb);
-    block_rank_sort(ptmp + pb, m, pair_tgt + pb, stage);
-    block_rank_sort(stmp + sb, ms, self_tgt + sb, stage);
+    block_sort(ptmp + pb, m, pair_tgt + pb, stage);
+    block_sort(stmp + sb, ms, self_tgt + sb, stage);
     int64_t abase = ad_ptr[j], nbase = an_ptr[j];
     const double r1 = v.eta1[j] * v.rad[j];
     for (int i0 = 0; i0 < m; i0 += blockDim.x) {

@@ -250,9 +250,10 @@ def test_mixed_precision_error_stated(ctx, eps):
 def test_near_lists_grid_uneven_sizes(ctx):
     """Near lists through the centroid grid on three bodies whose patch radii differ by about
     an order of magnitude, with on-surface nodes, near-surface points and a cloud of
-    off-surface targets partly far outside every ball: the patch-major lists (ascending
-    targets, adaptive flags), the self counts and the CSR size equal the oracle's all-pairs
-    search."""
+    off-surface targets partly far outside every ball, plus a dense blob that gives some
+    patches several thousand near targets (long segments take the merge sort): the
+    patch-major lists (ascending targets, adaptive flags), the self counts and the CSR size
+    equal the oracle's all-pairs search."""
     import torch
     from oracle import geometry as OG
     from oracle import nearlist as ON
@@ -274,7 +275,10 @@ def test_near_lists_grid_uneven_sizes(ctx):
     rng = np.random.default_rng(11)
     cloud = rng.uniform([-3, -3, -3], [9, 7, 5], size=(20000, 3)).T
     far = rng.uniform(-1e3, 1e3, size=(3, 50))
-    x = np.ascontiguousarray(np.concatenate([xs, xr, cloud, far], axis=1))
+    u = rng.standard_normal((3, 6000))
+    u /= np.linalg.norm(u, axis=0)
+    blob = np.array([1.05, 0.0, 0.0])[:, None] + 0.3 * u * rng.uniform(0, 1, 6000) ** (1 / 3)
+    x = np.ascontiguousarray(np.concatenate([xs, xr, cloud, far, blob], axis=1))
     tn = np.concatenate([tns, -np.ones(x.shape[1] - xs.shape[1], np.int64)])
 
     ds = lcq.DeviceSurface(s.deg, s.node_off, torch.from_numpy(s.xyz).to(dev))
@@ -298,6 +302,7 @@ def test_near_lists_grid_uneven_sizes(ctx):
         nnz += (len(ids) + np.count_nonzero(tpatch == j)) * nb[j]
     assert near.n_self == xs.shape[1] and near.nnz == nnz
     assert near.n_pairs > 50000
+    assert max(len(ids) for ids, _, _ in ref) > 4 * 1024
     near.close()
 
 
