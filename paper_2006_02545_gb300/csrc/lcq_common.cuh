@@ -70,7 +70,6 @@ __device__ __forceinline__ double eta_default(int d) {
 template <int D>
 struct Cfg {
   static constexpr int n = (D + 1) * (D + 2) / 2;
-  static constexpr int NP = n <= 32 ? 32 : (n <= 64 ? 64 : 96);
   static constexpr int CH = 128;  // nodes per chunk (two blocks per SM fit in shared memory)
   static constexpr int BS = n + 1;
   static constexpr int TT = 16;
@@ -116,6 +115,9 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
   float* Nf = Bf + C::CH * C::BS;
   float* Jf = Nf + 3 * C::CH;
   float2* Gf = reinterpret_cast<float2*>(G);
+  float* Evf = reinterpret_cast<float*>(Ev);
+  static_assert(C::n < C::BS, "the basis rows need a spare column");
+  (void)ostride;
   const KernelParamsF kf = to_f32(kp);
   const float fR = (float)R;
   const int total = nseg * Q;
@@ -132,6 +134,7 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
       const double w = rw[l] * S.det;
       double X[3], Xu[3], Xv[3], Nn[3];
       kw_geometry_proj<D>(u, v, cf, cfd, X, Xu, Xv, B + ql * C::BS);
+      B[ql * C::BS + C::n] = 1.0;  // the envelope's column
       cross3(Xu, Xv, Nn);
       const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
 #pragma unroll
@@ -144,7 +147,7 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
 #pragma unroll
         for (int c = 0; c < 3; ++c) Nf[c * C::CH + ql] = (float)(Nn[c] * w);
         Jf[ql] = (float)(J * w);
-        for (int nm = 0; nm < C::n; ++nm) Bf[ql * C::BS + nm] = (float)B[ql * C::BS + nm];
+        for (int nm = 0; nm <= C::n; ++nm) Bf[ql * C::BS + nm] = (float)B[ql * C::BS + nm];
       }
     }
     __syncthreads();
@@ -159,75 +162,78 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
         if (kp.kind == 3) ta.nrm(t0 + threadIdx.x, xp, tn + 3 * threadIdx.x);
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < nt * C::CH; e += blockDim.x) {
-        const int i = e / C::CH, ql = e - i * C::CH;
+      for (int e = threadIdx.x; e < nt * nch; e += blockDim.x) {
+        const int i = e / nch, ql = e - i * nch;
         if (mixed) {
           float2 g = make_float2(0.0f, 0.0f);
           float ev = 0.0f;
-          if (ql < nch) {
-            const double d0 = tx[3 * i] - Xs[ql], d1 = tx[3 * i + 1] - Xs[C::CH + ql],
-                         d2 = tx[3 * i + 2] - Xs[2 * C::CH + ql];
-            const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-            if (r2 > 0.0)
-              g = kernel_eval_f32f(kp, kf, d0, d1, d2, r2, Nf[ql], Nf[C::CH + ql],
-                                   Nf[2 * C::CH + ql], Jf[ql], fR, ENV ? &ev : nullptr);
-          }
+          const double d0 = tx[3 * i] - Xs[ql], d1 = tx[3 * i + 1] - Xs[C::CH + ql],
+                       d2 = tx[3 * i + 2] - Xs[2 * C::CH + ql];
+          const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+          if (r2 > 0.0)
+            g = kernel_eval_f32f(kp, kf, d0, d1, d2, r2, Nf[ql], Nf[C::CH + ql],
+                                 Nf[2 * C::CH + ql], Jf[ql], fR, ENV ? &ev : nullptr);
           Gf[i * C::CH + ql] = g;
-          if (ENV) Ev[i * C::CH + ql] = (double)ev * (kF32Floor / kRoundingFloor);
+          if (ENV) Evf[i * C::CH + ql] = ev;
         } else {
-          cplx g = {0.0, 0.0};
           double ev = 0.0;
-          if (ql < nch)
-            g = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql], Xs[C::CH + ql],
-                            Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql], Ns[2 * C::CH + ql],
-                            Js[ql], R, ENV ? &ev : nullptr, tn + 3 * i);
+          const cplx g = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql],
+                                     Xs[C::CH + ql], Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql],
+                                     Ns[2 * C::CH + ql], Js[ql], R, ENV ? &ev : nullptr,
+                                     tn + 3 * i);
           G[i * C::CH + ql] = g;
           if (ENV) Ev[i * C::CH + ql] = ev;
         }
       }
       __syncthreads();
-      const int nout = nt * nseg * C::NP;
+      // one thread per (target, nm), outputs packed densely; with ENV the extra index nm = n
+      // sums the envelope through the basis rows' column of ones.  Node ranges are uniform
+      // across the block, so the loops do not diverge.
+      constexpr int W = C::n + (ENV ? 1 : 0);
+      const int nout = nt * W;
       for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-        const int nm = o % C::NP;
-        const int rest = o / C::NP;
-        const int sg = rest % nseg, i = rest / nseg;
-        if (nm >= C::n) continue;
-        const int qa = max(sg * Q - c0, 0), qb = min((sg + 1) * Q - c0, nch);
-        double are = 0.0, aim = 0.0;
-        if (mixed) {
-          float fre = 0.0f, fim = 0.0f;
-          const float2* Gi = Gf + i * C::CH;
-          for (int ql = qa; ql < qb; ++ql) {
-            const float2 g = Gi[ql];
-            const float bv = Bf[ql * C::BS + nm];
-            fre = fmaf(g.x, bv, fre);
-            fim = fmaf(g.y, bv, fim);
+        const int i = o / W, nm = o - i * W;
+        const bool env = ENV && nm == C::n;
+        for (int sg = 0; sg < nseg; ++sg) {
+          const int qa = max(sg * Q - c0, 0), qb = min((sg + 1) * Q - c0, nch);
+          if (qa >= qb) continue;
+          const bool first = sg * Q >= c0;  // the segment starts in this chunk
+          double are = 0.0, aim = 0.0;
+          if (mixed) {
+            const float* pr = env ? Evf + i * C::CH : &Gf[i * C::CH].x;
+            const int st = env ? 1 : 2;
+            const float* pi = env ? pr : pr + 1;
+            float fre = 0.0f, fim = 0.0f;
+            for (int ql = qa; ql < qb; ++ql) {
+              const float bv = Bf[ql * C::BS + nm];
+              fre = fmaf(pr[ql * st], bv, fre);
+              fim = fmaf(pi[ql * st], bv, fim);
+            }
+            are = env ? (double)fre * (kF32Floor / kRoundingFloor) : (double)fre;
+            aim = fim;
+          } else {
+            const double* pr = env ? Ev + i * C::CH : &G[i * C::CH].re;
+            const int st = env ? 1 : 2;
+            const double* pi = env ? pr : pr + 1;
+            for (int ql = qa; ql < qb; ++ql) {
+              const double bv = B[ql * C::BS + nm];
+              are = fma(pr[ql * st], bv, are);
+              aim = fma(pi[ql * st], bv, aim);
+            }
           }
-          are = fre;
-          aim = fim;
-        } else {
-          const cplx* Gi = G + i * C::CH;
-          for (int ql = qa; ql < qb; ++ql) {
-            const cplx g = Gi[ql];
-            const double bv = B[ql * C::BS + nm];
-            are = fma(g.re, bv, are);
-            aim = fma(g.im, bv, aim);
+          if (env) {
+            double* ed = eout + (int64_t)(t0 + i) * nseg + sg;
+            *ed = first ? are : *ed + are;
+          } else {
+            cplx* dst = reinterpret_cast<cplx*>(orow(t0 + i)) + (int64_t)sg * C::n + nm;
+            if (first) {
+              dst->re = are;
+              dst->im = aim;
+            } else {
+              dst->re += are;
+              dst->im += aim;
+            }
           }
-        }
-        cplx* dst = reinterpret_cast<cplx*>(orow(t0 + i)) + (int64_t)sg * C::n + nm;
-        (void)ostride;
-        if (c0 == 0) {
-          dst->re = are;
-          dst->im = aim;
-        } else {
-          dst->re += are;
-          dst->im += aim;
-        }
-        if (ENV && nm == 0) {
-          double es = 0.0;
-          for (int ql = qa; ql < qb; ++ql) es += Ev[i * C::CH + ql];
-          double* ed = eout + (int64_t)(t0 + i) * nseg + sg;
-          *ed = (c0 == 0) ? es : *ed + es;
         }
       }
       __syncthreads();
