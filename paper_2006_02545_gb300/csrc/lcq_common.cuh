@@ -558,22 +558,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
       const int L = (int)(top & 0xff);
       const int cidx = (int)((top >> 8) & 3);
       const unsigned long long path = top >> 16;  // child digits of T, level 1 at bits 0-1
-      // vertices of T
-      double ax = 0, ay = 0, bx = 1, by = 0, cx = 0, cy = 1;
-      for (int l = 0; l < L; ++l) {
-        const int dgt = (int)((path >> (2 * l)) & 3);
-        const double abx = 0.5 * (ax + bx), aby = 0.5 * (ay + by);
-        const double bcx = 0.5 * (bx + cx), bcy = 0.5 * (by + cy);
-        const double cax = 0.5 * (cx + ax), cay = 0.5 * (cy + ay);
-        if (dgt == 0) { bx = abx; by = aby; cx = cax; cy = cay; }
-        else if (dgt == 1) { ax = abx; ay = aby; cx = bcx; cy = bcy; }
-        else if (dgt == 2) { ax = cax; ay = cay; bx = bcx; by = bcy; }
-        else { ax = bcx; ay = bcy; bx = cax; by = cay; cx = abx; cy = aby; }
-      }
       const int S = cnt[L];
       const int* ST = lvlT + (int64_t)L * A_max;
       const cplx* IT = lvlI + (int64_t)L * A_max * 4 * n;
       if (threadIdx.x == 0) {
+        // vertices of T from its path, then the maps of its four children
+        double ax = 0, ay = 0, bx = 1, by = 0, cx = 0, cy = 1;
+        for (int l = 0; l < L; ++l) {
+          const int dgt = (int)((path >> (2 * l)) & 3);
+          const double abx = 0.5 * (ax + bx), aby = 0.5 * (ay + by);
+          const double bcx = 0.5 * (bx + cx), bcy = 0.5 * (by + cy);
+          const double cax = 0.5 * (cx + ax), cay = 0.5 * (cy + ay);
+          if (dgt == 0) { bx = abx; by = aby; cx = cax; cy = cay; }
+          else if (dgt == 1) { ax = abx; ay = aby; cx = bcx; cy = bcy; }
+          else if (dgt == 2) { ax = cax; ay = cay; bx = bcx; by = bcy; }
+          else { ax = bcx; ay = bcy; bx = cax; by = cay; cx = abx; cy = aby; }
+        }
         const double abx = 0.5 * (ax + bx), aby = 0.5 * (ay + by);
         const double bcx = 0.5 * (bx + cx), bcy = 0.5 * (by + cy);
         const double cax = 0.5 * (cx + ax), cay = 0.5 * (cy + ay);
@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
       const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
       const double tauL = tol0 * ldexp(1.0, -2 * L);
       for (int s = w; s < S; s += nw) {
-        double e2 = 0.0, s2 = 0.0;
+        double e2 = 0.0;
         for (int nm = lane; nm < n; nm += 32) {
           const cplx* tc = tmp + (int64_t)s * 4 * n + nm;
           const double sr = tc[0].re + tc[n].re + tc[2 * n].re + tc[3 * n].re;
@@ -615,7 +615,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
           const cplx it = IT[(int64_t)s * 4 * n + (int64_t)cidx * n + nm];
           const double dr = it.re - sr, di = it.im - si;
           e2 += dr * dr + di * di;
-          s2 += sr * sr + si * si;
         }
         e2 = warp_sum(e2);
         const double err = sqrt(e2);

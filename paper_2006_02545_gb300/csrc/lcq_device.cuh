@@ -310,35 +310,29 @@ __device__ __forceinline__ cplx kernel_eval(const KernelParams& kp, double x0, d
     return {0.0, 0.0};
   }
   const double rinv = rsqrt(r2);
-  const double r = r2 * rinv;
+  const double r = r2 * rinv, rinv2 = rinv * rinv;
+  const double th = kp.kr * r;
   double sn, cs;
-  sincos(kp.kr * r, &sn, &cs);
+  sincos(th, &sn, &cs);
   double ex = 0.07957747154594767 * rinv;  // 1/(4 pi r)
   if (kp.ki != 0.0) ex *= exp(-kp.ki * r);
-  const cplx G = {ex * cs, ex * sn};
   if (env) {
     // |G| Jw (|beta| + |alpha| |1 - ik r| R / r^2); |1 - ik r| only scales a floor, FP32 is ample
-    const float f0 = (float)(1.0 + kp.ki * r), f1 = (float)(kp.kr * r);
+    const float f0 = (float)(1.0 + kp.ki * r), f1 = (float)th;
     const double fa = (double)sqrtf(f0 * f0 + f1 * f1);
-    *env = ex * Jw * (kp.eb + kp.ea * fa * R * rinv * rinv);
+    *env = ex * Jw * (kp.eb + kp.ea * fa * R * rinv2);
   }
-  cplx out = {0.0, 0.0};
-  if (kp.kind == 0 || kp.kind == 2) {  // S part
-    const cplx s = {G.re * Jw, G.im * Jw};
-    if (kp.kind == 0) return s;
-    out = cmul({kp.br, kp.bi}, s);
+  if (kp.kind == 0) return {ex * cs * Jw, ex * sn * Jw};  // G Jw
+  // e^{ikr}/(4 pi r) times c: the double-layer factor (1 - ikr) (N.d)/r^2, with
+  // k = kr + i ki so 1 - ikr = (1 + ki r) - i kr r; for the CFIE c = alpha c + beta Jw
+  const double ndx = (N0 * d0 + N1 * d1 + N2 * d2) * rinv2;
+  cplx c = {(1.0 + kp.ki * r) * ndx, -th * ndx};
+  if (kp.kind == 2) {
+    c = cmul({kp.ar, kp.ai}, c);
+    c.re = fma(kp.br, Jw, c.re);
+    c.im = fma(kp.bi, Jw, c.im);
   }
-  const double ndx = (N0 * d0 + N1 * d1 + N2 * d2) * rinv * rinv;
-  // (1 - i k r) with k = kr + i ki: (1 + ki r) - i kr r
-  const cplx f = {1.0 + kp.ki * r, -kp.kr * r};
-  cplx dd = cmul(G, f);
-  dd.re *= ndx;
-  dd.im *= ndx;
-  if (kp.kind != 2) return dd;
-  const cplx ad = cmul({kp.ar, kp.ai}, dd);
-  out.re += ad.re;
-  out.im += ad.im;
-  return out;
+  return {ex * (cs * c.re - sn * c.im), ex * (cs * c.im + sn * c.re)};
 }
 
 // Kernel parameters converted to FP32 once per patch (the mixed form's pair evaluations).
