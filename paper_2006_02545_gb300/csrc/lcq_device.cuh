@@ -122,8 +122,9 @@ __device__ __forceinline__ void kw_geometry(double u, double v, const double* __
 // cfd = (X_u coefficients [nd][3], X_v coefficients [nd][3]) in the degree D-1 basis
 // (nd its size: the first nd basis functions, those with n < D).  Only the values
 // recurrence runs; K (stride 1, written first and read back) receives the basis values.
-// Same polynomials as kw_geometry at about half its cost.
-template <int D>
+// Same polynomials as kw_geometry at about half its cost.  WITH_X = false: X is not
+// formed (nor written).
+template <int D, bool WITH_X = true>
 __device__ __forceinline__ void kw_geometry_proj(double u, double v, const double* cf,
                                                  const double* cfd, double* X, double* Xu,
                                                  double* Xv, double* K) {
@@ -135,9 +136,11 @@ __device__ __forceinline__ void kw_geometry_proj(double u, double v, const doubl
 #pragma unroll 1
   for (int idx = 0; idx < nd; ++idx) {
     const double k = K[idx];
-    x0 = fma(cf[idx * 3], k, x0);
-    x1 = fma(cf[idx * 3 + 1], k, x1);
-    x2 = fma(cf[idx * 3 + 2], k, x2);
+    if (WITH_X) {
+      x0 = fma(cf[idx * 3], k, x0);
+      x1 = fma(cf[idx * 3 + 1], k, x1);
+      x2 = fma(cf[idx * 3 + 2], k, x2);
+    }
     u0 = fma(cfd[idx * 3], k, u0);
     u1 = fma(cfd[idx * 3 + 1], k, u1);
     u2 = fma(cfd[idx * 3 + 2], k, u2);
@@ -145,16 +148,18 @@ __device__ __forceinline__ void kw_geometry_proj(double u, double v, const doubl
     v1 = fma(cfd[(nd + idx) * 3 + 1], k, v1);
     v2 = fma(cfd[(nd + idx) * 3 + 2], k, v2);
   }
+  if (WITH_X) {
 #pragma unroll 1
-  for (int idx = nd; idx < n; ++idx) {
-    const double k = K[idx];
-    x0 = fma(cf[idx * 3], k, x0);
-    x1 = fma(cf[idx * 3 + 1], k, x1);
-    x2 = fma(cf[idx * 3 + 2], k, x2);
+    for (int idx = nd; idx < n; ++idx) {
+      const double k = K[idx];
+      x0 = fma(cf[idx * 3], k, x0);
+      x1 = fma(cf[idx * 3 + 1], k, x1);
+      x2 = fma(cf[idx * 3 + 2], k, x2);
+    }
+    X[0] = x0;
+    X[1] = x1;
+    X[2] = x2;
   }
-  X[0] = x0;
-  X[1] = x1;
-  X[2] = x2;
   Xu[0] = u0;
   Xu[1] = u1;
   Xu[2] = u2;
@@ -178,65 +183,125 @@ __device__ __forceinline__ void load_coef_derivs(const double* cf, const double*
   }
 }
 
-// Self-rule geometry at Q = P + delta: the chord dX = X(Q) - X(P), formed from Koornwinder
-// differences K_nm(Q) - K_nm(P) that obey the same recurrences as the values (so dX keeps
-// its relative precision as delta -> 0); X_u, X_v at Q from the derivative series cfd (as
-// in kw_geometry_proj); KQ receives K_nm(Q).
+// Index helpers for bivariate power series in (du, dv) truncated at degree D: entry
+// g(g+1)/2 + j holds the coefficient of du^(g-j) dv^j (the ordering of the basis).
+__device__ __forceinline__ void tri_split(int e, int& g, int& j) {
+  g = 0;
+  while ((g + 1) * (g + 2) / 2 <= e) ++g;
+  j = e - g * (g + 1) / 2;
+}
+
+// Taylor coefficients of the chord dX(d) = X(P + d) - X(P), d = (du, dv), of the chart
+// X = sum_nm cf_nm K_nm of degree D, about the node P = (pu, pv): the Koornwinder
+// recurrences of kw_values run on power series in (du, dv) truncated at degree D, which
+// is exact for these polynomials, and their coefficients stay those of the derivatives
+// at P (no expansion about another point, so no cancellation).  tX[c * n + e] receives
+// the coefficient of entry e of component c, tX[c * n] = 0.  Block-wide, with
+// __syncthreads; scratch holds (D + 1) n + 2 n^2 doubles.
 template <int D>
-__device__ __forceinline__ void kw_delta_geometry_proj(double pu, double pv, double du, double dv,
-                                                       const double* __restrict__ cf,
-                                                       const double* __restrict__ cfd, double* dX,
-                                                       double* Xu, double* Xv, double* KQ) {
-  constexpr int nd = D * (D + 1) / 2;
-  const double uq = pu + du, vq = pv + dv;
-  const double sP = 2.0 * pu + pv - 1.0, qP = 1.0 - pv, yP = 1.0 - 2.0 * pv;
-  const double sQ = 2.0 * uq + vq - 1.0, qQ = 1.0 - vq, yQ = 1.0 - 2.0 * vq;
-  const double ds = 2.0 * du + dv, dq2 = -dv * (qQ + qP), dy = -2.0 * dv;
-  const double qQ2 = qQ * qQ, qP2 = qP * qP;
-  double LPp = 0.0, LP = 1.0, LQp = 0.0, LQ = 1.0, dLp = 0.0, dL = 0.0;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) dX[c] = Xu[c] = Xv[c] = 0.0;
-#pragma unroll
-  for (int m = 0; m <= D; ++m) {
-    if (m > 0) {
-      const double f1 = 2.0 * m - 1.0, f2 = m - 1.0, im = 1.0 / m;
-      const double nLP = (f1 * sP * LP - f2 * qP2 * LPp) * im;
-      const double nLQ = (f1 * sQ * LQ - f2 * qQ2 * LQp) * im;
-      const double ndL = (f1 * (sQ * dL + ds * LP) - f2 * (qQ2 * dLp + dq2 * LPp)) * im;
-      LPp = LP; LP = nLP;
-      LQp = LQ; LQ = nLQ;
-      dLp = dL; dL = ndL;
-    }
-    const int b = 2 * m + 1;
-    double PPp = 0.0, PP = 1.0, PQp = 0.0, PQ = 1.0, dPp = 0.0, dP = 0.0;
-#pragma unroll
-    for (int a = 0; a <= D - m; ++a) {
-      const int n = m + a, idx = n * (n + 1) / 2 + m;
-      const double cn = c_kw[idx];
-      const double dk = cn * (dL * PQ + LP * dP);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) dX[c] = fma(cf[idx * 3 + c], dk, dX[c]);
-      const double kq = cn * LQ * PQ;
-      KQ[idx] = kq;
-      if (n < D) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          Xu[c] = fma(cfd[idx * 3 + c], kq, Xu[c]);
-          Xv[c] = fma(cfd[(nd + idx) * 3 + c], kq, Xv[c]);
+__device__ void chart_taylor(double pu, double pv, const double* cf, double* scratch,
+                             double* tX) {
+  constexpr int n = (D + 1) * (D + 2) / 2;
+  double* Ls = scratch;          // [D + 1][n]: (1 - v)^m P_m((2u + v - 1) / (1 - v))
+  double* Ps = Ls + (D + 1) * n;  // [n][n]: the Jacobi factor of basis index nm
+  double* Ks = Ps + n * n;        // [n][n]: K_nm
+  const double s0 = 2.0 * pu + pv - 1.0, q0 = 1.0 - pv, y0 = 1.0 - 2.0 * pv;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int e = lane; e < n; e += 32) Ls[e] = e == 0 ? 1.0 : 0.0;
+    __syncwarp();
+    // s = s0 + 2 du + dv, (1 - v)^2 = q0^2 - 2 q0 dv + dv^2, y = 1 - 2v = y0 - 2 dv
+    for (int m = 1; m <= D; ++m) {
+      const double* L1 = Ls + (m - 1) * n;
+      const double* L2 = Ls + (m >= 2 ? m - 2 : 0) * n;
+      for (int e = lane; e < n; e += 32) {
+        int g, j;
+        tri_split(e, g, j);
+        double sL = s0 * L1[e];
+        if (g - j >= 1) sL += 2.0 * L1[e - g];
+        if (j >= 1) sL += L1[e - g - 1];
+        double qL = 0.0;
+        if (m >= 2) {
+          qL = q0 * q0 * L2[e];
+          if (j >= 1) qL -= 2.0 * q0 * L2[e - g - 1];
+          if (j >= 2) qL += L2[e - 2 * g - 1];
         }
+        Ls[m * n + e] = ((2.0 * m - 1.0) * sL - (m - 1.0) * qL) * (1.0 / m);
       }
-      if (a < D - m) {
+      __syncwarp();
+    }
+#pragma unroll
+    for (int m = 0; m <= D; ++m) {
+      const int b = 2 * m + 1;
+      double* P0 = Ps + (m * (m + 1) / 2 + m) * n;
+      for (int e = lane; e < n; e += 32) P0[e] = e == 0 ? 1.0 : 0.0;
+      __syncwarp();
+#pragma unroll
+      for (int a = 0; a < D - m; ++a) {
         double c1, c0, c2;
         jacobi_coef(a, b, &c1, &c0, &c2);
-        const double tQ = c1 * yQ + c0;
-        const double nPP = (c1 * yP + c0) * PP - c2 * PPp;
-        const double nPQ = tQ * PQ - c2 * PQp;
-        const double ndP = tQ * dP + c1 * dy * PP - c2 * dPp;
-        PPp = PP; PP = nPP;
-        PQp = PQ; PQ = nPQ;
-        dPp = dP; dP = ndP;
+        const double* Pa = Ps + ((m + a) * (m + a + 1) / 2 + m) * n;
+        const double* Pb = a > 0 ? Ps + ((m + a - 1) * (m + a) / 2 + m) * n : Pa;
+        double* Pn = Ps + ((m + a + 1) * (m + a + 2) / 2 + m) * n;
+        for (int e = lane; e < n; e += 32) {
+          int g, j;
+          tri_split(e, g, j);
+          double v = (c1 * y0 + c0) * Pa[e];
+          if (j >= 1) v -= 2.0 * c1 * Pa[e - g - 1];
+          if (a > 0) v -= c2 * Pb[e];
+          Pn[e] = v;
+        }
+        __syncwarp();
       }
     }
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < n * n; o += blockDim.x) {
+    const int idx = o / n, e = o - idx * n;
+    int nn, m, g, j;
+    tri_split(idx, nn, m);
+    tri_split(e, g, j);
+    const int i = g - j;
+    const double* L = Ls + m * n;
+    const double* P = Ps + idx * n;
+    double acc = 0.0;
+    for (int ja = 0; ja <= j; ++ja)
+      for (int ia = 0; ia <= i; ++ia) {
+        const int ga = ia + ja, gb = g - ga, jb = j - ja;
+        acc = fma(L[ga * (ga + 1) / 2 + ja], P[gb * (gb + 1) / 2 + jb], acc);
+      }
+    Ks[o] = c_kw[idx] * acc;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < 3 * n; o += blockDim.x) {
+    const int c = o / n, e = o - c * n;
+    double acc = 0.0;
+    if (e > 0)
+      for (int idx = 0; idx < n; ++idx) acc = fma(cf[idx * 3 + c], Ks[idx * n + e], acc);
+    tX[o] = acc;
+  }
+  __syncthreads();
+}
+
+// The chord dX(d) from the coefficients of chart_taylor: Horner in du inside Horner in dv.
+template <int D>
+__device__ __forceinline__ void chart_chord(const double* tX, double du, double dv, double* dX) {
+  constexpr int n = (D + 1) * (D + 2) / 2;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double* t = tX + c * n;
+    double acc = 0.0;
+#pragma unroll
+    for (int j = D; j >= 0; --j) {
+      double in = 0.0;
+#pragma unroll
+      for (int i = D - j; i >= 0; --i) {
+        const int g = i + j;
+        in = fma(in, du, t[g * (g + 1) / 2 + j]);
+      }
+      acc = fma(acc, dv, in);
+    }
+    dX[c] = acc;
   }
 }
 

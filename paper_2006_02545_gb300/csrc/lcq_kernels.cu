@@ -425,6 +425,7 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
   __shared__ double nP[3];  // unit chart normal at the target node (S')
   __shared__ double cfd[2 * 3 * (D * (D + 1) / 2)];  // derivative series of the chart
   __shared__ cplx gbuf[128];                          // kernel values of a chunk's nodes
+  __shared__ double tX[3 * n];                        // Taylor coefficients of the chord at P
   extern __shared__ double krows[];                   // [128][n + 1] basis rows of a chunk
   long long my_nodes = 0;
   for (int64_t s = blockIdx.x; s < dv.n_self; s += gridDim.x) {
@@ -505,6 +506,7 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
       total = off;
     }
     __syncthreads();
+    chart_taylor<D>(P[0], P[1], cf, krows, tX);  // krows is free until the first chunk
     // the target is the chart's value at the node: x - X(P + delta) = -(dX)
     // chunks of 128 nodes: each thread forms one node's kernel value and basis row in
     // shared memory, then the block contracts them, thread (nm, quarter of the chunk)
@@ -536,7 +538,8 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
         const double du = Mm[0] * zx + Mm[1] * zy;
         const double dvv = Mm[2] * zx + Mm[3] * zy;
         double dX[3], Xu[3], Xv[3], Nn[3];
-        kw_delta_geometry_proj<D>(P[0], P[1], du, dvv, cf, cfd, dX, Xu, Xv, Kq);
+        kw_geometry_proj<D, false>(P[0] + du, P[1] + dvv, cf, cfd, nullptr, Xu, Xv, Kq);
+        chart_chord<D>(tX, du, dvv, dX);
         cross3(Xu, Xv, Nn);
         const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
         gk = kernel_eval(kps, 0.0, 0.0, 0.0, dX[0], dX[1], dX[2], Nn[0] * w, Nn[1] * w,
@@ -921,7 +924,9 @@ struct SelfL {
     const int64_t g = dv.n_self < (int64_t)lc.num_sms * 16 ? dv.n_self : (int64_t)lc.num_sms * 16;
     if (g <= 0) return;
     ++*lc.launches;
-    const size_t sm = (size_t)128 * ((D + 1) * (D + 2) / 2 + 1) * sizeof(double);
+    constexpr size_t n = (D + 1) * (D + 2) / 2;
+    constexpr size_t rows = 128 * (n + 1), taylor = (D + 1) * n + 2 * n * n;
+    const size_t sm = (rows > taylor ? rows : taylor) * sizeof(double);
     set_smem(k_self<D>, sm);
     k_self<D><<<(int)g, 128, sm, lc.stream>>>(dv, deg, kp, order, (cplx*)out);
   }
