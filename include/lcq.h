@@ -274,10 +274,12 @@ lcq_status lcq_sync(lcq_ctx* ctx, int64_t timeout_ms);
 lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out8);
 
 /* Stage timings of the last lcq_build_near_lists and lcq_gen_corrections on ctx, from
- * CUDA events recorded on the context's stream (host out, milliseconds):
+ * CUDA events recorded on the streams that run them (host out, milliseconds):
  *   ms[0] near lists (geometry + both orientations)   ms[1] far order q_j
  *   ms[2] smooth-rule and annulus moments              ms[3] adaptive near moments
- *   ms[4] self weights (on an internal side stream, concurrently with ms[1]-ms[3])
+ *   ms[4] self weights (on an internal low-priority stream, concurrently with ms[1]-ms[3];
+ *         the chain ms[1]-ms[3], ms[5] runs on an internal high-priority stream, forked
+ *         from and joined back into the context's stream)
  *   ms[5] V contraction into the CSR
  * *launches receives the number of kernels those two calls launched.  Synchronizes. */
 lcq_status lcq_stage_times(lcq_ctx* ctx, float* ms6, int64_t* launches);

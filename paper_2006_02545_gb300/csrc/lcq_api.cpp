@@ -213,9 +213,13 @@ lcq_status lcq_create(lcq_ctx** out, int device, void* cuda_stream) {
   CK(upload_constants(ctx->stream));
   CK(upload_constants_adjoint(ctx->stream));
   for (int i = 0; i < 8; ++i) CK(cudaEventCreate(&ctx->ev[i]));
-  CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+  int prio_least = 0, prio_greatest = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+  CK(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_least));
+  CK(cudaStreamCreateWithPriority(&ctx->hi, cudaStreamNonBlocking, prio_greatest));
   CK(cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming));
   for (int i = 0; i < 2; ++i) CK(cudaEventCreate(&ctx->ev_self[i]));
   lcq_status s = ensure_rules(ctx);
   if (s != LCQ_OK) {
@@ -247,12 +251,14 @@ void lcq_destroy(lcq_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (int i = 0; i < 8; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
-  if (ctx->side) {
-    cudaStreamSynchronize(ctx->side);
-    cudaStreamDestroy(ctx->side);
-  }
+  for (cudaStream_t* sp : {&ctx->side, &ctx->hi})
+    if (*sp) {
+      cudaStreamSynchronize(*sp);
+      cudaStreamDestroy(*sp);
+    }
   if (ctx->fork) cudaEventDestroy(ctx->fork);
   if (ctx->join) cudaEventDestroy(ctx->join);
+  if (ctx->done) cudaEventDestroy(ctx->done);
   for (int i = 0; i < 2; ++i)
     if (ctx->ev_self[i]) cudaEventDestroy(ctx->ev_self[i]);
   cudaFree(ctx->d_status);
@@ -294,7 +300,7 @@ lcq_status lcq_stage_times(lcq_ctx* ctx, float* ms6, int64_t* launches) {
   if (ms6) {
     CK(cudaEventElapsedTime(&ms6[0], ctx->ev[0], ctx->ev[1]));
     for (int i = 0; i < 5; ++i) CK(cudaEventElapsedTime(&ms6[1 + i], ctx->ev[2 + i], ctx->ev[3 + i]));
-    // the self weights run on the side stream, concurrently with stages 1-3
+    // the self weights run on the low-priority stream, concurrently with stages 1-3
     CK(cudaEventElapsedTime(&ms6[4], ctx->ev_self[0], ctx->ev_self[1]));
   }
   if (launches) *launches = ctx->launches_near + ctx->launches_corr;
@@ -876,56 +882,37 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   }
   Dev dv = make_dev(ctx, nr, c->q, ldI, c->grp);
 
-  CK(cudaEventRecord(ctx->ev[2], st));
   // the mixed form (FP32 pair evaluation in the smooth, annulus and adaptive moments);
   // per surface of a batch the kernels also check the surface's tolerance
   const bool mixed_form = precision == LCQ_MIXED && kernel != LCQ_SP &&
                           (nr->grouped || eps0 >= kMixedMinEps);
   c->mixed_form = mixed_form;
-  // 1. far order q_j and annulus order (Sec. 4.2, Eq. qj)
   const int fgrid = ctx->num_sms * 2;
   double* fscr;
   CK(dalloc(st, &fscr, (size_t)fgrid * 2 * kMaxTestPts * kMaxBasis * 2));
+  const int levels = params->max_depth;
+  int64_t astride = 0;
+  int agrid = 0;
+  if (nr->n_adaptive > 0) CK(adaptive_work(ctx, nr, levels, &astride, &agrid));
+  // Stages 1-4 and 6 depend on one another and run on the highest-priority stream; the
+  // self weights (5) depend on none of them and run on the lowest-priority one from the
+  // start, so their blocks fill what the chain leaves idle (the small far-order and
+  // smooth-rule launches, the end of the adaptive walk) without delaying it.
+  CK(cudaEventRecord(ctx->fork, st));
+  CK(cudaStreamWaitEvent(ctx->hi, ctx->fork, 0));
+  CK(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
+  LaunchCommon lh{ctx->hi, ctx->num_sms, &ctx->launches_corr};
+  cudaStream_t sh = ctx->hi;
+  CK(cudaEventRecord(ctx->ev[2], sh));
+  // 1. far order q_j and annulus order (Sec. 4.2, Eq. qj)
   for (int d = 1; d <= kMaxDeg; ++d) {
     if (!nr->plist_count[d]) continue;
-    launch_farorder(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, kp, eps0, params->m_max,
+    launch_farorder(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, kp, eps0, params->m_max,
                     ctx->deg[d].normV, ddirs, ndirs, fscr, fgrid, c->q, c->q_near);
   }
   CK(cudaGetLastError());
-  CK(cudaEventRecord(ctx->ev[3], st));
-  // 2. smooth-rule moments of every near and self pair; 3. annulus moments
-  for (int d = 1; d <= kMaxDeg; ++d) {
-    if (!nr->plist_count[d]) continue;
-    launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 0, c->q, kp, Is, IsS,
-                        mixed_form);
-    launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 1, c->q_near, kp, In,
-                        nullptr, mixed_form);
-  }
-  CK(cudaGetLastError());
-  CK(cudaEventRecord(ctx->ev[4], st));
-  CK(cudaEventRecord(ctx->fork, st));
-  // 4. adaptive near moments (Sec. 4.3)
-  if (nr->n_adaptive > 0) {
-    const int levels = params->max_depth;
-    const int64_t A = nr->max_adaptive;
-    int64_t stride;
-    int agrid;
-    CK(adaptive_work(ctx, nr, levels, &stride, &agrid));
-    for (int d = 1; d <= kMaxDeg; ++d) {
-      if (!nr->ad_count[d]) continue;
-      launch_adaptive(d, lc, nr->ad_list_dev[d], nr->ad_count[d], dv, kp,
-                      eps0 * params->eps_loosen, ctx->deg[d].normV, params->leaf_order,
-                      params->max_depth, Is, In, c->leaves, ctx->work, stride, (int)A, levels, agrid,
-                      ctx->d_status, ctx->d_sched + d,
-                      mixed_form ? 2.0 : 0.0);
-    }
-    CK(cudaGetLastError());
-  }
-  // 5. self weights (Sec. 4, Eq. errestself), on the side stream: released together with
-  // the adaptive kernel but queued after it, so that their blocks take the SMs the
-  // persistent adaptive blocks release at the end of their work instead of delaying them
+  // 5. self weights (Sec. 4, Eq. errestself), on the side stream
   const int sorder = params->self_order > 0 ? params->self_order : default_self_order(eps0);
-  CK(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
   CK(cudaEventRecord(ctx->ev_self[0], ctx->side));
   if (nr->n_self > 0) {
     LaunchCommon ls{ctx->side, ctx->num_sms, &ctx->launches_corr};
@@ -937,16 +924,41 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev_self[1], ctx->side));
   CK(cudaEventRecord(ctx->join, ctx->side));
-  CK(cudaEventRecord(ctx->ev[5], st));
-  CK(cudaStreamWaitEvent(st, ctx->join, 0));  // self weights done
-  CK(cudaEventRecord(ctx->ev[6], st));
+  CK(cudaEventRecord(ctx->ev[3], sh));
+  // 2. smooth-rule moments of every near and self pair; 3. annulus moments
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_rule_moments(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, 0, c->q, kp, Is, IsS,
+                        mixed_form);
+    launch_rule_moments(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, 1, c->q_near, kp, In,
+                        nullptr, mixed_form);
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev[4], sh));
+  // 4. adaptive near moments (Sec. 4.3)
+  if (nr->n_adaptive > 0) {
+    const int64_t A = nr->max_adaptive;
+    for (int d = 1; d <= kMaxDeg; ++d) {
+      if (!nr->ad_count[d]) continue;
+      launch_adaptive(d, lh, nr->ad_list_dev[d], nr->ad_count[d], dv, kp,
+                      eps0 * params->eps_loosen, ctx->deg[d].normV, params->leaf_order,
+                      params->max_depth, Is, In, c->leaves, ctx->work, astride, (int)A, levels,
+                      agrid, ctx->d_status, ctx->d_sched + d, mixed_form ? 2.0 : 0.0);
+    }
+    CK(cudaGetLastError());
+  }
+  CK(cudaEventRecord(ctx->ev[5], sh));
+  CK(cudaStreamWaitEvent(sh, ctx->join, 0));  // self weights done
+  CK(cudaEventRecord(ctx->ev[6], sh));
   // 6. c = V^T (I_near - I_smooth) into the CSR
   for (int d = 1; d <= kMaxDeg; ++d) {
     if (!nr->plist_count[d]) continue;
-    launch_v2c(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, In, Is, InS, IsS, c->val);
+    launch_v2c(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, In, Is, InS, IsS, c->val);
   }
   CK(cudaGetLastError());
-  CK(cudaEventRecord(ctx->ev[7], st));
+  CK(cudaEventRecord(ctx->ev[7], sh));
+  CK(cudaEventRecord(ctx->done, sh));
+  CK(cudaStreamWaitEvent(st, ctx->done, 0));
   dfree(st, ddirs);
   dfree(st, fscr);
   cudaFreeAsync(Is, st);

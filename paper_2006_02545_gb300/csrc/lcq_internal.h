@@ -122,8 +122,10 @@ struct lcq_ctx {
   // stage events: [0,1] near lists, [2..7] corrections
   cudaEvent_t ev[8] = {};
   // side stream: the self weights run beside far order, moments and adaptive integration
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr, ev_self[2] = {};
+  // correction generation: the dependent stages run on `hi` (highest priority), the self
+  // weights beside them on `side` (lowest), both forked from and joined back into `stream`
+  cudaStream_t side = nullptr, hi = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, done = nullptr, ev_self[2] = {};
   long long launches_near = 0, launches_corr = 0;
 };
 

@@ -921,7 +921,9 @@ template <int D>
 struct SelfL {
   static void run(const LaunchCommon& lc, const Dev& dv, const int32_t* deg, const KernelParams& kp,
                   int order, void* out) {
-    const int64_t g = dv.n_self < (int64_t)lc.num_sms * 16 ? dv.n_self : (int64_t)lc.num_sms * 16;
+    // one block per self target: short-lived blocks, so that kernels on higher-priority
+    // streams take the SMs they free first
+    const int64_t g = dv.n_self < (int64_t)0x7fffffff ? dv.n_self : (int64_t)0x7fffffff;
     if (g <= 0) return;
     ++*lc.launches;
     constexpr size_t n = (D + 1) * (D + 2) / 2;
