@@ -849,10 +849,9 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
 
   const int ldI = nr->n_max;
   const int64_t npr = std::max<int64_t>(nr->n_pairs, 1), nsf = std::max<int64_t>(nr->n_self, 1);
-  void *Is, *In, *IsS, *InS;
+  void *Is, *In, *InS;
   CK(dalloc(st, reinterpret_cast<double**>(&Is), (size_t)2 * npr * ldI));
   CK(dalloc(st, reinterpret_cast<double**>(&In), (size_t)2 * npr * ldI));
-  CK(dalloc(st, reinterpret_cast<double**>(&IsS), (size_t)2 * nsf * ldI));
   CK(dalloc(st, reinterpret_cast<double**>(&InS), (size_t)2 * nsf * ldI));
   if (nr->grouped) {
     std::vector<GroupParams> gp(n_phys);
@@ -908,7 +907,8 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   for (int d = 1; d <= kMaxDeg; ++d) {
     if (!nr->plist_count[d]) continue;
     launch_farorder(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, kp, eps0, params->m_max,
-                    ctx->deg[d].normV, ddirs, ndirs, fscr, fgrid, c->q, c->q_near);
+                    ctx->deg[d].normV, ddirs, ndirs, fscr, fgrid, c->q, c->q_near,
+                    ctx->d_sched);
   }
   CK(cudaGetLastError());
   // 5. self weights (Sec. 4, Eq. errestself), on the side stream
@@ -928,10 +928,8 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   // 2. smooth-rule moments of every near and self pair; 3. annulus moments
   for (int d = 1; d <= kMaxDeg; ++d) {
     if (!nr->plist_count[d]) continue;
-    launch_rule_moments(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, 0, c->q, kp, Is, IsS,
-                        mixed_form);
-    launch_rule_moments(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, 1, c->q_near, kp, In,
-                        nullptr, mixed_form);
+    launch_rule_moments(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, 3, c->q, c->q_near, kp,
+                        Is, In, mixed_form);
   }
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[4], sh));
@@ -953,7 +951,8 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   // 6. c = V^T (I_near - I_smooth) into the CSR
   for (int d = 1; d <= kMaxDeg; ++d) {
     if (!nr->plist_count[d]) continue;
-    launch_v2c(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, In, Is, InS, IsS, c->val);
+    launch_v2c(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, In, Is, InS,
+               c->val);
   }
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[7], sh));
@@ -963,7 +962,6 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   dfree(st, fscr);
   cudaFreeAsync(Is, st);
   cudaFreeAsync(In, st);
-  cudaFreeAsync(IsS, st);
   cudaFreeAsync(InS, st);
   // stash the stream/device for later calls on the correction object
   c->q_h.clear();
@@ -1232,8 +1230,8 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
     if (pr.leaf_order <= 0)  // root moments of the adaptive pairs: the smooth rule q_j
       for (int d = 1; d <= kMaxDeg; ++d) {
         if (!nr->plist_count[d]) continue;
-        launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 0, c->q, c->kp, Is,
-                            nullptr, c->mixed_form);
+        launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 1, c->q, nullptr,
+                            c->kp, Is, nullptr, c->mixed_form);
       }
     const GradArgs ga{g, shat, M};
     for (int d = 1; d <= kMaxDeg; ++d) {

@@ -167,12 +167,14 @@ __global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* 
   if (i < n) out[i] += boff[blockIdx.x];
 }
 
-// Smooth rule q_j moments for every near pair and self target of the patch (Sec. 4.2):
-// I_smooth; and annulus-rule moments for annulus pairs (Remark on eta_1).
+// Smooth rule q_j moments for every near pair of the patch (Sec. 4.2): I_smooth (modes
+// bit 0, rule qv, out_smooth); and annulus-rule moments for the annulus pairs (Remark on
+// eta_1; modes bit 1, rule qn, out_ann).  One block per patch and launch, both passes in it.
 template <int D>
 __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
-    const int* __restrict__ plist, int count, Dev dv, int mode, const int32_t* __restrict__ qv,
-    const KernelParams kp, cplx* __restrict__ out_pairs, cplx* __restrict__ out_self, bool mixed) {
+    const int* __restrict__ plist, int count, Dev dv, int modes, const int32_t* __restrict__ qv,
+    const int32_t* __restrict__ qn, const KernelParams kp, cplx* __restrict__ out_smooth,
+    cplx* __restrict__ out_ann, bool mixed) {
   using C = Cfg<D>;
   extern __shared__ double smem[];
   double* cf = smem;
@@ -181,9 +183,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
   __shared__ KernelParams kps;
   __shared__ double cfd[2 * 3 * (D * (D + 1) / 2)];  // derivative series of the chart
   const double* cfdp = cfd;
+  const int64_t ld = dv.ldI;
   for (int b = blockIdx.x; b < count; b += gridDim.x) {
     const int j = plist[b];
-    const int m = qv[j];
     // mixed form: FP32 pair evaluation where the (surface's) tolerance allows it
     const bool mixj = mixed && !(dv.pgroup && dv.grp[dv.pgroup[j]].eps < kMixedMinEps);
     __syncthreads();
@@ -193,35 +195,35 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
       kps = patch_kp(dv, j, kp);
     }
     __syncthreads();
-    if (m <= 0) continue;
     load_coef_derivs<D>(cf, dv.duv[D], cfd);
-    const double* ru = dv.ru + dv.roff[m];
-    const double* rv = dv.rv + dv.roff[m];
-    const double* rw = dv.rw + dv.roff[m];
-    if (mode == 0) {
-      const int64_t p0 = dv.pair_ptr[j], np = dv.pair_ptr[j + 1] - p0;
-      TgtIdx ta{dv.tgt, dv.NT, dv.pair_tgt + p0, dv.tnrm};
-      const int64_t ld = dv.ldI;
-      cplx* base = out_pairs + p0 * ld;
-      block_moments<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)np,
-                       [=] __device__(int i) { return base + (int64_t)i * ld; }, C::n, kps, ws,
-                       dv.cen + 3 * j, 0.0, nullptr, mixj);
-      (void)out_self;
-    } else {
-      const int64_t a0 = dv.an_ptr[j], na = dv.an_ptr[j + 1] - a0;
-      const int32_t* pl = dv.an_pair + a0;
-      TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl, dv.tnrm};
-      const int64_t ld = dv.ldI;
-      block_moments<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)na,
-                       [=] __device__(int i) { return out_pairs + (int64_t)pl[i] * ld; }, C::n, kps,
-                       ws, dv.cen + 3 * j, 0.0, nullptr, mixj);
+    long long evals = 0;
+    for (int mode = 0; mode < 2; ++mode) {
+      if (!(modes & (1 << mode))) continue;
+      const int m = mode == 0 ? qv[j] : qn[j];
+      if (m <= 0) continue;
+      const double* ru = dv.ru + dv.roff[m];
+      const double* rv = dv.rv + dv.roff[m];
+      const double* rw = dv.rw + dv.roff[m];
+      if (mode == 0) {
+        const int64_t p0 = dv.pair_ptr[j], np = dv.pair_ptr[j + 1] - p0;
+        TgtIdx ta{dv.tgt, dv.NT, dv.pair_tgt + p0, dv.tnrm};
+        cplx* base = out_smooth + p0 * ld;
+        block_moments<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)np,
+                         [=] __device__(int i) { return base + (int64_t)i * ld; }, C::n, kps, ws,
+                         dv.cen + 3 * j, 0.0, nullptr, mixj);
+        evals += np * m * m;
+      } else {
+        const int64_t a0 = dv.an_ptr[j], na = dv.an_ptr[j + 1] - a0;
+        const int32_t* pl = dv.an_pair + a0;
+        TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl, dv.tnrm};
+        block_moments<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)na,
+                         [=] __device__(int i) { return out_ann + (int64_t)pl[i] * ld; }, C::n,
+                         kps, ws, dv.cen + 3 * j, 0.0, nullptr, mixj);
+        evals += na * m * m;
+      }
     }
-    if (threadIdx.x == 0) {
-      const long long nt = mode == 0 ? (dv.pair_ptr[j + 1] - dv.pair_ptr[j])
-                                     : (dv.an_ptr[j + 1] - dv.an_ptr[j]);
-      atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 3),
-                (unsigned long long)(nt * m * m));
-    }
+    if (threadIdx.x == 0 && evals > 0)
+      atomicAdd(reinterpret_cast<unsigned long long*>(dv.counters + 3), (unsigned long long)evals);
   }
 }
 
@@ -235,7 +237,8 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
                                                        const double* __restrict__ dirs, int ndirs,
                                                        cplx* __restrict__ scratch,
                                                        int32_t* __restrict__ q_out,
-                                                       int32_t* __restrict__ qn_out) {
+                                                       int32_t* __restrict__ qn_out,
+                                                       int* __restrict__ sched) {
   using C = Cfg<D>;
   extern __shared__ double smem[];
   double* cf = smem;
@@ -250,9 +253,16 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
   cplx* bufA = scratch + (int64_t)blockIdx.x * 2 * kMaxTestPts * C::n;
   cplx* bufB = bufA + kMaxTestPts * C::n;
   const int m_min = (D + 2) / 2;
-  for (int b = blockIdx.x; b < count; b += gridDim.x) {
-    const int j = plist[b];
+  __shared__ int next_b;
+  // patches are taken from the counter *sched (zeroed before the launch), so blocks that
+  // drew cheap patches take more of them
+  for (;;) {
     __syncthreads();
+    if (threadIdx.x == 0) next_b = atomicAdd(sched, 1);
+    __syncthreads();
+    const int b = next_b;
+    if (b >= count) break;
+    const int j = plist[b];
     load_coef<D>(dv.coef, dv.node_off[j], cf);
     if (threadIdx.x == 0) {
       segs[0] = seg_T0();
@@ -621,7 +631,7 @@ template <int D>
 __global__ void k_v2c(const int* __restrict__ plist, int count, Dev dv,
                       const double* __restrict__ Vt, const cplx* __restrict__ In,
                       const cplx* __restrict__ Is, const cplx* __restrict__ InS,
-                      const cplx* __restrict__ IsS, double* __restrict__ val) {
+                      double* __restrict__ val) {
   constexpr int n = (D + 1) * (D + 2) / 2;
   __shared__ double V[n * n];
   __shared__ cplx diff[kThreads / 32][n];
@@ -872,15 +882,15 @@ size_t moments_smem_bytes(int extra_doubles) {
 
 template <int D>
 struct RuleMomL {
-  static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv, int mode,
-                  const int32_t* qv, const KernelParams& kp, void* out_pairs, void* out_self,
-                  bool mixed) {
+  static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv, int modes,
+                  const int32_t* qv, const int32_t* qn, const KernelParams& kp, void* out_smooth,
+                  void* out_ann, bool mixed) {
     const size_t sm = moments_smem_bytes<D>(0) + (mixed ? Cfg<D>::WS_F32 * sizeof(double) : 0);
     set_smem(k_rule_moments<D>, sm);
-    const int grid = count < 2 * lc.num_sms ? count : 2 * lc.num_sms;
     ++*lc.launches;
-    k_rule_moments<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, mode, qv, kp,
-                                                         (cplx*)out_pairs, (cplx*)out_self, mixed);
+    // one block per patch: the hardware hands the next patch to whichever block slot frees
+    k_rule_moments<D><<<count, kThreads, sm, lc.stream>>>(plist, count, dv, modes, qv, qn, kp,
+                                                          (cplx*)out_smooth, (cplx*)out_ann, mixed);
   }
 };
 
@@ -888,12 +898,13 @@ template <int D>
 struct FarOrderL {
   static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                   const KernelParams& kp, double eps, int m_max, double normV, const double* dirs,
-                  int ndirs, void* scratch, int grid, int32_t* q, int32_t* qn) {
+                  int ndirs, void* scratch, int grid, int32_t* q, int32_t* qn, int* sched) {
     const size_t sm = moments_smem_bytes<D>(3 * kMaxTestPts + kThreads / 32 + 4);
     set_smem(k_farorder<D>, sm);
     ++*lc.launches;
+    cudaMemsetAsync(sched, 0, sizeof(int), lc.stream);
     k_farorder<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, kp, eps, m_max, normV, dirs,
-                                                     ndirs, (cplx*)scratch, q, qn);
+                                                     ndirs, (cplx*)scratch, q, qn, sched);
   }
 };
 
@@ -949,12 +960,11 @@ template <int D>
 struct V2cL {
   static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                   const double* Vt, const void* In, const void* Is, const void* InS,
-                  const void* IsS, double* val) {
+                  double* val) {
     const int grid = count < lc.num_sms * 4 ? count : lc.num_sms * 4;
     ++*lc.launches;
     k_v2c<D><<<grid, kThreads, 0, lc.stream>>>(plist, count, dv, Vt, (const cplx*)In,
-                                               (const cplx*)Is, (const cplx*)InS, (const cplx*)IsS,
-                                               val);
+                                               (const cplx*)Is, (const cplx*)InS, val);
   }
 };
 
@@ -1012,15 +1022,16 @@ void launch_scan(const LaunchCommon& lc, const int64_t* in, int64_t* out, int64_
 }
 
 bool launch_rule_moments(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
-                         int mode, const int32_t* qv, const KernelParams& kp, void* out_pairs,
-                         void* out_self, bool mixed) {
-  return dispatch<RuleMomL>(d, lc, plist, count, dv, mode, qv, kp, out_pairs, out_self, mixed);
+                         int modes, const int32_t* qv, const int32_t* qn, const KernelParams& kp,
+                         void* out_smooth, void* out_ann, bool mixed) {
+  return dispatch<RuleMomL>(d, lc, plist, count, dv, modes, qv, qn, kp, out_smooth, out_ann,
+                            mixed);
 }
 bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, int m_max, double normV, const double* dirs,
-                     int ndirs, void* scratch, int grid, int32_t* q, int32_t* qn) {
+                     int ndirs, void* scratch, int grid, int32_t* q, int32_t* qn, int* sched) {
   return dispatch<FarOrderL>(d, lc, plist, count, dv, kp, eps, m_max, normV, dirs, ndirs, scratch,
-                             grid, q, qn);
+                             grid, q, qn, sched);
 }
 bool launch_adaptive(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
@@ -1039,9 +1050,9 @@ bool launch_tgt_normals(int d, const LaunchCommon& lc, const Dev& dv, const int3
   return dispatch<TgtNormalsL>(d, lc, dv, deg, user, do_off, out);
 }
 bool launch_v2c(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
-                const double* Vt, const void* In, const void* Is, const void* InS, const void* IsS,
+                const double* Vt, const void* In, const void* Is, const void* InS,
                 double* val) {
-  return dispatch<V2cL>(d, lc, plist, count, dv, Vt, In, Is, InS, IsS, val);
+  return dispatch<V2cL>(d, lc, plist, count, dv, Vt, In, Is, InS, val);
 }
 bool launch_far_src(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                     const double* Vt, const int32_t* qv, const int64_t* src_off, const void* sigma,

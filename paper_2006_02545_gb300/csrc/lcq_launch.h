@@ -125,12 +125,14 @@ void launch_patch_fill(const LaunchCommon& lc, const NearArgs& a, const int32_t*
                        int32_t* an_pair, int32_t* self_tgt, int64_t* self_csr);
 void launch_scan(const LaunchCommon& lc, const int64_t* in, int64_t* out, int64_t n,
                  int64_t* scratch);
+// modes: bit 0 the smooth rule qv into out_smooth, bit 1 the annulus rule qn into out_ann
 bool launch_rule_moments(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
-                         int mode, const int32_t* qv, const KernelParams& kp, void* out_pairs,
-                         void* out_self, bool mixed = false);
+                         int modes, const int32_t* qv, const int32_t* qn, const KernelParams& kp,
+                         void* out_smooth, void* out_ann, bool mixed = false);
+// sched: a device counter the launch zeroes and the blocks draw patches from
 bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, int m_max, double normV, const double* dirs,
-                     int ndirs, void* scratch, int grid, int32_t* q, int32_t* qn);
+                     int ndirs, void* scratch, int grid, int32_t* q, int32_t* qn, int* sched);
 bool launch_adaptive(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                      const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
@@ -138,7 +140,7 @@ bool launch_adaptive(int d, const LaunchCommon& lc, const int* plist, int count,
 bool launch_self(int d, const LaunchCommon& lc, const Dev& dv, const int32_t* deg,
                  const KernelParams& kp, int order, void* out);
 bool launch_v2c(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
-                const double* Vt, const void* In, const void* Is, const void* InS, const void* IsS,
+                const double* Vt, const void* In, const void* Is, const void* InS,
                 double* val);
 bool launch_far_src(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                     const double* Vt, const int32_t* qv, const int64_t* src_off, const void* sigma,

@@ -300,10 +300,10 @@ extern "C" lcq_status lcq_adaptive_corrections_noalloc(
   dv.status = I(L.status);
   dv.ldI = n;
   // smooth-rule moments (the root of the adaptive walk), adaptive moments, V^T contraction
-  launch_rule_moments(deg, lc, I(L.plist), 1, dv, 0, I32(L.q), kp, F(L.Is), nullptr);
+  launch_rule_moments(deg, lc, I(L.plist), 1, dv, 1, I32(L.q), nullptr, kp, F(L.Is), nullptr);
   launch_adaptive(deg, lc, I(L.plist), 1, dv, kp, eps, dt.normV, 0, max_depth, F(L.Is), F(L.In),
                   I32(L.leaves), b + L.work, stride, NT, max_depth, 1, I(L.status), I(L.sched));
-  launch_v2c(deg, lc, I(L.plist), 1, dv, F(L.Vt), F(L.In), F(L.Is), nullptr, nullptr, out);
+  launch_v2c(deg, lc, I(L.plist), 1, dv, F(L.Vt), F(L.In), F(L.Is), nullptr, out);
   int hst = 0;
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, I(L.status), sizeof(int), cudaMemcpyDeviceToHost, st);
