@@ -121,19 +121,47 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
   const KernelParamsF kf = to_f32(kp);
   const float fR = (float)R;
   const int total = nseg * Q;
+  // The rules are conical products, rows of mr nodes sharing v, and every segment map
+  // here keeps v a function of the rule's v alone (e1y = 0: T0 and all its midpoint
+  // descendants); the v-only factors of the basis and chart sums are then formed once per
+  // row (kw_row_factors), into the tile area, which is free during the geometry phase.
+  const int mr = (int)lrint(sqrt((double)Q));
+  bool by_rows = mr * mr == Q;
+  for (int sg = 0; sg < nseg; ++sg) by_rows = by_rows && segs[sg].e1y == 0.0;
+  using RW = KwRow<D>;
+  constexpr int kRowMax = 3 * C::TT * C::CH / RW::size;
+  double* rows = reinterpret_cast<double*>(G);
   for (int c0 = 0; c0 < total; c0 += C::CH) {
     const int nch = min(C::CH, total - c0);
+    const int row0 = by_rows ? c0 / mr : 0;
+    const bool use_rows = by_rows && (c0 + nch - 1) / mr - row0 + 1 <= kRowMax;
     __syncthreads();
+    if (use_rows) {
+      // one thread per (row, m): the rows spread over all warps, hence all SM sub-partitions
+      const int nrow = (c0 + nch - 1) / mr - row0 + 1;
+      for (int e = threadIdx.x; e < nrow * (D + 1); e += blockDim.x) {
+        const int rr = e / (D + 1), m = e - rr * (D + 1);
+        const int rg = row0 + rr, sg = rg / mr, l0 = (rg - sg * mr) * mr;
+        const SegMap& S = segs[sg];
+        kw_row_factors<D>(S.ay + ru[l0] * S.e1y + rv[l0] * S.e2y, m, cf, cfd,
+                          rows + rr * RW::size);
+      }
+      __syncthreads();
+    }
     for (int ql = threadIdx.x; ql < nch; ql += blockDim.x) {
       const int q = c0 + ql;
       const int sg = q / Q, l = q - sg * Q;
       const SegMap& S = segs[sg];
       const double r0 = ru[l], r1 = rv[l];
       const double u = S.ax + r0 * S.e1x + r1 * S.e2x;
-      const double v = S.ay + r0 * S.e1y + r1 * S.e2y;
       const double w = rw[l] * S.det;
       double X[3], Xu[3], Xv[3], Nn[3];
-      kw_geometry_proj<D>(u, v, cf, cfd, X, Xu, Xv, B + ql * C::BS);
+      if (use_rows) {
+        kw_geometry_row<D>(u, rows + (q / mr - row0) * RW::size, X, Xu, Xv, B + ql * C::BS);
+      } else {
+        const double v = S.ay + r0 * S.e1y + r1 * S.e2y;
+        kw_geometry_proj<D>(u, v, cf, cfd, X, Xu, Xv, B + ql * C::BS);
+      }
       B[ql * C::BS + C::n] = 1.0;  // the envelope's column
       cross3(Xu, Xv, Nn);
       const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);

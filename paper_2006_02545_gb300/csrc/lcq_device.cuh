@@ -34,6 +34,31 @@ __host__ __device__ __forceinline__ void jacobi_coef(int a, int b, double* c1, d
   *c2 = (double)(2 * a * (a + b) * (2 * a + b + 2)) / den;
 }
 
+// Three-term coefficients of P^{(0, 2m+1)}_a, [m][a][c1, c0, c2], and 1/m, for loops that
+// are not unrolled; same values as jacobi_coef.  Filled with c_kw by upload_kw_tables.
+static __constant__ double c_jac[(kMaxDeg + 1) * (kMaxDeg + 1) * 3];
+static __constant__ double c_rcp[kMaxDeg + 1];
+
+// Fills c_kw, c_jac and c_rcp of the calling translation unit (stream-ordered).
+static inline cudaError_t upload_kw_tables(cudaStream_t st) {
+  double c[kMaxBasis], jc[(kMaxDeg + 1) * (kMaxDeg + 1) * 3] = {}, rc[kMaxDeg + 1] = {};
+  for (int nn = 0; nn <= kMaxDeg; ++nn)
+    for (int m = 0; m <= nn; ++m) c[nn * (nn + 1) / 2 + m] = sqrt(2.0 * (2 * m + 1) * (nn + 1));
+  for (int m = 0; m <= kMaxDeg; ++m) {
+    rc[m] = m > 0 ? 1.0 / m : 0.0;
+    for (int a = 0; a <= kMaxDeg; ++a) {
+      double* q = jc + (m * (kMaxDeg + 1) + a) * 3;
+      jacobi_coef(a, 2 * m + 1, q, q + 1, q + 2);
+    }
+  }
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_kw, c, sizeof(c), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyToSymbolAsync(c_jac, jc, sizeof(jc), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyToSymbolAsync(c_rcp, rc, sizeof(rc), 0, cudaMemcpyHostToDevice, st);
+  return e;
+}
+
 // Koornwinder values K[nm] at (u, v) written with stride `ks`.
 template <int D>
 __device__ __forceinline__ void kw_values(double u, double v, double* K, int ks) {
@@ -160,6 +185,112 @@ __device__ __forceinline__ void kw_geometry_proj(double u, double v, const doubl
     X[1] = x1;
     X[2] = x2;
   }
+  Xu[0] = u0;
+  Xu[1] = u1;
+  Xu[2] = u2;
+  Xv[0] = v0;
+  Xv[1] = v1;
+  Xv[2] = v2;
+}
+
+// Row form of kw_geometry_proj for nodes that share v.  K_nm = L_m(u, v) J_nm(v) with
+// L_m = (1 - v)^m P_m((2u + v - 1) / (1 - v)) and J_nm = c_nm P^{(0,2m+1)}_{n-m}(1 - 2v), so
+// per value of v the J factors and the chart's sums over n at fixed m can be formed once:
+// row = [v, (1 - v)^2, J (n), BX (3 (D+1)), BU (3 D), BV (3 D)], BX[m][c] = sum_n cf_nm[c]
+// J_nm and BU, BV likewise from the derivative series (n < D).
+template <int D>
+struct KwRow {
+  static constexpr int n = (D + 1) * (D + 2) / 2;
+  static constexpr int J = 2, BX = J + n, BU = BX + 3 * (D + 1), BV = BU + 3 * D;
+  static constexpr int size = BV + 3 * D;
+};
+
+// The part of the row factors that belongs to one m (the header too when m = 0), so that
+// a block spreads a row over D + 1 threads.
+template <int D>
+__device__ __forceinline__ void kw_row_factors(double v, int m, const double* cf,
+                                               const double* cfd, double* row) {
+  using RW = KwRow<D>;
+  constexpr int nd = D * (D + 1) / 2;
+  const double y = 1.0 - 2.0 * v;
+  if (m == 0) {
+    row[0] = v;
+    row[1] = (1.0 - v) * (1.0 - v);
+  }
+  double Pp = 0.0, P = 1.0;
+  double x0 = 0.0, x1 = 0.0, x2 = 0.0, u0 = 0.0, u1 = 0.0, u2 = 0.0, v0 = 0.0, v1 = 0.0,
+         v2 = 0.0;
+  const double* jc = c_jac + m * (kMaxDeg + 1) * 3;
+#pragma unroll 1
+  for (int a = 0; a <= D - m; ++a) {
+    const int nn = m + a, idx = nn * (nn + 1) / 2 + m;
+    const double jv = c_kw[idx] * P;
+    row[RW::J + idx] = jv;
+    x0 = fma(cf[idx * 3], jv, x0);
+    x1 = fma(cf[idx * 3 + 1], jv, x1);
+    x2 = fma(cf[idx * 3 + 2], jv, x2);
+    if (nn < D) {
+      u0 = fma(cfd[idx * 3], jv, u0);
+      u1 = fma(cfd[idx * 3 + 1], jv, u1);
+      u2 = fma(cfd[idx * 3 + 2], jv, u2);
+      v0 = fma(cfd[(nd + idx) * 3], jv, v0);
+      v1 = fma(cfd[(nd + idx) * 3 + 1], jv, v1);
+      v2 = fma(cfd[(nd + idx) * 3 + 2], jv, v2);
+    }
+    const double Pn = (jc[3 * a] * y + jc[3 * a + 1]) * P - jc[3 * a + 2] * Pp;
+    Pp = P;
+    P = Pn;
+  }
+  row[RW::BX + 3 * m] = x0;
+  row[RW::BX + 3 * m + 1] = x1;
+  row[RW::BX + 3 * m + 2] = x2;
+  if (m < D) {
+    row[RW::BU + 3 * m] = u0;
+    row[RW::BU + 3 * m + 1] = u1;
+    row[RW::BU + 3 * m + 2] = u2;
+    row[RW::BV + 3 * m] = v0;
+    row[RW::BV + 3 * m + 1] = v1;
+    row[RW::BV + 3 * m + 2] = v2;
+  }
+}
+
+// X, X_u, X_v and the basis values K (stride 1) at (u, v) from the row factors of v.
+template <int D>
+__device__ __forceinline__ void kw_geometry_row(double u, const double* row, double* X,
+                                                double* Xu, double* Xv, double* K) {
+  using RW = KwRow<D>;
+  const double v = row[0], q2 = row[1];
+  const double s = 2.0 * u + v - 1.0;
+  double Lp = 0.0, L = 1.0;
+  double x0 = 0.0, x1 = 0.0, x2 = 0.0, u0 = 0.0, u1 = 0.0, u2 = 0.0, v0 = 0.0, v1 = 0.0,
+         v2 = 0.0;
+#pragma unroll
+  for (int m = 0; m <= D; ++m) {
+    if (m > 0) {
+      const double Ln = ((2.0 * m - 1.0) * s * L - (m - 1.0) * q2 * Lp) * (1.0 / m);
+      Lp = L;
+      L = Ln;
+    }
+    x0 = fma(row[RW::BX + 3 * m], L, x0);
+    x1 = fma(row[RW::BX + 3 * m + 1], L, x1);
+    x2 = fma(row[RW::BX + 3 * m + 2], L, x2);
+    if (m < D) {
+      u0 = fma(row[RW::BU + 3 * m], L, u0);
+      u1 = fma(row[RW::BU + 3 * m + 1], L, u1);
+      u2 = fma(row[RW::BU + 3 * m + 2], L, u2);
+      v0 = fma(row[RW::BV + 3 * m], L, v0);
+      v1 = fma(row[RW::BV + 3 * m + 1], L, v1);
+      v2 = fma(row[RW::BV + 3 * m + 2], L, v2);
+    }
+#pragma unroll
+    for (int a = 0; a <= D - m; ++a) {
+      const int nn = m + a, idx = nn * (nn + 1) / 2 + m;
+      K[idx] = L * row[RW::J + idx];
+    }
+  }
+  X[0] = x0;
+  X[1] = x1;
+  X[2] = x2;
   Xu[0] = u0;
   Xu[1] = u1;
   Xu[2] = u2;

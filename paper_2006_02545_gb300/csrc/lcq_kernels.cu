@@ -982,10 +982,7 @@ struct FarSrcL {
 }  // namespace
 
 cudaError_t upload_constants(cudaStream_t st) {
-  double c[kMaxBasis];
-  for (int nn = 0; nn <= kMaxDeg; ++nn)
-    for (int m = 0; m <= nn; ++m) c[nn * (nn + 1) / 2 + m] = sqrt(2.0 * (2 * m + 1) * (nn + 1));
-  cudaError_t e = cudaMemcpyToSymbolAsync(c_kw, c, sizeof(c), 0, cudaMemcpyHostToDevice, st);
+  const cudaError_t e = upload_kw_tables(st);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(st);
 }
