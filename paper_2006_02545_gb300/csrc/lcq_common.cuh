@@ -589,37 +589,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
       const int S = cnt[L];
       const int* ST = lvlT + (int64_t)L * A_max;
       const cplx* IT = lvlI + (int64_t)L * A_max * 4 * n;
-      if (threadIdx.x == 0) {
-        // vertices of T from its path, then the maps of its four children
-        double ax = 0, ay = 0, bx = 1, by = 0, cx = 0, cy = 1;
+      if ((threadIdx.x & 31) == 0 && threadIdx.x < 128) {
+        // Every subtriangle of the midpoint tree is T0 scaled by 2^-L, translated and
+        // possibly point-reflected: vertex a at (ia, ja) 2^-L, b = a + o (2^-L, 0),
+        // c = a + o (0, 2^-L).  The walk down the path runs in integers; the first lane of
+        // warp k writes the map of child k (all exact dyadic values).
+        const int k = threadIdx.x >> 5;
+        long long ia = 0, ja = 0;
+        int o = 1;
         for (int l = 0; l < L; ++l) {
           const int dgt = (int)((path >> (2 * l)) & 3);
-          const double abx = 0.5 * (ax + bx), aby = 0.5 * (ay + by);
-          const double bcx = 0.5 * (bx + cx), bcy = 0.5 * (by + cy);
-          const double cax = 0.5 * (cx + ax), cay = 0.5 * (cy + ay);
-          if (dgt == 0) { bx = abx; by = aby; cx = cax; cy = cay; }
-          else if (dgt == 1) { ax = abx; ay = aby; cx = bcx; cy = bcy; }
-          else if (dgt == 2) { ax = cax; ay = cay; bx = bcx; by = bcy; }
-          else { ax = bcx; ay = bcy; bx = cax; by = cay; cx = abx; cy = aby; }
+          ia = 2 * ia + ((dgt & 1) ? o : 0);
+          ja = 2 * ja + ((dgt & 2) ? o : 0);
+          if (dgt == 3) o = -o;
         }
-        const double abx = 0.5 * (ax + bx), aby = 0.5 * (ay + by);
-        const double bcx = 0.5 * (bx + cx), bcy = 0.5 * (by + cy);
-        const double cax = 0.5 * (cx + ax), cay = 0.5 * (cy + ay);
-        const double V[4][6] = {{ax, ay, abx, aby, cax, cay},
-                                {abx, aby, bx, by, bcx, bcy},
-                                {cax, cay, bcx, bcy, cx, cy},
-                                {bcx, bcy, cax, cay, abx, aby}};
-        for (int k = 0; k < 4; ++k) {
-          SegMap s;
-          s.ax = V[k][0];
-          s.ay = V[k][1];
-          s.e1x = V[k][2] - V[k][0];
-          s.e1y = V[k][3] - V[k][1];
-          s.e2x = V[k][4] - V[k][0];
-          s.e2y = V[k][5] - V[k][1];
-          s.det = fabs(s.e1x * s.e2y - s.e1y * s.e2x);
-          segs[k] = s;
-        }
+        const double h = ldexp(1.0, -(L + 1));
+        const int ok = k == 3 ? -o : o;
+        SegMap sm;
+        sm.ax = (double)(2 * ia + ((k & 1) ? o : 0)) * h;
+        sm.ay = (double)(2 * ja + ((k & 2) ? o : 0)) * h;
+        sm.e1x = ok * h;
+        sm.e1y = 0.0;
+        sm.e2x = 0.0;
+        sm.e2y = ok * h;
+        sm.det = h * h;
+        segs[k] = sm;
       }
       __syncthreads();
       // children moments of every target in S

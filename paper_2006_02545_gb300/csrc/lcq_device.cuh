@@ -34,18 +34,16 @@ __host__ __device__ __forceinline__ void jacobi_coef(int a, int b, double* c1, d
   *c2 = (double)(2 * a * (a + b) * (2 * a + b + 2)) / den;
 }
 
-// Three-term coefficients of P^{(0, 2m+1)}_a, [m][a][c1, c0, c2], and 1/m, for loops that
-// are not unrolled; same values as jacobi_coef.  Filled with c_kw by upload_kw_tables.
+// Three-term coefficients of P^{(0, 2m+1)}_a, [m][a][c1, c0, c2], for loops that are not
+// unrolled; same values as jacobi_coef.  Filled with c_kw by upload_kw_tables.
 static __constant__ double c_jac[(kMaxDeg + 1) * (kMaxDeg + 1) * 3];
-static __constant__ double c_rcp[kMaxDeg + 1];
 
-// Fills c_kw, c_jac and c_rcp of the calling translation unit (stream-ordered).
+// Fills c_kw and c_jac of the calling translation unit (stream-ordered).
 static inline cudaError_t upload_kw_tables(cudaStream_t st) {
-  double c[kMaxBasis], jc[(kMaxDeg + 1) * (kMaxDeg + 1) * 3] = {}, rc[kMaxDeg + 1] = {};
+  double c[kMaxBasis], jc[(kMaxDeg + 1) * (kMaxDeg + 1) * 3] = {};
   for (int nn = 0; nn <= kMaxDeg; ++nn)
     for (int m = 0; m <= nn; ++m) c[nn * (nn + 1) / 2 + m] = sqrt(2.0 * (2 * m + 1) * (nn + 1));
   for (int m = 0; m <= kMaxDeg; ++m) {
-    rc[m] = m > 0 ? 1.0 / m : 0.0;
     for (int a = 0; a <= kMaxDeg; ++a) {
       double* q = jc + (m * (kMaxDeg + 1) + a) * 3;
       jacobi_coef(a, 2 * m + 1, q, q + 1, q + 2);
@@ -54,8 +52,6 @@ static inline cudaError_t upload_kw_tables(cudaStream_t st) {
   cudaError_t e = cudaMemcpyToSymbolAsync(c_kw, c, sizeof(c), 0, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyToSymbolAsync(c_jac, jc, sizeof(jc), 0, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyToSymbolAsync(c_rcp, rc, sizeof(rc), 0, cudaMemcpyHostToDevice, st);
   return e;
 }
 

@@ -280,14 +280,15 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
         int F = 0;
         if (pass == 0) {
           const int cnt = np >= 20 ? 10 : (int)(np / 2);
-          // repeated selection: largest d2, ties by smaller target id
-          double lastd = 1e300;
+          // repeated selection: largest d2, ties by smaller target id.  d2 >= 0, whose bit
+          // patterns order like the values: the compares run on the integer pipe.
+          long long lastd = 0x7fffffffffffffffll;
           int lastt = -1;
           for (int k = 0; k < cnt; ++k) {
-            double bd = -1.0;
+            long long bd = -1;
             int bt = 0x7fffffff;
             for (int64_t p = 0; p < np; ++p) {
-              const double d = dv.pair_d2[p0 + p];
+              const long long d = __double_as_longlong(dv.pair_d2[p0 + p]);
               const int t = dv.pair_tgt[p0 + p];
               const bool after = (d < lastd) || (d == lastd && t > lastt);
               if (!after) continue;
@@ -322,14 +323,14 @@ __global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ p
               ++F;
             }
             const int cnt = na < 10 ? (int)na : 10;
-            double lastd = -1.0;
+            long long lastd = -1;
             int lastt = -1;
             for (int k = 0; k < cnt && F < kMaxTestPts; ++k) {
-              double bd = 1e300;
+              long long bd = 0x7fffffffffffffffll;
               int bt = 0x7fffffff;
               for (int64_t a = 0; a < na; ++a) {
                 const int64_t p = dv.an_pair[a0 + a];
-                const double d = dv.pair_d2[p];
+                const long long d = __double_as_longlong(dv.pair_d2[p]);
                 const int t = dv.pair_tgt[p];
                 const bool after = (d > lastd) || (d == lastd && t > lastt);
                 if (!after) continue;
