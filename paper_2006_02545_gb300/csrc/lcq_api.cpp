@@ -911,7 +911,7 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
                     ctx->d_sched);
   }
   CK(cudaGetLastError());
-  // 5. self weights (Sec. 4, Eq. errestself), on the side stream
+  // 5. self weights (Sec. 4, Eq. errestself), on the low-priority stream
   const int sorder = params->self_order > 0 ? params->self_order : default_self_order(eps0);
   CK(cudaEventRecord(ctx->ev_self[0], ctx->side));
   if (nr->n_self > 0) {
