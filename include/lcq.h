@@ -290,8 +290,7 @@ lcq_status lcq_stage_times(lcq_ctx* ctx, float* ms6, int64_t* launches);
  * every byte of the device).  The paper has no counterpart; this is a library facility.
  *
  * Computes the adaptive near corrections of ONE patch for targets that are all treated
- * as adaptive (Sec. 4.3), exactly as lcq_gen_corrections computes them for adaptive
- * near pairs: out[t][l] = sum_nm V[nm][l] (I^adaptive_nm(x_t) - I^{rule q}_nm(x_t)).
+ * as adaptive, exactly as lcq_gen_corrections computes them for adaptive near pairs: out[t][l] = sum_nm V[nm][l] (I^adaptive_nm(x_t) - I^{rule q}_nm(x_t)).
  *   deg       patch degree, 1..8
  *   y         device double SoA [3][n] node coordinates, n = (deg+1)(deg+2)/2
  *   n_targets 1..128; tgt_xyz device double SoA [3][n_targets] (off-surface points)
@@ -306,7 +305,8 @@ lcq_status lcq_stage_times(lcq_ctx* ctx, float* ms6, int64_t* launches);
  * first call before any stream capture.  Calls share the array and keep the previous
  * call's contents (each call rewrites what it reads): calls that overlap on the GPU --
  * on different streams or from different threads -- race and must be serialized by the
- * caller.  The call queues its work on cuda_stream (NULL: legacy default stream) and
+ * caller.  Host-side set-up is safe when several host threads make their first calls at
+ * once.  The call queues its work on cuda_stream (NULL: legacy default stream) and
  * synchronizes that stream before returning.  Returns LCQ_ERR_CAPACITY when deg,
  * n_targets or max_depth exceed the limits above, LCQ_ERR_MAX_DEPTH (result kept) or
  * LCQ_ERR_NONFINITE as lcq_gen_corrections does. */
@@ -316,6 +316,20 @@ lcq_status lcq_adaptive_corrections_noalloc(int deg, const double* y, int64_t n_
                                             double alpha_im, double beta_re, double beta_im,
                                             int q, double eps, int max_depth, void* cuda_stream,
                                             double* out);
+
+/* Pipe-throughput microbenchmarks on `device` (no counterpart in the paper; the measured
+ * denominators of the roofline fractions the benchmark reports).  Writes host out[n_out],
+ * up to 8 values, each a rate measured by CUDA events over about 20 ms of one kernel that
+ * keeps every SM busy with independent dependency chains:
+ *   [0] FP64 FMA, TFLOP/s              [1] FP32 FMA, TFLOP/s
+ *   [2] special-function unit (sin.approx.f32), 10^12 results/s
+ *   [3] INT32 xor + add, 10^12 operations/s
+ *   [4] mma.sync m8n8k4 f64, TFLOP/s   [5] mma.sync m16n8k16 f16 -> f32, TFLOP/s
+ *   [6] mma.sync m16n8k16 bf16 -> f32, TFLOP/s   [7] mma.sync m16n8k8 tf32 -> f32, TFLOP/s
+ * Allocates 32 KB of device memory and a private stream for the duration of the call;
+ * takes about a second; LCQ_ERR_ARG for a null out or n_out < 1, LCQ_ERR_CUDA on any
+ * CUDA failure (entries that were measured are kept). */
+lcq_status lcq_pipe_peaks(int device, double* out, int n_out);
 
 const char* lcq_status_string(lcq_status s);
 const char* lcq_last_error(const lcq_ctx* ctx);

@@ -105,19 +105,23 @@ int64_t work_stride(int64_t A, int64_t n, int levels) {
   return (s + 255) / 256 * 256;
 }
 
+// Host tables, built once per process.  Both are safe when several host threads make
+// their first calls at the same time (different GPUs may be driven concurrently): the rule
+// tables are a function-local static (initialized once, under the runtime's lock) and each
+// degree's tables are built under std::call_once.
 const RuleTables& host_rules() {
-  static RuleTables r;
-  static bool built = false;
-  if (!built) {
-    build_rule_tables(&r);
-    built = true;
-  }
+  static const RuleTables r = [] {
+    RuleTables t;
+    build_rule_tables(&t);
+    return t;
+  }();
   return r;
 }
 
 const DegTables& host_deg(int d) {
   static DegTables t[kMaxDeg + 1];
-  if (t[d].n == 0) build_deg_tables(d, &t[d]);
+  static std::once_flag once[kMaxDeg + 1];
+  std::call_once(once[d], [d] { build_deg_tables(d, &t[d]); });
   return t[d];
 }
 

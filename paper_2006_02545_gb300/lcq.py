@@ -85,6 +85,7 @@ _sig = {
     "lcq_stage_times": (C.c_int, [_vp, _vp, _vp]),
     "lcq_adaptive_corrections_noalloc": (C.c_int, [C.c_int, _vp, _i64, _vp, C.c_int, _d, _d, _d,
                                                    _d, _d, _d, C.c_int, _d, C.c_int, _vp, _vp]),
+    "lcq_pipe_peaks": (C.c_int, [C.c_int, _vp, C.c_int]),
     "lcq_status_string": (C.c_char_p, [C.c_int]),
     "lcq_last_error": (C.c_char_p, [_vp]),
 }
@@ -396,3 +397,16 @@ def adaptive_corrections_noalloc(deg, y_dev, tgt_dev, kernel, k, q, eps, out, al
         deg, _ptr(y_dev), int(tgt_dev.shape[1]), _ptr(tgt_dev), KERNELS[kernel], k.real, k.imag,
         alpha.real, alpha.imag, beta.real, beta.imag, int(q), float(eps), int(max_depth),
         C.c_void_p(stream.cuda_stream), _ptr(out))
+
+
+PEAK_KEYS = ("fp64_fma_tflops", "fp32_fma_tflops", "mufu_sin_tops", "int32_tops",
+             "mma_f64_tflops", "mma_f16_tflops", "mma_bf16_tflops", "mma_tf32_tflops")
+
+
+def pipe_peaks(device: int = 0) -> dict:
+    """Measured pipe throughputs on `device` (lcq_pipe_peaks), keyed by PEAK_KEYS."""
+    out = np.zeros(len(PEAK_KEYS))
+    st = _lib.lcq_pipe_peaks(device, _ptr(out), len(PEAK_KEYS))
+    if st:
+        raise LCQError(st, "lcq_pipe_peaks")
+    return dict(zip(PEAK_KEYS, out.tolist()))

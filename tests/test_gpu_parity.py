@@ -164,17 +164,24 @@ def test_deterministic(ctx):
     assert np.array_equal(a["val"], b["val"]) and np.array_equal(a["u"], b["u"])
 
 
-def test_sphere_eigenvalue_gpu(ctx):
-    """S_k Y_0 = i k j_0(k) h_0(k) on a finer sphere, from the GPU alone."""
+@pytest.mark.parametrize("kind", ["S", "D"])
+def test_sphere_eigenvalue_gpu(ctx, kind):
+    """S_k Y_n = i k j_n(k) h_n(k) Y_n and D_k Y_n = (i k^2 j_n(k) h_n'(k) + 1/2) Y_n for
+    n = 0, 1, 2 (Y_0 = 1, Y_1 = z, Y_2 = (3 z^2 - 1)/2 at the nodes) on the 320-patch
+    degree-6 sphere, from the GPU alone."""
     s = W.ellipsoid(4, 6)
     x, tn = W.onsurface_targets(s)
     import torch
     from paper_2006_02545_gb300 import lcq
-    g = run_gpu(ctx, s, x, tn, "S", 1.0, 1e-9)
-    one = torch.ones(s.n_points, dtype=torch.complex128, device=ctx.torch_device)
-    u = lcq.apply_corrected_S(ctx, g["ds"], g["near"], g["corr"], one, x.shape[1]).cpu().numpy()
-    lam = truth.sphere_eigen_S(0, 1.0)
-    assert np.abs(u - lam).max() / abs(lam) < 1e-6
+    g = run_gpu(ctx, s, x, tn, kind, 1.0, 1e-9)
+    fn = lcq.apply_corrected_S if kind == "S" else lcq.apply_corrected_D
+    lamf = truth.sphere_eigen_S if kind == "S" else truth.sphere_eigen_D
+    z = s.xyz[2] / np.linalg.norm(s.xyz, axis=0)
+    for n, Y in enumerate((np.ones_like(z), z, 0.5 * (3 * z * z - 1))):
+        sig = torch.from_numpy(Y.astype(complex)).to(ctx.torch_device)
+        u = fn(ctx, g["ds"], g["near"], g["corr"], sig, x.shape[1]).cpu().numpy()
+        lam = lamf(n, 1.0)
+        assert np.abs(u - lam * Y).max() / abs(lam) < 1e-6, (n, kind)
 
 
 def test_edge_cases(ctx):
