@@ -35,17 +35,15 @@ METRIC = ("near-field correction points/sec on 1 GB300 (FP64 vs mixed/batched) a
 UNIT = "points/s"
 WORKLOAD = "CFIE D-ikS k=2pi ellipsoid(1,2,3) 1280 order-6 patches (35,840 pts) eps=1e-9 FP64"
 
-# Algorithmic FLOPs of one (target, leaf node) evaluation in the adaptive kernel:
-# kernel (difference, r^2, r, 1/r, phase, e^{ikr}/(4 pi r), S and D parts, CFIE
-# combination: 50 arithmetic operations + sqrt, reciprocal and sincos counted as one
-# each) plus the contraction onto n Koornwinder moments (complex x real: 4 per moment).
-KERNEL_FLOPS = 53
+# Algorithmic FLOPs of one (target, leaf node) evaluation in the adaptive kernel: the
+# kernel value (difference, r^2, phase, e^{ikr}/(4 pi r), S and D parts, CFIE combination:
+# 20 arithmetic operations, and sqrt, reciprocal and sincos counted as one each), plus the
+# contraction onto n Koornwinder moments (complex x real: 4 per moment).
+KERNEL_FLOPS = 20 + 3
 
 
-def fp64_peak_tflops():
-    """Derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (the 1.25 TFLOP/s
-    nominal GB300 figure corresponds to 2 FP64 FMA lanes per SM per clock)."""
-    return 152 * 2 * 2 * 2.07e9 / 1e12
+def flops_per_eval(n):
+    return KERNEL_FLOPS + 4 * n
 
 
 def parse():
@@ -55,13 +53,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--batched-scale", type=float, default=0.0,
+    ap.add_argument("--batched-scale", type=float, default=1.0,
                     help="patch-count scale of the 64-torus batch variant (0: skip it; 1: the "
-                         "full batch, about three minutes)")
+                         "full batch)")
     ap.add_argument("--no-table1", action="store_true",
                     help="skip the twisted-torus sweep over order p and eps (the paper's Table 1)")
-    ap.add_argument("--large", action="store_true",
-                    help="also time the 40,000-patch torus (k=20, eps=1e-9), FP64 and mixed")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 40,000-patch torus (k=20, eps=1e-9; FP64 and mixed, and the "
+                         "direct-sum apply on a 100,000-point subset)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--s", type=int, default=8, help="icosahedral refinement (1280 patches at 8)")
     ap.add_argument("--leaf-order", type=int, default=0,
@@ -231,6 +230,7 @@ def run_ours(args, rank, world, local_rank):
     n = 28
     ctx = lcq.Context(local_rank)
     stream = ctx.stream
+    peaks = lcq.pipe_peaks(local_rank)   # measured denominators of the roofline fractions
     xyz_d = torch.from_numpy(surf.xyz).to(dev)
     tx_d = torch.from_numpy(np.ascontiguousarray(wl.tgt_xyz)).to(dev)
     tn_d = torch.from_numpy(wl.tgt_node).to(dev)
@@ -451,9 +451,12 @@ def run_ours(args, rank, world, local_rank):
                                "S_init": ts.n_points / (ms[-1] / 1e3), "status": st_t})
             del tds, tx_d1, ttn_d1
 
-    # the 40,000-patch torus (k = 20, eps = 1e-9), FP64 and mixed, one timed step each
+    # the 40,000-patch torus (k = 20, eps = 1e-9), FP64 and mixed, one timed step each; the
+    # two CSRs are compared on the device; then the corrected potential at a 100,000-point
+    # subset of the nodes (its own near lists and corrections, and the direct far sum over
+    # every oversampled source), the apply timed alone
     large = None
-    if args.large:
+    if not args.no_large and not args.no_variants:
         lw = W.torus_cfie_k20(100)
         ls = lw.surface
         lds = lcq.DeviceSurface(ls.deg, ls.node_off, torch.from_numpy(ls.xyz).to(dev))
@@ -472,14 +475,41 @@ def run_ours(args, rank, world, local_rank):
             e1.record(stream)
             st_l = ctx.sync()
             ms = e0.elapsed_time(e1)
-            vals[prec] = corr.export(ls.n_points)[2].copy()
+            nnz = near.nnz
+            dv = torch.empty(nnz, dtype=torch.complex128, device=dev)
+            corr.export(ls.n_points, out=(None, None, dv))
+            vals[prec] = dv
             large[prec] = {"value": ls.n_points / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-                           "status": st_l, "nnz": near.nnz}
+                           "status": st_l, "nnz": nnz,
+                           "adaptive_ms": ctx.stage_times()[0][3]}
             corr.close()
             near.close()
-        large["mixed"]["csr_rel_l2_vs_fp64"] = float(np.linalg.norm(vals["mixed"] - vals["fp64"]) /
-                                                     np.linalg.norm(vals["fp64"]))
-        del vals, lds, lx, ltn
+        large["mixed"]["csr_rel_l2_vs_fp64"] = float(
+            torch.linalg.vector_norm(vals["mixed"] - vals["fp64"]) /
+            torch.linalg.vector_norm(vals["fp64"]))
+        large["mixed"]["fp32_used"] = lw.eps >= 1e-6
+        del vals
+        sub = np.arange(0, ls.n_points, ls.n_points // 100000)[:100000]
+        sx = torch.from_numpy(np.ascontiguousarray(lw.tgt_xyz[:, sub])).to(dev)
+        stn = torch.from_numpy(np.ascontiguousarray(lw.tgt_node[sub])).to(dev)
+        near = lcq.build_near_lists(ctx, lds, sx, stn, lp)
+        corr = lcq.gen_corrections(ctx, lds, near, lw.kernel, lw.k, lp, lw.alpha, lw.beta)
+        sig = torch.from_numpy(W.density(ls.n_points, 0)).to(dev)
+        lcq.apply_corrected_CFIE(ctx, lds, near, corr, sig, len(sub))   # warm-up
+        ctx.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u = lcq.apply_corrected_CFIE(ctx, lds, near, corr, sig, len(sub))
+        e1.record(stream)
+        st_a = ctx.sync()
+        nnz_s, n_over = corr.info()
+        large["apply_100k"] = {"targets": len(sub), "sources_oversampled": n_over,
+                               "ms": e0.elapsed_time(e1), "status": st_a,
+                               "finite": bool(torch.isfinite(u).all())}
+        corr.close()
+        near.close()
+        del lds, lx, ltn, sx, stn, sig, u
 
     # end to end through the C ABI with host buffers: H2D of inputs, D2H of the CSR
     e2e = None
@@ -523,14 +553,21 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return
-    flops = nodes * (4 * n + KERNEL_FLOPS)
+    fpe = flops_per_eval(n)
+    flops = nodes * fpe
     a_ms = statistics.mean(adapt_ms)
     achieved = flops / (a_ms / 1e3) / 1e12
-    peak = fp64_peak_tflops()
-    roofline = {"bound": "alu", "kernel": "k_adaptive<6> (FP64)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+    peak = peaks["fp64_fma_tflops"]
+    roofline = {"bound": "alu",
+                "kernel": "k_adaptive<6>: FP64 kernel values; contraction on the f16 tensor "
+                          "cores by an exact 8-slice split",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic_for("k_adaptive"),
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz",
+                "peak_source": "measured in this run: FP64 FMA chains on every SM "
+                               "(lcq_pipe_peaks), CUDA events",
+                "flops_per_eval": fpe,
+                "flops_per_eval_terms": "20 arithmetic + 3 special functions (sqrt, reciprocal, "
+                                        "sincos) + 4n contraction, n = 28",
                 "flops_per_launch": flops, "node_evals_per_launch": nodes,
                 "tests_per_launch": tests, "union_tree_nodes_per_launch": tree_nodes,
                 "avg_launch_ms": a_ms}
@@ -540,9 +577,17 @@ def run_ours(args, rank, world, local_rank):
         pool = make_pool(workers)
         v, done, worst = oracle_sample(args.s, P, workers, 1, 0, pool, args.eps, args.leaf_order)
         pool.close()
+        # one core, beside the paper's single-core figures: median of 3 samples of 2 patches
+        pool1 = make_pool(1)
+        one = [oracle_sample(args.s, P, 1, 2, 101 * r, pool1, args.eps, args.leaf_order)[0]
+               for r in range(3)]
+        pool1.close()
         cpu = {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
                "sample": f"{done} of {P} patches (1 per worker, spread over the surface); "
-                         f"sampled points / slowest worker's compute time ({worst:.1f} s)"}
+                         f"sampled points / slowest worker's compute time ({worst:.1f} s)",
+               "single_core": {"value": statistics.median(one), "unit": UNIT, "cores": 1,
+                               "sample": "median of 3 samples of 2 patches each, one process",
+                               "samples": one}}
     st_mean = [statistics.mean(s[i] for s in stages) for i in range(6)]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -552,6 +597,7 @@ def run_ours(args, rank, world, local_rank):
                    "eps": args.eps, "leaf_order": args.leaf_order or "q_j",
                    "l2": "256 MiB buffer written between steps (outside the timed events)"},
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+        "pipe_peaks": peaks,
         "clocks": clk, "status": max(statuses) if statuses else None,
         "stages_ms": dict(zip(["near_lists", "far_order", "smooth_annulus", "adaptive", "self",
                                "v2c"], st_mean)),

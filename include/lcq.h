@@ -201,8 +201,9 @@ lcq_status lcq_gen_corrections_batched(lcq_ctx* ctx, const lcq_surface* surf, co
 /* nnz of the CSR, N_over = sum_j n_{q_j} (Sec. 5.2), value dtype (0 = complex128). */
 lcq_status lcq_corr_info(const lcq_corr* corr, int64_t* nnz, int64_t* n_over, int* value_dtype);
 
-/* CSR to host: row_ptr[NT+1], col[nnz] (global node ids), val[2*nnz] (complex128).
- * Synchronizes the stream.  Any pointer may be NULL. */
+/* CSR out of the library: row_ptr[NT+1], col[nnz] (global node ids), val[2*nnz]
+ * (complex128), each into host or device memory of the context's device (copied with
+ * unified addressing).  Synchronizes the stream.  Any pointer may be NULL. */
 lcq_status lcq_corr_export(lcq_corr* corr, int64_t* row_ptr, int32_t* col, double* val);
 
 /* Per-patch far order q_j and annulus order (0: no annulus targets) to host
@@ -330,6 +331,17 @@ lcq_status lcq_adaptive_corrections_noalloc(int deg, const double* y, int64_t n_
  * takes about a second; LCQ_ERR_ARG for a null out or n_out < 1, LCQ_ERR_CUDA on any
  * CUDA failure (entries that were measured are kept). */
 lcq_status lcq_pipe_peaks(int device, double* out, int n_out);
+
+/* Device self-checks of the adaptive kernel's arithmetic (no counterpart in the paper).
+ * Writes host out[n_out], up to 3 values (-1 where not measured):
+ *   [0] max |sin - sin_ref|, |cos - cos_ref| of the table-driven sincos against CUDA's
+ *       sincos over 4M arguments in [-3000, 3000] and around the table's breakpoints;
+ *   [1] degree 6 and [2] degree 10: max over every output of |tensor-core contraction -
+ *       FP64 contraction| / sum_q |a_q| |b_q| for random kernel-like rows (12 decades of
+ *       magnitude, random phases) and basis-like columns at their bounds.
+ * Allocates 32 bytes of device memory and a private stream for the call; LCQ_ERR_ARG for a
+ * null out or n_out < 1, LCQ_ERR_CUDA on any CUDA failure. */
+lcq_status lcq_selftest(int device, double* out, int n_out);
 
 const char* lcq_status_string(lcq_status s);
 const char* lcq_last_error(const lcq_ctx* ctx);

@@ -20,7 +20,8 @@ LIB = os.path.join(BUILD, "liblcq.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lcq_kernels.cu", "lcq_adjoint.cu", "lcq_nearlist.cu", "lcq_api.cpp",
-           "lcq_tables.cpp", "lcq_noalloc.cu", "lcq_peaks.cu"]
+           "lcq_tables.cpp", "lcq_noalloc.cu", "lcq_peaks.cu",
+           "lcq_selftest.cu"]
 
 
 def _nvcc() -> str:

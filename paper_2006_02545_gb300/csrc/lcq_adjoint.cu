@@ -370,10 +370,7 @@ struct AdaptiveGradL {
                   const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
                   int A_max, int levels, int grid, int* status, int* sched, double mix,
                   const GradArgs& ga) {
-    using C = Cfg<D>;
-    const size_t sm = sizeof(double) * (C::n * 3 + 64 / 2 + 4 * 32 + C::WS) +
-                      sizeof(SegMap) * 4 + 1024 + 64 * sizeof(int) +
-                      (mix > 0.0 ? C::WS_F32 * sizeof(double) : 0);
+    const size_t sm = adaptive_smem_bytes<D>();
     cudaFuncSetAttribute(k_adaptive<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     AdaptiveWS w{stride, A_max, levels};
     cudaMemsetAsync(sched, 0, sizeof(int), lc.stream);

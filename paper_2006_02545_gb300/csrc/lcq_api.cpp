@@ -1036,10 +1036,11 @@ lcq_status lcq_corr_export(lcq_corr* c, int64_t* row_ptr, int32_t* col, double* 
   CK(cudaSetDevice(c->device));
   const lcq_near* nr = c->near;
   cudaStream_t st = c->stream;
+  // cudaMemcpyDefault: the destinations may be host or device memory (unified addressing)
   if (row_ptr)
-    CK(cudaMemcpyAsync(row_ptr, nr->row_ptr, (nr->n_targets + 1) * 8, cudaMemcpyDeviceToHost, st));
-  if (col && c->nnz) CK(cudaMemcpyAsync(col, nr->col, c->nnz * 4, cudaMemcpyDeviceToHost, st));
-  if (val && c->nnz) CK(cudaMemcpyAsync(val, c->val, c->nnz * 16, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(row_ptr, nr->row_ptr, (nr->n_targets + 1) * 8, cudaMemcpyDefault, st));
+  if (col && c->nnz) CK(cudaMemcpyAsync(col, nr->col, c->nnz * 4, cudaMemcpyDefault, st));
+  if (val && c->nnz) CK(cudaMemcpyAsync(val, c->val, c->nnz * 16, cudaMemcpyDefault, st));
   CK(cudaStreamSynchronize(st));
   return LCQ_OK;
 }

@@ -9,6 +9,7 @@
 
 #include "lcq_device.cuh"
 #include "lcq_launch.h"
+#include "lcq_tc.cuh"
 
 namespace lcq {
 
@@ -269,6 +270,312 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
   }
 }
 
+// Moments with the rounding envelope, as block_moments<D, true>, for the adaptive walk:
+// I[i][seg][nm] = sum_{q in seg} w_q K(x_i, X_q) J_q K_nm(u_q, v_q) and
+// eout[i * nseg + seg] = sum_q of the kernel's rounding envelope (FP32 sums), with the
+// contraction over the nodes on the tensor cores by the exact NS-slice split (lcq_tc.cuh):
+// NS = 8 for FP64 kernel values, NS = 5 for the mixed form's FP32 ones.
+// Chunks never straddle a segment: segment sg's Q nodes are cut into parts of at most
+// TcCfg::CH nodes, each padded with zero columns to a multiple of 16 (the MMA depth), and
+// each chunk's contribution is assembled in FP64 and written (first part) or added.
+// Per chunk: (1) geometry, thread per node: X, N w, J w and the basis row (FP64); (2) per
+// tile of 8 targets: kernel values and envelopes, thread per (target, node); (3) one warp
+// per target splits the Re and Im rows of its kernel values on their own power-of-two
+// scales into NS f16 slices; (4) one warp per n-tile of 8 basis columns slices its basis
+// values (fixed per-column bounds) into MMA fragments and accumulates the NS diagonals over
+// the chunk's 16-node steps with mma.sync, then assembles and stores the 8 x 8 complex
+// block.  smb: TcCfg<D>::BYTES of shared memory (16-byte aligned); sct: the sincos table.
+template <int NS>
+__device__ __forceinline__ void split_store(const uint32_t* signs2, const unsigned long long* M,
+                                            int nv, uint16_t* dst, int AST) {
+  // nv values (2 or 4) of one row at consecutive columns; dst: slice 0 of this row
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    uint16_t* d = dst + (size_t)i * 16 * AST;
+    const uint32_t w0 = half2_ints(slice_of<NS>(M[0], i), slice_of<NS>(M[1], i), signs2[0]);
+    if (nv == 4) {
+      const uint32_t w1 = half2_ints(slice_of<NS>(M[2], i), slice_of<NS>(M[3], i), signs2[1]);
+      *reinterpret_cast<uint2*>(d) = make_uint2(w0, w1);
+    } else {
+      *reinterpret_cast<uint32_t*>(d) = w0;
+    }
+  }
+}
+
+template <int NS, int VPL, class V>
+__device__ __forceinline__ void split_row_pair(const V* re, const V* im, bool on, int nt_ok,
+                                               uint16_t* Asl, int AST, int t, int q0,
+                                               int* rowE) {
+  // exponents of the Re and Im rows (max over the warp's values)
+  int fr = 0, fi = 0;
+  bool bad = false;
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    const int a = exp_field(re[v]), b = exp_field(im[v]);
+    bad = bad || exp_nonfinite(a, V()) || exp_nonfinite(b, V());
+    fr = max(fr, a);
+    fi = max(fi, b);
+  }
+  fr = (int)__reduce_max_sync(0xffffffffu, (unsigned)fr);
+  fi = (int)__reduce_max_sync(0xffffffffu, (unsigned)fi);
+  bad = __any_sync(0xffffffffu, bad);
+  const int Er = exp_bound(fr, V()), Ei = exp_bound(fi, V());
+  (void)nt_ok;
+  if ((threadIdx.x & 31) == 0) {
+    rowE[t] = !on ? 0 : (bad ? kPoisonExp : Er);
+    rowE[t + 8] = !on ? 0 : (bad ? kPoisonExp : Ei);
+  }
+  unsigned long long Mr[VPL], Mi[VPL];
+  uint32_t sr[VPL / 2], si[VPL / 2];
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    Mr[v] = on ? fix_mag<NS>(re[v], Er) : 0ull;
+    Mi[v] = on ? fix_mag<NS>(im[v], Ei) : 0ull;
+  }
+#pragma unroll
+  for (int v = 0; v < VPL / 2; ++v) {
+    sr[v] = sign_bits(re[2 * v], re[2 * v + 1]);
+    si[v] = sign_bits(im[2 * v], im[2 * v + 1]);
+  }
+  split_store<NS>(sr, Mr, VPL, Asl + (size_t)t * AST + q0, AST);
+  split_store<NS>(si, Mi, VPL, Asl + (size_t)(t + 8) * AST + q0, AST);
+}
+
+// One n-tile (basis columns 8 ct .. 8 ct + 7) of the chunk: diagonals over the k-steps, then
+// the assembled complex 8 x 8 block into the outputs.
+template <int D, int NS, class OR>
+__device__ __forceinline__ void tc_tile(const double* Bd, const uint16_t* Asl, const int* rowE,
+                                        int ct, int ncp, int nt, int t0, int sg, bool first,
+                                        OR orow) {
+  using C = TcCfg<D>;
+  constexpr int n = C::n;
+  const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+  const int col = ct * 8 + g;
+  const int Eb = col < n ? c_kwexp[col] : 0;
+  float acc[NS][4];
+#pragma unroll
+  for (int d = 0; d < NS; ++d) acc[d][0] = acc[d][1] = acc[d][2] = acc[d][3] = 0.0f;
+  const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
+  for (int k0 = 0; k0 < ncp; k0 += 16) {
+    const double b0 = Bd[(k0 + 2 * c) * C::BST + col];
+    const double b1 = Bd[(k0 + 2 * c + 1) * C::BST + col];
+    const double b2 = Bd[(k0 + 2 * c + 8) * C::BST + col];
+    const double b3 = Bd[(k0 + 2 * c + 9) * C::BST + col];
+    const unsigned long long M0 = fix_mag<NS>(b0, Eb), M1 = fix_mag<NS>(b1, Eb);
+    const unsigned long long M2 = fix_mag<NS>(b2, Eb), M3 = fix_mag<NS>(b3, Eb);
+    const uint32_t s01 = sign_bits(b0, b1), s23 = sign_bits(b2, b3);
+    uint32_t bf[NS][2];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      bf[j][0] = half2_ints(slice_of<NS>(M0, j), slice_of<NS>(M1, j), s01);
+      bf[j][1] = half2_ints(slice_of<NS>(M2, j), slice_of<NS>(M3, j), s23);
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+      uint32_t af[4];
+      ldsm_x4(af, Asl + ((size_t)i * 16 + arow) * C::AST + k0 + acol);
+#pragma unroll
+      for (int j = 0; j < NS - i; ++j) mma_f16_16816(acc[i + j], af, bf[j]);
+    }
+  }
+  if (g < nt) {
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      const int nm = ct * 8 + 2 * c + cc;
+      if (nm >= n) continue;
+      const int e2 = c_kwexp[nm];
+      const double re = assemble<NS>(acc, cc, rowE[g] + e2);
+      const double im = assemble<NS>(acc, 2 + cc, rowE[g + 8] + e2);
+      cplx* dst = reinterpret_cast<cplx*>(orow(t0 + g)) + (int64_t)sg * n + nm;
+      if (first) {
+        dst->re = re;
+        dst->im = im;
+      } else {
+        dst->re += re;
+        dst->im += im;
+      }
+    }
+  }
+}
+
+template <int D, class TA, class OR>
+__device__ void block_moments_tc(const double* cf, const double* cfd, const double* __restrict__ ru,
+                                 const double* __restrict__ rv, const double* __restrict__ rw,
+                                 int Q, const SegMap* segs, int nseg, const TA& ta, int T, OR orow,
+                                 const KernelParams& kp, unsigned char* smb, const double* cen,
+                                 double R, double* eout, bool mixed) {
+  using C = TcCfg<D>;
+  constexpr int n = C::n;
+  double* Xs = reinterpret_cast<double*>(smb + C::OFF_X);
+  double* Ns = reinterpret_cast<double*>(smb + C::OFF_N);
+  double* Js = reinterpret_cast<double*>(smb + C::OFF_J);
+  double* Bd = reinterpret_cast<double*>(smb + C::OFF_B);
+  cplx* Gs = reinterpret_cast<cplx*>(smb + C::OFF_G);
+  float2* Gf = reinterpret_cast<float2*>(smb + C::OFF_G);
+  uint16_t* Asl = reinterpret_cast<uint16_t*>(smb + C::OFF_G);
+  double* rows = reinterpret_cast<double*>(smb + C::OFF_G);
+  float* Ef = reinterpret_cast<float*>(smb + C::OFF_E);
+  float* Jf = reinterpret_cast<float*>(smb + C::OFF_JF);
+  float* Nf = reinterpret_cast<float*>(smb + C::OFF_NF);
+  int* rowE = reinterpret_cast<int*>(smb + C::OFF_ROWE);
+  double* tx = reinterpret_cast<double*>(smb + C::OFF_TX);
+  double* tn = tx + 3 * C::TT;
+  const KernelParamsF kf = to_f32(kp);
+  const float fR = f32_bits(R);
+  const float escale = mixed ? (float)(kF32Floor / kRoundingFloor) : 1.0f;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // conical rules: rows of mr nodes sharing v (see block_moments)
+  const int mr = (int)lrint(sqrt((double)Q));
+  bool by_rows = mr * mr == Q;
+  for (int sg = 0; sg < nseg; ++sg) by_rows = by_rows && segs[sg].e1y == 0.0;
+  using RW = KwRow<D>;
+  constexpr int kRowMax = C::G_BYTES / 8 / RW::size;
+  const int nparts = (Q + C::CH - 1) / C::CH;
+  const int psize = (Q + nparts - 1) / nparts;
+  for (int sg = 0; sg < nseg; ++sg) {
+    const SegMap S = segs[sg];
+    for (int part = 0; part < nparts; ++part) {
+      const int l0 = part * psize;
+      const int nq = min(psize, Q - l0);
+      if (nq <= 0) break;
+      const int ncp = (nq + 15) & ~15;
+      const int row0 = by_rows ? l0 / mr : 0;
+      const int nrow = by_rows ? (l0 + nq - 1) / mr - row0 + 1 : 0;
+      const bool use_rows = by_rows && nrow <= kRowMax;
+      __syncthreads();
+      if (use_rows) {
+        for (int e = threadIdx.x; e < nrow * (D + 1); e += blockDim.x) {
+          const int rr = e / (D + 1), m = e - rr * (D + 1);
+          const int l = (row0 + rr) * mr;
+          kw_row_factors<D>(S.ay + ru[l] * S.e1y + rv[l] * S.e2y, m, cf, cfd, rows + rr * RW::size);
+        }
+        __syncthreads();
+      }
+      for (int ql = threadIdx.x; ql < ncp; ql += blockDim.x) {
+        double* Bq = Bd + ql * C::BST;
+        if (ql < nq) {
+          const int l = l0 + ql;
+          const double r0 = ru[l], r1 = rv[l];
+          const double u = S.ax + r0 * S.e1x + r1 * S.e2x;
+          const double w = rw[l] * S.det;
+          double X[3], Xu[3], Xv[3], Nn[3];
+          if (use_rows) {
+            kw_geometry_row<D>(u, rows + (l / mr - row0) * RW::size, X, Xu, Xv, Bq);
+          } else {
+            const double v = S.ay + r0 * S.e1y + r1 * S.e2y;
+            kw_geometry_proj<D>(u, v, cf, cfd, X, Xu, Xv, Bq);
+          }
+          cross3(Xu, Xv, Nn);
+          const double Jw = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]) * w;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            Xs[c * C::CH + ql] = X[c];
+            Ns[c * C::CH + ql] = Nn[c] * w;
+          }
+          Js[ql] = Jw;
+          Jf[ql] = f32_bits(Jw);
+          if (mixed) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Nf[c * C::CH + ql] = (float)(Nn[c] * w);
+            Jf[ql] = (float)Jw;
+          }
+        } else {
+#pragma unroll 1
+          for (int nm = 0; nm < n; ++nm) Bq[nm] = 0.0;
+        }
+#pragma unroll
+        for (int nm = n; nm < C::NP; ++nm) Bq[nm] = 0.0;
+      }
+      __syncthreads();
+      for (int t0 = 0; t0 < T; t0 += C::TT) {
+        const int nt = min(C::TT, T - t0);
+        if (threadIdx.x < nt) {
+          double* xp = tx + 3 * threadIdx.x;
+          ta.pos(t0 + threadIdx.x, xp);
+          xp[0] -= cen[0];
+          xp[1] -= cen[1];
+          xp[2] -= cen[2];
+          if (kp.kind == 3) ta.nrm(t0 + threadIdx.x, xp, tn + 3 * threadIdx.x);
+        }
+        __syncthreads();
+        // (2) kernel values and envelopes; zero padding columns
+        for (int e = threadIdx.x; e < nt * ncp; e += blockDim.x) {
+          const int i = e / ncp, ql = e - i * ncp;
+          float ev = 0.0f;
+          if (mixed) {
+            float2 g = make_float2(0.0f, 0.0f);
+            if (ql < nq) {
+              const double d0 = tx[3 * i] - Xs[ql], d1 = tx[3 * i + 1] - Xs[C::CH + ql],
+                           d2 = tx[3 * i + 2] - Xs[2 * C::CH + ql];
+              const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+              if (r2 > 0.0)
+                g = kernel_eval_f32f(kp, kf, d0, d1, d2, r2, Nf[ql], Nf[C::CH + ql],
+                                     Nf[2 * C::CH + ql], Jf[ql], fR, &ev);
+            }
+            Gf[i * C::CH + ql] = g;
+          } else {
+            cplx g = {0.0, 0.0};
+            if (ql < nq)
+              g = kernel_eval_tc(kp, kf, g_sct, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql],
+                                 Xs[C::CH + ql], Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql],
+                                 Ns[2 * C::CH + ql], Js[ql], Jf[ql], fR, &ev, tn + 3 * i);
+            Gs[i * C::CH + ql] = g;
+          }
+          Ef[i * C::CH + ql] = ev;
+        }
+        __syncthreads();
+        // envelope sums, one warp per target
+        if (warp < nt) {
+          float es = 0.0f;
+          for (int ql = lane; ql < nq; ql += 32) es += Ef[warp * C::CH + ql];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) es += __shfl_xor_sync(0xffffffffu, es, o);
+          if (lane == 0) {
+            double* ed = eout + (int64_t)(t0 + warp) * nseg + sg;
+            const double v = (double)(es * escale);
+            *ed = part == 0 ? v : *ed + v;
+          }
+        }
+        // (3) split the kernel rows: warp w owns target w (rows w: Re, w + 8: Im); values
+        // are read before the barrier because the slices overwrite them
+        constexpr int VPL = C::CH / 32;
+        const int q0 = lane * VPL;
+        const bool on = warp < nt;
+        if (mixed) {
+          float re[VPL], im[VPL];
+#pragma unroll
+          for (int v = 0; v < VPL; ++v) {
+            const float2 g = (on && q0 + v < ncp) ? Gf[warp * C::CH + q0 + v] : make_float2(0.0f, 0.0f);
+            re[v] = g.x;
+            im[v] = g.y;
+          }
+          __syncthreads();
+          if (warp < C::TT) split_row_pair<5, VPL>(re, im, on, nt, Asl, C::AST, warp, q0, rowE);
+        } else {
+          double re[VPL], im[VPL];
+#pragma unroll
+          for (int v = 0; v < VPL; ++v) {
+            const cplx g = (on && q0 + v < ncp) ? Gs[warp * C::CH + q0 + v] : cplx{0.0, 0.0};
+            re[v] = g.re;
+            im[v] = g.im;
+          }
+          __syncthreads();
+          if (warp < C::TT) split_row_pair<8, VPL>(re, im, on, nt, Asl, C::AST, warp, q0, rowE);
+        }
+        __syncthreads();
+        // (4) tensor-core contraction, one warp per n-tile
+        for (int ct = warp; ct < C::NTILE; ct += nwarp) {
+          if (mixed)
+            tc_tile<D, 5>(Bd, Asl, rowE, ct, ncp, nt, t0, sg, part == 0, orow);
+          else
+            tc_tile<D, 8>(Bd, Asl, rowE, ct, ncp, nt, t0, sg, part == 0, orow);
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
 template <int D>
 __device__ __forceinline__ void load_coef(const double* __restrict__ coef, int64_t off, double* cf) {
   constexpr int n = (D + 1) * (D + 2) / 2;
@@ -472,6 +779,14 @@ struct AdaptiveWS {
   int A_max, levels;
 };
 
+// Dynamic shared memory of k_adaptive<D>: chart coefficients, the four child maps, scan
+// scratch, the walk's stack, alignment, and the tensor-core moment workspace.
+template <int D>
+constexpr size_t adaptive_smem_bytes() {
+  return sizeof(double) * 3 * Cfg<D>::n + sizeof(SegMap) * 4 + 64 * sizeof(int) +
+         4 * 32 * sizeof(unsigned long long) + 128 + TcCfg<D>::BYTES;
+}
+
 // Patches are taken dynamically from `plist` (ordered by decreasing number of adaptive
 // targets) through the counter *sched, which the caller zeroes before the launch.
 template <int D, bool GRAD = false>
@@ -495,7 +810,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
   SegMap* segs = reinterpret_cast<SegMap*>(cf + n * 3);
   int* ism = reinterpret_cast<int*>(segs + 4);  // [64]: scan scratch + misc
   unsigned long long* stk = reinterpret_cast<unsigned long long*>(ism + 64);  // [4 * 32]
-  double* ws = reinterpret_cast<double*>(stk + 4 * 32);
+  // tensor-core moment workspace, 128-byte aligned (ldmatrix needs 16)
+  unsigned char* smb = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(stk + 4 * 32) + 127) & ~static_cast<uintptr_t>(127));
+  double* ws = reinterpret_cast<double*>(smb);
   // per-block global workspace
   unsigned char* wb = work + (int64_t)blockIdx.x * wsd.stride;
   const int A_max = wsd.A_max;
@@ -566,9 +884,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
     __syncthreads();
     if (leaf_order > 0) {
       TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, dv.tnrm};
-      block_moments<D>(cf, cfdp, ru, rv, rw, Q, segs, 1, ta, A,
-                       [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, 4 * n, kps, ws,
-                       dv.cen + 3 * j);
+      block_moments_tc<D>(cf, cfdp, ru, rv, rw, Q, segs, 1, ta, A,
+                          [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, kps, smb,
+                          dv.cen + 3 * j, Rj, tmpE, mixj);
     }
     // DFS stack entries: level (8 bits) | child (2 bits) | path (2 bits per level) << 16
     int sp = 0;
@@ -618,9 +936,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
       __syncthreads();
       // children moments of every target in S
       TgtAdaptive ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, ST, dv.tnrm};
-      block_moments<D, true>(cf, cfdp, ru, rv, rw, Q, segs, 4, ta, S,
-                             [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, 4 * n, kps,
-                             ws, dv.cen + 3 * j, Rj, tmpE, mixj);
+      block_moments_tc<D>(cf, cfdp, ru, rv, rw, Q, segs, 4, ta, S,
+                          [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, kps, smb,
+                          dv.cen + 3 * j, Rj, tmpE, mixj);
       __syncthreads();
       my_tests += S;
       my_nodes += (long long)S * 4 * Q;

@@ -38,20 +38,48 @@ __host__ __device__ __forceinline__ void jacobi_coef(int a, int b, double* c1, d
 // unrolled; same values as jacobi_coef.  Filled with c_kw by upload_kw_tables.
 static __constant__ double c_jac[(kMaxDeg + 1) * (kMaxDeg + 1) * 3];
 
-// Fills c_kw and c_jac of the calling translation unit (stream-ordered).
+// Exponents E_nm with |K_nm| < 2^E_nm on T0: |(1-v)^m P_m| <= 1 there and, for Jacobi
+// polynomials with max(alpha, beta) >= -1/2, max |P^{(0,b)}_a| on [-1, 1] = binom(a + b, a)
+// (Szego, Orthogonal Polynomials, Thm. 7.32.1), so |K_nm| <= c_nm binom(n + m + 1, n - m).
+// The split-precision contraction scales basis column nm by 2^-E_nm.
+static __constant__ int c_kwexp[kMaxBasis];
+
+// (cos, sin)(2 pi j / 256), j = 0..255: the table of sincos_tab (lcq_tc.cuh).
+static __device__ double2 g_sct[256];
+
+// Fills c_kw, c_jac, c_kwexp and g_sct of the calling translation unit (stream-ordered).
 static inline cudaError_t upload_kw_tables(cudaStream_t st) {
   double c[kMaxBasis], jc[(kMaxDeg + 1) * (kMaxDeg + 1) * 3] = {};
+  int ke[kMaxBasis];
+  double2 sct[256];
   for (int nn = 0; nn <= kMaxDeg; ++nn)
-    for (int m = 0; m <= nn; ++m) c[nn * (nn + 1) / 2 + m] = sqrt(2.0 * (2 * m + 1) * (nn + 1));
+    for (int m = 0; m <= nn; ++m) {
+      const int idx = nn * (nn + 1) / 2 + m;
+      c[idx] = sqrt(2.0 * (2 * m + 1) * (nn + 1));
+      double binom = 1.0;  // binom(n + m + 1, n - m)
+      for (int i = 1; i <= nn - m; ++i) binom = binom * (2 * m + 1 + i) / i;
+      int e2 = 0;
+      frexp(c[idx] * binom * (1.0 + 1e-12), &e2);
+      ke[idx] = e2;
+    }
   for (int m = 0; m <= kMaxDeg; ++m) {
     for (int a = 0; a <= kMaxDeg; ++a) {
       double* q = jc + (m * (kMaxDeg + 1) + a) * 3;
       jacobi_coef(a, 2 * m + 1, q, q + 1, q + 2);
     }
   }
+  for (int j = 0; j < 256; ++j) {
+    const double a = 2.0 * M_PI * j / 256.0;
+    sct[j] = make_double2(cos(a), sin(a));
+  }
   cudaError_t e = cudaMemcpyToSymbolAsync(c_kw, c, sizeof(c), 0, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyToSymbolAsync(c_jac, jc, sizeof(jc), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyToSymbolAsync(c_kwexp, ke, sizeof(ke), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyToSymbolAsync(g_sct, sct, sizeof(sct), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the sources live on this stack
   return e;
 }
 

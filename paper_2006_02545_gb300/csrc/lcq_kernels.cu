@@ -916,8 +916,7 @@ struct AdaptiveL {
                   const void* I_smooth, void* I_near, int32_t* leaves, void* work,
                   int64_t stride, int A_max, int levels, int grid, int* status, int* sched,
                   double mix) {
-    const size_t sm = moments_smem_bytes<D>(64 / 2 + 4 * 32) + 64 * sizeof(int) +
-                      (mix > 0.0 ? Cfg<D>::WS_F32 * sizeof(double) : 0);
+    const size_t sm = adaptive_smem_bytes<D>();
     set_smem(k_adaptive<D>, sm);
     AdaptiveWS w{stride, A_max, levels};
     ++*lc.launches;
@@ -1089,7 +1088,7 @@ int adaptive_blocks_per_sm(int d) {
   switch (d) {
 #define LCQ_CASE(D)                                                                          \
   case D: {                                                                                  \
-    const size_t sm = moments_smem_bytes<D>(64 / 2 + 4 * 32) + 64 * sizeof(int);             \
+    const size_t sm = adaptive_smem_bytes<D>();                                              \
     set_smem(k_adaptive<D>, sm);                                                             \
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adaptive<D>, kThreads, sm);         \
     break;                                                                                   \

@@ -1,0 +1,259 @@
+// Building blocks of the split-precision tensor-core contraction and the lean FP64 kernel
+// evaluation used by the adaptive near integration (Sec. 4.3).
+//
+// On GB300 the FP64 pipe retires 2 FMA per clock per SM (measured 1.26 TFLOP/s), the FP32
+// pipe 128 and the warp-level f16 tensor-core MMA about 0.47 m16n8k16 per clock per SM
+// (measured 602 TFLOP/s).  The dense part of the adaptive integration, the contraction of
+// kernel values (targets x leaf nodes) with basis values (leaf nodes x n), is therefore
+// done exactly on the tensor cores: each FP64 operand is written as a sum of NS slices of
+// 7 bits on a common power-of-two scale (the row's for the kernel values, a fixed per-column
+// bound for the basis values; the Ozaki splitting of Ozaki, Ogita, Oishi and Rump,
+// Numer. Algorithms 59, 2012), every product of two slices (< 2^14) and every sum of them
+// over a chunk of at most 128 nodes and over the at most 8 slice pairs of one diagonal stays
+// below 2^24, so the f16 MMA with FP32 accumulators computes each diagonal exactly; the
+// diagonals are combined in 64-bit integers and converted to FP64 once per chunk.  With
+// NS = 8 (56 bits per operand, diagonals i + j <= 7) the result matches an FP64 contraction
+// to within a few units of 2^-53 relative to max|kernel| * bound|basis| per node.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lcq_device.cuh"
+
+namespace lcq {
+
+constexpr int kSliceBits = 7;
+constexpr int kPoisonExp = 0x40000000;  // row exponent marking a non-finite kernel value
+
+// Shared-memory layout of the tensor-core moment engine for degree D (byte offsets).
+template <int D>
+struct TcCfg {
+  static constexpr int n = (D + 1) * (D + 2) / 2;
+  static constexpr int NP = (n + 7) / 8 * 8;       // basis columns padded to MMA n-tiles of 8
+  static constexpr int NTILE = NP / 8;
+  static constexpr int CH = D <= 8 ? 128 : 64;     // padded nodes per chunk (multiple of 16)
+  static constexpr int BST = NP + 4;               // FP64 basis row stride: conflict-free B loads
+  static constexpr int TT = 8;                     // targets per tile: 16 MMA rows (Re, then Im)
+  static constexpr int AST = CH + 8;               // halves per A-slice row: conflict-free ldmatrix
+  static constexpr int NSMAX = 8;
+  static constexpr int OFF_X = 0;                                  // Xs[3][CH] double
+  static constexpr int OFF_N = OFF_X + 3 * CH * 8;                 // Ns[3][CH] double (N w)
+  static constexpr int OFF_J = OFF_N + 3 * CH * 8;                 // Js[CH] double (J w)
+  static constexpr int OFF_B = OFF_J + CH * 8;                     // Bd[CH][BST] double
+  static constexpr int OFF_G = OFF_B + CH * BST * 8;               // Gs / Asl / row factors
+  static constexpr int G_A = NSMAX * 16 * AST * 2;
+  static constexpr int G_BYTES = G_A > TT * CH * 16 ? G_A : TT * CH * 16;
+  static constexpr int OFF_E = OFF_G + G_BYTES;                    // Ef[TT][CH] float
+  static constexpr int OFF_JF = OFF_E + TT * CH * 4;               // Jf[CH] float
+  static constexpr int OFF_NF = OFF_JF + CH * 4;                   // Nf[3][CH] float (mixed)
+  static constexpr int OFF_ROWE = OFF_NF + 3 * CH * 4;             // rowE[16] int
+  static constexpr int OFF_TX = (OFF_ROWE + 16 * 4 + 15) / 16 * 16;  // tx[3 TT], tn[3 TT] double
+  static constexpr int BYTES = OFF_TX + 6 * TT * 8;
+};
+
+// |x| 2^(7 NS - E) rounded to the nearest integer, for |x| < 2^E: below 2^(7 NS).  Zero,
+// subnormal and non-finite x give 0 (non-finite values are flagged by the caller).
+template <int NS>
+__device__ __forceinline__ unsigned long long fix_mag(double x, int E) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0 || ex == 0x7ff) return 0ull;
+  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;  // 53 bits
+  const int sh = 1075 + E - ex - kSliceBits * NS;
+  unsigned long long M;
+  if (sh <= 0) {
+    M = m << (-sh);
+  } else {
+    if (sh >= 54) return 0ull;
+    M = (m + (1ull << (sh - 1))) >> sh;
+  }
+  const unsigned long long top = (1ull << (kSliceBits * NS)) - 1ull;
+  return M < top ? M : top;
+}
+template <int NS>
+__device__ __forceinline__ unsigned long long fix_mag(float x, int E) {
+  const unsigned b = __float_as_uint(x);
+  const int ex = (int)((b >> 23) & 0xff);
+  if (ex == 0 || ex == 0xff) return 0ull;
+  const unsigned long long m = (b & 0x7fffffu) | 0x800000u;  // 24 bits
+  const int sh = 150 + E - ex - kSliceBits * NS;
+  unsigned long long M;
+  if (sh <= 0) {
+    M = m << (-sh);
+  } else {
+    if (sh >= 25) return 0ull;
+    M = (m + (1ull << (sh - 1))) >> sh;
+  }
+  const unsigned long long top = (1ull << (kSliceBits * NS)) - 1ull;
+  return M < top ? M : top;
+}
+
+// Biased exponent field and the exponent E with |x| < 2^E for a normal number.
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7ff);
+}
+__device__ __forceinline__ int exp_field(float x) { return (int)((__float_as_uint(x) >> 23) & 0xff); }
+__device__ __forceinline__ int exp_bound(int field, double) { return field - 1022; }
+__device__ __forceinline__ int exp_bound(int field, float) { return field - 126; }
+__device__ __forceinline__ bool exp_nonfinite(int field, double) { return field == 0x7ff; }
+__device__ __forceinline__ bool exp_nonfinite(int field, float) { return field == 0xff; }
+
+// Slice i (0: most significant) of M, 7 bits.
+template <int NS>
+__device__ __forceinline__ unsigned slice_of(unsigned long long M, int i) {
+  return (unsigned)(M >> (kSliceBits * (NS - 1 - i))) & 0x7fu;
+}
+
+// Two f16 values (low half first) holding the integers c0, c1 in [0, 128) with the given
+// signs: 1024 + c is the f16 bit pattern 0x6400 | c, and subtracting 1024 is exact.
+__device__ __forceinline__ uint32_t half2_ints(unsigned c0, unsigned c1, uint32_t signs) {
+  const uint32_t w = (0x6400u | c0) | ((0x6400u | c1) << 16);
+  uint32_t r;
+  asm("sub.f16x2 %0, %1, %2;" : "=r"(r) : "r"(w), "r"(0x64006400u));
+  return r ^ signs;
+}
+__device__ __forceinline__ uint32_t sign_bits(double a, double b) {
+  return ((uint32_t)(__double2hiint(a) < 0) << 15) | ((uint32_t)(__double2hiint(b) < 0) << 31);
+}
+__device__ __forceinline__ uint32_t sign_bits(float a, float b) {
+  return ((__float_as_uint(a) >> 31) << 15) | ((__float_as_uint(b) >> 31) << 31);
+}
+
+// D += A B for one m16n8k16 tile: A row-major f16 (4 registers), B column-major f16 (2),
+// D FP32 (4).
+__device__ __forceinline__ void mma_f16_16816(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// The four 8x8 f16 matrices of an m16n8k16 A operand from shared memory; p is this lane's row
+// address (rows (lane & 7) + 8 ((lane >> 3) & 1), columns 8 (lane >> 4) of the 16x16 tile).
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+// FP64 value of one accumulator element: the diagonals d = 0..NS-1 (exact integers in FP32)
+// weighted 2^(-7 d), combined in 64-bit integers, times 2^(E - 14 - 7 (NS - 1)), E = Ea + Eb.
+template <int NS>
+__device__ __forceinline__ double assemble(const float (*acc)[4], int e, int E) {
+  if (E >= kPoisonExp / 2) return __longlong_as_double(0x7ff8000000000000ll);  // NaN
+  double v;
+  if (NS <= 5) {
+    long long s = 0;
+#pragma unroll
+    for (int d = 0; d < NS; ++d) s += (long long)__float2int_rn(acc[d][e]) * (1ll << (kSliceBits * (NS - 1 - d)));
+    v = (double)s;
+  } else {
+    constexpr int H = NS / 2;  // diagonals 0..H-1 in hi, H..NS-1 in lo
+    long long hi = 0, lo = 0;
+#pragma unroll
+    for (int d = 0; d < H; ++d) hi += (long long)__float2int_rn(acc[d][e]) * (1ll << (kSliceBits * (H - 1 - d)));
+#pragma unroll
+    for (int d = H; d < NS; ++d) lo += (long long)__float2int_rn(acc[d][e]) * (1ll << (kSliceBits * (NS - 1 - d)));
+    v = fma((double)hi, (double)(1ll << (kSliceBits * (NS - H))), (double)lo);
+  }
+  const int ue = E - 2 * kSliceBits - kSliceBits * (NS - 1);
+  if (ue < -1022) return 0.0;
+  return v * __longlong_as_double((long long)(ue + 1023) << 52);
+}
+
+// FP32 value of an FP64 number by its bits (truncating the mantissa; exponents outside the
+// FP32 range flush to zero or saturate): no FP64 instruction, for quantities that only set
+// a tolerance floor.
+__device__ __forceinline__ float f32_bits(double x) {
+  const long long b = __double_as_longlong(x);
+  const int hi = (int)(b >> 32);
+  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+  if (e <= 0) return 0.0f;
+  const unsigned s = (unsigned)hi & 0x80000000u;
+  if (e >= 255) return __uint_as_float(s | 0x7f800000u);
+  return __uint_as_float(s | ((unsigned)e << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
+}
+
+// sin and cos of th by table lookup and Taylor polynomials (the table method of Gal and
+// Bachelis, ACM TOMS 17, 1991): th = j (2 pi / 256) + t with j = rint(th 256 / (2 pi)) (the
+// 1.5 2^52 shifter) and |t| <= pi / 256; sin t and cos t by their Taylor series through t^7
+// and t^6 (truncation below 1.3e-20); then the angle-addition formulas with the table's
+// (cos, sin)(2 pi j / 256).  Valid for |th| < 2^20; larger arguments use sincos().
+__device__ __forceinline__ void sincos_tab(double th, const double2* __restrict__ tab, double* sn,
+                                           double* cs) {
+  if (!(fabs(th) < 1048576.0)) {
+    sincos(th, sn, cs);
+    return;
+  }
+  constexpr double kInvStep = 40.74366543152521;         // 256 / (2 pi)
+  constexpr double kStepHi = 0x1.921fb54p-6;             // 2 pi / 256 to 27 bits: j kStepHi exact
+  constexpr double kStepLo = 1.5501462182508444e-11;     // 2 pi / 256 - kStepHi
+  constexpr double kShift = 6755399441055744.0;                 // 1.5 2^52
+  const double y = fma(th, kInvStep, kShift);
+  const int j = __double2loint(y) & 255;
+  const double jd = y - kShift;
+  double t = fma(-jd, kStepHi, th);
+  t = fma(-jd, kStepLo, t);
+  const double z = t * t;
+  const double ps = fma(z, fma(z, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0);
+  const double s = fma(t * z, ps, t);
+  const double c = fma(z, fma(z, fma(z, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+  const double2 e = __ldg(tab + j);
+  *cs = fma(e.x, c, -e.y * s);
+  *sn = fma(e.y, c, e.x * s);
+}
+
+// kernel_eval (lcq_device.cuh) with the table sincos and the rounding envelope formed in FP32
+// from the FP64 quantities' bits: the same kernel value to a few ulps.  fJw: FP32 copy of
+// Jw; fR: FP32 patch radius.  r = 0 gives 0.
+__device__ __forceinline__ cplx kernel_eval_tc(const KernelParams& kp, const KernelParamsF& kf,
+                                               const double2* __restrict__ sct, double x0,
+                                               double x1, double x2, double X0, double X1,
+                                               double X2, double N0, double N1, double N2,
+                                               double Jw, float fJw, float fR, float* env,
+                                               const double* nx) {
+  if (kp.kind == 3) {
+    N0 = -nx[0] * Jw;
+    N1 = -nx[1] * Jw;
+    N2 = -nx[2] * Jw;
+  }
+  const double d0 = x0 - X0, d1 = x1 - X1, d2 = x2 - X2;
+  const double r2 = fma(d0, d0, fma(d1, d1, d2 * d2));
+  if ((__double_as_longlong(r2) << 1) == 0) {
+    *env = 0.0f;
+    return {0.0, 0.0};
+  }
+  const double rinv = rsqrt(r2);
+  const double r = r2 * rinv;
+  const double th = kp.kr * r;
+  double sn, cs;
+  sincos_tab(th, sct, &sn, &cs);
+  double ex = 0.07957747154594767 * rinv;  // 1/(4 pi r)
+  if (kp.ki != 0.0) ex *= exp(-kp.ki * r);
+  {
+    // |G| Jw (|beta| + |alpha| |1 - ik r| R / r^2) in FP32
+    const float fr = f32_bits(r), fri = 1.0f / fr;
+    const float f0 = fmaf(kf.ki, fr, 1.0f), f1 = kf.kr * fr;
+    const float fa = sqrtf(fmaf(f0, f0, f1 * f1));
+    *env = f32_bits(ex) * fJw * fmaf(kf.ea * fa * fR, fri * fri, kf.eb);
+  }
+  const double ec = ex * cs, es = ex * sn;
+  if (kp.kind == 0) return {ec * Jw, es * Jw};
+  const double rinv2 = rinv * rinv;
+  const double ndx = fma(N0, d0, fma(N1, d1, N2 * d2)) * rinv2;
+  // (1 - ikr) ndx with k = kr + i ki: ((1 + ki r) ndx, -kr r ndx)
+  double cr = kp.ki != 0.0 ? fma(kp.ki, r, 1.0) * ndx : ndx;
+  double ci = -th * ndx;
+  if (kp.kind == 2) {
+    const double tr = fma(kp.ar, cr, fma(-kp.ai, ci, kp.br * Jw));
+    const double ti = fma(kp.ar, ci, fma(kp.ai, cr, kp.bi * Jw));
+    cr = tr;
+    ci = ti;
+  }
+  return {fma(ec, cr, -es * ci), fma(ec, ci, es * cr)};
+}
+
+}  // namespace lcq

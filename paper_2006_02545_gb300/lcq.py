@@ -86,6 +86,7 @@ _sig = {
     "lcq_adaptive_corrections_noalloc": (C.c_int, [C.c_int, _vp, _i64, _vp, C.c_int, _d, _d, _d,
                                                    _d, _d, _d, C.c_int, _d, C.c_int, _vp, _vp]),
     "lcq_pipe_peaks": (C.c_int, [C.c_int, _vp, C.c_int]),
+    "lcq_selftest": (C.c_int, [C.c_int, _vp, C.c_int]),
     "lcq_status_string": (C.c_char_p, [C.c_int]),
     "lcq_last_error": (C.c_char_p, [_vp]),
 }
@@ -265,7 +266,8 @@ class Corrections:
         return int(nnz.value), int(nover.value)
 
     def export(self, n_targets: int, out=None):
-        """CSR (row_ptr, col, val) to host; `out` may supply preallocated (pinned) arrays."""
+        """CSR (row_ptr, col, val) to host; `out` may supply preallocated arrays: pinned host
+        arrays or device tensors (int64, int32, complex128)."""
         nnz = self.near.nnz
         if out is None:
             out = (np.empty(n_targets + 1, np.int64), np.empty(max(nnz, 1), np.int32),
@@ -273,7 +275,7 @@ class Corrections:
         rp, col, val = out
         self.ctx.check(_lib.lcq_corr_export(self.h, _ptr(rp), _ptr(col), _ptr(val)),
                        "lcq_corr_export")
-        return rp, col[:nnz], val[:nnz]
+        return (rp, None if col is None else col[:nnz], None if val is None else val[:nnz])
 
     def stats(self, n_patches: int):
         q = np.empty(n_patches, np.int32)
@@ -410,3 +412,13 @@ def pipe_peaks(device: int = 0) -> dict:
     if st:
         raise LCQError(st, "lcq_pipe_peaks")
     return dict(zip(PEAK_KEYS, out.tolist()))
+
+
+def selftest(device: int = 0) -> dict:
+    """Device self-checks (lcq_selftest): sincos table error, tensor-core contraction error."""
+    out = np.zeros(3)
+    st = _lib.lcq_selftest(device, _ptr(out), 3)
+    if st:
+        raise LCQError(st, "lcq_selftest")
+    return {"sincos_abs_err": float(out[0]), "tc_rel_err_d6": float(out[1]),
+            "tc_rel_err_d10": float(out[2])}
