@@ -254,7 +254,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     clocks = ClockSampler(local_rank) if rank == 0 else None
     step_ms, adapt_ms, stages, statuses, launches, nodes = [], [], [], [], 0, 0
-    tree_nodes = tests = 0
+    tree_nodes = tests = group_size = items = 0
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
@@ -275,6 +275,7 @@ def run_ours(args, rank, world, local_rank):
         nodes = int(cnt[1])
         tree_nodes = int(cnt[4])
         tests = int(cnt[0])
+        group_size, items = int(cnt[5]), int(cnt[6])
         corr.close()
         near.close()
     torch.cuda.synchronize()
@@ -338,8 +339,8 @@ def run_ours(args, rank, world, local_rank):
         sx = torch.from_numpy(sw.tgt_xyz).to(dev)
         stn = torch.from_numpy(sw.tgt_node).to(dev)
         sp = lcq.params(sw.eps, eta=sw.eta, test_dirs=W.test_directions(7))
-        times = []
-        for it in range(8):
+        times, sst = [], []
+        for it in range(12):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -347,13 +348,17 @@ def run_ours(args, rank, world, local_rank):
             corr = lcq.gen_corrections(ctx, sds, near, "S", 1.0, sp)
             e1.record(stream)
             st_s = ctx.sync()
-            if it >= 3:
+            if it >= 6:
                 times.append(e0.elapsed_time(e1))
+                sst.append(ctx.stage_times()[0])
             corr.close()
             near.close()
         small = {"workload": sw.name, "points": sw.surface.n_points,
                  "value": sw.surface.n_points / (statistics.median(times) / 1e3), "unit": UNIT,
-                 "ms_per_step": statistics.median(times), "status": st_s}
+                 "ms_per_step": statistics.median(times), "status": st_s,
+                 "stages_ms": dict(zip(["near_lists", "far_order", "smooth_annulus", "adaptive",
+                                        "self", "v2c"],
+                                       [statistics.median(x[i] for x in sst) for i in range(6)]))}
 
     # 64 independent tori in one batched generation against the same surfaces one by one
     batched = None
@@ -570,6 +575,7 @@ def run_ours(args, rank, world, local_rank):
                                         "sincos) + 4n contraction, n = 28",
                 "flops_per_launch": flops, "node_evals_per_launch": nodes,
                 "tests_per_launch": tests, "union_tree_nodes_per_launch": tree_nodes,
+                "work_items_per_launch": items, "targets_per_item_max": group_size,
                 "avg_launch_ms": a_ms}
     cpu = None
     if not args.no_cpu_baseline:

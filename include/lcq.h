@@ -271,7 +271,12 @@ lcq_status lcq_sync(lcq_ctx* ctx, int64_t timeout_ms);
  * [0] adaptive tests, [1] adaptive leaf-rule node evaluations (target x node),
  * [2] self node evaluations, [3] smooth/annulus node evaluations (target x node),
  * [4] union-tree nodes walked by the adaptive kernel (each evaluates the chart geometry
- * at 4Q leaf nodes), [5..7] zero.  Synchronizes. */
+ * at 4Q leaf nodes), [5] the largest number of adaptive targets per work item (the
+ * group size the context's tuner chose), [6] adaptive work items, [7] zero.  Synchronizes.
+ * The adaptive walk takes its work in items of at most a group size of targets of one
+ * patch; an online tuner in the context times each candidate size once per key (degree,
+ * kernel, tolerance decade, precision, size of the adaptive work) on the generations that
+ * use it and keeps the fastest.  Every result is the same for every group size. */
 lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out8);
 
 /* Stage timings of the last lcq_build_near_lists and lcq_gen_corrections on ctx, from

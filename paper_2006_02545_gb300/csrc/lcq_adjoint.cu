@@ -377,7 +377,7 @@ struct AdaptiveGradL {
     ++*lc.launches;
     k_adaptive<D, true><<<grid, kThreads, sm, lc.stream>>>(
         plist, count, dv, kp, eps, normV, leaf_order, max_depth, (const cplx*)I_smooth,
-        (cplx*)I_near, leaves, (unsigned char*)work, w, status, sched, mix, ga);
+        (cplx*)I_near, leaves, (unsigned char*)work, w, status, sched, mix, ga, nullptr, 0);
   }
 };
 

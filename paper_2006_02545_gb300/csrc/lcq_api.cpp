@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <chrono>
+#include <functional>
 #include <thread>
 #include <vector>
 
@@ -232,6 +233,10 @@ lcq_status lcq_create(lcq_ctx** out, int device, void* cuda_stream) {
 
 void lcq_destroy(lcq_ctx* ctx) {
   if (!ctx) return;
+  for (auto& kv : ctx->tune) {
+    if (kv.second.e0) cudaEventDestroy(kv.second.e0);
+    if (kv.second.e1) cudaEventDestroy(kv.second.e1);
+  }
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   for (int d = 0; d <= kMaxDeg; ++d) {
@@ -314,6 +319,8 @@ lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out8) {
   long long h[8];
   CK(cudaMemcpy(h, ctx->d_counters, sizeof(h), cudaMemcpyDeviceToHost));
   for (int i = 0; i < 8; ++i) out8[i] = h[i];
+  out8[5] = ctx->last_group_size;
+  out8[6] = ctx->last_items;
   return LCQ_OK;
 }
 
@@ -537,6 +544,11 @@ static lcq_status build_near_impl(lcq_ctx* ctx, const lcq_surface* surf, int n_g
       if (h_nad[j] > 0) l.push_back(j);
     std::stable_sort(l.begin(), l.end(), [&](int a, int b) { return h_nad[a] > h_nad[b]; });
     nr->ad_count[d] = (int)l.size();
+    for (int j : l) {
+      nr->ad_total[d] += h_nad[j];
+      nr->ad_max[d] = std::max(nr->ad_max[d], h_nad[j]);
+      nr->ad_nad_h[d].push_back(h_nad[j]);
+    }
     if (!l.empty()) {
       CK(dalloc(st, &nr->ad_list_dev[d], l.size()));
       CK(cudaMemcpyAsync(nr->ad_list_dev[d], l.data(), l.size() * sizeof(int),
@@ -739,9 +751,8 @@ static Dev make_dev(lcq_ctx* ctx, const lcq_near* nr, const int32_t* q, int ldI,
 
 // Per-block workspace of the adaptive kernel (sized by the largest adaptive set and the
 // depth cap) and its grid; grows ctx->work when needed.
-static cudaError_t adaptive_work(lcq_ctx* ctx, const lcq_near* nr, int levels, int64_t* stride_out,
-                                 int* grid_out) {
-  const int64_t A = nr->max_adaptive;
+static cudaError_t adaptive_work(lcq_ctx* ctx, const lcq_near* nr, int64_t A, int levels,
+                                 int64_t* stride_out, int* grid_out) {
   const int64_t n = nr->n_max;
   int64_t stride = A * n * 16 + A * 4 * n * 16 + (int64_t)levels * A * 4 * n * 16 +
                    (int64_t)levels * A * 4 + 2 * A * 4 + (int64_t)levels * 4 + 8 + A * 4 * 8 + 256;
@@ -765,6 +776,78 @@ static cudaError_t adaptive_work(lcq_ctx* ctx, const lcq_near* nr, int levels, i
   *stride_out = stride;
   *grid_out = agrid;
   return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------- tuner
+static bool mixed_form_hint(lcq_precision precision, lcq_kernel kernel, const lcq_near* nr,
+                            double eps0) {
+  return precision == LCQ_MIXED && kernel != LCQ_SP && (nr->grouped || eps0 >= kMixedMinEps);
+}
+
+// Tuner state of (degree, kernel, tolerance decade, precision, size class of the degree's
+// adaptive work, batch or not), with its candidates on first use.
+static lcq_tune& tune_state(lcq_ctx* ctx, const lcq_near* nr, int d, int kernel, double eps,
+                            bool mixed, int64_t slots) {
+  const int dec = (int)std::floor(std::log10(eps)) + 40;
+  int cls = 0;
+  while ((int64_t(1) << cls) < nr->ad_total[d] + 1 && cls < 62) ++cls;
+  const uint64_t key = (uint64_t)d | ((uint64_t)kernel << 4) | ((uint64_t)(dec & 63) << 8) |
+                       ((uint64_t)mixed << 14) | ((uint64_t)cls << 15) |
+                       ((uint64_t)nr->grouped << 21) | ((uint64_t)(nr->ad_max[d] > 16) << 22);
+  lcq_tune& tu = ctx->tune[key];
+  if (tu.cand.empty()) {
+    std::vector<int> c;
+    const int64_t amax = std::max<int64_t>(nr->ad_max[d], 1);
+    c.push_back((int)std::min<int64_t>(amax, 0x7fffffff));  // whole patches
+    for (int64_t ips : {1, 4, 16}) {
+      const int64_t want = ips * slots;
+      int64_t g = (nr->ad_total[d] + want - 1) / want;
+      g = std::max<int64_t>(16, (g + 7) / 8 * 8);
+      c.push_back((int)std::min<int64_t>(g, amax));
+    }
+    c.push_back((int)std::min<int64_t>(16, amax));
+    std::sort(c.begin(), c.end(), std::greater<int>());
+    c.erase(std::unique(c.begin(), c.end()), c.end());
+    tu.cand = c;
+    tu.ms_per.assign(c.size(), -1.0);
+    cudaEventCreate(&tu.e0);
+    cudaEventCreate(&tu.e1);
+  }
+  return tu;
+}
+
+// Collects a finished timing, then returns the candidate to use; *measure receives it when
+// this launch is to be timed (else -1).
+static int tune_pick(lcq_tune& tu, int* measure) {
+  *measure = -1;
+  if (tu.pending >= 0) {
+    const cudaError_t q = cudaEventQuery(tu.e1);
+    if (q == cudaSuccess) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, tu.e0, tu.e1) == cudaSuccess && tu.pend_pairs > 0.0) {
+        const double v = ms / tu.pend_pairs;
+        double& slot = tu.ms_per[tu.pending];
+        slot = slot < 0.0 ? v : std::min(slot, v);
+      }
+      tu.pending = -1;
+    } else if (q != cudaErrorNotReady) {
+      cudaGetLastError();
+      tu.pending = -1;
+    }
+  }
+  int best = -1;
+  for (size_t i = 0; i < tu.cand.size(); ++i) {
+    if (tu.ms_per[i] < 0.0) {
+      if (tu.pending < 0) {
+        *measure = (int)i;
+        return (int)i;
+      }
+      continue;
+    }
+    if (best < 0 || tu.ms_per[i] < tu.ms_per[best]) best = (int)i;
+  }
+  if (best >= 0) return best;
+  return tu.pending >= 0 ? tu.pending : 0;
 }
 
 static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, int n_phys,
@@ -892,7 +975,44 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   const int levels = params->max_depth;
   int64_t astride = 0;
   int agrid = 0;
-  if (nr->n_adaptive > 0) CK(adaptive_work(ctx, nr, levels, &astride, &agrid));
+  // Work groups of the adaptive walk: at most gsz[d] targets of one patch per item.  The
+  // size is chosen per degree by the context's online tuner (tune_group_size) among
+  // candidates that give about 1, 4 or 16 items per resident block, 16 targets, or whole
+  // patches; the grouping changes no result.
+  int gsz[kMaxDeg + 1] = {0};
+  int tune_meas[kMaxDeg + 1];
+  lcq_tune* tune_st[kMaxDeg + 1] = {nullptr};
+  int64_t A_eff = 0;
+  ctx->last_group_size = 0;
+  ctx->last_items = 0;
+  if (nr->n_adaptive > 0) {
+    int bps = 1;
+    for (int d = 1; d <= kMaxDeg; ++d)
+      if (nr->ad_count[d]) bps = std::max(bps, adaptive_blocks_per_sm(d));
+    const int64_t slots = (int64_t)ctx->num_sms * bps;
+    for (int d = 1; d <= kMaxDeg; ++d) {
+      tune_meas[d] = -1;
+      if (!nr->ad_count[d]) continue;
+      lcq_tune& tu = tune_state(ctx, nr, d, (int)kernel, eps0, mixed_form_hint(precision, kernel, nr, eps0),
+                                slots);
+      tune_st[d] = &tu;
+      const int pick = tune_pick(tu, &tune_meas[d]);
+      gsz[d] = tu.cand[pick];
+      A_eff = std::max<int64_t>(A_eff, gsz[d]);
+      ctx->last_group_size = std::max(ctx->last_group_size, gsz[d]);
+      for (int64_t a : nr->ad_nad_h[d]) ctx->last_items += (a + gsz[d] - 1) / gsz[d];
+    }
+    CK(adaptive_work(ctx, nr, A_eff, levels, &astride, &agrid));
+  }
+  int64_t *gng = nullptr, *gscr = nullptr, *ggofs[kMaxDeg + 1] = {nullptr};
+  if (nr->n_adaptive > 0) {
+    int maxc = 0;
+    for (int d = 1; d <= kMaxDeg; ++d) maxc = std::max(maxc, nr->ad_count[d]);
+    CK(dalloc(st, &gng, (size_t)maxc + 1));
+    CK(dalloc(st, &gscr, (size_t)2 * ((maxc + 1 + 1023) / 1024) + 64));
+    for (int d = 1; d <= kMaxDeg; ++d)
+      if (nr->ad_count[d]) CK(dalloc(st, &ggofs[d], (size_t)nr->ad_count[d] + 1));
+  }
   // Stages 1-4 and 6 depend on one another and run on the highest-priority stream; the
   // self weights (5) depend on none of them and run on the lowest-priority one from the
   // start, so their blocks fill what the chain leaves idle (the small far-order and
@@ -935,13 +1055,21 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   CK(cudaEventRecord(ctx->ev[4], sh));
   // 4. adaptive near moments (Sec. 4.3)
   if (nr->n_adaptive > 0) {
-    const int64_t A = nr->max_adaptive;
     for (int d = 1; d <= kMaxDeg; ++d) {
       if (!nr->ad_count[d]) continue;
-      launch_adaptive(d, lh, nr->ad_list_dev[d], nr->ad_count[d], dv, kp,
-                      eps0 * params->eps_loosen, ctx->deg[d].normV, params->leaf_order,
-                      params->max_depth, Is, In, c->leaves, ctx->work, astride, (int)A, levels,
-                      agrid, ctx->d_status, ctx->d_sched + d, mixed_form ? 2.0 : 0.0);
+      const int cnt = nr->ad_count[d];
+      lcq_tune* tu = tune_st[d];
+      if (tune_meas[d] >= 0) CK(cudaEventRecord(tu->e0, sh));
+      launch_group_offsets(lh, nr->ad_list_dev[d], cnt, nr->ad_ptr, gsz[d], gng, ggofs[d], gscr);
+      launch_adaptive(d, lh, nr->ad_list_dev[d], cnt, dv, kp, eps0 * params->eps_loosen,
+                      ctx->deg[d].normV, params->leaf_order, params->max_depth, Is, In,
+                      c->leaves, ctx->work, astride, (int)A_eff, levels, agrid, ctx->d_status,
+                      ctx->d_sched + d, mixed_form ? 2.0 : 0.0, ggofs[d], gsz[d]);
+      if (tune_meas[d] >= 0) {
+        CK(cudaEventRecord(tu->e1, sh));
+        tu->pending = tune_meas[d];
+        tu->pend_pairs = (double)nr->ad_total[d];
+      }
     }
     CK(cudaGetLastError());
   }
@@ -960,6 +1088,10 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   CK(cudaStreamWaitEvent(st, ctx->done, 0));
   dfree(st, ddirs);
   dfree(st, fscr);
+  if (gng) dfree(st, gng);
+  if (gscr) dfree(st, gscr);
+  for (int d = 1; d <= kMaxDeg; ++d)
+    if (ggofs[d]) dfree(st, ggofs[d]);
   cudaFreeAsync(Is, st);
   cudaFreeAsync(In, st);
   cudaFreeAsync(InS, st);
@@ -1221,7 +1353,7 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
     const int levels = pr.max_depth;
     int64_t stride;
     int agrid;
-    CK(adaptive_work(ctx, nr, levels, &stride, &agrid));
+    CK(adaptive_work(ctx, nr, nr->max_adaptive, levels, &stride, &agrid));
     const int64_t npr = std::max<int64_t>(nr->n_pairs, 1);
     double *Is, *In;
     int32_t* leaves;

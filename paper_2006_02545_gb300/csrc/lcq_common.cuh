@@ -270,9 +270,9 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
   }
 }
 
-// Moments with the rounding envelope, as block_moments<D, true>, for the adaptive walk:
-// I[i][seg][nm] = sum_{q in seg} w_q K(x_i, X_q) J_q K_nm(u_q, v_q) and
-// eout[i * nseg + seg] = sum_q of the kernel's rounding envelope (FP32 sums), with the
+// Moments as block_moments<D, ENV> (the adaptive walk, the smooth-rule and annulus moments):
+// I[i][seg][nm] = sum_{q in seg} w_q K(x_i, X_q) J_q K_nm(u_q, v_q) and, when eout is not
+// null, eout[i * nseg + seg] = sum_q of the kernel's rounding envelope (FP32 sums), with the
 // contraction over the nodes on the tensor cores by the exact NS-slice split (lcq_tc.cuh):
 // NS = 8 for FP64 kernel values, NS = 5 for the mixed form's FP32 ones.
 // Chunks never straddle a segment: segment sg's Q nodes are cut into parts of at most
@@ -282,7 +282,8 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
 // tile of 8 targets: kernel values and envelopes, thread per (target, node); (3) one warp
 // per target splits the Re and Im rows of its kernel values on their own power-of-two
 // scales into NS f16 slices; (4) one warp per n-tile of 8 basis columns slices its basis
-// values (fixed per-column bounds) into MMA fragments and accumulates the NS diagonals over
+// values (fixed per-column bounds) into MMA fragments and accumulates the diagonals
+// i + j <= 8 (FP64; i + j < 5 for the mixed form) over
 // the chunk's 16-node steps with mma.sync, then assembles and stores the 8 x 8 complex
 // block.  smb: TcCfg<D>::BYTES of shared memory (16-byte aligned); sct: the sincos table.
 template <int NS>
@@ -341,9 +342,10 @@ __device__ __forceinline__ void split_row_pair(const V* re, const V* im, bool on
   split_store<NS>(si, Mi, VPL, Asl + (size_t)(t + 8) * AST + q0, AST);
 }
 
-// One n-tile (basis columns 8 ct .. 8 ct + 7) of the chunk: diagonals over the k-steps, then
-// the assembled complex 8 x 8 block into the outputs.
-template <int D, int NS, class OR>
+// One n-tile (basis columns 8 ct .. 8 ct + 7) of the chunk: the diagonals d = i + j < ND of
+// the slice products over the k-steps, then the assembled complex 8 x 8 block into the
+// outputs.
+template <int D, int NS, int ND, class OR>
 __device__ __forceinline__ void tc_tile(const double* Bd, const uint16_t* Asl, const int* rowE,
                                         int ct, int ncp, int nt, int t0, int sg, bool first,
                                         OR orow) {
@@ -352,9 +354,9 @@ __device__ __forceinline__ void tc_tile(const double* Bd, const uint16_t* Asl, c
   const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
   const int col = ct * 8 + g;
   const int Eb = col < n ? c_kwexp[col] : 0;
-  float acc[NS][4];
+  float acc[ND][4];
 #pragma unroll
-  for (int d = 0; d < NS; ++d) acc[d][0] = acc[d][1] = acc[d][2] = acc[d][3] = 0.0f;
+  for (int d = 0; d < ND; ++d) acc[d][0] = acc[d][1] = acc[d][2] = acc[d][3] = 0.0f;
   const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
   for (int k0 = 0; k0 < ncp; k0 += 16) {
     const double b0 = Bd[(k0 + 2 * c) * C::BST + col];
@@ -375,7 +377,7 @@ __device__ __forceinline__ void tc_tile(const double* Bd, const uint16_t* Asl, c
       uint32_t af[4];
       ldsm_x4(af, Asl + ((size_t)i * 16 + arow) * C::AST + k0 + acol);
 #pragma unroll
-      for (int j = 0; j < NS - i; ++j) mma_f16_16816(acc[i + j], af, bf[j]);
+      for (int j = 0; j < NS && i + j < ND; ++j) mma_f16_16816(acc[i + j], af, bf[j]);
     }
   }
   if (g < nt) {
@@ -384,8 +386,8 @@ __device__ __forceinline__ void tc_tile(const double* Bd, const uint16_t* Asl, c
       const int nm = ct * 8 + 2 * c + cc;
       if (nm >= n) continue;
       const int e2 = c_kwexp[nm];
-      const double re = assemble<NS>(acc, cc, rowE[g] + e2);
-      const double im = assemble<NS>(acc, 2 + cc, rowE[g + 8] + e2);
+      const double re = assemble<ND>(acc, cc, rowE[g] + e2);
+      const double im = assemble<ND>(acc, 2 + cc, rowE[g + 8] + e2);
       cplx* dst = reinterpret_cast<cplx*>(orow(t0 + g)) + (int64_t)sg * n + nm;
       if (first) {
         dst->re = re;
@@ -423,6 +425,7 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
   const KernelParamsF kf = to_f32(kp);
   const float fR = f32_bits(R);
   const float escale = mixed ? (float)(kF32Floor / kRoundingFloor) : 1.0f;
+  const bool has_ki = kp.ki != 0.0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   // conical rules: rows of mr nodes sharing v (see block_moments)
   const int mr = (int)lrint(sqrt((double)Q));
@@ -466,7 +469,8 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
             kw_geometry_proj<D>(u, v, cf, cfd, X, Xu, Xv, Bq);
           }
           cross3(Xu, Xv, Nn);
-          const double Jw = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]) * w;
+          const double N2 = fma(Nn[0], Nn[0], fma(Nn[1], Nn[1], Nn[2] * Nn[2]));
+          const double Jw = N2 > 0.0 ? N2 * rsqrt_nr(N2) * w : 0.0;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             Xs[c * C::CH + ql] = X[c];
@@ -518,14 +522,14 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
             if (ql < nq)
               g = kernel_eval_tc(kp, kf, g_sct, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql],
                                  Xs[C::CH + ql], Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql],
-                                 Ns[2 * C::CH + ql], Js[ql], Jf[ql], fR, &ev, tn + 3 * i);
+                                 Ns[2 * C::CH + ql], Js[ql], Jf[ql], fR, &ev, tn + 3 * i, has_ki);
             Gs[i * C::CH + ql] = g;
           }
           Ef[i * C::CH + ql] = ev;
         }
         __syncthreads();
         // envelope sums, one warp per target
-        if (warp < nt) {
+        if (eout && warp < nt) {
           float es = 0.0f;
           for (int ql = lane; ql < nq; ql += 32) es += Ef[warp * C::CH + ql];
 #pragma unroll
@@ -566,9 +570,9 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
         // (4) tensor-core contraction, one warp per n-tile
         for (int ct = warp; ct < C::NTILE; ct += nwarp) {
           if (mixed)
-            tc_tile<D, 5>(Bd, Asl, rowE, ct, ncp, nt, t0, sg, part == 0, orow);
+            tc_tile<D, 5, 5>(Bd, Asl, rowE, ct, ncp, nt, t0, sg, part == 0, orow);
           else
-            tc_tile<D, 8>(Bd, Asl, rowE, ct, ncp, nt, t0, sg, part == 0, orow);
+            tc_tile<D, 8, 9>(Bd, Asl, rowE, ct, ncp, nt, t0, sg, part == 0, orow);
         }
         __syncthreads();
       }
@@ -787,8 +791,16 @@ constexpr size_t adaptive_smem_bytes() {
          4 * 32 * sizeof(unsigned long long) + 128 + TcCfg<D>::BYTES;
 }
 
-// Patches are taken dynamically from `plist` (ordered by decreasing number of adaptive
-// targets) through the counter *sched, which the caller zeroes before the launch.
+// Work items are taken dynamically through the counter *sched, which the caller zeroes
+// before the launch.  gofs == nullptr: item b is the patch plist[b] with all its adaptive
+// targets.  Otherwise item i is group g of patch plist[b], gofs[b] <= i < gofs[b + 1]
+// (an exclusive scan of the groups per listed patch, gofs[count] their total), the group
+// being the adaptive targets g gsz .. g gsz + gsz - 1 of the patch: small groups spread one
+// patch's walk over several blocks.  Every target's refinement tree, moments and leaf
+// count are the same whichever group it walks with (its tests and sums are its own, and a
+// depth-first walk of a union tree visits the nodes of each member tree in that tree's own
+// depth-first order), so the grouping changes the schedule, not the results.  plist is
+// ordered by decreasing number of adaptive targets (longest items first).
 template <int D, bool GRAD = false>
 __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict__ plist, int count,
                                                        Dev dv, const KernelParams kp, double eps,
@@ -799,7 +811,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
                                                        unsigned char* __restrict__ work,
                                                        AdaptiveWS wsd, int* __restrict__ status,
                                                        int* __restrict__ sched, double mix,
-                                                       GradArgs ga) {
+                                                       GradArgs ga,
+                                                       const int64_t* __restrict__ gofs, int gsz) {
   using C = Cfg<D>;
   constexpr int n = C::n;
   // gradient mode: dL/dx_nm of the accepted leaves, per thread, reduced per patch
@@ -827,21 +840,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
   double* tmpE = reinterpret_cast<double*>(                          // [A_max][4], 8-aligned
       (reinterpret_cast<uintptr_t>(cnt + wsd.levels) + 7) & ~static_cast<uintptr_t>(7));
   long long my_tests = 0, my_nodes = 0, my_tree = 0;
-  __shared__ int next_b;
+  __shared__ int next_b, next_g;
   __shared__ KernelParams kps;
   __shared__ double cfd[2 * 3 * (D * (D + 1) / 2)];  // derivative series of the chart
   const double* cfdp = cfd;
 
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) next_b = atomicAdd(sched, 1);
+    if (threadIdx.x == 0) {
+      const int it = atomicAdd(sched, 1);
+      int bb = -1, gg = 0;
+      if (gofs == nullptr) {
+        if (it < count) bb = it;
+      } else if (it < gofs[count]) {
+        int lo = 0, hi = count;  // gofs[lo] <= it < gofs[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (gofs[mid] <= it) lo = mid;
+          else hi = mid;
+        }
+        bb = lo;
+        gg = it - (int)gofs[lo];
+      }
+      next_b = bb;
+      next_g = gg;
+    }
     __syncthreads();
     const int b = next_b;
-    if (b >= count) break;
+    if (b < 0) break;
     const int j = plist[b];
-    const int64_t a0 = dv.ad_ptr[j];
-    const int A = (int)(dv.ad_ptr[j + 1] - a0);
-    if (A == 0) continue;
+    const int64_t ap = dv.ad_ptr[j];
+    const int Aall = (int)(dv.ad_ptr[j + 1] - ap);
+    const int64_t a0 = gofs ? ap + (int64_t)next_g * gsz : ap;
+    const int A = gofs ? min(gsz, Aall - next_g * gsz) : Aall;
+    if (A <= 0) continue;
     if (A > A_max) {
       if (threadIdx.x == 0) atomicOr(status, kStCapacity);
       continue;

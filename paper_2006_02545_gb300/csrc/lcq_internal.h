@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -105,8 +106,23 @@ void koornwinder_host(int d, double u, double v, double* K);
 }  // namespace lcq
 
 // ----------------------------------------------------------------------------- handles
+// Online tuner of the adaptive walk's work-group size for one key (degree, kernel, tolerance
+// decade, precision, size class of the adaptive work): every candidate is timed once, on the
+// generations that use the key, by events around that degree's adaptive launch; later
+// generations use the fastest.  The group size changes the schedule, never a result.
+struct lcq_tune {
+  std::vector<int> cand;        // candidate group sizes (targets per work item)
+  std::vector<double> ms_per;   // adaptive milliseconds per adaptive pair, < 0 untried
+  int pending = -1;             // candidate whose timing is in flight
+  double pend_pairs = 0.0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
 struct lcq_ctx {
   int device = 0;
+  std::map<uint64_t, lcq_tune> tune;
+  int last_group_size = 0;      // largest work-group size of the last generation
+  long long last_items = 0;     // adaptive work items of the last generation (host count)
   cudaStream_t stream = nullptr;
   int* d_status = nullptr;
   long long* d_counters = nullptr;   // [8]
@@ -173,6 +189,9 @@ struct lcq_near {
   int* plist_dev[lcq::kMaxDeg + 1] = {nullptr};
   int ad_count[lcq::kMaxDeg + 1] = {0};       // patches with adaptive targets, by degree,
   int* ad_list_dev[lcq::kMaxDeg + 1] = {nullptr};  // most adaptive targets first
+  int64_t ad_total[lcq::kMaxDeg + 1] = {0};   // adaptive pairs of each degree
+  int64_t ad_max[lcq::kMaxDeg + 1] = {0};     // largest adaptive set of each degree
+  std::vector<int64_t> ad_nad_h[lcq::kMaxDeg + 1];  // adaptive targets of each listed patch
   // batches of independent surfaces (n_groups > 1 or built by the batched entry point)
   int n_groups = 1;
   bool grouped = false;

@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
   extern __shared__ double smem[];
   double* cf = smem;
   SegMap* segs = reinterpret_cast<SegMap*>(cf + C::n * 3);
-  double* ws = reinterpret_cast<double*>(segs + 4);
+  // tensor-core moment workspace, 128-byte aligned
+  unsigned char* smb = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(segs + 4) + 127) & ~static_cast<uintptr_t>(127));
   __shared__ KernelParams kps;
   __shared__ double cfd[2 * 3 * (D * (D + 1) / 2)];  // derivative series of the chart
   const double* cfdp = cfd;
@@ -208,17 +210,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
         const int64_t p0 = dv.pair_ptr[j], np = dv.pair_ptr[j + 1] - p0;
         TgtIdx ta{dv.tgt, dv.NT, dv.pair_tgt + p0, dv.tnrm};
         cplx* base = out_smooth + p0 * ld;
-        block_moments<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)np,
-                         [=] __device__(int i) { return base + (int64_t)i * ld; }, C::n, kps, ws,
-                         dv.cen + 3 * j, 0.0, nullptr, mixj);
+        block_moments_tc<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)np,
+                            [=] __device__(int i) { return base + (int64_t)i * ld; }, kps, smb,
+                            dv.cen + 3 * j, 0.0, nullptr, mixj);
         evals += np * m * m;
       } else {
         const int64_t a0 = dv.an_ptr[j], na = dv.an_ptr[j + 1] - a0;
         const int32_t* pl = dv.an_pair + a0;
         TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl, dv.tnrm};
-        block_moments<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)na,
-                         [=] __device__(int i) { return out_ann + (int64_t)pl[i] * ld; }, C::n,
-                         kps, ws, dv.cen + 3 * j, 0.0, nullptr, mixj);
+        block_moments_tc<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)na,
+                            [=] __device__(int i) { return out_ann + (int64_t)pl[i] * ld; }, kps,
+                            smb, dv.cen + 3 * j, 0.0, nullptr, mixj);
         evals += na * m * m;
       }
     }
@@ -886,7 +888,7 @@ struct RuleMomL {
   static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv, int modes,
                   const int32_t* qv, const int32_t* qn, const KernelParams& kp, void* out_smooth,
                   void* out_ann, bool mixed) {
-    const size_t sm = moments_smem_bytes<D>(0) + (mixed ? Cfg<D>::WS_F32 * sizeof(double) : 0);
+    const size_t sm = sizeof(double) * 3 * Cfg<D>::n + sizeof(SegMap) * 4 + 128 + TcCfg<D>::BYTES;
     set_smem(k_rule_moments<D>, sm);
     ++*lc.launches;
     // one block per patch: the hardware hands the next patch to whichever block slot frees
@@ -915,7 +917,7 @@ struct AdaptiveL {
                   const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                   const void* I_smooth, void* I_near, int32_t* leaves, void* work,
                   int64_t stride, int A_max, int levels, int grid, int* status, int* sched,
-                  double mix) {
+                  double mix, const int64_t* gofs, int gsz) {
     const size_t sm = adaptive_smem_bytes<D>();
     set_smem(k_adaptive<D>, sm);
     AdaptiveWS w{stride, A_max, levels};
@@ -924,7 +926,7 @@ struct AdaptiveL {
     k_adaptive<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, kp, eps, normV, leaf_order,
                                                      max_depth, (const cplx*)I_smooth, (cplx*)I_near,
                                                      leaves, (unsigned char*)work, w, status, sched,
-                                                     mix, GradArgs{});
+                                                     mix, GradArgs{}, gofs, gsz);
   }
 };
 
@@ -1033,10 +1035,35 @@ bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count,
 bool launch_adaptive(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                      const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
-                     int A_max, int levels, int grid, int* status, int* sched, double mix) {
+                     int A_max, int levels, int grid, int* status, int* sched, double mix,
+                     const int64_t* gofs, int gsz) {
   return dispatch<AdaptiveL>(d, lc, plist, count, dv, kp, eps, normV, leaf_order, max_depth,
                              I_smooth, I_near, leaves, work, stride, A_max, levels, grid, status,
-                             sched, mix);
+                             sched, mix, gofs, gsz);
+}
+
+// Groups of at most gsz adaptive targets per listed patch: ng[b] = ceil(A_b / gsz) for
+// b < count and ng[count] = 0, so that the exclusive scan of the count + 1 entries (gofs)
+// ends with the number of groups.
+__global__ void k_group_counts(const int* __restrict__ plist, int count,
+                               const int64_t* __restrict__ ad_ptr, int gsz, int64_t* __restrict__ ng) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= count; b += gridDim.x * blockDim.x) {
+    int64_t g = 0;
+    if (b < count) {
+      const int j = plist[b];
+      g = (ad_ptr[j + 1] - ad_ptr[j] + gsz - 1) / gsz;
+    }
+    ng[b] = g;
+  }
+}
+
+void launch_group_offsets(const LaunchCommon& lc, const int* plist, int count, const int64_t* ad_ptr,
+                          int gsz, int64_t* ng, int64_t* gofs, int64_t* scratch) {
+  const int blocks = (count + 1 + 255) / 256;
+  ++*lc.launches;
+  k_group_counts<<<blocks < lc.num_sms * 4 ? blocks : lc.num_sms * 4, 256, 0, lc.stream>>>(
+      plist, count, ad_ptr, gsz, ng);
+  launch_scan(lc, ng, gofs, count + 1, scratch);
 }
 bool launch_self(int d, const LaunchCommon& lc, const Dev& dv, const int32_t* deg,
                  const KernelParams& kp, int order, void* out) {

@@ -136,7 +136,12 @@ bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count,
 bool launch_adaptive(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                      const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
-                     int A_max, int levels, int grid, int* status, int* sched, double mix = 0.0);
+                     int A_max, int levels, int grid, int* status, int* sched, double mix = 0.0,
+                     const int64_t* gofs = nullptr, int gsz = 0);
+// gofs[count + 1]: exclusive scan of ceil(A_b / gsz) over the listed patches (work groups of
+// at most gsz adaptive targets for launch_adaptive); ng[count + 1] and scratch as launch_scan.
+void launch_group_offsets(const LaunchCommon& lc, const int* plist, int count, const int64_t* ad_ptr,
+                          int gsz, int64_t* ng, int64_t* gofs, int64_t* scratch);
 bool launch_self(int d, const LaunchCommon& lc, const Dev& dv, const int32_t* deg,
                  const KernelParams& kp, int order, void* out);
 bool launch_v2c(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,

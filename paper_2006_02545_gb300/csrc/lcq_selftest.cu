@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) k_check_tc(int nq, unsigned long long see
   split_row_pair<8, VPL>(re, im, true, C::TT, Asl, C::AST, warp, q0, rowE);
   __syncthreads();
   for (int ct = warp; ct < C::NTILE; ct += blockDim.x >> 5)
-    tc_tile<D, 8>(Bd, Asl, rowE, ct, ncp, C::TT, 0, 0, true,
+    tc_tile<D, 8, 9>(Bd, Asl, rowE, ct, ncp, C::TT, 0, 0, true,
                   [&](int t) { return &res[t][0]; });
   __syncthreads();
   for (int e = threadIdx.x; e < C::TT * n; e += blockDim.x) {

@@ -12,8 +12,9 @@
 // over a chunk of at most 128 nodes and over the at most 8 slice pairs of one diagonal stays
 // below 2^24, so the f16 MMA with FP32 accumulators computes each diagonal exactly; the
 // diagonals are combined in 64-bit integers and converted to FP64 once per chunk.  With
-// NS = 8 (56 bits per operand, diagonals i + j <= 7) the result matches an FP64 contraction
-// to within a few units of 2^-53 relative to max|kernel| * bound|basis| per node.
+// NS = 8 (56 bits per operand) and the diagonals i + j <= 8 (43 MMAs per 16-node step; the
+// dropped products are below 2^-60 of the operands' scales) the result matches an FP64
+// contraction to the FP64 rounding level of the sum of |products|.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -139,27 +140,31 @@ __device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
                : "r"(a));
 }
 
-// FP64 value of one accumulator element: the diagonals d = 0..NS-1 (exact integers in FP32)
-// weighted 2^(-7 d), combined in 64-bit integers, times 2^(E - 14 - 7 (NS - 1)), E = Ea + Eb.
-template <int NS>
+// FP64 value of one accumulator element: the diagonals d = 0..ND-1 (exact integers in FP32)
+// weighted 2^(-7 d), combined in 64-bit integers (two halves of at most 53 bits, so that each
+// converts exactly), times 2^(E - 14 - 7 (ND - 1)), E = Ea + Eb.
+template <int ND>
 __device__ __forceinline__ double assemble(const float (*acc)[4], int e, int E) {
   if (E >= kPoisonExp / 2) return __longlong_as_double(0x7ff8000000000000ll);  // NaN
   double v;
-  if (NS <= 5) {
+  if (ND <= 5) {
     long long s = 0;
 #pragma unroll
-    for (int d = 0; d < NS; ++d) s += (long long)__float2int_rn(acc[d][e]) * (1ll << (kSliceBits * (NS - 1 - d)));
+    for (int d = 0; d < ND; ++d)
+      s += (long long)__float2int_rn(acc[d][e]) * (1ll << (kSliceBits * (ND - 1 - d)));
     v = (double)s;
   } else {
-    constexpr int H = NS / 2;  // diagonals 0..H-1 in hi, H..NS-1 in lo
+    constexpr int H = ND / 2;  // diagonals 0..H-1 in hi, H..ND-1 in lo
     long long hi = 0, lo = 0;
 #pragma unroll
-    for (int d = 0; d < H; ++d) hi += (long long)__float2int_rn(acc[d][e]) * (1ll << (kSliceBits * (H - 1 - d)));
+    for (int d = 0; d < H; ++d)
+      hi += (long long)__float2int_rn(acc[d][e]) * (1ll << (kSliceBits * (H - 1 - d)));
 #pragma unroll
-    for (int d = H; d < NS; ++d) lo += (long long)__float2int_rn(acc[d][e]) * (1ll << (kSliceBits * (NS - 1 - d)));
-    v = fma((double)hi, (double)(1ll << (kSliceBits * (NS - H))), (double)lo);
+    for (int d = H; d < ND; ++d)
+      lo += (long long)__float2int_rn(acc[d][e]) * (1ll << (kSliceBits * (ND - 1 - d)));
+    v = fma((double)hi, (double)(1ll << (kSliceBits * (ND - H))), (double)lo);
   }
-  const int ue = E - 2 * kSliceBits - kSliceBits * (NS - 1);
+  const int ue = E - 2 * kSliceBits - kSliceBits * (ND - 1);
   if (ue < -1022) return 0.0;
   return v * __longlong_as_double((long long)(ue + 1023) << 52);
 }
@@ -177,6 +182,25 @@ __device__ __forceinline__ float f32_bits(double x) {
   return __uint_as_float(s | ((unsigned)e << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
 }
 
+// FP64 value of a positive normal FP32 number by its bits (exact; no FP64 instruction).
+__device__ __forceinline__ double f64_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned long long e = (unsigned long long)(((b >> 23) & 0xffu) + (1023u - 127u));
+  return __longlong_as_double((long long)((e << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// 1/sqrt(x) for x > 0: the FP32 estimate (special function unit) refined by one third-order
+// Newton-Raphson step in FP64, y1 = y0 (1 + e/2 + 3 e^2/8) with e = 1 - x y0^2 (relative
+// error O(e^3), e <= 2^-21): five FP64 instructions.  Arguments outside the FP32 range
+// take rsqrt().
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const int ex = (__double2hiint(x) >> 20) & 0x7ff;
+  if (ex < 1023 - 120 || ex > 1023 + 120) return rsqrt(x);
+  const double y0 = f64_bits(rsqrtf(f32_bits(x)));
+  const double e = fma(-(x * y0), y0, 1.0);
+  return fma(y0, e * fma(e, 0.375, 0.5), y0);
+}
+
 // sin and cos of th by table lookup and Taylor polynomials (the table method of Gal and
 // Bachelis, ACM TOMS 17, 1991): th = j (2 pi / 256) + t with j = rint(th 256 / (2 pi)) (the
 // 1.5 2^52 shifter) and |t| <= pi / 256; sin t and cos t by their Taylor series through t^7
@@ -184,7 +208,7 @@ __device__ __forceinline__ float f32_bits(double x) {
 // (cos, sin)(2 pi j / 256).  Valid for |th| < 2^20; larger arguments use sincos().
 __device__ __forceinline__ void sincos_tab(double th, const double2* __restrict__ tab, double* sn,
                                            double* cs) {
-  if (!(fabs(th) < 1048576.0)) {
+  if (((__double2hiint(th) >> 20) & 0x7ff) >= 1023 + 20) {  // |th| >= 2^20 or not finite
     sincos(th, sn, cs);
     return;
   }
@@ -206,15 +230,16 @@ __device__ __forceinline__ void sincos_tab(double th, const double2* __restrict_
   *sn = fma(e.y, c, e.x * s);
 }
 
-// kernel_eval (lcq_device.cuh) with the table sincos and the rounding envelope formed in FP32
-// from the FP64 quantities' bits: the same kernel value to a few ulps.  fJw: FP32 copy of
-// Jw; fR: FP32 patch radius.  r = 0 gives 0.
+// kernel_eval (lcq_device.cuh) with the table sincos, the Newton-refined FP32 reciprocal
+// square root and the rounding envelope formed in FP32 from the FP64 quantities' bits: the
+// same kernel value to a few ulps.  fJw: FP32 copy of Jw; fR: FP32 patch radius; has_ki:
+// Im k != 0.  r = 0 gives 0.
 __device__ __forceinline__ cplx kernel_eval_tc(const KernelParams& kp, const KernelParamsF& kf,
                                                const double2* __restrict__ sct, double x0,
                                                double x1, double x2, double X0, double X1,
                                                double X2, double N0, double N1, double N2,
                                                double Jw, float fJw, float fR, float* env,
-                                               const double* nx) {
+                                               const double* nx, bool has_ki) {
   if (kp.kind == 3) {
     N0 = -nx[0] * Jw;
     N1 = -nx[1] * Jw;
@@ -226,13 +251,13 @@ __device__ __forceinline__ cplx kernel_eval_tc(const KernelParams& kp, const Ker
     *env = 0.0f;
     return {0.0, 0.0};
   }
-  const double rinv = rsqrt(r2);
+  const double rinv = rsqrt_nr(r2);
   const double r = r2 * rinv;
   const double th = kp.kr * r;
   double sn, cs;
   sincos_tab(th, sct, &sn, &cs);
   double ex = 0.07957747154594767 * rinv;  // 1/(4 pi r)
-  if (kp.ki != 0.0) ex *= exp(-kp.ki * r);
+  if (has_ki) ex *= exp(-kp.ki * r);
   {
     // |G| Jw (|beta| + |alpha| |1 - ik r| R / r^2) in FP32
     const float fr = f32_bits(r), fri = 1.0f / fr;
@@ -245,7 +270,7 @@ __device__ __forceinline__ cplx kernel_eval_tc(const KernelParams& kp, const Ker
   const double rinv2 = rinv * rinv;
   const double ndx = fma(N0, d0, fma(N1, d1, N2 * d2)) * rinv2;
   // (1 - ikr) ndx with k = kr + i ki: ((1 + ki r) ndx, -kr r ndx)
-  double cr = kp.ki != 0.0 ? fma(kp.ki, r, 1.0) * ndx : ndx;
+  double cr = has_ki ? fma(kp.ki, r, 1.0) * ndx : ndx;
   double ci = -th * ndx;
   if (kp.kind == 2) {
     const double tr = fma(kp.ar, cr, fma(-kp.ai, ci, kp.br * Jw));

@@ -17,9 +17,9 @@ def test_sincos_table_and_tensor_contraction():
     # table entries and the angle-addition step round, the Taylor tails are below 1.3e-20
     assert 0.0 <= r["sincos_abs_err"] <= 8 * U, r
     # the 8-slice split keeps 56 bits per operand on the row's (kernel) and the column's
-    # bound (basis) power-of-two scales, and drops the slice products of diagonals i + j >= 8
-    # (each below 2^-50 of its scale): against a double-double reference, within 1e-14 of
-    # sum |products| (12 decades of kernel magnitudes within one row, up to 128 nodes),
-    # 20 times below the adaptive test's rounding floor of 2e-13 of the envelope
-    assert 0.0 <= r["tc_rel_err_d6"] <= 1e-14, r
-    assert 0.0 <= r["tc_rel_err_d10"] <= 1e-14, r
+    # bound (basis) power-of-two scales and keeps the slice products of diagonals i + j <= 8
+    # (the dropped ones are below 2^-60 of the scales): against a double-double reference,
+    # at the FP64 rounding level of sum |products| (12 decades of kernel magnitudes within one
+    # row, up to 128 nodes)
+    assert 0.0 <= r["tc_rel_err_d6"] <= 8 * U, r
+    assert 0.0 <= r["tc_rel_err_d10"] <= 8 * U, r
