@@ -22,6 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lcq_kernels.cu", "lcq_adjoint.cu", "lcq_nearlist.cu", "lcq_api.cpp",
            "lcq_tables.cpp", "lcq_noalloc.cu", "lcq_peaks.cu",
            "lcq_selftest.cu"]
+DEGREES = range(1, 11)   # lcq_deg.cu is built once per patch degree (-DLCQ_DEG=d)
 
 
 def _nvcc() -> str:
@@ -52,21 +53,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
     common = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
                      "-I" + INCLUDE, "-I" + CSRC]
     jobs = []
-    for src in SOURCES:
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
+    units = [(src, []) for src in SOURCES] + [("lcq_deg.cu", [f"-DLCQ_DEG={d}"]) for d in DEGREES]
+    for src, defs in units:
+        stem = os.path.splitext(src)[0] + (defs[0].split("=")[1] if defs else "")
+        obj = os.path.join(BUILD, stem + ".o")
+        cmd = [nvcc] + common + defs + ["-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd[1:1] = ["--extended-lambda", "-Xptxas", "-v"] if verbose else ["--extended-lambda"]
         else:
             cmd[1:1] = ["-x", "cu"]
-        jobs.append((src, obj, cmd))
+        jobs.append((src + " ".join(defs), obj, cmd))
 
     def run(job):
         src, obj, cmd = job
         r = subprocess.run(cmd, capture_output=True, text=True)
         return src, r
 
-    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+    with ThreadPoolExecutor(max_workers=min(len(jobs), max(4, os.cpu_count() or 4))) as ex:
         results = list(ex.map(run, jobs))
     for src, r in results:
         if verbose and r.stderr:

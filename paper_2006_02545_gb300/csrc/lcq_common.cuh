@@ -58,6 +58,16 @@ __device__ __forceinline__ int block_flag_scan(int flag, int* sm, int* total) {
 }
 
 // Kernel of patch j: its surface's in a batch of independent surfaces, else the launch's.
+// Patch of oversampled source q: the largest j with src_off[j] <= q.
+__device__ __forceinline__ int patch_of_source(const int64_t* src_off, int64_t P, int64_t q) {
+  int64_t lo = 0, hi = P;  // largest j with src_off[j] <= q
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) / 2;
+    if (src_off[mid] <= q) lo = mid; else hi = mid;
+  }
+  return (int)lo;
+}
+
 __device__ __forceinline__ KernelParams patch_kp(const Dev& dv, int j, const KernelParams& kp) {
   return dv.pgroup ? dv.grp[dv.pgroup[j]].kp : kp;
 }
@@ -286,28 +296,12 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
 // i + j <= 8 (FP64; i + j < 5 for the mixed form) over
 // the chunk's 16-node steps with mma.sync, then assembles and stores the 8 x 8 complex
 // block.  smb: TcCfg<D>::BYTES of shared memory (16-byte aligned); sct: the sincos table.
-template <int NS>
-__device__ __forceinline__ void split_store(const uint32_t* signs2, const unsigned long long* M,
-                                            int nv, uint16_t* dst, int AST) {
-  // nv values (2 or 4) of one row at consecutive columns; dst: slice 0 of this row
-#pragma unroll
-  for (int i = 0; i < NS; ++i) {
-    uint16_t* d = dst + (size_t)i * 16 * AST;
-    const uint32_t w0 = half2_ints(slice_of<NS>(M[0], i), slice_of<NS>(M[1], i), signs2[0]);
-    if (nv == 4) {
-      const uint32_t w1 = half2_ints(slice_of<NS>(M[2], i), slice_of<NS>(M[3], i), signs2[1]);
-      *reinterpret_cast<uint2*>(d) = make_uint2(w0, w1);
-    } else {
-      *reinterpret_cast<uint32_t*>(d) = w0;
-    }
-  }
-}
-
-template <int NS, int VPL, class V>
-__device__ __forceinline__ void split_row_pair(const V* re, const V* im, bool on, int nt_ok,
-                                               uint16_t* Asl, int AST, int t, int q0,
-                                               int* rowE) {
-  // exponents of the Re and Im rows (max over the warp's values)
+// Rows t (Re) and t + 8 (Im) of the kernel values, VPL consecutive columns q0.. per lane,
+// on their own power-of-two scales into NS f16 slices of the swizzled A array (one warp).
+template <int D, int NS, int VPL, class V>
+__device__ __forceinline__ void split_row_pair(const V* re, const V* im, bool on, uint16_t* Asl,
+                                               int t, int q0, int* rowE) {
+  using C = TcCfg<D>;
   int fr = 0, fi = 0;
   bool bad = false;
 #pragma unroll
@@ -321,61 +315,83 @@ __device__ __forceinline__ void split_row_pair(const V* re, const V* im, bool on
   fi = (int)__reduce_max_sync(0xffffffffu, (unsigned)fi);
   bad = __any_sync(0xffffffffu, bad);
   const int Er = exp_bound(fr, V()), Ei = exp_bound(fi, V());
-  (void)nt_ok;
   if ((threadIdx.x & 31) == 0) {
     rowE[t] = !on ? 0 : (bad ? kPoisonExp : Er);
     rowE[t + 8] = !on ? 0 : (bad ? kPoisonExp : Ei);
   }
-  unsigned long long Mr[VPL], Mi[VPL];
-  uint32_t sr[VPL / 2], si[VPL / 2];
 #pragma unroll
-  for (int v = 0; v < VPL; ++v) {
-    Mr[v] = on ? fix_mag<NS>(re[v], Er) : 0ull;
-    Mi[v] = on ? fix_mag<NS>(im[v], Ei) : 0ull;
-  }
+  for (int part = 0; part < 2; ++part) {
+    const V* x = part ? im : re;
+    const int E = part ? Ei : Er;
+    const int row = t + 8 * part;
+    unsigned long long M[VPL];
+    uint32_t sg[VPL / 2];
 #pragma unroll
-  for (int v = 0; v < VPL / 2; ++v) {
-    sr[v] = sign_bits(re[2 * v], re[2 * v + 1]);
-    si[v] = sign_bits(im[2 * v], im[2 * v + 1]);
+    for (int v = 0; v < VPL; ++v) M[v] = on ? fix_mag<NS>(x[v], E) : 0ull;
+#pragma unroll
+    for (int v = 0; v < VPL / 2; ++v) sg[v] = sign_bits(x[2 * v], x[2 * v + 1]);
+    uint16_t* dst = Asl + C::swz(row, q0);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+      uint16_t* d = dst + (size_t)i * 16 * C::CH;
+      const uint32_t w0 = half2_ints(slice_of<NS>(M[0], i), slice_of<NS>(M[1], i), sg[0]);
+      if (VPL == 4) {
+        const uint32_t w1 = half2_ints(slice_of<NS>(M[2], i), slice_of<NS>(M[3], i), sg[1]);
+        *reinterpret_cast<uint2*>(d) = make_uint2(w0, w1);
+      } else {
+        *reinterpret_cast<uint32_t*>(d) = w0;
+      }
+    }
   }
-  split_store<NS>(sr, Mr, VPL, Asl + (size_t)t * AST + q0, AST);
-  split_store<NS>(si, Mi, VPL, Asl + (size_t)(t + 8) * AST + q0, AST);
 }
 
-// One n-tile (basis columns 8 ct .. 8 ct + 7) of the chunk: the diagonals d = i + j < ND of
-// the slice products over the k-steps, then the assembled complex 8 x 8 block into the
-// outputs.
+// The 8 slices of basis value K_nm (column idx) of node k into the swizzled B array.
+template <int D>
+__device__ __forceinline__ void store_basis_slices(uint16_t* Bsl, int idx, int k, double v) {
+  using C = TcCfg<D>;
+  const unsigned long long M = fix_mag<8>(v, c_kwexp[idx]);
+  const bool neg = __double2hiint(v) < 0;
+  uint16_t* b = Bsl + C::swz(idx, k);
+#pragma unroll
+  for (int i = 0; i < 8; i += 2) {
+    const uint32_t h = half2_pair(slice_of<8>(M, i), slice_of<8>(M, i + 1), neg);
+    b[(size_t)i * C::NP * C::CH] = (uint16_t)(h & 0xffffu);
+    b[(size_t)(i + 1) * C::NP * C::CH] = (uint16_t)(h >> 16);
+  }
+}
+
+// One n-tile (basis columns 8 ct .. 8 ct + 7) of one piece of the chunk (columns kbeg ..
+// kend - 1, one segment sg): the diagonals d = i + j < ND of the slice products over the
+// k-steps (A and B fragments by ldmatrix), then the assembled complex 8 x 8 block into the
+// outputs (stored when first, else added).
 template <int D, int NS, int ND, class OR>
-__device__ __forceinline__ void tc_tile(const double* Bd, const uint16_t* Asl, const int* rowE,
-                                        int ct, int ncp, int nt, int t0, int sg, bool first,
-                                        OR orow) {
+__device__ __forceinline__ void tc_tile(const uint16_t* Bsl, const uint16_t* Asl, const int* rowE,
+                                        int ct, int kbeg, int kend, int nt, int t0, int sg,
+                                        bool first, OR orow) {
   using C = TcCfg<D>;
   constexpr int n = C::n;
+  constexpr int NB = (NS + 1) / 2;  // slice pairs of B loaded per k-step
   const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-  const int col = ct * 8 + g;
-  const int Eb = col < n ? c_kwexp[col] : 0;
   float acc[ND][4];
 #pragma unroll
   for (int d = 0; d < ND; ++d) acc[d][0] = acc[d][1] = acc[d][2] = acc[d][3] = 0.0f;
   const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, acol = (lane >> 4) * 8;
-  for (int k0 = 0; k0 < ncp; k0 += 16) {
-    const double b0 = Bd[(k0 + 2 * c) * C::BST + col];
-    const double b1 = Bd[(k0 + 2 * c + 1) * C::BST + col];
-    const double b2 = Bd[(k0 + 2 * c + 8) * C::BST + col];
-    const double b3 = Bd[(k0 + 2 * c + 9) * C::BST + col];
-    const unsigned long long M0 = fix_mag<NS>(b0, Eb), M1 = fix_mag<NS>(b1, Eb);
-    const unsigned long long M2 = fix_mag<NS>(b2, Eb), M3 = fix_mag<NS>(b3, Eb);
-    const uint32_t s01 = sign_bits(b0, b1), s23 = sign_bits(b2, b3);
-    uint32_t bf[NS][2];
+  const int brow = ct * 8 + (lane & 7), bcol = ((lane >> 3) & 1) * 8, bsl = lane >> 4;
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
+    uint32_t bf[2 * NB][2];
 #pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      bf[j][0] = half2_ints(slice_of<NS>(M0, j), slice_of<NS>(M1, j), s01);
-      bf[j][1] = half2_ints(slice_of<NS>(M2, j), slice_of<NS>(M3, j), s23);
+    for (int p = 0; p < NB; ++p) {
+      uint32_t r[4];
+      ldsm_x4(r, Bsl + (size_t)(2 * p + bsl) * C::NP * C::CH + C::swz(brow, k0 + bcol));
+      bf[2 * p][0] = r[0];
+      bf[2 * p][1] = r[1];
+      bf[2 * p + 1][0] = r[2];
+      bf[2 * p + 1][1] = r[3];
     }
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
       uint32_t af[4];
-      ldsm_x4(af, Asl + ((size_t)i * 16 + arow) * C::AST + k0 + acol);
+      ldsm_x4(af, Asl + (size_t)i * 16 * C::CH + C::swz(arow, k0 + acol));
 #pragma unroll
       for (int j = 0; j < NS && i + j < ND; ++j) mma_f16_16816(acc[i + j], af, bf[j]);
     }
@@ -400,6 +416,25 @@ __device__ __forceinline__ void tc_tile(const double* Bd, const uint16_t* Asl, c
   }
 }
 
+// Moments as block_moments<D, ENV> (the adaptive walk, the smooth-rule and annulus moments):
+// I[i][seg][nm] = sum_{q in seg} w_q K(x_i, X_q) J_q K_nm(u_q, v_q) and, when eout is not
+// null, eout[i * nseg + seg] = sum_q of the kernel's rounding envelope (FP32 sums), with the
+// contraction over the nodes on the tensor cores by the exact slice split (lcq_tc.cuh):
+// 8 slices per FP64 operand and the diagonals i + j <= 8 for FP64 kernel values; for the mixed
+// form's FP32 kernel values 5 slices and the diagonals i + j <= 4.
+// A chunk is a run of pieces (segment sg, its nodes l0 .. l0 + nq - 1), each padded with
+// zero columns to a multiple of 16 (the MMA depth), packed while they fit in TcCfg::CH
+// columns: the four children of a small rule share one chunk.  Each piece's contribution is
+// assembled in FP64 and written (the segment's first part) or added.
+// Per chunk: (1) geometry, thread per node: X, N w, J w (FP64), and each basis value split
+// into 8 f16 slices on its column's fixed bound as it is formed (integer work that runs in
+// the shadow of the FP64 geometry); (2) per tile of 8 targets: kernel values and envelopes,
+// thread per (target, node); (3) one warp per target splits the Re and Im rows of its kernel
+// values on their own power-of-two scales; (4) one warp per n-tile of 8 basis columns
+// accumulates the diagonals over each piece's 16-node steps with mma.sync, both operands read
+// by ldmatrix, and assembles and stores its 8 x 8 complex block.
+// For real k and kinds S, D and CFIE with a real alpha the kernel constants are folded into
+// the node data (kernel_eval_fold).  smb: TcCfg<D>::BYTES of shared memory (16-byte aligned).
 template <int D, class TA, class OR>
 __device__ void block_moments_tc(const double* cf, const double* cfd, const double* __restrict__ ru,
                                  const double* __restrict__ rv, const double* __restrict__ rw,
@@ -411,21 +446,29 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
   double* Xs = reinterpret_cast<double*>(smb + C::OFF_X);
   double* Ns = reinterpret_cast<double*>(smb + C::OFF_N);
   double* Js = reinterpret_cast<double*>(smb + C::OFF_J);
-  double* Bd = reinterpret_cast<double*>(smb + C::OFF_B);
+  double* Ks = reinterpret_cast<double*>(smb + C::OFF_K);
+  uint16_t* Bsl = reinterpret_cast<uint16_t*>(smb + C::OFF_BS);
   cplx* Gs = reinterpret_cast<cplx*>(smb + C::OFF_G);
   float2* Gf = reinterpret_cast<float2*>(smb + C::OFF_G);
   uint16_t* Asl = reinterpret_cast<uint16_t*>(smb + C::OFF_G);
   double* rows = reinterpret_cast<double*>(smb + C::OFF_G);
-  float* Ef = reinterpret_cast<float*>(smb + C::OFF_E);
+  float* Ef = reinterpret_cast<float*>(smb + C::OFF_EF);
   float* Jf = reinterpret_cast<float*>(smb + C::OFF_JF);
   float* Nf = reinterpret_cast<float*>(smb + C::OFF_NF);
   int* rowE = reinterpret_cast<int*>(smb + C::OFF_ROWE);
   double* tx = reinterpret_cast<double*>(smb + C::OFF_TX);
   double* tn = tx + 3 * C::TT;
+  int* colinfo = reinterpret_cast<int*>(smb + C::OFF_CI);  // (piece << 16) | node, 0xffff: pad
+  int* pcs = reinterpret_cast<int*>(smb + C::OFF_PC);      // [piece][sg, l0, nq, po, row0, rb, first]
   const KernelParamsF kf = to_f32(kp);
   const float fR = f32_bits(R);
   const float escale = mixed ? (float)(kF32Floor / kRoundingFloor) : 1.0f;
   const bool has_ki = kp.ki != 0.0;
+  // real k, kinds S, D and CFIE with a real alpha: constants folded into the node data
+  const bool fold = !mixed && !has_ki && kp.kind <= 2 && kp.ai == 0.0;
+  constexpr double kInv4Pi = 0.07957747154594767;
+  const double fa_n = (kp.kind == 1 ? 1.0 : kp.ar) * kInv4Pi;
+  const double fj_r = (kp.kind == 0 ? 1.0 : kp.br) * kInv4Pi, fj_i = kp.bi * kInv4Pi;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   // conical rules: rows of mr nodes sharing v (see block_moments)
   const int mr = (int)lrint(sqrt((double)Q));
@@ -435,147 +478,205 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
   constexpr int kRowMax = C::G_BYTES / 8 / RW::size;
   const int nparts = (Q + C::CH - 1) / C::CH;
   const int psize = (Q + nparts - 1) / nparts;
-  for (int sg = 0; sg < nseg; ++sg) {
-    const SegMap S = segs[sg];
-    for (int part = 0; part < nparts; ++part) {
-      const int l0 = part * psize;
-      const int nq = min(psize, Q - l0);
-      if (nq <= 0) break;
-      const int ncp = (nq + 15) & ~15;
-      const int row0 = by_rows ? l0 / mr : 0;
-      const int nrow = by_rows ? (l0 + nq - 1) / mr - row0 + 1 : 0;
-      const bool use_rows = by_rows && nrow <= kRowMax;
-      __syncthreads();
-      if (use_rows) {
-        for (int e = threadIdx.x; e < nrow * (D + 1); e += blockDim.x) {
-          const int rr = e / (D + 1), m = e - rr * (D + 1);
-          const int l = (row0 + rr) * mr;
-          kw_row_factors<D>(S.ay + ru[l] * S.e1y + rv[l] * S.e2y, m, cf, cfd, rows + rr * RW::size);
-        }
-        __syncthreads();
+  // the padding columns n .. NP-1 of the basis slices stay zero
+  __syncthreads();
+  for (int e = threadIdx.x; e < C::NSMAX * (C::NP - n) * C::CH; e += blockDim.x) {
+    const int i = e / ((C::NP - n) * C::CH), r = e - i * (C::NP - n) * C::CH;
+    const int col = n + r / C::CH, k = r - (col - n) * C::CH;
+    Bsl[(size_t)i * C::NP * C::CH + C::swz(col, k)] = 0;
+  }
+  int sg_next = 0, part_next = 0;
+  while (sg_next < nseg) {
+    // plan the chunk (uniform across the block); thread 0 records it for indexed lookups
+    int np = 0, ncp = 0, nrow = 0;
+    __syncthreads();
+    while (sg_next < nseg && np < C::MAXP) {
+      const int l0 = part_next * psize, nq = min(psize, Q - l0), pad = (nq + 15) & ~15;
+      if (np > 0 && ncp + pad > C::CH) break;
+      if (threadIdx.x == 0) {
+        int* pc = pcs + 8 * np;
+        pc[0] = sg_next;
+        pc[1] = l0;
+        pc[2] = nq;
+        pc[3] = ncp;
+        pc[4] = by_rows ? l0 / mr : 0;
+        pc[5] = nrow;
+        pc[6] = part_next == 0;
       }
-      for (int ql = threadIdx.x; ql < ncp; ql += blockDim.x) {
-        double* Bq = Bd + ql * C::BST;
-        if (ql < nq) {
-          const int l = l0 + ql;
-          const double r0 = ru[l], r1 = rv[l];
-          const double u = S.ax + r0 * S.e1x + r1 * S.e2x;
-          const double w = rw[l] * S.det;
-          double X[3], Xu[3], Xv[3], Nn[3];
-          if (use_rows) {
-            kw_geometry_row<D>(u, rows + (l / mr - row0) * RW::size, X, Xu, Xv, Bq);
-          } else {
-            const double v = S.ay + r0 * S.e1y + r1 * S.e2y;
-            kw_geometry_proj<D>(u, v, cf, cfd, X, Xu, Xv, Bq);
-          }
-          cross3(Xu, Xv, Nn);
-          const double N2 = fma(Nn[0], Nn[0], fma(Nn[1], Nn[1], Nn[2] * Nn[2]));
-          const double Jw = N2 > 0.0 ? N2 * rsqrt_nr(N2) * w : 0.0;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            Xs[c * C::CH + ql] = X[c];
-            Ns[c * C::CH + ql] = Nn[c] * w;
-          }
-          Js[ql] = Jw;
-          Jf[ql] = f32_bits(Jw);
-          if (mixed) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) Nf[c * C::CH + ql] = (float)(Nn[c] * w);
-            Jf[ql] = (float)Jw;
-          }
+      nrow += by_rows ? (l0 + nq - 1) / mr - l0 / mr + 1 : 0;
+      ncp += pad;
+      ++np;
+      if (++part_next == nparts) {
+        part_next = 0;
+        ++sg_next;
+      }
+    }
+    const bool use_rows = by_rows && nrow <= kRowMax;
+    __syncthreads();
+    for (int p = threadIdx.x; p < ncp; p += blockDim.x) {
+      int k = 0;
+      for (int kk = 1; kk < np; ++kk)
+        if (pcs[8 * kk + 3] <= p) k = kk;
+      const int ql = p - pcs[8 * k + 3];
+      colinfo[p] = (k << 16) | (ql < pcs[8 * k + 2] ? ql : 0xffff);
+    }
+    if (use_rows) {
+      for (int e = threadIdx.x; e < nrow * (D + 1); e += blockDim.x) {
+        const int rr = e / (D + 1), m = e - rr * (D + 1);
+        int k = 0;
+        for (int kk = 1; kk < np; ++kk)
+          if (pcs[8 * kk + 5] <= rr) k = kk;
+        const int* pc = pcs + 8 * k;
+        const SegMap& S = segs[pc[0]];
+        const int l = (pc[4] + rr - pc[5]) * mr;
+        kw_row_factors<D>(S.ay + ru[l] * S.e1y + rv[l] * S.e2y, m, cf, cfd, rows + rr * RW::size);
+      }
+    }
+    __syncthreads();
+    // (1) geometry and basis slices, thread per node
+    for (int p = threadIdx.x; p < ncp; p += blockDim.x) {
+      const int ci = colinfo[p], ql = ci & 0xffff;
+      if (ql != 0xffff) {
+        const int* pc = pcs + 8 * (ci >> 16);
+        const SegMap& S = segs[pc[0]];
+        const int l = pc[1] + ql;
+        const double r0 = ru[l], r1 = rv[l];
+        const double u = S.ax + r0 * S.e1x + r1 * S.e2x;
+        const double w = rw[l] * S.det;
+        double X[3], Xu[3], Xv[3], Nn[3];
+        if (use_rows) {
+          kw_geometry_row_emit<D>(u, rows + (pc[5] + l / mr - pc[4]) * RW::size, X, Xu, Xv,
+                                  [&](int idx, double kv) { store_basis_slices<D>(Bsl, idx, p, kv); });
         } else {
+          double K[n];
+          const double v = S.ay + r0 * S.e1y + r1 * S.e2y;
+          kw_geometry_proj<D>(u, v, cf, cfd, X, Xu, Xv, K);
 #pragma unroll 1
-          for (int nm = 0; nm < n; ++nm) Bq[nm] = 0.0;
+          for (int idx = 0; idx < n; ++idx) store_basis_slices<D>(Bsl, idx, p, K[idx]);
         }
+        cross3(Xu, Xv, Nn);
+        const double N2 = fma(Nn[0], Nn[0], fma(Nn[1], Nn[1], Nn[2] * Nn[2]));
+        const double Jw = N2 > 0.0 ? N2 * rsqrt_nr(N2) * w : 0.0;
+        const double wn = fold ? w * fa_n : w;
 #pragma unroll
-        for (int nm = n; nm < C::NP; ++nm) Bq[nm] = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          Xs[c * C::CH + p] = X[c];
+          Ns[c * C::CH + p] = Nn[c] * wn;
+        }
+        Js[p] = fold ? Jw * fj_r : Jw;
+        Ks[p] = fold ? Jw * fj_i : 0.0;
+        Jf[p] = f32_bits(fold ? Jw * kInv4Pi : Jw);
+        if (mixed) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) Nf[c * C::CH + p] = (float)(Nn[c] * w);
+          Jf[p] = (float)Jw;
+        }
+      } else {
+#pragma unroll 1
+        for (int idx = 0; idx < n; ++idx)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) Bsl[(size_t)i * C::NP * C::CH + C::swz(idx, p)] = 0;
+      }
+    }
+    __syncthreads();
+    for (int t0 = 0; t0 < T; t0 += C::TT) {
+      const int nt = min(C::TT, T - t0);
+      if (threadIdx.x < nt) {
+        double* xp = tx + 3 * threadIdx.x;
+        ta.pos(t0 + threadIdx.x, xp);
+        xp[0] -= cen[0];
+        xp[1] -= cen[1];
+        xp[2] -= cen[2];
+        if (kp.kind == 3) ta.nrm(t0 + threadIdx.x, xp, tn + 3 * threadIdx.x);
       }
       __syncthreads();
-      for (int t0 = 0; t0 < T; t0 += C::TT) {
-        const int nt = min(C::TT, T - t0);
-        if (threadIdx.x < nt) {
-          double* xp = tx + 3 * threadIdx.x;
-          ta.pos(t0 + threadIdx.x, xp);
-          xp[0] -= cen[0];
-          xp[1] -= cen[1];
-          xp[2] -= cen[2];
-          if (kp.kind == 3) ta.nrm(t0 + threadIdx.x, xp, tn + 3 * threadIdx.x);
-        }
-        __syncthreads();
-        // (2) kernel values and envelopes; zero padding columns
-        for (int e = threadIdx.x; e < nt * ncp; e += blockDim.x) {
-          const int i = e / ncp, ql = e - i * ncp;
-          float ev = 0.0f;
-          if (mixed) {
-            float2 g = make_float2(0.0f, 0.0f);
-            if (ql < nq) {
-              const double d0 = tx[3 * i] - Xs[ql], d1 = tx[3 * i + 1] - Xs[C::CH + ql],
-                           d2 = tx[3 * i + 2] - Xs[2 * C::CH + ql];
-              const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-              if (r2 > 0.0)
-                g = kernel_eval_f32f(kp, kf, d0, d1, d2, r2, Nf[ql], Nf[C::CH + ql],
-                                     Nf[2 * C::CH + ql], Jf[ql], fR, &ev);
-            }
-            Gf[i * C::CH + ql] = g;
-          } else {
-            cplx g = {0.0, 0.0};
-            if (ql < nq)
-              g = kernel_eval_tc(kp, kf, g_sct, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql],
-                                 Xs[C::CH + ql], Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql],
-                                 Ns[2 * C::CH + ql], Js[ql], Jf[ql], fR, &ev, tn + 3 * i, has_ki);
-            Gs[i * C::CH + ql] = g;
+      // (2) kernel values and envelopes; zero padding columns
+      for (int e = threadIdx.x; e < nt * ncp; e += blockDim.x) {
+        const int i = e / ncp, p = e - i * ncp;
+        const bool real = (colinfo[p] & 0xffff) != 0xffff;
+        float ev = 0.0f;
+        if (mixed) {
+          float2 g = make_float2(0.0f, 0.0f);
+          if (real) {
+            const double d0 = tx[3 * i] - Xs[p], d1 = tx[3 * i + 1] - Xs[C::CH + p],
+                         d2 = tx[3 * i + 2] - Xs[2 * C::CH + p];
+            const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            if (r2 > 0.0)
+              g = kernel_eval_f32f(kp, kf, d0, d1, d2, r2, Nf[p], Nf[C::CH + p],
+                                   Nf[2 * C::CH + p], Jf[p], fR, &ev);
           }
-          Ef[i * C::CH + ql] = ev;
+          Gf[i * C::CH + p] = g;
+        } else {
+          cplx g = {0.0, 0.0};
+          if (real) {
+            if (fold)
+              g = kernel_eval_fold(kp.kind, kp.kr, kf, g_sct, tx[3 * i], tx[3 * i + 1],
+                                   tx[3 * i + 2], Xs[p], Xs[C::CH + p], Xs[2 * C::CH + p], Ns[p],
+                                   Ns[C::CH + p], Ns[2 * C::CH + p], Js[p], Ks[p], Jf[p], fR, &ev);
+            else
+              g = kernel_eval_tc(kp, kf, g_sct, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[p],
+                                 Xs[C::CH + p], Xs[2 * C::CH + p], Ns[p], Ns[C::CH + p],
+                                 Ns[2 * C::CH + p], Js[p], Jf[p], fR, &ev, tn + 3 * i, has_ki);
+          }
+          Gs[i * C::CH + p] = g;
         }
-        __syncthreads();
-        // envelope sums, one warp per target
-        if (eout && warp < nt) {
+        Ef[i * C::CH + p] = ev;
+      }
+      __syncthreads();
+      // envelope sums, one warp per target, one sum per piece
+      if (eout && warp < nt) {
+        for (int k = 0; k < np; ++k) {
+          const int* pc = pcs + 8 * k;
           float es = 0.0f;
-          for (int ql = lane; ql < nq; ql += 32) es += Ef[warp * C::CH + ql];
+          for (int ql = lane; ql < pc[2]; ql += 32) es += Ef[warp * C::CH + pc[3] + ql];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) es += __shfl_xor_sync(0xffffffffu, es, o);
           if (lane == 0) {
-            double* ed = eout + (int64_t)(t0 + warp) * nseg + sg;
+            double* ed = eout + (int64_t)(t0 + warp) * nseg + pc[0];
             const double v = (double)(es * escale);
-            *ed = part == 0 ? v : *ed + v;
+            *ed = pc[6] ? v : *ed + v;
           }
         }
-        // (3) split the kernel rows: warp w owns target w (rows w: Re, w + 8: Im); values
-        // are read before the barrier because the slices overwrite them
-        constexpr int VPL = C::CH / 32;
-        const int q0 = lane * VPL;
-        const bool on = warp < nt;
-        if (mixed) {
-          float re[VPL], im[VPL];
-#pragma unroll
-          for (int v = 0; v < VPL; ++v) {
-            const float2 g = (on && q0 + v < ncp) ? Gf[warp * C::CH + q0 + v] : make_float2(0.0f, 0.0f);
-            re[v] = g.x;
-            im[v] = g.y;
-          }
-          __syncthreads();
-          if (warp < C::TT) split_row_pair<5, VPL>(re, im, on, nt, Asl, C::AST, warp, q0, rowE);
-        } else {
-          double re[VPL], im[VPL];
-#pragma unroll
-          for (int v = 0; v < VPL; ++v) {
-            const cplx g = (on && q0 + v < ncp) ? Gs[warp * C::CH + q0 + v] : cplx{0.0, 0.0};
-            re[v] = g.re;
-            im[v] = g.im;
-          }
-          __syncthreads();
-          if (warp < C::TT) split_row_pair<8, VPL>(re, im, on, nt, Asl, C::AST, warp, q0, rowE);
-        }
-        __syncthreads();
-        // (4) tensor-core contraction, one warp per n-tile
-        for (int ct = warp; ct < C::NTILE; ct += nwarp) {
-          if (mixed)
-            tc_tile<D, 5, 5>(Bd, Asl, rowE, ct, ncp, nt, t0, sg, part == 0, orow);
-          else
-            tc_tile<D, 8, 9>(Bd, Asl, rowE, ct, ncp, nt, t0, sg, part == 0, orow);
-        }
-        __syncthreads();
       }
+      // (3) split the kernel rows: warp w owns target w (rows w: Re, w + 8: Im); values are
+      // read before the barrier because the slices overwrite them
+      constexpr int VPL = C::CH / 32;
+      const int q0 = lane * VPL;
+      const bool on = warp < nt;
+      if (mixed) {
+        float re[VPL], im[VPL];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+          const float2 g = (on && q0 + v < ncp) ? Gf[warp * C::CH + q0 + v] : make_float2(0.0f, 0.0f);
+          re[v] = g.x;
+          im[v] = g.y;
+        }
+        __syncthreads();
+        if (warp < C::TT) split_row_pair<D, 5, VPL>(re, im, on, Asl, warp, q0, rowE);
+      } else {
+        double re[VPL], im[VPL];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+          const cplx g = (on && q0 + v < ncp) ? Gs[warp * C::CH + q0 + v] : cplx{0.0, 0.0};
+          re[v] = g.re;
+          im[v] = g.im;
+        }
+        __syncthreads();
+        if (warp < C::TT) split_row_pair<D, 8, VPL>(re, im, on, Asl, warp, q0, rowE);
+      }
+      __syncthreads();
+      // (4) tensor-core contraction, one warp per n-tile, piece by piece
+      for (int ct = warp; ct < C::NTILE; ct += nwarp) {
+        for (int k = 0; k < np; ++k) {
+          const int* pc = pcs + 8 * k;
+          const int kb = pc[3], ke = pc[3] + ((pc[2] + 15) & ~15);
+          if (mixed)
+            tc_tile<D, 5, 5>(Bsl, Asl, rowE, ct, kb, ke, nt, t0, pc[0], pc[6] != 0, orow);
+          else
+            tc_tile<D, 8, 9>(Bsl, Asl, rowE, ct, kb, ke, nt, t0, pc[0], pc[6] != 0, orow);
+        }
+      }
+      __syncthreads();
     }
   }
 }

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <vector>
+
 #include "lcq_internal.h"
 
 namespace lcq {
@@ -44,14 +46,15 @@ static __constant__ double c_jac[(kMaxDeg + 1) * (kMaxDeg + 1) * 3];
 // The split-precision contraction scales basis column nm by 2^-E_nm.
 static __constant__ int c_kwexp[kMaxBasis];
 
-// (cos, sin)(2 pi j / 256), j = 0..255: the table of sincos_tab (lcq_tc.cuh).
-static __device__ double2 g_sct[256];
+// (cos, sin)(2 pi j / 1024), j = 0..1023: the table of sincos_tab (lcq_tc.cuh).
+constexpr int kSinCosTable = 1024;
+static __device__ double2 g_sct[kSinCosTable];
 
 // Fills c_kw, c_jac, c_kwexp and g_sct of the calling translation unit (stream-ordered).
 static inline cudaError_t upload_kw_tables(cudaStream_t st) {
   double c[kMaxBasis], jc[(kMaxDeg + 1) * (kMaxDeg + 1) * 3] = {};
   int ke[kMaxBasis];
-  double2 sct[256];
+  std::vector<double2> sct(kSinCosTable);
   for (int nn = 0; nn <= kMaxDeg; ++nn)
     for (int m = 0; m <= nn; ++m) {
       const int idx = nn * (nn + 1) / 2 + m;
@@ -68,8 +71,8 @@ static inline cudaError_t upload_kw_tables(cudaStream_t st) {
       jacobi_coef(a, 2 * m + 1, q, q + 1, q + 2);
     }
   }
-  for (int j = 0; j < 256; ++j) {
-    const double a = 2.0 * M_PI * j / 256.0;
+  for (int j = 0; j < kSinCosTable; ++j) {
+    const double a = 2.0 * M_PI * j / kSinCosTable;
     sct[j] = make_double2(cos(a), sin(a));
   }
   cudaError_t e = cudaMemcpyToSymbolAsync(c_kw, c, sizeof(c), 0, cudaMemcpyHostToDevice, st);
@@ -78,7 +81,8 @@ static inline cudaError_t upload_kw_tables(cudaStream_t st) {
   if (e == cudaSuccess)
     e = cudaMemcpyToSymbolAsync(c_kwexp, ke, sizeof(ke), 0, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyToSymbolAsync(g_sct, sct, sizeof(sct), 0, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyToSymbolAsync(g_sct, sct.data(), sizeof(double2) * kSinCosTable, 0,
+                                cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the sources live on this stack
   return e;
 }
@@ -278,10 +282,11 @@ __device__ __forceinline__ void kw_row_factors(double v, int m, const double* cf
   }
 }
 
-// X, X_u, X_v and the basis values K (stride 1) at (u, v) from the row factors of v.
-template <int D>
-__device__ __forceinline__ void kw_geometry_row(double u, const double* row, double* X,
-                                                double* Xu, double* Xv, double* K) {
+// X, X_u, X_v at (u, v) from the row factors of v; each basis value K_nm is handed to
+// emit(idx, K_nm) as it is formed (idx = n(n+1)/2 + m).
+template <int D, class F>
+__device__ __forceinline__ void kw_geometry_row_emit(double u, const double* row, double* X,
+                                                     double* Xu, double* Xv, F&& emit) {
   using RW = KwRow<D>;
   const double v = row[0], q2 = row[1];
   const double s = 2.0 * u + v - 1.0;
@@ -309,7 +314,7 @@ __device__ __forceinline__ void kw_geometry_row(double u, const double* row, dou
 #pragma unroll
     for (int a = 0; a <= D - m; ++a) {
       const int nn = m + a, idx = nn * (nn + 1) / 2 + m;
-      K[idx] = L * row[RW::J + idx];
+      emit(idx, L * row[RW::J + idx]);
     }
   }
   X[0] = x0;
@@ -321,6 +326,13 @@ __device__ __forceinline__ void kw_geometry_row(double u, const double* row, dou
   Xv[0] = v0;
   Xv[1] = v1;
   Xv[2] = v2;
+}
+
+// X, X_u, X_v and the basis values K (stride 1) at (u, v) from the row factors of v.
+template <int D>
+__device__ __forceinline__ void kw_geometry_row(double u, const double* row, double* X,
+                                                double* Xu, double* Xv, double* K) {
+  kw_geometry_row_emit<D>(u, row, X, Xu, Xv, [&](int idx, double k) { K[idx] = k; });
 }
 
 // cfd for kw_geometry_proj from cf and the projections duv (Du [n][nd], then Dv), by

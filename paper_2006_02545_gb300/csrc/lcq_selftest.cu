@@ -17,14 +17,14 @@ __device__ __forceinline__ void max_into(unsigned long long* slot, double v) {
 }
 
 // Arguments: a uniform spread over [-lim, lim] plus points just around multiples of
-// 2 pi / 256 (the table's breakpoints).
+// 2 pi / 1024 (the table's breakpoints).
 __global__ void k_check_sincos(int64_t count, double lim, unsigned long long* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
     double th;
     if (i & 1) {
       const int64_t j = (i >> 1) % 20000 - 10000;
-      th = j * (6.283185307179586 / 256.0) + ((i >> 2) % 7 - 3) * 1e-9;
+      th = j * (6.283185307179586 / kSinCosTable) + ((i >> 2) % 7 - 3) * 1e-9;
     } else {
       th = -lim + 2.0 * lim * ((double)(i >> 1) / (double)(count / 2 + 1));
     }
@@ -38,18 +38,19 @@ __global__ void k_check_sincos(int64_t count, double lim, unsigned long long* ou
 
 // One block: random complex rows (8 targets, magnitudes over 12 decades, random signs) and
 // basis-like columns bounded by 2^E_nm, nq nodes padded to ncp; the tensor-core result of
-// each (target, nm) against the FP64 sum, relative to sum_q |a_q| |b_q|.
+// each (target, nm) against a double-double sum, relative to sum_q |a_q| |b_q|.
 template <int D>
 __global__ void __launch_bounds__(256) k_check_tc(int nq, unsigned long long seed,
                                                   unsigned long long* out) {
   using C = TcCfg<D>;
   constexpr int n = C::n;
   extern __shared__ __align__(128) unsigned char smb[];
-  double* Bd = reinterpret_cast<double*>(smb + C::OFF_B);
+  uint16_t* Bsl = reinterpret_cast<uint16_t*>(smb + C::OFF_BS);
   cplx* Gs = reinterpret_cast<cplx*>(smb + C::OFF_G);
   uint16_t* Asl = reinterpret_cast<uint16_t*>(smb + C::OFF_G);
   int* rowE = reinterpret_cast<int*>(smb + C::OFF_ROWE);
   __shared__ cplx A0[C::TT][C::CH];
+  __shared__ double Bref[C::CH][n];
   __shared__ cplx res[C::TT][n];
   const int ncp = (nq + 15) & ~15;
   auto rnd = [&](unsigned long long k) {  // splitmix64 of (seed, k) -> [0, 1)
@@ -59,11 +60,17 @@ __global__ void __launch_bounds__(256) k_check_tc(int nq, unsigned long long see
     z ^= z >> 31;
     return (double)(z >> 11) * (1.0 / 9007199254740992.0);
   };
-  for (int e = threadIdx.x; e < ncp * C::BST; e += blockDim.x) {
-    const int q = e / C::BST, nm = e - q * C::BST;
+  for (int e = threadIdx.x; e < C::CH * C::NP; e += blockDim.x) {
+    const int q = e / C::NP, nm = e - q * C::NP;
     double b = 0.0;
     if (q < nq && nm < n) b = (2.0 * rnd(4 * e) - 1.0) * ldexp(1.0, c_kwexp[nm]) * rnd(4 * e + 1);
-    Bd[e] = b;
+    if (nm < n) {
+      Bref[q][nm] = b;
+      store_basis_slices<D>(Bsl, nm, q, b);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) Bsl[(size_t)i * C::NP * C::CH + C::swz(nm, q)] = 0;
+    }
   }
   for (int e = threadIdx.x; e < C::TT * C::CH; e += blockDim.x) {
     const int t = e / C::CH, q = e - t * C::CH;
@@ -88,11 +95,11 @@ __global__ void __launch_bounds__(256) k_check_tc(int nq, unsigned long long see
     im[v] = g.im;
   }
   __syncthreads();
-  split_row_pair<8, VPL>(re, im, true, C::TT, Asl, C::AST, warp, q0, rowE);
+  split_row_pair<D, 8, VPL>(re, im, true, Asl, warp, q0, rowE);
   __syncthreads();
   for (int ct = warp; ct < C::NTILE; ct += blockDim.x >> 5)
-    tc_tile<D, 8, 9>(Bd, Asl, rowE, ct, ncp, C::TT, 0, 0, true,
-                  [&](int t) { return &res[t][0]; });
+    tc_tile<D, 8, 9>(Bsl, Asl, rowE, ct, 0, ncp, C::TT, 0, 0, true,
+                     [&](int t) { return &res[t][0]; });
   __syncthreads();
   for (int e = threadIdx.x; e < C::TT * n; e += blockDim.x) {
     const int t = e / n, nm = e - t * n;
@@ -100,7 +107,7 @@ __global__ void __launch_bounds__(256) k_check_tc(int nq, unsigned long long see
     // the measured difference is the tensor-core path's own error
     double sr = 0.0, lr = 0.0, si = 0.0, li = 0.0, sa = 0.0;
     for (int q = 0; q < nq; ++q) {
-      const double b = Bd[q * C::BST + nm];
+      const double b = Bref[q][nm];
       const double pr = A0[t][q].re * b, er = fma(A0[t][q].re, b, -pr);
       const double pi = A0[t][q].im * b, ei = fma(A0[t][q].im, b, -pi);
       double s2 = sr + pr, z = s2 - sr;

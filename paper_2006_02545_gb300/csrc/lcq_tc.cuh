@@ -27,30 +27,39 @@ namespace lcq {
 constexpr int kSliceBits = 7;
 constexpr int kPoisonExp = 0x40000000;  // row exponent marking a non-finite kernel value
 
-// Shared-memory layout of the tensor-core moment engine for degree D (byte offsets).
+// Shared-memory layout of the tensor-core moment engine for degree D (byte offsets).  The
+// f16 slice arrays are [slice][row][CH] with the 16-byte chunks of each row XOR-swizzled by
+// the row index (swz), so that ldmatrix reads 8 rows of one chunk without bank conflicts.
 template <int D>
 struct TcCfg {
   static constexpr int n = (D + 1) * (D + 2) / 2;
   static constexpr int NP = (n + 7) / 8 * 8;       // basis columns padded to MMA n-tiles of 8
   static constexpr int NTILE = NP / 8;
-  static constexpr int CH = D <= 8 ? 128 : 64;     // padded nodes per chunk (multiple of 16)
-  static constexpr int BST = NP + 4;               // FP64 basis row stride: conflict-free B loads
+  static constexpr int CH = D <= 6 ? 128 : 64;     // padded nodes per chunk (multiple of 16)
   static constexpr int TT = 8;                     // targets per tile: 16 MMA rows (Re, then Im)
-  static constexpr int AST = CH + 8;               // halves per A-slice row: conflict-free ldmatrix
-  static constexpr int NSMAX = 8;
+  static constexpr int NSMAX = 8;                  // slices per FP64 operand
+  static constexpr int MAXP = CH / 16;             // pieces (segment parts) per chunk at most
   static constexpr int OFF_X = 0;                                  // Xs[3][CH] double
   static constexpr int OFF_N = OFF_X + 3 * CH * 8;                 // Ns[3][CH] double (N w)
   static constexpr int OFF_J = OFF_N + 3 * CH * 8;                 // Js[CH] double (J w)
-  static constexpr int OFF_B = OFF_J + CH * 8;                     // Bd[CH][BST] double
-  static constexpr int OFF_G = OFF_B + CH * BST * 8;               // Gs / Asl / row factors
-  static constexpr int G_A = NSMAX * 16 * AST * 2;
-  static constexpr int G_BYTES = G_A > TT * CH * 16 ? G_A : TT * CH * 16;
-  static constexpr int OFF_E = OFF_G + G_BYTES;                    // Ef[TT][CH] float
-  static constexpr int OFF_JF = OFF_E + TT * CH * 4;               // Jf[CH] float
+  static constexpr int OFF_K = OFF_J + CH * 8;                     // Ks[CH] double (folded)
+  static constexpr int OFF_BS = OFF_K + CH * 8;                    // Bsl[NSMAX][NP][CH] f16
+  static constexpr int OFF_G = OFF_BS + NSMAX * NP * CH * 2;       // Gs + Ef / Asl / row factors
+  static constexpr int G_EVAL = TT * CH * 16 + TT * CH * 4;        // Gs[TT][CH] cplx, Ef[TT][CH]
+  static constexpr int G_A = NSMAX * 16 * CH * 2;                  // Asl[NSMAX][16][CH] f16
+  static constexpr int G_BYTES = G_A > G_EVAL ? G_A : G_EVAL;
+  static constexpr int OFF_EF = OFF_G + TT * CH * 16;              // Ef, after Gs
+  static constexpr int OFF_JF = OFF_G + G_BYTES;                   // Jf[CH] float
   static constexpr int OFF_NF = OFF_JF + CH * 4;                   // Nf[3][CH] float (mixed)
   static constexpr int OFF_ROWE = OFF_NF + 3 * CH * 4;             // rowE[16] int
   static constexpr int OFF_TX = (OFF_ROWE + 16 * 4 + 15) / 16 * 16;  // tx[3 TT], tn[3 TT] double
-  static constexpr int BYTES = OFF_TX + 6 * TT * 8;
+  static constexpr int OFF_CI = OFF_TX + 6 * TT * 8;               // colinfo[CH] int
+  static constexpr int OFF_PC = OFF_CI + CH * 4;                   // pieces[MAXP][8] int
+  static constexpr int BYTES = OFF_PC + MAXP * 8 * 4;
+  // element (row, k) of a [rows][CH] f16 array, 16-byte chunks XOR-swizzled by row
+  static __device__ __forceinline__ int swz(int row, int k) {
+    return row * CH + ((((k >> 3) ^ (row & 7)) << 3) | (k & 7));
+  }
 };
 
 // |x| 2^(7 NS - E) rounded to the nearest integer, for |x| < 2^E: below 2^(7 NS).  Zero,
@@ -114,6 +123,16 @@ __device__ __forceinline__ uint32_t half2_ints(unsigned c0, unsigned c1, uint32_
   asm("sub.f16x2 %0, %1, %2;" : "=r"(r) : "r"(w), "r"(0x64006400u));
   return r ^ signs;
 }
+// Slices i and i + 1 of one value as two f16 values (low half: slice i), negative when neg:
+// -(1024 + c) is 0xE400 | c, and subtracting -1024 leaves -c.
+__device__ __forceinline__ uint32_t half2_pair(unsigned c0, unsigned c1, bool neg) {
+  const uint32_t base = neg ? 0xE400E400u : 0x64006400u;
+  const uint32_t w = base | c0 | (c1 << 16);
+  uint32_t r;
+  asm("sub.f16x2 %0, %1, %2;" : "=r"(r) : "r"(w), "r"(base));
+  return r;
+}
+
 __device__ __forceinline__ uint32_t sign_bits(double a, double b) {
   return ((uint32_t)(__double2hiint(a) < 0) << 15) | ((uint32_t)(__double2hiint(b) < 0) << 31);
 }
@@ -202,32 +221,68 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 }
 
 // sin and cos of th by table lookup and Taylor polynomials (the table method of Gal and
-// Bachelis, ACM TOMS 17, 1991): th = j (2 pi / 256) + t with j = rint(th 256 / (2 pi)) (the
-// 1.5 2^52 shifter) and |t| <= pi / 256; sin t and cos t by their Taylor series through t^7
-// and t^6 (truncation below 1.3e-20); then the angle-addition formulas with the table's
-// (cos, sin)(2 pi j / 256).  Valid for |th| < 2^20; larger arguments use sincos().
+// Bachelis, ACM TOMS 17, 1991): th = j (2 pi / 1024) + t with j = rint(th 1024 / (2 pi))
+// (the 1.5 2^52 shifter) and |t| <= pi / 1024; sin t through t^5 and cos t through t^4
+// (the next terms are below 2^-59 relative); then the angle-addition formulas with the
+// table's (cos, sin)(2 pi j / 1024): 13 FP64 instructions.  Valid for |th| < 2^20 (j times
+// the 27-bit leading part of the step stays exact); larger arguments use sincos().
 __device__ __forceinline__ void sincos_tab(double th, const double2* __restrict__ tab, double* sn,
                                            double* cs) {
   if (((__double2hiint(th) >> 20) & 0x7ff) >= 1023 + 20) {  // |th| >= 2^20 or not finite
     sincos(th, sn, cs);
     return;
   }
-  constexpr double kInvStep = 40.74366543152521;         // 256 / (2 pi)
-  constexpr double kStepHi = 0x1.921fb54p-6;             // 2 pi / 256 to 27 bits: j kStepHi exact
-  constexpr double kStepLo = 1.5501462182508444e-11;     // 2 pi / 256 - kStepHi
-  constexpr double kShift = 6755399441055744.0;                 // 1.5 2^52
+  constexpr double kInvStep = 162.97466172610083;        // 1024 / (2 pi)
+  constexpr double kStepHi = 0x1.921fb54p-8;             // 2 pi / 1024 to 27 bits
+  constexpr double kStepLo = 3.875365545627111e-12;      // 2 pi / 1024 - kStepHi
+  constexpr double kShift = 6755399441055744.0;          // 1.5 2^52
   const double y = fma(th, kInvStep, kShift);
-  const int j = __double2loint(y) & 255;
+  const int j = __double2loint(y) & (kSinCosTable - 1);
   const double jd = y - kShift;
   double t = fma(-jd, kStepHi, th);
   t = fma(-jd, kStepLo, t);
   const double z = t * t;
-  const double ps = fma(z, fma(z, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0);
-  const double s = fma(t * z, ps, t);
-  const double c = fma(z, fma(z, fma(z, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+  const double s = fma(t * z, fma(z, 1.0 / 120.0, -1.0 / 6.0), t);
+  const double c = fma(z, fma(z, 1.0 / 24.0, -0.5), 1.0);
   const double2 e = __ldg(tab + j);
   *cs = fma(e.x, c, -e.y * s);
   *sn = fma(e.y, c, e.x * s);
+}
+
+// kernel_eval_tc for real k, kinds S, D and CFIE with a real alpha, with the constants folded
+// into the per-node source data: N' = N w alpha / (4 pi) (alpha = 1 for D), Js = beta_r Jw /
+// (4 pi) (Jw / (4 pi) for S), Ks = beta_i Jw / (4 pi), fJ = FP32 Jw / (4 pi).  Then
+//   S: e^{ikr}/r Js,   D and CFIE: e^{ikr}/r ((1 - ikr) N'.d / r^2 + Js + i Ks),
+// about 39 FP64 instructions for the CFIE.  r = 0 gives 0.
+__device__ __forceinline__ cplx kernel_eval_fold(int kind, double kr, const KernelParamsF& kf,
+                                                 const double2* __restrict__ sct, double x0,
+                                                 double x1, double x2, double X0, double X1,
+                                                 double X2, double N0, double N1, double N2,
+                                                 double Js, double Ks, float fJ, float fR,
+                                                 float* env) {
+  const double d0 = x0 - X0, d1 = x1 - X1, d2 = x2 - X2;
+  const double r2 = fma(d0, d0, fma(d1, d1, d2 * d2));
+  if ((__double_as_longlong(r2) << 1) == 0) {
+    *env = 0.0f;
+    return {0.0, 0.0};
+  }
+  const double rinv = rsqrt_nr(r2);
+  const double r = r2 * rinv;
+  const double th = kr * r;
+  double sn, cs;
+  sincos_tab(th, sct, &sn, &cs);
+  {
+    // |G| Jw (|beta| + |alpha| |1 - ik r| R / r^2) in FP32, k real
+    const float fri = f32_bits(rinv), f1 = kf.kr * f32_bits(r);
+    const float fa = sqrtf(fmaf(f1, f1, 1.0f));
+    *env = fri * fJ * fmaf(kf.ea * fa * fR, fri * fri, kf.eb);
+  }
+  const double ec = cs * rinv, es = sn * rinv;
+  if (kind == 0) return {ec * Js, es * Js};
+  const double nd = fma(N0, d0, fma(N1, d1, N2 * d2)) * (rinv * rinv);
+  const double mr = kind == 2 ? nd + Js : nd;
+  const double mi = kind == 2 ? fma(-th, nd, Ks) : -th * nd;
+  return {fma(ec, mr, -es * mi), fma(ec, mi, es * mr)};
 }
 
 // kernel_eval (lcq_device.cuh) with the table sincos, the Newton-refined FP32 reciprocal
