@@ -186,7 +186,8 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- our leg
-KERNEL_SOURCES = ("lcq_common.cuh", "lcq_device.cuh")  # where k_adaptive and its helpers live
+FORM_NAMES = {0: "fp64", 1: "fp32", 2: "two-float", 3: "fp32+two-float"}  # lcq_counters [7]
+KERNEL_SOURCES = ("lcq_common.cuh", "lcq_device.cuh", "lcq_tc.cuh")  # k_adaptive and its helpers
 
 
 def kernel_source_sha():
@@ -296,7 +297,10 @@ def run_ours(args, rank, world, local_rank):
                 p2 = lcq.params(eps, eta=wl.eta, test_dirs=W.test_directions(7),
                                 leaf_order=args.leaf_order)
                 times, ad = [], []
-                for it in range(3):
+                # the first generations of a new (precision, tolerance) key time the group
+                # size tuner's candidates (at most five); the last two are timed
+                nit = 7
+                for it in range(nit):
                     flush.zero_()
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
@@ -306,12 +310,13 @@ def run_ours(args, rank, world, local_rank):
                                                precision=prec)
                     e1.record(stream)
                     st = ctx.sync()
-                    if it > 0:
+                    if it >= nit - 2:
                         times.append(e0.elapsed_time(e1))
                         ad.append(ctx.stage_times()[0][3])
-                    if it < 2:
+                    if it < nit - 1:
                         corr.close()
                         near.close()
+                forms = int(ctx.counters()[7])
                 u = lcq.apply_corrected_CFIE(ctx, ds, near, corr, sig, NT).cpu().numpy()
                 val = corr.export(NT)[2].copy()
                 corr.close()
@@ -326,7 +331,8 @@ def run_ours(args, rank, world, local_rank):
                     ru, rv = ref_u[eps]
                     rec["rel_l2_vs_fp64"] = float(np.linalg.norm(u - ru) / np.linalg.norm(ru))
                     rec["csr_rel_l2_vs_fp64"] = float(np.linalg.norm(val - rv) / np.linalg.norm(rv))
-                    rec["fp32_used"] = eps >= 1e-6
+                    rec["fp32_used"] = forms != 0
+                    rec["pair_form"] = FORM_NAMES[forms]
                 variants[key] = rec
 
     # the 20-patch sphere (single layer, k = 1, eps = 1e-6, eta = 1.25): 300 points, a
@@ -340,7 +346,7 @@ def run_ours(args, rank, world, local_rank):
         stn = torch.from_numpy(sw.tgt_node).to(dev)
         sp = lcq.params(sw.eps, eta=sw.eta, test_dirs=W.test_directions(7))
         times, sst = [], []
-        for it in range(12):
+        for it in range(16):   # the first generations time the group-size candidates
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -348,14 +354,41 @@ def run_ours(args, rank, world, local_rank):
             corr = lcq.gen_corrections(ctx, sds, near, "S", 1.0, sp)
             e1.record(stream)
             st_s = ctx.sync()
-            if it >= 6:
+            if it >= 8:
                 times.append(e0.elapsed_time(e1))
                 sst.append(ctx.stage_times()[0])
+                s_group = int(ctx.counters()[5])
             corr.close()
             near.close()
+        # the same generation captured once as a CUDA graph (lcq_plan) and replayed: the
+        # geometry refresh and stages 1-6 with no host synchronization (near lists frozen)
+        near = lcq.build_near_lists(ctx, sds, sx, stn, sp)
+        corr = lcq.gen_corrections(ctx, sds, near, "S", 1.0, sp)
+        ctx.sync()
+        plan = lcq.Plan(ctx, sds, near, corr)
+        gtimes = []
+        for it in range(13):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.launch()
+            e1.record(stream)
+            st_g = ctx.sync()
+            if it >= 3:
+                gtimes.append(e0.elapsed_time(e1))
+        g_launches = int(ctx.stage_times()[1])
+        plan.close()
+        corr.close()
+        near.close()
         small = {"workload": sw.name, "points": sw.surface.n_points,
                  "value": sw.surface.n_points / (statistics.median(times) / 1e3), "unit": UNIT,
                  "ms_per_step": statistics.median(times), "status": st_s,
+                 "group_size": s_group,
+                 "graph": {"ms_per_step": statistics.median(gtimes),
+                           "value": sw.surface.n_points / (statistics.median(gtimes) / 1e3),
+                           "unit": UNIT, "status": st_g, "launches_per_step": g_launches,
+                           "note": "lcq_plan replay: geometry refresh + generation, near "
+                                   "lists frozen, no host synchronization"},
                  "stages_ms": dict(zip(["near_lists", "far_order", "smooth_annulus", "adaptive",
                                         "self", "v2c"],
                                        [statistics.median(x[i] for x in sst) for i in range(6)]))}
@@ -392,6 +425,20 @@ def run_ours(args, rank, world, local_rank):
         b_launches = ctx.stage_times()[1]
         corr.close()
         near.close()
+        # the same batch in the mixed form (per surface: FP32 pairs at eps = 1e-6,
+        # two-float ones at 1e-9)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        near = lcq.build_near_lists_batched(ctx, bds, poff, bx_d, btn_d, bp)
+        corr = lcq.gen_corrections_batched(ctx, bds, near, "CFIE", phys, bp, precision="mixed")
+        e1.record(stream)
+        st_bm = ctx.sync()
+        bm_ms = e0.elapsed_time(e1)
+        bm_forms = int(ctx.counters()[7])
+        corr.close()
+        near.close()
         one_ms, one_launches = 0.0, 0
         for i, (k, a, b, eps) in enumerate(phys):
             n0, n1 = int(bs.node_off[poff[i]]), int(bs.node_off[poff[i + 1]])
@@ -420,7 +467,10 @@ def run_ours(args, rank, world, local_rank):
                    "value": bs.n_points / (bms / 1e3), "unit": UNIT, "ms_per_step": bms,
                    "launches_per_step": int(b_launches), "status": st_b,
                    "one_by_one": {"value": bs.n_points / (one_ms / 1e3), "ms": one_ms,
-                                  "launches": int(one_launches)}}
+                                  "launches": int(one_launches)},
+                   "mixed": {"value": bs.n_points / (bm_ms / 1e3), "unit": UNIT,
+                             "ms_per_step": bm_ms, "status": st_bm,
+                             "pair_form": FORM_NAMES[bm_forms]}}
         del bds, bx_d, btn_d
 
     # the paper's Table 1 on its twisted torus (2400 patches, S, k = 1): oversampling
@@ -484,15 +534,17 @@ def run_ours(args, rank, world, local_rank):
             dv = torch.empty(nnz, dtype=torch.complex128, device=dev)
             corr.export(ls.n_points, out=(None, None, dv))
             vals[prec] = dv
+            forms = int(ctx.counters()[7])
             large[prec] = {"value": ls.n_points / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
                            "status": st_l, "nnz": nnz,
-                           "adaptive_ms": ctx.stage_times()[0][3]}
+                           "adaptive_ms": ctx.stage_times()[0][3],
+                           "pair_form": FORM_NAMES[forms], "fp32_used": forms != 0}
             corr.close()
             near.close()
         large["mixed"]["csr_rel_l2_vs_fp64"] = float(
             torch.linalg.vector_norm(vals["mixed"] - vals["fp64"]) /
             torch.linalg.vector_norm(vals["fp64"]))
-        large["mixed"]["fp32_used"] = lw.eps >= 1e-6
+
         del vals
         sub = np.arange(0, ls.n_points, ls.n_points // 100000)[:100000]
         sx = torch.from_numpy(np.ascontiguousarray(lw.tgt_xyz[:, sub])).to(dev)
@@ -500,8 +552,7 @@ def run_ours(args, rank, world, local_rank):
         near = lcq.build_near_lists(ctx, lds, sx, stn, lp)
         corr = lcq.gen_corrections(ctx, lds, near, lw.kernel, lw.k, lp, lw.alpha, lw.beta)
         sig = torch.from_numpy(W.density(ls.n_points, 0)).to(dev)
-        lcq.apply_corrected_CFIE(ctx, lds, near, corr, sig, len(sub))   # warm-up
-        ctx.sync()
+        ctx.sync()   # one timed apply: a minute-long launch needs no warm-up
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)

@@ -36,6 +36,7 @@ extern "C" {
 typedef struct lcq_ctx lcq_ctx;
 typedef struct lcq_near lcq_near;
 typedef struct lcq_corr lcq_corr;
+typedef struct lcq_plan lcq_plan;
 
 typedef enum {
   LCQ_OK = 0,
@@ -263,6 +264,27 @@ lcq_status lcq_apply_corrected(lcq_ctx* ctx, const lcq_surface* surf, const lcq_
 
 void lcq_corr_destroy(lcq_corr* corr);
 
+/* Captured regeneration (an extension: the paper has no counterpart).  lcq_plan_create
+ * records, as one CUDA graph, the device work that regenerates corr in place from the
+ * current contents of surf->xyz: the positions of the on-surface targets (their nodes),
+ * the chart geometry of every patch (Sec. 3.2, Sec. 4; and for S' the target normals), then the far orders, the smooth, annulus and adaptive
+ * moments, the self weights and the V contraction (Sec. 4.2-4.3, 5.3) with the kernel,
+ * tolerance, precision, test directions and adaptive work-group sizes of corr's
+ * generation.  lcq_plan_launch replays it on ctx's stream: no host synchronization and no
+ * allocation, a few launches' worth of CPU time.  The near lists (pairs, adaptive flags,
+ * CSR layout) are not rebuilt: between launches the caller may move the nodes (write new
+ * coordinates into surf->xyz on the stream) only as far as the lists stay those of the
+ * moved surface, as for lcq_shape_gradient.  Results equal those of lcq_gen_corrections on
+ * the same coordinates and lists bit for bit.  lcq_stage_times are not recorded by a
+ * launch; lcq_counters are.  The plan owns its work buffers (about the generation's
+ * transient memory); ctx, near, corr and surf->xyz must outlive it.
+ * Errors: LCQ_ERR_ARG when corr does not belong to near and surf, LCQ_ERR_CUDA when the
+ * capture or instantiation fails (nothing is left allocated). */
+lcq_status lcq_plan_create(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
+                           lcq_corr* corr, lcq_plan** out);
+lcq_status lcq_plan_launch(lcq_plan* plan);
+void lcq_plan_destroy(lcq_plan* plan);
+
 /* Wait for the context's stream (polling, at most timeout_ms; < 0 waits
  * without limit), then return and clear the latched device status. */
 lcq_status lcq_sync(lcq_ctx* ctx, int64_t timeout_ms);
@@ -276,7 +298,9 @@ lcq_status lcq_sync(lcq_ctx* ctx, int64_t timeout_ms);
  * The adaptive walk takes its work in items of at most a group size of targets of one
  * patch; an online tuner in the context times each candidate size once per key (degree,
  * kernel, tolerance decade, precision, size of the adaptive work) on the generations that
- * use it and keeps the fastest.  Every result is the same for every group size. */
+ * use it and keeps the fastest; with at least 16 patches of adaptive targets per resident
+ * block it takes whole patches without timing.  Every result is the same for every group
+ * size. */
 lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out8);
 
 /* Stage timings of the last lcq_build_near_lists and lcq_gen_corrections on ctx, from
@@ -338,13 +362,17 @@ lcq_status lcq_adaptive_corrections_noalloc(int deg, const double* y, int64_t n_
 lcq_status lcq_pipe_peaks(int device, double* out, int n_out);
 
 /* Device self-checks of the adaptive kernel's arithmetic (no counterpart in the paper).
- * Writes host out[n_out], up to 3 values (-1 where not measured):
+ * Writes host out[n_out], up to 5 values (-1 where not measured):
  *   [0] max |sin - sin_ref|, |cos - cos_ref| of the table-driven sincos against CUDA's
  *       sincos over 4M arguments in [-3000, 3000] and around the table's breakpoints;
  *   [1] degree 6 and [2] degree 10: max over every output of |tensor-core contraction -
  *       FP64 contraction| / sum_q |a_q| |b_q| for random kernel-like rows (12 decades of
- *       magnitude, random phases) and basis-like columns at their bounds.
- * Allocates 32 bytes of device memory and a private stream for the call; LCQ_ERR_ARG for a
+ *       magnitude, random phases) and basis-like columns at their bounds;
+ *   [3] max |two-float kernel value - FP64 kernel value| relative to the sum of the
+ *       magnitudes of its terms, S, D and CFIE at k = 1.3, 2 pi, 20, 2M near-singular and
+ *       tangent-plane configurations (the mixed form below eps = 1e-6);
+ *   [4] max |two-float sin, cos - CUDA's| / (1 + |th|) over |th| < 3000.
+ * Allocates 64 bytes of device memory and a private stream for the call; LCQ_ERR_ARG for a
  * null out or n_out < 1, LCQ_ERR_CUDA on any CUDA failure. */
 lcq_status lcq_selftest(int device, double* out, int n_out);
 

@@ -190,10 +190,10 @@ bool launch_adaptive_grad(int d, const LaunchCommon& lc, const int* plist, int c
                           const Dev& dv, const KernelParams& kp, double eps, double normV,
                           int leaf_order, int max_depth, const void* I_smooth, void* I_near,
                           int32_t* leaves, void* work, int64_t stride, int A_max, int levels,
-                          int grid, int* status, int* sched, double mix, const GradArgs& ga) {
+                          int grid, int* status, int* sched, int form, const GradArgs& ga) {
   return dispatch<AdaptiveGradL>(d, lc, plist, count, dv, kp, eps, normV, leaf_order, max_depth,
                                  I_smooth, I_near, leaves, work, stride, A_max, levels, grid,
-                                 status, sched, mix, ga);
+                                 status, sched, form, ga);
 }
 
 bool launch_grad_v2c(int d, const LaunchCommon& lc, const int* plist, int count,

@@ -211,7 +211,7 @@ template <int D>
 void AdaptiveGradL<D>::run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                   const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                   const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
-                  int A_max, int levels, int grid, int* status, int* sched, double mix,
+                  int A_max, int levels, int grid, int* status, int* sched, int form,
                   const GradArgs& ga) {
     const size_t sm = adaptive_smem_bytes<D>();
     cudaFuncSetAttribute(k_adaptive<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -220,7 +220,7 @@ void AdaptiveGradL<D>::run(const LaunchCommon& lc, const int* plist, int count, 
     ++*lc.launches;
     k_adaptive<D, true><<<grid, kThreads, sm, lc.stream>>>(
         plist, count, dv, kp, eps, normV, leaf_order, max_depth, (const cplx*)I_smooth,
-        (cplx*)I_near, leaves, (unsigned char*)work, w, status, sched, mix, ga, nullptr, 0);
+        (cplx*)I_near, leaves, (unsigned char*)work, w, status, sched, form, ga, nullptr, 0);
   }
 
 template <int D>

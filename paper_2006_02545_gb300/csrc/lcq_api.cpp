@@ -321,6 +321,7 @@ lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out8) {
   for (int i = 0; i < 8; ++i) out8[i] = h[i];
   out8[5] = ctx->last_group_size;
   out8[6] = ctx->last_items;
+  out8[7] = ctx->last_forms;
   return LCQ_OK;
 }
 
@@ -749,18 +750,25 @@ static Dev make_dev(lcq_ctx* ctx, const lcq_near* nr, const int32_t* q, int ldI,
   return dv;
 }
 
-// Per-block workspace of the adaptive kernel (sized by the largest adaptive set and the
-// depth cap) and its grid; grows ctx->work when needed.
-static cudaError_t adaptive_work(lcq_ctx* ctx, const lcq_near* nr, int64_t A, int levels,
-                                 int64_t* stride_out, int* grid_out) {
+// Per-block workspace of the adaptive kernel (sized by the largest work item and the depth
+// cap) and its grid.
+static void adaptive_stride(lcq_ctx* ctx, const lcq_near* nr, int64_t A, int levels,
+                            int64_t* stride_out, int* grid_out) {
   const int64_t n = nr->n_max;
   int64_t stride = A * n * 16 + A * 4 * n * 16 + (int64_t)levels * A * 4 * n * 16 +
                    (int64_t)levels * A * 4 + 2 * A * 4 + (int64_t)levels * 4 + 8 + A * 4 * 8 + 256;
-  stride = (stride + 255) / 256 * 256;
+  *stride_out = (stride + 255) / 256 * 256;
   int bps = 1;
   for (int d = 1; d <= kMaxDeg; ++d)
     if (nr->ad_count[d]) bps = std::max(bps, adaptive_blocks_per_sm(d));
-  const int agrid = ctx->num_sms * bps;
+  *grid_out = ctx->num_sms * bps;
+}
+// The same in the context's workspace, grown when needed.
+static cudaError_t adaptive_work(lcq_ctx* ctx, const lcq_near* nr, int64_t A, int levels,
+                                 int64_t* stride_out, int* grid_out) {
+  int64_t stride = 0;
+  int agrid = 0;
+  adaptive_stride(ctx, nr, A, levels, &stride, &agrid);
   const size_t need = (size_t)stride * agrid;
   if (ctx->work_bytes < need) {
     if (ctx->work) {
@@ -779,33 +787,61 @@ static cudaError_t adaptive_work(lcq_ctx* ctx, const lcq_near* nr, int64_t A, in
 }
 
 // ---------------------------------------------------------------------------- tuner
-static bool mixed_form_hint(lcq_precision precision, lcq_kernel kernel, const lcq_near* nr,
-                            double eps0) {
-  return precision == LCQ_MIXED && kernel != LCQ_SP && (nr->grouped || eps0 >= kMixedMinEps);
+// Form of the pair evaluations in the moment kernels (pair_form): 0 FP64; for LCQ_MIXED
+// 1 (FP32) for eps >= kMixedMinEps, 2 (two-float) for eps >= kTwoFloatMinEps, 0 below; 3 in
+// a batch, where each surface's tolerance decides.  S' is always FP64.
+static int pair_form_mode(lcq_precision precision, lcq_kernel kernel, const lcq_near* nr,
+                          double eps0) {
+  if (precision != LCQ_MIXED || kernel == LCQ_SP) return 0;
+  if (nr->grouped) return 3;
+  return eps0 >= kMixedMinEps ? 1 : (eps0 >= kTwoFloatMinEps ? 2 : 0);
+}
+// The forms a generation uses, as a bit mask (1: FP32, 2: two-float; 0: FP64 only); the
+// two-float form needs a real k and a real alpha (the folded kernel constants).
+static int forms_used(int mode, const KernelParams& kp, const std::vector<GroupParams>& grp) {
+  auto one = [](int f, const KernelParams& p) {
+    if (f == 1) return 1;
+    if (f == 2 && p.ki == 0.0 && p.kind <= 2 && p.ai == 0.0) return 2;
+    return 0;
+  };
+  if (mode != 3) return one(mode, kp);
+  int m = 0;
+  for (const GroupParams& g : grp)
+    m |= one(g.eps >= kMixedMinEps ? 1 : (g.eps >= kTwoFloatMinEps ? 2 : 0), g.kp);
+  return m;
 }
 
 // Tuner state of (degree, kernel, tolerance decade, precision, size class of the degree's
 // adaptive work, batch or not), with its candidates on first use.
 static lcq_tune& tune_state(lcq_ctx* ctx, const lcq_near* nr, int d, int kernel, double eps,
-                            bool mixed, int64_t slots) {
+                            int form, int64_t slots) {
   const int dec = (int)std::floor(std::log10(eps)) + 40;
   int cls = 0;
   while ((int64_t(1) << cls) < nr->ad_total[d] + 1 && cls < 62) ++cls;
   const uint64_t key = (uint64_t)d | ((uint64_t)kernel << 4) | ((uint64_t)(dec & 63) << 8) |
-                       ((uint64_t)mixed << 14) | ((uint64_t)cls << 15) |
-                       ((uint64_t)nr->grouped << 21) | ((uint64_t)(nr->ad_max[d] > 16) << 22);
+                       ((uint64_t)cls << 15) | ((uint64_t)nr->grouped << 21) |
+                       ((uint64_t)(nr->ad_max[d] > 16) << 22) | ((uint64_t)form << 23);
   lcq_tune& tu = ctx->tune[key];
   if (tu.cand.empty()) {
     std::vector<int> c;
     const int64_t amax = std::max<int64_t>(nr->ad_max[d], 1);
     c.push_back((int)std::min<int64_t>(amax, 0x7fffffff));  // whole patches
-    for (int64_t ips : {1, 4, 16}) {
-      const int64_t want = ips * slots;
-      int64_t g = (nr->ad_total[d] + want - 1) / want;
-      g = std::max<int64_t>(16, (g + 7) / 8 * 8);
-      c.push_back((int)std::min<int64_t>(g, amax));
+    // Splitting patches into groups only pays when whole patches leave slots idle or
+    // unbalanced; with 16 or more whole patches per resident block (longest first) they do
+    // neither, and timing the other candidates would cost whole generations.
+    if ((int64_t)nr->ad_count[d] < 16 * slots) {
+      for (int64_t ips : {1, 4, 16}) {
+        const int64_t want = ips * slots;
+        int64_t g = (nr->ad_total[d] + want - 1) / want;
+        g = std::max<int64_t>(16, (g + 7) / 8 * 8);
+        c.push_back((int)std::min<int64_t>(g, amax));
+      }
+      c.push_back((int)std::min<int64_t>(16, amax));
+      // small adaptive work (fewer 16-target items than resident blocks): smaller groups
+      // spread one patch's targets over more blocks, shortening the longest walk
+      if ((nr->ad_total[d] + 15) / 16 < slots)
+        for (int g : {8, 4, 2, 1}) c.push_back((int)std::min<int64_t>(g, amax));
     }
-    c.push_back((int)std::min<int64_t>(16, amax));
     std::sort(c.begin(), c.end(), std::greater<int>());
     c.erase(std::unique(c.begin(), c.end()), c.end());
     tu.cand = c;
@@ -848,6 +884,205 @@ static int tune_pick(lcq_tune& tu, int* measure) {
   }
   if (best >= 0) return best;
   return tu.pending >= 0 ? tu.pending : 0;
+}
+
+// The fastest candidate timed so far (the first when none is).
+static int tune_best(const lcq_tune& tu) {
+  int best = 0;
+  for (size_t i = 0; i < tu.cand.size(); ++i)
+    if (tu.ms_per[i] >= 0.0 && (tu.ms_per[best] < 0.0 || tu.ms_per[i] < tu.ms_per[best]))
+      best = (int)i;
+  return best;
+}
+
+// Work buffers and launch choices of one generation (gen_impl) or of a captured one
+// (lcq_plan_create).
+struct GenScratch {
+  Dev dv{};
+  double* ddirs = nullptr;
+  int ndirs = 0;
+  void *Is = nullptr, *In = nullptr, *InS = nullptr;
+  double* fscr = nullptr;
+  int fgrid = 0;
+  int64_t *gng = nullptr, *gscr = nullptr, *ggofs[kMaxDeg + 1] = {nullptr};
+  int gsz[kMaxDeg + 1] = {0};
+  int tune_meas[kMaxDeg + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+  lcq_tune* tune_st[kMaxDeg + 1] = {nullptr};
+  int64_t A_eff = 0, astride = 0;
+  int agrid = 0, levels = 0, sorder = 0, form = 0;
+  void* work = nullptr;   // adaptive workspace (the context's, or the plan's own)
+  bool own_work = false;
+};
+
+// A captured generation (lcq_plan_create): its own work buffers and the graph.
+struct lcq_plan {
+  lcq_ctx* ctx = nullptr;
+  const lcq_near* near = nullptr;
+  lcq_corr* corr = nullptr;
+  lcq_params params{};
+  GenScratch gs;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;   // kernel launches in the graph
+};
+
+// The far-order scratch, the work groups of the adaptive walk and the adaptive workspace.
+// Group sizes: fixed_gsz where given, else the context's tuner (timing a candidate when
+// `tune`, else each key's best so far).  With own_work the workspace belongs to gs alone.
+static lcq_status gen_scratch(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, double eps0,
+                              const lcq_params* params, bool tune, GenScratch* gs,
+                              const int* fixed_gsz = nullptr) {
+  cudaStream_t st = ctx->stream;
+  gs->fgrid = ctx->num_sms * 2;
+  CK(dalloc(st, &gs->fscr, (size_t)gs->fgrid * 2 * kMaxTestPts * kMaxBasis * 2));
+  gs->levels = params->max_depth;
+  // Work groups of the adaptive walk: at most gsz[d] targets of one patch per item, chosen
+  // per degree among candidates that give about 1, 4 or 16 items per resident block, 16
+  // targets (fewer for small work) or whole patches; the grouping changes no result.
+  ctx->last_group_size = 0;
+  ctx->last_items = 0;
+  if (nr->n_adaptive > 0) {
+    int bps = 1;
+    for (int d = 1; d <= kMaxDeg; ++d)
+      if (nr->ad_count[d]) bps = std::max(bps, adaptive_blocks_per_sm(d));
+    const int64_t slots = (int64_t)ctx->num_sms * bps;
+    for (int d = 1; d <= kMaxDeg; ++d) {
+      gs->tune_meas[d] = -1;
+      if (!nr->ad_count[d]) continue;
+      if (fixed_gsz && fixed_gsz[d] > 0) {
+        gs->gsz[d] = fixed_gsz[d];
+      } else {
+        lcq_tune& tu = tune_state(ctx, nr, d, (int)kernel, eps0, gs->form, slots);
+        gs->tune_st[d] = &tu;
+        if (tune) {
+          const int pick = tune_pick(tu, &gs->tune_meas[d]);
+          gs->gsz[d] = tu.cand[pick];
+        } else {
+          gs->gsz[d] = tu.cand[tune_best(tu)];
+        }
+      }
+      gs->A_eff = std::max<int64_t>(gs->A_eff, gs->gsz[d]);
+      ctx->last_group_size = std::max(ctx->last_group_size, gs->gsz[d]);
+      for (int64_t a : nr->ad_nad_h[d]) ctx->last_items += (a + gs->gsz[d] - 1) / gs->gsz[d];
+    }
+    if (gs->own_work) {
+      adaptive_stride(ctx, nr, gs->A_eff, gs->levels, &gs->astride, &gs->agrid);
+      CK(cudaMallocAsync(&gs->work, (size_t)gs->astride * gs->agrid, st));
+    } else {
+      CK(adaptive_work(ctx, nr, gs->A_eff, gs->levels, &gs->astride, &gs->agrid));
+      gs->work = ctx->work;
+    }
+    int maxc = 0;
+    for (int d = 1; d <= kMaxDeg; ++d) maxc = std::max(maxc, nr->ad_count[d]);
+    CK(dalloc(st, &gs->gng, (size_t)maxc + 1));
+    CK(dalloc(st, &gs->gscr, (size_t)2 * ((maxc + 1 + 1023) / 1024) + 64));
+    for (int d = 1; d <= kMaxDeg; ++d)
+      if (nr->ad_count[d]) CK(dalloc(st, &gs->ggofs[d], (size_t)nr->ad_count[d] + 1));
+  }
+  return LCQ_OK;
+}
+
+// Releases gs's buffers (stream-ordered).
+static void gen_free(cudaStream_t st, GenScratch* gs) {
+  if (gs->ddirs) dfree(st, gs->ddirs);
+  if (gs->fscr) dfree(st, gs->fscr);
+  if (gs->gng) dfree(st, gs->gng);
+  if (gs->gscr) dfree(st, gs->gscr);
+  for (int d = 1; d <= kMaxDeg; ++d)
+    if (gs->ggofs[d]) dfree(st, gs->ggofs[d]);
+  if (gs->Is) cudaFreeAsync(gs->Is, st);
+  if (gs->In) cudaFreeAsync(gs->In, st);
+  if (gs->InS) cudaFreeAsync(gs->InS, st);
+  if (gs->own_work && gs->work) cudaFreeAsync(gs->work, st);
+  *gs = GenScratch{};
+}
+
+// Stages 1-6 of a generation into c: launches, event records and stream waits only (no
+// allocation and no host synchronization), so that the sequence can be captured into a
+// CUDA graph.  `timed` adds the stage events and the tuner's timing events.
+static lcq_status gen_launch(lcq_ctx* ctx, const lcq_near* nr, lcq_corr* c,
+                             const lcq_params* params, const GenScratch& gs, bool timed) {
+  cudaStream_t st = ctx->stream;
+  const Dev& dv = gs.dv;
+  const KernelParams& kp = c->kp;
+  const double eps0 = c->eps0;
+  CK(cudaMemsetAsync(c->leaves, 0, std::max<int64_t>(nr->n_pairs, 1) * 4, st));
+  CK(cudaMemsetAsync(c->val, 0, std::max<int64_t>(nr->nnz, 1) * 16, st));
+  CK(cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(long long), st));
+  // Stages 1-4 and 6 depend on one another and run on the highest-priority stream; the
+  // self weights (5) depend on none of them and run on the lowest-priority one from the
+  // start, so their blocks fill what the chain leaves idle (the small far-order and
+  // smooth-rule launches, the end of the adaptive walk) without delaying it.
+  CK(cudaEventRecord(ctx->fork, st));
+  CK(cudaStreamWaitEvent(ctx->hi, ctx->fork, 0));
+  CK(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
+  LaunchCommon lh{ctx->hi, ctx->num_sms, &ctx->launches_corr};
+  cudaStream_t sh = ctx->hi;
+  if (timed) CK(cudaEventRecord(ctx->ev[2], sh));
+  // 1. far order q_j and annulus order (Sec. 4.2, Eq. qj)
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_farorder(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, kp, eps0, params->m_max,
+                    ctx->deg[d].normV, gs.ddirs, gs.ndirs, gs.fscr, gs.fgrid, c->q, c->q_near,
+                    ctx->d_sched);
+  }
+  CK(cudaGetLastError());
+  // 5. self weights (Sec. 4, Eq. errestself), on the low-priority stream
+  if (timed) CK(cudaEventRecord(ctx->ev_self[0], ctx->side));
+  if (nr->n_self > 0) {
+    LaunchCommon ls{ctx->side, ctx->num_sms, &ctx->launches_corr};
+    for (int d = 1; d <= kMaxDeg; ++d) {
+      if (!nr->plist_count[d]) continue;
+      launch_self(d, ls, dv, nr->deg, kp, gs.sorder, gs.InS);
+    }
+  }
+  CK(cudaGetLastError());
+  if (timed) CK(cudaEventRecord(ctx->ev_self[1], ctx->side));
+  CK(cudaEventRecord(ctx->join, ctx->side));
+  if (timed) CK(cudaEventRecord(ctx->ev[3], sh));
+  // 2. smooth-rule moments of every near and self pair; 3. annulus moments
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_rule_moments(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, 3, c->q, c->q_near, kp,
+                        gs.Is, gs.In, gs.form);
+  }
+  CK(cudaGetLastError());
+  if (timed) CK(cudaEventRecord(ctx->ev[4], sh));
+  // 4. adaptive near moments (Sec. 4.3)
+  if (nr->n_adaptive > 0) {
+    for (int d = 1; d <= kMaxDeg; ++d) {
+      if (!nr->ad_count[d]) continue;
+      const int cnt = nr->ad_count[d];
+      lcq_tune* tu = gs.tune_st[d];
+      const bool meas = timed && tu && gs.tune_meas[d] >= 0;
+      if (meas) CK(cudaEventRecord(tu->e0, sh));
+      launch_group_offsets(lh, nr->ad_list_dev[d], cnt, nr->ad_ptr, gs.gsz[d], gs.gng,
+                           gs.ggofs[d], gs.gscr);
+      launch_adaptive(d, lh, nr->ad_list_dev[d], cnt, dv, kp, eps0 * params->eps_loosen,
+                      ctx->deg[d].normV, params->leaf_order, params->max_depth, gs.Is, gs.In,
+                      c->leaves, gs.work, gs.astride, (int)gs.A_eff, gs.levels, gs.agrid,
+                      ctx->d_status, ctx->d_sched + d, gs.form, gs.ggofs[d], gs.gsz[d]);
+      if (meas) {
+        CK(cudaEventRecord(tu->e1, sh));
+        tu->pending = gs.tune_meas[d];
+        tu->pend_pairs = (double)nr->ad_total[d];
+      }
+    }
+    CK(cudaGetLastError());
+  }
+  if (timed) CK(cudaEventRecord(ctx->ev[5], sh));
+  CK(cudaStreamWaitEvent(sh, ctx->join, 0));  // self weights done
+  if (timed) CK(cudaEventRecord(ctx->ev[6], sh));
+  // 6. c = V^T (I_near - I_smooth) into the CSR
+  for (int d = 1; d <= kMaxDeg; ++d) {
+    if (!nr->plist_count[d]) continue;
+    launch_v2c(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, gs.In, gs.Is,
+               gs.InS, c->val);
+  }
+  CK(cudaGetLastError());
+  if (timed) CK(cudaEventRecord(ctx->ev[7], sh));
+  CK(cudaEventRecord(ctx->done, sh));
+  CK(cudaStreamWaitEvent(st, ctx->done, 0));
+  return LCQ_OK;
 }
 
 static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, int n_phys,
@@ -907,9 +1142,6 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   CK(dalloc(st, &c->q, P));
   CK(dalloc(st, &c->q_near, P));
   CK(dalloc(st, &c->leaves, nr->n_pairs));
-  CK(cudaMemsetAsync(c->leaves, 0, std::max<int64_t>(nr->n_pairs, 1) * 4, st));
-  CK(cudaMemsetAsync(c->val, 0, std::max<int64_t>(nr->nnz, 1) * 16, st));
-  CK(cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(long long), st));
 
   // test directions
   std::vector<double> dirs;
@@ -964,140 +1196,29 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   }
   Dev dv = make_dev(ctx, nr, c->q, ldI, c->grp);
 
-  // the mixed form (FP32 pair evaluation in the smooth, annulus and adaptive moments);
-  // per surface of a batch the kernels also check the surface's tolerance
-  const bool mixed_form = precision == LCQ_MIXED && kernel != LCQ_SP &&
-                          (nr->grouped || eps0 >= kMixedMinEps);
-  c->mixed_form = mixed_form;
-  const int fgrid = ctx->num_sms * 2;
-  double* fscr;
-  CK(dalloc(st, &fscr, (size_t)fgrid * 2 * kMaxTestPts * kMaxBasis * 2));
-  const int levels = params->max_depth;
-  int64_t astride = 0;
-  int agrid = 0;
-  // Work groups of the adaptive walk: at most gsz[d] targets of one patch per item.  The
-  // size is chosen per degree by the context's online tuner (tune_group_size) among
-  // candidates that give about 1, 4 or 16 items per resident block, 16 targets, or whole
-  // patches; the grouping changes no result.
-  int gsz[kMaxDeg + 1] = {0};
-  int tune_meas[kMaxDeg + 1];
-  lcq_tune* tune_st[kMaxDeg + 1] = {nullptr};
-  int64_t A_eff = 0;
-  ctx->last_group_size = 0;
-  ctx->last_items = 0;
-  if (nr->n_adaptive > 0) {
-    int bps = 1;
-    for (int d = 1; d <= kMaxDeg; ++d)
-      if (nr->ad_count[d]) bps = std::max(bps, adaptive_blocks_per_sm(d));
-    const int64_t slots = (int64_t)ctx->num_sms * bps;
-    for (int d = 1; d <= kMaxDeg; ++d) {
-      tune_meas[d] = -1;
-      if (!nr->ad_count[d]) continue;
-      lcq_tune& tu = tune_state(ctx, nr, d, (int)kernel, eps0, mixed_form_hint(precision, kernel, nr, eps0),
-                                slots);
-      tune_st[d] = &tu;
-      const int pick = tune_pick(tu, &tune_meas[d]);
-      gsz[d] = tu.cand[pick];
-      A_eff = std::max<int64_t>(A_eff, gsz[d]);
-      ctx->last_group_size = std::max(ctx->last_group_size, gsz[d]);
-      for (int64_t a : nr->ad_nad_h[d]) ctx->last_items += (a + gsz[d] - 1) / gsz[d];
-    }
-    CK(adaptive_work(ctx, nr, A_eff, levels, &astride, &agrid));
-  }
-  int64_t *gng = nullptr, *gscr = nullptr, *ggofs[kMaxDeg + 1] = {nullptr};
-  if (nr->n_adaptive > 0) {
-    int maxc = 0;
-    for (int d = 1; d <= kMaxDeg; ++d) maxc = std::max(maxc, nr->ad_count[d]);
-    CK(dalloc(st, &gng, (size_t)maxc + 1));
-    CK(dalloc(st, &gscr, (size_t)2 * ((maxc + 1 + 1023) / 1024) + 64));
-    for (int d = 1; d <= kMaxDeg; ++d)
-      if (nr->ad_count[d]) CK(dalloc(st, &ggofs[d], (size_t)nr->ad_count[d] + 1));
-  }
-  // Stages 1-4 and 6 depend on one another and run on the highest-priority stream; the
-  // self weights (5) depend on none of them and run on the lowest-priority one from the
-  // start, so their blocks fill what the chain leaves idle (the small far-order and
-  // smooth-rule launches, the end of the adaptive walk) without delaying it.
-  CK(cudaEventRecord(ctx->fork, st));
-  CK(cudaStreamWaitEvent(ctx->hi, ctx->fork, 0));
-  CK(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
-  LaunchCommon lh{ctx->hi, ctx->num_sms, &ctx->launches_corr};
-  cudaStream_t sh = ctx->hi;
-  CK(cudaEventRecord(ctx->ev[2], sh));
-  // 1. far order q_j and annulus order (Sec. 4.2, Eq. qj)
-  for (int d = 1; d <= kMaxDeg; ++d) {
-    if (!nr->plist_count[d]) continue;
-    launch_farorder(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, kp, eps0, params->m_max,
-                    ctx->deg[d].normV, ddirs, ndirs, fscr, fgrid, c->q, c->q_near,
-                    ctx->d_sched);
-  }
-  CK(cudaGetLastError());
-  // 5. self weights (Sec. 4, Eq. errestself), on the low-priority stream
-  const int sorder = params->self_order > 0 ? params->self_order : default_self_order(eps0);
-  CK(cudaEventRecord(ctx->ev_self[0], ctx->side));
-  if (nr->n_self > 0) {
-    LaunchCommon ls{ctx->side, ctx->num_sms, &ctx->launches_corr};
-    for (int d = 1; d <= kMaxDeg; ++d) {
-      if (!nr->plist_count[d]) continue;
-      launch_self(d, ls, dv, nr->deg, kp, sorder, InS);
-    }
-  }
-  CK(cudaGetLastError());
-  CK(cudaEventRecord(ctx->ev_self[1], ctx->side));
-  CK(cudaEventRecord(ctx->join, ctx->side));
-  CK(cudaEventRecord(ctx->ev[3], sh));
-  // 2. smooth-rule moments of every near and self pair; 3. annulus moments
-  for (int d = 1; d <= kMaxDeg; ++d) {
-    if (!nr->plist_count[d]) continue;
-    launch_rule_moments(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, 3, c->q, c->q_near, kp,
-                        Is, In, mixed_form);
-  }
-  CK(cudaGetLastError());
-  CK(cudaEventRecord(ctx->ev[4], sh));
-  // 4. adaptive near moments (Sec. 4.3)
-  if (nr->n_adaptive > 0) {
-    for (int d = 1; d <= kMaxDeg; ++d) {
-      if (!nr->ad_count[d]) continue;
-      const int cnt = nr->ad_count[d];
-      lcq_tune* tu = tune_st[d];
-      if (tune_meas[d] >= 0) CK(cudaEventRecord(tu->e0, sh));
-      launch_group_offsets(lh, nr->ad_list_dev[d], cnt, nr->ad_ptr, gsz[d], gng, ggofs[d], gscr);
-      launch_adaptive(d, lh, nr->ad_list_dev[d], cnt, dv, kp, eps0 * params->eps_loosen,
-                      ctx->deg[d].normV, params->leaf_order, params->max_depth, Is, In,
-                      c->leaves, ctx->work, astride, (int)A_eff, levels, agrid, ctx->d_status,
-                      ctx->d_sched + d, mixed_form ? 2.0 : 0.0, ggofs[d], gsz[d]);
-      if (tune_meas[d] >= 0) {
-        CK(cudaEventRecord(tu->e1, sh));
-        tu->pending = tune_meas[d];
-        tu->pend_pairs = (double)nr->ad_total[d];
-      }
-    }
-    CK(cudaGetLastError());
-  }
-  CK(cudaEventRecord(ctx->ev[5], sh));
-  CK(cudaStreamWaitEvent(sh, ctx->join, 0));  // self weights done
-  CK(cudaEventRecord(ctx->ev[6], sh));
-  // 6. c = V^T (I_near - I_smooth) into the CSR
-  for (int d = 1; d <= kMaxDeg; ++d) {
-    if (!nr->plist_count[d]) continue;
-    launch_v2c(d, lh, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, In, Is, InS,
-               c->val);
-  }
-  CK(cudaGetLastError());
-  CK(cudaEventRecord(ctx->ev[7], sh));
-  CK(cudaEventRecord(ctx->done, sh));
-  CK(cudaStreamWaitEvent(st, ctx->done, 0));
-  dfree(st, ddirs);
-  dfree(st, fscr);
-  if (gng) dfree(st, gng);
-  if (gscr) dfree(st, gscr);
-  for (int d = 1; d <= kMaxDeg; ++d)
-    if (ggofs[d]) dfree(st, ggofs[d]);
-  cudaFreeAsync(Is, st);
-  cudaFreeAsync(In, st);
-  cudaFreeAsync(InS, st);
+  // the mixed form (FP32 or two-float pair evaluation in the smooth, annulus and adaptive
+  // moments); per surface of a batch the kernels choose by the surface's tolerance
+  const int form = pair_form_mode(precision, kernel, nr, eps0);
+  c->form = form;
+  ctx->last_forms = forms_used(form, c->kp, c->grp_h);
+  GenScratch gs;
+  gs.dv = dv;
+  gs.ddirs = ddirs;
+  gs.ndirs = ndirs;
+  gs.Is = Is;
+  gs.In = In;
+  gs.InS = InS;
+  gs.form = form;
+  gs.sorder = params->self_order > 0 ? params->self_order : default_self_order(eps0);
+  lcq_status ls = gen_scratch(ctx, nr, kernel, eps0, params, true, &gs);
+  if (ls == LCQ_OK) ls = gen_launch(ctx, nr, c, params, gs, true);
+  if (ls != LCQ_OK) return ls;
+  for (int d = 0; d <= kMaxDeg; ++d) c->gsz[d] = gs.gsz[d];
+  gen_free(st, &gs);
   // stash the stream/device for later calls on the correction object
   c->q_h.clear();
   c->src_off = nullptr;
+  c->dirs_h = dirs;
   *out = c;
   return LCQ_OK;
 }
@@ -1364,7 +1485,7 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
       for (int d = 1; d <= kMaxDeg; ++d) {
         if (!nr->plist_count[d]) continue;
         launch_rule_moments(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, 1, c->q, nullptr,
-                            c->kp, Is, nullptr, c->mixed_form);
+                            c->kp, Is, nullptr, c->form);
       }
     const GradArgs ga{g, shat, M};
     for (int d = 1; d <= kMaxDeg; ++d) {
@@ -1373,7 +1494,7 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
                            c->eps0 * pr.eps_loosen, ctx->deg[d].normV, pr.leaf_order, pr.max_depth,
                            Is, In, leaves, ctx->work, stride, (int)nr->max_adaptive, levels, agrid,
                            ctx->d_status, ctx->d_sched + d,
-                           c->mixed_form ? 2.0 : 0.0, ga);
+                           c->form, ga);
     }
     dfree(st, Is);
     dfree(st, In);
@@ -1391,6 +1512,130 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
   dfree(st, tg);
   dfree(st, src);
   return LCQ_OK;
+}
+
+// ---------------------------------------------------------------------------- plans
+// The apply path's cached oversampling offsets follow q_j, which a plan launch recomputes.
+static void corr_forget_q(lcq_corr* c) {
+  c->q_h.clear();
+  if (c->src_off) dfree(c->stream, c->src_off);
+  if (c->gsrc) dfree(c->stream, c->gsrc);
+  c->src_off = nullptr;
+  c->gsrc = nullptr;
+  c->gsrc_h.clear();
+  c->n_over = 0;
+}
+
+lcq_status lcq_plan_create(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* nr,
+                           lcq_corr* c, lcq_plan** out) {
+  if (!ctx || !surf || !nr || !c || !out) return fail(ctx, LCQ_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (c->near != nr || surf->n_patches != nr->n_patches || !surf->xyz)
+    return fail(ctx, LCQ_ERR_ARG, "the corrections must come from these near lists and surface");
+  if (c->device != ctx->device) return fail(ctx, LCQ_ERR_ARG, "corrections of another device");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  lcq_plan* p = new lcq_plan();
+  p->ctx = ctx;
+  p->near = nr;
+  p->corr = c;
+  p->params = c->params;
+  GenScratch& gs = p->gs;
+  const int ldI = nr->n_max;
+  const int64_t npr = std::max<int64_t>(nr->n_pairs, 1), nsf = std::max<int64_t>(nr->n_self, 1);
+  gs.dv = make_dev(ctx, nr, c->q, ldI, c->grp);
+  gs.ndirs = (int)c->dirs_h.size() / 3;
+  gs.form = c->form;
+  gs.sorder = c->params.self_order > 0 ? c->params.self_order : default_self_order(c->eps0);
+  gs.own_work = true;
+  lcq_status ls = LCQ_OK;
+  auto ck = [&](cudaError_t e, const char* what) {
+    if (ls == LCQ_OK && e != cudaSuccess) ls = cuda_fail(ctx, e, what);
+  };
+  ck(dalloc(st, &gs.ddirs, std::max<size_t>(c->dirs_h.size(), 1)), "plan directions");
+  if (ls == LCQ_OK && !c->dirs_h.empty())
+    ck(cudaMemcpyAsync(gs.ddirs, c->dirs_h.data(), c->dirs_h.size() * 8, cudaMemcpyHostToDevice,
+                       st), "plan directions");
+  ck(dalloc(st, reinterpret_cast<double**>(&gs.Is), (size_t)2 * npr * ldI), "plan moments");
+  ck(dalloc(st, reinterpret_cast<double**>(&gs.In), (size_t)2 * npr * ldI), "plan moments");
+  ck(dalloc(st, reinterpret_cast<double**>(&gs.InS), (size_t)2 * nsf * ldI), "plan moments");
+  if (ls == LCQ_OK)
+    ls = gen_scratch(ctx, nr, (lcq_kernel)c->kernel, c->eps0, &p->params, false, &gs, c->gsz);
+  ck(cudaStreamSynchronize(st), "plan set-up");
+  // The context's stream may be the legacy default stream, which cannot be captured: the
+  // sequence is captured on a private stream standing in for it (the graph is launched on
+  // the context's stream).
+  cudaStream_t cs = nullptr;
+  const cudaStream_t saved = ctx->stream;
+  ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+  if (ls == LCQ_OK) {
+    // capture: the on-surface targets and the geometry of the current node coordinates
+    // (and, for S', the target normals), then stages 1-6 into c
+    ctx->launches_corr = 0;
+    ctx->stream = cs;
+    st = cs;
+    ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "begin capture");
+    if (ls == LCQ_OK) {
+      long long launches = 0;
+      LaunchCommon lc{st, ctx->num_sms, &launches};
+      launch_tgt_from_nodes(lc, nr->tgt, nr->tnode, nr->n_targets, surf->xyz, nr->n_points);
+      for (int d = 1; d <= kMaxDeg; ++d) {
+        if (!nr->plist_count[d]) continue;
+        launch_geom(d, lc, nr->plist_dev[d], nr->plist_count[d], nr->node_off, surf->xyz,
+                    nr->n_points, ctx->deg[d].dV, ctx->deg[d].dnodes, nr->params.eta,
+                    nr->params.eta1, nr->coef, nr->cen, nr->rad, nr->dj, nr->eta, nr->eta1,
+                    ctx->d_status);
+      }
+      if (c->kernel == LCQ_SP && nr->tnrm) {
+        bool first = true;
+        for (int d = 1; d <= kMaxDeg; ++d) {
+          if (!nr->plist_count[d]) continue;
+          launch_tgt_normals(d, lc, gs.dv, nr->deg, nr->unrm, first && nr->unrm, nr->tnrm);
+          first = false;
+        }
+      }
+      const lcq_status lg = gen_launch(ctx, nr, c, &p->params, gs, false);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(st, &g);
+      if (lg != LCQ_OK) ls = lg;
+      ck(ee, "end capture");
+      if (ls == LCQ_OK) ck(cudaGraphInstantiate(&p->exec, g, 0), "graph instantiate");
+      if (g) cudaGraphDestroy(g);
+      p->launches = launches + ctx->launches_corr;
+    }
+    ctx->stream = saved;
+    st = saved;
+  }
+  if (cs) cudaStreamDestroy(cs);
+  if (ls != LCQ_OK) {
+    cudaGetLastError();
+    gen_free(st, &gs);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    delete p;
+    return ls;
+  }
+  *out = p;
+  return LCQ_OK;
+}
+
+lcq_status lcq_plan_launch(lcq_plan* p) {
+  if (!p) return LCQ_ERR_ARG;
+  lcq_ctx* ctx = p->ctx;
+  CK(cudaSetDevice(ctx->device));
+  corr_forget_q(p->corr);
+  CK(cudaGraphLaunch(p->exec, ctx->stream));
+  ctx->launches_near = 0;
+  ctx->launches_corr = p->launches;
+  return LCQ_OK;
+}
+
+void lcq_plan_destroy(lcq_plan* p) {
+  if (!p) return;
+  cudaSetDevice(p->ctx->device);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  gen_free(p->ctx->stream, &p->gs);
+  cudaGetLastError();
+  delete p;
 }
 
 void lcq_corr_destroy(lcq_corr* c) {

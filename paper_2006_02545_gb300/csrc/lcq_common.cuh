@@ -16,8 +16,19 @@ namespace lcq {
 constexpr int kThreads = 256;
 constexpr double kRoundingFloor = 2e-13;  // multiple of the FP64 rounding envelope never asked below
 constexpr double kF32Floor = 2e-6;        // the same for kernel values evaluated in FP32
+constexpr double kTwoFloatFloor = 5e-11;  // and in two-float arithmetic (2^8 times the FP64 one)
 
 // ============================================================================ helpers
+// Form of the pair evaluations for patch j (block_moments_tc): mode 0, 1 or 2 as given; 3
+// chooses per surface of a batch from its tolerance (FP32 for eps >= kMixedMinEps,
+// two-float for eps >= kTwoFloatMinEps, FP64 below).
+__device__ __forceinline__ int pair_form(const Dev& dv, int j, int mode) {
+  if (mode != 3) return mode;
+  if (!dv.pgroup) return 0;
+  const double e = dv.grp[dv.pgroup[j]].eps;
+  return e >= kMixedMinEps ? 1 : (e >= kTwoFloatMinEps ? 2 : 0);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -435,12 +446,15 @@ __device__ __forceinline__ void tc_tile(const uint16_t* Bsl, const uint16_t* Asl
 // by ldmatrix, and assembles and stores its 8 x 8 complex block.
 // For real k and kinds S, D and CFIE with a real alpha the kernel constants are folded into
 // the node data (kernel_eval_fold).  smb: TcCfg<D>::BYTES of shared memory (16-byte aligned).
+// form: 0 FP64 kernel values; 1 FP32 ones (the mixed form for eps >= kMixedMinEps); 2
+// two-float ones (kernel_eval_ff; the mixed form below that) where the constants fold, else
+// FP64.
 template <int D, class TA, class OR>
 __device__ void block_moments_tc(const double* cf, const double* cfd, const double* __restrict__ ru,
                                  const double* __restrict__ rv, const double* __restrict__ rw,
                                  int Q, const SegMap* segs, int nseg, const TA& ta, int T, OR orow,
                                  const KernelParams& kp, unsigned char* smb, const double* cen,
-                                 double R, double* eout, bool mixed) {
+                                 double R, double* eout, int form) {
   using C = TcCfg<D>;
   constexpr int n = C::n;
   double* Xs = reinterpret_cast<double*>(smb + C::OFF_X);
@@ -462,10 +476,17 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
   int* pcs = reinterpret_cast<int*>(smb + C::OFF_PC);      // [piece][sg, l0, nq, po, row0, rb, first]
   const KernelParamsF kf = to_f32(kp);
   const float fR = f32_bits(R);
-  const float escale = mixed ? (float)(kF32Floor / kRoundingFloor) : 1.0f;
+  const bool mixed = form == 1;
   const bool has_ki = kp.ki != 0.0;
   // real k, kinds S, D and CFIE with a real alpha: constants folded into the node data
   const bool fold = !mixed && !has_ki && kp.kind <= 2 && kp.ai == 0.0;
+  const bool ffe = fold && form == 2;  // two-float kernel values
+  const float escale = mixed ? (float)(kF32Floor / kRoundingFloor)
+                             : ffe ? (float)(kTwoFloatFloor / kRoundingFloor) : 1.0f;
+  const ff krf = ff_of(kp.kr);
+  ff* Nff = reinterpret_cast<ff*>(Ns);  // two-float node data in the FP64 slots
+  ff* Jff = reinterpret_cast<ff*>(Js);
+  ff* Kff = reinterpret_cast<ff*>(Ks);
   constexpr double kInv4Pi = 0.07957747154594767;
   const double fa_n = (kp.kind == 1 ? 1.0 : kp.ar) * kInv4Pi;
   const double fj_r = (kp.kind == 0 ? 1.0 : kp.br) * kInv4Pi, fj_i = kp.bi * kInv4Pi;
@@ -561,10 +582,16 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           Xs[c * C::CH + p] = X[c];
-          Ns[c * C::CH + p] = Nn[c] * wn;
+          if (ffe) Nff[c * C::CH + p] = ff_of(Nn[c] * wn);
+          else Ns[c * C::CH + p] = Nn[c] * wn;
         }
-        Js[p] = fold ? Jw * fj_r : Jw;
-        Ks[p] = fold ? Jw * fj_i : 0.0;
+        if (ffe) {
+          Jff[p] = ff_of(Jw * fj_r);
+          Kff[p] = ff_of(Jw * fj_i);
+        } else {
+          Js[p] = fold ? Jw * fj_r : Jw;
+          Ks[p] = fold ? Jw * fj_i : 0.0;
+        }
         Jf[p] = f32_bits(fold ? Jw * kInv4Pi : Jw);
         if (mixed) {
 #pragma unroll
@@ -609,7 +636,12 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
         } else {
           cplx g = {0.0, 0.0};
           if (real) {
-            if (fold)
+            if (ffe) {
+              const ff Np[3] = {Nff[p], Nff[C::CH + p], Nff[2 * C::CH + p]};
+              g = kernel_eval_ff(kp.kind, kp.kr, krf, kf, g_sct, g_sctf, tx[3 * i], tx[3 * i + 1],
+                                 tx[3 * i + 2], Xs[p], Xs[C::CH + p], Xs[2 * C::CH + p], Np,
+                                 Jff[p], Kff[p], Jf[p], fR, &ev);
+            } else if (fold)
               g = kernel_eval_fold(kp.kind, kp.kr, kf, g_sct, tx[3 * i], tx[3 * i + 1],
                                    tx[3 * i + 2], Xs[p], Xs[C::CH + p], Xs[2 * C::CH + p], Ns[p],
                                    Ns[C::CH + p], Ns[2 * C::CH + p], Js[p], Ks[p], Jf[p], fR, &ev);
@@ -911,7 +943,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
                                                        int32_t* __restrict__ leaves_out,
                                                        unsigned char* __restrict__ work,
                                                        AdaptiveWS wsd, int* __restrict__ status,
-                                                       int* __restrict__ sched, double mix,
+                                                       int* __restrict__ sched, int form,
                                                        GradArgs ga,
                                                        const int64_t* __restrict__ gofs, int gsz) {
   using C = Cfg<D>;
@@ -985,8 +1017,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
     const double* rv = dv.rv + dv.roff[m];
     const double* rw = dv.rw + dv.roff[m];
     const double tol0 = (dv.pgroup ? dv.grp[dv.pgroup[j]].eps_ad : eps) * dv.dj[j] / normV;
-    // per surface of a batch, the mixed form applies only where eps >= kMixedMinEps
-    const bool mixj = mix > 0.0 && !(dv.pgroup && dv.grp[dv.pgroup[j]].eps < kMixedMinEps);
+    const int formj = pair_form(dv, j, form);
     const double Rj = dv.rad[j];
     const int32_t* apairs = dv.ad_pair + a0;
     __syncthreads();
@@ -1019,7 +1050,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
       TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, dv.tnrm};
       block_moments_tc<D>(cf, cfdp, ru, rv, rw, Q, segs, 1, ta, A,
                           [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, kps, smb,
-                          dv.cen + 3 * j, Rj, tmpE, mixj);
+                          dv.cen + 3 * j, Rj, tmpE, formj);
     }
     // DFS stack entries: level (8 bits) | child (2 bits) | path (2 bits per level) << 16
     int sp = 0;
@@ -1071,7 +1102,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
       TgtAdaptive ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, ST, dv.tnrm};
       block_moments_tc<D>(cf, cfdp, ru, rv, rw, Q, segs, 4, ta, S,
                           [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, kps, smb,
-                          dv.cen + 3 * j, Rj, tmpE, mixj);
+                          dv.cen + 3 * j, Rj, tmpE, formj);
       __syncthreads();
       my_tests += S;
       my_nodes += (long long)S * 4 * Q;

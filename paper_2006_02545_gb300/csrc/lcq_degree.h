@@ -23,7 +23,7 @@ template <int D>
 struct RuleMomL {
   static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv, int modes,
                   const int32_t* qv, const int32_t* qn, const KernelParams& kp, void* out_smooth,
-                  void* out_ann, bool mixed);
+                  void* out_ann, int form);
 };
 
 template <int D>
@@ -40,7 +40,7 @@ struct AdaptiveL {
                   const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                   const void* I_smooth, void* I_near, int32_t* leaves, void* work,
                   int64_t stride, int A_max, int levels, int grid, int* status, int* sched,
-                  double mix, const int64_t* gofs, int gsz);
+                  int form, const int64_t* gofs, int gsz);
 };
 
 template <int D>
@@ -87,7 +87,7 @@ struct AdaptiveGradL {
   static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                   const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                   const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
-                  int A_max, int levels, int grid, int* status, int* sched, double mix,
+                  int A_max, int levels, int grid, int* status, int* sched, int form,
                   const GradArgs& ga);
 };
 

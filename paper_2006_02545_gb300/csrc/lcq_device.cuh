@@ -49,12 +49,15 @@ static __constant__ int c_kwexp[kMaxBasis];
 // (cos, sin)(2 pi j / 1024), j = 0..1023: the table of sincos_tab (lcq_tc.cuh).
 constexpr int kSinCosTable = 1024;
 static __device__ double2 g_sct[kSinCosTable];
+// the same angles as two-float pairs (cos_h, cos_l, sin_h, sin_l) for the two-float kernel
+static __device__ float4 g_sctf[kSinCosTable];
 
-// Fills c_kw, c_jac, c_kwexp and g_sct of the calling translation unit (stream-ordered).
+// Fills c_kw, c_jac, c_kwexp, g_sct and g_sctf of the calling translation unit.
 static inline cudaError_t upload_kw_tables(cudaStream_t st) {
   double c[kMaxBasis], jc[(kMaxDeg + 1) * (kMaxDeg + 1) * 3] = {};
   int ke[kMaxBasis];
   std::vector<double2> sct(kSinCosTable);
+  std::vector<float4> sctf(kSinCosTable);
   for (int nn = 0; nn <= kMaxDeg; ++nn)
     for (int m = 0; m <= nn; ++m) {
       const int idx = nn * (nn + 1) / 2 + m;
@@ -74,6 +77,8 @@ static inline cudaError_t upload_kw_tables(cudaStream_t st) {
   for (int j = 0; j < kSinCosTable; ++j) {
     const double a = 2.0 * M_PI * j / kSinCosTable;
     sct[j] = make_double2(cos(a), sin(a));
+    const float ch = (float)sct[j].x, sh = (float)sct[j].y;
+    sctf[j] = make_float4(ch, (float)(sct[j].x - ch), sh, (float)(sct[j].y - sh));
   }
   cudaError_t e = cudaMemcpyToSymbolAsync(c_kw, c, sizeof(c), 0, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -82,6 +87,9 @@ static inline cudaError_t upload_kw_tables(cudaStream_t st) {
     e = cudaMemcpyToSymbolAsync(c_kwexp, ke, sizeof(ke), 0, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyToSymbolAsync(g_sct, sct.data(), sizeof(double2) * kSinCosTable, 0,
+                                cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyToSymbolAsync(g_sctf, sctf.data(), sizeof(float4) * kSinCosTable, 0,
                                 cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the sources live on this stack
   return e;

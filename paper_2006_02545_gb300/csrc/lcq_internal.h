@@ -29,10 +29,12 @@ enum : int {
   kStBadGroup = 16,
 };
 
-// The mixed form evaluates kernel values in FP32 only for tolerances eps >= kMixedMinEps:
-// with FP32 kernel values and contractions the result moves by about 1e-7 relative, so
-// below this tolerance the form is FP64.
+// The mixed form evaluates kernel values in FP32 for tolerances eps >= kMixedMinEps (with
+// FP32 kernel values and contractions the result moves by about 1e-7 relative), in
+// two-float arithmetic on the FP32 pipe for kMixedMinEps > eps >= kTwoFloatMinEps (about
+// 1e-13 relative) and in FP64 below.
 constexpr double kMixedMinEps = 1e-6;
+constexpr double kTwoFloatMinEps = 1e-11;
 
 // Kernel parameters (Sec. 3): K = alpha D + beta S for CFIE.
 struct KernelParams {
@@ -123,6 +125,7 @@ struct lcq_ctx {
   std::map<uint64_t, lcq_tune> tune;
   int last_group_size = 0;      // largest work-group size of the last generation
   long long last_items = 0;     // adaptive work items of the last generation (host count)
+  int last_forms = 0;           // pair evaluation forms of the last generation (bit 0 FP32, bit 1 two-float)
   cudaStream_t stream = nullptr;
   int* d_status = nullptr;
   long long* d_counters = nullptr;   // [8]
@@ -213,7 +216,7 @@ struct lcq_corr {
   lcq_params params{};           // generation parameters (test directions dropped)
   double eps0 = 0.0;             // tolerance (first surface's in a batch)
   int precision = 0;             // lcq_precision of the generation
-  bool mixed_form = false;       // FP32 pair evaluation used (precision and tolerance)
+  int form = 0;                  // pair evaluation form of the moment kernels (pair_form)
   double* val = nullptr;         // [nnz][2]
   int32_t* q = nullptr;          // [P]
   int32_t* q_near = nullptr;     // [P]
@@ -224,4 +227,6 @@ struct lcq_corr {
   std::vector<lcq::GroupParams> grp_h;
   int64_t* gsrc = nullptr;          // [n_groups+1] oversampled source range of each surface
   std::vector<int64_t> gsrc_h;
+  std::vector<double> dirs_h;       // far-order test directions of the generation
+  int gsz[lcq::kMaxDeg + 1] = {0};  // adaptive work-group size of each degree
 };

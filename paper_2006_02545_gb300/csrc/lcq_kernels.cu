@@ -67,7 +67,9 @@ __global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* 
 }
 
 // Direct far sum over all oversampled sources, one thread per target (tiles of sources
-// staged through shared memory).
+// staged through shared memory); kernel values by kernel_eval_tc (table sincos and the
+// Newton-refined reciprocal square root: FP64 throughout, about 40 FP64 instructions per
+// pair for the CFIE).
 // The sources of an on-surface target's own patch are skipped (their contribution is
 // carried entirely by the self correction).  In a batch of independent surfaces a target
 // sums only its own surface's sources [gsrc[g], gsrc[g+1]) with that surface's kernel.
@@ -119,6 +121,9 @@ __global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__
   }
   __syncthreads();
   const int64_t b0 = (int64_t)blo, b1 = (int64_t)bhi;
+  const KernelParamsF kf = to_f32(kt);
+  const bool has_ki = kt.ki != 0.0;
+  float env;  // not used: the far sum needs no rounding envelope
   double re = 0.0, im = 0.0;
   for (int64_t s0 = b0; s0 < b1; s0 += kThreads) {
     __syncthreads();
@@ -130,8 +135,9 @@ __global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__
       for (int k = 0; k < cnt; ++k) {
         const int64_t qq = s0 + k;
         if (qq < lo || qq >= hi || (qq >= skip0 && qq < skip1)) continue;
-        const cplx g = kernel_eval(kt, x0, x1, x2, s[0][k], s[1][k], s[2][k], s[3][k], s[4][k],
-                                   s[5][k], s[6][k], 0.0, nullptr, nx);
+        const cplx g = kernel_eval_tc(kt, kf, g_sct, x0, x1, x2, s[0][k], s[1][k], s[2][k],
+                                      s[3][k], s[4][k], s[5][k], s[6][k], 0.0f, 0.0f, &env, nx,
+                                      has_ki);
         re = fma(g.re, s[7][k], re);
         re = fma(-g.im, s[8][k], re);
         im = fma(g.re, s[8][k], im);
@@ -234,6 +240,26 @@ void launch_tgt_patch(const LaunchCommon& lc, const double* tgt, const int64_t* 
   k_tgt_patch<<<g, 256, 0, lc.stream>>>(tgt, tnode, NT, node_off, P, N, tpatch, tlnode, status);
 }
 
+// On-surface targets follow their nodes (a captured regeneration after the nodes moved):
+// tgt[:, t] = xyz[:, tnode[t]] where 0 <= tnode[t] < N; off-surface targets are kept.
+__global__ void k_tgt_from_nodes(double* __restrict__ tgt, const int64_t* __restrict__ tnode,
+                                 int64_t NT, const double* __restrict__ xyz, int64_t N) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < NT;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nd = tnode[t];
+    if (nd < 0 || nd >= N) continue;
+    for (int c = 0; c < 3; ++c) tgt[c * NT + t] = xyz[c * N + nd];
+  }
+}
+void launch_tgt_from_nodes(const LaunchCommon& lc, double* tgt, const int64_t* tnode, int64_t NT,
+                           const double* xyz, int64_t N) {
+  if (NT <= 0) return;
+  const int64_t blocks = (NT + 255) / 256;
+  const int g = (int)(blocks < lc.num_sms * 16 ? blocks : lc.num_sms * 16);
+  ++*lc.launches;
+  k_tgt_from_nodes<<<g, 256, 0, lc.stream>>>(tgt, tnode, NT, xyz, N);
+}
+
 // out[i] = sum_{k<i} in[i]; needs scratch of >= 2 * ceil(n/1024) + 2048 int64 elements.
 void launch_scan(const LaunchCommon& lc, const int64_t* in, int64_t* out, int64_t n,
                  int64_t* scratch) {
@@ -250,9 +276,9 @@ void launch_scan(const LaunchCommon& lc, const int64_t* in, int64_t* out, int64_
 
 bool launch_rule_moments(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                          int modes, const int32_t* qv, const int32_t* qn, const KernelParams& kp,
-                         void* out_smooth, void* out_ann, bool mixed) {
+                         void* out_smooth, void* out_ann, int form) {
   return dispatch<RuleMomL>(d, lc, plist, count, dv, modes, qv, qn, kp, out_smooth, out_ann,
-                            mixed);
+                            form);
 }
 bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, int m_max, double normV, const double* dirs,
@@ -263,11 +289,11 @@ bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count,
 bool launch_adaptive(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                      const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
-                     int A_max, int levels, int grid, int* status, int* sched, double mix,
+                     int A_max, int levels, int grid, int* status, int* sched, int form,
                      const int64_t* gofs, int gsz) {
   return dispatch<AdaptiveL>(d, lc, plist, count, dv, kp, eps, normV, leaf_order, max_depth,
                              I_smooth, I_near, leaves, work, stride, A_max, levels, grid, status,
-                             sched, mix, gofs, gsz);
+                             sched, form, gofs, gsz);
 }
 
 // Groups of at most gsz adaptive targets per listed patch: ng[b] = ceil(A_b / gsz) for

@@ -129,7 +129,7 @@ template <int D>
 __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
     const int* __restrict__ plist, int count, Dev dv, int modes, const int32_t* __restrict__ qv,
     const int32_t* __restrict__ qn, const KernelParams kp, cplx* __restrict__ out_smooth,
-    cplx* __restrict__ out_ann, bool mixed) {
+    cplx* __restrict__ out_ann, int form) {
   using C = Cfg<D>;
   extern __shared__ double smem[];
   double* cf = smem;
@@ -143,8 +143,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
   const int64_t ld = dv.ldI;
   for (int b = blockIdx.x; b < count; b += gridDim.x) {
     const int j = plist[b];
-    // mixed form: FP32 pair evaluation where the (surface's) tolerance allows it
-    const bool mixj = mixed && !(dv.pgroup && dv.grp[dv.pgroup[j]].eps < kMixedMinEps);
+    const int formj = pair_form(dv, j, form);  // FP64, FP32 or two-float pair evaluation
     __syncthreads();
     load_coef<D>(dv.coef, dv.node_off[j], cf);
     if (threadIdx.x == 0) {
@@ -167,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
         cplx* base = out_smooth + p0 * ld;
         block_moments_tc<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)np,
                             [=] __device__(int i) { return base + (int64_t)i * ld; }, kps, smb,
-                            dv.cen + 3 * j, 0.0, nullptr, mixj);
+                            dv.cen + 3 * j, 0.0, nullptr, formj);
         evals += np * m * m;
       } else {
         const int64_t a0 = dv.an_ptr[j], na = dv.an_ptr[j + 1] - a0;
@@ -175,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
         TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl, dv.tnrm};
         block_moments_tc<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)na,
                             [=] __device__(int i) { return out_ann + (int64_t)pl[i] * ld; }, kps,
-                            smb, dv.cen + 3 * j, 0.0, nullptr, mixj);
+                            smb, dv.cen + 3 * j, 0.0, nullptr, formj);
         evals += na * m * m;
       }
     }
@@ -188,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
 // q_j (Eq. qj) and the annulus order: smallest m with
 //   max_x ||I_m(x) - I_{m+1}(x)||_2 <= eps d_j / ||V||  over the test points.
 template <int D>
-__global__ void __launch_bounds__(kThreads) k_farorder(const int* __restrict__ plist, int count,
+__global__ void __launch_bounds__(kThreads, 2) k_farorder(const int* __restrict__ plist, int count,
                                                        Dev dv, const KernelParams kp, double eps,
                                                        int m_max, double normV,
                                                        const double* __restrict__ dirs, int ndirs,
@@ -636,12 +635,15 @@ __global__ void k_far_src(const int* __restrict__ plist, int count, Dev dv,
                           double* __restrict__ src /*[8][N_over]*/, int64_t n_over) {
   constexpr int n = (D + 1) * (D + 2) / 2;
   __shared__ double cf[3 * n];
+  __shared__ double cfd[2 * 3 * (D * (D + 1) / 2)];  // derivative series of the chart
   __shared__ cplx sc[n];
   for (int b = blockIdx.x; b < count; b += gridDim.x) {
     const int j = plist[b];
     const int64_t off = dv.node_off[j];
     __syncthreads();
     load_coef<D>(dv.coef, off, cf);
+    __syncthreads();
+    load_coef_derivs<D>(cf, dv.duv[D], cfd);
     for (int nm = threadIdx.x; nm < n; nm += blockDim.x) {
       double re = 0.0, im = 0.0;
       if (sigma)  // null: geometry only (the adjoint's sources)
@@ -657,17 +659,19 @@ __global__ void k_far_src(const int* __restrict__ plist, int count, Dev dv,
     const double* rv = dv.rv + dv.roff[m];
     const double* rw = dv.rw + dv.roff[m];
     for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+      // chart and tangents by the projected derivative series (rolled sums over the stored
+      // basis values keep the register count low), then the interpolated density
       double X[3], Xu[3], Xv[3], Nn[3], K[n];
-      kw_geometry<D>(ru[q], rv[q], cf, X, Xu, Xv, K, 1);
-      cross3(Xu, Xv, Nn);
-      const double w = rw[q];
-      const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
+      kw_geometry_proj<D>(ru[q], rv[q], cf, cfd, X, Xu, Xv, K);
       double re = 0.0, im = 0.0;
-#pragma unroll
+#pragma unroll 1
       for (int k = 0; k < n; ++k) {
         re = fma(K[k], sc[k].re, re);
         im = fma(K[k], sc[k].im, im);
       }
+      cross3(Xu, Xv, Nn);
+      const double w = rw[q];
+      const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
       const int64_t o = src_off[j] + q;
       src[0 * n_over + o] = X[0] + dv.cen[3 * j];
       src[1 * n_over + o] = X[1] + dv.cen[3 * j + 1];
@@ -709,13 +713,13 @@ size_t moments_smem_bytes(int extra_doubles) {
 template <int D>
 void RuleMomL<D>::run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv, int modes,
                   const int32_t* qv, const int32_t* qn, const KernelParams& kp, void* out_smooth,
-                  void* out_ann, bool mixed) {
+                  void* out_ann, int form) {
     const size_t sm = sizeof(double) * 3 * Cfg<D>::n + sizeof(SegMap) * 4 + 128 + TcCfg<D>::BYTES;
     set_smem(k_rule_moments<D>, sm);
     ++*lc.launches;
     // one block per patch: the hardware hands the next patch to whichever block slot frees
     k_rule_moments<D><<<count, kThreads, sm, lc.stream>>>(plist, count, dv, modes, qv, qn, kp,
-                                                          (cplx*)out_smooth, (cplx*)out_ann, mixed);
+                                                          (cplx*)out_smooth, (cplx*)out_ann, form);
   }
 
 template <int D>
@@ -745,7 +749,7 @@ void AdaptiveL<D>::run(const LaunchCommon& lc, const int* plist, int count, cons
                   const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                   const void* I_smooth, void* I_near, int32_t* leaves, void* work,
                   int64_t stride, int A_max, int levels, int grid, int* status, int* sched,
-                  double mix, const int64_t* gofs, int gsz) {
+                  int form, const int64_t* gofs, int gsz) {
     const size_t sm = adaptive_smem_bytes<D>();
     set_smem(k_adaptive<D>, sm);
     AdaptiveWS w{stride, A_max, levels};
@@ -754,7 +758,7 @@ void AdaptiveL<D>::run(const LaunchCommon& lc, const int* plist, int count, cons
     k_adaptive<D><<<grid, kThreads, sm, lc.stream>>>(plist, count, dv, kp, eps, normV, leaf_order,
                                                      max_depth, (const cplx*)I_smooth, (cplx*)I_near,
                                                      leaves, (unsigned char*)work, w, status, sched,
-                                                     mix, GradArgs{}, gofs, gsz);
+                                                     form, GradArgs{}, gofs, gsz);
   }
 
 template <int D>

@@ -88,6 +88,8 @@ bool launch_geom(int d, const LaunchCommon& lc, const int* plist, int count, con
                  const double* xyz, int64_t N, const double* Vt, const double* nodes, double eta_p,
                  double eta1_p, double* coef, double* cen, double* rad, double* dj, double* eta,
                  double* eta1, int* status);
+void launch_tgt_from_nodes(const LaunchCommon& lc, double* tgt, const int64_t* tnode, int64_t NT,
+                           const double* xyz, int64_t N);
 void launch_tgt_patch(const LaunchCommon& lc, const double* tgt, const int64_t* tnode, int64_t NT,
                       const int64_t* node_off, int64_t P, int64_t N, int32_t* tpatch,
                       int32_t* tlnode, int* status);
@@ -128,7 +130,7 @@ void launch_scan(const LaunchCommon& lc, const int64_t* in, int64_t* out, int64_
 // modes: bit 0 the smooth rule qv into out_smooth, bit 1 the annulus rule qn into out_ann
 bool launch_rule_moments(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                          int modes, const int32_t* qv, const int32_t* qn, const KernelParams& kp,
-                         void* out_smooth, void* out_ann, bool mixed = false);
+                         void* out_smooth, void* out_ann, int form = 0);
 // sched: a device counter the launch zeroes and the blocks draw patches from
 bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, int m_max, double normV, const double* dirs,
@@ -136,7 +138,7 @@ bool launch_farorder(int d, const LaunchCommon& lc, const int* plist, int count,
 bool launch_adaptive(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                      const KernelParams& kp, double eps, double normV, int leaf_order, int max_depth,
                      const void* I_smooth, void* I_near, int32_t* leaves, void* work, int64_t stride,
-                     int A_max, int levels, int grid, int* status, int* sched, double mix = 0.0,
+                     int A_max, int levels, int grid, int* status, int* sched, int form = 0,
                      const int64_t* gofs = nullptr, int gsz = 0);
 // gofs[count + 1]: exclusive scan of ceil(A_b / gsz) over the listed patches (work groups of
 // at most gsz adaptive targets for launch_adaptive); ng[count + 1] and scratch as launch_scan.
@@ -180,7 +182,7 @@ bool launch_adaptive_grad(int d, const LaunchCommon& lc, const int* plist, int c
                           const Dev& dv, const KernelParams& kp, double eps, double normV,
                           int leaf_order, int max_depth, const void* I_smooth, void* I_near,
                           int32_t* leaves, void* work, int64_t stride, int A_max, int levels,
-                          int grid, int* status, int* sched, double mix, const GradArgs& ga);
+                          int grid, int* status, int* sched, int form, const GradArgs& ga);
 bool launch_grad_v2c(int d, const LaunchCommon& lc, const int* plist, int count,
                      const int64_t* node_off, const double* Vt, const double* M, int64_t N,
                      double* out);

@@ -1,6 +1,7 @@
 // Device self-checks of the adaptive kernel's arithmetic building blocks (no counterpart in
-// the paper): the table-driven sincos against CUDA's sincos, and the split-precision
-// tensor-core contraction against a plain FP64 contraction of the same operands.
+// the paper): the table-driven sincos against CUDA's sincos, the split-precision
+// tensor-core contraction against a plain FP64 contraction of the same operands, and the
+// two-float kernel value and sincos against their FP64 counterparts.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -126,6 +127,72 @@ __global__ void __launch_bounds__(256) k_check_tc(int nq, unsigned long long see
   }
 }
 
+// Two-float kernel values (kernel_eval_ff) against the FP64 ones (kernel_eval_fold) at the
+// same inputs: sources |X| <= 0.3, targets at 10^-4 .. 1 of that in random directions (half
+// in the source's tangent plane), random weighted normals and folded constants, k in
+// {1.3, 2 pi, 20} and kinds S, D and CFIE; the difference relative to the sum of the
+// magnitudes of the terms (|e^{ikr}/r| (|N'| (1 + k r) / r + |Js| + |Ks|)), out[0]; and
+// the two-float sincos against sincos over |th| < 3000, relative to 1 + |th|, out[1].
+__global__ void k_check_ff(int64_t count, unsigned long long* out) {
+  auto rnd = [](unsigned long long k) {  // splitmix64 of k -> [0, 1)
+    unsigned long long z = 0x9e3779b97f4a7c15ull * (k + 1);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = 64ull * (unsigned long long)i;
+    double X[3], N[3], u[3];
+    for (int c = 0; c < 3; ++c) {
+      X[c] = 0.3 * (2.0 * rnd(b + c) - 1.0);
+      N[c] = 2.0 * rnd(b + 3 + c) - 1.0;
+      u[c] = 2.0 * rnd(b + 6 + c) - 1.0;
+    }
+    const double nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    if (i & 1) {  // tangent plane of the source
+      const double t = (u[0] * N[0] + u[1] * N[1] + u[2] * N[2]) / (nn * nn);
+      for (int c = 0; c < 3; ++c) u[c] -= t * N[c];
+    }
+    const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double dist = 0.3 * pow(10.0, -4.0 * rnd(b + 9));
+    double x[3];
+    for (int c = 0; c < 3; ++c) x[c] = X[c] + dist * u[c] / un;
+    const double ks[3] = {1.3, 6.283185307179586, 20.0};
+    const double kr = ks[(i >> 1) % 3];
+    const int kind = (int)((i >> 3) % 3);
+    const double w = 0.01 + rnd(b + 10);
+    const double Js = kind == 0 ? w * 0.0795 : (kind == 2 ? 0.7 * w * 0.0795 : 0.0);
+    const double Ks = kind == 2 ? -kr * w * 0.0795 : 0.0;
+    const double Np[3] = {N[0] * w * 0.0795, N[1] * w * 0.0795, N[2] * w * 0.0795};
+    const KernelParamsF kf = {(float)kr, 0.0f, 1.0f, 0.0f, 0.7f, 0.0f, 1.0f, 1.0f};
+    const ff Nf[3] = {ff_of(Np[0]), ff_of(Np[1]), ff_of(Np[2])};
+    float e1 = 0.0f, e2 = 0.0f;
+    const cplx g64 = kernel_eval_fold(kind, kr, kf, g_sct, x[0], x[1], x[2], X[0], X[1], X[2],
+                                      Np[0], Np[1], Np[2], Js, Ks, 1.0f, 0.3f, &e1);
+    const cplx gff = kernel_eval_ff(kind, kr, ff_of(kr), kf, g_sct, g_sctf, x[0], x[1], x[2], X[0],
+                                    X[1], X[2], Nf, ff_of(Js), ff_of(Ks), 1.0f, 0.3f, &e2);
+    const double r = sqrt((x[0] - X[0]) * (x[0] - X[0]) + (x[1] - X[1]) * (x[1] - X[1]) +
+                          (x[2] - X[2]) * (x[2] - X[2]));
+    const double nq = sqrt(Np[0] * Np[0] + Np[1] * Np[1] + Np[2] * Np[2]);
+    const double mag = (kind == 0 ? 0.0 : nq * (1.0 + kr * r) / r) + fabs(Js) + fabs(Ks);
+    const double scale = mag / r;
+    max_into(out, fmax(fabs(gff.re - g64.re), fabs(gff.im - g64.im)) / scale);
+    // sincos over |th| < 3000
+    const double th = 3000.0 * (2.0 * rnd(b + 11) - 1.0);
+    ff sn, cs;
+    if (ff_sincos(ff_of(th), g_sctf, &sn, &cs)) {
+      double s2, c2;
+      sincos(th, &s2, &c2);
+      const double e = fmax(fabs(dbl_of(sn) - s2), fabs(dbl_of(cs) - c2)) / (1.0 + fabs(th));
+      max_into(out + 1, e);
+    } else {
+      max_into(out + 1, 1.0);  // |th| < 2^14 must be in range
+    }
+  }
+}
+
 }  // namespace
 }  // namespace lcq
 
@@ -143,8 +210,8 @@ extern "C" lcq_status lcq_selftest(int device, double* out, int n_out) {
   unsigned long long* d = nullptr;
   cudaStream_t st = nullptr;
   if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMalloc(&d, 4 * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), st) != cudaSuccess ||
+      cudaMalloc(&d, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemsetAsync(d, 0, 8 * sizeof(unsigned long long), st) != cudaSuccess ||
       upload_kw_tables(st) != cudaSuccess)
     status = LCQ_ERR_CUDA;
   if (status == LCQ_OK) {
@@ -158,14 +225,17 @@ extern "C" lcq_status lcq_selftest(int device, double* out, int n_out) {
     const int sm10 = C10::BYTES;
     cudaFuncSetAttribute(k_check_tc<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm10);
     k_check_tc<10><<<1, 256, sm10, st>>>(49, 4242ull, d + 2);
-    unsigned long long h[4] = {0, 0, 0, 0};
+    k_check_ff<<<256, 256, 0, st>>>(int64_t(1) << 21, d + 3);
+    unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
       status = LCQ_ERR_CUDA;
     } else {
       // [0] max |sincos_tab - sincos| over sin and cos; [1] D = 6 and [2] D = 10: max
-      // |tensor-core - FP64| / sum |a| |b| over every output
-      for (int i = 0; i < 3 && i < n_out; ++i) memcpy(&out[i], &h[i], sizeof(double));
+      // |tensor-core - FP64| / sum |a| |b| over every output; [3] two-float kernel values
+      // against FP64 ones relative to the magnitude of their terms; [4] two-float sincos
+      // against sincos relative to 1 + |th|
+      for (int i = 0; i < 5 && i < n_out; ++i) memcpy(&out[i], &h[i], sizeof(double));
     }
   }
   if (d) cudaFree(d);

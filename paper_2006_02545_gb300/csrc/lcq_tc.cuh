@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include "lcq_device.cuh"
+#include "lcq_ff.cuh"
 
 namespace lcq {
 
@@ -283,6 +284,69 @@ __device__ __forceinline__ cplx kernel_eval_fold(int kind, double kr, const Kern
   const double mr = kind == 2 ? nd + Js : nd;
   const double mi = kind == 2 ? fma(-th, nd, Ks) : -th * nd;
   return {fma(ec, mr, -es * mi), fma(ec, mi, es * mr)};
+}
+
+// kernel_eval_fold in two-float arithmetic (lcq_ff.cuh) on the FP32 pipe: x - X in FP64 (the
+// difference stays FP64 near the singularity), then r^2, 1/r, k r, e^{ikr} and the S, D and
+// CFIE factors in two-float, the result converted to FP64 exactly; five FP64 instructions.
+// Np, Js, Ks: the folded node data (as kernel_eval_fold) as two-float pairs; krf: k.  Each
+// value carries a relative error of a few 2^-46 (plus k r 2^-48 in the phase).  Arguments
+// outside the two-float range (r^2 outside [1e-30, 1e30], |k r| >= 2^14) take
+// kernel_eval_fold.  r = 0 gives 0.
+__device__ __forceinline__ cplx kernel_eval_ff(int kind, double kr, ff krf, const KernelParamsF& kf,
+                                               const double2* __restrict__ sct,
+                                               const float4* __restrict__ sctf, double x0,
+                                               double x1, double x2, double X0, double X1,
+                                               double X2, const ff* Np, ff Js, ff Ks, float fJ,
+                                               float fR, float* env) {
+  const double dd0 = x0 - X0, dd1 = x1 - X1, dd2 = x2 - X2;
+  if (((__double_as_longlong(dd0) | __double_as_longlong(dd1) | __double_as_longlong(dd2)) << 1) ==
+      0) {
+    *env = 0.0f;
+    return {0.0, 0.0};
+  }
+  const ff d[3] = {ff_of(dd0), ff_of(dd1), ff_of(dd2)};
+  // r^2: exact squares of the leading parts plus 2 d_h d_l (d_l^2 is below 2^-48 of d_h^2)
+  ff sq[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    sq[c] = ff_two_prod(d[c].h, d[c].h);
+    sq[c].l = __fmaf_rn(2.0f * d[c].h, d[c].l, sq[c].l);
+  }
+  const ff s1 = ff_two_sum(sq[0].h, sq[1].h), s2 = ff_two_sum(s1.h, sq[2].h);
+  const ff r2 = ff_fast_two_sum(
+      s2.h, __fadd_rn(__fadd_rn(s1.l, s2.l), __fadd_rn(__fadd_rn(sq[0].l, sq[1].l), sq[2].l)));
+  bool ok = r2.h >= 1e-30f && r2.h <= 1e30f;
+  ff rinv = {0.0f, 0.0f}, r = rinv, th = rinv, sn = rinv, cs = rinv;
+  if (ok) {
+    rinv = ff_rsqrt(r2);
+    r = ff_mul(r2, rinv);
+    th = ff_mul(krf, r);
+    ok = ff_sincos(th, sctf, &sn, &cs);
+  }
+  if (!ok)
+    return kernel_eval_fold(kind, kr, kf, sct, x0, x1, x2, X0, X1, X2, dbl_of(Np[0]), dbl_of(Np[1]),
+                            dbl_of(Np[2]), dbl_of(Js), dbl_of(Ks), fJ, fR, env);
+  {
+    // |G| Jw (|beta| + |alpha| |1 - ik r| R / r^2) in FP32, k real
+    const float fri = rinv.h, f1 = kf.kr * r.h;
+    const float fa = sqrtf(fmaf(f1, f1, 1.0f));
+    *env = fri * fJ * fmaf(kf.ea * fa * fR, fri * fri, kf.eb);
+  }
+  const ff ec = ff_mul(cs, rinv), es = ff_mul(sn, rinv);
+  ff re, im;
+  if (kind == 0) {
+    re = ff_mul(ec, Js);
+    im = ff_mul(es, Js);
+  } else {
+    const ff nd = ff_mul(ff_dot3(Np, d), ff_mul(rinv, rinv));
+    const ff tn = ff_mul(th, nd);
+    const ff mr = kind == 2 ? ff_add(nd, Js) : nd;
+    const ff mi = kind == 2 ? ff_sub(Ks, tn) : ff_neg(tn);
+    re = ff_sub(ff_mul(ec, mr), ff_mul(es, mi));
+    im = ff_add(ff_mul(ec, mi), ff_mul(es, mr));
+  }
+  return {dbl_of(re), dbl_of(im)};
 }
 
 // kernel_eval (lcq_device.cuh) with the table sincos, the Newton-refined FP32 reciprocal

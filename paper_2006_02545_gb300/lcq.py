@@ -78,6 +78,9 @@ _sig = {
     "lcq_apply_corrected": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _vp, C.c_int, _d, _vp]),
     "lcq_near_set_target_normals": (C.c_int, [_vp, _vp]),
     "lcq_corr_destroy": (None, [_vp]),
+    "lcq_plan_create": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "lcq_plan_launch": (C.c_int, [_vp]),
+    "lcq_plan_destroy": (None, [_vp]),
     "lcq_apply_adjoint": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _d, _vp]),
     "lcq_shape_gradient": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "lcq_sync": (C.c_int, [_vp, _i64]),
@@ -300,6 +303,31 @@ class Corrections:
 PRECISIONS = {"fp64": 0, "mixed": 1}
 
 
+class Plan:
+    """A captured regeneration of `corr` (lcq_plan_create): launch() regenerates it in place
+    from the current node coordinates of `surf` with one CUDA graph launch."""
+
+    def __init__(self, ctx: Context, surf: DeviceSurface, near: NearLists, corr: Corrections):
+        h = C.c_void_p()
+        ctx.check(_lib.lcq_plan_create(ctx.h, C.byref(surf.s), near.h, corr.h, C.byref(h)),
+                  "lcq_plan_create")
+        self.ctx, self.h, self._keep = ctx, h, (surf, near, corr)
+
+    def launch(self):
+        self.ctx.check(_lib.lcq_plan_launch(self.h), "lcq_plan_launch")
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.lcq_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def gen_corrections(ctx: Context, surf: DeviceSurface, near: NearLists, kernel: str, k,
                     prm, alpha=1.0, beta=0.0, precision: str = "fp64") -> Corrections:
     k, alpha, beta = complex(k), complex(alpha), complex(beta)
@@ -415,10 +443,12 @@ def pipe_peaks(device: int = 0) -> dict:
 
 
 def selftest(device: int = 0) -> dict:
-    """Device self-checks (lcq_selftest): sincos table error, tensor-core contraction error."""
-    out = np.zeros(3)
-    st = _lib.lcq_selftest(device, _ptr(out), 3)
+    """Device self-checks (lcq_selftest): sincos table error, tensor-core contraction error,
+    two-float kernel value and sincos errors."""
+    out = np.zeros(5)
+    st = _lib.lcq_selftest(device, _ptr(out), 5)
     if st:
         raise LCQError(st, "lcq_selftest")
     return {"sincos_abs_err": float(out[0]), "tc_rel_err_d6": float(out[1]),
-            "tc_rel_err_d10": float(out[2])}
+            "tc_rel_err_d10": float(out[2]), "ff_kernel_rel_err": float(out[3]),
+            "ff_sincos_err": float(out[4])}

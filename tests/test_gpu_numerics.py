@@ -1,6 +1,7 @@
 """Device checks of the adaptive kernel's arithmetic building blocks, through the C ABI:
-the table-driven sincos against CUDA's sincos, and the exact split-precision tensor-core
-contraction against a plain FP64 contraction of the same operands (lcq_selftest)."""
+the table-driven sincos against CUDA's sincos, the exact split-precision tensor-core
+contraction against a plain FP64 contraction of the same operands, and the two-float kernel
+value and sincos of the mixed form against FP64 (lcq_selftest)."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -23,3 +24,11 @@ def test_sincos_table_and_tensor_contraction():
     # row, up to 128 nodes)
     assert 0.0 <= r["tc_rel_err_d6"] <= 8 * U, r
     assert 0.0 <= r["tc_rel_err_d10"] <= 8 * U, r
+    # two-float arithmetic carries 48 bits (2^-48 = 32 U per stored value); the kernel value
+    # chains about 20 products and sums, each within a few 2^-48 relative (products) or of
+    # the magnitudes summed (sums), so the difference from the FP64 value stays within
+    # 2^-40 of the magnitude of its terms, at every distance (x - X is FP64)
+    assert 0.0 <= r["ff_kernel_rel_err"] <= 2.0 ** -40, r
+    # sin and cos: the argument's own two-float rounding (2^-48 |th|) plus the table and
+    # angle-addition roundings
+    assert 0.0 <= r["ff_sincos_err"] <= 2.0 ** -44, r
