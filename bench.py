@@ -35,6 +35,15 @@ METRIC = ("near-field correction points/sec on 1 GB300 (FP64 vs mixed/batched) a
 UNIT = "points/s"
 WORKLOAD = "CFIE D-ikS k=2pi ellipsoid(1,2,3) 1280 order-6 patches (35,840 pts) eps=1e-9 FP64"
 
+
+def workload_name(patches, points, eps, precision="fp64"):
+    """WORKLOAD for the default configuration, else the same description at other sizes."""
+    if patches == 1280 and eps == 1e-9 and precision == "fp64":
+        return WORKLOAD
+    form = "FP64" if precision == "fp64" else "mixed"
+    return (f"CFIE D-ikS k=2pi ellipsoid(1,2,3) {patches} order-6 patches ({points:,} pts) "
+            f"eps={eps:g} {form}")
+
 # Algorithmic FLOPs of one (target, leaf node) evaluation in the adaptive kernel: the
 # kernel value (difference, r^2, phase, e^{ikr}/(4 pi r), S and D parts, CFIE combination:
 # 20 arithmetic operations, and sqrt, reciprocal and sincos counted as one each), plus the
@@ -66,6 +75,8 @@ def parse():
     ap.add_argument("--leaf-order", type=int, default=0,
                     help="smooth rule used on subtriangles (0: the patch's far order q_j)")
     ap.add_argument("--eps", type=float, default=1e-9)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="form of the timed steps (the variants compare both)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the mixed-precision and eps=1e-6 comparison runs")
     return ap.parse_args()
@@ -186,6 +197,10 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- our leg
+TUNING_GENERATIONS = 6
+# arithmetic of the pair evaluations by form (lcq_counters [7]); FP64 everywhere else
+MIXED_DTYPE = {"fp64": "f64", "fp32": "f32+f64", "two-float": "f32x2+f64",
+               "fp32+two-float": "f32+f32x2+f64"}
 FORM_NAMES = {0: "fp64", 1: "fp32", 2: "two-float", 3: "fp32+two-float"}  # lcq_counters [7]
 KERNEL_SOURCES = ("lcq_common.cuh", "lcq_device.cuh", "lcq_tc.cuh")  # k_adaptive and its helpers
 
@@ -242,10 +257,14 @@ def run_ours(args, rank, world, local_rank):
 
     def step():
         near = lcq.build_near_lists(ctx, ds, tx_d, tn_d, prm)
-        corr = lcq.gen_corrections(ctx, ds, near, wl.kernel, wl.k, prm, wl.alpha, wl.beta)
+        corr = lcq.gen_corrections(ctx, ds, near, wl.kernel, wl.k, prm, wl.alpha, wl.beta,
+                                   precision=args.precision)
         return near, corr
 
-    for _ in range(args.warmup):
+    # the context's group-size tuner times one candidate per generation on a new workload
+    # (at most five here): untimed generations before the warm-up settle it, so that the
+    # timed steps run its choice whatever W is
+    for _ in range(TUNING_GENERATIONS + args.warmup):
         near, corr = step()
         st = ctx.sync()
         corr.close()
@@ -255,7 +274,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     clocks = ClockSampler(local_rank) if rank == 0 else None
     step_ms, adapt_ms, stages, statuses, launches, nodes = [], [], [], [], 0, 0
-    tree_nodes = tests = group_size = items = 0
+    tree_nodes = tests = group_size = items = main_forms = 0
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
@@ -277,6 +296,7 @@ def run_ours(args, rank, world, local_rank):
         tree_nodes = int(cnt[4])
         tests = int(cnt[0])
         group_size, items = int(cnt[5]), int(cnt[6])
+        main_forms = int(cnt[7])
         corr.close()
         near.close()
     torch.cuda.synchronize()
@@ -488,7 +508,7 @@ def run_ours(args, rank, world, local_rank):
             for eps in (5e-3, 5e-4, 5e-7, 5e-10):
                 tp = lcq.params(eps, test_dirs=W.test_directions(7))
                 ms = []
-                for it in range(2):
+                for it in range(TUNING_GENERATIONS + 2):   # tuner candidates, warm-up, timed
                     flush.zero_()
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
@@ -615,8 +635,11 @@ def run_ours(args, rank, world, local_rank):
     achieved = flops / (a_ms / 1e3) / 1e12
     peak = peaks["fp64_fma_tflops"]
     roofline = {"bound": "alu",
-                "kernel": "k_adaptive<6>: FP64 kernel values; contraction on the f16 tensor "
-                          "cores by an exact 8-slice split",
+                "kernel": ("k_adaptive<6>: " + {"fp64": "FP64", "fp32": "FP32",
+                                                 "two-float": "two-float"}.get(
+                               FORM_NAMES[main_forms], "mixed") +
+                           " kernel values, FP64 geometry; contraction on the f16 tensor "
+                           "cores by an exact slice split"),
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic_for("k_adaptive"),
                 "peak_source": "measured in this run: FP64 FMA chains on every SM "
@@ -649,10 +672,15 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "patches": P, "order": 6, "points": N,
-                   "eps": args.eps, "leaf_order": args.leaf_order or "q_j",
-                   "l2": "256 MiB buffer written between steps (outside the timed events)"},
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else MIXED_DTYPE[FORM_NAMES[main_forms]],
+        "data": "synthetic",
+        "config": {"workload": workload_name(P, N, args.eps, args.precision), "patches": P,
+                   "order": 6, "precision": args.precision,
+                   "points": N, "eps": args.eps, "leaf_order": args.leaf_order or "q_j",
+                   "l2": "256 MiB buffer written between steps (outside the timed events)",
+                   "tuning": f"{TUNING_GENERATIONS} untimed generations before the warm-up "
+                             f"time the group-size tuner's candidates"},
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
         "pipe_peaks": peaks,
         "clocks": clk, "status": max(statuses) if statuses else None,

@@ -18,7 +18,9 @@
  *    owned by the library and released by the matching _destroy call.
  *  - Complex values are interleaved (re, im) doubles (complex128).
  *  - All device work is queued on the context's stream.  Calls that must size
- *    outputs (lcq_build_near_lists) synchronize that stream once.  Errors found
+ *    outputs synchronize that stream: lcq_build_near_lists four times (the grid box,
+ *    the pair count, the per-patch sizes, the adaptive work lists); a generation on
+ *    fixed near lists can be replayed without any (lcq_plan).  Errors found
  *    on the device (depth cap, capacity) are latched in a device status word and
  *    returned by lcq_sync() or the next call that synchronizes.
  *  - No call aborts, traps or throws across the ABI; every failure is a status.
@@ -331,9 +333,11 @@ lcq_status lcq_stage_times(lcq_ctx* ctx, float* ms6, int64_t* launches);
  * All device storage (tables, geometry, moments, the union-tree workspace) lives in one
  * static 8 MiB device array that every GPU loading liblcq holds until process exit; no
  * call allocates or frees device memory.  The first call on a device, with that device
- * current, looks up the array's device address and uploads constant tables; make that
- * first call before any stream capture.  Calls share the array and keep the previous
- * call's contents (each call rewrites what it reads): calls that overlap on the GPU --
+ * current, looks up the array's device address and uploads constant tables.  No call may
+ * be made while cuda_stream is being captured (each copies host values and synchronizes
+ * the stream): such a call returns LCQ_ERR_ARG and queues nothing.  Calls share the array
+ * and keep the previous call's contents (each call rewrites what it reads): calls that
+ * overlap on the GPU --
  * on different streams or from different threads -- race and must be serialized by the
  * caller.  Host-side set-up is safe when several host threads make their first calls at
  * once.  The call queues its work on cuda_stream (NULL: legacy default stream) and

@@ -141,6 +141,7 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
   static_assert(C::n < C::BS, "the basis rows need a spare column");
   (void)ostride;
   const KernelParamsF kf = to_f32(kp);
+  const bool has_ki = kp.ki != 0.0;
   const float fR = (float)R;
   const int total = nseg * Q;
   // The rules are conical products, rows of mr nodes sharing v, and every segment map
@@ -225,14 +226,20 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
                                  Nf[2 * C::CH + ql], Jf[ql], fR, ENV ? &ev : nullptr);
           Gf[i * C::CH + ql] = g;
           if (ENV) Evf[i * C::CH + ql] = ev;
-        } else {
+        } else if (ENV) {
           double ev = 0.0;
           const cplx g = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql],
                                      Xs[C::CH + ql], Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql],
-                                     Ns[2 * C::CH + ql], Js[ql], R, ENV ? &ev : nullptr,
-                                     tn + 3 * i);
+                                     Ns[2 * C::CH + ql], Js[ql], R, &ev, tn + 3 * i);
           G[i * C::CH + ql] = g;
-          if (ENV) Ev[i * C::CH + ql] = ev;
+          Ev[i * C::CH + ql] = ev;
+        } else {
+          // no envelope wanted: the table sincos and the Newton-refined 1/sqrt
+          float unused;
+          G[i * C::CH + ql] = kernel_eval_tc(kp, kf, g_sct, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2],
+                                             Xs[ql], Xs[C::CH + ql], Xs[2 * C::CH + ql], Ns[ql],
+                                             Ns[C::CH + ql], Ns[2 * C::CH + ql], Js[ql], 0.0f,
+                                             0.0f, &unused, tn + 3 * i, has_ki);
         }
       }
       __syncthreads();

@@ -218,6 +218,13 @@ extern "C" lcq_status lcq_adaptive_corrections_noalloc(
     return LCQ_ERR_CUDA;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  // the call copies host values and synchronizes its stream: not allowed in a capture
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return LCQ_ERR_ARG;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return LCQ_ERR_ARG;
   lcq_status s = setup_device(dev, st);
   if (s != LCQ_OK) return s;
   const DeviceState& ds = g_dev[dev];

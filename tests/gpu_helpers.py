@@ -76,11 +76,17 @@ def compare_pairs(g, oc, node_off, pairs=None):
         vals[(t, j)] = (vo, vg)
         c_max = max(c_max, np.linalg.norm(vo))
     worst, where = 0.0, None
+    used_slack = 0      # pairs within tolerance only thanks to the decision slack
     for (t, j), (vo, vg) in vals.items():
-        tol = pair_tolerance(oc, t, j, np.linalg.norm(vo), c_max)
-        r = np.linalg.norm(vo - vg) / tol
+        nv = np.linalg.norm(vo)
+        tol = pair_tolerance(oc, t, j, nv, c_max)
+        err = np.linalg.norm(vo - vg)
+        if err > 1e-10 * nv + 1e-12 * c_max:
+            used_slack += 1
+        r = err / tol
         if r > worst:
             worst, where = r, (t, j)
+    compare_pairs.used_slack = used_slack
     return worst, len(keys), where
 
 

@@ -38,9 +38,15 @@ def check_full(g, oc, uo, node_off):
     rel = np.linalg.norm(g["u"] - uo) / np.linalg.norm(uo)
     assert rel <= APPLY_TOL, rel
     worst, npairs, where = compare_pairs(g, oc, node_off)
-    assert worst <= 1.0, (worst, where)
+    slack = compare_pairs.used_slack
     lv = leaves_by_pair(g, oc)
     same = sum(a == b for a, b, _ in lv)
+    # reported, and bounded: a change that flips more refinement decisions fails here
+    print(f"parity: {npairs} pairs, worst {worst:.3f} of tolerance, {slack} outside 1e-10 "
+          f"(within the decision slack), leaf counts differ on {len(lv) - same} of {len(lv)} "
+          f"adaptive pairs, applied potential {rel:.2e}")
+    assert worst <= 1.0, (worst, where)
+    assert slack <= 0.02 * npairs, (slack, npairs)
     assert same >= 0.98 * len(lv), (same, len(lv))
     return rel
 
@@ -115,7 +121,7 @@ def test_ellipsoid_cfie_full_size_sampled(ctx):
     g = run_gpu(ctx, s, wl.tgt_xyz, wl.tgt_node, "CFIE", wl.k, wl.eps, wl.eta, wl.alpha, wl.beta,
                 dirs_seed=7)
     assert g["status"] == 0
-    sample = [0, 517, 1279]
+    sample = [0, 160, 317, 517, 700, 901, 1100, 1279]
     oc, _ = run_oracle(s, wl.tgt_xyz, wl.tgt_node, "CFIE", wl.k, wl.eps, wl.eta, wl.alpha,
                        wl.beta, dirs_seed=7, only_patches=sample, apply=False)
     for j in sample:
@@ -124,9 +130,146 @@ def test_ellipsoid_cfie_full_size_sampled(ctx):
         assert np.array_equal(seg, oc.near[j][0])
         assert np.array_equal(g["pair_ad"][g["pair_ptr"][j]:g["pair_ptr"][j + 1]], oc.near[j][1])
     worst, npairs, where = compare_pairs(g, oc, s.node_off)
-    assert npairs > 1000 and worst <= 1.0, (worst, where)
+    slack = compare_pairs.used_slack
     lv = leaves_by_pair(g, oc)
-    assert sum(a == b for a, b, _ in lv) >= 0.98 * len(lv)
+    same = sum(a == b for a, b, _ in lv)
+    print(f"sampled parity: {npairs} pairs of {len(sample)} patches, worst {worst:.3f} of "
+          f"tolerance, {slack} outside 1e-10, leaf counts differ on {len(lv) - same} of "
+          f"{len(lv)}")
+    assert npairs > 2500 and worst <= 1.0, (worst, where)
+    assert slack <= 0.02 * npairs, (slack, npairs)
+    assert same >= 0.98 * len(lv)
+
+
+def _sampled_rows(ctx, corr, near_exp, n_targets, sample):
+    """The CSR rows of the targets near the sampled patches, gathered on the device from a
+    full export into device tensors (the full CSR of the large workloads is gigabytes);
+    returns host (row_ptr, col, val) in which every other row is empty."""
+    import torch
+    dev = ctx.torch_device
+    pp, tg = near_exp[0], near_exp[1]
+    rows = np.unique(np.concatenate([tg[pp[j]:pp[j + 1]] for j in sample] +
+                                    [np.zeros(0, np.int32)])).astype(np.int64)
+    nnz = near_exp[5]
+    rp_d = torch.empty(n_targets + 1, dtype=torch.int64, device=dev)
+    col_d = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+    val_d = torch.empty(max(nnz, 1), dtype=torch.complex128, device=dev)
+    corr.export(n_targets, out=(rp_d, col_d, val_d))
+    rp = rp_d.cpu().numpy()
+    lens = np.zeros(n_targets, np.int64)
+    lens[rows] = rp[rows + 1] - rp[rows]
+    rp2 = np.concatenate([[0], np.cumsum(lens)])
+    idx = np.concatenate([np.arange(rp[r], rp[r + 1]) for r in rows] + [np.zeros(0, np.int64)])
+    it = torch.from_numpy(idx).to(dev)
+    col = col_d[it].cpu().numpy()
+    val = val_d[it].cpu().numpy()
+    del rp_d, col_d, val_d
+    return rp2, col, val
+
+
+def _sampled_check(ctx, s, x, tn, near, corr, kind, k, eps, alpha, beta, sample, label):
+    """The GPU corrections of the sampled patches' near pairs against the oracle run on
+    those patches alone: far orders, near lists, pair corrections and leaf counts."""
+    pe = near.export(s.n_patches)
+    q, qn, leaves = corr.stats(s.n_patches)
+    rp, col, val = _sampled_rows(ctx, corr, pe + (near.nnz,), x.shape[1], sample)
+    g = dict(row_ptr=rp, col=col, val=val, pair_ptr=pe[0], pair_tgt=pe[1], leaves=leaves)
+    oc, _ = run_oracle(s, x, tn, kind, k, eps, alpha=alpha, beta=beta, dirs_seed=7,
+                       only_patches=sample, apply=False)
+    for j in sample:
+        assert q[j] == oc.q[j] and qn[j] == oc.q_near[j], (label, j)
+        assert np.array_equal(pe[1][pe[0][j]:pe[0][j + 1]], oc.near[j][0]), (label, j)
+        assert np.array_equal(pe[2][pe[0][j]:pe[0][j + 1]], oc.near[j][1]), (label, j)
+    worst, npairs, where = compare_pairs(g, oc, s.node_off)
+    slack = compare_pairs.used_slack
+    lv = leaves_by_pair(g, oc)
+    same = sum(a == b for a, b, _ in lv)
+    print(f"{label}: {npairs} pairs of {len(sample)} patches, worst {worst:.3f} of tolerance, "
+          f"{slack} outside 1e-10, leaf counts differ on {len(lv) - same} of {len(lv)}")
+    assert npairs > 50 * len(sample) and worst <= 1.0, (label, worst, where)
+    assert slack <= 0.02 * npairs, (label, slack, npairs)
+    assert same >= 0.98 * len(lv), (label, same, len(lv))
+
+
+def test_large_torus_full_size_sampled(ctx):
+    """The 40,000-patch perturbed torus (degree 6, 1.12M points, CFIE, k = 20, eps = 1e-9)
+    at full size in the benchmark's launch configuration; the oracle recomputes 5 patches."""
+    import torch
+    from paper_2006_02545_gb300 import lcq
+    wl = W.torus_cfie_k20(100)
+    s = wl.surface
+    dev = ctx.torch_device
+    ds = lcq.DeviceSurface(s.deg, s.node_off, torch.from_numpy(s.xyz).to(dev))
+    prm = lcq.params(wl.eps, test_dirs=W.test_directions(7))
+    near = lcq.build_near_lists(ctx, ds, torch.from_numpy(wl.tgt_xyz).to(dev),
+                                torch.from_numpy(wl.tgt_node).to(dev), prm)
+    corr = lcq.gen_corrections(ctx, ds, near, wl.kernel, wl.k, prm, wl.alpha, wl.beta)
+    assert ctx.sync(300000) == 0
+    _sampled_check(ctx, s, wl.tgt_xyz, wl.tgt_node, near, corr, wl.kernel, wl.k, wl.eps,
+                   wl.alpha, wl.beta, [0, 9999, 20123, 31000, 39999], "torus40000")
+    corr.close()
+    near.close()
+
+
+def test_batched_tori_full_size_sampled(ctx):
+    """The 64-torus batch at full size (160,996 patches, 4.77M points, degrees 3-8,
+    k in [1, 20], eps 1e-6 or 1e-9) as one batched generation; the oracle recomputes two
+    patches of each of three surfaces (of different degree and tolerance) on that surface
+    alone."""
+    import torch
+    from paper_2006_02545_gb300 import lcq
+    bs, poff, phys, _ = W.batched_tori_batch(64, 0, 1.0)
+    x, tn = W.onsurface_targets(bs)
+    dev = ctx.torch_device
+    ds = lcq.DeviceSurface(bs.deg, bs.node_off, torch.from_numpy(bs.xyz).to(dev))
+    prm = lcq.params(1e-6, test_dirs=W.test_directions(7))
+    near = lcq.build_near_lists_batched(ctx, ds, poff, torch.from_numpy(x).to(dev),
+                                        torch.from_numpy(tn).to(dev), prm)
+    corr = lcq.gen_corrections_batched(ctx, ds, near, "CFIE", phys, prm)
+    assert ctx.sync(600000) == 0
+    pe = near.export(bs.n_patches)
+    q, qn, leaves = corr.stats(bs.n_patches)
+    picks = []
+    for i in range(len(phys)):
+        if len(picks) == 3:
+            break
+        if all(bs.deg[poff[i]] != bs.deg[poff[p]] for p in picks) and \
+                (not picks or phys[i][3] != phys[picks[-1]][3]):
+            picks.append(i)
+    samples = {i: [int(poff[i]) + 3, int(poff[i + 1]) - 5] for i in picks}
+    rp, col, val = _sampled_rows(ctx, corr, pe + (near.nnz,), x.shape[1],
+                                 [j for v in samples.values() for j in v])
+    for i in picks:
+        k, a, b, eps = phys[i]
+        p0, p1 = int(poff[i]), int(poff[i + 1])
+        n0, n1 = int(bs.node_off[p0]), int(bs.node_off[p1])
+        sub = W.Surface(f"torus{i}", bs.deg[p0:p1], bs.node_off[p0:p1 + 1] - n0,
+                        np.ascontiguousarray(bs.xyz[:, n0:n1]), {})
+        xs, ts = W.onsurface_targets(sub)
+        sample = [j - p0 for j in samples[i]]
+        oc, _ = run_oracle(sub, xs, ts, "CFIE", k, eps, alpha=a, beta=b, dirs_seed=7,
+                           only_patches=sample, apply=False)
+        # the batch's rows, targets and pair lists shifted to the surface's own numbering
+        pp = pe[0][p0:p1 + 1] - pe[0][p0]
+        g = dict(row_ptr=rp[n0:n1 + 1] - rp[n0], col=None, val=None, pair_ptr=pp,
+                 pair_tgt=pe[1][pe[0][p0]:pe[0][p1]] - n0, leaves=leaves[pe[0][p0]:pe[0][p1]])
+        g["col"] = col[rp[n0]:rp[n1]] - n0
+        g["val"] = val[rp[n0]:rp[n1]]
+        for j in sample:
+            assert q[p0 + j] == oc.q[j] and qn[p0 + j] == oc.q_near[j], (i, j)
+            assert np.array_equal(g["pair_tgt"][pp[j]:pp[j + 1]], oc.near[j][0]), (i, j)
+        worst, npairs, where = compare_pairs(g, oc, sub.node_off)
+        slack = compare_pairs.used_slack
+        lv = leaves_by_pair(g, oc)
+        same = sum(a_ == b_ for a_, b_, _ in lv)
+        print(f"batch surface {i} (degree {bs.deg[p0]}, eps {eps:g}, k {k:.2f}): {npairs} "
+              f"pairs, worst {worst:.3f}, {slack} outside 1e-10, leaf counts differ on "
+              f"{len(lv) - same} of {len(lv)}")
+        assert npairs > 50 and worst <= 1.0, (i, worst, where)
+        assert slack <= 0.02 * npairs, (i, slack, npairs)
+        assert same >= 0.98 * len(lv), (i, same, len(lv))
+    corr.close()
+    near.close()
 
 
 def test_torus_sampled_parity(ctx):
