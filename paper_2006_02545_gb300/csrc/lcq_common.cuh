@@ -163,7 +163,7 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
       // one thread per (row, m): the rows spread over all warps, hence all SM sub-partitions
       const int nrow = (c0 + nch - 1) / mr - row0 + 1;
       for (int e = threadIdx.x; e < nrow * (D + 1); e += blockDim.x) {
-        const int rr = e / (D + 1), m = e - rr * (D + 1);
+        const int m = e / nrow, rr = e - m * nrow;  // m-major: the lanes share m
         const int rg = row0 + rr, sg = rg / mr, l0 = (rg - sg * mr) * mr;
         const SegMap& S = segs[sg];
         kw_row_factors<D>(S.ay + ru[l0] * S.e1y + rv[l0] * S.e2y, m, cf, cfd,
@@ -516,7 +516,7 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
   int sg_next = 0, part_next = 0;
   while (sg_next < nseg) {
     // plan the chunk (uniform across the block); thread 0 records it for indexed lookups
-    int np = 0, ncp = 0, nrow = 0;
+    int np = 0, ncp = 0, nrow = 0, ncr = 0;
     __syncthreads();
     while (sg_next < nseg && np < C::MAXP) {
       const int l0 = part_next * psize, nq = min(psize, Q - l0), pad = (nq + 15) & ~15;
@@ -530,9 +530,11 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
         pc[4] = by_rows ? l0 / mr : 0;
         pc[5] = nrow;
         pc[6] = part_next == 0;
+        pc[7] = ncr;
       }
       nrow += by_rows ? (l0 + nq - 1) / mr - l0 / mr + 1 : 0;
       ncp += pad;
+      ncr += nq;
       ++np;
       if (++part_next == nparts) {
         part_next = 0;
@@ -549,8 +551,9 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
       colinfo[p] = (k << 16) | (ql < pcs[8 * k + 2] ? ql : 0xffff);
     }
     if (use_rows) {
+      // m-major, so that the lanes of a warp share m and with it the loop length
       for (int e = threadIdx.x; e < nrow * (D + 1); e += blockDim.x) {
-        const int rr = e / (D + 1), m = e - rr * (D + 1);
+        const int m = e / nrow, rr = e - m * nrow;
         int k = 0;
         for (int kk = 1; kk < np; ++kk)
           if (pcs[8 * kk + 5] <= rr) k = kk;
@@ -561,10 +564,27 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
       }
     }
     __syncthreads();
-    // (1) geometry and basis slices, thread per node
-    for (int p = threadIdx.x; p < ncp; p += blockDim.x) {
+    // column of the r-th real node of the chunk (the pieces' real columns are contiguous):
+    // the FP64 loops run over real nodes only, so that no lane of theirs idles on padding
+    auto real_col = [&](int r) {
+      int k = 0;
+      for (int kk = 1; kk < np; ++kk)
+        if (pcs[8 * kk + 7] <= r) k = kk;
+      return pcs[8 * k + 3] + (r - pcs[8 * k + 7]);
+    };
+    // padding columns: zero basis slices
+    for (int p = threadIdx.x; p < ncp; p += blockDim.x)
+      if ((colinfo[p] & 0xffff) == 0xffff) {
+#pragma unroll 1
+        for (int idx = 0; idx < n; ++idx)
+#pragma unroll
+          for (int i = 0; i < 8; ++i) Bsl[(size_t)i * C::NP * C::CH + C::swz(idx, p)] = 0;
+      }
+    // (1) geometry and basis slices, thread per real node
+    for (int rn = threadIdx.x; rn < ncr; rn += blockDim.x) {
+      const int p = real_col(rn);
       const int ci = colinfo[p], ql = ci & 0xffff;
-      if (ql != 0xffff) {
+      {
         const int* pc = pcs + 8 * (ci >> 16);
         const SegMap& S = segs[pc[0]];
         const int l = pc[1] + ql;
@@ -605,11 +625,6 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
           for (int c = 0; c < 3; ++c) Nf[c * C::CH + p] = (float)(Nn[c] * w);
           Jf[p] = (float)Jw;
         }
-      } else {
-#pragma unroll 1
-        for (int idx = 0; idx < n; ++idx)
-#pragma unroll
-          for (int i = 0; i < 8; ++i) Bsl[(size_t)i * C::NP * C::CH + C::swz(idx, p)] = 0;
       }
     }
     __syncthreads();
@@ -624,38 +639,42 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
         if (kp.kind == 3) ta.nrm(t0 + threadIdx.x, xp, tn + 3 * threadIdx.x);
       }
       __syncthreads();
-      // (2) kernel values and envelopes; zero padding columns
+      // (2) kernel values and envelopes of the real columns; zeros in the padding ones
       for (int e = threadIdx.x; e < nt * ncp; e += blockDim.x) {
         const int i = e / ncp, p = e - i * ncp;
-        const bool real = (colinfo[p] & 0xffff) != 0xffff;
+        if ((colinfo[p] & 0xffff) == 0xffff) {
+          if (mixed) Gf[i * C::CH + p] = make_float2(0.0f, 0.0f);
+          else Gs[i * C::CH + p] = cplx{0.0, 0.0};
+          Ef[i * C::CH + p] = 0.0f;
+        }
+      }
+      for (int e = threadIdx.x; e < nt * ncr; e += blockDim.x) {
+        const int i = e / ncr, p = real_col(e - i * ncr);
         float ev = 0.0f;
         if (mixed) {
           float2 g = make_float2(0.0f, 0.0f);
-          if (real) {
-            const double d0 = tx[3 * i] - Xs[p], d1 = tx[3 * i + 1] - Xs[C::CH + p],
-                         d2 = tx[3 * i + 2] - Xs[2 * C::CH + p];
-            const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-            if (r2 > 0.0)
-              g = kernel_eval_f32f(kp, kf, d0, d1, d2, r2, Nf[p], Nf[C::CH + p],
-                                   Nf[2 * C::CH + p], Jf[p], fR, &ev);
-          }
+          const double d0 = tx[3 * i] - Xs[p], d1 = tx[3 * i + 1] - Xs[C::CH + p],
+                       d2 = tx[3 * i + 2] - Xs[2 * C::CH + p];
+          const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+          if (r2 > 0.0)
+            g = kernel_eval_f32f(kp, kf, d0, d1, d2, r2, Nf[p], Nf[C::CH + p], Nf[2 * C::CH + p],
+                                 Jf[p], fR, &ev);
           Gf[i * C::CH + p] = g;
         } else {
-          cplx g = {0.0, 0.0};
-          if (real) {
-            if (ffe) {
-              const ff Np[3] = {Nff[p], Nff[C::CH + p], Nff[2 * C::CH + p]};
-              g = kernel_eval_ff(kp.kind, kp.kr, krf, kf, g_sct, g_sctf, tx[3 * i], tx[3 * i + 1],
-                                 tx[3 * i + 2], Xs[p], Xs[C::CH + p], Xs[2 * C::CH + p], Np,
-                                 Jff[p], Kff[p], Jf[p], fR, &ev);
-            } else if (fold)
-              g = kernel_eval_fold(kp.kind, kp.kr, kf, g_sct, tx[3 * i], tx[3 * i + 1],
-                                   tx[3 * i + 2], Xs[p], Xs[C::CH + p], Xs[2 * C::CH + p], Ns[p],
-                                   Ns[C::CH + p], Ns[2 * C::CH + p], Js[p], Ks[p], Jf[p], fR, &ev);
-            else
-              g = kernel_eval_tc(kp, kf, g_sct, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[p],
-                                 Xs[C::CH + p], Xs[2 * C::CH + p], Ns[p], Ns[C::CH + p],
-                                 Ns[2 * C::CH + p], Js[p], Jf[p], fR, &ev, tn + 3 * i, has_ki);
+          cplx g;
+          if (ffe) {
+            const ff Np[3] = {Nff[p], Nff[C::CH + p], Nff[2 * C::CH + p]};
+            g = kernel_eval_ff(kp.kind, kp.kr, krf, kf, g_sct, g_sctf, tx[3 * i], tx[3 * i + 1],
+                               tx[3 * i + 2], Xs[p], Xs[C::CH + p], Xs[2 * C::CH + p], Np,
+                               Jff[p], Kff[p], Jf[p], fR, &ev);
+          } else if (fold) {
+            g = kernel_eval_fold(kp.kind, kp.kr, kf, g_sct, tx[3 * i], tx[3 * i + 1],
+                                 tx[3 * i + 2], Xs[p], Xs[C::CH + p], Xs[2 * C::CH + p], Ns[p],
+                                 Ns[C::CH + p], Ns[2 * C::CH + p], Js[p], Ks[p], Jf[p], fR, &ev);
+          } else {
+            g = kernel_eval_tc(kp, kf, g_sct, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[p],
+                               Xs[C::CH + p], Xs[2 * C::CH + p], Ns[p], Ns[C::CH + p],
+                               Ns[2 * C::CH + p], Js[p], Jf[p], fR, &ev, tn + 3 * i, has_ki);
           }
           Gs[i * C::CH + p] = g;
         }

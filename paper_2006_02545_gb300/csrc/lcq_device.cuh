@@ -232,12 +232,14 @@ __device__ __forceinline__ void kw_geometry_proj(double u, double v, const doubl
 // Row form of kw_geometry_proj for nodes that share v.  K_nm = L_m(u, v) J_nm(v) with
 // L_m = (1 - v)^m P_m((2u + v - 1) / (1 - v)) and J_nm = c_nm P^{(0,2m+1)}_{n-m}(1 - 2v), so
 // per value of v the J factors and the chart's sums over n at fixed m can be formed once:
-// row = [v, (1 - v)^2, J (n), BX (3 (D+1)), BU (3 D), BV (3 D)], BX[m][c] = sum_n cf_nm[c]
-// J_nm and BU, BV likewise from the derivative series (n < D).
+// row = [v, (1 - v)^2, Q (D+1), J (n), BX (3 (D+1)), BU (3 D), BV (3 D)], Q[m] = (m-1)/m
+// (1 - v)^2 (the v-only coefficient of the L_m recurrence), BX[m][c] = sum_n cf_nm[c] J_nm
+// and BU, BV likewise from the derivative series (n < D).
 template <int D>
 struct KwRow {
   static constexpr int n = (D + 1) * (D + 2) / 2;
-  static constexpr int J = 2, BX = J + n, BU = BX + 3 * (D + 1), BV = BU + 3 * D;
+  static constexpr int Q = 2, J = Q + D + 1, BX = J + n, BU = BX + 3 * (D + 1),
+                       BV = BU + 3 * D;
   static constexpr int size = BV + 3 * D;
 };
 
@@ -250,8 +252,11 @@ __device__ __forceinline__ void kw_row_factors(double v, int m, const double* cf
   constexpr int nd = D * (D + 1) / 2;
   const double y = 1.0 - 2.0 * v;
   if (m == 0) {
+    const double q2 = (1.0 - v) * (1.0 - v);
     row[0] = v;
-    row[1] = (1.0 - v) * (1.0 - v);
+    row[1] = q2;
+#pragma unroll
+    for (int mm = 0; mm <= D; ++mm) row[RW::Q + mm] = mm < 2 ? 0.0 : (mm - 1.0) / mm * q2;
   }
   double Pp = 0.0, P = 1.0;
   double x0 = 0.0, x1 = 0.0, x2 = 0.0, u0 = 0.0, u1 = 0.0, u2 = 0.0, v0 = 0.0, v1 = 0.0,
@@ -296,7 +301,7 @@ template <int D, class F>
 __device__ __forceinline__ void kw_geometry_row_emit(double u, const double* row, double* X,
                                                      double* Xu, double* Xv, F&& emit) {
   using RW = KwRow<D>;
-  const double v = row[0], q2 = row[1];
+  const double v = row[0];
   const double s = 2.0 * u + v - 1.0;
   double Lp = 0.0, L = 1.0;
   double x0 = 0.0, x1 = 0.0, x2 = 0.0, u0 = 0.0, u1 = 0.0, u2 = 0.0, v0 = 0.0, v1 = 0.0,
@@ -304,7 +309,8 @@ __device__ __forceinline__ void kw_geometry_row_emit(double u, const double* row
 #pragma unroll
   for (int m = 0; m <= D; ++m) {
     if (m > 0) {
-      const double Ln = ((2.0 * m - 1.0) * s * L - (m - 1.0) * q2 * Lp) * (1.0 / m);
+      // m L_m = (2m - 1) s L_{m-1} - (m - 1) (1 - v)^2 L_{m-2}, the v-only factor per row
+      const double Ln = m == 1 ? s : fma((2.0 * m - 1.0) / m * s, L, -row[RW::Q + m] * Lp);
       Lp = L;
       L = Ln;
     }

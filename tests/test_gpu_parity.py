@@ -141,14 +141,16 @@ def test_ellipsoid_cfie_full_size_sampled(ctx):
     assert same >= 0.98 * len(lv)
 
 
-def _sampled_rows(ctx, corr, near_exp, n_targets, sample):
-    """The CSR rows of the targets near the sampled patches, gathered on the device from a
-    full export into device tensors (the full CSR of the large workloads is gigabytes);
-    returns host (row_ptr, col, val) in which every other row is empty."""
+def _sampled_rows(ctx, corr, near_exp, n_targets, sample, node_off):
+    """The CSR rows of the targets near the sampled patches and of their own nodes (the
+    self targets), gathered on the device from a full export into device tensors (the full
+    CSR of the large workloads is gigabytes); returns host (row_ptr, col, val) in which
+    every other row is empty."""
     import torch
     dev = ctx.torch_device
     pp, tg = near_exp[0], near_exp[1]
     rows = np.unique(np.concatenate([tg[pp[j]:pp[j + 1]] for j in sample] +
+                                    [np.arange(node_off[j], node_off[j + 1]) for j in sample] +
                                     [np.zeros(0, np.int32)])).astype(np.int64)
     nnz = near_exp[5]
     rp_d = torch.empty(n_targets + 1, dtype=torch.int64, device=dev)
@@ -172,7 +174,7 @@ def _sampled_check(ctx, s, x, tn, near, corr, kind, k, eps, alpha, beta, sample,
     those patches alone: far orders, near lists, pair corrections and leaf counts."""
     pe = near.export(s.n_patches)
     q, qn, leaves = corr.stats(s.n_patches)
-    rp, col, val = _sampled_rows(ctx, corr, pe + (near.nnz,), x.shape[1], sample)
+    rp, col, val = _sampled_rows(ctx, corr, pe + (near.nnz,), x.shape[1], sample, s.node_off)
     g = dict(row_ptr=rp, col=col, val=val, pair_ptr=pe[0], pair_tgt=pe[1], leaves=leaves)
     oc, _ = run_oracle(s, x, tn, kind, k, eps, alpha=alpha, beta=beta, dirs_seed=7,
                        only_patches=sample, apply=False)
@@ -238,7 +240,7 @@ def test_batched_tori_full_size_sampled(ctx):
             picks.append(i)
     samples = {i: [int(poff[i]) + 3, int(poff[i + 1]) - 5] for i in picks}
     rp, col, val = _sampled_rows(ctx, corr, pe + (near.nnz,), x.shape[1],
-                                 [j for v in samples.values() for j in v])
+                                 [j for v in samples.values() for j in v], bs.node_off)
     for i in picks:
         k, a, b, eps = phys[i]
         p0, p1 = int(poff[i]), int(poff[i + 1])
