@@ -473,6 +473,7 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
       total = off;
     }
     __syncthreads();
+    const KernelParamsF kfs = to_f32(kps);
     chart_taylor<D>(P[0], P[1], cf, krows, tX);  // krows is free until the first chunk
     // the target is the chart's value at the node: x - X(P + delta) = -(dX)
     // chunks of 128 nodes: each thread forms one node's kernel value and basis row in
@@ -497,8 +498,11 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
         const int ti = rem / ns, si = rem - ti * ns;
         const double lo = g.xi_max * p / g.npan, hi = g.xi_max * (p + 1) / g.npan;
         const double xi = lo + (hi - lo) * glx_t[ti];
-        const double tpar = g.t0 + g.side * g.mu * sinh(xi);
-        const double wt = glw_t[ti] * (hi - lo) * g.mu * cosh(xi);
+        // sinh and cosh from one exponential (xi >= 0: the difference loses at most a few
+        // 1e-16 absolute near xi = 0, which moves the node by mu times that)
+        const double ex = exp(xi), exi = 1.0 / ex;
+        const double tpar = g.t0 + g.side * g.mu * (0.5 * (ex - exi));
+        const double wt = glw_t[ti] * (hi - lo) * g.mu * (0.5 * (ex + exi));
         const double sv = glx_s[si];
         const double w = glw_s[si] * wt * sv * g.area2 * Mm[4];
         const double zx = sv * (g.E0x + tpar * g.Dx), zy = sv * (g.E0y + tpar * g.Dy);
@@ -509,8 +513,9 @@ __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict_
         chart_chord<D>(tX, du, dvv, dX);
         cross3(Xu, Xv, Nn);
         const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
-        gk = kernel_eval(kps, 0.0, 0.0, 0.0, dX[0], dX[1], dX[2], Nn[0] * w, Nn[1] * w,
-                         Nn[2] * w, J * w, 0.0, nullptr, nP);
+        float unused;
+        gk = kernel_eval_tc(kps, kfs, g_sct, 0.0, 0.0, 0.0, dX[0], dX[1], dX[2], Nn[0] * w,
+                            Nn[1] * w, Nn[2] * w, J * w, 0.0f, 0.0f, &unused, nP, kps.ki != 0.0);
       } else {
         for (int e = 0; e < n; ++e) Kq[e] = 0.0;
       }
