@@ -97,9 +97,6 @@ struct Cfg {
   static constexpr int TT = 16;
   // doubles of shared workspace used by block_moments
   static constexpr int WS = CH * BS + 7 * CH + 3 * TT * CH + 6 * TT;
-  // doubles the mixed form adds after WS: FP32 copies of the basis rows, weighted
-  // normals and area elements of a chunk
-  static constexpr int WS_F32 = (CH * BS + 4 * CH + 1) / 2;
 };
 
 struct SegMap {
@@ -107,42 +104,30 @@ struct SegMap {
 };
 
 // Moments I[i][seg][nm] = sum_{q in seg} w_q K(x_i, X_q) J_q K_nm(u_q, v_q) for a smooth
-// rule (Q nodes) pushed onto nseg affine images of T0, for T targets.  Geometry is
-// evaluated once per chunk of nodes and shared by all targets (Sec. 4.3 reuse).
+// rule (Q nodes) pushed onto nseg affine images of T0, for T targets, in FP64 throughout
+// (the far order q_j, whose decisions compare these moments).  Geometry is evaluated once
+// per chunk of nodes and shared by all targets (Sec. 4.3 reuse).
 // TA: target accessor (pos(i, x[3])); out row of target i: out + orow(i) * ostride.
 // Positions are relative to the patch centroid cen (the coefficients cf describe
 // X - cen); cfd holds the derivative series of load_coef_derivs, which replace the
-// derivative recurrences.  With ENV, eout[i * nseg + seg] also receives the summed rounding envelope.
-// mixed (the mixed form; sm then has Cfg<D>::WS_F32 more doubles): every (target, node)
-// pair is evaluated by kernel_eval_f32f from the FP64 difference x - X, its envelope
-// scaled by kF32Floor / kRoundingFloor, and contracted with FP32 basis values in FP32 per
-// chunk (accumulated into the FP64 moments).
-template <int D, bool ENV = false, class TA, class OR>
+// derivative recurrences.
+template <int D, class TA, class OR>
 __device__ void block_moments(const double* cf, const double* cfd, const double* __restrict__ ru,
                               const double* __restrict__ rv, const double* __restrict__ rw, int Q,
                               const SegMap* segs, int nseg, const TA& ta, int T, OR orow,
                               int64_t ostride, const KernelParams& kp, double* sm,
-                              const double* cen, double R = 0.0, double* eout = nullptr,
-                              bool mixed = false) {
+                              const double* cen) {
   using C = Cfg<D>;
   double* B = sm;
   double* Xs = B + C::CH * C::BS;
   double* Ns = Xs + 3 * C::CH;
   double* Js = Ns + 3 * C::CH;
   cplx* G = reinterpret_cast<cplx*>(Js + C::CH);
-  double* Ev = reinterpret_cast<double*>(G + C::TT * C::CH);
-  double* tx = Ev + C::TT * C::CH;
+  double* tx = reinterpret_cast<double*>(G + C::TT * C::CH) + C::TT * C::CH;
   double* tn = tx + 3 * C::TT;  // target normals (S')
-  float* Bf = reinterpret_cast<float*>(sm + C::WS);  // mixed form only
-  float* Nf = Bf + C::CH * C::BS;
-  float* Jf = Nf + 3 * C::CH;
-  float2* Gf = reinterpret_cast<float2*>(G);
-  float* Evf = reinterpret_cast<float*>(Ev);
-  static_assert(C::n < C::BS, "the basis rows need a spare column");
   (void)ostride;
   const KernelParamsF kf = to_f32(kp);
   const bool has_ki = kp.ki != 0.0;
-  const float fR = (float)R;
   const int total = nseg * Q;
   // The rules are conical products, rows of mr nodes sharing v, and every segment map
   // here keeps v a function of the rule's v alone (e1y = 0: T0 and all its midpoint
@@ -185,7 +170,6 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
         const double v = S.ay + r0 * S.e1y + r1 * S.e2y;
         kw_geometry_proj<D>(u, v, cf, cfd, X, Xu, Xv, B + ql * C::BS);
       }
-      B[ql * C::BS + C::n] = 1.0;  // the envelope's column
       cross3(Xu, Xv, Nn);
       const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
 #pragma unroll
@@ -194,12 +178,6 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
         Ns[c * C::CH + ql] = Nn[c] * w;
       }
       Js[ql] = J * w;
-      if (mixed) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) Nf[c * C::CH + ql] = (float)(Nn[c] * w);
-        Jf[ql] = (float)(J * w);
-        for (int nm = 0; nm <= C::n; ++nm) Bf[ql * C::BS + nm] = (float)B[ql * C::BS + nm];
-      }
     }
     __syncthreads();
     for (int t0 = 0; t0 < T; t0 += C::TT) {
@@ -213,83 +191,40 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
         if (kp.kind == 3) ta.nrm(t0 + threadIdx.x, xp, tn + 3 * threadIdx.x);
       }
       __syncthreads();
+      // kernel values by the table sincos and the Newton-refined 1/sqrt (no envelope)
       for (int e = threadIdx.x; e < nt * nch; e += blockDim.x) {
         const int i = e / nch, ql = e - i * nch;
-        if (mixed) {
-          float2 g = make_float2(0.0f, 0.0f);
-          float ev = 0.0f;
-          const double d0 = tx[3 * i] - Xs[ql], d1 = tx[3 * i + 1] - Xs[C::CH + ql],
-                       d2 = tx[3 * i + 2] - Xs[2 * C::CH + ql];
-          const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-          if (r2 > 0.0)
-            g = kernel_eval_f32f(kp, kf, d0, d1, d2, r2, Nf[ql], Nf[C::CH + ql],
-                                 Nf[2 * C::CH + ql], Jf[ql], fR, ENV ? &ev : nullptr);
-          Gf[i * C::CH + ql] = g;
-          if (ENV) Evf[i * C::CH + ql] = ev;
-        } else if (ENV) {
-          double ev = 0.0;
-          const cplx g = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql],
-                                     Xs[C::CH + ql], Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql],
-                                     Ns[2 * C::CH + ql], Js[ql], R, &ev, tn + 3 * i);
-          G[i * C::CH + ql] = g;
-          Ev[i * C::CH + ql] = ev;
-        } else {
-          // no envelope wanted: the table sincos and the Newton-refined 1/sqrt
-          float unused;
-          G[i * C::CH + ql] = kernel_eval_tc(kp, kf, g_sct, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2],
-                                             Xs[ql], Xs[C::CH + ql], Xs[2 * C::CH + ql], Ns[ql],
-                                             Ns[C::CH + ql], Ns[2 * C::CH + ql], Js[ql], 0.0f,
-                                             0.0f, &unused, tn + 3 * i, has_ki);
-        }
+        float unused;
+        G[i * C::CH + ql] = kernel_eval_tc(kp, kf, g_sct, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2],
+                                           Xs[ql], Xs[C::CH + ql], Xs[2 * C::CH + ql], Ns[ql],
+                                           Ns[C::CH + ql], Ns[2 * C::CH + ql], Js[ql], 0.0f, 0.0f,
+                                           &unused, tn + 3 * i, has_ki);
       }
       __syncthreads();
-      // one thread per (target, nm), outputs packed densely; with ENV the extra index nm = n
-      // sums the envelope through the basis rows' column of ones.  Node ranges are uniform
+      // one thread per (target, nm), outputs packed densely.  Node ranges are uniform
       // across the block, so the loops do not diverge.
-      constexpr int W = C::n + (ENV ? 1 : 0);
+      constexpr int W = C::n;
       const int nout = nt * W;
       for (int o = threadIdx.x; o < nout; o += blockDim.x) {
         const int i = o / W, nm = o - i * W;
-        const bool env = ENV && nm == C::n;
         for (int sg = 0; sg < nseg; ++sg) {
           const int qa = max(sg * Q - c0, 0), qb = min((sg + 1) * Q - c0, nch);
           if (qa >= qb) continue;
           const bool first = sg * Q >= c0;  // the segment starts in this chunk
           double are = 0.0, aim = 0.0;
-          if (mixed) {
-            const float* pr = env ? Evf + i * C::CH : &Gf[i * C::CH].x;
-            const int st = env ? 1 : 2;
-            const float* pi = env ? pr : pr + 1;
-            float fre = 0.0f, fim = 0.0f;
-            for (int ql = qa; ql < qb; ++ql) {
-              const float bv = Bf[ql * C::BS + nm];
-              fre = fmaf(pr[ql * st], bv, fre);
-              fim = fmaf(pi[ql * st], bv, fim);
-            }
-            are = env ? (double)fre * (kF32Floor / kRoundingFloor) : (double)fre;
-            aim = fim;
-          } else {
-            const double* pr = env ? Ev + i * C::CH : &G[i * C::CH].re;
-            const int st = env ? 1 : 2;
-            const double* pi = env ? pr : pr + 1;
-            for (int ql = qa; ql < qb; ++ql) {
-              const double bv = B[ql * C::BS + nm];
-              are = fma(pr[ql * st], bv, are);
-              aim = fma(pi[ql * st], bv, aim);
-            }
+          const double* pr = &G[i * C::CH].re;
+          for (int ql = qa; ql < qb; ++ql) {
+            const double bv = B[ql * C::BS + nm];
+            are = fma(pr[2 * ql], bv, are);
+            aim = fma(pr[2 * ql + 1], bv, aim);
           }
-          if (env) {
-            double* ed = eout + (int64_t)(t0 + i) * nseg + sg;
-            *ed = first ? are : *ed + are;
+          cplx* dst = reinterpret_cast<cplx*>(orow(t0 + i)) + (int64_t)sg * C::n + nm;
+          if (first) {
+            dst->re = are;
+            dst->im = aim;
           } else {
-            cplx* dst = reinterpret_cast<cplx*>(orow(t0 + i)) + (int64_t)sg * C::n + nm;
-            if (first) {
-              dst->re = are;
-              dst->im = aim;
-            } else {
-              dst->re += are;
-              dst->im += aim;
-            }
+            dst->re += are;
+            dst->im += aim;
           }
         }
       }
@@ -298,9 +233,7 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
   }
 }
 
-// Moments as block_moments<D, ENV> (the adaptive walk, the smooth-rule and annulus moments):
-// I[i][seg][nm] = sum_{q in seg} w_q K(x_i, X_q) J_q K_nm(u_q, v_q) and, when eout is not
-// null, eout[i * nseg + seg] = sum_q of the kernel's rounding envelope (FP32 sums), with the
+// The split of kernel rows for the tensor-core moments (block_moments_tc below), with the
 // contraction over the nodes on the tensor cores by the exact NS-slice split (lcq_tc.cuh):
 // NS = 8 for FP64 kernel values, NS = 5 for the mixed form's FP32 ones.
 // Chunks never straddle a segment: segment sg's Q nodes are cut into parts of at most
@@ -434,7 +367,7 @@ __device__ __forceinline__ void tc_tile(const uint16_t* Bsl, const uint16_t* Asl
   }
 }
 
-// Moments as block_moments<D, ENV> (the adaptive walk, the smooth-rule and annulus moments):
+// Moments as block_moments (the adaptive walk, the smooth-rule and annulus moments):
 // I[i][seg][nm] = sum_{q in seg} w_q K(x_i, X_q) J_q K_nm(u_q, v_q) and, when eout is not
 // null, eout[i * nseg + seg] = sum_q of the kernel's rounding envelope (FP32 sums), with the
 // contraction over the nodes on the tensor cores by the exact slice split (lcq_tc.cuh):
