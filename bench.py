@@ -518,12 +518,16 @@ def run_ours(args, rank, world, local_rank):
                     e1.record(stream)
                     st_t = ctx.sync()
                     ms.append(e0.elapsed_time(e1))
+                    t_stages = ctx.stage_times()[0]
+                    t_group = int(ctx.counters()[5])
                     nnz, n_over = corr.info()
                     corr.close()
                     near.close()
                 table1.append({"p": d + 1, "eps": eps, "points": ts.n_points,
                                "alpha": n_over / ts.n_points, "m": nnz / ts.n_points,
-                               "S_init": ts.n_points / (ms[-1] / 1e3), "status": st_t})
+                               "S_init": ts.n_points / (ms[-1] / 1e3), "status": st_t,
+                               "group_size": t_group,
+                               "stages_ms": [round(float(x), 3) for x in t_stages]})
             del tds, tx_d1, ttn_d1
 
     # the 40,000-patch torus (k = 20, eps = 1e-9), FP64 and mixed, one timed step each; the
