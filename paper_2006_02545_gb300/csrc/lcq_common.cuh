@@ -105,26 +105,30 @@ struct SegMap {
 
 // Moments I[i][seg][nm] = sum_{q in seg} w_q K(x_i, X_q) J_q K_nm(u_q, v_q) for a smooth
 // rule (Q nodes) pushed onto nseg affine images of T0, for T targets, in FP64 throughout
-// (the far order q_j, whose decisions compare these moments).  Geometry is evaluated once
-// per chunk of nodes and shared by all targets (Sec. 4.3 reuse).
+// (the far order q_j, whose decisions compare these moments, and the moments of the
+// smallest degrees, block_moments_any).  Geometry is evaluated once per chunk of nodes and
+// shared by all targets (Sec. 4.3 reuse).
 // TA: target accessor (pos(i, x[3])); out row of target i: out + orow(i) * ostride.
 // Positions are relative to the patch centroid cen (the coefficients cf describe
 // X - cen); cfd holds the derivative series of load_coef_derivs, which replace the
-// derivative recurrences.
-template <int D, class TA, class OR>
+// derivative recurrences.  With ENV, eout[i * nseg + seg] also receives the summed FP64
+// rounding envelope (through the basis rows' column of ones).
+template <int D, bool ENV = false, class TA, class OR>
 __device__ void block_moments(const double* cf, const double* cfd, const double* __restrict__ ru,
                               const double* __restrict__ rv, const double* __restrict__ rw, int Q,
                               const SegMap* segs, int nseg, const TA& ta, int T, OR orow,
                               int64_t ostride, const KernelParams& kp, double* sm,
-                              const double* cen) {
+                              const double* cen, double R = 0.0, double* eout = nullptr) {
   using C = Cfg<D>;
   double* B = sm;
   double* Xs = B + C::CH * C::BS;
   double* Ns = Xs + 3 * C::CH;
   double* Js = Ns + 3 * C::CH;
   cplx* G = reinterpret_cast<cplx*>(Js + C::CH);
-  double* tx = reinterpret_cast<double*>(G + C::TT * C::CH) + C::TT * C::CH;
+  double* Ev = reinterpret_cast<double*>(G + C::TT * C::CH);
+  double* tx = Ev + C::TT * C::CH;
   double* tn = tx + 3 * C::TT;  // target normals (S')
+  static_assert(C::n < C::BS, "the basis rows need a spare column");
   (void)ostride;
   const KernelParamsF kf = to_f32(kp);
   const bool has_ki = kp.ki != 0.0;
@@ -170,6 +174,7 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
         const double v = S.ay + r0 * S.e1y + r1 * S.e2y;
         kw_geometry_proj<D>(u, v, cf, cfd, X, Xu, Xv, B + ql * C::BS);
       }
+      if (ENV) B[ql * C::BS + C::n] = 1.0;  // the envelope's column
       cross3(Xu, Xv, Nn);
       const double J = sqrt(Nn[0] * Nn[0] + Nn[1] * Nn[1] + Nn[2] * Nn[2]);
 #pragma unroll
@@ -191,40 +196,60 @@ __device__ void block_moments(const double* cf, const double* cfd, const double*
         if (kp.kind == 3) ta.nrm(t0 + threadIdx.x, xp, tn + 3 * threadIdx.x);
       }
       __syncthreads();
-      // kernel values by the table sincos and the Newton-refined 1/sqrt (no envelope)
+      // kernel values by the table sincos and the Newton-refined 1/sqrt; with ENV the
+      // FP64 form with its rounding envelope
       for (int e = threadIdx.x; e < nt * nch; e += blockDim.x) {
         const int i = e / nch, ql = e - i * nch;
-        float unused;
-        G[i * C::CH + ql] = kernel_eval_tc(kp, kf, g_sct, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2],
-                                           Xs[ql], Xs[C::CH + ql], Xs[2 * C::CH + ql], Ns[ql],
-                                           Ns[C::CH + ql], Ns[2 * C::CH + ql], Js[ql], 0.0f, 0.0f,
-                                           &unused, tn + 3 * i, has_ki);
+        if (ENV) {
+          double ev = 0.0;
+          G[i * C::CH + ql] = kernel_eval(kp, tx[3 * i], tx[3 * i + 1], tx[3 * i + 2], Xs[ql],
+                                          Xs[C::CH + ql], Xs[2 * C::CH + ql], Ns[ql],
+                                          Ns[C::CH + ql], Ns[2 * C::CH + ql], Js[ql], R, &ev,
+                                          tn + 3 * i);
+          Ev[i * C::CH + ql] = ev;
+        } else {
+          float unused;
+          G[i * C::CH + ql] = kernel_eval_tc(kp, kf, g_sct, tx[3 * i], tx[3 * i + 1],
+                                             tx[3 * i + 2], Xs[ql], Xs[C::CH + ql],
+                                             Xs[2 * C::CH + ql], Ns[ql], Ns[C::CH + ql],
+                                             Ns[2 * C::CH + ql], Js[ql], 0.0f, 0.0f, &unused,
+                                             tn + 3 * i, has_ki);
+        }
       }
       __syncthreads();
-      // one thread per (target, nm), outputs packed densely.  Node ranges are uniform
+      // one thread per (target, nm), outputs packed densely; with ENV the extra index nm = n
+      // sums the envelope through the basis rows' column of ones.  Node ranges are uniform
       // across the block, so the loops do not diverge.
-      constexpr int W = C::n;
+      constexpr int W = C::n + (ENV ? 1 : 0);
       const int nout = nt * W;
       for (int o = threadIdx.x; o < nout; o += blockDim.x) {
         const int i = o / W, nm = o - i * W;
+        const bool env = ENV && nm == C::n;
         for (int sg = 0; sg < nseg; ++sg) {
           const int qa = max(sg * Q - c0, 0), qb = min((sg + 1) * Q - c0, nch);
           if (qa >= qb) continue;
           const bool first = sg * Q >= c0;  // the segment starts in this chunk
           double are = 0.0, aim = 0.0;
-          const double* pr = &G[i * C::CH].re;
+          const double* pr = env ? Ev + i * C::CH : &G[i * C::CH].re;
+          const int st = env ? 1 : 2;
+          const double* pi = env ? pr : pr + 1;
           for (int ql = qa; ql < qb; ++ql) {
             const double bv = B[ql * C::BS + nm];
-            are = fma(pr[2 * ql], bv, are);
-            aim = fma(pr[2 * ql + 1], bv, aim);
+            are = fma(pr[ql * st], bv, are);
+            aim = fma(pi[ql * st], bv, aim);
           }
-          cplx* dst = reinterpret_cast<cplx*>(orow(t0 + i)) + (int64_t)sg * C::n + nm;
-          if (first) {
-            dst->re = are;
-            dst->im = aim;
+          if (env) {
+            double* ed = eout + (int64_t)(t0 + i) * nseg + sg;
+            *ed = first ? are : *ed + are;
           } else {
-            dst->re += are;
-            dst->im += aim;
+            cplx* dst = reinterpret_cast<cplx*>(orow(t0 + i)) + (int64_t)sg * C::n + nm;
+            if (first) {
+              dst->re = are;
+              dst->im = aim;
+            } else {
+              dst->re += are;
+              dst->im += aim;
+            }
           }
         }
       }
@@ -672,6 +697,41 @@ __device__ void block_moments_tc(const double* cf, const double* cfd, const doub
   }
 }
 
+// The moments of the smallest degrees in the FP64 form (n <= 10 basis functions) by the
+// plain FP64 engine (16-target tiles, one thread per output): there the contraction is too
+// small to pay for the tensor-core pipeline's fixed cost per 8-target tile (barriers, the
+// slice split).  Every other case: block_moments_tc.  smb holds either engine's workspace.
+constexpr int kFp64MomentsMaxDeg = 3;
+template <int D, class TA, class OR>
+__device__ __forceinline__ void block_moments_any(
+    const double* cf, const double* cfd, const double* __restrict__ ru,
+    const double* __restrict__ rv, const double* __restrict__ rw, int Q, const SegMap* segs,
+    int nseg, const TA& ta, int T, OR orow, const KernelParams& kp, unsigned char* smb,
+    const double* cen, double R, double* eout, int form) {
+  if constexpr (D <= kFp64MomentsMaxDeg) {
+    if (form == 0) {
+      double* sm = reinterpret_cast<double*>(smb);
+      if (eout)
+        block_moments<D, true>(cf, cfd, ru, rv, rw, Q, segs, nseg, ta, T, orow, Cfg<D>::n, kp, sm,
+                               cen, R, eout);
+      else
+        block_moments<D, false>(cf, cfd, ru, rv, rw, Q, segs, nseg, ta, T, orow, Cfg<D>::n, kp, sm,
+                                cen);
+      return;
+    }
+  }
+  block_moments_tc<D>(cf, cfd, ru, rv, rw, Q, segs, nseg, ta, T, orow, kp, smb, cen, R, eout,
+                      form);
+}
+
+// Shared-memory bytes of the moment workspace (either engine's).
+template <int D>
+constexpr size_t moment_ws_bytes() {
+  return D <= kFp64MomentsMaxDeg && sizeof(double) * Cfg<D>::WS > (size_t)TcCfg<D>::BYTES
+             ? sizeof(double) * Cfg<D>::WS
+             : (size_t)TcCfg<D>::BYTES;
+}
+
 template <int D>
 __device__ __forceinline__ void load_coef(const double* __restrict__ coef, int64_t off, double* cf) {
   constexpr int n = (D + 1) * (D + 2) / 2;
@@ -880,7 +940,7 @@ struct AdaptiveWS {
 template <int D>
 constexpr size_t adaptive_smem_bytes() {
   return sizeof(double) * 3 * Cfg<D>::n + sizeof(SegMap) * 4 + 64 * sizeof(int) +
-         4 * 32 * sizeof(unsigned long long) + 128 + TcCfg<D>::BYTES;
+         4 * 32 * sizeof(unsigned long long) + 128 + moment_ws_bytes<D>();
 }
 
 // Work items are taken dynamically through the counter *sched, which the caller zeroes
@@ -1007,9 +1067,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
     __syncthreads();
     if (leaf_order > 0) {
       TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, dv.tnrm};
-      block_moments_tc<D>(cf, cfdp, ru, rv, rw, Q, segs, 1, ta, A,
-                          [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, kps, smb,
-                          dv.cen + 3 * j, Rj, tmpE, formj);
+      block_moments_any<D>(cf, cfdp, ru, rv, rw, Q, segs, 1, ta, A,
+                           [=] __device__(int i) { return lvlI + (int64_t)i * 4 * n; }, kps, smb,
+                           dv.cen + 3 * j, Rj, tmpE, formj);
     }
     // DFS stack entries: level (8 bits) | child (2 bits) | path (2 bits per level) << 16
     int sp = 0;
@@ -1059,9 +1119,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_adaptive(const int* __restrict_
       __syncthreads();
       // children moments of every target in S
       TgtAdaptive ta{dv.tgt, dv.NT, dv.pair_tgt, apairs, ST, dv.tnrm};
-      block_moments_tc<D>(cf, cfdp, ru, rv, rw, Q, segs, 4, ta, S,
-                          [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, kps, smb,
-                          dv.cen + 3 * j, Rj, tmpE, formj);
+      block_moments_any<D>(cf, cfdp, ru, rv, rw, Q, segs, 4, ta, S,
+                           [=] __device__(int i) { return tmp + (int64_t)i * 4 * n; }, kps, smb,
+                           dv.cen + 3 * j, Rj, tmpE, formj);
       __syncthreads();
       my_tests += S;
       my_nodes += (long long)S * 4 * Q;

@@ -164,17 +164,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_rule_moments(
         const int64_t p0 = dv.pair_ptr[j], np = dv.pair_ptr[j + 1] - p0;
         TgtIdx ta{dv.tgt, dv.NT, dv.pair_tgt + p0, dv.tnrm};
         cplx* base = out_smooth + p0 * ld;
-        block_moments_tc<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)np,
-                            [=] __device__(int i) { return base + (int64_t)i * ld; }, kps, smb,
-                            dv.cen + 3 * j, 0.0, nullptr, formj);
+        block_moments_any<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)np,
+                             [=] __device__(int i) { return base + (int64_t)i * ld; }, kps, smb,
+                             dv.cen + 3 * j, 0.0, nullptr, formj);
         evals += np * m * m;
       } else {
         const int64_t a0 = dv.an_ptr[j], na = dv.an_ptr[j + 1] - a0;
         const int32_t* pl = dv.an_pair + a0;
         TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl, dv.tnrm};
-        block_moments_tc<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)na,
-                            [=] __device__(int i) { return out_ann + (int64_t)pl[i] * ld; }, kps,
-                            smb, dv.cen + 3 * j, 0.0, nullptr, formj);
+        block_moments_any<D>(cf, cfdp, ru, rv, rw, m * m, segs, 1, ta, (int)na,
+                             [=] __device__(int i) { return out_ann + (int64_t)pl[i] * ld; }, kps,
+                             smb, dv.cen + 3 * j, 0.0, nullptr, formj);
         evals += na * m * m;
       }
     }
@@ -719,7 +719,7 @@ template <int D>
 void RuleMomL<D>::run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv, int modes,
                   const int32_t* qv, const int32_t* qn, const KernelParams& kp, void* out_smooth,
                   void* out_ann, int form) {
-    const size_t sm = sizeof(double) * 3 * Cfg<D>::n + sizeof(SegMap) * 4 + 128 + TcCfg<D>::BYTES;
+    const size_t sm = sizeof(double) * 3 * Cfg<D>::n + sizeof(SegMap) * 4 + 128 + moment_ws_bytes<D>();
     set_smem(k_rule_moments<D>, sm);
     ++*lc.launches;
     // one block per patch: the hardware hands the next patch to whichever block slot frees
