@@ -143,7 +143,12 @@ def run_reference(args, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "patches": npat, "order": 6},
+        "data": "synthetic",
+        "config": {"workload": workload_name(npat, 28 * npat, args.eps), "patches": npat,
+                   "order": 6, "precision": "fp64", "points": 28 * npat, "eps": args.eps,
+                   "leaf_order": args.leaf_order or "q_j",
+                   "l2": "host cores: no device cache to flush",
+                   "tuning": "none (the oracle has no tuner)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
