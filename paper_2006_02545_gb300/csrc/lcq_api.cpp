@@ -1324,16 +1324,23 @@ static lcq_status apply_impl(lcq_ctx* ctx, const lcq_near* nr, const lcq_corr* c
   long long napply = 0;
   LaunchCommon lc{st, ctx->num_sms, &napply};
   Dev dv = make_dev(ctx, nr, c->q, nr->n_max, c->grp);
+  // the kernel constants fold into the sources when every surface has a real k and a real
+  // alpha (kinds S, D, CFIE)
+  auto foldable = [](const KernelParams& p) {
+    return p.ki == 0.0 && p.kind <= 2 && p.ai == 0.0;
+  };
+  bool fold = foldable(c->kp);
+  for (const GroupParams& g : c->grp_h) fold = fold && foldable(g.kp);
   double* src;
-  CK(dalloc(st, &src, (size_t)9 * std::max<int64_t>(c->n_over, 1)));
+  CK(dalloc(st, &src, (size_t)(fold ? 10 : 9) * std::max<int64_t>(c->n_over, 1)));
   for (int d = 1; d <= kMaxDeg; ++d) {
     if (!nr->plist_count[d]) continue;
     launch_far_src(d, lc, nr->plist_dev[d], nr->plist_count[d], dv, ctx->deg[d].dV, c->q,
-                   c->src_off, sigma, src, c->n_over);
+                   c->src_off, sigma, src, c->n_over, c->kp, fold);
   }
   launch_far_sum(lc, nr->tgt, nr->n_targets, src, c->n_over, c->kp, nr->tgt_patch, c->src_off,
                  c->grp ? nr->tgroup : nullptr, c->grp, c->gsrc,
-                 kind == LCQ_SP ? nr->tnrm : nullptr, out);
+                 kind == LCQ_SP ? nr->tnrm : nullptr, out, fold);
   launch_csr_apply(lc, nr->row_ptr, nr->col, c->val, sigma, nr->tnode, nr->n_targets, jump, out);
   CK(cudaGetLastError());
   dfree(st, src);

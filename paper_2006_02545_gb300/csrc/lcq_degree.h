@@ -66,7 +66,7 @@ template <int D>
 struct FarSrcL {
   static void run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                   const double* Vt, const int32_t* qv, const int64_t* src_off, const void* sigma,
-                  double* src, int64_t n_over);
+                  double* src, int64_t n_over, const KernelParams& kp, bool fold);
 };
 
 template <int D>

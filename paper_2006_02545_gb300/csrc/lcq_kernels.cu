@@ -68,8 +68,9 @@ __global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* 
 
 // Direct far sum over all oversampled sources, one thread per target (tiles of sources
 // staged through shared memory); kernel values by kernel_eval_tc (table sincos and the
-// Newton-refined reciprocal square root: FP64 throughout, about 40 FP64 instructions per
-// pair for the CFIE).
+// Newton-refined reciprocal square root: FP64 throughout, about 48 FP64 instructions per
+// pair for the CFIE), or with fold by kernel_eval_fold on sources that carry the kernel
+// constants (about 41).
 // The sources of an on-surface target's own patch are skipped (their contribution is
 // carried entirely by the self correction).  In a batch of independent surfaces a target
 // sums only its own surface's sources [gsrc[g], gsrc[g+1]) with that surface's kernel.
@@ -82,8 +83,8 @@ __global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__
                                                       const GroupParams* __restrict__ grp,
                                                       const int64_t* __restrict__ gsrc,
                                                       const double* __restrict__ tnrm,
-                                                      cplx* __restrict__ out) {
-  __shared__ double s[9][kThreads];
+                                                      cplx* __restrict__ out, bool fold) {
+  __shared__ double s[10][kThreads];
   __shared__ unsigned long long blo, bhi;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double x0 = 0, x1 = 0, x2 = 0;
@@ -125,19 +126,23 @@ __global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__
   const bool has_ki = kt.ki != 0.0;
   float env;  // not used: the far sum needs no rounding envelope
   double re = 0.0, im = 0.0;
+  const int rows = fold ? 10 : 9;
   for (int64_t s0 = b0; s0 < b1; s0 += kThreads) {
     __syncthreads();
     const int64_t q = s0 + threadIdx.x;
-    for (int c = 0; c < 9; ++c) s[c][threadIdx.x] = q < b1 ? src[c * n_over + q] : 0.0;
+    for (int c = 0; c < rows; ++c) s[c][threadIdx.x] = q < b1 ? src[c * n_over + q] : 0.0;
     __syncthreads();
     const int cnt = (int)min((int64_t)kThreads, b1 - s0);
     if (t < NT)
       for (int k = 0; k < cnt; ++k) {
         const int64_t qq = s0 + k;
         if (qq < lo || qq >= hi || (qq >= skip0 && qq < skip1)) continue;
-        const cplx g = kernel_eval_tc(kt, kf, g_sct, x0, x1, x2, s[0][k], s[1][k], s[2][k],
-                                      s[3][k], s[4][k], s[5][k], s[6][k], 0.0f, 0.0f, &env, nx,
-                                      has_ki);
+        const cplx g =
+            fold ? kernel_eval_fold(kt.kind, kt.kr, kf, g_sct, x0, x1, x2, s[0][k], s[1][k],
+                                    s[2][k], s[3][k], s[4][k], s[5][k], s[6][k], s[9][k], 0.0f,
+                                    0.0f, &env)
+                 : kernel_eval_tc(kt, kf, g_sct, x0, x1, x2, s[0][k], s[1][k], s[2][k], s[3][k],
+                                  s[4][k], s[5][k], s[6][k], 0.0f, 0.0f, &env, nx, has_ki);
         re = fma(g.re, s[7][k], re);
         re = fma(-g.im, s[8][k], re);
         im = fma(g.re, s[8][k], im);
@@ -334,18 +339,18 @@ bool launch_v2c(int d, const LaunchCommon& lc, const int* plist, int count, cons
 }
 bool launch_far_src(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                     const double* Vt, const int32_t* qv, const int64_t* src_off, const void* sigma,
-                    double* src, int64_t n_over) {
-  return dispatch<FarSrcL>(d, lc, plist, count, dv, Vt, qv, src_off, sigma, src, n_over);
+                    double* src, int64_t n_over, const KernelParams& kp, bool fold) {
+  return dispatch<FarSrcL>(d, lc, plist, count, dv, Vt, qv, src_off, sigma, src, n_over, kp, fold);
 }
 void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const double* src,
                     int64_t n_over, const KernelParams& kp, const int32_t* tpatch,
                     const int64_t* src_off, const int32_t* tgroup, const GroupParams* grp,
-                    const int64_t* gsrc, const double* tnrm, void* out) {
+                    const int64_t* gsrc, const double* tnrm, void* out, bool fold) {
   const int64_t g = (NT + kThreads - 1) / kThreads;
   if (g <= 0) return;
   ++*lc.launches;
   k_far_sum<<<(unsigned)g, kThreads, 0, lc.stream>>>(tgt, NT, src, n_over, kp, tpatch, src_off,
-                                                     tgroup, grp, gsrc, tnrm, (cplx*)out);
+                                                     tgroup, grp, gsrc, tnrm, (cplx*)out, fold);
 }
 void launch_widen_c64(const LaunchCommon& lc, const void* in, int64_t n, void* out) {
   if (n <= 0) return;

@@ -632,12 +632,16 @@ __global__ void k_v2c(const int* __restrict__ plist, int count, Dev dv,
 
 // ============================================================================ apply
 // Oversampled sources of rule q_j: X, (X_u x X_v) w, |.| w and w-weighted density
-// sigma~_q = sum_nm K_nm(u_q) s_nm, s = V sigma (Sec. 4.2 Remark, Sec. 5.3).
+// sigma~_q = sum_nm K_nm(u_q) s_nm, s = V sigma (Sec. 4.2 Remark, Sec. 5.3).  With fold
+// (real k, kinds S, D and CFIE with a real alpha) the patch's kernel constants are folded
+// into the source data as kernel_eval_fold takes them: rows 3-5 N w alpha / (4 pi), row 6
+// beta_r J w / (4 pi), row 9 beta_i J w / (4 pi).
 template <int D>
 __global__ void k_far_src(const int* __restrict__ plist, int count, Dev dv,
                           const double* __restrict__ Vt, const int32_t* __restrict__ qv,
                           const int64_t* __restrict__ src_off, const cplx* __restrict__ sigma,
-                          double* __restrict__ src /*[8][N_over]*/, int64_t n_over) {
+                          double* __restrict__ src /*[9 or 10][N_over]*/, int64_t n_over,
+                          const KernelParams kp, bool fold) {
   constexpr int n = (D + 1) * (D + 2) / 2;
   __shared__ double cf[3 * n];
   __shared__ double cfd[2 * 3 * (D * (D + 1) / 2)];  // derivative series of the chart
@@ -645,6 +649,11 @@ __global__ void k_far_src(const int* __restrict__ plist, int count, Dev dv,
   for (int b = blockIdx.x; b < count; b += gridDim.x) {
     const int j = plist[b];
     const int64_t off = dv.node_off[j];
+    const KernelParams kj = patch_kp(dv, j, kp);
+    constexpr double kInv4Pi = 0.07957747154594767;
+    const double fa_n = fold ? (kj.kind == 1 ? 1.0 : kj.ar) * kInv4Pi : 1.0;
+    const double fj_r = fold ? (kj.kind == 0 ? 1.0 : kj.br) * kInv4Pi : 1.0;
+    const double fj_i = kj.bi * kInv4Pi;
     __syncthreads();
     load_coef<D>(dv.coef, off, cf);
     __syncthreads();
@@ -681,12 +690,14 @@ __global__ void k_far_src(const int* __restrict__ plist, int count, Dev dv,
       src[0 * n_over + o] = X[0] + dv.cen[3 * j];
       src[1 * n_over + o] = X[1] + dv.cen[3 * j + 1];
       src[2 * n_over + o] = X[2] + dv.cen[3 * j + 2];
-      src[3 * n_over + o] = Nn[0] * w;
-      src[4 * n_over + o] = Nn[1] * w;
-      src[5 * n_over + o] = Nn[2] * w;
-      src[6 * n_over + o] = J * w;
+      const double wn = w * fa_n;
+      src[3 * n_over + o] = Nn[0] * wn;
+      src[4 * n_over + o] = Nn[1] * wn;
+      src[5 * n_over + o] = Nn[2] * wn;
+      src[6 * n_over + o] = J * w * fj_r;
       src[7 * n_over + o] = re;
       src[8 * n_over + o] = im;
+      if (fold) src[9 * n_over + o] = J * w * fj_i;
     }
   }
 }
@@ -803,11 +814,11 @@ void V2cL<D>::run(const LaunchCommon& lc, const int* plist, int count, const Dev
 template <int D>
 void FarSrcL<D>::run(const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                   const double* Vt, const int32_t* qv, const int64_t* src_off, const void* sigma,
-                  double* src, int64_t n_over) {
+                  double* src, int64_t n_over, const KernelParams& kp, bool fold) {
     const int grid = count < lc.num_sms * 4 ? count : lc.num_sms * 4;
     ++*lc.launches;
     k_far_src<D><<<grid, 128, 0, lc.stream>>>(plist, count, dv, Vt, qv, src_off,
-                                              (const cplx*)sigma, src, n_over);
+                                              (const cplx*)sigma, src, n_over, kp, fold);
   }
 
 template <int D>

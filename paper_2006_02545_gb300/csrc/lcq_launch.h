@@ -149,13 +149,16 @@ bool launch_self(int d, const LaunchCommon& lc, const Dev& dv, const int32_t* de
 bool launch_v2c(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                 const double* Vt, const void* In, const void* Is, const void* InS,
                 double* val);
+// fold: the sources carry the kernel constants (k_far_src), the far sum evaluates by
+// kernel_eval_fold; only for real k and kinds S, D, CFIE with a real alpha (every surface's)
 bool launch_far_src(int d, const LaunchCommon& lc, const int* plist, int count, const Dev& dv,
                     const double* Vt, const int32_t* qv, const int64_t* src_off, const void* sigma,
-                    double* src, int64_t n_over);
+                    double* src, int64_t n_over, const KernelParams& kp = KernelParams{},
+                    bool fold = false);
 void launch_far_sum(const LaunchCommon& lc, const double* tgt, int64_t NT, const double* src,
                     int64_t n_over, const KernelParams& kp, const int32_t* tpatch,
                     const int64_t* src_off, const int32_t* tgroup, const GroupParams* grp,
-                    const int64_t* gsrc, const double* tnrm, void* out);
+                    const int64_t* gsrc, const double* tnrm, void* out, bool fold = false);
 void launch_widen_c64(const LaunchCommon& lc, const void* in, int64_t n, void* out);
 void launch_csr_apply(const LaunchCommon& lc, const int64_t* row_ptr, const int32_t* col,
                       const double* val, const void* sigma, const int64_t* tnode, int64_t NT,
