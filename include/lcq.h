@@ -64,16 +64,22 @@ typedef enum {
  *              from the patch centroid.  LCQ_MIXED falls back to FP64 for S'. */
 typedef enum { LCQ_S = 0, LCQ_D = 1, LCQ_CFIE = 2, LCQ_SP = 3 } lcq_kernel;
 
-/* LCQ_FP64: every step in FP64.
- * LCQ_MIXED: in the adaptive near integration and the smooth-rule and annulus moments,
- * every (target, node) kernel value is computed in FP32 from the FP64 difference x - X
- * (r and the phase k r formed and reduced in FP64) and contracted with FP32 basis
- * values, summed in FP32 per chunk of nodes into FP64 moments; the chart geometry, self
- * rules, far orders, refinement decisions and the values-to-coefficients contraction stay
- * FP64.  The adaptive test's rounding floor is raised to FP32's level.  The result moves
- * by about 1e-7 relative, so the FP32 evaluation is used only for eps >= 1e-6 (per
- * surface in a batch); below, LCQ_MIXED is LCQ_FP64.  S' always runs FP64.  The
- * difference from LCQ_FP64 is stated per result by the tests and the benchmark. */
+/* LCQ_FP64: every step in FP64 (the contraction of kernel values with basis values on the
+ * tensor cores by an exact split of the FP64 operands).
+ * LCQ_MIXED: the (target, node) kernel values of the adaptive near integration and of the
+ * smooth-rule and annulus moments move to the FP32 pipe, always from the FP64 difference
+ * x - X; the chart geometry, self rules, far orders, refinement tests (on the moments),
+ * the values-to-coefficients contraction and the apply stay FP64.  By tolerance (per
+ * surface in a batch):
+ *   eps >= 1e-6          FP32 kernel values (r and the phase k r reduced in FP64),
+ *                        contracted from 5 slices; the adaptive test's rounding floor is
+ *                        raised to FP32's level; results move by about 1e-7 relative;
+ *   1e-6 > eps >= 1e-11  two-float kernel values (pairs of FP32 numbers, about 48 bits),
+ *                        contracted like FP64 values; results move by about 1e-14
+ *                        relative; needs a real k and a real alpha (else FP64);
+ *   eps < 1e-11          FP64.
+ * S' always runs FP64.  lcq_counters reports the forms a generation used; the difference
+ * from LCQ_FP64 is stated per result by the tests and the benchmark. */
 typedef enum { LCQ_FP64 = 0, LCQ_MIXED = 1 } lcq_precision;
 
 /* Surface: n_patches charts; patch j owns nodes node_off[j] .. node_off[j+1]-1,
@@ -296,7 +302,9 @@ lcq_status lcq_sync(lcq_ctx* ctx, int64_t timeout_ms);
  * [2] self node evaluations, [3] smooth/annulus node evaluations (target x node),
  * [4] union-tree nodes walked by the adaptive kernel (each evaluates the chart geometry
  * at 4Q leaf nodes), [5] the largest number of adaptive targets per work item (the
- * group size the context's tuner chose), [6] adaptive work items, [7] zero.  Synchronizes.
+ * group size the context's tuner chose), [6] adaptive work items, [7] the pair
+ * evaluation forms the generation used, a bit mask (1: FP32, 2: two-float; 0: FP64 only;
+ * see lcq_precision).  Synchronizes.
  * The adaptive walk takes its work in items of at most a group size of targets of one
  * patch; an online tuner in the context times each candidate size once per key (degree,
  * kernel, tolerance decade, precision, size of the adaptive work) on the generations that
