@@ -402,10 +402,11 @@ __device__ __forceinline__ void tc_tile(const uint16_t* Bsl, const uint16_t* Asl
 // zero columns to a multiple of 16 (the MMA depth), packed while they fit in TcCfg::CH
 // columns: the four children of a small rule share one chunk.  Each piece's contribution is
 // assembled in FP64 and written (the segment's first part) or added.
-// Per chunk: (1) geometry, thread per node: X, N w, J w (FP64), and each basis value split
-// into 8 f16 slices on its column's fixed bound as it is formed (integer work that runs in
-// the shadow of the FP64 geometry); (2) per tile of 8 targets: kernel values and envelopes,
-// thread per (target, node); (3) one warp per target splits the Re and Im rows of its kernel
+// Per chunk: (1) geometry, thread per real node (padding columns are zeroed apart, so no
+// lane of the FP64 work idles): X, N w, J w (FP64), and each basis value split into 8 f16
+// slices on its column's fixed bound as it is formed (integer work that runs in the shadow
+// of the FP64 geometry); (2) per tile of 8 targets: kernel values and envelopes, thread per
+// (target, real node); (3) one warp per target splits the Re and Im rows of its kernel
 // values on their own power-of-two scales; (4) one warp per n-tile of 8 basis columns
 // accumulates the diagonals over each piece's 16-node steps with mma.sync, both operands read
 // by ldmatrix, and assembles and stores its 8 x 8 complex block.
