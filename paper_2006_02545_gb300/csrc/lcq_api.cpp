@@ -61,6 +61,28 @@ void dfree(cudaStream_t st, T*& p) {
   p = nullptr;
 }
 
+// Runs f when the enclosing scope ends unless dismissed: a call that fails part-way
+// releases what it has set up (the partly built handle, its work buffers).
+template <class F>
+class ScopeExit {
+ public:
+  explicit ScopeExit(F f) : f_(std::move(f)) {}
+  ~ScopeExit() {
+    if (armed_) f_();
+  }
+  void dismiss() { armed_ = false; }
+  ScopeExit(const ScopeExit&) = delete;
+  ScopeExit& operator=(const ScopeExit&) = delete;
+
+ private:
+  F f_;
+  bool armed_ = true;
+};
+template <class F>
+ScopeExit<F> on_exit(F f) {
+  return ScopeExit<F>(std::move(f));
+}
+
 int default_self_order(double eps) {
   const double e = std::min(std::max(eps, 1e-15), 1e-1);
   const double digits = -log10(e);
@@ -73,6 +95,15 @@ lcq_status ensure_rules(lcq_ctx* ctx) {
   RuleTables& r = ctx->rules;
   if (!build_rule_tables(&r)) return fail(ctx, LCQ_ERR_TABLES, "rule tables");
   cudaStream_t st = ctx->stream;
+  auto undo = on_exit([&] {
+    dfree(st, r.doff);
+    dfree(st, r.du);
+    dfree(st, r.dv);
+    dfree(st, r.dw);
+    dfree(st, r.dgl_off);
+    dfree(st, r.dgl_x);
+    dfree(st, r.dgl_w);
+  });
   CK(dalloc(st, &r.doff, r.off.size()));
   CK(dalloc(st, &r.du, r.u.size()));
   CK(dalloc(st, &r.dv, r.v.size()));
@@ -89,15 +120,23 @@ lcq_status ensure_rules(lcq_ctx* ctx) {
   CK(cudaMemcpyAsync(r.dgl_x, r.gl_x.data(), r.gl_x.size() * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(r.dgl_w, r.gl_w.data(), r.gl_w.size() * 8, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
+  undo.dismiss();
   ctx->rules_ready = true;
   return LCQ_OK;
 }
 
+// A degree's device tables are all present (dV set) or none is: a failed upload frees
+// what it allocated, so that the next call starts again.
 lcq_status ensure_deg(lcq_ctx* ctx, int d) {
   DegTables& t = ctx->deg[d];
   if (t.dV) return LCQ_OK;
   if (!build_deg_tables(d, &t)) return fail(ctx, LCQ_ERR_TABLES, "degree tables");
   cudaStream_t st = ctx->stream;
+  auto undo = on_exit([&] {
+    dfree(st, t.dV);
+    dfree(st, t.dnodes);
+    dfree(st, t.dDuv);
+  });
   const int n = t.n;
   std::vector<double> nodes(3 * n);
   for (int i = 0; i < n; ++i) {
@@ -114,6 +153,7 @@ lcq_status ensure_deg(lcq_ctx* ctx, int d) {
   CK(dalloc(st, &t.dDuv, duv.size()));
   CK(cudaMemcpyAsync(t.dDuv, duv.data(), duv.size() * 8, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
+  undo.dismiss();
   return LCQ_OK;
 }
 
@@ -204,6 +244,7 @@ lcq_status lcq_create(lcq_ctx** out, int device, void* cuda_stream) {
   lcq_ctx* ctx = new lcq_ctx();
   ctx->device = device;
   ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  auto undo = on_exit([&] { lcq_destroy(ctx); });
   CK(cudaSetDevice(device));
   CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
   CK(cudaMalloc(&ctx->d_status, sizeof(int)));
@@ -223,10 +264,8 @@ lcq_status lcq_create(lcq_ctx** out, int device, void* cuda_stream) {
   CK(cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming));
   for (int i = 0; i < 2; ++i) CK(cudaEventCreate(&ctx->ev_self[i]));
   lcq_status s = ensure_rules(ctx);
-  if (s != LCQ_OK) {
-    lcq_destroy(ctx);
-    return s;
-  }
+  if (s != LCQ_OK) return s;
+  undo.dismiss();
   *out = ctx;
   return LCQ_OK;
 }
@@ -373,6 +412,38 @@ static lcq_status build_near_impl(lcq_ctx* ctx, const lcq_surface* surf, int n_g
   nr->node_off_h.assign(surf->node_off, surf->node_off + P + 1);
   nr->stream = st;
   nr->device = ctx->device;
+  auto undo = on_exit([&] { lcq_near_destroy(nr); });
+  // work buffers of this call, released on every return (the success path frees them
+  // itself as soon as they are no longer needed)
+  int64_t* goff = nullptr;
+  double* bnd = nullptr;
+  unsigned long long *cell_cnt = nullptr, *cell_cur = nullptr;
+  int64_t* cell_ptr = nullptr;
+  int32_t* cell_patch = nullptr;
+  int64_t* scr = nullptr;
+  int64_t *row_np = nullptr, *row_nnz = nullptr;
+  unsigned long long *npair = nullptr, *nad = nullptr, *nself = nullptr, *pcur = nullptr,
+                     *scur = nullptr;
+  int32_t *row_tmp = nullptr, *ptmp = nullptr, *stmp = nullptr;
+  auto tmp_free = on_exit([&] {
+    dfree(st, goff);
+    dfree(st, bnd);
+    dfree(st, cell_cnt);
+    dfree(st, cell_cur);
+    dfree(st, cell_ptr);
+    dfree(st, cell_patch);
+    dfree(st, scr);
+    dfree(st, row_np);
+    dfree(st, row_nnz);
+    dfree(st, npair);
+    dfree(st, nad);
+    dfree(st, nself);
+    dfree(st, pcur);
+    dfree(st, scur);
+    dfree(st, row_tmp);
+    dfree(st, ptmp);
+    dfree(st, stmp);
+  });
   nr->grouped = grouped;
   nr->n_groups = grouped ? n_groups : 1;
   if (grouped) nr->gpatch_off.assign(group_patch_off, group_patch_off + n_groups + 1);
@@ -418,7 +489,6 @@ static lcq_status build_near_impl(lcq_ctx* ctx, const lcq_surface* surf, int n_g
   }
   CK(cudaGetLastError());
   if (grouped) {
-    int64_t* goff;
     CK(dalloc(st, &goff, n_groups + 1));
     CK(cudaMemcpyAsync(goff, group_patch_off, (n_groups + 1) * 8, cudaMemcpyHostToDevice, st));
     CK(dalloc(st, &nr->pgroup, P));
@@ -429,7 +499,6 @@ static lcq_status build_near_impl(lcq_ctx* ctx, const lcq_surface* surf, int n_g
   }
   NearArgs na{nr->tgt, NT, nr->cen, nr->rad, nr->eta, nr->eta1, nr->pgroup, nr->tgroup};
   // uniform grid over the patch centroids (cell edge >= max eta_j R_j)
-  double* bnd;
   CK(dalloc(st, &bnd, 8));
   launch_grid_bounds(lc, na, P, bnd);
   double hb[7];
@@ -440,23 +509,16 @@ static lcq_status build_near_impl(lcq_ctx* ctx, const lcq_surface* surf, int n_g
     CK(cudaMemcpy(&hst, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (hst & kStBadGroup) {
       cudaMemset(ctx->d_status, 0, sizeof(int));
-      dfree(st, bnd);
-      lcq_near_destroy(nr);
       return fail(ctx, LCQ_ERR_ARG, "target surface index outside [0, n_surfaces)");
     }
     if (hst & (kStNonFinite | kStDegenerate)) {
       cudaMemset(ctx->d_status, 0, sizeof(int));
-      dfree(st, bnd);
-      lcq_near_destroy(nr);
       return fail(ctx, (hst & kStNonFinite) ? LCQ_ERR_NONFINITE : LCQ_ERR_DEGENERATE_PATCH,
                   (hst & kStNonFinite) ? "non-finite coordinates" : "degenerate patch");
     }
   }
   const GridSpec g = make_grid(hb, P);
   const int64_t ncell = (int64_t)g.nx * g.ny * g.nz;
-  unsigned long long *cell_cnt, *cell_cur;
-  int64_t* cell_ptr;
-  int32_t* cell_patch;
   CK(dalloc(st, &cell_cnt, ncell + 1));
   CK(dalloc(st, &cell_cur, ncell));
   CK(dalloc(st, &cell_ptr, ncell + 1));
@@ -464,13 +526,10 @@ static lcq_status build_near_impl(lcq_ctx* ctx, const lcq_surface* surf, int n_g
   CK(cudaMemsetAsync(cell_cnt, 0, (ncell + 1) * 8, st));
   CK(cudaMemsetAsync(cell_cur, 0, ncell * 8, st));
   const int64_t mx = std::max(std::max(NT, P), ncell) + 1;
-  int64_t* scr;
   CK(dalloc(st, &scr, 2 * ((mx + 1023) / 1024) + 4096));
   launch_cell_bins(lc, na, P, g, cell_cnt, cell_ptr, cell_cur, cell_patch, scr);
 
   // rows: counts, offsets, then the sorted patches of each row and the CSR columns
-  int64_t *row_np, *row_nnz;
-  unsigned long long *npair, *nad, *nself, *pcur, *scur;
   CK(dalloc(st, &row_np, NT + 1));
   CK(dalloc(st, &row_nnz, NT + 1));
   CK(dalloc(st, &npair, P + 1));
@@ -502,7 +561,6 @@ static lcq_status build_near_impl(lcq_ctx* ctx, const lcq_surface* surf, int n_g
   CK(cudaStreamSynchronize(st));
   nr->nnz = tot[0];
   const int64_t rowp_total = tot[1];
-  int32_t* row_tmp;
   CK(dalloc(st, &nr->col, nr->nnz));
   CK(dalloc(st, &nr->rowp_patch, rowp_total));
   CK(dalloc(st, &nr->rowp_off, rowp_total));
@@ -533,10 +591,8 @@ static lcq_status build_near_impl(lcq_ctx* ctx, const lcq_surface* surf, int n_g
     acc_n += h_np[j] - h_nad[j];
   }
   an_h[P] = acc_n;
-  if (acc_p >= (int64_t)0x7fffffff) {
-    lcq_near_destroy(nr);
+  if (acc_p >= (int64_t)0x7fffffff)
     return fail(ctx, LCQ_ERR_CAPACITY, "more than 2^31-1 near pairs");
-  }
   // patches with adaptive targets, per degree, most adaptive targets first (the adaptive
   // kernel takes them in this order from a shared counter: longest jobs first)
   for (int d = 1; d <= kMaxDeg; ++d) {
@@ -561,7 +617,6 @@ static lcq_status build_near_impl(lcq_ctx* ctx, const lcq_surface* surf, int n_g
   nr->n_self = acc_s;
   nr->n_annulus = acc_n;
   CK(cudaMemcpyAsync(nr->an_ptr, an_h.data(), (P + 1) * 8, cudaMemcpyHostToDevice, st));
-  int32_t *ptmp, *stmp;
   CK(dalloc(st, &ptmp, nr->n_pairs));
   CK(dalloc(st, &stmp, nr->n_self));
   CK(dalloc(st, &nr->pair_tgt, nr->n_pairs));
@@ -595,6 +650,7 @@ static lcq_status build_near_impl(lcq_ctx* ctx, const lcq_surface* surf, int n_g
   dfree(st, nad);
   dfree(st, nself);
   dfree(st, scr);
+  undo.dismiss();
   *out = nr;
   return LCQ_OK;
 }
@@ -1138,6 +1194,10 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   c->params.n_test_dirs = 0;
   c->eps0 = eps0;
   c->precision = (int)precision;
+  auto undo = on_exit([&] { lcq_corr_destroy(c); });
+  // the generation's work buffers; gen_free releases them on every return
+  GenScratch gs;
+  auto gs_free = on_exit([&] { gen_free(st, &gs); });
   CK(dalloc(st, &c->val, (size_t)2 * std::max<int64_t>(nr->nnz, 1)));
   CK(dalloc(st, &c->q, P));
   CK(dalloc(st, &c->q_near, P));
@@ -1157,17 +1217,15 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
       dirs.push_back(z);
     }
   }
-  const int ndirs = (int)dirs.size() / 3;
-  double* ddirs;
-  CK(dalloc(st, &ddirs, dirs.size()));
-  CK(cudaMemcpyAsync(ddirs, dirs.data(), dirs.size() * 8, cudaMemcpyHostToDevice, st));
+  gs.ndirs = (int)dirs.size() / 3;
+  CK(dalloc(st, &gs.ddirs, dirs.size()));
+  CK(cudaMemcpyAsync(gs.ddirs, dirs.data(), dirs.size() * 8, cudaMemcpyHostToDevice, st));
 
   const int ldI = nr->n_max;
   const int64_t npr = std::max<int64_t>(nr->n_pairs, 1), nsf = std::max<int64_t>(nr->n_self, 1);
-  void *Is, *In, *InS;
-  CK(dalloc(st, reinterpret_cast<double**>(&Is), (size_t)2 * npr * ldI));
-  CK(dalloc(st, reinterpret_cast<double**>(&In), (size_t)2 * npr * ldI));
-  CK(dalloc(st, reinterpret_cast<double**>(&InS), (size_t)2 * nsf * ldI));
+  CK(dalloc(st, reinterpret_cast<double**>(&gs.Is), (size_t)2 * npr * ldI));
+  CK(dalloc(st, reinterpret_cast<double**>(&gs.In), (size_t)2 * npr * ldI));
+  CK(dalloc(st, reinterpret_cast<double**>(&gs.InS), (size_t)2 * nsf * ldI));
   if (nr->grouped) {
     std::vector<GroupParams> gp(n_phys);
     for (int g = 0; g < n_phys; ++g) {
@@ -1201,13 +1259,7 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   const int form = pair_form_mode(precision, kernel, nr, eps0);
   c->form = form;
   ctx->last_forms = forms_used(form, c->kp, c->grp_h);
-  GenScratch gs;
   gs.dv = dv;
-  gs.ddirs = ddirs;
-  gs.ndirs = ndirs;
-  gs.Is = Is;
-  gs.In = In;
-  gs.InS = InS;
   gs.form = form;
   gs.sorder = params->self_order > 0 ? params->self_order : default_self_order(eps0);
   lcq_status ls = gen_scratch(ctx, nr, kernel, eps0, params, true, &gs);
@@ -1219,6 +1271,7 @@ static lcq_status gen_impl(lcq_ctx* ctx, const lcq_near* nr, lcq_kernel kernel, 
   c->q_h.clear();
   c->src_off = nullptr;
   c->dirs_h = dirs;
+  undo.dismiss();
   *out = c;
   return LCQ_OK;
 }
@@ -1331,7 +1384,8 @@ static lcq_status apply_impl(lcq_ctx* ctx, const lcq_near* nr, const lcq_corr* c
   };
   bool fold = foldable(c->kp);
   for (const GroupParams& g : c->grp_h) fold = fold && foldable(g.kp);
-  double* src;
+  double* src = nullptr;
+  auto src_free = on_exit([&] { dfree(st, src); });
   CK(dalloc(st, &src, (size_t)(fold ? 10 : 9) * std::max<int64_t>(c->n_over, 1)));
   for (int d = 1; d <= kMaxDeg; ++d) {
     if (!nr->plist_count[d]) continue;
@@ -1343,7 +1397,6 @@ static lcq_status apply_impl(lcq_ctx* ctx, const lcq_near* nr, const lcq_corr* c
                  kind == LCQ_SP ? nr->tnrm : nullptr, out, fold);
   launch_csr_apply(lc, nr->row_ptr, nr->col, c->val, sigma, nr->tnode, nr->n_targets, jump, out);
   CK(cudaGetLastError());
-  dfree(st, src);
   return LCQ_OK;
 }
 
@@ -1418,10 +1471,13 @@ lcq_status lcq_apply_adjoint(lcq_ctx* ctx, const lcq_surface* surf, const lcq_ne
   long long nl = 0;
   LaunchCommon lc{st, ctx->num_sms, &nl};
   Dev dv = make_dev(ctx, nr, c->q, nr->n_max, c->grp);
-  double* src;
+  double *src = nullptr, *z = nullptr;
+  auto tmp_free = on_exit([&] {
+    dfree(st, src);
+    dfree(st, z);
+  });
   s = far_sources(ctx, nr, c, dv, lc, nullptr, &src);
   if (s != LCQ_OK) return s;
-  double* z;
   CK(dalloc(st, &z, (size_t)2 * std::max<int64_t>(c->n_over, 1)));
   launch_far_sum_T(lc, dv, nr->n_patches, src, c->n_over, c->src_off, c->kp,
                    c->grp ? nr->tgroup : nullptr, g, z);
@@ -1431,8 +1487,6 @@ lcq_status lcq_apply_adjoint(lcq_ctx* ctx, const lcq_surface* surf, const lcq_ne
                      c->val, g, jump, out);
   }
   CK(cudaGetLastError());
-  dfree(st, src);
-  dfree(st, z);
   return LCQ_OK;
 }
 
@@ -1456,7 +1510,18 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
   const int ldI = nr->n_max;
   Dev dv = make_dev(ctx, nr, c->q, ldI, c->grp);
   const int64_t N = nr->n_points, P = nr->n_patches;
-  double *shat, *M, *tg, *src;
+  double *shat = nullptr, *M = nullptr, *tg = nullptr, *src = nullptr, *Is = nullptr,
+         *In = nullptr;
+  int32_t* leaves = nullptr;
+  auto tmp_free = on_exit([&] {
+    dfree(st, shat);
+    dfree(st, M);
+    dfree(st, tg);
+    dfree(st, src);
+    dfree(st, Is);
+    dfree(st, In);
+    dfree(st, leaves);
+  });
   CK(dalloc(st, &shat, (size_t)2 * N));
   CK(dalloc(st, &M, (size_t)3 * N));
   CK(dalloc(st, &tg, (size_t)12 * std::max<int64_t>(c->n_over, 1)));
@@ -1483,8 +1548,6 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
     int agrid;
     CK(adaptive_work(ctx, nr, nr->max_adaptive, levels, &stride, &agrid));
     const int64_t npr = std::max<int64_t>(nr->n_pairs, 1);
-    double *Is, *In;
-    int32_t* leaves;
     CK(dalloc(st, &Is, (size_t)2 * npr * ldI));
     CK(dalloc(st, &In, (size_t)2 * npr * ldI));
     CK(dalloc(st, &leaves, npr));
@@ -1503,9 +1566,6 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
                            ctx->d_status, ctx->d_sched + d,
                            c->form, ga);
     }
-    dfree(st, Is);
-    dfree(st, In);
-    dfree(st, leaves);
   }
   // 4. dL/dy = V^T M per patch
   for (int d = 1; d <= kMaxDeg; ++d) {
@@ -1514,10 +1574,6 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
                     N, out);
   }
   CK(cudaGetLastError());
-  dfree(st, shat);
-  dfree(st, M);
-  dfree(st, tg);
-  dfree(st, src);
   return LCQ_OK;
 }
 
