@@ -23,7 +23,9 @@
  *    fixed near lists can be replayed without any (lcq_plan).  Errors found
  *    on the device (depth cap, capacity) are latched in a device status word and
  *    returned by lcq_sync() or the next call that synchronizes.
- *  - No call aborts, traps or throws across the ABI; every failure is a status.
+ *  - No call aborts, traps or throws across the ABI; every failure is a status.  A call
+ *    that fails part-way releases what it allocated: a creating call leaves its output
+ *    handle NULL, and no work buffer of the call stays behind.
  *  - Results are deterministic: fixed orderings, no floating-point atomics.
  */
 #ifndef LCQ_H
