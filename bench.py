@@ -71,7 +71,9 @@ def parse():
                     help="skip the 40,000-patch torus (k=20, eps=1e-9; FP64 and mixed, and the "
                          "direct-sum apply on a 100,000-point subset)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--s", type=int, default=8, help="icosahedral refinement (1280 patches at 8)")
+    ap.add_argument("--s", "--subdiv", dest="s", type=int, default=8,
+                    help="icosahedral refinement (1280 patches at 8); under torchrun spell it "
+                         "--subdiv (the launcher takes --s for one of its own options)")
     ap.add_argument("--leaf-order", type=int, default=0,
                     help="smooth rule used on subtriangles (0: the patch's far order q_j)")
     ap.add_argument("--eps", type=float, default=1e-9)
