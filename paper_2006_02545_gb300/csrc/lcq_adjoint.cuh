@@ -32,19 +32,22 @@ __global__ void k_shat(const int* __restrict__ plist, int count, const int64_t* 
 
 
 // Block per patch: M_j = far-rule part (from tg) + annulus pairs (rule q_near), written.
+// Each warp sums its nodes' contributions into its own row of `red` (warp sums in a fixed
+// order, no per-thread gradient row); the rows are added in warp order at the end.
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_grad_rules(
     const int* __restrict__ plist, int count, Dev dv, const KernelParams kp,
     const int32_t* __restrict__ qn, const int64_t* __restrict__ src_off, int64_t n_over,
     const double* __restrict__ tg, const cplx* __restrict__ g, const cplx* __restrict__ shat_g,
     double* __restrict__ M) {
-  constexpr int n = (D + 1) * (D + 2) / 2;
+  constexpr int n = (D + 1) * (D + 2) / 2, n3 = 3 * n, nwarps = kThreads / 32;
   __shared__ double cf[3 * n];
   __shared__ cplx shat[n];
   __shared__ SegMap segs[1];
   __shared__ KernelParams kps;
-  __shared__ double red[(kThreads / 32) * 3 * n];
-  double Mg[3 * n];
+  __shared__ double red[nwarps * n3];
+  double* Mw = red + (threadIdx.x >> 5) * n3;
+  const bool lead = (threadIdx.x & 31) == 0;
   for (int b = blockIdx.x; b < count; b += gridDim.x) {
     const int j = plist[b];
     const int64_t off = dv.node_off[j];
@@ -55,39 +58,47 @@ __global__ void __launch_bounds__(kThreads) k_grad_rules(
       segs[0] = seg_T0();
       kps = patch_kp(dv, j, kp);
     }
-    for (int e = threadIdx.x; e < 3 * n; e += blockDim.x) M[off * 3 + e] = 0.0;
-#pragma unroll
-    for (int e = 0; e < 3 * n; ++e) Mg[e] = 0.0;
+    for (int e = threadIdx.x; e < nwarps * n3; e += blockDim.x) red[e] = 0.0;
     __syncthreads();
-    // far rule q_j: node q of the rule is source src_off[j] + q
+    // far rule q_j: node q of the rule is source src_off[j] + q; every lane runs the same
+    // number of passes (zeros where q >= Q) so that the warp sums see all 32 lanes
     const int m = dv.q[j], Q = m * m;
     const double* ru = dv.ru + dv.roff[m];
     const double* rv = dv.rv + dv.roff[m];
     const double* rw = dv.rw + dv.roff[m];
-    for (int q = threadIdx.x; q < Q; q += blockDim.x) {
-      const double u = ru[q], v = rv[q], w = rw[q];
-      double X[3], Xu[3], Xv[3];
-      kw_geometry<D>(u, v, cf, X, Xu, Xv, nullptr, 1);
-      cplx sg = {0.0, 0.0};
-      kw_for_each<D>(u, v, [&](int idx, double k0, double, double) {
-        sg.re = fma(shat[idx].re, k0, sg.re);
-        sg.im = fma(shat[idx].im, k0, sg.im);
-      });
-      const int64_t o = src_off[j] + q;
-      double aX[3], aN[3];
+    for (int q0 = 0; q0 < Q; q0 += blockDim.x) {
+      const int q = q0 + threadIdx.x;
+      double u = 0.0, v = 0.0;
+      double X[3] = {0, 0, 0}, Xu[3] = {0, 0, 0}, Xv[3] = {0, 0, 0};
+      double aX[3] = {0, 0, 0}, aN[3] = {0, 0, 0};
+      if (q < Q) {
+        u = ru[q];
+        v = rv[q];
+        const double w = rw[q];
+        kw_geometry<D>(u, v, cf, X, Xu, Xv, nullptr, 1);
+        cplx sg = {0.0, 0.0};
+        kw_for_each<D>(u, v, [&](int idx, double k0, double, double) {
+          sg.re = fma(shat[idx].re, k0, sg.re);
+          sg.im = fma(shat[idx].im, k0, sg.im);
+        });
+        const int64_t o = src_off[j] + q;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const double xr = tg[(2 * k) * n_over + o], xi = tg[(2 * k + 1) * n_over + o];
-        const double nr = tg[(6 + 2 * k) * n_over + o], ni = tg[(6 + 2 * k + 1) * n_over + o];
-        aX[k] = sg.re * xr - sg.im * xi;
-        aN[k] = w * (sg.re * nr - sg.im * ni);
+        for (int k = 0; k < 3; ++k) {
+          const double xr = tg[(2 * k) * n_over + o], xi = tg[(2 * k + 1) * n_over + o];
+          const double nr = tg[(6 + 2 * k) * n_over + o], ni = tg[(6 + 2 * k + 1) * n_over + o];
+          aX[k] = sg.re * xr - sg.im * xi;
+          aN[k] = w * (sg.re * nr - sg.im * ni);
+        }
       }
       double bu[3], bv[3];
       cross3(Xv, aN, bu);
       cross3(aN, Xu, bv);
       kw_for_each<D>(u, v, [&](int idx, double k0, double ku, double kv) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) Mg[idx * 3 + k] += k0 * aX[k] + ku * bu[k] + kv * bv[k];
+        for (int k = 0; k < 3; ++k) {
+          const double s = warp_sum(k0 * aX[k] + ku * bu[k] + kv * bv[k]);
+          if (lead) Mw[idx * 3 + k] += s;
+        }
       });
     }
     // annulus pairs: one rule q_near on T0
@@ -96,15 +107,20 @@ __global__ void __launch_bounds__(kThreads) k_grad_rules(
     if (na > 0 && mn > 0) {
       const int32_t* pl = dv.an_pair + a0;
       TgtPairIdx ta{dv.tgt, dv.NT, dv.pair_tgt, pl, dv.tnrm};
-      block_grad<D>(cf, dv.ru + dv.roff[mn], dv.rv + dv.roff[mn], dv.rw + dv.roff[mn], mn * mn,
-                    segs, 1, ta, (int)na,
-                    [&](int i) -> cplx {
-                      const cplx c = g[dv.pair_tgt[pl[i]]];
-                      return {c.re, -c.im};
-                    },
-                    kps, shat, dv.cen + 3 * j, Mg);
+      block_grad<D, true>(cf, dv.ru + dv.roff[mn], dv.rv + dv.roff[mn], dv.rw + dv.roff[mn],
+                          mn * mn, segs, 1, ta, (int)na,
+                          [&](int i) -> cplx {
+                            const cplx c = g[dv.pair_tgt[pl[i]]];
+                            return {c.re, -c.im};
+                          },
+                          kps, shat, dv.cen + 3 * j, Mw);
     }
-    block_reduce_M<D>(Mg, red, M + off * 3);
+    __syncthreads();
+    for (int e = threadIdx.x; e < n3; e += blockDim.x) {
+      double acc = 0.0;
+      for (int wp = 0; wp < nwarps; ++wp) acc += red[wp * n3 + e];
+      M[off * 3 + e] = acc;
+    }
   }
 }
 

@@ -824,7 +824,9 @@ __device__ __forceinline__ SegMap seg_T0() { return {0.0, 0.0, 1.0, 0.0, 0.0, 1.
 //   a_X = Re(w sigma(u) sum_i wf(i) dK~/dX),  a_N = Re(w sigma(u) sum_i wf(i) dK~/dN),
 // where sigma(u) = sum_nm shat_nm K_nm(u) and N = X_u x X_v (so a_N.dN splits into the
 // two cross products).  Thread per node; targets staged through shared memory.
-template <int D, class TA, class WF>
+// WARP_ACC: M is instead this warp's row of per-warp sums in shared memory; every lane
+// takes part (zeros for lanes without a node) and lane 0 adds the warp's sum.
+template <int D, bool WARP_ACC = false, class TA, class WF>
 __device__ void block_grad(const double* cf, const double* __restrict__ ru,
                            const double* __restrict__ rv, const double* __restrict__ rw, int Q,
                            const SegMap* segs, int nseg, const TA& ta, int T, WF wf,
@@ -882,7 +884,7 @@ __device__ void block_grad(const double* cf, const double* __restrict__ ru,
           }
         }
     }
-    if (on) {
+    if (WARP_ACC || on) {
       double aX[3], aN[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -892,10 +894,21 @@ __device__ void block_grad(const double* cf, const double* __restrict__ ru,
       double bu[3], bv[3];
       cross3(Xv, aN, bu);
       cross3(aN, Xu, bv);
-      kw_for_each<D>(u, v, [&](int idx, double k0, double ku, double kv) {
+      if constexpr (WARP_ACC) {
+        const bool lead = (threadIdx.x & 31) == 0;
+        kw_for_each<D>(u, v, [&](int idx, double k0, double ku, double kv) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) M[idx * 3 + k] += k0 * aX[k] + ku * bu[k] + kv * bv[k];
-      });
+          for (int k = 0; k < 3; ++k) {
+            const double s = warp_sum(k0 * aX[k] + ku * bu[k] + kv * bv[k]);
+            if (lead) M[idx * 3 + k] += s;
+          }
+        });
+      } else {
+        kw_for_each<D>(u, v, [&](int idx, double k0, double ku, double kv) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) M[idx * 3 + k] += k0 * aX[k] + ku * bu[k] + kv * bv[k];
+        });
+      }
     }
   }
 }
