@@ -54,3 +54,18 @@ def test_params_and_status_strings(lcq):
 def test_bad_degree_rejected_on_host(lcq):
     with pytest.raises(lcq.LCQError):
         lcq.ref_nodes(11)
+
+
+def test_binding_refuses_to_load_without_the_library(tmp_path):
+    """Without liblcq.so the binding raises on import: there is no CPU fallback."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "pkg"
+    pkg.mkdir()
+    (pkg / "__init__.py").write_text("")
+    shutil.copy(os.path.join(ROOT, "paper_2006_02545_gb300", "lcq.py"), pkg / "lcq.py")
+    r = subprocess.run([sys.executable, "-c", "import pkg.lcq"], cwd=tmp_path,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "liblcq.so not built" in r.stderr
