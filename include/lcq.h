@@ -18,9 +18,10 @@
  *    owned by the library and released by the matching _destroy call.
  *  - Complex values are interleaved (re, im) doubles (complex128).
  *  - All device work is queued on the context's stream.  Calls that must size
- *    outputs synchronize that stream: lcq_build_near_lists four times (the grid box,
- *    the pair count, the per-patch sizes, the adaptive work lists); a generation on
- *    fixed near lists can be replayed without any (lcq_plan).  Errors found
+ *    outputs synchronize that stream: lcq_build_near_lists three times (the grid box,
+ *    followed by a read of the status word; the pair count; the per-patch sizes), plus
+ *    once more the first time a context meets a patch degree (its tables are uploaded);
+ *    a generation on fixed near lists can be replayed without any (lcq_plan).  Errors found
  *    on the device (depth cap, capacity) are latched in a device status word and
  *    returned by lcq_sync() or the next call that synchronizes.
  *  - No call aborts, traps or throws across the ABI; every failure is a status.  A call
