@@ -1,6 +1,7 @@
-"""The parameters and rules the paper states in its text (tests/golden/paper_parameters.txt,
-each value with its section) against the oracle, and against the library's host-side
-defaults and node tables where the library exposes them without a GPU."""
+"""The parameters and rules the paper states in its text or tables
+(tests/golden/paper_parameters.txt, each value with its section or table) against the
+oracle, the input generators, and the library's host-side defaults and node tables where
+the library exposes them without a GPU."""
 import ctypes as C
 import os
 
@@ -21,7 +22,7 @@ def load_golden():
             if not line or line.startswith("#"):
                 continue
             name, value, cite = line.split(None, 2)
-            assert cite.startswith("Sec. "), f"{name} has no citation"
+            assert cite.startswith(("Sec. ", "Table ")), f"{name} has no citation"
             out[name] = float(value)
     return out
 
@@ -40,7 +41,7 @@ def paper_eta(p):
 def test_golden_file_complete():
     assert set(G) == {"eta.p_le_4", "eta.p_le_8", "eta.p_gt_8", "eta1", "far_test.count",
                       "far_test.small_list", "far_test.sphere_pts", "subdivision.children",
-                      "nodes.p16"}
+                      "nodes.p16", "stellarator.a_avg"}
 
 
 @pytest.mark.parametrize("d", range(0, 13))
@@ -101,6 +102,15 @@ def test_nodes_per_patch():
     assert len(u) == len(v) == G["nodes.p16"]
     for d in range(1, 11):
         assert len(rules.interp_nodes(d)[0]) == (d + 1) * (d + 2) // 2
+
+
+def test_twisted_torus_aspect_ratio():
+    # the paper's twisted torus (Sec. 6) on the 20 x 60 cell grid: 2400 patches whose
+    # average aspect ratio (Sec. 6.1 definition) is Table 2's first column, to its digits
+    from paper_2006_02545_gb300 import workloads as W
+    s = W.stellarator(20, 60, 3)
+    assert s.n_patches == 2400
+    assert round(float(W.aspect_ratios(s).mean()), 2) == G["stellarator.a_avg"]
 
 
 @pytest.fixture(scope="module")
