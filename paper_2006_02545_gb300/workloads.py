@@ -444,6 +444,12 @@ def ellipsoid_adjoint_s_k5(s: int = 10):
     return surf, x
 
 
+# (n_u, n_v) cell grids of the twisted torus for the five columns of the paper's Table 2
+# (aspect-ratio sweep at about 2400 patches): 2 n_u n_v patches, average aspect ratios
+# 1.610, 2.333, 4.658, 9.314, 13.97 at degree 3 (printed: 1.61, 2.33, 4.66, 9.32, 14).
+TABLE2_GRIDS = ((20, 60), (24, 48), (35, 35), (48, 24), (60, 20))
+
+
 def stellarator_s_k1(deg: int = 3) -> Workload:
     """Single layer, k=1, on the paper's twisted torus with 2400 patches (20 x 60 cells,
     average aspect ratio 1.61 as in the paper's Table 2 first column); eps=5e-7."""

@@ -15,6 +15,7 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
 
 
 def load_golden():
+    """name -> (value, printed text of the value)"""
     out = {}
     with open(GOLDEN) as f:
         for line in f:
@@ -23,11 +24,12 @@ def load_golden():
                 continue
             name, value, cite = line.split(None, 2)
             assert cite.startswith(("Sec. ", "Table ")), f"{name} has no citation"
-            out[name] = float(value)
+            out[name] = (float(value), value)
     return out
 
 
-G = load_golden()
+G = {k: v for k, (v, _) in load_golden().items()}
+PRINTED = {k: t for k, (_, t) in load_golden().items()}
 
 
 def paper_eta(p):
@@ -41,7 +43,8 @@ def paper_eta(p):
 def test_golden_file_complete():
     assert set(G) == {"eta.p_le_4", "eta.p_le_8", "eta.p_gt_8", "eta1", "far_test.count",
                       "far_test.small_list", "far_test.sphere_pts", "subdivision.children",
-                      "nodes.p16", "stellarator.a_avg"}
+                      "nodes.p16"} | {f"table2.{q}.{c}" for q in ("npat", "a_avg")
+                                      for c in range(1, 6)}
 
 
 @pytest.mark.parametrize("d", range(0, 13))
@@ -104,13 +107,18 @@ def test_nodes_per_patch():
         assert len(rules.interp_nodes(d)[0]) == (d + 1) * (d + 2) // 2
 
 
-def test_twisted_torus_aspect_ratio():
-    # the paper's twisted torus (Sec. 6) on the 20 x 60 cell grid: 2400 patches whose
-    # average aspect ratio (Sec. 6.1 definition) is Table 2's first column, to its digits
+@pytest.mark.parametrize("col", range(1, 6))
+def test_twisted_torus_aspect_ratio_row_of_table2(col):
+    # the paper's twisted torus (Sec. 6) at p = 4 (degree 3) on the input generator's grid
+    # for column `col` of Table 2: its patch count, and its average aspect ratio (Sec. 6.1
+    # definition) within one unit of the last printed digit
     from paper_2006_02545_gb300 import workloads as W
-    s = W.stellarator(20, 60, 3)
-    assert s.n_patches == 2400
-    assert round(float(W.aspect_ratios(s).mean()), 2) == G["stellarator.a_avg"]
+    n_u, n_v = W.TABLE2_GRIDS[col - 1]
+    s = W.stellarator(n_u, n_v, 3)
+    assert s.n_patches == G[f"table2.npat.{col}"]
+    text = PRINTED[f"table2.a_avg.{col}"]
+    unit = 10.0 ** -(len(text.split(".")[1]) if "." in text else 0)
+    assert abs(float(W.aspect_ratios(s).mean()) - G[f"table2.a_avg.{col}"]) <= unit
 
 
 @pytest.fixture(scope="module")
