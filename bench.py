@@ -67,6 +67,9 @@ def parse():
                          "full batch)")
     ap.add_argument("--no-table1", action="store_true",
                     help="skip the twisted-torus sweep over order p and eps (the paper's Table 1)")
+    ap.add_argument("--no-table2", action="store_true",
+                    help="skip the twisted-torus sweep over the patches' aspect ratio (the "
+                         "paper's Table 2: p = 4, eps = 5e-7, five grids)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 40,000-patch torus (k=20, eps=1e-9; FP64 and mixed, and the "
                          "direct-sum apply on a 100,000-point subset)")
@@ -233,6 +236,44 @@ def traffic_for(kernel_name):
     except (OSError, ValueError):
         pass
     return None
+
+
+def table2_sweep(ctx, lcq, W, dev, stream, flush):
+    """The paper's Table 2 on its twisted torus: p = 4 (degree 3), S, k = 1, eps = 5e-7 on the
+    five grids of the aspect-ratio sweep; per column the patch count, the average aspect
+    ratio, alpha = N_over / N, m = nnz / N and S_init = N / T_init (the last of the tuner's
+    generations, one warm-up and one timed)."""
+    import torch
+    rows = []
+    for col, (n_u, n_v) in enumerate(W.TABLE2_GRIDS, start=1):
+        ts = W.stellarator(n_u, n_v, 3)
+        tx, ttn = W.onsurface_targets(ts)
+        tds = lcq.DeviceSurface(ts.deg, ts.node_off, torch.from_numpy(ts.xyz).to(dev))
+        tx_d = torch.from_numpy(tx).to(dev)
+        ttn_d = torch.from_numpy(ttn).to(dev)
+        tp = lcq.params(5e-7, test_dirs=W.test_directions(7))
+        ms = []
+        for _ in range(TUNING_GENERATIONS + 2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            near = lcq.build_near_lists(ctx, tds, tx_d, ttn_d, tp)
+            corr = lcq.gen_corrections(ctx, tds, near, "S", 1.0, tp)
+            e1.record(stream)
+            st = ctx.sync()
+            ms.append(e0.elapsed_time(e1))
+            t_stages = ctx.stage_times()[0]
+            nnz, n_over = corr.info()
+            corr.close()
+            near.close()
+        rows.append({"column": col, "grid": [n_u, n_v], "patches": ts.n_patches,
+                     "points": ts.n_points, "a_avg": float(W.aspect_ratios(ts).mean()),
+                     "alpha": n_over / ts.n_points, "m": nnz / ts.n_points,
+                     "S_init": ts.n_points / (ms[-1] / 1e3), "status": st,
+                     "stages_ms": [round(float(x), 3) for x in t_stages]})
+        del tds, tx_d, ttn_d
+    return rows
 
 
 def run_ours(args, rank, world, local_rank):
@@ -537,6 +578,15 @@ def run_ours(args, rank, world, local_rank):
                                "stages_ms": [round(float(x), 3) for x in t_stages]})
             del tds, tx_d1, ttn_d1
 
+    # the paper's Table 2 (performance against the patches' aspect ratio); a failure is
+    # recorded in the line rather than ending the run
+    table2 = None
+    if not args.no_variants and not args.no_table2:
+        try:
+            table2 = table2_sweep(ctx, lcq, W, dev, stream, flush)
+        except Exception as exc:  # noqa: BLE001
+            table2 = {"error": repr(exc)}
+
     # the 40,000-patch torus (k = 20, eps = 1e-9), FP64 and mixed, one timed step each; the
     # two CSRs are compared on the device; then the corrected potential at a 100,000-point
     # subset of the nodes (its own near lists and corrections, and the direct far sum over
@@ -701,6 +751,7 @@ def run_ours(args, rank, world, local_rank):
         "sphere20": small,
         "batched": batched,
         "table1": table1,
+        "table2": table2,
         "large": large,
         "wall_s_timed_region": t_wall,
     }
