@@ -107,6 +107,15 @@ def test_nodes_per_patch():
         assert len(rules.interp_nodes(d)[0]) == (d + 1) * (d + 2) // 2
 
 
+def test_aspect_ratio_closed_form():
+    # the chart A + u(B - A) + v(C - A) of an equilateral triangle has DX = [B - A, C - A]
+    # with singular values in the ratio sqrt(3) everywhere, so a_j = sqrt(3) exactly
+    # (Sec. 6.1 definition, sigma read as the singular values of DX)
+    from paper_2006_02545_gb300 import workloads as W
+    a = W.aspect_ratios(W.ellipsoid(2, 3, flat=True))   # flat icosahedron, 80 equilateral faces
+    assert len(a) == 80 and np.abs(a - np.sqrt(3.0)).max() < 1e-12
+
+
 @pytest.mark.parametrize("col", range(1, 6))
 def test_twisted_torus_aspect_ratio_row_of_table2(col):
     # the paper's twisted torus (Sec. 6) at p = 4 (degree 3) on the input generator's grid
