@@ -125,8 +125,15 @@ typedef struct {
 
 void lcq_params_default(lcq_params* p);
 
-/* Context on one CUDA device; stream may be NULL (legacy default stream) or a
- * cudaStream_t.  Allocates the device status word and per-device constants. */
+/* Context on one CUDA device (a library facility; the paper has no counterpart).
+ * cuda_stream may be NULL (legacy default stream) or a cudaStream_t that the caller owns
+ * and keeps alive while the context exists.  Allocates the device status word, the
+ * per-device constants and the smooth-rule tables; *out receives the context.
+ * Errors: LCQ_ERR_ARG (out NULL, device out of range), LCQ_ERR_CUDA, LCQ_ERR_OOM,
+ * LCQ_ERR_TABLES; *out stays NULL.
+ * lcq_destroy synchronizes the stream and frees everything the context allocated; the
+ * near lists, corrections and plans made with it must be destroyed first.  NULL is a
+ * no-op. */
 lcq_status lcq_create(lcq_ctx** out, int device, void* cuda_stream);
 void lcq_destroy(lcq_ctx* ctx);
 
@@ -145,21 +152,29 @@ lcq_status lcq_build_near_lists(lcq_ctx* ctx, const lcq_surface* surf, const dou
                                 const int64_t* tgt_node, int64_t n_targets,
                                 const lcq_params* params, lcq_near** out);
 
-/* Sizes of a near-list object: near pairs, self pairs, adaptive pairs, CSR nnz. */
+/* Sizes of the near lists of Sec. 4 held by a near-list object: near pairs, self pairs,
+ * adaptive pairs (inside N_eta1) and CSR entries, each to a host int64 (NULL skips it).
+ * Host only, no synchronization.  LCQ_ERR_ARG for a NULL object. */
 lcq_status lcq_near_info(const lcq_near* near, int64_t* n_pairs, int64_t* n_self,
                          int64_t* n_adaptive, int64_t* nnz);
 
-/* Patch-major near lists to host: pair_ptr[n_patches+1], tgt[n_pairs] (ascending
- * per patch), adaptive[n_pairs] (0/1); per-patch centroid c[3*n_patches] and
- * radius R[n_patches].  Any pointer may be NULL to skip it. */
+/* Patch-major near lists N_eta(Gamma_j) of Sec. 4 to caller-owned host arrays:
+ * pair_ptr[n_patches+1], tgt[n_pairs] (ascending per patch), adaptive[n_pairs] (0/1);
+ * per-patch centroid c_j [3*n_patches] and radius R_j [n_patches] (Sec. 4, Eq. rjdef).
+ * Any pointer may be NULL to skip it.  Synchronizes the stream; LCQ_ERR_ARG for a NULL
+ * object, LCQ_ERR_CUDA if a copy fails. */
 lcq_status lcq_near_export(lcq_near* near, int64_t* pair_ptr, int32_t* tgt, uint8_t* adaptive,
                            double* centroid, double* radius);
 
-/* Normals of the targets for LCQ_SP: device double SoA [3][NT] (copied; only the
- * off-surface targets' columns are used, normalized by the library).  Required before an
- * S' generation when the near lists have off-surface targets. */
+/* Normals n(x) of the targets for LCQ_SP (Sec. 3, S' = n(x) . grad_x S): device double
+ * SoA [3][NT], copied (the caller keeps its buffer); only the off-surface targets'
+ * columns are used, normalized by the library.  Required before an S' generation when the
+ * near lists have off-surface targets.  LCQ_ERR_ARG for NULL arguments, LCQ_ERR_CUDA or
+ * LCQ_ERR_OOM if the copy fails. */
 lcq_status lcq_near_set_target_normals(lcq_near* near, const double* tgt_normal);
 
+/* Frees a near-list object (stream-ordered; a library facility with no counterpart in
+ * the paper); corrections made from it must be destroyed first.  NULL is a no-op. */
 void lcq_near_destroy(lcq_near* near);
 
 /* Net corrections (Sec. 4.2-4.3, 5.2-5.3), stored as a target-major CSR matrix: for
@@ -200,8 +215,9 @@ typedef struct {
   double eps;
 } lcq_surface_physics;
 
-/* lcq_gen_corrections over near lists built by lcq_build_near_lists_batched, with
- * physics[s] (host [n_surfaces]) for surface s.  One launch per stage and patch
+/* lcq_gen_corrections (Sec. 4.2-4.3, 5.2-5.3, per surface; the batch is an extension)
+ * over near lists built by lcq_build_near_lists_batched, with physics[s] (host
+ * [n_surfaces]) for surface s.  One launch per stage and patch
  * degree covers every surface.  The CSR and the apply functions work on the whole
  * batch: the far sum of a target runs over its own surface's sources with that
  * surface's kernel. */
@@ -213,14 +229,18 @@ lcq_status lcq_gen_corrections_batched(lcq_ctx* ctx, const lcq_surface* surf, co
 /* nnz of the CSR, N_over = sum_j n_{q_j} (Sec. 5.2), value dtype (0 = complex128). */
 lcq_status lcq_corr_info(const lcq_corr* corr, int64_t* nnz, int64_t* n_over, int* value_dtype);
 
-/* CSR out of the library: row_ptr[NT+1], col[nnz] (global node ids), val[2*nnz]
- * (complex128), each into host or device memory of the context's device (copied with
- * unified addressing).  Synchronizes the stream.  Any pointer may be NULL. */
+/* The correction matrix of Sec. 5.3 (the near and self corrections, CSR by target) out
+ * of the library: row_ptr[NT+1], col[nnz] (global node ids), val[2*nnz] (complex128),
+ * each into caller-owned host or device memory of the context's device (copied with
+ * unified addressing).  Synchronizes the stream.  Any pointer may be NULL.  LCQ_ERR_ARG
+ * for a NULL object, LCQ_ERR_CUDA if a copy fails. */
 lcq_status lcq_corr_export(lcq_corr* corr, int64_t* row_ptr, int32_t* col, double* val);
 
-/* Per-patch far order q_j and annulus order (0: no annulus targets) to host
- * [n_patches]; per-near-pair number of accepted leaf triangles (0 for annulus
- * pairs) to host [n_pairs] in patch-major order.  Any pointer may be NULL. */
+/* Per-patch far order q_j (Sec. 4.2, Eq. qj) and annulus order (0: no annulus targets)
+ * to caller-owned host [n_patches]; per-near-pair number of accepted leaf triangles of the
+ * adaptive integration (Sec. 4.3; 0 for annulus pairs) to host [n_pairs] in patch-major
+ * order.  Any pointer may be NULL.  Synchronizes the stream; LCQ_ERR_ARG for a NULL
+ * object, LCQ_ERR_CUDA if a copy fails. */
 lcq_status lcq_corr_export_stats(lcq_corr* corr, int32_t* q, int32_t* q_near, int32_t* leaves);
 
 /* Corrected layer potential (Sec. 5.3, subtract-and-add with a direct far sum; the
@@ -266,13 +286,16 @@ lcq_status lcq_shape_gradient(lcq_ctx* ctx, const lcq_surface* surf, const lcq_n
                               const lcq_corr* corr, const double* sigma, const double* g,
                               double* out);
 
-/* lcq_apply_corrected_S/D/CFIE/Sp by kernel, for a density in either precision:
+/* The corrected potential of Sec. 5.3 as lcq_apply_corrected_S/D/CFIE/Sp, chosen by
+ * kernel, for a density in either precision:
  * sigma_dtype 0 = complex128, 1 = complex64 (widened to complex128 on the device before
  * the FP64 sums).  out is complex128 [NT].  The kernel must match the corrections'. */
 lcq_status lcq_apply_corrected(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near* near,
                                const lcq_corr* corr, lcq_kernel kernel, const void* sigma,
                                int sigma_dtype, double jump, double* out);
 
+/* Frees a correction object (stream-ordered; a library facility with no counterpart in
+ * the paper); plans made on it must be destroyed first.  NULL is a no-op. */
 void lcq_corr_destroy(lcq_corr* corr);
 
 /* Captured regeneration (an extension: the paper has no counterpart).  lcq_plan_create
@@ -296,11 +319,18 @@ lcq_status lcq_plan_create(lcq_ctx* ctx, const lcq_surface* surf, const lcq_near
 lcq_status lcq_plan_launch(lcq_plan* plan);
 void lcq_plan_destroy(lcq_plan* plan);
 
-/* Wait for the context's stream (polling, at most timeout_ms; < 0 waits
- * without limit), then return and clear the latched device status. */
+/* Wait for the context's stream (a library facility; the paper has no counterpart):
+ * polling, at most timeout_ms (< 0 waits without limit), then return and clear the
+ * latched device status: LCQ_ERR_NONFINITE, LCQ_ERR_DEGENERATE_PATCH, LCQ_ERR_CAPACITY or
+ * LCQ_ERR_MAX_DEPTH (results kept) as the device reported them, else LCQ_OK.  A wait that
+ * runs out returns LCQ_ERR_TIMEOUT and leaves the work in flight and the status word
+ * untouched, so a later call completes it.  LCQ_ERR_ARG for a NULL context, LCQ_ERR_CUDA
+ * if the stream reports an error. */
 lcq_status lcq_sync(lcq_ctx* ctx, int64_t timeout_ms);
 
-/* Device-side work counters of the last lcq_gen_corrections on ctx (host out8[8]):
+/* Device-side work counters of the last lcq_gen_corrections on ctx (a measurement
+ * facility with no counterpart in the paper; [1] is the evaluation count behind the
+ * adaptive kernel's algorithmic FLOP rate), to caller-owned host out8[8]:
  * [0] adaptive tests, [1] adaptive leaf-rule node evaluations (target x node),
  * [2] self node evaluations, [3] smooth/annulus node evaluations (target x node),
  * [4] union-tree nodes walked by the adaptive kernel (each evaluates the chart geometry
@@ -316,8 +346,9 @@ lcq_status lcq_sync(lcq_ctx* ctx, int64_t timeout_ms);
  * size. */
 lcq_status lcq_counters(lcq_ctx* ctx, int64_t* out8);
 
-/* Stage timings of the last lcq_build_near_lists and lcq_gen_corrections on ctx, from
- * CUDA events recorded on the streams that run them (host out, milliseconds):
+/* Stage timings of the last lcq_build_near_lists and lcq_gen_corrections on ctx (a
+ * measurement facility with no counterpart in the paper), from CUDA events recorded on the
+ * streams that run them, to caller-owned host ms6[6] (milliseconds; NULL skips them):
  *   ms[0] near lists (geometry + both orientations)   ms[1] far order q_j
  *   ms[2] smooth-rule and annulus moments              ms[3] adaptive near moments
  *   ms[4] self weights (on an internal low-priority stream, concurrently with ms[1]-ms[3];

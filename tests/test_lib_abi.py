@@ -69,3 +69,19 @@ def test_binding_refuses_to_load_without_the_library(tmp_path):
                        capture_output=True, text=True, timeout=120)
     assert r.returncode != 0
     assert "ImportError" in r.stderr and "liblcq.so not built" in r.stderr
+
+
+def test_every_declaration_cites_its_passage_or_says_it_has_none():
+    """Each entry point's comment in include/lcq.h names the paper's passage (section,
+    equation or table) or states that the paper has no counterpart."""
+    with open(os.path.join(ROOT, "include", "lcq.h")) as f:
+        text = f.read()
+    decls = list(re.finditer(r"^(?:const char\*|void|lcq_status)\s+(lcq_[A-Za-z0-9_]+)\s*\(",
+                             text, re.M))
+    assert len(decls) >= 30
+    for m in decls:
+        before = text[:m.start()]
+        end = before.rfind("*/")
+        comment = before[before.rfind("/*", 0, end):end]
+        assert re.search(r"Sec\.|Eq\.|Table|counterpart|extension|library facility", comment), \
+            m.group(1)
