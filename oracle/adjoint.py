@@ -32,7 +32,8 @@ FOUR_PI = 4.0 * np.pi
 
 
 def kernel_jac_grad(x, X, N, k, kind: str, alpha=1.0, beta=0.0):
-    """Derivatives of kernels.kernel_jac with respect to the source position X and the
+    """Derivatives of kernels.kernel_jac (the Sec. 3 kernels; the gradient itself has no
+    counterpart in the paper) with respect to the source position X and the
     unnormalized normal N: (dX [3,P], dN [3,P]), complex.  With r = |x - X|:
       S~ = G(r) |N|, G = e^{ikr}/(4 pi r):
           dS~/dX = G (ik - 1/r) |N| (X - x)/r,      dS~/dN = G N/|N|
@@ -71,7 +72,8 @@ def kernel_jac_grad(x, X, N, k, kind: str, alpha=1.0, beta=0.0):
 
 
 def apply_adjoint(corr, node_off, g, tgt_xyz, kind, k, alpha=1.0, beta=0.0):
-    """A^H g for the corrected potential of corrections.apply_corrected.
+    """A^H g for the corrected potential of corrections.apply_corrected (the adjoint of the
+    Sec. 5.3 apply; no counterpart in the paper).
 
     Far part: u_t = sum_{q, patch(q) != own(t)} K~(x_t, X_q) (B_j sigma_j)_q with the real
     matrix B_j = diag(w) K^T V (interpolation to the rule q_j times its weights), so
@@ -95,7 +97,8 @@ def apply_adjoint(corr, node_off, g, tgt_xyz, kind, k, alpha=1.0, beta=0.0):
 
 
 def _rule_grad(pt, s_hat, ru, rv, rw, targets, tgt_xyz, g, k, kind, alpha, beta):
-    """sum over the rule's nodes and the targets of dL/dx_nm (x the chart coefficients):
+    """sum over the rule's nodes and the targets of dL/dx_nm (x the chart coefficients of
+    Sec. 3.2; one rule of Sec. 4.2-4.3 with the rule frozen):
     per node a_X = Re(sum_t conj(g_t) w sigma(u) dK~/dX), a_N likewise with dK~/dN; since
     dN = dX_u x X_v + X_u x dX_v, a_N.dN = dX_u.(X_v x a_N) + dX_v.(a_N x X_u), so
         dL/dx_nm = sum_nodes K_nm a_X + dK_nm/du (X_v x a_N) + dK_nm/dv (a_N x X_u)."""
@@ -118,7 +121,8 @@ def _rule_grad(pt, s_hat, ru, rv, rw, targets, tgt_xyz, g, k, kind, alpha, beta)
 def shape_gradient(deg, node_off, xyz, tgt_xyz, tgt_node, kind, k, alpha, beta, params, sigma,
                    g):
     """dL/dy [3, N] for dL = Re sum_t conj(g_t) du_t at off-surface targets, with the
-    discrete choices of gen_corrections frozen (module docstring).  Returns (grad, corr)."""
+    discrete choices of gen_corrections (Sec. 4.2-4.3) frozen (module docstring; no
+    counterpart in the paper).  Returns (grad, corr)."""
     tgt_node = np.asarray(tgt_node)
     if (tgt_node >= 0).any():
         raise ValueError("shape gradient: off-surface targets only")

@@ -31,6 +31,8 @@ from .quadrature import Kern
 
 @dataclass
 class Params:
+    """Parameters of the generation (Sec. 4.1-4.3): tolerance, near-field cutoffs eta and
+    eta_1, the termination loosening, depth cap, rule orders and test directions."""
     eps: float
     eta: float = -1.0            # <= 0: default by degree (Sec. 4.1)
     eta1: float = 1.25           # Remark on eta_1
@@ -44,7 +46,10 @@ class Params:
 
 
 def fibonacci_dirs(n: int = 15) -> np.ndarray:
-    """Default test directions: z_k = 1 - (2k+1)/n, azimuth k pi (3 - sqrt 5)."""
+    """Default test directions for the points on the sphere of radius eta R_j that the far
+    test set of Sec. 4.2 adds when a near list is short (the paper draws 15 at random; a
+    fixed set lets both implementations see the same points): z_k = 1 - (2k+1)/n, azimuth
+    k pi (3 - sqrt 5)."""
     k = np.arange(n, dtype=np.float64)
     z = 1.0 - (2.0 * k + 1.0) / n
     r = np.sqrt(1.0 - z * z)
@@ -54,6 +59,8 @@ def fibonacci_dirs(n: int = 15) -> np.ndarray:
 
 @dataclass
 class Corrections:
+    """The corrections of Sec. 5.3 as a CSR by target (row_ptr, col, val), with the far and
+    annulus orders of Sec. 4.2-4.3, the cutoffs and near lists used and per-pair records."""
     row_ptr: np.ndarray
     col: np.ndarray
     val: np.ndarray
@@ -70,8 +77,8 @@ class Corrections:
 
 
 class LazyPatches:
-    """Patches built on first use (for runs restricted to a few patches of a large
-    surface)."""
+    """Patches (Sec. 3.2, Sec. 4 geometry) built on first use, for runs restricted to a few
+    patches of a large surface."""
 
     def __init__(self, deg, node_off, xyz):
         self.deg, self.node_off, self.xyz = deg, node_off, xyz
@@ -88,6 +95,8 @@ class LazyPatches:
 
 
 def patch_of_node(node_off, tgt_node):
+    """Own patch of each target (-1 off the surface): the patch whose nodes hold the
+    target's node id, which makes the pair a self pair (Sec. 4, Sec. 5.2)."""
     tp = np.full(tgt_node.shape, -1, dtype=np.int64)
     on = tgt_node >= 0
     tp[on] = np.searchsorted(node_off, tgt_node[on], side="right") - 1
@@ -95,7 +104,7 @@ def patch_of_node(node_off, tgt_node):
 
 
 def target_normals(patches, node_off, tgt_node, tgt_normal):
-    """Unit target normals for S': the chart normal at the node for an on-surface target
+    """Unit target normals n(x) for S' (Sec. 3): the chart normal at the node for an on-surface target
     (so that n_x.(x - y) vanishes to second order on its own patch), the caller's
     tgt_normal [3, NT] (normalized) for an off-surface target."""
     tgt_node = np.asarray(tgt_node)
@@ -114,9 +123,11 @@ def target_normals(patches, node_off, tgt_node, tgt_normal):
 
 def gen_corrections(deg, node_off, xyz, tgt_xyz, tgt_node, kind, k, alpha=1.0, beta=0.0,
                     params: Params = None, patches=None, only_patches=None, tgt_normal=None):
-    """All corrections for the targets; `only_patches` restricts the work to some patches
-    (rows then hold only those patches' entries).  kind "Sp" (S') uses target normals
-    (target_normals)."""
+    """All corrections for the targets, in the order of Sec. 4.2-4.3 and 5.2: geometry,
+    near lists, far order q_j (Eq. qj), then per near pair the adaptive or annulus moments
+    and per self pair the self weights, each contracted with V and stored net of the smooth
+    rule's weights.  `only_patches` restricts the work to some patches (rows then hold only
+    those patches' entries).  kind "Sp" (S') uses target normals (target_normals)."""
     p = params
     kern = Kern(kind, k, alpha, beta)
     deg = np.asarray(deg)

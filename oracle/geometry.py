@@ -27,6 +27,8 @@ from . import rules
 
 @dataclass
 class Patch:
+    """One patch's chart (Sec. 3.2) and the quantities of Sec. 4 built from it: V, ||V||,
+    node weights and Jacobians, centroid c_j, radius R_j and d_j."""
     d: int
     y: np.ndarray          # [3, n] node coordinates
     coefs: np.ndarray      # [n, 3] Koornwinder coefficients x_nm
@@ -41,17 +43,21 @@ class Patch:
 
     @property
     def n(self) -> int:
+        """Nodes of the patch, n = (d+1)(d+2)/2 (Sec. 2.1)."""
         return kw.n_basis(self.d)
 
     def eval(self, u, v):
-        """X, n = X_u x X_v at reference points; returns (X [3,P], N [3,P], K [n,P])."""
+        """The chart X(u, v) = sum x_nm K_nm(u, v) and its normal N = X_u x X_v (Sec. 3.1-3.2)
+        at reference points; returns (X [3,P], N [3,P], K [n,P])."""
         return self._eval(self.coefs, u, v)
 
     def eval_rel(self, u, v):
-        """As eval, with X measured from the centroid: X - c_j (series with shifted x_00)."""
+        """As eval (Sec. 3.2), with X measured from the centroid c_j of Sec. 4: X - c_j
+        (the series with shifted x_00)."""
         return self._eval(self.coefs_rel, u, v)
 
     def _eval(self, coefs, u, v):
+        """Chart series sum coefs_nm K_nm and its u, v derivatives (Sec. 3.2)."""
         K, Ku, Kv = kw.basis(self.d, u, v, derivs=True)
         X = coefs.T @ K
         Xu = coefs.T @ Ku
@@ -64,6 +70,8 @@ _TABLES: dict = {}
 
 
 def tables(d: int):
+    """Per degree: V = U^{-1} (Eq. v2c), ||V||_2 (the scale of Eq. qj), the node weights and
+    the nodes (Sec. 2.1-2.2)."""
     if d not in _TABLES:
         V = rules.vals_to_coefs(d)
         _TABLES[d] = (V, float(np.linalg.norm(V, 2)), rules.interp_weights(d), rules.interp_nodes(d))
@@ -71,12 +79,18 @@ def tables(d: int):
 
 
 def sample_points_level4():
+    """The 153 vertices of the level-4 uniform subdivision of T0, the sample over which the
+    radius R_j of Sec. 4 (Eq. rjdef) is taken (the paper does not say how R_j is found)."""
     a, b = np.meshgrid(np.arange(17), np.arange(17), indexing="ij")
     keep = (a + b) <= 16
     return a[keep] / 16.0, b[keep] / 16.0
 
 
 def make_patch(d: int, y: np.ndarray) -> Patch:
+    """One patch from its node coordinates y [3, n]: chart coefficients x_nm = V y (Sec. 3.2,
+    Eq. v2c), Jacobian at the nodes, the area-weighted centroid c_j and radius R_j of Sec. 4
+    (printed garbled: the centroid is read as sum w J y / sum w J), and d_j = min sqrt(J w)
+    of Sec. 4.2."""
     V, nV, w, (un, vn) = tables(d)
     coefs = V @ y.T
     K, Ku, Kv = kw.basis(d, un, vn, derivs=True)
@@ -97,6 +111,7 @@ def make_patch(d: int, y: np.ndarray) -> Patch:
 
 
 def make_patches(deg, node_off, xyz):
+    """make_patch (Sec. 3.2, Sec. 4) for every patch of a surface."""
     return [make_patch(int(deg[j]), xyz[:, node_off[j]:node_off[j + 1]]) for j in range(len(deg))]
 
 

@@ -18,7 +18,9 @@ FOUR_PI = 4.0 * np.pi
 
 
 def kernel_jac(x, X, N, k, kind: str, alpha=1.0, beta=0.0, nx=None):
-    """Kernel values times J at sources X [3,P] with normals N [3,P] for target x [3].
+    """Kernel values times J at sources X [3,P] with normals N [3,P] for target x [3]:
+    G_k = e^{ikr}/(4 pi r) for S, n(y) . grad_y G_k for D, alpha D + beta S for the CFIE,
+    and n(x) . grad_x G_k for S' (Sec. 3, the single- and double-layer definitions).
 
     kind: "S", "D", "CFIE" (alpha D + beta S) or "Sp" (S', needs the target's unit
     normal nx [3]).  Returns complex [P].
@@ -45,8 +47,8 @@ def kernel_jac(x, X, N, k, kind: str, alpha=1.0, beta=0.0, nx=None):
 
 
 def kernel_envelope(x, X, N, k, kind: str, alpha=1.0, beta=0.0, R=1.0, nx=None):
-    """Rounding envelope of kernel_jac at each source (a reading; the paper is silent on
-    finite precision): |G| J (b + a |1 - ik r| R / r^2), with b = 1, 0, |beta|, 0 and
+    """Rounding envelope of kernel_jac at each source, which sets the floor of the adaptive
+    test of Sec. 4.3 (a reading; the paper is silent on finite precision): |G| J (b + a |1 - ik r| R / r^2), with b = 1, 0, |beta|, 0 and
     a = 0, 1, |alpha|, 1 for S, D, CFIE, S' (the target-normal factor of S' rounds like the
     source-normal factor of D).  The double-layer term is the size of
     |n| |delta(x - X)| / r^2 for a coordinate rounding error delta ~ u R (charts and

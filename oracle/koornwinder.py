@@ -21,19 +21,26 @@ from scipy.special import eval_jacobi
 
 
 def n_basis(d: int) -> int:
+    """Number of Koornwinder polynomials of total degree <= d: the paper's n_p = p(p+1)/2
+    with p = d + 1 (Sec. 2.1)."""
     return (d + 1) * (d + 2) // 2
 
 
 def index(n: int, m: int) -> int:
+    """Position of K_nm in the basis, n-major with m ascending (Sec. 2.1 indexes the
+    basis by (n, m) without fixing an order; this one is used throughout)."""
     return n * (n + 1) // 2 + m
 
 
 def c_nm(n: int, m: int) -> float:
+    """Normalization of K_nm (Sec. 2.1 leaves it to the cited basis): sqrt(2(2m+1)(n+1)),
+    the constant that makes the integral of K_nm^2 over T0 equal to 1."""
     return float(np.sqrt(2.0 * (2 * m + 1) * (n + 1)))
 
 
 def scaled_legendre(mmax: int, u, v):
-    """L_m = (1-v)^m P_m((2u+v-1)/(1-v)) for m = 0..mmax with d/du and d/dv.
+    """L_m = (1-v)^m P_m((2u+v-1)/(1-v)) for m = 0..mmax with d/du and d/dv: the Legendre
+    factor of the Koornwinder polynomials of Sec. 2.1.
 
     Legendre: (m+1) P_{m+1}(x) = (2m+1) x P_m(x) - m P_{m-1}(x); with s = 2u+v-1 and
     q = 1-v this becomes (m+1) L_{m+1} = (2m+1) s L_m - m q^2 L_{m-1}.
@@ -54,7 +61,8 @@ def scaled_legendre(mmax: int, u, v):
 
 
 def basis(d: int, u, v, derivs: bool = False):
-    """K[nm, point] for all 0 <= m <= n <= d; with derivs also dK/du and dK/dv."""
+    """K[nm, point] for all 0 <= m <= n <= d (the Koornwinder basis of Sec. 2.1,
+    K_nm = c_nm L_m P^{(0,2m+1)}_{n-m}(1-2v)); with derivs also dK/du and dK/dv."""
     u = np.atleast_1d(np.asarray(u, dtype=np.float64))
     v = np.atleast_1d(np.asarray(v, dtype=np.float64))
     L, Lu, Lv = scaled_legendre(d, u, v)
@@ -80,7 +88,8 @@ def basis(d: int, u, v, derivs: bool = False):
 
 
 def jacobi_recurrence(a: int, b: int):
-    """P^{(0,b)}_{a+1}(y) = (c1 y + c0) P_a(y) - c2 P_{a-1}(y) (standard three-term recurrence)."""
+    """P^{(0,b)}_{a+1}(y) = (c1 y + c0) P_a(y) - c2 P_{a-1}(y): the textbook three-term
+    recurrence of the Jacobi factor of the Sec. 2.1 basis."""
     den = 2.0 * (a + 1) * (a + b + 1) * (2 * a + b)
     c1 = (2 * a + b + 1) * (2 * a + b + 2) * (2 * a + b) / den
     c0 = -(2 * a + b + 1) * b * b / den
@@ -89,7 +98,8 @@ def jacobi_recurrence(a: int, b: int):
 
 
 def basis_delta(d: int, P, du, dv):
-    """K_nm(P + delta) - K_nm(P) for offsets delta = (du, dv), computed without forming
+    """K_nm(P + delta) - K_nm(P) (the Sec. 2.1 basis) for offsets delta = (du, dv), as the
+    self rules of Sec. 4 need them near the target node, computed without forming
     the two values: the differences obey the same recurrences, e.g. for the scaled
     Legendre factor
         (m) dL_m = (2m-1)(s_Q dL_{m-1} + ds L_{m-1}(P)) - (m-1)(q_Q^2 dL_{m-2} + d(q^2) L_{m-2}(P)),

@@ -11,7 +11,8 @@ import numpy as np
 
 
 def near_lists(centers, radii, eta, eta1, tgt_xyz, tgt_patch, only=None):
-    """Per patch: (ascending target ids, adaptive flags, squared distances).  With `only`,
+    """The near lists N_eta(Gamma_j) of Sec. 4 with the N_eta1 flag of the Sec. 4.3 remark.
+    Per patch: (ascending target ids, adaptive flags, squared distances).  With `only`,
     the lists of the other patches are left empty (their centers and radii are unused)."""
     out = []
     keep = None if only is None else set(int(j) for j in only)
@@ -37,7 +38,9 @@ def far_test_targets(ids, d2):
 
 
 def annulus_test_targets(ids, adaptive, d2, count=10):
-    """The `count` nearest annulus targets (reading for the annulus rule order), ties by id."""
+    """The `count` nearest annulus targets, ties by id: test points for the order of the
+    single rule the Sec. 4.3 remark uses between N_eta1 and N_eta (an order it leaves
+    unstated; chosen like q_j of Sec. 4.2)."""
     sel = ~adaptive
     a_ids, a_d2 = ids[sel], d2[sel]
     order = np.lexsort((a_ids, a_d2))

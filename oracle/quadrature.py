@@ -16,6 +16,8 @@ from .kernels import kernel_envelope, kernel_jac
 
 
 class Kern:
+    """A kernel of Sec. 3 (S, D, CFIE or S') with its wavenumber and CFIE coefficients."""
+
     def __init__(self, kind, k, alpha=1.0, beta=0.0):
         self.kind, self.k, self.alpha, self.beta = kind, complex(k), complex(alpha), complex(beta)
 
@@ -27,7 +29,7 @@ class Kern:
 
 
 def rule_moments(patch, x, ru, rv, rw, kern, nx=None):
-    """I_nm(x) by one rule (u_q, v_q, w_q) on T0: sum_q w_q K(x, X_q) J_q K_nm(u_q, v_q).
+    """I_nm(x) of Sec. 4.2 by one rule (u_q, v_q, w_q) on T0: sum_q w_q K(x, X_q) J_q K_nm(u_q, v_q).
     Positions are taken relative to the patch centroid (x - c_j against X - c_j); nx is
     the target normal of S'."""
     X, N, K = patch.eval_rel(ru, rv)
@@ -35,8 +37,8 @@ def rule_moments(patch, x, ru, rv, rw, kern, nx=None):
 
 
 def radial_normal(patch, x):
-    """Target normal given to S' at a far-order test point: the unit vector from c_j to x
-    (a reading: the paper's test points carry no normal)."""
+    """Target normal given to S' (Sec. 3) at a far-order test point of Sec. 4.2: the unit
+    vector from c_j to x (a reading: the paper's test points carry no normal)."""
     d = np.asarray(x, dtype=np.float64) - patch.c
     r = np.linalg.norm(d)
     return d / r if r > 0.0 else np.array([0.0, 0.0, 1.0])
@@ -74,7 +76,9 @@ def smooth_weights(patch, x, m, kern, nx=None):
 
 
 def conformal_map(patch, i):
-    """M = G^{-1/2}, G = DX^T DX at node i (first fundamental form), by eigendecomposition."""
+    """M = G^{-1/2}, G = DX^T DX at node i (first fundamental form), by eigendecomposition:
+    the change of variables that makes the chart conformal at the node, used by the self
+    rules of Sec. 4 (whose printed tables are not available)."""
     un, vn = rules.interp_nodes(patch.d)
     _, Ku, Kv = kw.basis(patch.d, un[i:i + 1], vn[i:i + 1], derivs=True)
     A = np.stack([patch.coefs.T @ Ku[:, 0], patch.coefs.T @ Kv[:, 0]], axis=1)
@@ -83,7 +87,8 @@ def conformal_map(patch, i):
 
 
 def node_normal(patch, i):
-    """Unit normal of the chart at node i (the target normal of S' for on-surface targets)."""
+    """Unit normal of the chart at node i (Sec. 3.2; the target normal of S', Sec. 3, for
+    on-surface targets)."""
     un, vn = rules.interp_nodes(patch.d)
     _, N, _ = patch.eval(un[i:i + 1], vn[i:i + 1])
     return N[:, 0] / np.linalg.norm(N[:, 0])
@@ -115,6 +120,7 @@ class LeafCache:
         self.memo = {}
 
     def get(self, path, T):
+        """Leaf-rule geometry of sub-triangle T (path: its position in the Sec. 4.3 tree)."""
         if path not in self.memo:
             u, v, w = rules.map_rule(T, *self.rule)
             X, N, K = self.patch.eval_rel(u, v)

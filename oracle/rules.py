@@ -28,6 +28,8 @@ from . import koornwinder as kw
 
 
 def gauss_legendre01(n: int):
+    """Textbook n-point Gauss-Legendre rule moved to [0, 1] (a building block of the smooth
+    and self rules that stand in for the tables of Sec. 2.2)."""
     x, w = roots_legendre(n)
     return (x + 1.0) / 2.0, w / 2.0
 
@@ -57,7 +59,8 @@ def vals_to_coefs(d: int) -> np.ndarray:
 
 
 def interp_weights(d: int) -> np.ndarray:
-    """Interpolatory weights w_l of the node set: w = V^T m, m_(nm) = integral of K_nm = delta/sqrt(2)."""
+    """Interpolatory weights w_l of the node set (the quadrature use of the nodes, Sec. 2.2):
+    w = V^T m, m_(nm) = integral of K_nm = delta/sqrt(2)."""
     V = vals_to_coefs(d)
     mom = np.zeros(V.shape[0])
     mom[0] = 1.0 / np.sqrt(2.0)
@@ -70,7 +73,9 @@ def norm_V(d: int) -> float:
 
 
 def conical_rule(m: int):
-    """Smooth rule of the family, m^2 nodes, exact to total degree 2m-1.
+    """Smooth rule of the family, m^2 nodes, exact to total degree 2m-1: the stand-in for
+    the order-q rules of Sec. 2.2 and 4.2 (their tables are not printed), a Stroud
+    conical product.
 
     Integral over T0 of f = int_0^1 int_0^1 f(b(1-a), a) (1-a) db da.
     """
@@ -143,7 +148,9 @@ SELF_XI_PANEL = 1.5
 
 
 def default_self_order(eps: float) -> int:
-    """n_s = n_t of the self rule for precision eps: ceil(1.2 digits) + 3, within [6, 24]."""
+    """n_s = n_t of the self rule for precision eps: ceil(1.2 digits) + 3, within [6, 24]
+    (the self rules of Sec. 4 come from tables the paper does not print; this order is
+    this oracle's choice, shared with the library)."""
     digits = -np.log10(min(max(eps, 1e-15), 1e-1))
     return int(min(24, max(6, int(np.ceil(1.2 * digits - 1e-9)) + 3)))
 
@@ -159,7 +166,8 @@ def subdivide(T):
 
 
 def map_rule(T, ru, rv, rw):
-    """Push a T0 rule onto the sub-triangle T = (a, b, c) of T0: y = a + s(b-a) + t(c-a)."""
+    """Push a T0 rule onto the sub-triangle T = (a, b, c) of T0: y = a + s(b-a) + t(c-a)
+    (the rules on the descendants of Sec. 4.3)."""
     a, b, c = T
     e1, e2 = b - a, c - a
     det = abs(e1[0] * e2[1] - e1[1] * e2[0])

@@ -25,6 +25,8 @@ from . import rules
 
 
 def solid_angle(x, A, B, C):
+    """Signed solid angle of the flat triangle (A, B, C) seen from x, in closed form (Van
+    Oosterom and Strackee): a pin of the Laplace double layer, not a step of the paper."""
     R1, R2, R3 = A - x, B - x, C - x
     r1, r2, r3 = np.linalg.norm(R1), np.linalg.norm(R2), np.linalg.norm(R3)
     num = np.dot(R1, np.cross(R2, R3))
@@ -33,12 +35,14 @@ def solid_angle(x, A, B, C):
 
 
 def laplace_dl_flat(x, A, B, C):
-    """int_T n.grad_y (1/(4 pi |x-y|)) dA, n oriented by (B-A) x (C-A)."""
+    """int_T n.grad_y (1/(4 pi |x-y|)) dA, n oriented by (B-A) x (C-A): the k = 0 double
+    layer of Sec. 3 over a flat triangle, in closed form from the solid angle."""
     return -solid_angle(np.asarray(x, float), A, B, C) / (4.0 * np.pi)
 
 
 def flat_single_layer(x, A, B, C):
-    """int_T 1/(4 pi |x-y|) dA for a flat triangle T = (A, B, C) and any point x."""
+    """int_T 1/(4 pi |x-y|) dA for a flat triangle T = (A, B, C) and any point x: the k = 0
+    single layer of Sec. 3, radial part in closed form (module docstring)."""
     x = np.asarray(x, float)
     n = np.cross(B - A, C - A)
     n = n / np.linalg.norm(n)
@@ -68,6 +72,8 @@ def flat_single_layer(x, A, B, C):
 
 
 def _collapsed_gl(m):
+    """Collapsed (Duffy) Gauss-Legendre product rule on T0, independent of the scheme
+    oracle's conical rules (a textbook construction)."""
     a, wa = roots_legendre(m)
     a = (a + 1) / 2
     wa = wa / 2
@@ -78,7 +84,8 @@ def _collapsed_gl(m):
 
 
 def moments_adaptive(patch, x, kern, rtol=1e-15, m=14, max_level=14):
-    """I_nm(x) for a target off the patch, by adaptive midpoint subdivision (depth first).
+    """I_nm(x) (the Sec. 4.2 moments) for a target off the patch, to near machine
+    precision, by adaptive midpoint subdivision (depth first) with an independent rule.
 
     A triangle is accepted when its children agree with it to rtol * |I_T0| (absolute,
     independent of the level), so the total error is below (#leaves) rtol |I_T0|."""
@@ -104,7 +111,8 @@ def moments_adaptive(patch, x, kern, rtol=1e-15, m=14, max_level=14):
 
 
 def _graded_panels(length, mu, ratio=0.2):
-    """Panels of [0, length] graded geometrically toward 0, finest ~ mu*1e-2."""
+    """Panels of [0, length] graded geometrically toward 0, finest ~ mu*1e-2 (textbook
+    graded quadrature for the near-singular direction of the self integrals of Sec. 4)."""
     edges = [length]
     while edges[-1] > max(mu * 1e-2, 1e-14 * length):
         edges.append(edges[-1] * ratio)
@@ -113,7 +121,8 @@ def _graded_panels(length, mu, ratio=0.2):
 
 
 def moments_self(patch, i, x, kern, ns=40, nt=24):
-    """I_nm at node i: affine-conformal change of variables at the node (G^{-1/2} from
+    """I_nm (Sec. 4.2 moments) at node i, the self integral, to near machine precision:
+    affine-conformal change of variables at the node (G^{-1/2} from
     the closed-form 2x2 square root), Duffy split at the node, Gauss-Legendre in s and
     geometrically graded Gauss-Legendre panels in t."""
     from . import koornwinder as kw
@@ -158,10 +167,14 @@ def moments_self(patch, i, x, kern, ns=40, nt=24):
 
 
 def sphere_eigen_S(n, k):
+    """Eigenvalue of the single layer S_k of Sec. 3 on the unit sphere for spherical
+    harmonics of degree n, in closed form: i k j_n(k) h_n(k)."""
     h = spherical_jn(n, k) + 1j * spherical_yn(n, k)
     return 1j * k * spherical_jn(n, k) * h
 
 
 def sphere_eigen_D(n, k):
+    """Eigenvalue of the double layer D_k of Sec. 3 (principal value, outward normal) on the
+    unit sphere for degree-n harmonics, in closed form: i k^2 j_n(k) h_n'(k) + 1/2."""
     hp = spherical_jn(n, k, derivative=True) + 1j * spherical_yn(n, k, derivative=True)
     return 1j * k * k * spherical_jn(n, k) * hp + 0.5
