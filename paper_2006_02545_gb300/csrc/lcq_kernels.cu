@@ -61,6 +61,7 @@ __global__ void k_scan_block(const int64_t* __restrict__ in, int64_t* __restrict
   if (i < n) out[i] = s[threadIdx.x] - x;
   if (threadIdx.x == 1023) bsum[blockIdx.x] = s[1023];
 }
+// Second pass: adds the scanned block sums to each block's entries.
 __global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ boff) {
   const int64_t i = blockIdx.x * 1024ll + threadIdx.x;
   if (i < n) out[i] += boff[blockIdx.x];
@@ -152,6 +153,8 @@ __global__ void __launch_bounds__(kThreads) k_far_sum(const double* __restrict__
   if (t < NT) out[t] = {re, im};
 }
 
+// The correction part of the corrected potential (Sec. 5.3): warp per target row,
+// out_t += sum_row c sigma, plus jump * sigma at an on-surface target's own node.
 __global__ void k_csr_apply(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                             const double* __restrict__ val, const cplx* __restrict__ sigma,
                             const int64_t* __restrict__ tnode, int64_t NT, double jump,

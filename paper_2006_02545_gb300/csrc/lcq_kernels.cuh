@@ -376,6 +376,8 @@ struct SelfSeg {
   int npan, off;
 };
 
+// Block per self target: the self rule above applied to the chart, contracted with the
+// basis into the target's self weights (Sec. 4).
 template <int D>
 __global__ void __launch_bounds__(128) k_self(Dev dv, const int32_t* __restrict__ deg_of_patch,
                                               const KernelParams kp, int order,

@@ -123,6 +123,7 @@ __global__ void k_tgt_group(int64_t NT, const int32_t* __restrict__ tpatch,
   }
 }
 
+// Surface of each patch of a batch, from the surfaces' patch ranges.
 __global__ void k_patch_group(const int64_t* __restrict__ gpatch_off, int G,
                               int32_t* __restrict__ pgroup) {
   for (int g = blockIdx.x; g < G; g += gridDim.x)
@@ -159,6 +160,8 @@ __global__ void k_grid_bounds(const double* __restrict__ cen, const double* __re
   }
 }
 
+// Counting sort of the patches into the grid cells by centroid: counts, then (after a
+// scan) the fill; the order within a cell is fixed later by the per-row sort.
 __global__ void k_cell_count(const double* __restrict__ cen, int64_t P, GridSpec g,
                              unsigned long long* __restrict__ cnt) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P;
@@ -166,6 +169,7 @@ __global__ void k_cell_count(const double* __restrict__ cen, int64_t P, GridSpec
     atomicAdd(&cnt[cell_of(g, cen, (int)j)], 1ull);
 }
 
+// Fill pass of the counting sort.
 __global__ void k_cell_fill(const double* __restrict__ cen, int64_t P, GridSpec g,
                             const int64_t* __restrict__ cell_ptr,
                             unsigned long long* __restrict__ cursor, int32_t* __restrict__ cell_patch) {

@@ -18,6 +18,7 @@ namespace {
 
 constexpr int kPeakThreads = 256;
 
+// FP64 FMA chains (the FP64 pipe's peak).
 template <int U>
 __global__ void k_peak_dfma(double* sink, int iters, double a, double b) {
   double x[U];
@@ -33,6 +34,7 @@ __global__ void k_peak_dfma(double* sink, int iters, double a, double b) {
   if (s == -1.2345) sink[blockIdx.x] = s;
 }
 
+// FP32 FMA chains (the FP32 pipe's peak).
 template <int U>
 __global__ void k_peak_ffma(float* sink, int iters, float a, float b) {
   float x[U];
