@@ -84,20 +84,30 @@ def test_sphere_eigenvalues_converge(kind):
 
 def test_sphere_adjoint_double_layer_eigenvalue_converges():
     """S' (normal derivative of S at the target) on the unit sphere with outward normals:
-    S'_k Y_0 = (i k^2 / 2)(j_0 h_0' + j_0' h_0) Y_0, the same eigenvalue as D there
-    (truth.sphere_eigen_D); the error of the full pipeline falls with the chart error."""
+    S'_k Y_n = (i k^2 / 2)(j_n h_n' + j_n' h_n) Y_n, which the Wronskian j_n h_n' - j_n' h_n
+    = i / k^2 makes the same eigenvalue as D's (truth.sphere_eigen_D), for n = 0, 1, 2 with
+    the densities Y_0 = 1, Y_1 = z, Y_2 = (3 z^2 - 1)/2; the error of the full pipeline
+    falls with the chart error.  For n >= 1 the potential has a tangential gradient, which
+    the error of the target normal (a derivative of the interpolated chart) multiplies at
+    first order, so those errors fall more slowly than D's (measured: 0.115, 0.034, 0.0078
+    for n = 1 at degrees 2, 4, 6, and 2.9e-4 on 80 degree-6 patches)."""
     k = 1.0
-    lam = truth.sphere_eigen_D(0, k)
-    errs = []
+    lam = {n: truth.sphere_eigen_D(n, k) for n in range(3)}
+    errs = {n: [] for n in range(3)}
     for sdiv, d in ((1, 2), (1, 4), (1, 6)):
         s = workloads.ellipsoid(sdiv, d)
         x, tn = workloads.onsurface_targets(s)
+        z = s.xyz[2] / np.linalg.norm(s.xyz, axis=0)
         p = C.Params(eps=1e-7, eta=1.25, test_dirs=workloads.test_directions(4))
         corr = C.gen_corrections(s.deg, s.node_off, s.xyz, x, tn, "Sp", k, params=p)
-        u = C.apply_corrected(corr, s.node_off, np.ones(s.n_points, complex), x, "Sp", k,
-                              tgt_node=tn)
-        errs.append(np.abs(u - lam).max() / abs(lam))
-    assert errs[1] < 0.2 * errs[0] and errs[2] < 0.2 * errs[1] and errs[2] < 3e-3, errs
+        for n, Y in enumerate((np.ones_like(z), z, 0.5 * (3 * z * z - 1))):
+            u = C.apply_corrected(corr, s.node_off, Y.astype(complex), x, "Sp", k, tgt_node=tn)
+            errs[n].append(np.abs(u - lam[n] * Y).max() / abs(lam[n]))
+    e = errs[0]
+    assert e[1] < 0.2 * e[0] and e[2] < 0.2 * e[1] and e[2] < 3e-3, (0, e)
+    for n in (1, 2):
+        e = errs[n]
+        assert e[1] < 0.4 * e[0] and e[2] < 0.3 * e[1] and e[2] < 1.5e-2, (n, e)
 
 
 def test_adjoint_double_layer_kernel_is_normal_derivative_of_single_layer():
